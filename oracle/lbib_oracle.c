@@ -1,0 +1,496 @@
+/*
+ * lbib_oracle.c -- plain, slow FP64 CPU oracle of the LBIBCell coupled step.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The CUDA product
+ * path never calls, links or includes anything here, and this file shares no
+ * code, header, table or constant generator with it.
+ *
+ * Every routine follows one passage of Tanaka, Sichau & Iber,
+ * "LBIBCell: a cell-based simulation environment for morphogenetic problems"
+ * (arXiv:1503.06726), written as directly as possible: naive loops over nodes
+ * and directions, a full copy for streaming, serial spreading in vertex order.
+ * Where the paper is silent or garbled the reading taken is stated beside the
+ * code.  Build: gcc -O2 -ffp-contract=off (no FMA contraction, so that the
+ * point-in-polygon decisions are taken in plain IEEE double everywhere).
+ *
+ * Lattice conventions: node (i,j) at position (i,j), linear index j*nx+i.
+ * Populations are stored as post-collision values f*_q(x) in planes q*N + idx;
+ * a step first streams (pulls) them, then collides.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int32_t nx, ny, bc_y;      /* bc_y: 0 periodic, 1 half-way bounce-back walls at y=-1/2, ny-1/2 */
+    int32_t n_species;
+    double tau, rho0;
+    double D[4], decay[4], react[4][4], src_rate[4];
+    int32_t forcing;           /* 0 Guo et al. 2002, 1 the paper's simple term (Eq. bgkequation) */
+    int32_t pad;
+} orc_params;
+
+/* D2Q9 velocities: v0 = 0; v1..v4 = (cos, sin)(pi(i-1)/2); v5..v8 the diagonals
+ * sqrt(2)(cos, sin)(pi(i-1)/2 + pi/4) (footnote to Eq. bgkequation; the
+ * printed bracket is misplaced, the diagonals are (1,1),(-1,1),(-1,-1),(1,-1)).
+ * Weights 4/9, 1/9, 1/36 (Sec. 6.1, after Eq. standardequilibrium). */
+static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+static double W9(int q) { return q == 0 ? 4.0 / 9.0 : (q < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+/* D2Q5: v0 = 0 and v1..v4 as above; weights 1/3 and 1/6 (Sec. 6.1, D2Q5). */
+static double W5(int q) { return q == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+
+static int wrap(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sec. 6.2, Eq. 1Dkernel: delta1D(r) = (1 + cos(pi |r| / 2)) / 4 for |r| <= 2. */
+double orc_delta1d(double r) {
+    double a = fabs(r);
+    if (a > 2.0) return 0.0;
+    return 0.25 * (1.0 + cos(M_PI * a / 2.0));
+}
+
+/* Lower-left node of the 4x4 support of a point at coordinate X: the nodes
+ * floor(X)-1 .. floor(X)+2 are the only ones with |node - X| <= 2 that can
+ * carry weight (at integer X the far node has r = 2 and weight 0). */
+static int support_base(double X) { return (int)floor(X) - 1; }
+
+/* ------------------------------------------------------------------------- */
+/* Polygon forces on the vertices.
+ * Hookean membrane springs (Sec. 3.2.3, BioSolverHookeanMembraneTension; the
+ * same spring form as Eq. celljunctionforce): for the edge from vertex l to
+ * its successor m, d = X_m - X_l, the force k_l (|d| - L0_l) d/|d| acts on l
+ * and its opposite on m.
+ * Internal pressure p (a term of the measured workloads, not of the paper):
+ * F_l = p dA/dX_l = (p/2) (y_{l+1} - y_{l-1}, x_{l-1} - x_{l+1}) for a CCW
+ * polygon of area A; it points outward.  F has shape (V, 2). */
+void orc_polygon_forces(int nc, const int32_t* off, const double* xy, const double* L0,
+                        const double* k, const double* p, double* F) {
+    int V = off[nc];
+    for (int l = 0; l < 2 * V; ++l) F[l] = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        int a = off[c], b = off[c + 1], n = b - a;
+        for (int t = 0; t < n; ++t) {
+            int l = a + t, m = a + (t + 1) % n;
+            double dx = xy[2 * m] - xy[2 * l];
+            double dy = xy[2 * m + 1] - xy[2 * l + 1];
+            double len = sqrt(dx * dx + dy * dy);
+            double s = k[l] * (len - L0[l]) / len;
+            F[2 * l] += s * dx;
+            F[2 * l + 1] += s * dy;
+            F[2 * m] -= s * dx;
+            F[2 * m + 1] -= s * dy;
+        }
+        for (int t = 0; t < n; ++t) {
+            int l = a + t, nx_ = a + (t + 1) % n, pv = a + (t + n - 1) % n;
+            F[2 * l] += 0.5 * p[c] * (xy[2 * nx_ + 1] - xy[2 * pv + 1]);
+            F[2 * l + 1] += 0.5 * p[c] * (xy[2 * pv] - xy[2 * nx_]);
+        }
+    }
+}
+
+/* Constant membrane tension, Eq. membraneforce (Sec. 3.2.3): for each vertex,
+ * phi_m times the sum of the unit vectors towards its two neighbours.  Added
+ * to F (does not clear it). */
+void orc_tension_forces(int nc, const int32_t* off, const double* xy, double phim, double* F) {
+    for (int c = 0; c < nc; ++c) {
+        int a = off[c], n = off[c + 1] - a;
+        for (int t = 0; t < n; ++t) {
+            int l = a + t, pv = a + (t + n - 1) % n, nx_ = a + (t + 1) % n;
+            double ax = xy[2 * pv] - xy[2 * l], ay = xy[2 * pv + 1] - xy[2 * l + 1];
+            double bx = xy[2 * nx_] - xy[2 * l], by = xy[2 * nx_ + 1] - xy[2 * l + 1];
+            double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
+            F[2 * l] += phim * (ax / la + bx / lb);
+            F[2 * l + 1] += phim * (ay / la + by / lb);
+        }
+    }
+}
+
+/* Per-cell polygon area by the shoelace formula, taken relative to the
+ * cell's first vertex (the same quantity, better conditioned for large
+ * coordinates) -- GeometryHandler::computeAreas, Sec. 3.3. */
+void orc_cell_areas(int nc, const int32_t* off, const double* xy, double* area) {
+    for (int c = 0; c < nc; ++c) {
+        int a = off[c], n = off[c + 1] - a;
+        double x0 = xy[2 * a], y0 = xy[2 * a + 1], s = 0.0;
+        for (int t = 0; t < n; ++t) {
+            int l = a + t, m = a + (t + 1) % n;
+            double xl = xy[2 * l] - x0, yl = xy[2 * l + 1] - y0;
+            double xm = xy[2 * m] - x0, ym = xy[2 * m + 1] - y0;
+            s += xl * ym - xm * yl;
+        }
+        area[c] = 0.5 * s;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Lattice labelling (Fig. 2: the domainID of the lattice nodes is set from
+ * the polygons).  Reading: a node belongs to a cell when its centre is inside
+ * the polygon by the crossing-number rule, half-open in y -- an edge a->b
+ * crosses the row of the node when (y_a <= y) != (y_b <= y), and counts when
+ * x < x_a + (y - y_a)(x_b - x_a)/(y_b - y_a).  On overlap the lower cell index
+ * wins.  Coordinates are unwrapped; the node index is taken modulo the
+ * periodic sizes, rows outside a walled domain are skipped.
+ * id[N]: 0 outside, c+1 inside cell c.  src[N]: src_flag of that cell. */
+void orc_rasterize(int nx, int ny, int bc_y, int nc, const int32_t* off, const double* xy,
+                   const uint8_t* src_flag, int32_t* id, uint8_t* src) {
+    long N = (long)nx * ny;
+    for (long t = 0; t < N; ++t) { id[t] = 0; src[t] = 0; }
+    for (int c = 0; c < nc; ++c) {
+        int a = off[c], n = off[c + 1] - a;
+        double xmin = xy[2 * a], xmax = xmin, ymin = xy[2 * a + 1], ymax = ymin;
+        for (int t = 1; t < n; ++t) {
+            double x = xy[2 * (a + t)], y = xy[2 * (a + t) + 1];
+            if (x < xmin) xmin = x;
+            if (x > xmax) xmax = x;
+            if (y < ymin) ymin = y;
+            if (y > ymax) ymax = y;
+        }
+        for (int J = (int)floor(ymin); J <= (int)ceil(ymax); ++J) {
+            if (bc_y == 1 && (J < 0 || J >= ny)) continue;
+            for (int I = (int)floor(xmin); I <= (int)ceil(xmax); ++I) {
+                double xn = (double)I, yn = (double)J;
+                int inside = 0;
+                for (int t = 0; t < n; ++t) {
+                    int l = a + t, m = a + (t + 1) % n;
+                    double xa = xy[2 * l], ya = xy[2 * l + 1], xb = xy[2 * m], yb = xy[2 * m + 1];
+                    if ((ya <= yn) != (yb <= yn)) {
+                        double xc = xa + (yn - ya) * (xb - xa) / (yb - ya);
+                        if (xn < xc) inside = !inside;
+                    }
+                }
+                if (!inside) continue;
+                long idx = (long)wrap(J, ny) * nx + wrap(I, nx);
+                if (id[idx] == 0) {
+                    id[idx] = c + 1;
+                    src[idx] = src_flag[c];
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Force spreading, Eq. forcedistribution with the 4x4 kernel of Eq. 1Dkernel:
+ * f(x) += F_l delta1D(x - X_l) delta1D(y - Y_l) (the two-dimensional kernel is
+ * the product of the 1-D kernel in each axis; the printed delta1D(r)delta1D(r)
+ * is read that way).  F_l is a per-vertex force, h = 1.  Serial, vertex
+ * order.  Adds into fx, fy. */
+void orc_spread(int nx, int ny, int bc_y, int nv, const double* xy, const double* F,
+                double* fx, double* fy) {
+    for (int l = 0; l < nv; ++l) {
+        double X = xy[2 * l], Y = xy[2 * l + 1];
+        int i0 = support_base(X), j0 = support_base(Y);
+        for (int b = 0; b < 4; ++b) {
+            int J = j0 + b;
+            if (bc_y == 1 && (J < 0 || J >= ny)) continue;
+            double wy = orc_delta1d((double)J - Y);
+            for (int a = 0; a < 4; ++a) {
+                int I = i0 + a;
+                double w = orc_delta1d((double)I - X) * wy;
+                long idx = (long)wrap(J, ny) * nx + wrap(I, nx);
+                fx[idx] += F[2 * l] * w;
+                fy[idx] += F[2 * l + 1] * w;
+            }
+        }
+    }
+}
+
+/* Velocity interpolation, Eq. conversion2: U_l = sum_x u(x) delta(x - X_l). */
+void orc_interp(int nx, int ny, int bc_y, int nv, const double* xy, const double* ux,
+                const double* uy, double* U) {
+    for (int l = 0; l < nv; ++l) {
+        double X = xy[2 * l], Y = xy[2 * l + 1];
+        int i0 = support_base(X), j0 = support_base(Y);
+        double sx = 0.0, sy = 0.0;
+        for (int b = 0; b < 4; ++b) {
+            int J = j0 + b;
+            if (bc_y == 1 && (J < 0 || J >= ny)) continue;
+            double wy = orc_delta1d((double)J - Y);
+            for (int a = 0; a < 4; ++a) {
+                int I = i0 + a;
+                double w = orc_delta1d((double)I - X) * wy;
+                long idx = (long)wrap(J, ny) * nx + wrap(I, nx);
+                sx += ux[idx] * w;
+                sy += uy[idx] * w;
+            }
+        }
+        U[2 * l] = sx;
+        U[2 * l + 1] = sy;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Streaming by pulling: the population q arriving at (i,j) left (i-cx, j-cy)
+ * after the previous collision (left-hand side of Eq. bgkequation).  With
+ * walls (reading c13: half-way bounce-back, the fluid walls are not described
+ * in the paper), a population whose source row lies outside the domain is the
+ * opposite population of the same node reflected back. */
+static double pull(const double* post, const int* opp, int q, int i, int j, int nx, int ny,
+                   int bc_y) {
+    long N = (long)nx * ny;
+    int si = wrap(i - CX[q], nx), sj = j - CY[q];
+    if (sj < 0 || sj >= ny) {
+        if (bc_y == 1) return post[(long)opp[q] * N + (long)j * nx + i];
+        sj = wrap(sj, ny);
+    }
+    return post[(long)q * N + (long)sj * nx + si];
+}
+
+/* One lattice update: stream, then collide (Sec. 6.1).
+ * Fluid, Eq. bgkequation with the equilibrium of Eq. standardequilibrium read
+ * as the standard second-order polynomial
+ *   f_eq = w rho [1 + 3 v.u + 9/2 (v.u)^2 - 3/2 u.u]   (c_s^2 = 1/3).
+ * Moments rho = sum f, rho u = sum f v.  The body force f(x) from the spread:
+ *   forcing 0 (Guo, Zheng & Shi 2002, the form the measured method uses):
+ *     u = (sum f v + F/2) / rho,
+ *     S_q = (1 - 1/(2 tau)) w_q [3 (v_q - u) + 9 (v_q.u) v_q] . F
+ *   forcing 1 (the paper's term, He 1997, F a force density):
+ *     u = sum f v / rho,  S_q = 3 w_q v_q . F
+ *   f*_q = f_q - (f_q - f_eq_q)/tau + S_q.
+ * Species s (D2Q5, Sec. 6.1): g_eq = phi w (1 + 3 v.u) with the fluid u,
+ *   phi = sum g, tau_D = 3 D + 1/2 (D = c_s^2 (tau_D - 1/2), c_s^2 = 1/3 for
+ *   weights 1/3, 1/6), g*_q = g_q - (g_q - g_eq_q)/tau_D + w_q R_s with the
+ *   reaction (reading c10: added after collision, evaluated on the
+ *   pre-collision phi of the same node)
+ *   R_s = sum_b react[s][b] phi_b - decay[s] phi_s + src_rate[s] [src bit s].
+ * Walls bounce species back too (zero flux).
+ * fpost_*: 9 planes of N; gpost_*: S*5 planes; fx, fy may be NULL (no force);
+ * rho, ux, uy, phi (S planes) may be NULL. */
+void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost_out,
+                      const double* gpost_in, double* gpost_out, const double* fx,
+                      const double* fy, const uint8_t* src, double* rho_out, double* ux_out,
+                      double* uy_out, double* phi_out) {
+    int nx = P->nx, ny = P->ny, S = P->n_species;
+    long N = (long)nx * ny;
+    double tau = P->tau;
+    static const int OPP5[5] = {0, 3, 4, 1, 2};
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long idx = (long)j * nx + i;
+            double f[9];
+            for (int q = 0; q < 9; ++q) f[q] = pull(fpost_in, OPP, q, i, j, nx, ny, P->bc_y);
+            double rho = 0.0, jx = 0.0, jy = 0.0;
+            for (int q = 0; q < 9; ++q) {
+                rho += f[q];
+                jx += f[q] * CX[q];
+                jy += f[q] * CY[q];
+            }
+            double Fx = fx ? fx[idx] : 0.0, Fy = fy ? fy[idx] : 0.0;
+            double ux, uy;
+            if (P->forcing == 0) {
+                ux = (jx + 0.5 * Fx) / rho;
+                uy = (jy + 0.5 * Fy) / rho;
+            } else {
+                ux = jx / rho;
+                uy = jy / rho;
+            }
+            double usq = ux * ux + uy * uy;
+            for (int q = 0; q < 9; ++q) {
+                double vu = CX[q] * ux + CY[q] * uy;
+                double feq = W9(q) * rho * (1.0 + 3.0 * vu + 4.5 * vu * vu - 1.5 * usq);
+                double Sq;
+                if (P->forcing == 0)
+                    Sq = (1.0 - 0.5 / tau) * W9(q) *
+                         (3.0 * ((CX[q] - ux) * Fx + (CY[q] - uy) * Fy) +
+                          9.0 * vu * (CX[q] * Fx + CY[q] * Fy));
+                else
+                    Sq = 3.0 * W9(q) * (CX[q] * Fx + CY[q] * Fy);
+                fpost_out[(long)q * N + idx] = f[q] - (f[q] - feq) / tau + Sq;
+            }
+            if (rho_out) rho_out[idx] = rho;
+            if (ux_out) ux_out[idx] = ux;
+            if (uy_out) uy_out[idx] = uy;
+
+            double g[4][5], phi[4];
+            for (int s = 0; s < S; ++s) {
+                phi[s] = 0.0;
+                for (int q = 0; q < 5; ++q) {
+                    g[s][q] = pull(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny, P->bc_y);
+                    phi[s] += g[s][q];
+                }
+            }
+            for (int s = 0; s < S; ++s) {
+                double R = -P->decay[s] * phi[s];
+                for (int b = 0; b < S; ++b) R += P->react[s][b] * phi[b];
+                if (src && ((src[idx] >> s) & 1)) R += P->src_rate[s];
+                double tauD = 3.0 * P->D[s] + 0.5;
+                for (int q = 0; q < 5; ++q) {
+                    double vu = CX[q] * ux + CY[q] * uy;
+                    double geq = phi[s] * W5(q) * (1.0 + 3.0 * vu);
+                    gpost_out[((long)s * 5 + q) * N + idx] =
+                        g[s][q] - (g[s][q] - geq) / tauD + W5(q) * R;
+                }
+                if (phi_out) phi_out[(long)s * N + idx] = phi[s];
+            }
+        }
+    }
+}
+
+/* Species-only update with a frozen velocity field (u = 0 when ux, uy are
+ * NULL): the D2Q5 part of orc_lattice_step, used by the steady solve. */
+void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost_out,
+                      const double* ux_in, const double* uy_in, const uint8_t* src,
+                      double* phi_out) {
+    int nx = P->nx, ny = P->ny, S = P->n_species;
+    long N = (long)nx * ny;
+    static const int OPP5[5] = {0, 3, 4, 1, 2};
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long idx = (long)j * nx + i;
+            double ux = ux_in ? ux_in[idx] : 0.0, uy = uy_in ? uy_in[idx] : 0.0;
+            double g[4][5], phi[4];
+            for (int s = 0; s < S; ++s) {
+                phi[s] = 0.0;
+                for (int q = 0; q < 5; ++q) {
+                    g[s][q] = pull(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny, P->bc_y);
+                    phi[s] += g[s][q];
+                }
+            }
+            for (int s = 0; s < S; ++s) {
+                double R = -P->decay[s] * phi[s];
+                for (int b = 0; b < S; ++b) R += P->react[s][b] * phi[b];
+                if (src && ((src[idx] >> s) & 1)) R += P->src_rate[s];
+                double tauD = 3.0 * P->D[s] + 0.5;
+                for (int q = 0; q < 5; ++q) {
+                    double vu = CX[q] * ux + CY[q] * uy;
+                    double geq = phi[s] * W5(q) * (1.0 + 3.0 * vu);
+                    gpost_out[((long)s * 5 + q) * N + idx] =
+                        g[s][q] - (g[s][q] - geq) / tauD + W5(q) * R;
+                }
+                if (phi_out) phi_out[(long)s * N + idx] = phi[s];
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* The coupled time step, in the order of Fig. 1: from the geometry X^n the
+ * vertex forces F^n are computed and spread to the lattice; the fluid (and
+ * the species, which receive the fluid velocity and the cell labels) is
+ * advanced one step; the velocity u^n is interpolated back to the vertices
+ * and they move by forward Euler, X^{n+1} = X^n + U^n (first order explicit,
+ * Sec. 3.4).  Labels are recomputed from X^n at the start of each step.
+ *
+ * State in/out: xy (V,2), f (9 planes, post-collision), g (5S planes).
+ * Outputs of the last step (any may be NULL): rho, ux, uy, phi (S planes),
+ * id, src, fx, fy (the spread force), Fv (V,2 vertex forces).
+ * tension: constant membrane tension magnitude (0 = off). */
+int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const double* L0,
+            const double* k, const double* p, double tension, const uint8_t* src_flag,
+            int n_steps, double* f, double* g, double* rho, double* ux, double* uy, double* phi,
+            int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv) {
+    int nx = P->nx, ny = P->ny, S = P->n_species;
+    long N = (long)nx * ny;
+    int V = nc > 0 ? off[nc] : 0;
+    double* f2 = (double*)malloc(sizeof(double) * 9 * N);
+    double* g2 = (double*)malloc(sizeof(double) * (S > 0 ? 5 * S * N : 1));
+    double* Fx = (double*)malloc(sizeof(double) * N);
+    double* Fy = (double*)malloc(sizeof(double) * N);
+    double* Ux = (double*)malloc(sizeof(double) * N);
+    double* Uy = (double*)malloc(sizeof(double) * N);
+    double* F = (double*)malloc(sizeof(double) * 2 * (V > 0 ? V : 1));
+    double* U = (double*)malloc(sizeof(double) * 2 * (V > 0 ? V : 1));
+    int32_t* lid = (int32_t*)malloc(sizeof(int32_t) * N);
+    uint8_t* lsrc = (uint8_t*)malloc(N);
+    if (!f2 || !g2 || !Fx || !Fy || !Ux || !Uy || !F || !U || !lid || !lsrc) return -1;
+    double *fa = f, *fb = f2, *ga = g, *gb = g2;
+    for (int n = 0; n < n_steps; ++n) {
+        int last = (n == n_steps - 1);
+        orc_rasterize(nx, ny, P->bc_y, nc, off, xy, src_flag, lid, lsrc);
+        if (V > 0) {
+            orc_polygon_forces(nc, off, xy, L0, k, p, F);
+            if (tension != 0.0) orc_tension_forces(nc, off, xy, tension, F);
+        }
+        for (long t = 0; t < N; ++t) { Fx[t] = 0.0; Fy[t] = 0.0; }
+        if (V > 0) orc_spread(nx, ny, P->bc_y, V, xy, F, Fx, Fy);
+        orc_lattice_step(P, fa, fb, ga, gb, Fx, Fy, lsrc, last ? rho : NULL, Ux, Uy,
+                         last ? phi : NULL);
+        if (V > 0) {
+            orc_interp(nx, ny, P->bc_y, V, xy, Ux, Uy, U);
+            if (last && Fv) memcpy(Fv, F, sizeof(double) * 2 * V);
+            for (int l = 0; l < 2 * V; ++l) xy[l] += U[l];
+        }
+        if (last) {
+            if (ux) memcpy(ux, Ux, sizeof(double) * N);
+            if (uy) memcpy(uy, Uy, sizeof(double) * N);
+            if (id) memcpy(id, lid, sizeof(int32_t) * N);
+            if (src) memcpy(src, lsrc, N);
+            if (fx) memcpy(fx, Fx, sizeof(double) * N);
+            if (fy) memcpy(fy, Fy, sizeof(double) * N);
+        }
+        double* t;
+        t = fa; fa = fb; fb = t;
+        t = ga; ga = gb; gb = t;
+    }
+    if (fa != f) memcpy(f, fa, sizeof(double) * 9 * N);
+    if (S > 0 && ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
+    free(f2); free(g2); free(Fx); free(Fy); free(Ux); free(Uy); free(F); free(U);
+    free(lid); free(lsrc);
+    return 0;
+}
+
+/* Steady morphogen solve on a static labelling with u = 0: repeat the D2Q5
+ * update until the residual r = max|phi^{n+1} - phi^n| / max|phi^{n+1}|
+ * (reading c20 of the undefined "resid"), checked every `check_every` steps
+ * on the last step pair, is <= tol, or max_steps is reached.
+ * g (5S planes) in/out; phi (S planes) out; returns the steps taken. */
+long orc_steady(const orc_params* P, const uint8_t* src, double* g, double tol, long max_steps,
+                int check_every, double* phi, double* resid_out) {
+    int S = P->n_species;
+    long N = (long)P->nx * P->ny;
+    double* g2 = (double*)malloc(sizeof(double) * 5 * S * N);
+    double* p0 = (double*)malloc(sizeof(double) * S * N);
+    double* p1 = (double*)malloc(sizeof(double) * S * N);
+    double *ga = g, *gb = g2;
+    double r = INFINITY;
+    long n = 0;
+    while (n < max_steps) {
+        int check = ((n + 1) % check_every) == 0;
+        orc_species_step(P, ga, gb, NULL, NULL, src, p0);
+        double* t = ga; ga = gb; gb = t;
+        ++n;
+        if (check) {
+            /* phi^{n+1}: the zeroth moment of the populations just streamed */
+            orc_species_step(P, ga, gb, NULL, NULL, src, p1);
+            double dmax = 0.0, pmax = 0.0;
+            for (long x = 0; x < S * N; ++x) {
+                double d = fabs(p1[x] - p0[x]);
+                if (d > dmax) dmax = d;
+                if (fabs(p1[x]) > pmax) pmax = fabs(p1[x]);
+            }
+            r = pmax > 0.0 ? dmax / pmax : (dmax > 0.0 ? INFINITY : 0.0);
+            if (r <= tol) break;
+        }
+    }
+    /* phi of the final state */
+    orc_species_step(P, ga, gb, NULL, NULL, src, phi);
+    if (ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
+    free(g2); free(p0); free(p1);
+    if (resid_out) *resid_out = r;
+    return n;
+}

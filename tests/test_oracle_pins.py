@@ -1,0 +1,501 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden), closed forms, exact conservation budgets of the
+scheme, energy gradients taken by finite differences, and brute-force
+geometry on tiny inputs.  They are chosen so that a dropped term, a wrong
+sign or index, or a transposed operand in the oracle fails at least one.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lbib_inputs as li
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_lattices():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "paper_lattices.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        lat, q, cx, cy, wn, wd = line.split()
+        rows.setdefault(lat, []).append((int(q), int(cx), int(cy), int(wn) / int(wd)))
+    return rows
+
+
+def _params(nx, ny, tau=1.0, bc=li.BC_PERIODIC, S=0, forcing=0):
+    p = li.LatticeParams(nx=nx, ny=ny, bc_y=bc, tau=tau, n_species=S, forcing=forcing)
+    return p
+
+
+# ---------------------------------------------------------------- delta kernel
+def test_delta_golden_values(orc):
+    """Eq. 1Dkernel evaluated at closed-form points (tests/golden/delta_kernel.txt)."""
+    for line in open(os.path.join(GOLDEN, "delta_kernel.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        r, expr = line.split(None, 1)
+        want = eval(expr.strip(), {"sqrt": math.sqrt})
+        assert orc.delta1d(float(r)) == pytest.approx(want, abs=1e-15)
+
+
+def test_delta_partition_of_unity_and_second_moment(orc):
+    """Sum over the integer nodes of delta1D(j - x) is 1 for every x, the even
+    and odd node sums are 1/2 each, and the sum of squares is 3/8: the
+    discrete moment conditions that make the cosine kernel a regularised
+    delta (Sec. 2.2, Sec. 6.2)."""
+    for x in np.linspace(-3.0, 3.0, 97):
+        js = np.arange(math.floor(x) - 3, math.floor(x) + 4)
+        w = np.array([orc.delta1d(j - x) for j in js])
+        assert w.sum() == pytest.approx(1.0, abs=1e-14)
+        assert w[js % 2 == 0].sum() == pytest.approx(0.5, abs=1e-14)
+        assert (w * w).sum() == pytest.approx(3.0 / 8.0, abs=1e-14)
+        assert np.count_nonzero(w > 1e-300) <= 4
+
+
+# ---------------------------------------------------------------- polygons
+def _regular(n, R, cx=10.0, cy=7.0, phase=0.0):
+    a = 2 * math.pi * np.arange(n) / n + phase
+    return np.stack([cx + R * np.cos(a), cy + R * np.sin(a)], 1)
+
+
+def test_regular_polygon_pressure_and_area(orc):
+    """Regular N-gon at rest length: only pressure acts, radially outward with
+    magnitude p R sin(2 pi / N); the area is (N/2) R^2 sin(2 pi / N)."""
+    n, R, p = 64, 12.0, 1e-3
+    xy = _regular(n, R)
+    off = np.array([0, n], np.int32)
+    L0 = li.edge_lengths(off, xy)
+    F = orc.polygon_forces(off, xy, L0, np.full(n, 0.01), np.array([p]))
+    radial = (xy - np.array([10.0, 7.0])) / R
+    mag = np.einsum("ij,ij->i", F, radial)
+    assert np.allclose(mag, p * R * math.sin(2 * math.pi / n), rtol=1e-12)
+    tang = F - mag[:, None] * radial
+    assert np.abs(tang).max() < 1e-15
+    A = orc.cell_areas(off, xy)[0]
+    assert A == pytest.approx(0.5 * n * R * R * math.sin(2 * math.pi / n), rel=1e-13)
+
+
+def test_regular_polygon_stretched_springs(orc):
+    """Springs stretched uniformly by L - L0 pull each vertex of a regular
+    N-gon inward with magnitude 2 k (L - L0) sin(pi / N)."""
+    n, R, k = 40, 9.0, 0.02
+    xy = _regular(n, R, phase=0.3)
+    off = np.array([0, n], np.int32)
+    L = li.edge_lengths(off, xy)
+    L0 = 0.9 * L
+    F = orc.polygon_forces(off, xy, L0, np.full(n, k), np.array([0.0]))
+    radial = (xy - np.array([10.0, 7.0])) / R
+    mag = np.einsum("ij,ij->i", F, radial)
+    assert np.allclose(mag, -2 * k * (L - L0) * math.sin(math.pi / n), rtol=1e-12)
+
+
+def _energy(xy, off, L0, k, p):
+    E = 0.0
+    for c in range(len(off) - 1):
+        a, b = off[c], off[c + 1]
+        P = xy[a:b]
+        d = np.roll(P, -1, 0) - P
+        E += 0.5 * np.sum(k[a:b] * (np.hypot(d[:, 0], d[:, 1]) - L0[a:b]) ** 2)
+        x, y = P[:, 0], P[:, 1]
+        A = 0.5 * np.sum(x * np.roll(y, -1) - np.roll(x, -1) * y)
+        E -= p[c] * A
+    return E
+
+
+def test_forces_are_minus_energy_gradient(orc):
+    """Spring plus pressure forces equal -dE/dX for
+    E = sum_l k_l/2 (|d_l| - L0_l)^2 - sum_c p_c A_c (central differences),
+    on jittered two-cell tissues: pins both the sign and the partner vertex of
+    every term."""
+    rng = np.random.default_rng(5)
+    xy = np.concatenate([_regular(7, 3.0, 0, 0), _regular(5, 2.0, 9, 1)])
+    xy += rng.uniform(-0.3, 0.3, xy.shape)
+    off = np.array([0, 7, 12], np.int32)
+    L0 = li.edge_lengths(off, xy) * rng.uniform(0.8, 1.2, 12)
+    k = rng.uniform(0.01, 0.05, 12)
+    p = np.array([2e-3, -1e-3])
+    F = orc.polygon_forces(off, xy, L0, k, p)
+    h = 1e-6
+    G = np.zeros_like(xy)
+    for i in range(xy.shape[0]):
+        for d in range(2):
+            xp = xy.copy(); xp[i, d] += h
+            xm = xy.copy(); xm[i, d] -= h
+            G[i, d] = (_energy(xp, off, L0, k, p) - _energy(xm, off, L0, k, p)) / (2 * h)
+    assert np.allclose(F, -G, atol=1e-9)
+    assert np.abs(F.sum(0)).max() < 1e-15
+
+
+def test_tension_is_minus_perimeter_gradient(orc):
+    """Eq. membraneforce: constant tension phi_m gives F = -phi_m dP/dX with
+    P the perimeter (central differences)."""
+    rng = np.random.default_rng(6)
+    xy = _regular(9, 4.0) + rng.uniform(-0.4, 0.4, (9, 2))
+    off = np.array([0, 9], np.int32)
+    zero = np.zeros(9)
+    F = orc.polygon_forces(off, xy, zero, zero, np.array([0.0]), tension=0.7)
+
+    def per(z):
+        d = np.roll(z, -1, 0) - z
+        return np.hypot(d[:, 0], d[:, 1]).sum()
+
+    h = 1e-6
+    for i in range(9):
+        for d in range(2):
+            xp = xy.copy(); xp[i, d] += h
+            xm = xy.copy(); xm[i, d] -= h
+            assert F[i, d] == pytest.approx(-0.7 * (per(xp) - per(xm)) / (2 * h), abs=1e-8)
+
+
+def test_area_sign_and_translation(orc):
+    sq = np.array([[0.0, 0.0], [2.0, 0.0], [2.0, 3.0], [0.0, 3.0]])
+    off = np.array([0, 4], np.int32)
+    assert orc.cell_areas(off, sq)[0] == 6.0
+    assert orc.cell_areas(off, sq[::-1].copy())[0] == -6.0
+    assert orc.cell_areas(off, sq + 1234.5)[0] == pytest.approx(6.0, abs=1e-12)
+
+
+# ---------------------------------------------------------------- rasterisation
+def _inside_halfplanes(P, x, y):
+    """Brute force for a convex CCW polygon: inside iff strictly left of every
+    edge (points within 1e-9 of an edge are reported as ambiguous)."""
+    d = np.roll(P, -1, 0) - P
+    cr = d[:, 0] * (y - P[:, 1]) - d[:, 1] * (x - P[:, 0])
+    ln = np.hypot(d[:, 0], d[:, 1])
+    if np.any(np.abs(cr) / ln < 1e-9):
+        return None
+    return bool(np.all(cr > 0))
+
+
+def test_rasterize_convex_bruteforce(orc):
+    rng = np.random.default_rng(7)
+    nx = ny = 32
+    for trial in range(20):
+        n = int(rng.integers(3, 12))
+        R = rng.uniform(2, 9)
+        P = _regular(n, R, rng.uniform(10, 22), rng.uniform(10, 22), rng.uniform(0, 6.3))
+        off = np.array([0, n], np.int32)
+        idp, src = orc.rasterize(nx, ny, 0, off, P, np.array([5], np.uint8))
+        for j in range(ny):
+            for i in range(nx):
+                want = _inside_halfplanes(P, float(i), float(j))
+                if want is None:
+                    continue
+                assert (idp[j, i] == 1) == want, (trial, i, j)
+                assert src[j, i] == (5 if want else 0)
+
+
+def test_rasterize_periodic_shift_and_overlap(orc):
+    """Integer shifts across the periodic boundary roll the labels; where two
+    polygons overlap, the lower cell index wins."""
+    nx, ny = 24, 20
+    P = _regular(8, 5.0, 12.3, 9.7, 0.2)
+    off = np.array([0, 8], np.int32)
+    base, _ = orc.rasterize(nx, ny, 0, off, P, np.array([1], np.uint8))
+    shifted, _ = orc.rasterize(nx, ny, 0, off, P + np.array([17.0, 13.0]), np.array([1], np.uint8))
+    assert np.array_equal(np.roll(np.roll(base, 13, 0), 17, 1), shifted)
+    two = np.concatenate([P, P + np.array([3.0, 0.0])])
+    off2 = np.array([0, 8, 16], np.int32)
+    idp, src = orc.rasterize(nx, ny, 0, off2, two, np.array([1, 2], np.uint8))
+    a, _ = orc.rasterize(nx, ny, 0, off, P, np.array([1], np.uint8))
+    b, _ = orc.rasterize(nx, ny, 0, off, P + np.array([3.0, 0.0]), np.array([1], np.uint8))
+    assert np.array_equal(idp == 1, a == 1)
+    assert np.array_equal(idp == 2, (b == 1) & (a == 0))
+    assert np.array_equal(src, np.where(idp == 1, 1, np.where(idp == 2, 2, 0)))
+
+
+def test_rasterize_walls_drop_rows(orc):
+    P = _regular(12, 4.0, 10.0, 1.0)
+    off = np.array([0, 12], np.int32)
+    per, _ = orc.rasterize(16, 16, 0, off, P, np.array([1], np.uint8))
+    wal, _ = orc.rasterize(16, 16, 1, off, P, np.array([1], np.uint8))
+    assert np.array_equal(wal[:8], per[:8])
+    assert wal[8:].sum() == 0 and per[13:].sum() > 0
+
+
+# ---------------------------------------------------------------- spread / interp
+def test_spread_total_and_adjointness(orc):
+    rng = np.random.default_rng(8)
+    nx, ny = 20, 18
+    xy = rng.uniform(-5, 25, (30, 2))
+    F = rng.normal(size=(30, 2))
+    fx, fy = orc.spread(nx, ny, 0, xy, F)
+    assert fx.sum() == pytest.approx(F[:, 0].sum(), abs=1e-12)
+    assert fy.sum() == pytest.approx(F[:, 1].sum(), abs=1e-12)
+    ux, uy = rng.normal(size=(ny, nx)), rng.normal(size=(ny, nx))
+    U = orc.interp(nx, ny, 0, xy, ux, uy)
+    assert (fx * ux + fy * uy).sum() == pytest.approx((F * U).sum(), abs=1e-12)
+    # a constant field interpolates exactly (partition of unity)
+    U1 = orc.interp(nx, ny, 0, xy, np.full((ny, nx), 0.3), np.full((ny, nx), -2.0))
+    assert np.allclose(U1, [0.3, -2.0], atol=1e-14)
+
+
+def test_spread_single_point_weights(orc):
+    """One unit force at (5.25, 7.5): the node weights are the tensor product
+    delta1D(i - 5.25) delta1D(j - 7.5) over the 4x4 support, no other node."""
+    fx, fy = orc.spread(16, 16, 0, np.array([[5.25, 7.5]]), np.array([[1.0, 0.0]]))
+    for j in range(16):
+        for i in range(16):
+            di, dj = i - 5.25, j - 7.5
+            want = 0.0
+            if abs(di) <= 2 and abs(dj) <= 2:
+                want = 0.25 * (1 + math.cos(math.pi * di / 2)) * 0.25 * (1 + math.cos(math.pi * dj / 2))
+            assert fx[j, i] == pytest.approx(want, abs=1e-15)
+    assert np.count_nonzero(fx) == 16 and not fy.any()
+
+
+# ---------------------------------------------------------------- D2Q9 fluid
+def test_equilibrium_moments_match_paper_lattice(orc):
+    """With tau = 1 and no force the post-collision populations are the
+    equilibrium; its moments against the paper's printed velocities and
+    weights are rho, rho u and rho (I/3 + u u) (the second moment that
+    recovers Navier-Stokes)."""
+    lat = _golden_lattices()["D2Q9"]
+    c = np.array([[cx, cy] for _, cx, cy, _ in lat], float)
+    w = np.array([wt for *_, wt in lat])
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    nx = ny = 4
+    p = _params(nx, ny, tau=1.0)
+    rng = np.random.default_rng(9)
+    # uniform non-equilibrium populations with known moments
+    fin = w[:, None, None] * (1.0 + 0.05 * rng.uniform(-1, 1, (9, 1, 1))) * np.ones((9, ny, nx))
+    fo, _, rho, ux, uy, _ = orc.lattice_step(p, fin, np.zeros(1))
+    r = fin[:, 0, 0].sum()
+    u = (fin[:, 0, 0] @ c) / r
+    feq = fo[:, 0, 0]
+    assert feq.sum() == pytest.approx(r, abs=1e-15)
+    assert np.allclose(feq @ c, r * u, atol=1e-15)
+    Pi = np.einsum("q,qa,qb->ab", feq, c, c)
+    assert np.allclose(Pi, r * (np.eye(2) / 3 + np.outer(u, u)), atol=1e-15)
+    assert rho[0, 0] == pytest.approx(r) and ux[0, 0] == pytest.approx(u[0])
+
+
+def test_rest_state_fixed_point_and_conservation(orc):
+    nx, ny = 12, 10
+    p = _params(nx, ny, tau=0.8)
+    f, g = orc.equilibrium_state(p)
+    fo, *_ = orc.lattice_step(p, f, g)
+    assert np.abs(fo - f).max() < 1e-15
+    rng = np.random.default_rng(10)
+    f = f * (1 + 0.01 * rng.uniform(-1, 1, f.shape))
+    fx, fy = 1e-3 * rng.normal(size=(2, ny, nx))
+    for forcing in (0, 1):
+        p.forcing = forcing
+        fo, _, rho, ux, uy, _ = orc.lattice_step(p, f, g, fx, fy)
+        c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+        assert fo.sum() == pytest.approx(f.sum(), rel=1e-14)
+        mom_in = np.einsum("qji,qa->a", f, c)
+        mom_out = np.einsum("qji,qa->a", fo, c)
+        # each update adds exactly the total body force to the momentum
+        assert np.allclose(mom_out - mom_in, [fx.sum(), fy.sum()], atol=1e-14)
+
+
+def test_guo_velocity_includes_half_force(orc):
+    """Guo forcing: u = (sum f v + F/2)/rho, and the post-collision momentum
+    is rho u + F/2 at every node."""
+    nx, ny = 6, 5
+    p = _params(nx, ny, tau=0.7)
+    f, g = orc.equilibrium_state(p)
+    rng = np.random.default_rng(11)
+    fx, fy = 1e-2 * rng.normal(size=(2, ny, nx))
+    fo, _, rho, ux, uy, _ = orc.lattice_step(p, f, g, fx, fy)
+    assert np.allclose(ux, 0.5 * fx / rho, atol=1e-16)
+    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+    jx = np.einsum("qji,q->ji", fo, c[:, 0])
+    assert np.allclose(jx, rho * ux + 0.5 * fx, atol=1e-16)
+
+
+@pytest.mark.parametrize("tau", [0.5 + math.sqrt(3.0) / 4.0, 0.8])
+def test_poiseuille(orc, tau):
+    """Body-force-driven channel between half-way bounce-back walls: the
+    steady profile is a parabola with discrete curvature -g/nu; at
+    tau = 1/2 + sqrt(3)/4 it equals g/(2 nu) (y + 1/2)(ny - 1/2 - y)."""
+    nx, ny, gF = 4, 16, 1e-6
+    p = _params(nx, ny, tau=tau, bc=li.BC_WALLS)
+    nu = (tau - 0.5) / 3
+    f, g = orc.equilibrium_state(p)
+    fx = np.full((ny, nx), gF)
+    fy = np.zeros((ny, nx))
+    for _ in range(8000):
+        f, g, rho, ux, uy, _ = orc.lattice_step(p, f, g, fx, fy)
+    u = ux[:, 0]
+    y = np.arange(ny)
+    exact = gF / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    curv = u[2:] - 2 * u[1:-1] + u[:-2]
+    assert np.allclose(curv, -gF / nu, rtol=2e-5)
+    assert np.abs(uy).max() < 1e-13 * (1 + 0 * u.max())
+    if tau > 0.9:
+        assert np.abs(u - exact).max() < 1e-6 * exact.max()
+    else:
+        assert np.abs(u - exact).max() < 2e-2 * exact.max()
+
+
+def _taylor_green_error(orc, N, tau=0.8, u0=1e-3):
+    p = _params(N, N, tau=tau)
+    nu = (tau - 0.5) / 3
+    k = 2 * math.pi / N
+    x = np.arange(N)[None, :]
+    y = np.arange(N)[:, None]
+    ux = -u0 * np.cos(k * x) * np.sin(k * y)
+    uy = u0 * np.sin(k * x) * np.cos(k * y)
+    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    rho = 1.0 - 3 * u0 * u0 / 4 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    vu = c[:, 0, None, None] * ux + c[:, 1, None, None] * uy
+    f = w[:, None, None] * rho * (1 + 3 * vu + 4.5 * vu ** 2 - 1.5 * (ux ** 2 + uy ** 2))
+    # the stored state is post-collision: undo one streaming step so that the
+    # first pull sees the Taylor-Green equilibrium at t = 0
+    f = np.stack([np.roll(np.roll(f[q], -c[q, 1], 0), -c[q, 0], 1) for q in range(9)])
+    T = int(round(0.25 * N * N / (nu * 4 * math.pi ** 2)))  # fixed fraction of the decay time
+    g = np.zeros(1)
+    for _ in range(T + 1):
+        f, g, rho_o, ux_o, uy_o, _ = orc.lattice_step(p, f, g)
+    amp = np.sum(ux_o * ux) / np.sum(ux * ux)
+    return abs(amp - math.exp(-2 * nu * k * k * T)) / math.exp(-2 * nu * k * k * T)
+
+
+def test_taylor_green_decay_second_order(orc):
+    """Decaying Taylor-Green vortex: the amplitude follows exp(-2 nu k^2 t);
+    under diffusive scaling the relative error falls by about 4 per doubling
+    of N (second order, Sec. 3.4)."""
+    e16 = _taylor_green_error(orc, 16)
+    e32 = _taylor_green_error(orc, 32)
+    assert e32 < 1e-2
+    assert 3.0 < e16 / e32 < 5.0
+
+
+# ---------------------------------------------------------------- D2Q5 species
+def test_species_point_diffusion_variance_and_mass(orc):
+    """From a point source the total is conserved and the per-axis variance
+    grows by exactly 2D per step once the start-up transient has decayed."""
+    N, D = 81, 0.1
+    p = _params(N, N, S=1)
+    p.D[0] = D
+    g = np.zeros((5, N, N))
+    g[:, 40, 40] = np.array([1 / 3] + [1 / 6] * 4)
+    x = np.arange(N) - 40.0
+    var = []
+    for t in range(60):
+        g, phi = orc.species_step(p, g)
+        var.append(np.sum(phi[0] * x[None, :] ** 2) / phi[0].sum())
+        assert phi[0].sum() == pytest.approx(1.0, abs=1e-13)
+    assert var[-1] - var[-2] == pytest.approx(2 * D, abs=1e-12)
+
+
+def test_species_green_function_profile(orc):
+    """The point-source profile tends to (4 pi D t)^-1 exp(-r^2 / 4 D t)."""
+    N, D, T = 81, 0.15, 300
+    p = _params(N, N, S=1)
+    p.D[0] = D
+    g = np.zeros((5, N, N))
+    g[:, 40, 40] = np.array([1 / 3] + [1 / 6] * 4)
+    for _ in range(T):
+        g, phi = orc.species_step(p, g)
+    t = T - 0.5
+    r2 = (np.arange(N)[None, :] - 40.0) ** 2 + (np.arange(N)[:, None] - 40.0) ** 2
+    G = np.exp(-r2 / (4 * D * t)) / (4 * math.pi * D * t)
+    assert np.abs(phi[0] - G).max() < 2e-2 * G.max()
+
+
+def test_species_budget_decay_source_and_advection(orc):
+    """sum phi^{n+1} = (1 - k) sum phi^n + s |M| exactly on a fixed mask, and
+    with a uniform frozen velocity the centroid drifts at exactly u."""
+    N = 24
+    p = _params(N, N, S=1)
+    p.D[0], p.decay[0], p.src_rate[0] = 0.1, 2e-3, 1e-3
+    src = np.zeros((N, N), np.uint8)
+    src[5:9, 3:11] = 1
+    rng = np.random.default_rng(12)
+    g = rng.uniform(0, 1, (5, N, N))
+    prev = g.sum()
+    for _ in range(5):
+        g, phi = orc.species_step(p, g, src)
+        # phi is the moment of the pulled populations = the previous total
+        assert phi[0].sum() == pytest.approx(prev, rel=1e-14)
+        prev = (1 - 2e-3) * phi[0].sum() + 1e-3 * src.sum()
+    p.decay[0], p.src_rate[0] = 0.0, 0.0
+    M = 64
+    p.nx = p.ny = M
+    g = np.zeros((5, M, M))
+    g[:, 32, 32] = np.array([1 / 3] + [1 / 6] * 4)
+    ux = np.full((M, M), 0.02)
+    uy = np.full((M, M), -0.01)
+    cx = []
+    xs = np.arange(M)
+    for _ in range(80):
+        g, phi = orc.species_step(p, g, None, ux, uy)
+        cx.append(((phi[0] * xs[None, :]).sum(), (phi[0] * xs[:, None]).sum()))
+    assert cx[-1][0] - cx[-2][0] == pytest.approx(0.02, abs=1e-10)
+    assert cx[-1][1] - cx[-2][1] == pytest.approx(-0.01, abs=1e-10)
+
+
+def test_species_linear_reaction_uniform_closed_form(orc):
+    """Uniform fields: the D2Q5 update is exactly the explicit Euler map of
+    the reaction, phi^{n+1} = (I + K) phi^n + s; checked for the two-species
+    linear system of the 1024^2 workload against a matrix power."""
+    w = li.config2(nx=8, ny=8, n_cells_side=1)
+    p = w.params
+    p.bc_y = li.BC_PERIODIC
+    K = np.array(p.react)[:2, :2] - np.diag(p.decay[:2])
+    s = np.array([p.src_rate[0], 0.0])
+    g = np.zeros((10, 8, 8))
+    src = np.ones((8, 8), np.uint8)
+    phi_exact = np.zeros(2)
+    for n in range(30):
+        g, phi = orc.species_step(p, g, src)
+        assert np.allclose(phi[:, 3, 5], phi_exact, atol=1e-15)
+        phi_exact = phi_exact + K @ phi_exact + s
+
+
+def test_steady_uniform_closed_form(orc):
+    N = 16
+    p = _params(N, N, S=1)
+    p.D[0], p.decay[0], p.src_rate[0] = 0.1, 1e-2, 1e-3
+    src = np.ones((N, N), np.uint8)
+    phi, steps, r, _ = orc.steady(p, src, tol=1e-9)
+    assert r <= 1e-9
+    assert np.allclose(phi, 0.1, rtol=1e-6)
+    assert steps % 16 == 0
+
+
+# ---------------------------------------------------------------- coupled
+def test_coupled_invariants_config1(orc):
+    """Config-1 tissue, 40 coupled steps: periodic mass is conserved, the
+    total momentum stays at the (zero) accumulated net force, the species
+    budget closes step by step, and the vertices moved by the interpolated
+    velocity of the last step."""
+    w = li.config1()
+    p = w.params
+    f, g = orc.equilibrium_state(p)
+    xy = w.tissue.xy.copy()
+    m0 = f.sum()
+    tot_prev = 0.0
+    for n in range(40):
+        r = orc.run(p, w.tissue, 1, f=f, g=g, xy=xy)
+        assert r.f.sum() == pytest.approx(m0, rel=1e-13)
+        assert abs(r.Fv.sum(0)).max() < 1e-15
+        # phi of this step is the total after the previous update
+        assert r.phi[0].sum() == pytest.approx(tot_prev, abs=1e-13)
+        tot_prev = (1 - 1e-3) * r.phi[0].sum() + 1e-3 * (r.src > 0).sum()
+        U = orc.interp(p.nx, p.ny, p.bc_y, xy, r.ux, r.uy)
+        assert np.allclose(r.xy, xy + U, atol=1e-15)
+        f, g, xy = r.f, r.g, r.xy
+    c = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]])
+    assert np.abs(np.einsum("qji,qa->a", f, c)).max() < 1e-11
+
+
+def test_tension_cell_leaks_area(orc):
+    """A cell under constant membrane tension only loses area through the
+    immersed boundary (the leakage the paper reports in its Case IV)."""
+    w = li.scaled_config1(48, 10.0, 48, jitter=0.0)
+    T = w.tissue
+    T.pressure[:] = 0.0
+    T.k_spring[:] = 0.0
+    r = orc.run(w.params, T, 300, tension=2e-3)
+    a0 = orc.cell_areas(T.cell_off, T.xy)[0]
+    assert r.area[0] < a0 - 1e-3
