@@ -1,0 +1,358 @@
+"""Benchmark of the coupled LB-IB time step on GB300.
+
+Workload (default): the 1024^2 FP32 tissue -- no-slip walls in y, periodic
+x, tau 0.8, 400 hexagonally packed 100-vertex cells, two reacting D2Q5
+species -- one benchmark step = one coupled time step (labels, vertex
+forces, spreading, fused lattice update, interpolation and vertex update).
+
+Printed JSON line (rank 0):
+  value       MLUPS = lattice nodes x steps / device time of the K timed steps
+              (all ranks' nodes for N > 1, max time over ranks), inputs
+              resident in HBM, steps replayed from the library's CUDA graph;
+  roofline    the lattice-update kernel: algorithmic population bytes per
+              launch / its mean launch time (CUDA events on the context
+              stream, from a profiled pass of the same steps) against the
+              measured HBM copy peak;
+  e2e         MLUPS through the public C ABI from host buffers: every step
+              uploads the per-cell pressure and source flags from pinned host
+              memory, advances one step and reads the vertex positions and
+              cell areas back to pinned host memory;
+  cpu_baseline the FP64 oracle on the host cores on a bounded sample.
+
+--impl reference times the FP64 oracle (the reference arm of this build)
+on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import lbib_inputs as li  # noqa: E402
+
+METRIC = "coupled LB-IB MLUPS and % HBM peak; time-to-steady morphogen (warm vs cold) at resid 1e-6"
+UNIT = "MLUPS"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def alg_bytes_per_node(precision: str, n_species: int) -> int:
+    """Populations read once and written once per node and step."""
+    b = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    return 2 * 9 * b + 2 * 5 * n_species * b
+
+
+def workload(name: str):
+    if name == "c2":
+        return li.config2(), "fp32"
+    if name == "c3-fp32":
+        return li.config3(), "fp32"
+    if name == "c3-fp16":
+        return li.config3(), "fp16"
+    if name == "c3-fp64":
+        return li.config3(), "fp64"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def workload_config(w, precision, extra=None):
+    p = w.params
+    cfg = {
+        "workload": w.name,
+        "lattice": [p.nx, p.ny],
+        "bc_y": "walls" if p.bc_y else "periodic",
+        "tau": p.tau,
+        "cells": w.tissue.n_cells,
+        "vertices": w.tissue.n_vertices,
+        "species": p.n_species,
+        "storage": precision,
+        "vertex_precision": "fp64",
+        "seed": w.seed,
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of one GPU during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def lattice_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lattice.cu", "lbib_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1503_06726_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name: str):
+    """DRAM bytes per lattice launch from the committed ncu summary, if it
+    was taken on the current lattice kernel source."""
+    path = os.path.join(ROOT, "profiles", "lattice_kernel_traffic.json")
+    try:
+        d = json.load(open(path))
+        e = d.get(workload_name)
+        if e and e.get("kernel_sha") == lattice_kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def oracle_sample(w, target_s: float, max_steps: int, threads: int | None = None):
+    """Time the FP64 oracle on the workload: whole coupled steps until
+    target_s of CPU time or max_steps.  Returns (mlups, steps, seconds, cores)."""
+    import oracle
+    oracle.build()
+    if threads:
+        oracle.set_threads(threads)
+    cores = oracle.max_threads()
+    p, T = w.params, w.tissue
+    f, g = oracle.equilibrium_state(p)
+    xy = T.xy.copy()
+    steps, t0 = 0, time.perf_counter()
+    while steps < max_steps:
+        r = oracle.run(p, T, 1, f=f, g=g, xy=xy)
+        f, g, xy = r.f, r.g, r.xy
+        steps += 1
+        if time.perf_counter() - t0 >= target_s:
+            break
+    dt = time.perf_counter() - t0
+    return p.nx * p.ny * steps / dt / 1e6, steps, dt, cores
+
+
+# ------------------------------------------------------------------ arms
+def run_gb300(args, rank, world, dist):
+    import torch
+    from paper_1503_06726_gb300 import lbib
+
+    lbib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w, prec = workload(args.workload)
+    p, T = w.params, w.tissue
+    N = p.nx * p.ny
+    sim = lbib.Simulation(p, lbib.PRECISIONS[prec], T.n_vertices, T.n_cells, device=dev)
+    sim.set_cells(T)
+    stream = sim.stream
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dev.index if dev.index is not None else 0) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+
+    # profiled pass: the same steps, every launch bracketed by events
+    n_prof = max(10, min(args.steps, 400))
+    lat_ms, ib_ms = sim.step_profiled(n_prof)
+    lat_avg = lat_ms / n_prof
+    bpn = alg_bytes_per_node(prec, p.n_species)
+    alg_bytes = bpn * N
+    achieved = alg_bytes / (lat_avg * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    sh = sim.fields(lbib.LBIB_U)  # raises on non-finite state
+    assert np.isfinite(sh["ux"]).all()
+
+    # end-to-end through the C ABI with pinned host buffers
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    pin_p = torch.empty(T.n_cells, dtype=torch.float64).pin_memory()
+    pin_s = torch.empty(T.n_cells, dtype=torch.uint8).pin_memory()
+    pin_p.numpy()[:] = T.pressure
+    pin_s.numpy()[:] = T.src_flag
+    out_xy = torch.empty((T.n_vertices, 2), dtype=torch.float64).pin_memory()
+    out_area = torch.empty(T.n_cells, dtype=torch.float64).pin_memory()
+    L = lbib.load()
+    vp = ctypes.c_void_p
+    which = lbib.LBIB_X | lbib.LBIB_AREA
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        rc = L.lbib_set_cell_params(sim.ctx, vp(pin_p.data_ptr()), vp(pin_s.data_ptr()))
+        rc = rc or L.lbib_step(sim.ctx, 1)
+        rc = rc or L.lbib_get_fields(sim.ctx, which, None, None, None, None,
+                                     vp(out_xy.data_ptr()), vp(out_area.data_ptr()), None, None,
+                                     None)
+        if rc:
+            raise RuntimeError(lbib.lbib_last_error(sim.ctx))
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * N * e2e_steps / t_e2e / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": T.n_cells * 9, "d2h_bytes_per_step": T.n_vertices * 16 + T.n_cells * 8,
+           "steps": e2e_steps,
+           "api": "lbib_set_cell_params + lbib_step(1) + lbib_get_fields(X|AREA) per step"}
+    sim.close()
+
+    if rank != 0:
+        return None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        mlups, steps, dt, cores = oracle_sample(w, args.cpu_seconds, 60)
+        cpu = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{steps} coupled FP64 steps of {w.name} from rest ({dt:.1f} s)"}
+    ws = 2 * alg_bytes + N * (8 + 8 + 4)
+    rec = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
+        "data": "synthetic (seeded tissue generator)",
+        "config": workload_config(w, prec, {
+            "l2": f"inputs larger than L2: {ws / 2**20:.0f} MiB working set > 129 MiB L2, no flush",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "graph": "two-step CUDA graph chunks"}),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+                     "kernel": "lattice_kernel", "alg_bytes_per_launch": alg_bytes,
+                     "alg_bytes_per_node": bpn, "launch_ms": lat_avg,
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "ib_launch_ms": ib_ms / (n_prof + 1)},
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps + 1,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    return rec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w, prec = workload(args.workload)
+    p = w.params
+    # bounded sample: at most a minute of whole coupled oracle steps
+    max_steps = max(1, args.steps)
+    _, wsteps, _, _ = oracle_sample(w, 0.0, max(1, min(args.warmup, 1)))
+    mlups, steps, dt, cores = oracle_sample(w, args.ref_seconds, max_steps)
+    return {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": wsteps, "ms_per_step": dt / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded tissue generator)",
+        "config": workload_config(w, "fp64", {"implementation": "FP64 CPU oracle (plain C)"}),
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{steps} coupled FP64 steps of {w.name} from rest "
+                                   f"(bounded to {args.ref_seconds:.0f} s of {args.steps} asked)"},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        rec = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as tdist
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            tdist.init_process_group("nccl")
+            dist = tdist
+        rec = run_gb300(args, rank, world, dist)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+    if rec is not None:
+        print(json.dumps(rec), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * lbib.h -- C ABI of the GB300 (sm_103a) coupled lattice-Boltzmann /
+ * immersed-boundary step of LBIBCell (Tanaka, Sichau & Iber,
+ * arXiv:1503.06726).
+ *
+ * One context simulates one tissue on one GPU: a D2Q9 BGK fluid with a body
+ * force (Sec. 6.1, Eq. bgkequation, Eq. standardequilibrium), up to four
+ * D2Q5 advection-diffusion-reaction species that receive the fluid velocity
+ * (Sec. 6.1, D2Q5 scheme), and closed polygon cells whose vertex forces are
+ * spread to the lattice and whose vertices move with the interpolated fluid
+ * velocity (Sec. 6.2, Eq. forcedistribution, Eq. conversion2, Eq. 1Dkernel;
+ * the cycle of Fig. 1).
+ *
+ * Memory and threading rules common to every call:
+ *   - All device memory is owned by the caller.  lbib_workspace_size() says
+ *     how many bytes one context needs; the caller allocates them (any
+ *     allocator; 256-byte alignment) and passes the pointer to
+ *     lbib_create().  The library allocates no device memory of its own; it
+ *     only mallocs the small host-side context header.
+ *   - Host pointers passed in are read before the call returns; the caller
+ *     keeps ownership.  Host output buffers are caller-allocated.
+ *   - Work is enqueued on the CUDA stream given to lbib_create().
+ *     lbib_step() is asynchronous; lbib_set_*() and lbib_get_*() synchronise
+ *     that stream before they return.
+ *   - A context must not be used from two host threads at once.
+ *   - Every call returns LBIB_OK (0) or a negative LBIB_E_* code; no call
+ *     aborts or throws.  lbib_last_error() gives a one-line reason.
+ *
+ * Lattice conventions: node (i, j) sits at position (i, j), i along x.
+ * Fields returned to the host are dense nx*ny arrays, row-major in j (index
+ * j*nx + i), in double precision whatever the storage precision.
+ */
+#ifndef LBIB_H
+#define LBIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBIB_OK 0
+#define LBIB_E_PARAM (-1)       /* invalid parameter (size, tau <= 1/2, D <= 0, ...) */
+#define LBIB_E_WORKSPACE (-2)   /* workspace pointer NULL, misaligned or too small */
+#define LBIB_E_CELLS (-3)       /* invalid cell data (CSR, < 3 vertices, too many) */
+#define LBIB_E_NONFINITE (-4)   /* a non-finite density or velocity appeared */
+#define LBIB_E_TIMEOUT (-5)     /* a bounded device-side wait ran out */
+#define LBIB_E_CUDA (-6)        /* a CUDA runtime call failed */
+#define LBIB_E_STATE (-7)       /* call not valid in the context's current state */
+
+/* storage precision of the lattice populations */
+#define LBIB_FP64 0   /* FP64 storage, FP64 arithmetic */
+#define LBIB_FP32 1   /* FP32 storage of f - w rho0 (shifted), FP32 arithmetic */
+#define LBIB_FP16 2   /* FP16 storage of (f - w rho0)/(w sigma), FP32 arithmetic */
+
+/* body-force scheme */
+#define LBIB_GUO 0        /* Guo, Zheng & Shi 2002: u = (sum f v + F/2)/rho */
+#define LBIB_HE_PAPER 1   /* the paper's term of Eq. bgkequation, 3 w_i v_i.F */
+
+/* lbib_get_fields() selection bits */
+#define LBIB_RHO 1u
+#define LBIB_U 2u
+#define LBIB_PHI 4u
+#define LBIB_X 8u
+#define LBIB_AREA 16u
+#define LBIB_ID 32u
+#define LBIB_FORCE 64u
+#define LBIB_VFORCE 128u
+
+/* The global configuration of Sec. 3.1 (simulation size, viscosity through
+ * tau, diffusion coefficients) plus the reaction terms of the species.
+ *   nx, ny       lattice size (x periodic; y periodic or walls), >= 8 each
+ *   bc_y         0: periodic in y; 1: half-way bounce-back walls at y = -1/2
+ *                and y = ny - 1/2 for the fluid and the species
+ *   n_species    0..4 D2Q5 species
+ *   tau          fluid relaxation time (> 1/2); nu = (tau - 1/2)/3
+ *   rho0         reference density (initial state f = w rho0)
+ *   D[s]         diffusion coefficient of species s (> 0); tau_D = 3 D + 1/2
+ *   decay, react, src_rate: reaction rate of species s
+ *                R_s = sum_b react[s][b] phi_b - decay[s] phi_s
+ *                      + src_rate[s] * [the node lies in a cell whose
+ *                                       src_flag has bit s set]
+ *   forcing      LBIB_GUO or LBIB_HE_PAPER
+ *   precision    LBIB_FP64, LBIB_FP32 or LBIB_FP16
+ *   fp16_scale   sigma of the FP16 fluid storage (default 2^-10 when 0)
+ *   fp16_scale_species  sigma of the FP16 species storage g/(w sigma)
+ *                (default 2^-8 when 0)
+ *   tension      constant membrane tension phi_m of Eq. membraneforce added
+ *                to every vertex (0 = off)
+ *   body_force   uniform body force density (fx, fy) added at every node on
+ *                top of the spread cell forces (e.g. a channel driving force) */
+typedef struct lbib_params {
+    int32_t nx, ny, bc_y, n_species;
+    double tau, rho0;
+    double D[4], decay[4], react[4][4], src_rate[4];
+    int32_t forcing, precision;
+    double fp16_scale, fp16_scale_species;
+    double tension;
+    double body_force[2];
+} lbib_params;
+
+typedef struct lbib_ctx lbib_ctx;
+
+/* Bytes of device workspace one context needs for this lattice and at most
+ * max_vertices vertices in max_cells cells.  Returns LBIB_E_PARAM for invalid
+ * parameters. */
+int lbib_workspace_size(const lbib_params* params, int32_t max_vertices, int32_t max_cells,
+                        uint64_t* bytes_out);
+
+/* Create a context over a caller-owned device workspace of `bytes` bytes
+ * (256-byte aligned) and a CUDA stream (cudaStream_t passed as void*; NULL =
+ * the legacy default stream).  Populations start at rest, f = w rho0, g = 0.
+ * On success *out owns a small host header released by lbib_destroy(). */
+int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cells,
+                void* d_workspace, uint64_t bytes, void* cuda_stream, lbib_ctx** out);
+
+/* Load the geometry and force description of the cells (the geometry and
+ * force files of Sec. 3.1), all host arrays:
+ *   cell_off   n_cells+1 int32, CSR offsets of each cell's vertices
+ *   xy         2*V doubles, vertex positions (x, y), counter-clockwise per
+ *              cell (Fig. 2), unwrapped (may leave [0, nx) in periodic axes)
+ *   rest_len   V doubles, rest length of edge l -> next(l); NULL = the
+ *              current edge lengths
+ *   k_spring   V doubles, Hookean constant of edge l; NULL = 0
+ *   pressure   n_cells doubles, internal pressure p (force p dA/dX); NULL = 0
+ *   src_flag   n_cells bytes, bit s = the cell is a source of species s
+ * Cells need 3 .. 1024 vertices.  Replaces any previous cells. */
+int lbib_set_cells(lbib_ctx* ctx, int32_t n_cells, const int32_t* cell_off, const double* xy,
+                   const double* rest_len, const double* k_spring, const double* pressure,
+                   const uint8_t* src_flag);
+
+/* Update the per-cell pressure and source flags of the current cells (the
+ * inputs a host-side biology step changes between time steps).  Either
+ * pointer may be NULL to keep that array. */
+int lbib_set_cell_params(lbib_ctx* ctx, const double* pressure, const uint8_t* src_flag);
+
+/* Set the populations of species s to the rest equilibrium g_q = w_q phi of
+ * the host field phi (nx*ny doubles). */
+int lbib_set_species(lbib_ctx* ctx, int32_t s, const double* phi);
+
+/* Advance n_steps coupled time steps (Fig. 1): labels and vertex forces
+ * from X^n, spreading, one fused lattice update (stream, moments with the
+ * half-force velocity, BGK collision with the body force, all species with
+ * the same velocity and their reactions), interpolation of u^n and
+ * X^{n+1} = X^n + U^n.  Asynchronous on the context stream.  A non-finite
+ * density or velocity is reported by the next lbib_get_fields() as
+ * LBIB_E_NONFINITE. */
+int lbib_step(lbib_ctx* ctx, int32_t n_steps);
+
+/* Copy fields of the last completed step to host buffers (doubles unless
+ * stated), synchronising the stream.  `which` is a mask of LBIB_RHO (rho,
+ * nx*ny), LBIB_U (ux, uy), LBIB_PHI (phi, n_species*nx*ny), LBIB_X (xy,
+ * 2*V, the current vertex positions), LBIB_AREA (area, n_cells, FP64
+ * shoelace of the current polygons), LBIB_ID (id, nx*ny int32: 0 outside,
+ * c+1 inside cell c, as used by the last step), LBIB_FORCE (force, 2*nx*ny
+ * interleaved fx, fy spread in the last step) and LBIB_VFORCE (vforce, 2*V
+ * vertex forces of the last step).  Lattice fields need at least one step
+ * since create (else LBIB_E_STATE).  Unused pointers may be NULL. */
+int lbib_get_fields(lbib_ctx* ctx, uint32_t which, double* rho, double* ux, double* uy,
+                    double* phi, double* xy, double* area, int32_t* id, double* force,
+                    double* vforce);
+
+/* Run n_steps coupled steps like lbib_step(), launching each kernel
+ * directly (no graph) with CUDA events recorded on the context stream around
+ * every launch, and return the summed device time in milliseconds of the
+ * lattice-update launches in ms_out[0] and of the immersed-boundary launches
+ * in ms_out[1] (host array of 2).  Synchronises the stream. */
+int lbib_step_profiled(lbib_ctx* ctx, int32_t n_steps, double* ms_out);
+
+/* Number of vertices and cells currently loaded. */
+int lbib_get_sizes(const lbib_ctx* ctx, int32_t* n_vertices, int32_t* n_cells);
+
+/* Raw state snapshot (populations, vertices, cell data) for resume
+ * (Sec. 3.1: solver states can be saved and reloaded).  lbib_state_size()
+ * gives the byte count; get copies device state to `host`, set restores it
+ * into a context created with the same parameters and capacities. */
+int lbib_state_size(const lbib_ctx* ctx, uint64_t* bytes_out);
+int lbib_get_state(lbib_ctx* ctx, void* host, uint64_t bytes);
+int lbib_set_state(lbib_ctx* ctx, const void* host, uint64_t bytes);
+
+/* Release the host header (the workspace stays the caller's). */
+void lbib_destroy(lbib_ctx* ctx);
+
+/* One-line description of the last error on ctx (or of the last failed
+ * lbib_create when ctx is NULL). */
+const char* lbib_last_error(const lbib_ctx* ctx);
+
+/* Static name of a status code. */
+const char* lbib_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBIB_H */

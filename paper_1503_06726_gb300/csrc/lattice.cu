@@ -1,0 +1,305 @@
+// lattice.cu -- the fused lattice update of one coupled step (K1).
+//
+// One thread per lattice node, pull scheme: the kernel streams the
+// post-collision populations of the previous step from the neighbours
+// (left-hand side of Eq. bgkequation, Sec. 6.1), forms the moments, collides
+// the D2Q9 fluid with the BGK operator and the body force, and updates every
+// D2Q5 species with the same velocity and its reaction term, writing the new
+// post-collision populations to the other buffer.  The spread IB force and
+// the cell labels of the node are read and reset to their empty values in
+// the same pass, so no separate clearing pass is needed.
+//
+// Storage is SoA: one plane per population, rows of `pitch` elements, plane
+// q at q*plane.  Populations are stored as deviations from the rest state,
+// d_q = f_q - w_q rho0 (species: g_q itself), optionally scaled for FP16
+// (stored = d_q / (w_q sigma)).  The collision is evaluated in deviation
+// space, which keeps FP32/FP16 storage accurate:
+//   rho = rho0 + sum d,  rho u = sum d v (+ F/2 for Guo forcing)
+//   d_eq = w (drho + rho (3 v.u + 9/2 (v.u)^2 - 3/2 u.u))   (Eq. standardequilibrium)
+//   d*   = d + (d_eq - d)/tau + S_q                       (Eq. bgkequation)
+// with S_q the Guo source (1 - 1/(2 tau)) w [3 (v - u) + 9 (v.u) v].F or the
+// paper's 3 w v.F.  Species (D2Q5): phi = sum g, g_eq = phi w (1 + 3 v.u),
+// g* = g + (g_eq - g)/tau_D + w R with R the linear reaction plus the source
+// of the node's cell.
+#include <type_traits>
+
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+template <typename T, typename C>
+struct Store;
+template <>
+struct Store<double, double> {
+    static __device__ __forceinline__ double ld(const double* p) { return *p; }
+    static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
+};
+template <>
+struct Store<float, float> {
+    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
+};
+template <>
+struct Store<__half, float> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+
+template <typename C>
+struct Vec2;
+template <>
+struct Vec2<double> { using T = double2; };
+template <>
+struct Vec2<float> { using T = float2; };
+
+template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
+__global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k) {
+    using St = Store<T, C>;
+    using V2 = typename Vec2<C>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+
+    const int64_t P = a.plane;
+    const int xm = (x == 0) ? a.nx - 1 : x - 1;
+    const int xp = (x == a.nx - 1) ? 0 : x + 1;
+    const bool lo_wall = WALLS && (y == 0);
+    const bool hi_wall = WALLS && (y == a.ny - 1);
+    const int ym = (y == 0) ? a.ny - 1 : y - 1;
+    const int yp = (y == a.ny - 1) ? 0 : y + 1;
+    const int64_t r0 = (int64_t)y * a.pitch;
+    const int64_t rm = (int64_t)ym * a.pitch;
+    const int64_t rp = (int64_t)yp * a.pitch;
+    const int64_t node = r0 + x;
+
+    // ---- stream (pull) the fluid populations
+    const T* F = static_cast<const T*>(a.fsrc);
+    C d[9];
+    d[0] = St::ld(F + node);
+    d[1] = St::ld(F + 1 * P + r0 + xm);
+    d[3] = St::ld(F + 3 * P + r0 + xp);
+    if (lo_wall) {  // half-way bounce-back: v_y = +1 populations reflect off y = -1/2
+        d[2] = St::ld(F + 4 * P + node);
+        d[5] = St::ld(F + 7 * P + node);
+        d[6] = St::ld(F + 8 * P + node);
+    } else {
+        d[2] = St::ld(F + 2 * P + rm + x);
+        d[5] = St::ld(F + 5 * P + rm + xm);
+        d[6] = St::ld(F + 6 * P + rm + xp);
+    }
+    if (hi_wall) {  // v_y = -1 populations reflect off y = ny - 1/2
+        d[4] = St::ld(F + 2 * P + node);
+        d[7] = St::ld(F + 5 * P + node);
+        d[8] = St::ld(F + 6 * P + node);
+    } else {
+        d[4] = St::ld(F + 4 * P + rp + x);
+        d[7] = St::ld(F + 7 * P + rp + xp);
+        d[8] = St::ld(F + 8 * P + rp + xm);
+    }
+    if (SCALED) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) d[q] *= k.fscale[q];
+    }
+
+    // ---- body force: spread IB force (read, then reset) plus the uniform part
+    C Fx = k.bfx, Fy = k.bfy;
+    uint32_t label = kOutside;
+    if (a.ib) {
+        V2* fp = static_cast<V2*>(a.force) + node;
+        V2 fv = *fp;
+        Fx += fv.x;
+        Fy += fv.y;
+        V2 z;
+        z.x = C(0);
+        z.y = C(0);
+        *fp = z;
+        label = a.id[node];
+        a.id[node] = kOutside;
+        if (a.out) {
+            a.id_out[node] = label;
+            static_cast<V2*>(a.force_out)[node] = fv;
+        }
+    }
+
+    // ---- moments (Sec. 6.1) with the half-force velocity shift (Guo)
+    const C drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const C rho = k.rho0 + drho;
+    const C jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+    const C jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    const C irho = C(1) / rho;
+    C ux, uy;
+    if (FORCING == LBIB_GUO) {
+        ux = (jx + C(0.5) * Fx) * irho;
+        uy = (jy + C(0.5) * Fy) * irho;
+    } else {
+        ux = jx * irho;
+        uy = jy * irho;
+    }
+    const C usq15 = C(1.5) * (ux * ux + uy * uy);
+    const C uF = ux * Fx + uy * Fy;
+
+    // ---- collide and store
+    T* G = static_cast<T*>(a.fdst);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const C w = C(w9(q));
+        const C cu = C(cx(q)) * ux + C(cy(q)) * uy;
+        const C cF = C(cx(q)) * Fx + C(cy(q)) * Fy;
+        const C deq = w * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - usq15));
+        C Sq;
+        if (FORCING == LBIB_GUO)
+            Sq = k.pref * w * (C(3) * (cF - uF) + C(9) * cu * cF);
+        else
+            Sq = C(3) * w * cF;
+        C dn = d[q] + k.omega * (deq - d[q]) + Sq;
+        if (SCALED) dn *= k.finv[q];
+        St::st(G + q * P + node, dn);
+    }
+
+    {
+        V2 uv;
+        uv.x = ux;
+        uv.y = uy;
+        static_cast<V2*>(a.u)[node] = uv;
+    }
+    if (a.out) static_cast<C*>(a.rho)[node] = rho;
+    if (!(rho > C(0)) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.diag + kDiagNonFinite, 1u);
+
+    // ---- species (D2Q5): pull all, then react and collide with the fluid u
+    if (S > 0) {
+        const uint32_t bits = (label == kOutside) ? 0u : (label & 0xFu);
+        const T* Gi = static_cast<const T*>(a.gsrc);
+        T* Go = static_cast<T*>(a.gdst);
+        C g[S > 0 ? S : 1][5];
+        C ph[S > 0 ? S : 1];
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const T* B = Gi + (int64_t)s * 5 * P;
+            g[s][0] = St::ld(B + node);
+            g[s][1] = St::ld(B + 1 * P + r0 + xm);
+            g[s][3] = St::ld(B + 3 * P + r0 + xp);
+            g[s][2] = lo_wall ? St::ld(B + 4 * P + node) : St::ld(B + 2 * P + rm + x);
+            g[s][4] = hi_wall ? St::ld(B + 2 * P + node) : St::ld(B + 4 * P + rp + x);
+            if (SCALED) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) g[s][q] *= k.gscale[q];
+            }
+            ph[s] = ((g[s][0] + g[s][1]) + (g[s][2] + g[s][3])) + g[s][4];
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            C R = ((bits >> s) & 1u) ? k.srate[s] : C(0);
+#pragma unroll
+            for (int b = 0; b < S; ++b) R += k.K[s][b] * ph[b];
+            T* B = Go + (int64_t)s * 5 * P;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const C w = C(w5(q));
+                const C cu = C(cx(q)) * ux + C(cy(q)) * uy;
+                const C geq = ph[s] * w * (C(1) + C(3) * cu);
+                C gn = g[s][q] + k.omegaD[s] * (geq - g[s][q]) + w * R;
+                if (SCALED) gn *= k.ginv[q];
+                St::st(B + q * P + node, gn);
+            }
+            if (a.out) static_cast<C*>(a.phi)[(int64_t)s * P + node] = ph[s];
+        }
+    }
+}
+
+template <typename T, typename C, int S, bool WALLS, int FORCING>
+static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s) {
+    dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
+    const Coefs<C>& k = *static_cast<const Coefs<C>*>(coefs);
+    constexpr bool SC = std::is_same<T, __half>::value;
+    lattice_kernel<T, C, S, WALLS, FORCING, SC><<<grid, block, 0, s>>>(a, k);
+    return cudaGetLastError();
+}
+
+template <typename T, typename C, int S>
+static cudaError_t launch2(int bc_y, int forcing, const LatticeArgs& a, const void* coefs,
+                           dim3 block, cudaStream_t s) {
+    if (bc_y) {
+        return forcing ? launch3<T, C, S, true, 1>(a, coefs, block, s)
+                       : launch3<T, C, S, true, 0>(a, coefs, block, s);
+    }
+    return forcing ? launch3<T, C, S, false, 1>(a, coefs, block, s)
+                   : launch3<T, C, S, false, 0>(a, coefs, block, s);
+}
+
+template <typename T, typename C>
+static cudaError_t launch1(int n_species, int bc_y, int forcing, const LatticeArgs& a,
+                           const void* coefs, dim3 block, cudaStream_t s) {
+    switch (n_species) {
+        case 0: return launch2<T, C, 0>(bc_y, forcing, a, coefs, block, s);
+        case 1: return launch2<T, C, 1>(bc_y, forcing, a, coefs, block, s);
+        case 2: return launch2<T, C, 2>(bc_y, forcing, a, coefs, block, s);
+        case 3: return launch2<T, C, 3>(bc_y, forcing, a, coefs, block, s);
+        default: return launch2<T, C, 4>(bc_y, forcing, a, coefs, block, s);
+    }
+}
+
+cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
+                           const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s) {
+    if (precision == LBIB_FP64)
+        return launch1<double, double>(n_species, bc_y, forcing, a, coefs, block, s);
+    if (precision == LBIB_FP32)
+        return launch1<float, float>(n_species, bc_y, forcing, a, coefs, block, s);
+    return launch1<__half, float>(n_species, bc_y, forcing, a, coefs, block, s);
+}
+
+// ---------------------------------------------------------------------------
+// rest state: d = 0 (f = w rho0), g = 0 -- all stored values are zero
+template <typename T>
+__global__ void zero_planes(T* p, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t st = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n; i += st) p[i] = T(0);
+}
+
+cudaError_t launch_init_populations(int precision, int n_species, int nx, int ny, int64_t pitch,
+                                    int64_t plane, void* f, void* g, cudaStream_t s) {
+    (void)nx; (void)ny; (void)pitch; (void)precision;
+    // every storage type represents zero with all-zero bytes
+    int es = precision == LBIB_FP64 ? 8 : (precision == LBIB_FP32 ? 4 : 2);
+    cudaError_t e = cudaMemsetAsync(f, 0, (size_t)9 * plane * es, s);
+    if (e != cudaSuccess) return e;
+    if (n_species > 0) e = cudaMemsetAsync(g, 0, (size_t)5 * n_species * plane * es, s);
+    return e;
+}
+
+template <typename T, typename C>
+__global__ void set_species_kernel(int nx, int ny, int64_t pitch, int64_t plane,
+                                   const double* phi, T* g, Coefs<C> k, bool scaled) {
+    int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int y = blockIdx.y;
+    if (x >= nx || y >= ny) return;
+    double v = phi[(int64_t)y * nx + x];
+    for (int q = 0; q < 5; ++q) {
+        C gq = C(w5(q) * v);
+        if (scaled) gq *= k.ginv[q];
+        Store<T, C>::st(g + q * plane + (int64_t)y * pitch + x, gq);
+    }
+}
+
+cudaError_t launch_set_species(int precision, int n_species, int s_idx, int nx, int ny,
+                               int64_t pitch, int64_t plane, const double* phi, void* g,
+                               const void* coefs, cudaStream_t s) {
+    (void)n_species;
+    dim3 block(128), grid((nx + 127) / 128, ny);
+    if (precision == LBIB_FP64) {
+        set_species_kernel<double, double><<<grid, block, 0, s>>>(
+            nx, ny, pitch, plane, phi, static_cast<double*>(g) + (int64_t)s_idx * 5 * plane,
+            *static_cast<const Coefs<double>*>(coefs), false);
+    } else if (precision == LBIB_FP32) {
+        set_species_kernel<float, float><<<grid, block, 0, s>>>(
+            nx, ny, pitch, plane, phi, static_cast<float*>(g) + (int64_t)s_idx * 5 * plane,
+            *static_cast<const Coefs<float>*>(coefs), false);
+    } else {
+        set_species_kernel<__half, float><<<grid, block, 0, s>>>(
+            nx, ny, pitch, plane, phi, static_cast<__half*>(g) + (int64_t)s_idx * 5 * plane,
+            *static_cast<const Coefs<float>*>(coefs), true);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lbib

@@ -1,0 +1,716 @@
+// lbib.cu -- host engine and C ABI of the coupled LB-IB library.
+//
+// The context binds a caller-owned device workspace (layout below), keeps
+// the tau-derived coefficients, and sequences the kernels of a time step on
+// the caller's stream:
+//
+//   step n:  [IB prep  X^n -> labels, F^n, spread]      (ib.cu)
+//            [lattice  stream, collide fluid + species] (lattice.cu)
+//            [IB move  U^n = interp(u^n), X^{n+1}]       (ib.cu)
+//
+// Between two steps the move of step n and the prep of step n+1 are one
+// launch, so a step costs two launches.  A chunk of two steps (one full A/B
+// buffer cycle) is captured once into a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+static uint64_t align_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* L) {
+    if (p.nx < 8 || p.ny < 8 || p.nx > (1 << 20) || p.ny > (1 << 20)) return false;
+    if (p.precision < LBIB_FP64 || p.precision > LBIB_FP16) return false;
+    if (p.n_species < 0 || p.n_species > kMaxSpecies) return false;
+    if (max_vertices < 0 || max_cells < 0 || max_cells > (1 << 27)) return false;
+    Layout l;
+    l.es = p.precision == LBIB_FP64 ? 8 : (p.precision == LBIB_FP32 ? 4 : 2);
+    l.cs = p.precision == LBIB_FP64 ? 8 : 4;
+    l.pitch = (int64_t)align_up((uint64_t)p.nx, 64);
+    l.plane = l.pitch * p.ny;
+    const uint64_t P = (uint64_t)l.plane;
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        uint64_t at = o;
+        o = align_up(o + bytes, 256);
+        return at;
+    };
+    l.f[0] = take(9 * P * l.es);
+    l.f[1] = take(9 * P * l.es);
+    l.g[0] = take((uint64_t)5 * p.n_species * P * l.es);
+    l.g[1] = take((uint64_t)5 * p.n_species * P * l.es);
+    l.force = take(2 * P * l.cs);
+    l.u = take(2 * P * l.cs);
+    l.rho = take(P * l.cs);
+    l.phi = take((uint64_t)p.n_species * P * l.cs);
+    l.id = take(P * 4);
+    l.id_out = take(P * 4);
+    l.force_out = take(2 * P * l.cs);
+    const uint64_t V = (uint64_t)max_vertices, C = (uint64_t)max_cells;
+    l.xy = take(V * 16);
+    l.L0 = take(V * 8);
+    l.k = take(V * 8);
+    l.vforce = take(V * 16);
+    l.off = take((C + 1) * 4);
+    l.pres = take(C * 8);
+    l.srcf = take(C);
+    l.area = take(C * 8);
+    l.diag = take(kDiagWords * 4);
+    l.total = o;
+    *L = l;
+    return true;
+}
+
+}  // namespace lbib
+
+using namespace lbib;
+
+struct lbib_ctx {
+    lbib_params p;
+    int maxV = 0, maxC = 0;
+    char* ws = nullptr;
+    uint64_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    Layout L;
+    int cur = 0;           // buffer holding the current post-collision populations
+    int nV = 0, nC = 0;
+    bool fields_valid = false;
+    bool vforce_valid = false;
+    Coefs<double> kd;
+    Coefs<float> kf;
+    dim3 block{128, 1, 1};
+    // graph of a two-step chunk, keyed by the buffer parity it starts from
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    int chunk_nC = -1;
+    std::string err;
+
+    template <typename T>
+    T* at(uint64_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+static thread_local std::string g_create_err;
+
+static int fail(lbib_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return code;
+}
+
+static int cuda_fail(lbib_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, LBIB_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static int check_params(const lbib_params* p, std::string* why) {
+    if (!p) { *why = "params is NULL"; return LBIB_E_PARAM; }
+    if (p->nx < 8 || p->ny < 8) { *why = "nx and ny must be >= 8"; return LBIB_E_PARAM; }
+    if ((int64_t)p->nx * p->ny > ((int64_t)1 << 34)) { *why = "lattice too large"; return LBIB_E_PARAM; }
+    if (p->bc_y != 0 && p->bc_y != 1) { *why = "bc_y must be 0 or 1"; return LBIB_E_PARAM; }
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) { *why = "tau must be > 1/2"; return LBIB_E_PARAM; }
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) { *why = "rho0 must be > 0"; return LBIB_E_PARAM; }
+    if (p->n_species < 0 || p->n_species > 4) { *why = "n_species must be 0..4"; return LBIB_E_PARAM; }
+    for (int s = 0; s < p->n_species; ++s)
+        if (!(p->D[s] > 0.0) || !std::isfinite(p->D[s])) { *why = "D must be > 0"; return LBIB_E_PARAM; }
+    if (p->forcing != LBIB_GUO && p->forcing != LBIB_HE_PAPER) { *why = "unknown forcing"; return LBIB_E_PARAM; }
+    if (p->precision < LBIB_FP64 || p->precision > LBIB_FP16) { *why = "unknown precision"; return LBIB_E_PARAM; }
+    if (p->fp16_scale < 0 || p->fp16_scale_species < 0) { *why = "fp16 scales must be >= 0"; return LBIB_E_PARAM; }
+    return LBIB_OK;
+}
+
+template <typename C>
+static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
+    std::memset(k, 0, sizeof(*k));
+    k->rho0 = (C)p.rho0;
+    k->omega = (C)(1.0 / p.tau);
+    k->pref = (C)(1.0 - 0.5 / p.tau);
+    k->bfx = (C)p.body_force[0];
+    k->bfy = (C)p.body_force[1];
+    for (int s = 0; s < kMaxSpecies; ++s) {
+        double tauD = 3.0 * p.D[s] + 0.5;
+        k->omegaD[s] = (C)(s < p.n_species ? 1.0 / tauD : 0.0);
+        k->srate[s] = (C)p.src_rate[s];
+        for (int b = 0; b < kMaxSpecies; ++b)
+            k->K[s][b] = (C)(p.react[s][b] - (s == b ? p.decay[s] : 0.0));
+    }
+    const double sf = p.fp16_scale > 0 ? p.fp16_scale : std::ldexp(1.0, -10);
+    const double sg = p.fp16_scale_species > 0 ? p.fp16_scale_species : std::ldexp(1.0, -8);
+    const bool scaled = p.precision == LBIB_FP16;
+    for (int q = 0; q < 9; ++q) {
+        k->fscale[q] = (C)(scaled ? w9(q) * sf : 1.0);
+        k->finv[q] = (C)(scaled ? 1.0 / (w9(q) * sf) : 1.0);
+    }
+    for (int q = 0; q < 5; ++q) {
+        k->gscale[q] = (C)(scaled ? w5(q) * sg : 1.0);
+        k->ginv[q] = (C)(scaled ? 1.0 / (w5(q) * sg) : 1.0);
+    }
+}
+
+static const void* coefs_of(const lbib_ctx* c) {
+    return c->p.precision == LBIB_FP64 ? (const void*)&c->kd : (const void*)&c->kf;
+}
+
+static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
+    LatticeArgs a;
+    const Layout& L = c->L;
+    a.fsrc = c->ws + L.f[src_buf];
+    a.fdst = c->ws + L.f[1 - src_buf];
+    a.gsrc = c->ws + L.g[src_buf];
+    a.gdst = c->ws + L.g[1 - src_buf];
+    a.force = c->ws + L.force;
+    a.id = c->at<uint32_t>(L.id);
+    a.u = c->ws + L.u;
+    a.rho = c->ws + L.rho;
+    a.phi = c->ws + L.phi;
+    a.id_out = c->at<uint32_t>(L.id_out);
+    a.force_out = c->ws + L.force_out;
+    a.diag = c->at<uint32_t>(L.diag);
+    a.nx = c->p.nx;
+    a.ny = c->p.ny;
+    a.pitch = L.pitch;
+    a.plane = L.plane;
+    a.out = out ? 1 : 0;
+    a.ib = c->nC > 0 ? 1 : 0;
+    return a;
+}
+
+static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) {
+    IBArgs a;
+    const Layout& L = c->L;
+    a.xy = c->at<double2>(L.xy);
+    a.L0 = c->at<double>(L.L0);
+    a.k = c->at<double>(L.k);
+    a.off = c->at<int32_t>(L.off);
+    a.pres = c->at<double>(L.pres);
+    a.srcf = c->at<uint8_t>(L.srcf);
+    a.vforce = c->at<double2>(L.vforce);
+    a.force = c->ws + L.force;
+    a.id = c->at<uint32_t>(L.id);
+    a.u = c->ws + L.u;
+    a.diag = c->at<uint32_t>(L.diag);
+    a.nx = c->p.nx;
+    a.ny = c->p.ny;
+    a.bc_y = c->p.bc_y;
+    a.n_cells = c->nC;
+    a.pitch = L.pitch;
+    a.tension = c->p.tension;
+    a.do_move = move ? 1 : 0;
+    a.do_prep = prep ? 1 : 0;
+    a.do_mask = 1;
+    a.write_vforce = vforce ? 1 : 0;
+    return a;
+}
+
+static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out) {
+    LatticeArgs a = lattice_args(c, src_buf, out);
+    return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,
+                          coefs_of(c), c->block, c->stream);
+}
+
+static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool vforce) {
+    if (c->nC == 0) return cudaSuccess;
+    return launch_ib(c->p.precision, ib_args(c, move, prep, vforce), c->stream);
+}
+
+static void drop_graphs(lbib_ctx* c) {
+    for (int i = 0; i < 2; ++i)
+        if (c->chunk[i]) {
+            cudaGraphExecDestroy(c->chunk[i]);
+            c->chunk[i] = nullptr;
+        }
+    c->chunk_nC = -1;
+}
+
+// two full steps starting from buffer parity `par`, ending with the prep of
+// the following step: [lat(par), ib move+prep, lat(1-par), ib move+prep]
+static cudaError_t enqueue_chunk(lbib_ctx* c, int par) {
+    cudaError_t e = enqueue_lattice(c, par, false);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false);
+    if (e == cudaSuccess) e = enqueue_lattice(c, 1 - par, false);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false);
+    return e;
+}
+
+static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out) {
+    if (c->chunk_nC != c->nC) drop_graphs(c);
+    if (!c->chunk[par]) {
+        cudaStream_t cap;
+        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        cudaStream_t saved = c->stream;
+        c->stream = cap;
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e2 = enqueue_chunk(c, par);
+            e = cudaStreamEndCapture(cap, &g);
+            if (e2 != cudaSuccess) e = e2;
+        }
+        c->stream = saved;
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return e;
+        }
+        e = cudaGraphInstantiate(&c->chunk[par], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return e;
+        c->chunk_nC = c->nC;
+    }
+    *out = c->chunk[par];
+    return cudaSuccess;
+}
+
+extern "C" {
+
+int lbib_workspace_size(const lbib_params* params, int32_t max_vertices, int32_t max_cells,
+                        uint64_t* bytes_out) {
+    std::string why;
+    int rc = check_params(params, &why);
+    if (rc) return fail(nullptr, rc, why);
+    if (!bytes_out) return fail(nullptr, LBIB_E_PARAM, "bytes_out is NULL");
+    Layout L;
+    if (!make_layout(*params, max_vertices, max_cells, &L))
+        return fail(nullptr, LBIB_E_PARAM, "invalid capacities");
+    *bytes_out = L.total;
+    return LBIB_OK;
+}
+
+int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cells,
+                void* d_workspace, uint64_t bytes, void* cuda_stream, lbib_ctx** out) {
+    std::string why;
+    if (!out) return fail(nullptr, LBIB_E_PARAM, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(params, &why);
+    if (rc) return fail(nullptr, rc, why);
+    Layout L;
+    if (!make_layout(*params, max_vertices, max_cells, &L))
+        return fail(nullptr, LBIB_E_PARAM, "invalid capacities");
+    if (!d_workspace) return fail(nullptr, LBIB_E_WORKSPACE, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(d_workspace) % 256)
+        return fail(nullptr, LBIB_E_WORKSPACE, "workspace must be 256-byte aligned");
+    if (bytes < L.total)
+        return fail(nullptr, LBIB_E_WORKSPACE,
+                    "workspace too small: need " + std::to_string(L.total) + " bytes");
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, d_workspace);
+    if (e != cudaSuccess || (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        return fail(nullptr, LBIB_E_WORKSPACE, "workspace is not device memory");
+    }
+    lbib_ctx* c = new (std::nothrow) lbib_ctx();
+    if (!c) return fail(nullptr, LBIB_E_PARAM, "out of host memory");
+    c->p = *params;
+    c->maxV = max_vertices;
+    c->maxC = max_cells;
+    c->ws = static_cast<char*>(d_workspace);
+    c->bytes = bytes;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->L = L;
+    fill_coefs(c->p, &c->kd);
+    fill_coefs(c->p, &c->kf);
+    e = launch_init_populations(c->p.precision, c->p.n_species, c->p.nx, c->p.ny, L.pitch,
+                                L.plane, c->ws + L.f[0], c->ws + L.g[0], c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.u, 0, 2 * L.plane * L.cs, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(nullptr, e, "lbib_create");
+    }
+    *out = c;
+    return LBIB_OK;
+}
+
+int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const double* xy,
+                   const double* rest_len, const double* k_spring, const double* pressure,
+                   const uint8_t* src_flag) {
+    if (!c) return LBIB_E_PARAM;
+    if (n_cells < 0 || n_cells > c->maxC) return fail(c, LBIB_E_CELLS, "n_cells exceeds capacity");
+    if (n_cells > 0 && (!cell_off || !xy)) return fail(c, LBIB_E_CELLS, "cell_off and xy are required");
+    int V = n_cells > 0 ? cell_off[n_cells] : 0;
+    if (n_cells > 0 && cell_off[0] != 0) return fail(c, LBIB_E_CELLS, "cell_off[0] must be 0");
+    for (int i = 0; i < n_cells; ++i) {
+        int nv = cell_off[i + 1] - cell_off[i];
+        if (nv < 3) return fail(c, LBIB_E_CELLS, "a cell needs at least 3 vertices");
+        if (nv > kMaxVertsPerCell) return fail(c, LBIB_E_CELLS, "a cell has more than 1024 vertices");
+    }
+    if (V > c->maxV) return fail(c, LBIB_E_CELLS, "vertex count exceeds capacity");
+    for (int i = 0; i < 2 * V; ++i)
+        if (!std::isfinite(xy[i]) || std::fabs(xy[i]) > 1e9)
+            return fail(c, LBIB_E_NONFINITE, "non-finite or out-of-range vertex position");
+    for (int ci = 0; ci < n_cells; ++ci) {
+        int a = cell_off[ci], b = cell_off[ci + 1];
+        double xmn = xy[2 * a], xmx = xmn, ymn = xy[2 * a + 1], ymx = ymn, s = 0.0;
+        for (int l = a; l < b; ++l) {
+            int m = (l + 1 < b) ? l + 1 : a;
+            xmn = std::fmin(xmn, xy[2 * l]); xmx = std::fmax(xmx, xy[2 * l]);
+            ymn = std::fmin(ymn, xy[2 * l + 1]); ymx = std::fmax(ymx, xy[2 * l + 1]);
+            s += (xy[2 * l] - xy[2 * a]) * (xy[2 * m + 1] - xy[2 * a + 1]) -
+                 (xy[2 * m] - xy[2 * a]) * (xy[2 * l + 1] - xy[2 * a + 1]);
+        }
+        if (!(s > 0.0)) return fail(c, LBIB_E_CELLS, "cell polygons must be counter-clockwise");
+        if (xmx - xmn > c->p.nx - 4 || ymx - ymn > c->p.ny - 4)
+            return fail(c, LBIB_E_CELLS, "a cell is larger than the lattice");
+    }
+    std::vector<double> L0((size_t)V), kk((size_t)V, 0.0), pp((size_t)n_cells, 0.0);
+    std::vector<uint8_t> sf((size_t)n_cells, 0);
+    for (int ci = 0; ci < n_cells; ++ci) {
+        int a = cell_off[ci], b = cell_off[ci + 1];
+        for (int l = a; l < b; ++l) {
+            int m = (l + 1 < b) ? l + 1 : a;
+            double dx = xy[2 * m] - xy[2 * l], dy = xy[2 * m + 1] - xy[2 * l + 1];
+            L0[l] = rest_len ? rest_len[l] : std::sqrt(dx * dx + dy * dy);
+            if (k_spring) kk[l] = k_spring[l];
+        }
+        if (pressure) pp[ci] = pressure[ci];
+        if (src_flag) sf[ci] = src_flag[ci];
+    }
+    const Layout& L = c->L;
+    cudaError_t e = cudaSuccess;
+    if (V > 0) {
+        e = cudaMemcpyAsync(c->ws + L.xy, xy, (size_t)V * 16, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws + L.L0, L0.data(), (size_t)V * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws + L.k, kk.data(), (size_t)V * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws + L.off, cell_off, (size_t)(n_cells + 1) * 4,
+                                cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws + L.pres, pp.data(), (size_t)n_cells * 8, cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws + L.srcf, sf.data(), (size_t)n_cells, cudaMemcpyHostToDevice,
+                                c->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_cells");
+    c->nV = V;
+    c->nC = n_cells;
+    c->vforce_valid = false;
+    drop_graphs(c);
+    return LBIB_OK;
+}
+
+int lbib_set_cell_params(lbib_ctx* c, const double* pressure, const uint8_t* src_flag) {
+    if (!c) return LBIB_E_PARAM;
+    cudaError_t e = cudaSuccess;
+    if (pressure && c->nC > 0)
+        e = cudaMemcpyAsync(c->ws + c->L.pres, pressure, (size_t)c->nC * 8, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess && src_flag && c->nC > 0)
+        e = cudaMemcpyAsync(c->ws + c->L.srcf, src_flag, (size_t)c->nC, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_cell_params");
+    return LBIB_OK;
+}
+
+int lbib_set_species(lbib_ctx* c, int32_t s, const double* phi) {
+    if (!c) return LBIB_E_PARAM;
+    if (s < 0 || s >= c->p.n_species) return fail(c, LBIB_E_PARAM, "species index out of range");
+    if (!phi) return fail(c, LBIB_E_PARAM, "phi is NULL");
+    const size_t N = (size_t)c->p.nx * c->p.ny;
+    // The host field is staged in the force_out planes (2 planes of the compute
+    // type hold at least nx*ny doubles); they only carry the last step's output.
+    double* stage = c->at<double>(c->L.force_out);
+    if ((uint64_t)N * 8 > (uint64_t)2 * c->L.plane * c->L.cs)
+        return fail(c, LBIB_E_STATE, "staging area too small");
+    cudaError_t e = cudaMemcpyAsync(stage, phi, N * 8, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_set_species(c->p.precision, c->p.n_species, s, c->p.nx, c->p.ny, c->L.pitch,
+                               c->L.plane, stage, c->ws + c->L.g[c->cur], coefs_of(c), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_species");
+    c->fields_valid = false;
+    return LBIB_OK;
+}
+
+int lbib_step(lbib_ctx* c, int32_t n_steps) {
+    if (!c) return LBIB_E_PARAM;
+    if (n_steps < 0) return fail(c, LBIB_E_PARAM, "n_steps must be >= 0");
+    if (n_steps == 0) return LBIB_OK;
+    cudaError_t e = cudaSuccess;
+    const bool ib = c->nC > 0;
+    // prep of the first step (labels, forces, spreading from X^n)
+    if (ib) e = enqueue_ib(c, false, true, n_steps == 1);
+    int left = n_steps;
+    // full two-step chunks through the graph, keeping the last two steps apart
+    // (they write the vertex forces and the output fields)
+    while (e == cudaSuccess && left > 3) {
+        cudaGraphExec_t g;
+        e = get_chunk_graph(c, c->cur, &g);
+        if (e == cudaSuccess) e = cudaGraphLaunch(g, c->stream);
+        left -= 2;
+    }
+    while (e == cudaSuccess && left > 0) {
+        const bool last = (left == 1);
+        e = enqueue_lattice(c, c->cur, last);
+        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, !last, left == 2);
+        c->cur = 1 - c->cur;
+        --left;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
+    c->fields_valid = true;
+    c->vforce_valid = ib;
+    return LBIB_OK;
+}
+
+int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
+    if (!c || !ms_out) return LBIB_E_PARAM;
+    if (n_steps <= 0) return fail(c, LBIB_E_PARAM, "n_steps must be > 0");
+    const bool ib = c->nC > 0;
+    // one event before and after every launch: 2 per launch
+    const int n_launch = n_steps + (ib ? n_steps + 1 : 0);
+    std::vector<cudaEvent_t> ev((size_t)2 * n_launch, nullptr);
+    std::vector<int> kind((size_t)n_launch, 0);
+    cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    int li = 0;
+    auto timed = [&](int k, auto&& fn) {
+        if (e != cudaSuccess) return;
+        e = cudaEventRecord(ev[2 * li], c->stream);
+        if (e == cudaSuccess) e = fn();
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * li + 1], c->stream);
+        kind[li++] = k;
+    };
+    if (ib) timed(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
+    for (int left = n_steps; left > 0 && e == cudaSuccess; --left) {
+        const bool last = (left == 1);
+        timed(0, [&] { return enqueue_lattice(c, c->cur, last); });
+        if (ib) timed(1, [&] { return enqueue_ib(c, true, !last, left == 2); });
+        c->cur = 1 - c->cur;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    ms_out[0] = ms_out[1] = 0.0;
+    for (int i = 0; i < li && e == cudaSuccess; ++i) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+        ms_out[kind[i]] += ms;
+    }
+    for (auto& x : ev)
+        if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step_profiled");
+    c->fields_valid = true;
+    c->vforce_valid = ib;
+    return LBIB_OK;
+}
+
+int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double* uy, double* phi,
+                    double* xy, double* area, int32_t* id, double* force, double* vforce) {
+    if (!c) return LBIB_E_PARAM;
+    const uint32_t lattice_bits = LBIB_RHO | LBIB_U | LBIB_PHI | LBIB_ID | LBIB_FORCE;
+    if ((which & lattice_bits) && !c->fields_valid)
+        return fail(c, LBIB_E_STATE, "no completed step since the last create or reset");
+    if ((which & (LBIB_ID | LBIB_FORCE)) && c->nC == 0)
+        return fail(c, LBIB_E_STATE, "labels and spread force need cells");
+    const Layout& L = c->L;
+    const int nx = c->p.nx, ny = c->p.ny, S = c->p.n_species;
+    const size_t N = (size_t)nx * ny;
+    cudaError_t e = cudaSuccess;
+    // Each requested plane is copied raw (storage pitch, compute type) to host
+    // memory and converted there, so no device scratch is needed.
+    std::vector<char> raw;
+    auto fetch = [&](uint64_t off, size_t bytes) -> const char* {
+        raw.resize(bytes);
+        e = cudaMemcpyAsync(raw.data(), c->ws + off, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        return raw.data();
+    };
+    auto val = [&](const char* base, int64_t idx) -> double {
+        return c->L.cs == 8 ? reinterpret_cast<const double*>(base)[idx]
+                            : (double)reinterpret_cast<const float*>(base)[idx];
+    };
+    if (which & LBIB_RHO) {
+        const char* b = fetch(L.rho, (size_t)L.plane * L.cs);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) rho[(size_t)y * nx + x] = val(b, (int64_t)y * L.pitch + x);
+    }
+    if (which & LBIB_U) {
+        const char* b = fetch(L.u, (size_t)2 * L.plane * L.cs);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t n = (int64_t)y * L.pitch + x;
+                if (ux) ux[(size_t)y * nx + x] = val(b, 2 * n);
+                if (uy) uy[(size_t)y * nx + x] = val(b, 2 * n + 1);
+            }
+    }
+    if ((which & LBIB_PHI) && S > 0) {
+        const char* b = fetch(L.phi, (size_t)S * L.plane * L.cs);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+        for (int s = 0; s < S; ++s)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x)
+                    phi[(size_t)s * N + (size_t)y * nx + x] =
+                        val(b, (int64_t)s * L.plane + (int64_t)y * L.pitch + x);
+    }
+    if (which & LBIB_ID) {
+        const char* b = fetch(L.id_out, (size_t)L.plane * 4);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+        const uint32_t* v = reinterpret_cast<const uint32_t*>(b);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                uint32_t t = v[(int64_t)y * L.pitch + x];
+                id[(size_t)y * nx + x] = (t == kOutside) ? 0 : (int32_t)(t >> 4) + 1;
+            }
+    }
+    if (which & LBIB_FORCE) {
+        const char* b = fetch(L.force_out, (size_t)2 * L.plane * L.cs);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t n = (int64_t)y * L.pitch + x;
+                force[2 * ((size_t)y * nx + x)] = val(b, 2 * n);
+                force[2 * ((size_t)y * nx + x) + 1] = val(b, 2 * n + 1);
+            }
+    }
+    if ((which & LBIB_X) && c->nV > 0) {
+        e = cudaMemcpyAsync(xy, c->ws + L.xy, (size_t)c->nV * 16, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    }
+    if ((which & LBIB_VFORCE) && c->nV > 0) {
+        if (!c->vforce_valid) return fail(c, LBIB_E_STATE, "no vertex forces computed yet");
+        e = cudaMemcpyAsync(vforce, c->ws + L.vforce, (size_t)c->nV * 16, cudaMemcpyDeviceToHost,
+                            c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    }
+    if ((which & LBIB_AREA) && c->nC > 0) {
+        e = launch_areas(c->at<double2>(L.xy), c->at<int32_t>(L.off), c->nC, c->at<double>(L.area),
+                         c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(area, c->ws + L.area, (size_t)c->nC * 8, cudaMemcpyDeviceToHost,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    }
+    // surface the device-side diagnostics
+    uint32_t diag[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(diag, c->ws + L.diag, sizeof(diag), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    if (diag[kDiagNonFinite])
+        return fail(c, LBIB_E_NONFINITE, "a non-finite density or velocity was produced");
+    if (diag[kDiagGeometry])
+        return fail(c, LBIB_E_NONFINITE, "a cell became non-finite or larger than the lattice");
+    return LBIB_OK;
+}
+
+int lbib_get_sizes(const lbib_ctx* c, int32_t* n_vertices, int32_t* n_cells) {
+    if (!c) return LBIB_E_PARAM;
+    if (n_vertices) *n_vertices = c->nV;
+    if (n_cells) *n_cells = c->nC;
+    return LBIB_OK;
+}
+
+// state: populations of the current buffer (f then g), then xy, L0, k, off,
+// pres, srcf, then a small header {cur-independent}.
+static uint64_t state_bytes(const lbib_ctx* c) {
+    const Layout& L = c->L;
+    uint64_t P = (uint64_t)L.plane * L.es;
+    return 16 + 9 * P + (uint64_t)5 * c->p.n_species * P + (uint64_t)c->maxV * 32 +
+           (uint64_t)(c->maxC + 1) * 4 + (uint64_t)c->maxC * 9;
+}
+
+int lbib_state_size(const lbib_ctx* c, uint64_t* bytes_out) {
+    if (!c || !bytes_out) return LBIB_E_PARAM;
+    *bytes_out = state_bytes(c);
+    return LBIB_OK;
+}
+
+int lbib_get_state(lbib_ctx* c, void* host, uint64_t bytes) {
+    if (!c || !host) return LBIB_E_PARAM;
+    if (bytes < state_bytes(c)) return fail(c, LBIB_E_PARAM, "state buffer too small");
+    const Layout& L = c->L;
+    char* h = static_cast<char*>(host);
+    int32_t hdr[4] = {c->nV, c->nC, c->p.precision, c->p.n_species};
+    std::memcpy(h, hdr, 16);
+    uint64_t o = 16, P = (uint64_t)L.plane * L.es;
+    struct Piece { uint64_t off, bytes; } pieces[] = {
+        {L.f[c->cur], 9 * P}, {L.g[c->cur], (uint64_t)5 * c->p.n_species * P},
+        {L.xy, (uint64_t)c->maxV * 16}, {L.L0, (uint64_t)c->maxV * 8}, {L.k, (uint64_t)c->maxV * 8},
+        {L.off, (uint64_t)(c->maxC + 1) * 4}, {L.pres, (uint64_t)c->maxC * 8},
+        {L.srcf, (uint64_t)c->maxC}};
+    cudaError_t e = cudaSuccess;
+    for (auto& pc : pieces) {
+        if (pc.bytes && e == cudaSuccess)
+            e = cudaMemcpyAsync(h + o, c->ws + pc.off, pc.bytes, cudaMemcpyDeviceToHost, c->stream);
+        o += pc.bytes;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_state");
+    return LBIB_OK;
+}
+
+int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
+    if (!c || !host) return LBIB_E_PARAM;
+    if (bytes < state_bytes(c)) return fail(c, LBIB_E_PARAM, "state buffer too small");
+    const char* h = static_cast<const char*>(host);
+    int32_t hdr[4];
+    std::memcpy(hdr, h, 16);
+    if (hdr[0] < 0 || hdr[0] > c->maxV || hdr[1] < 0 || hdr[1] > c->maxC ||
+        hdr[2] != c->p.precision || hdr[3] != c->p.n_species)
+        return fail(c, LBIB_E_STATE, "state does not match this context");
+    const Layout& L = c->L;
+    uint64_t o = 16, P = (uint64_t)L.plane * L.es;
+    c->cur = 0;
+    struct Piece { uint64_t off, bytes; } pieces[] = {
+        {L.f[0], 9 * P}, {L.g[0], (uint64_t)5 * c->p.n_species * P},
+        {L.xy, (uint64_t)c->maxV * 16}, {L.L0, (uint64_t)c->maxV * 8}, {L.k, (uint64_t)c->maxV * 8},
+        {L.off, (uint64_t)(c->maxC + 1) * 4}, {L.pres, (uint64_t)c->maxC * 8},
+        {L.srcf, (uint64_t)c->maxC}};
+    cudaError_t e = cudaSuccess;
+    for (auto& pc : pieces) {
+        if (pc.bytes && e == cudaSuccess)
+            e = cudaMemcpyAsync(c->ws + pc.off, h + o, pc.bytes, cudaMemcpyHostToDevice, c->stream);
+        o += pc.bytes;
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_state");
+    c->nV = hdr[0];
+    c->nC = hdr[1];
+    c->fields_valid = false;
+    c->vforce_valid = false;
+    drop_graphs(c);
+    return LBIB_OK;
+}
+
+void lbib_destroy(lbib_ctx* c) {
+    if (!c) return;
+    drop_graphs(c);
+    delete c;
+}
+
+const char* lbib_last_error(const lbib_ctx* c) {
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+const char* lbib_status_string(int status) {
+    switch (status) {
+        case LBIB_OK: return "LBIB_OK";
+        case LBIB_E_PARAM: return "LBIB_E_PARAM";
+        case LBIB_E_WORKSPACE: return "LBIB_E_WORKSPACE";
+        case LBIB_E_CELLS: return "LBIB_E_CELLS";
+        case LBIB_E_NONFINITE: return "LBIB_E_NONFINITE";
+        case LBIB_E_TIMEOUT: return "LBIB_E_TIMEOUT";
+        case LBIB_E_CUDA: return "LBIB_E_CUDA";
+        case LBIB_E_STATE: return "LBIB_E_STATE";
+        default: return "LBIB_E_UNKNOWN";
+    }
+}
+
+}  // extern "C"

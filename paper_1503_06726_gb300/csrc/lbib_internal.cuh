@@ -1,0 +1,124 @@
+// lbib_internal.cuh -- structures shared by the CUDA translation units of the
+// coupled LB-IB library (not part of the public ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbib.h"
+
+namespace lbib {
+
+// D2Q9 velocity set in the order v0 = 0, v1..v4 = axes (cos, sin)(pi(i-1)/2),
+// v5..v8 = diagonals (1,1), (-1,1), (-1,-1), (1,-1)  (Sec. 6.1 footnotes).
+// D2Q5 uses v0..v4.  Weights: D2Q9 4/9, 1/9, 1/36; D2Q5 1/3, 1/6.
+__host__ __device__ constexpr int cx(int q) {
+    return (q == 1 || q == 5 || q == 8) ? 1 : ((q == 3 || q == 6 || q == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int q) {
+    return (q == 2 || q == 5 || q == 6) ? 1 : ((q == 4 || q == 7 || q == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int q) {
+    return q == 0 ? 0 : (q <= 4 ? ((q + 1) % 4) + 1 : ((q - 5 + 2) % 4) + 5);
+}
+__host__ __device__ constexpr double w9(int q) {
+    return q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr double w5(int q) { return q == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+
+constexpr int kMaxSpecies = 4;
+constexpr int kMaxVertsPerCell = 1024;  // vertices of one cell held in shared memory
+constexpr int kMaxRows = 128;           // scanline rows per cell (else brute force)
+constexpr int kMaxCross = 8;            // crossings per scanline row (else brute force)
+constexpr uint32_t kOutside = 0xFFFFFFFFu;
+
+// diagnostic words at the start of the diag region
+enum Diag : int {
+    kDiagNonFinite = 0,   // a non-finite rho or u was produced
+    kDiagWallStencil = 1, // an IB stencil node fell outside a walled domain (dropped)
+    kDiagRasterSlow = 2,  // a cell used the brute-force labelling path
+    kDiagGeometry = 3,    // a cell's bounding box became non-finite or wider than the lattice
+    kDiagWords = 64
+};
+
+// Workspace layout: byte offsets into the caller's device workspace.
+struct Layout {
+    int64_t pitch = 0;         // elements per lattice row
+    int64_t plane = 0;         // elements per plane (pitch * ny)
+    int es = 0, cs = 0;        // storage / compute element bytes
+    uint64_t f[2] = {0, 0}, g[2] = {0, 0};
+    uint64_t force = 0, u = 0, rho = 0, phi = 0, id = 0, id_out = 0, force_out = 0;
+    uint64_t xy = 0, L0 = 0, k = 0, vforce = 0, off = 0, pres = 0, srcf = 0, area = 0;
+    uint64_t diag = 0;
+    uint64_t total = 0;
+};
+
+bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* L);
+
+// Coefficients of the lattice update, in the compute type.
+template <typename C>
+struct Coefs {
+    C rho0, omega, pref;        // 1/tau, 1 - 1/(2 tau) (Guo)
+    C bfx, bfy;                 // uniform body force density
+    C omegaD[kMaxSpecies];      // 1/tau_D
+    C K[kMaxSpecies][kMaxSpecies];  // react - diag(decay)
+    C srate[kMaxSpecies];
+    C fscale[9], finv[9];       // stored = (f - w rho0) * finv; dev = stored * fscale
+    C gscale[5], ginv[5];
+};
+
+struct LatticeArgs {
+    const void* fsrc;
+    void* fdst;
+    const void* gsrc;
+    void* gdst;
+    void* force;        // interleaved (fx, fy) per node, compute type; read then cleared
+    uint32_t* id;       // packed labels (cell << 4 | src bits), kOutside = none; read then cleared
+    void* u;            // interleaved (ux, uy) per node, compute type (written)
+    void* rho;          // written when out
+    void* phi;          // S planes, written when out
+    uint32_t* id_out;   // written when out
+    void* force_out;    // written when out
+    uint32_t* diag;
+    int nx, ny;
+    int64_t pitch, plane;
+    int out;            // write rho, phi, id_out, force_out
+    int ib;             // read/clear force and labels
+};
+
+struct IBArgs {
+    double2* xy;
+    const double* L0;
+    const double* k;
+    const int32_t* off;
+    const double* pres;
+    const uint8_t* srcf;
+    double2* vforce;
+    void* force;
+    uint32_t* id;
+    const void* u;
+    uint32_t* diag;
+    int nx, ny, bc_y, n_cells;
+    int64_t pitch;
+    double tension;
+    int do_move, do_prep, do_mask, write_vforce;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
+                           const LatticeArgs& a, const void* coefs, dim3 block,
+                           cudaStream_t s);
+cudaError_t launch_ib(int precision, const IBArgs& a, cudaStream_t s);
+cudaError_t launch_areas(const double2* xy, const int32_t* off, int n_cells, double* area,
+                         cudaStream_t s);
+cudaError_t launch_init_populations(int precision, int n_species, int nx, int ny,
+                                    int64_t pitch, int64_t plane, void* f, void* g,
+                                    cudaStream_t s);
+cudaError_t launch_set_species(int precision, int n_species, int s_idx, int nx, int ny,
+                               int64_t pitch, int64_t plane, const double* phi, void* g,
+                               const void* coefs, cudaStream_t s);
+
+}  // namespace lbib

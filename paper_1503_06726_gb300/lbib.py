@@ -1,0 +1,325 @@
+"""Thin Python binding of the C ABI in include/lbib.h (ctypes).
+
+Argument marshalling only: every step of the coupled LB-IB path runs in the
+CUDA library ``_build/liblbib.so``.  PyTorch provides the device workspace
+(a uint8 CUDA tensor) and the stream; nothing here computes the method.
+The functions keep the C names (``lbib_create``, ``lbib_step``, ...);
+:class:`Simulation` bundles them for convenience.
+
+Importing this module does not need a GPU, but loading the library does
+need it to exist: there is no CPU fallback, and a missing library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblbib.so")
+
+LBIB_OK = 0
+LBIB_E_PARAM = -1
+LBIB_E_WORKSPACE = -2
+LBIB_E_CELLS = -3
+LBIB_E_NONFINITE = -4
+LBIB_E_TIMEOUT = -5
+LBIB_E_CUDA = -6
+LBIB_E_STATE = -7
+
+LBIB_FP64, LBIB_FP32, LBIB_FP16 = 0, 1, 2
+LBIB_GUO, LBIB_HE_PAPER = 0, 1
+LBIB_RHO, LBIB_U, LBIB_PHI, LBIB_X = 1, 2, 4, 8
+LBIB_AREA, LBIB_ID, LBIB_FORCE, LBIB_VFORCE = 16, 32, 64, 128
+
+PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
+
+# every symbol declared in include/lbib.h
+EXPORTS = (
+    "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_cell_params",
+    "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
+    "lbib_get_state", "lbib_set_state", "lbib_destroy", "lbib_last_error", "lbib_status_string",
+)
+
+
+class LbibError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_status_name(code)} ({code}): {msg}")
+        self.code = code
+
+
+class lbib_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("bc_y", ctypes.c_int32),
+        ("n_species", ctypes.c_int32), ("tau", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("D", ctypes.c_double * 4), ("decay", ctypes.c_double * 4),
+        ("react", (ctypes.c_double * 4) * 4), ("src_rate", ctypes.c_double * 4),
+        ("forcing", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("fp16_scale", ctypes.c_double), ("fp16_scale_species", ctypes.c_double),
+        ("tension", ctypes.c_double), ("body_force", ctypes.c_double * 2),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+    P = ctypes.POINTER(lbib_params)
+    sig = {
+        "lbib_workspace_size": (ctypes.c_int, [P, i32, i32, ctypes.POINTER(u64)]),
+        "lbib_create": (ctypes.c_int, [P, i32, i32, vp, u64, vp, ctypes.POINTER(vp)]),
+        "lbib_set_cells": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "lbib_set_cell_params": (ctypes.c_int, [vp, vp, vp]),
+        "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
+        "lbib_step": (ctypes.c_int, [vp, i32]),
+        "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
+        "lbib_get_fields": (ctypes.c_int, [vp, u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "lbib_get_sizes": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "lbib_state_size": (ctypes.c_int, [vp, ctypes.POINTER(u64)]),
+        "lbib_get_state": (ctypes.c_int, [vp, vp, u64]),
+        "lbib_set_state": (ctypes.c_int, [vp, vp, u64]),
+        "lbib_destroy": (None, [vp]),
+        "lbib_last_error": (ctypes.c_char_p, [vp]),
+        "lbib_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _status_name(code: int) -> str:
+    try:
+        return load().lbib_status_string(code).decode()
+    except Exception:
+        return str(code)
+
+
+def _check(rc: int, ctx=None):
+    if rc != LBIB_OK:
+        msg = load().lbib_last_error(ctx).decode(errors="replace")
+        raise LbibError(rc, msg)
+
+
+def _p(a, dtype):
+    if a is None:
+        return None, None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
+    """lbib_params from any object with the fields of the C struct."""
+    o = lbib_params()
+    o.nx, o.ny, o.bc_y, o.n_species = int(p.nx), int(p.ny), int(p.bc_y), int(p.n_species)
+    o.tau, o.rho0 = float(p.tau), float(p.rho0)
+    for s in range(4):
+        o.D[s] = float(p.D[s])
+        o.decay[s] = float(p.decay[s])
+        o.src_rate[s] = float(p.src_rate[s])
+        for b in range(4):
+            o.react[s][b] = float(p.react[s][b])
+    o.forcing = int(getattr(p, "forcing", 0))
+    o.precision = int(precision)
+    o.fp16_scale = float(getattr(p, "fp16_scale", 0.0) or 0.0)
+    o.fp16_scale_species = float(getattr(p, "fp16_scale_species", 0.0) or 0.0)
+    o.tension = float(getattr(p, "tension", 0.0) or 0.0)
+    bf = getattr(p, "body_force", (0.0, 0.0)) or (0.0, 0.0)
+    o.body_force[0], o.body_force[1] = float(bf[0]), float(bf[1])
+    return o
+
+
+# ---------------------------------------------------------------- C names
+def lbib_workspace_size(params: lbib_params, max_vertices: int, max_cells: int) -> int:
+    n = ctypes.c_uint64(0)
+    _check(load().lbib_workspace_size(ctypes.byref(params), max_vertices, max_cells, ctypes.byref(n)))
+    return int(n.value)
+
+
+def lbib_create(params: lbib_params, max_vertices: int, max_cells: int, d_workspace: int,
+                nbytes: int, stream: int) -> int:
+    ctx = ctypes.c_void_p(0)
+    _check(load().lbib_create(ctypes.byref(params), max_vertices, max_cells,
+                              ctypes.c_void_p(d_workspace), nbytes, ctypes.c_void_p(stream),
+                              ctypes.byref(ctx)))
+    return ctx.value
+
+
+def lbib_set_cells(ctx, cell_off, xy, rest_len=None, k_spring=None, pressure=None, src_flag=None):
+    off, off_p = _p(cell_off, np.int32)
+    xy_, xy_p = _p(xy, np.float64)
+    L0, L0_p = _p(rest_len, np.float64)
+    k, k_p = _p(k_spring, np.float64)
+    pr, pr_p = _p(pressure, np.float64)
+    sf, sf_p = _p(src_flag, np.uint8)
+    _check(load().lbib_set_cells(ctx, len(off) - 1, off_p, xy_p, L0_p, k_p, pr_p, sf_p), ctx)
+
+
+def lbib_set_cell_params(ctx, pressure=None, src_flag=None):
+    pr, pr_p = _p(pressure, np.float64)
+    sf, sf_p = _p(src_flag, np.uint8)
+    _check(load().lbib_set_cell_params(ctx, pr_p, sf_p), ctx)
+
+
+def lbib_set_species(ctx, s: int, phi):
+    a, a_p = _p(phi, np.float64)
+    _check(load().lbib_set_species(ctx, s, a_p), ctx)
+
+
+def lbib_step(ctx, n_steps: int):
+    _check(load().lbib_step(ctx, int(n_steps)), ctx)
+
+
+def lbib_step_profiled(ctx, n_steps: int):
+    """(lattice ms, IB ms) summed over the launches of n_steps steps."""
+    ms = np.zeros(2)
+    _check(load().lbib_step_profiled(ctx, int(n_steps), ms.ctypes.data_as(ctypes.c_void_p)), ctx)
+    return float(ms[0]), float(ms[1])
+
+
+def lbib_get_fields(ctx, which: int, nx: int, ny: int, n_species: int, n_vertices: int,
+                    n_cells: int) -> dict:
+    out = {}
+
+    def buf(key, shape, dtype=np.float64, flag=0):
+        if which & flag:
+            out[key] = np.empty(shape, dtype)
+            return out[key].ctypes.data_as(ctypes.c_void_p)
+        return None
+
+    rho = buf("rho", (ny, nx), flag=LBIB_RHO)
+    ux = buf("ux", (ny, nx), flag=LBIB_U)
+    uy = buf("uy", (ny, nx), flag=LBIB_U)
+    phi = buf("phi", (max(n_species, 1), ny, nx), flag=LBIB_PHI)
+    xy = buf("xy", (max(n_vertices, 1), 2), flag=LBIB_X)
+    area = buf("area", (max(n_cells, 1),), flag=LBIB_AREA)
+    idp = buf("id", (ny, nx), np.int32, flag=LBIB_ID)
+    force = buf("force", (ny, nx, 2), flag=LBIB_FORCE)
+    vf = buf("vforce", (max(n_vertices, 1), 2), flag=LBIB_VFORCE)
+    _check(load().lbib_get_fields(ctx, which, rho, ux, uy, phi, xy, area, idp, force, vf), ctx)
+    if "phi" in out:
+        out["phi"] = out["phi"][:n_species]
+    for k, n in (("xy", n_vertices), ("vforce", n_vertices), ("area", n_cells)):
+        if k in out:
+            out[k] = out[k][:n]
+    return out
+
+
+def lbib_get_sizes(ctx):
+    v, c = ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().lbib_get_sizes(ctx, ctypes.byref(v), ctypes.byref(c)), ctx)
+    return v.value, c.value
+
+
+def lbib_state_size(ctx) -> int:
+    n = ctypes.c_uint64(0)
+    _check(load().lbib_state_size(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def lbib_get_state(ctx) -> np.ndarray:
+    n = lbib_state_size(ctx)
+    buf = np.empty(n, np.uint8)
+    _check(load().lbib_get_state(ctx, buf.ctypes.data_as(ctypes.c_void_p), n), ctx)
+    return buf
+
+
+def lbib_set_state(ctx, state: np.ndarray):
+    b = np.ascontiguousarray(state, np.uint8)
+    _check(load().lbib_set_state(ctx, b.ctypes.data_as(ctypes.c_void_p), b.size), ctx)
+
+
+def lbib_destroy(ctx):
+    if ctx:
+        load().lbib_destroy(ctx)
+
+
+def lbib_last_error(ctx=None) -> str:
+    return load().lbib_last_error(ctx).decode(errors="replace")
+
+
+def lbib_status_string(code: int) -> str:
+    return load().lbib_status_string(code).decode()
+
+
+# ---------------------------------------------------------------- convenience
+class Simulation:
+    """One tissue on one GPU.  The workspace is a torch uint8 CUDA tensor
+    owned by this object; the stream defaults to torch's current stream."""
+
+    def __init__(self, params, precision: int = LBIB_FP64, max_vertices: int = 0,
+                 max_cells: int = 0, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbib needs a CUDA device; there is no CPU path")
+        load()
+        self.device = torch.device(device or "cuda")
+        self.cparams = make_params(params, precision)
+        self.nx, self.ny = int(params.nx), int(params.ny)
+        self.n_species = int(params.n_species)
+        self.nbytes = lbib_workspace_size(self.cparams, max_vertices, max_cells)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.ctx = lbib_create(self.cparams, max_vertices, max_cells, self.workspace.data_ptr(),
+                               self.nbytes, self.stream.cuda_stream)
+        self.n_vertices = 0
+        self.n_cells = 0
+
+    def set_cells(self, tissue=None, **kw):
+        if tissue is not None:
+            kw = dict(cell_off=tissue.cell_off, xy=tissue.xy, rest_len=tissue.rest_len,
+                      k_spring=tissue.k_spring, pressure=tissue.pressure,
+                      src_flag=tissue.src_flag)
+        lbib_set_cells(self.ctx, **kw)
+        self.n_vertices, self.n_cells = lbib_get_sizes(self.ctx)
+
+    def set_cell_params(self, pressure=None, src_flag=None):
+        lbib_set_cell_params(self.ctx, pressure, src_flag)
+
+    def set_species(self, s: int, phi):
+        lbib_set_species(self.ctx, s, phi)
+
+    def step(self, n: int = 1):
+        lbib_step(self.ctx, n)
+
+    def step_profiled(self, n: int):
+        return lbib_step_profiled(self.ctx, n)
+
+    def fields(self, which: int = LBIB_RHO | LBIB_U | LBIB_PHI | LBIB_X) -> dict:
+        if self.n_species == 0:
+            which &= ~LBIB_PHI
+        if self.n_cells == 0:
+            which &= ~(LBIB_X | LBIB_AREA | LBIB_ID | LBIB_FORCE | LBIB_VFORCE)
+        return lbib_get_fields(self.ctx, which, self.nx, self.ny, self.n_species,
+                               self.n_vertices, self.n_cells)
+
+    def get_state(self) -> np.ndarray:
+        return lbib_get_state(self.ctx)
+
+    def set_state(self, st):
+        lbib_set_state(self.ctx, st)
+        self.n_vertices, self.n_cells = lbib_get_sizes(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lbib_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
