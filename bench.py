@@ -273,7 +273,9 @@ def run_gb300(args, rank, world, dist):
         mlups, steps, dt, cores = oracle_sample(w, args.cpu_seconds, 60)
         cpu = {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{steps} coupled FP64 steps of {w.name} from rest ({dt:.1f} s)"}
-    ws = 2 * alg_bytes + N * (8 + 8 + 4)
+    # both population buffers (= the algorithmic bytes of one launch) plus the
+    # force, velocity and label planes
+    ws = alg_bytes + N * (2 * 4 * (2 if prec == "fp64" else 1) * 2 + 4)
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -304,7 +306,7 @@ def run_reference(args, rank, world):
     p = w.params
     # bounded sample: at most a minute of whole coupled oracle steps
     max_steps = max(1, args.steps)
-    _, wsteps, _, _ = oracle_sample(w, 0.0, max(1, min(args.warmup, 1)))
+    _, wsteps, _, _ = oracle_sample(w, 1e9, max(1, min(args.warmup, 3)))
     mlups, steps, dt, cores = oracle_sample(w, args.ref_seconds, max_steps)
     return {
         "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": world,

@@ -55,6 +55,15 @@ __device__ __forceinline__ void axis_weights(double X, int* base, C w[4]) {
     }
 }
 
+// spread one weighted force into a node: FP32 uses the float2 vector atomic
+__device__ __forceinline__ void spread_add(float2* p, float fx, float fy) {
+    atomicAdd(p, make_float2(fx, fy));
+}
+__device__ __forceinline__ void spread_add(double2* p, double fx, double fy) {
+    atomicAdd(&p->x, fx);
+    atomicAdd(&p->y, fy);
+}
+
 __device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
 
@@ -62,6 +71,7 @@ template <typename C>
 __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
     using V2 = typename std::conditional<sizeof(C) == 8, double2, float2>::type;
     __shared__ double2 sx[kMaxVertsPerCell];
+    __shared__ V2 sedge[kMaxVertsPerCell];
     __shared__ int rowcnt[kMaxRows];
     __shared__ int thr[kMaxRows * kMaxCross];
     __shared__ double red[4][4];
@@ -83,8 +93,9 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
             const V2* u = static_cast<const V2*>(a.u);
             C Ux = C(0), Uy = C(0);
             int ix[4];
+            ix[0] = wrapi(bx, a.nx);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ix[i] = wrapi(bx + i, a.nx);
+            for (int i = 1; i < 4; ++i) ix[i] = (ix[i - 1] + 1 == a.nx) ? 0 : ix[i - 1] + 1;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 int J = by + j;
@@ -112,47 +123,61 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
     __syncthreads();
 
     // ---- (2) vertex forces and spreading
+    // spring of edge t -> t+1, once per edge: the force on vertex t (its
+    // partner t+1 receives the opposite).  FP64 path: all FP64.  FP32 path:
+    // the stretch |d| - L0 = (|d|^2 - L0^2)/(|d| + L0) takes its cancelling
+    // difference in FP64 and the rest in FP32.
+    for (int t = tid; t < n; t += blockDim.x) {
+        const double2 X = sx[t], Xn = sx[(t == n - 1) ? 0 : t + 1];
+        const double dx = Xn.x - X.x, dy = Xn.y - X.y;
+        const double L0 = a.L0[v0 + t], kk = a.k[v0 + t];
+        V2 sp;
+        if (sizeof(C) == 8) {
+            double len = sqrt(dx * dx + dy * dy);
+            double sc = kk * (len - L0) / len;
+            sp.x = (C)(sc * dx);
+            sp.y = (C)(sc * dy);
+        } else {
+            const double len2 = dx * dx + dy * dy;
+            const float d2 = (float)(len2 - L0 * L0);
+            const float len = sqrtf((float)len2);
+            const float sc = (float)kk * (d2 / (len + (float)L0)) / len;
+            sp.x = (C)(sc * (float)dx);
+            sp.y = (C)(sc * (float)dy);
+        }
+        sedge[t] = sp;
+    }
+    __syncthreads();
     {
         V2* force = static_cast<V2*>(a.force);
-        const double p = a.pres[c];
+        const C p = (C)a.pres[c];
+        const C ten = (C)a.tension;
         for (int t = tid; t < n; t += blockDim.x) {
             const int tp = (t == 0) ? n - 1 : t - 1;
             const int tn = (t == n - 1) ? 0 : t + 1;
             const double2 X = sx[t], Xp = sx[tp], Xn = sx[tn];
-            double Fx = 0.0, Fy = 0.0;
-            {   // spring of edge t -> t+1 pulls towards the next vertex
-                double dx = Xn.x - X.x, dy = Xn.y - X.y;
-                double len = sqrt(dx * dx + dy * dy);
-                double s = a.k[v0 + t] * (len - a.L0[v0 + t]) / len;
-                Fx += s * dx;
-                Fy += s * dy;
-            }
-            {   // spring of edge t-1 -> t, the partner end
-                double dx = X.x - Xp.x, dy = X.y - Xp.y;
-                double len = sqrt(dx * dx + dy * dy);
-                double s = a.k[v0 + tp] * (len - a.L0[v0 + tp]) / len;
-                Fx -= s * dx;
-                Fy -= s * dy;
-            }
+            const V2 e0 = sedge[t], e1 = sedge[tp];
+            C Fx = e0.x - e1.x, Fy = e0.y - e1.y;
             // pressure p dA/dX for a CCW polygon
-            Fx += 0.5 * p * (Xn.y - Xp.y);
-            Fy += 0.5 * p * (Xp.x - Xn.x);
-            if (a.tension != 0.0) {  // Eq. membraneforce
-                double ax = Xp.x - X.x, ay = Xp.y - X.y, bx = Xn.x - X.x, by = Xn.y - X.y;
-                double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
-                Fx += a.tension * (ax / la + bx / lb);
-                Fy += a.tension * (ay / la + by / lb);
+            Fx += C(0.5) * p * (C)(Xn.y - Xp.y);
+            Fy += C(0.5) * p * (C)(Xp.x - Xn.x);
+            if (ten != C(0)) {  // Eq. membraneforce
+                const C ax = (C)(Xp.x - X.x), ay = (C)(Xp.y - X.y);
+                const C bx = (C)(Xn.x - X.x), by = (C)(Xn.y - X.y);
+                const C la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
+                Fx += ten * (ax / la + bx / lb);
+                Fy += ten * (ay / la + by / lb);
             }
-            if (a.write_vforce) a.vforce[v0 + t] = make_double2(Fx, Fy);
+            if (a.write_vforce) a.vforce[v0 + t] = make_double2((double)Fx, (double)Fy);
 
             int bxi, byi;
             C wx[4], wy[4];
             axis_weights<C>(X.x, &bxi, wx);
             axis_weights<C>(X.y, &byi, wy);
-            const C fx = (C)Fx, fy = (C)Fy;
             int ix[4];
+            ix[0] = wrapi(bxi, a.nx);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) ix[i] = wrapi(bxi + i, a.nx);
+            for (int i = 1; i < 4; ++i) ix[i] = (ix[i - 1] + 1 == a.nx) ? 0 : ix[i - 1] + 1;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 int J = byi + j;
@@ -167,9 +192,8 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
                 V2* row = force + (int64_t)J * a.pitch;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    C w = wx[i] * wy[j];
-                    atomicAdd(&row[ix[i]].x, fx * w);
-                    atomicAdd(&row[ix[i]].y, fy * w);
+                    const C w = wx[i] * wy[j];
+                    spread_add(&row[ix[i]], Fx * w, Fy * w);
                 }
             }
         }
@@ -248,13 +272,28 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
     }
     uint32_t* id = a.id;
     if (scan) {
-        for (int e = tid; e < rows * cols; e += blockDim.x) {
-            const int r = e / cols, I = I0 + e % cols, J = J0 + r;
+        // node e of the box = (row r, column cc), advanced by blockDim.x each
+        // iteration without divisions; wrapped indices follow incrementally
+        const int step_r = blockDim.x / cols, step_c = blockDim.x % cols;
+        int r = tid / cols, cc = tid % cols;
+        const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
+        for (; r < rows; r += step_r, cc += step_c) {
+            if (cc >= cols) {
+                cc -= cols;
+                ++r;
+                if (r >= rows) break;
+            }
+            const int J = J0 + r, I = I0 + cc;
             if (a.bc_y && (J < 0 || J >= a.ny)) continue;
             const int m = rowcnt[r];
             int cnt = 0;
             for (int q = 0; q < m; ++q) cnt += (thr[r * kMaxCross + q] > I);
-            if (cnt & 1) atomicMin(id + (int64_t)wrapi(J, a.ny) * a.pitch + wrapi(I, a.nx), code);
+            if (cnt & 1) {
+                int wI = wI0 + cc, wJ = wJ0 + r;
+                if (wI >= a.nx) wI -= a.nx;
+                if (wJ >= a.ny) wJ -= a.ny;
+                atomicMin(id + (int64_t)wJ * a.pitch + wI, code);
+            }
         }
     } else {
         // brute force: the same predicate per node over all edges

@@ -31,17 +31,17 @@ template <typename T, typename C>
 struct Store;
 template <>
 struct Store<double, double> {
-    static __device__ __forceinline__ double ld(const double* p) { return *p; }
+    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <>
 struct Store<float, float> {
-    static __device__ __forceinline__ float ld(const float* p) { return *p; }
+    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <>
 struct Store<__half, float> {
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -51,6 +51,19 @@ template <>
 struct Vec2<double> { using T = double2; };
 template <>
 struct Vec2<float> { using T = float2; };
+
+// Pull the 5 populations of one D2Q5 set (or the first 5 of D2Q9) at a node.
+template <typename T, typename C, bool WALLS>
+__device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64_t r0, int64_t rm,
+                                      int64_t rp, int x, int xm, int xp, bool lo, bool hi,
+                                      C g[5]) {
+    using St = Store<T, C>;
+    g[0] = St::ld(B + node);
+    g[1] = St::ld(B + 1 * P + r0 + xm);
+    g[3] = St::ld(B + 3 * P + r0 + xp);
+    g[2] = (WALLS && lo) ? St::ld(B + 4 * P + node) : St::ld(B + 2 * P + rm + x);
+    g[4] = (WALLS && hi) ? St::ld(B + 2 * P + node) : St::ld(B + 4 * P + rp + x);
+}
 
 template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k) {
@@ -72,56 +85,48 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
     const int64_t rp = (int64_t)yp * a.pitch;
     const int64_t node = r0 + x;
 
-    // ---- stream (pull) the fluid populations
+    // ---- every load of the node first (all independent, read-only path), so
+    // that a thread has all its DRAM requests in flight at once
     const T* F = static_cast<const T*>(a.fsrc);
     C d[9];
-    d[0] = St::ld(F + node);
-    d[1] = St::ld(F + 1 * P + r0 + xm);
-    d[3] = St::ld(F + 3 * P + r0 + xp);
+    pull5<T, C, WALLS>(F, P, node, r0, rm, rp, x, xm, xp, lo_wall, hi_wall, d);
     if (lo_wall) {  // half-way bounce-back: v_y = +1 populations reflect off y = -1/2
-        d[2] = St::ld(F + 4 * P + node);
         d[5] = St::ld(F + 7 * P + node);
         d[6] = St::ld(F + 8 * P + node);
     } else {
-        d[2] = St::ld(F + 2 * P + rm + x);
         d[5] = St::ld(F + 5 * P + rm + xm);
         d[6] = St::ld(F + 6 * P + rm + xp);
     }
     if (hi_wall) {  // v_y = -1 populations reflect off y = ny - 1/2
-        d[4] = St::ld(F + 2 * P + node);
         d[7] = St::ld(F + 5 * P + node);
         d[8] = St::ld(F + 6 * P + node);
     } else {
-        d[4] = St::ld(F + 4 * P + rp + x);
         d[7] = St::ld(F + 7 * P + rp + xp);
         d[8] = St::ld(F + 8 * P + rp + xm);
     }
+    C g[S > 0 ? S : 1][5];
+    {
+        const T* Gi = static_cast<const T*>(a.gsrc);
+#pragma unroll
+        for (int s = 0; s < S; ++s)
+            pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, lo_wall,
+                               hi_wall, g[s]);
+    }
+    V2 fv;
+    fv.x = C(0);
+    fv.y = C(0);
+    uint32_t label = kOutside;
+    if (a.ib) {
+        fv = static_cast<const V2*>(a.force)[node];
+        label = a.id[node];
+    }
+
+    // ---- moments (Sec. 6.1) with the half-force velocity shift (Guo)
     if (SCALED) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) d[q] *= k.fscale[q];
     }
-
-    // ---- body force: spread IB force (read, then reset) plus the uniform part
-    C Fx = k.bfx, Fy = k.bfy;
-    uint32_t label = kOutside;
-    if (a.ib) {
-        V2* fp = static_cast<V2*>(a.force) + node;
-        V2 fv = *fp;
-        Fx += fv.x;
-        Fy += fv.y;
-        V2 z;
-        z.x = C(0);
-        z.y = C(0);
-        *fp = z;
-        label = a.id[node];
-        a.id[node] = kOutside;
-        if (a.out) {
-            a.id_out[node] = label;
-            static_cast<V2*>(a.force_out)[node] = fv;
-        }
-    }
-
-    // ---- moments (Sec. 6.1) with the half-force velocity shift (Guo)
+    const C Fx = k.bfx + fv.x, Fy = k.bfy + fv.y;
     const C drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
     const C rho = k.rho0 + drho;
     const C jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
     const C usq15 = C(1.5) * (ux * ux + uy * uy);
     const C uF = ux * Fx + uy * Fy;
 
-    // ---- collide and store
+    // ---- collide and store the fluid
     T* G = static_cast<T*>(a.fdst);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
@@ -156,30 +161,13 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
         St::st(G + q * P + node, dn);
     }
 
-    {
-        V2 uv;
-        uv.x = ux;
-        uv.y = uy;
-        static_cast<V2*>(a.u)[node] = uv;
-    }
-    if (a.out) static_cast<C*>(a.rho)[node] = rho;
-    if (!(rho > C(0)) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.diag + kDiagNonFinite, 1u);
-
-    // ---- species (D2Q5): pull all, then react and collide with the fluid u
+    // ---- species (D2Q5): react and collide with the fluid u
     if (S > 0) {
         const uint32_t bits = (label == kOutside) ? 0u : (label & 0xFu);
-        const T* Gi = static_cast<const T*>(a.gsrc);
         T* Go = static_cast<T*>(a.gdst);
-        C g[S > 0 ? S : 1][5];
         C ph[S > 0 ? S : 1];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            const T* B = Gi + (int64_t)s * 5 * P;
-            g[s][0] = St::ld(B + node);
-            g[s][1] = St::ld(B + 1 * P + r0 + xm);
-            g[s][3] = St::ld(B + 3 * P + r0 + xp);
-            g[s][2] = lo_wall ? St::ld(B + 4 * P + node) : St::ld(B + 2 * P + rm + x);
-            g[s][4] = hi_wall ? St::ld(B + 2 * P + node) : St::ld(B + 4 * P + rp + x);
             if (SCALED) {
 #pragma unroll
                 for (int q = 0; q < 5; ++q) g[s][q] *= k.gscale[q];
@@ -204,6 +192,27 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
             if (a.out) static_cast<C*>(a.phi)[(int64_t)s * P + node] = ph[s];
         }
     }
+
+    // ---- velocity for the interpolation, resets, outputs
+    {
+        V2 uv;
+        uv.x = ux;
+        uv.y = uy;
+        static_cast<V2*>(a.u)[node] = uv;
+    }
+    if (a.ib) {
+        V2 z;
+        z.x = C(0);
+        z.y = C(0);
+        static_cast<V2*>(a.force)[node] = z;
+        a.id[node] = kOutside;
+        if (a.out) {
+            a.id_out[node] = label;
+            static_cast<V2*>(a.force_out)[node] = fv;
+        }
+    }
+    if (a.out) static_cast<C*>(a.rho)[node] = rho;
+    if (!(rho > C(0)) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.diag + kDiagNonFinite, 1u);
 }
 
 template <typename T, typename C, int S, bool WALLS, int FORCING>

@@ -60,9 +60,9 @@ def gpu_run(lb, w, n, precision, which=ALL, tension=0.0, body=None, forcing=None
 
 def check_fp64(got, ref, S, tol=1e-10, labels=True):
     eu = max(rel(got["ux"], ref.ux), rel(got["uy"], ref.uy))
-    # density: relative to its variation about rho0, floored at 1e-4 so that
+    # density: relative to its variation about rho0, floored at 1e-2 so that
     # the rest state (rho - 1 at the rounding level) is not ill-conditioned
-    er = np.abs(got["rho"] - ref.rho).max() / max(np.abs(ref.rho - 1.0).max(), 1e-4)
+    er = np.abs(got["rho"] - ref.rho).max() / max(np.abs(ref.rho - 1.0).max(), 1e-2)
     assert eu < tol, eu
     assert er < tol, er
     if S:
