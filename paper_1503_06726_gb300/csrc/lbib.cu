@@ -34,7 +34,9 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.es = p.precision == LBIB_FP64 ? 8 : (p.precision == LBIB_FP32 ? 4 : 2);
     l.cs = p.precision == LBIB_FP64 ? 8 : 4;
     l.pitch = (int64_t)align_up((uint64_t)p.nx, 64);
-    l.plane = l.pitch * p.ny;
+    // planes are padded by 1.5 KiB (six 256-byte blocks) so that the 9 + 5S
+    // streams of one node do not sit at a power-of-two distance from each other
+    l.plane = l.pitch * p.ny + 1536 / l.es;
     const uint64_t P = (uint64_t)l.plane;
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) {
