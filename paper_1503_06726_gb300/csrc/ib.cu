@@ -20,39 +20,50 @@
 // evaluated with explicitly rounded FP64 operations (no contraction), so the
 // labels are exact.  Overlapping cells: the lowest cell index wins (atomicMin
 // on the packed label cell << 4 | source bits).
+#include <climits>
 #include <type_traits>
 
 #include "lbib_internal.cuh"
 
 namespace lbib {
 
+constexpr int kIBThreads = 256;
+static_assert(kIBThreads >= kMaxRows, "row counters are cleared one per thread");
+
 __device__ __forceinline__ int wrapi(int a, int n) {
     int r = a % n;
     return r < 0 ? r + n : r;
 }
 
-__device__ __forceinline__ double delta1d(double r) {
-    double a = fabs(r);
-    return a > 2.0 ? 0.0 : 0.25 * (1.0 + cospi(0.5 * a));
-}
-__device__ __forceinline__ float delta1d(float r) {
-    float a = fabsf(r);
-    return a > 2.f ? 0.f : 0.25f * (1.f + cospif(0.5f * a));
-}
-
-// weights of the 4 support nodes along one axis, base = floor(X) - 1
+// Weights of the 4 support nodes along one axis, base = floor(X) - 1.
+// With f = X - floor(X) the four offsets are r = -1-f, -f, 1-f, 2-f, and
+// cos(pi |r| / 2) is -sin, cos, sin, -cos of pi f / 2 respectively, so one
+// sincospi gives all four values of Eq. 1Dkernel.
 template <typename C>
 __device__ __forceinline__ void axis_weights(double X, int* base, C w[4]) {
-    double fl = floor(X);
+    const double fl = floor(X);
     *base = (int)fl - 1;
+    C sn, cs;
     if (sizeof(C) == 8) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) w[a] = (C)delta1d((fl - 1.0 + a) - X);
+        double s2, c2;
+        sincospi(0.5 * (X - fl), &s2, &c2);
+        sn = (C)s2;
+        cs = (C)c2;
     } else {
-        float fr = (float)(X - fl);  // in [0, 1), exact in double
-#pragma unroll
-        for (int a = 0; a < 4; ++a) w[a] = (C)delta1d((float)(a - 1) - fr);
+        float s2, c2;
+        sincospif(0.5f * (float)(X - fl), &s2, &c2);
+        sn = (C)s2;
+        cs = (C)c2;
     }
+    w[0] = C(0.25) * (C(1) - sn);
+    w[1] = C(0.25) * (C(1) + cs);
+    w[2] = C(0.25) * (C(1) + sn);
+    w[3] = C(0.25) * (C(1) - cs);
+}
+
+// raise a diagnostic flag (labelling-only callers may pass no flag words)
+__device__ __forceinline__ void raise_flag(uint32_t* diag, int k) {
+    if (diag) atomicOr(diag + k, 1u);
 }
 
 // spread one weighted force into a node: FP32 uses the float2 vector atomic
@@ -64,26 +75,59 @@ __device__ __forceinline__ void spread_add(double2* p, double fx, double fy) {
     atomicAdd(&p->y, fy);
 }
 
-__device__ __forceinline__ double dmin(double a, double b) { return a < b ? a : b; }
-__device__ __forceinline__ double dmax(double a, double b) { return a > b ? a : b; }
+// Hookean spring of the edge A -> B with constant k and rest length L0: the
+// force on A (B receives the opposite).  FP64 path: all FP64.  FP32 path: the
+// stretch |d| - L0 = (|d|^2 - L0^2)/(|d| + L0) takes its cancelling difference
+// in FP64 and the rest in FP32.
+template <typename C>
+__device__ __forceinline__ void spring(double2 A, double2 B, double L0, double kk, C* fx, C* fy) {
+    const double dx = B.x - A.x, dy = B.y - A.y;
+    if (sizeof(C) == 8) {
+        const double len = sqrt(dx * dx + dy * dy);
+        const double sc = kk * (len - L0) / len;
+        *fx = (C)(sc * dx);
+        *fy = (C)(sc * dy);
+    } else {
+        const double len2 = dx * dx + dy * dy;
+        const float d2 = (float)(len2 - L0 * L0);
+        const float len = sqrtf((float)len2);
+        const float sc = (float)kk * (d2 / (len + (float)L0)) / len;
+        *fx = (C)(sc * (float)dx);
+        *fy = (C)(sc * (float)dy);
+    }
+}
+
+// crossing abscissa of edge A -> B with row y, every operation rounded on its own
+__device__ __forceinline__ double crossing_x(double2 A, double2 B, double yn) {
+    return __dadd_rn(A.x, __ddiv_rn(__dmul_rn(__dsub_rn(yn, A.y), __dsub_rn(B.x, A.x)),
+                                    __dsub_rn(B.y, A.y)));
+}
 
 template <typename C>
-__global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
+__global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
     using V2 = typename std::conditional<sizeof(C) == 8, double2, float2>::type;
     __shared__ double2 sx[kMaxVertsPerCell];
-    __shared__ V2 sedge[kMaxVertsPerCell];
     __shared__ int rowcnt[kMaxRows];
     __shared__ int thr[kMaxRows * kMaxCross];
-    __shared__ double red[4][4];
-    __shared__ int s_overflow;
+    __shared__ int sbox[4];  // I0, I1, J0, J1
+    __shared__ int s_flag;   // 1: a scanline row overflowed, 2: geometry not finite
 
     const int c = blockIdx.x;
     const int v0 = a.off[c];
     const int n = a.off[c + 1] - v0;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = kIBThreads / 32;
 
-    // ---- (1) interpolate and move, or just load
-    for (int t = tid; t < n; t += blockDim.x) {
+    if (tid < kMaxRows) rowcnt[tid] = 0;
+    if (tid == 0) {
+        sbox[0] = INT_MAX; sbox[1] = INT_MIN; sbox[2] = INT_MAX; sbox[3] = INT_MIN;
+        s_flag = 0;
+    }
+
+    // ---- (1) interpolate u^n at X^n and move (or just load); integer bounding box
+    int ilo = INT_MAX, ihi = INT_MIN, jlo = INT_MAX, jhi = INT_MIN;
+    bool finite = true;
+    for (int t = tid; t < n; t += kIBThreads) {
         double2 X = a.xy[v0 + t];
         if (a.do_move) {
             int bx, by;
@@ -107,8 +151,8 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
                 const V2* row = u + (int64_t)J * a.pitch;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    V2 v = row[ix[i]];
-                    C w = wx[i] * wy[j];
+                    const V2 v = row[ix[i]];
+                    const C w = wx[i] * wy[j];
                     Ux += v.x * w;
                     Uy += v.y * w;
                 }
@@ -118,55 +162,61 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
             a.xy[v0 + t] = X;
         }
         sx[t] = X;
+        finite = finite && isfinite(X.x) && isfinite(X.y) && fabs(X.x) < 1e9 && fabs(X.y) < 1e9;
+        ilo = min(ilo, __double2int_rd(X.x));
+        ihi = max(ihi, __double2int_ru(X.x));
+        jlo = min(jlo, __double2int_rd(X.y));
+        jhi = max(jhi, __double2int_ru(X.y));
     }
     if (!a.do_prep) return;
-    __syncthreads();
-
-    // ---- (2) vertex forces and spreading
-    // spring of edge t -> t+1, once per edge: the force on vertex t (its
-    // partner t+1 receives the opposite).  FP64 path: all FP64.  FP32 path:
-    // the stretch |d| - L0 = (|d|^2 - L0^2)/(|d| + L0) takes its cancelling
-    // difference in FP64 and the rest in FP32.
-    for (int t = tid; t < n; t += blockDim.x) {
-        const double2 X = sx[t], Xn = sx[(t == n - 1) ? 0 : t + 1];
-        const double dx = Xn.x - X.x, dy = Xn.y - X.y;
-        const double L0 = a.L0[v0 + t], kk = a.k[v0 + t];
-        V2 sp;
-        if (sizeof(C) == 8) {
-            double len = sqrt(dx * dx + dy * dy);
-            double sc = kk * (len - L0) / len;
-            sp.x = (C)(sc * dx);
-            sp.y = (C)(sc * dy);
-        } else {
-            const double len2 = dx * dx + dy * dy;
-            const float d2 = (float)(len2 - L0 * L0);
-            const float len = sqrtf((float)len2);
-            const float sc = (float)kk * (d2 / (len + (float)L0)) / len;
-            sp.x = (C)(sc * (float)dx);
-            sp.y = (C)(sc * (float)dy);
-        }
-        sedge[t] = sp;
+    ilo = __reduce_min_sync(0xffffffffu, ilo);
+    ihi = __reduce_max_sync(0xffffffffu, ihi);
+    jlo = __reduce_min_sync(0xffffffffu, jlo);
+    jhi = __reduce_max_sync(0xffffffffu, jhi);
+    finite = __all_sync(0xffffffffu, finite);
+    __syncthreads();  // sbox / rowcnt initialised
+    if (lane == 0) {
+        atomicMin(&sbox[0], ilo);
+        atomicMax(&sbox[1], ihi);
+        atomicMin(&sbox[2], jlo);
+        atomicMax(&sbox[3], jhi);
+        if (!finite) s_flag = 2;
     }
     __syncthreads();
-    {
+    const int I0 = sbox[0], I1 = sbox[1], J0 = sbox[2], J1 = sbox[3];
+    // Labels need a finite box no wider than the lattice; otherwise the
+    // geometry has blown up: flag it and leave the labels empty so that every
+    // loop below stays bounded by the lattice size.
+    const bool labels = a.do_mask && s_flag == 0 && (I1 - I0) <= a.nx && (J1 - J0) <= a.ny;
+    if (a.do_mask && !labels && tid == 0) raise_flag(a.diag, kDiagGeometry);
+    const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
+    const bool scan = labels && rows <= kMaxRows;
+
+    // ---- (2) first half of the CTA: vertex forces and spreading;
+    //          second half: scanline crossings of every edge
+    constexpr int half = kIBThreads / 2;
+    if (tid < half) {
+      if (a.do_force) {
         V2* force = static_cast<V2*>(a.force);
         const C p = (C)a.pres[c];
         const C ten = (C)a.tension;
-        for (int t = tid; t < n; t += blockDim.x) {
+        for (int t = tid; t < n; t += half) {
             const int tp = (t == 0) ? n - 1 : t - 1;
             const int tn = (t == n - 1) ? 0 : t + 1;
             const double2 X = sx[t], Xp = sx[tp], Xn = sx[tn];
-            const V2 e0 = sedge[t], e1 = sedge[tp];
-            C Fx = e0.x - e1.x, Fy = e0.y - e1.y;
+            C ax_, ay_, bx_, by_;
+            spring<C>(X, Xn, a.L0[v0 + t], a.k[v0 + t], &ax_, &ay_);
+            spring<C>(Xp, X, a.L0[v0 + tp], a.k[v0 + tp], &bx_, &by_);
+            C Fx = ax_ - bx_, Fy = ay_ - by_;
             // pressure p dA/dX for a CCW polygon
             Fx += C(0.5) * p * (C)(Xn.y - Xp.y);
             Fy += C(0.5) * p * (C)(Xp.x - Xn.x);
             if (ten != C(0)) {  // Eq. membraneforce
-                const C ax = (C)(Xp.x - X.x), ay = (C)(Xp.y - X.y);
-                const C bx = (C)(Xn.x - X.x), by = (C)(Xn.y - X.y);
-                const C la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
-                Fx += ten * (ax / la + bx / lb);
-                Fy += ten * (ay / la + by / lb);
+                const C ux_ = (C)(Xp.x - X.x), uy_ = (C)(Xp.y - X.y);
+                const C vx_ = (C)(Xn.x - X.x), vy_ = (C)(Xn.y - X.y);
+                const C la = sqrt(ux_ * ux_ + uy_ * uy_), lb = sqrt(vx_ * vx_ + vy_ * vy_);
+                Fx += ten * (ux_ / la + vx_ / lb);
+                Fy += ten * (uy_ / la + vy_ / lb);
             }
             if (a.write_vforce) a.vforce[v0 + t] = make_double2((double)Fx, (double)Fy);
 
@@ -183,7 +233,7 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
                 int J = byi + j;
                 if (a.bc_y) {
                     if (J < 0 || J >= a.ny) {
-                        atomicOr(a.diag + kDiagWallStencil, 1u);
+                        raise_flag(a.diag, kDiagWallStencil);
                         continue;
                     }
                 } else {
@@ -197,122 +247,101 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
                 }
             }
         }
-    }
-
-    if (!a.do_mask) return;
-
-    // ---- (3) labels: bounding box
-    double xmn = 1e300, xmx = -1e300, ymn = 1e300, ymx = -1e300;
-    for (int t = tid; t < n; t += blockDim.x) {
-        double2 X = sx[t];
-        xmn = dmin(xmn, X.x); xmx = dmax(xmx, X.x);
-        ymn = dmin(ymn, X.y); ymx = dmax(ymx, X.y);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        xmn = dmin(xmn, __shfl_xor_sync(0xffffffffu, xmn, o));
-        xmx = dmax(xmx, __shfl_xor_sync(0xffffffffu, xmx, o));
-        ymn = dmin(ymn, __shfl_xor_sync(0xffffffffu, ymn, o));
-        ymx = dmax(ymx, __shfl_xor_sync(0xffffffffu, ymx, o));
-    }
-    const int warp = tid >> 5, lane = tid & 31, nwarps = blockDim.x >> 5;
-    if (lane == 0) {
-        red[0][warp] = xmn; red[1][warp] = xmx; red[2][warp] = ymn; red[3][warp] = ymx;
-    }
-    if (tid == 0) s_overflow = 0;
-    __syncthreads();
-    xmn = red[0][0]; xmx = red[1][0]; ymn = red[2][0]; ymx = red[3][0];
-    for (int w = 1; w < nwarps; ++w) {
-        xmn = dmin(xmn, red[0][w]); xmx = dmax(xmx, red[1][w]);
-        ymn = dmin(ymn, red[2][w]); ymx = dmax(ymx, red[3][w]);
-    }
-    // A bounding box that is not finite or wider than the lattice means the
-    // geometry has blown up: flag it and leave the labels empty, so that the
-    // loops below stay bounded by the lattice size.
-    if (!(isfinite(xmn) && isfinite(xmx) && isfinite(ymn) && isfinite(ymx)) ||
-        xmx - xmn > (double)a.nx || ymx - ymn > (double)a.ny || fabs(xmn) > 1e9 ||
-        fabs(ymn) > 1e9) {
-        if (tid == 0) atomicOr(a.diag + kDiagGeometry, 1u);
-        return;
-    }
-    const int I0 = (int)floor(xmn), I1 = (int)ceil(xmx);
-    const int J0 = (int)floor(ymn), J1 = (int)ceil(ymx);
-    const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
-    const uint32_t code = ((uint32_t)c << 4) | (uint32_t)(a.srcf[c] & 0xF);
-
-    bool scan = rows <= kMaxRows;
-    if (scan) {
-        for (int r = tid; r < rows; r += blockDim.x) rowcnt[r] = 0;
-        __syncthreads();
-        for (int t = tid; t < n; t += blockDim.x) {
-            const double2 A = sx[t], B = sx[(t == n - 1) ? 0 : t + 1];
-            const double lo = dmin(A.y, B.y), hi = dmax(A.y, B.y);
-            int jlo = (int)ceil(lo) - 1, jhi = (int)ceil(hi);
-            if (jlo < J0) jlo = J0;
-            if (jhi > J1) jhi = J1;
-            for (int J = jlo; J <= jhi; ++J) {
+      }
+    } else if (scan) {
+        for (int e = tid - half; e < n; e += half) {
+            const double2 A = sx[e], B = sx[(e == n - 1) ? 0 : e + 1];
+            const double lo = fmin(A.y, B.y), hi = fmax(A.y, B.y);
+            int jl = __double2int_ru(lo) - 1, jh = __double2int_ru(hi);
+            if (jl < J0) jl = J0;
+            if (jh > J1) jh = J1;
+            for (int J = jl; J <= jh; ++J) {
                 const double yn = (double)J;
                 if ((A.y <= yn) != (B.y <= yn)) {
-                    // x_c = x_a + (y - y_a)(x_b - x_a)/(y_b - y_a), each operation rounded
-                    double xc = __dadd_rn(
-                        A.x, __ddiv_rn(__dmul_rn(__dsub_rn(yn, A.y), __dsub_rn(B.x, A.x)),
-                                       __dsub_rn(B.y, A.y)));
-                    double tc = ceil(xc);
-                    int ti = tc < (double)I0 ? I0 : (tc > (double)(I1 + 1) ? I1 + 1 : (int)tc);
-                    int slot = atomicAdd(&rowcnt[J - J0], 1);
+                    const double tc = ceil(crossing_x(A, B, yn));
+                    const int ti = tc < (double)I0 ? I0 : (tc > (double)(I1 + 1) ? I1 + 1 : (int)tc);
+                    const int slot = atomicAdd(&rowcnt[J - J0], 1);
                     if (slot < kMaxCross)
                         thr[(J - J0) * kMaxCross + slot] = ti;
                     else
-                        s_overflow = 1;
+                        s_flag = 1;
                 }
             }
         }
-        __syncthreads();
-        scan = (s_overflow == 0);
     }
+    if (!a.do_mask) return;
+    __syncthreads();
+    if (!labels) return;
+
+    // ---- (3) labels
     uint32_t* id = a.id;
-    if (scan) {
-        // node e of the box = (row r, column cc), advanced by blockDim.x each
-        // iteration without divisions; wrapped indices follow incrementally
-        const int step_r = blockDim.x / cols, step_c = blockDim.x % cols;
-        int r = tid / cols, cc = tid % cols;
-        const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
-        for (; r < rows; r += step_r, cc += step_c) {
-            if (cc >= cols) {
-                cc -= cols;
-                ++r;
-                if (r >= rows) break;
-            }
-            const int J = J0 + r, I = I0 + cc;
+    const uint32_t code = ((uint32_t)c << 4) | (uint32_t)(a.srcf[c] & 0xF);
+    const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
+    if (scan && s_flag == 0) {
+        // one warp per row: sort the row's thresholds, then fill each span
+        // [t_{2k}, t_{2k+1}) -- the nodes with an odd number of thresholds
+        // above them
+        for (int r = warp; r < rows; r += nwarps) {
+            const int J = J0 + r;
             if (a.bc_y && (J < 0 || J >= a.ny)) continue;
             const int m = rowcnt[r];
-            int cnt = 0;
-            for (int q = 0; q < m; ++q) cnt += (thr[r * kMaxCross + q] > I);
-            if (cnt & 1) {
+            int* tr = thr + r * kMaxCross;
+            if (lane == 0) {
+                for (int q = 1; q < m; ++q) {
+                    const int v = tr[q];
+                    int p = q - 1;
+                    while (p >= 0 && tr[p] > v) {
+                        tr[p + 1] = tr[p];
+                        --p;
+                    }
+                    tr[p + 1] = v;
+                }
+            }
+            __syncwarp();
+            int wJ = wJ0 + r;
+            if (wJ >= a.ny) wJ -= a.ny;
+            uint32_t* rowp = id + (int64_t)wJ * a.pitch;
+            if ((m & 1) == 0) {
+                for (int k = 0; k + 1 < m; k += 2) {
+                    const int lo = tr[k], hi = tr[k + 1];
+                    for (int I = lo + lane; I < hi; I += 32) {
+                        int wI = wI0 + (I - I0);
+                        if (wI >= a.nx) wI -= a.nx;
+                        atomicMin(rowp + wI, code);
+                    }
+                }
+            } else {  // odd count: evaluate the parity rule node by node
+                for (int cc = lane; cc < cols; cc += 32) {
+                    const int I = I0 + cc;
+                    int cnt = 0;
+                    for (int q = 0; q < m; ++q) cnt += (tr[q] > I);
+                    if (cnt & 1) {
+                        int wI = wI0 + cc;
+                        if (wI >= a.nx) wI -= a.nx;
+                        atomicMin(rowp + wI, code);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    } else {
+        // brute force: the same predicate per node over all edges
+        if (tid == 0) raise_flag(a.diag, kDiagRasterSlow);
+        for (int e = tid; e < rows * cols; e += kIBThreads) {
+            const int r = e / cols, cc = e % cols, J = J0 + r;
+            if (a.bc_y && (J < 0 || J >= a.ny)) continue;
+            const double xn = (double)(I0 + cc), yn = (double)J;
+            bool inside = false;
+            for (int t = 0; t < n; ++t) {
+                const double2 A = sx[t], B = sx[(t == n - 1) ? 0 : t + 1];
+                if ((A.y <= yn) != (B.y <= yn) && xn < crossing_x(A, B, yn)) inside = !inside;
+            }
+            if (inside) {
                 int wI = wI0 + cc, wJ = wJ0 + r;
                 if (wI >= a.nx) wI -= a.nx;
                 if (wJ >= a.ny) wJ -= a.ny;
                 atomicMin(id + (int64_t)wJ * a.pitch + wI, code);
             }
-        }
-    } else {
-        // brute force: the same predicate per node over all edges
-        if (tid == 0) atomicAdd(a.diag + kDiagRasterSlow, 1u);
-        for (int e = tid; e < rows * cols; e += blockDim.x) {
-            const int r = e / cols, I = I0 + e % cols, J = J0 + r;
-            if (a.bc_y && (J < 0 || J >= a.ny)) continue;
-            const double xn = (double)I, yn = (double)J;
-            bool inside = false;
-            for (int t = 0; t < n; ++t) {
-                const double2 A = sx[t], B = sx[(t == n - 1) ? 0 : t + 1];
-                if ((A.y <= yn) != (B.y <= yn)) {
-                    double xc = __dadd_rn(
-                        A.x, __ddiv_rn(__dmul_rn(__dsub_rn(yn, A.y), __dsub_rn(B.x, A.x)),
-                                       __dsub_rn(B.y, A.y)));
-                    if (xn < xc) inside = !inside;
-                }
-            }
-            if (inside) atomicMin(id + (int64_t)wrapi(J, a.ny) * a.pitch + wrapi(I, a.nx), code);
         }
     }
 }
@@ -320,9 +349,9 @@ __global__ void __launch_bounds__(128) ib_cell_kernel(IBArgs a) {
 cudaError_t launch_ib(int precision, const IBArgs& a, cudaStream_t s) {
     if (a.n_cells <= 0) return cudaSuccess;
     if (precision == LBIB_FP64)
-        ib_cell_kernel<double><<<a.n_cells, 128, 0, s>>>(a);
+        ib_cell_kernel<double><<<a.n_cells, kIBThreads, 0, s>>>(a);
     else
-        ib_cell_kernel<float><<<a.n_cells, 128, 0, s>>>(a);
+        ib_cell_kernel<float><<<a.n_cells, kIBThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -205,6 +205,7 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) {
     a.do_prep = prep ? 1 : 0;
     a.do_mask = 1;
     a.write_vforce = vforce ? 1 : 0;
+    a.do_force = 1;
     return a;
 }
 

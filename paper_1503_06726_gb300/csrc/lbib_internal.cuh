@@ -105,6 +105,7 @@ struct IBArgs {
     int64_t pitch;
     double tension;
     int do_move, do_prep, do_mask, write_vforce;
+    int do_force;       // compute and spread vertex forces (0: labels only)
 };
 
 // launchers (return cudaError_t of the launch)
