@@ -180,6 +180,49 @@ int lbib_state_size(const lbib_ctx* ctx, uint64_t* bytes_out);
 int lbib_get_state(lbib_ctx* ctx, void* host, uint64_t bytes);
 int lbib_set_state(lbib_ctx* ctx, const void* host, uint64_t bytes);
 
+/* Coupled steps without any allocation.  The paper has no counterpart: this
+ * entry point exists for callers that may not allocate device memory while
+ * they run -- code inside a framework whose memory pool owns the device,
+ * plug-ins that must keep the device footprint fixed after start-up, or host
+ * code that runs while a CUDA graph is being captured.  It runs the kernels of
+ * lbib_step() on state the caller already owns and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * The intermediate planes (second population buffer, spread force, labels,
+ * velocity, diagnostic words) live in one static device array of 4 MiB
+ * inside the library; every GPU that loads the library holds it until the
+ * process exits.  Lattices whose planes do not fit are rejected with
+ * LBIB_E_WORKSPACE (with FP64 storage and one species, 64x64 needs about
+ * 0.6 MiB and 128x128 about 2.4 MiB; 192x192 does not fit).
+ * All calls share the array: calls that overlap on the GPU (two streams, two
+ * host threads) race and give wrong results, so serialise them.  Each call
+ * resets the planes that must start empty.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture begins.  The call
+ * synchronises `cuda_stream` before it returns.
+ *
+ * Arguments (device pointers, on the current device):
+ *   params      as for lbib_create(); params->precision selects the storage
+ *   n_cells, d_cell_off, d_xy (in/out, 2*V), d_rest_len, d_k_spring (V),
+ *               d_pressure (n_cells), d_src_flag (n_cells): as lbib_set_cells()
+ *               but already on the device and complete (no NULL defaults)
+ *   d_f         9 population planes, d_g 5*n_species planes (in/out), in the
+ *               library's storage layout: element bytes b = 8 / 4 / 2 for
+ *               FP64 / FP32 / FP16, row pitch = nx rounded up to a multiple
+ *               of 64 elements, plane stride = pitch*ny + 1536/b elements,
+ *               values stored as the deviations f - w rho0 (FP16: divided by
+ *               w sigma) -- the population section of lbib_get_state(); all
+ *               zero bytes is the rest state
+ *   n_steps     steps to advance; the result is always left in d_f, d_g
+ *   cuda_stream cudaStream_t as void* (NULL = legacy default stream)
+ * Returns LBIB_OK, LBIB_E_PARAM, LBIB_E_WORKSPACE (lattice too large for the
+ * static array), LBIB_E_NONFINITE or LBIB_E_CUDA; lbib_last_error(NULL) gives
+ * the reason. */
+int lbib_step_noalloc(const lbib_params* params, int32_t n_cells, const int32_t* d_cell_off,
+                      double* d_xy, const double* d_rest_len, const double* d_k_spring,
+                      const double* d_pressure, const uint8_t* d_src_flag, void* d_f,
+                      void* d_g, int32_t n_steps, void* cuda_stream);
+
 /* Release the host header (the workspace stays the caller's). */
 void lbib_destroy(lbib_ctx* ctx);
 

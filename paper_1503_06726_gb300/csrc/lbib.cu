@@ -153,6 +153,15 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
     }
 }
 
+namespace lbib {
+void fill_coefs_public(const lbib_params& p, Coefs<double>* k) { fill_coefs(p, k); }
+void fill_coefs_public(const lbib_params& p, Coefs<float>* k) { fill_coefs(p, k); }
+int set_thread_error(int code, const std::string& msg) {
+    g_create_err = msg;
+    return code;
+}
+}  // namespace lbib
+
 static const void* coefs_of(const lbib_ctx* c) {
     return c->p.precision == LBIB_FP64 ? (const void*)&c->kd : (const void*)&c->kf;
 }

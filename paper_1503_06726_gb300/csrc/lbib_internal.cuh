@@ -108,6 +108,11 @@ struct IBArgs {
     int do_force;       // compute and spread vertex forces (0: labels only)
 };
 
+// coefficient tables and the calling thread's error text (lbib_last_error(NULL))
+void fill_coefs_public(const lbib_params& p, Coefs<double>* k);
+void fill_coefs_public(const lbib_params& p, Coefs<float>* k);
+int set_thread_error(int code, const std::string& msg);
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
                            const LatticeArgs& a, const void* coefs, dim3 block,

@@ -40,7 +40,8 @@ PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
 EXPORTS = (
     "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_cell_params",
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
-    "lbib_get_state", "lbib_set_state", "lbib_destroy", "lbib_last_error", "lbib_status_string",
+    "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
+    "lbib_status_string",
 )
 
 
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_state_size": (ctypes.c_int, [vp, ctypes.POINTER(u64)]),
         "lbib_get_state": (ctypes.c_int, [vp, vp, u64]),
         "lbib_set_state": (ctypes.c_int, [vp, vp, u64]),
+        "lbib_step_noalloc": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]),
         "lbib_destroy": (None, [vp]),
         "lbib_last_error": (ctypes.c_char_p, [vp]),
         "lbib_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -239,6 +241,18 @@ def lbib_get_state(ctx) -> np.ndarray:
 def lbib_set_state(ctx, state: np.ndarray):
     b = np.ascontiguousarray(state, np.uint8)
     _check(load().lbib_set_state(ctx, b.ctypes.data_as(ctypes.c_void_p), b.size), ctx)
+
+
+def lbib_step_noalloc(params: lbib_params, n_cells: int, d_cell_off: int, d_xy: int,
+                      d_rest_len: int, d_k_spring: int, d_pressure: int, d_src_flag: int,
+                      d_f: int, d_g: int, n_steps: int, stream: int):
+    """Allocation-free coupled steps on caller-owned device buffers (raw
+    device addresses); see include/lbib.h for the buffer layout."""
+    vp = ctypes.c_void_p
+    _check(load().lbib_step_noalloc(ctypes.byref(params), n_cells, vp(d_cell_off), vp(d_xy),
+                                    vp(d_rest_len), vp(d_k_spring), vp(d_pressure),
+                                    vp(d_src_flag), vp(d_f), vp(d_g), int(n_steps),
+                                    vp(stream)))
 
 
 def lbib_destroy(ctx):
