@@ -196,7 +196,10 @@ def run_gb300(args, rank, world, dist):
     sim = lbib.Simulation(p, lbib.PRECISIONS[prec], T.n_vertices, T.n_cells, device=dev)
     sim.set_cells(T)
     stream = sim.stream
-    sim.step(args.warmup)
+    # at least 4 warm-up steps so that the two-step graph is captured and
+    # instantiated before the timed region
+    warmup = max(args.warmup, 4)
+    sim.step(warmup)
     torch.cuda.synchronize()
 
     clocks = ClockSampler(dev.index if dev.index is not None else 0) if rank == 0 else None
@@ -278,7 +281,7 @@ def run_gb300(args, rank, world, dist):
     ws = alg_bytes + N * (2 * 4 * (2 if prec == "fp64" else 1) * 2 + 4)
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64",
         "data": "synthetic (seeded tissue generator)",
         "config": workload_config(w, prec, {

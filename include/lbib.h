@@ -180,6 +180,44 @@ int lbib_state_size(const lbib_ctx* ctx, uint64_t* bytes_out);
 int lbib_get_state(lbib_ctx* ctx, void* host, uint64_t bytes);
 int lbib_set_state(lbib_ctx* ctx, const void* host, uint64_t bytes);
 
+/* Label lattice nodes by cell (Fig. 2: the domainID of the lattice nodes is
+ * set from the polygons), on the device, without a context.  A node belongs to
+ * a cell when its centre is inside the polygon by the crossing-number rule,
+ * half-open in y; on overlap the lower cell index wins.
+ *   nx, ny, bc_y              lattice (bc_y 1: rows outside [0, ny) dropped)
+ *   n_cells, d_cell_off, d_xy, d_src_flag   device arrays as lbib_set_cells()
+ *   d_id       out, nx*ny int32 (dense, row-major): 0 outside, c+1 in cell c
+ *   d_src      out (may be NULL), nx*ny bytes: src_flag of the node's cell
+ *   cuda_stream  stream to enqueue on (asynchronous)
+ * Returns LBIB_OK, LBIB_E_PARAM or LBIB_E_CUDA (lbib_last_error(NULL)). */
+int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
+                     const int32_t* d_cell_off, const double* d_xy, const uint8_t* d_src_flag,
+                     int32_t* d_id, uint8_t* d_src, void* cuda_stream);
+
+/* Steady morphogen solve, batched: for each of `batch` independent periodic
+ * tissues of nx*ny nodes, the D2Q5 scheme of Sec. 6.1 with u = 0 and the
+ * reaction R = src_rate [source node] - decay phi is iterated from its initial
+ * state until the residual r = max|phi^{n+1} - phi^n| / max|phi^{n+1}|,
+ * evaluated every check_every steps on the last step pair, is <= tol, or
+ * max_steps steps have run.  Every tissue stops at its own step count.
+ *   d_src       batch*nx*ny bytes (device), bit 0 = source node
+ *   D, decay, src_rate   host arrays of batch doubles (D > 0, decay >= 0)
+ *   d_phi0      batch*nx*ny floats (device): populations start at the rest
+ *               equilibrium g_q = w_q phi0 (a warm start); NULL = cold start
+ *               from zero
+ *   d_phi_out   batch*nx*ny floats (device): phi of the final state
+ *   steps_out, resid_out  host arrays of batch: steps taken, last residual
+ *   d_workspace, ws_bytes  device scratch of lbib_steady_workspace_size()
+ *               bytes, 256-byte aligned, owned by the caller
+ * FP32 storage and arithmetic.  Synchronises the stream.  Returns LBIB_OK,
+ * LBIB_E_PARAM, LBIB_E_WORKSPACE or LBIB_E_CUDA. */
+int lbib_steady_workspace_size(int32_t nx, int32_t ny, int32_t batch, uint64_t* bytes_out);
+int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_src,
+                      const double* D, const double* decay, const double* src_rate,
+                      const float* d_phi0, double tol, int64_t max_steps, int32_t check_every,
+                      float* d_phi_out, int64_t* steps_out, double* resid_out,
+                      void* d_workspace, uint64_t ws_bytes, void* cuda_stream);
+
 /* Coupled steps without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory while
  * they run -- code inside a framework whose memory pool owns the device,

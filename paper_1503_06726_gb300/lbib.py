@@ -41,7 +41,7 @@ EXPORTS = (
     "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_cell_params",
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
-    "lbib_status_string",
+    "lbib_status_string", "lbib_label_cells", "lbib_steady_workspace_size", "lbib_steady_solve",
 )
 
 
@@ -90,6 +90,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_get_state": (ctypes.c_int, [vp, vp, u64]),
         "lbib_set_state": (ctypes.c_int, [vp, vp, u64]),
         "lbib_step_noalloc": (ctypes.c_int, [P, i32, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]),
+        "lbib_label_cells": (ctypes.c_int, [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]),
+        "lbib_steady_workspace_size": (ctypes.c_int, [i32, i32, i32, ctypes.POINTER(u64)]),
+        "lbib_steady_solve": (ctypes.c_int, [i32, i32, i32, vp, vp, vp, vp, vp, ctypes.c_double,
+                                             ctypes.c_int64, i32, vp, vp, vp, vp, u64, vp]),
         "lbib_destroy": (None, [vp]),
         "lbib_last_error": (ctypes.c_char_p, [vp]),
         "lbib_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -253,6 +257,67 @@ def lbib_step_noalloc(params: lbib_params, n_cells: int, d_cell_off: int, d_xy: 
                                     vp(d_rest_len), vp(d_k_spring), vp(d_pressure),
                                     vp(d_src_flag), vp(d_f), vp(d_g), int(n_steps),
                                     vp(stream)))
+
+
+def lbib_label_cells(nx: int, ny: int, bc_y: int, n_cells: int, d_cell_off: int, d_xy: int,
+                     d_src_flag: int, d_id: int, d_src: int, stream: int):
+    vp = ctypes.c_void_p
+    _check(load().lbib_label_cells(nx, ny, bc_y, n_cells, vp(d_cell_off), vp(d_xy),
+                                   vp(d_src_flag), vp(d_id), vp(d_src or None), vp(stream)))
+
+
+def lbib_steady_workspace_size(nx: int, ny: int, batch: int) -> int:
+    n = ctypes.c_uint64(0)
+    _check(load().lbib_steady_workspace_size(nx, ny, batch, ctypes.byref(n)))
+    return int(n.value)
+
+
+def lbib_steady_solve(nx, ny, batch, d_src, D, decay, src_rate, d_phi0, tol, max_steps,
+                      check_every, d_phi_out, d_workspace, ws_bytes, stream):
+    """Returns (steps, resid) host arrays; d_* are raw device addresses."""
+    vp = ctypes.c_void_p
+    D_, Dp = _p(D, np.float64)
+    k_, kp = _p(decay, np.float64)
+    s_, sp = _p(src_rate, np.float64)
+    steps = np.zeros(batch, np.int64)
+    resid = np.zeros(batch, np.float64)
+    _check(load().lbib_steady_solve(nx, ny, batch, vp(d_src), Dp, kp, sp, vp(d_phi0 or None),
+                                    float(tol), int(max_steps), int(check_every), vp(d_phi_out),
+                                    steps.ctypes.data_as(vp), resid.ctypes.data_as(vp),
+                                    vp(d_workspace), int(ws_bytes), vp(stream)))
+    return steps, resid
+
+
+def steady_solve(src, D, decay, src_rate, phi0=None, tol=1e-6, max_steps=200000,
+                 check_every=16, stream=None):
+    """Convenience wrapper on torch CUDA tensors: src (B, ny, nx) uint8,
+    phi0 (B, ny, nx) float32 or None.  Returns (phi, steps, resid)."""
+    import torch
+    B, ny, nx = src.shape
+    ws_n = lbib_steady_workspace_size(nx, ny, B)
+    ws = torch.empty(ws_n, dtype=torch.uint8, device=src.device)
+    out = torch.empty((B, ny, nx), dtype=torch.float32, device=src.device)
+    st = (stream or torch.cuda.current_stream(src.device)).cuda_stream
+    src = src.contiguous()
+    p0 = None if phi0 is None else phi0.contiguous().float()
+    steps, resid = lbib_steady_solve(nx, ny, B, src.data_ptr(), D, decay, src_rate,
+                                     None if p0 is None else p0.data_ptr(), tol, max_steps,
+                                     check_every, out.data_ptr(), ws.data_ptr(), ws_n, st)
+    return out, steps, resid
+
+
+def label_cells(nx, ny, bc_y, tissue, device="cuda"):
+    """Labels of a host tissue, computed on the device.  Returns (id, src)
+    torch tensors (ny, nx)."""
+    import torch
+    off = torch.as_tensor(np.ascontiguousarray(tissue.cell_off, np.int32), device=device)
+    xy = torch.as_tensor(np.ascontiguousarray(tissue.xy, np.float64), device=device)
+    sf = torch.as_tensor(np.ascontiguousarray(tissue.src_flag, np.uint8), device=device)
+    idt = torch.empty((ny, nx), dtype=torch.int32, device=device)
+    srt = torch.empty((ny, nx), dtype=torch.uint8, device=device)
+    lbib_label_cells(nx, ny, bc_y, tissue.n_cells, off.data_ptr(), xy.data_ptr(), sf.data_ptr(),
+                     idt.data_ptr(), srt.data_ptr(), torch.cuda.current_stream(device).cuda_stream)
+    return idt, srt
 
 
 def lbib_destroy(ctx):
