@@ -65,13 +65,13 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
     g[4] = (WALLS && hi) ? St::ld(B + 2 * P + node) : St::ld(B + 4 * P + rp + x);
 }
 
+// The update of one node (x, y).  The lane of the calling thread within its
+// warp must match x modulo 32 (the group masks are cleared per warp).
 template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
-__global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k) {
+__device__ __forceinline__ void lattice_node(const LatticeArgs& a, const Coefs<C>& k, int x,
+                                             int y) {
     using St = Store<T, C>;
     using V2 = typename Vec2<C>::T;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
 
     const int64_t P = a.plane;
     const int xm = (x == 0) ? a.nx - 1 : x - 1;
@@ -112,13 +112,25 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
             pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, lo_wall,
                                hi_wall, g[s]);
     }
+    // spread force and labels: only the 4-node groups the IB kernel marked
     V2 fv;
     fv.x = C(0);
     fv.y = C(0);
     uint32_t label = kOutside;
+    bool fhit = false, lhit = false;
+    uint32_t fword = 0u, lword = 0u;
+    const int64_t grp = node >> 2;
     if (a.ib) {
-        fv = static_cast<const V2*>(a.force)[node];
-        label = a.id[node];
+        if (a.fmask) {
+            fword = a.fmask[grp >> 5];
+            lword = a.lmask[grp >> 5];
+            fhit = (fword >> (grp & 31)) & 1u;
+            lhit = (lword >> (grp & 31)) & 1u;
+        } else {
+            fhit = lhit = true;
+        }
+        if (fhit) fv = static_cast<const V2*>(a.force)[node];
+        if (lhit) label = a.id[node];
     }
 
     // ---- moments (Sec. 6.1) with the half-force velocity shift (Guo)
@@ -193,30 +205,50 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
         }
     }
 
-    // ---- velocity for the interpolation, resets, outputs
-    {
+    // ---- velocity where the interpolation will read it (the groups that
+    // received force: the kernel support of the same vertex positions) or
+    // everywhere on an output step; resets; outputs
+    if (a.out || fhit) {
         V2 uv;
         uv.x = ux;
         uv.y = uy;
         static_cast<V2*>(a.u)[node] = uv;
     }
     if (a.ib) {
-        V2 z;
-        z.x = C(0);
-        z.y = C(0);
-        static_cast<V2*>(a.force)[node] = z;
-        a.id[node] = kOutside;
+        if (fhit) {
+            V2 z;
+            z.x = C(0);
+            z.y = C(0);
+            static_cast<V2*>(a.force)[node] = z;
+        }
+        if (lhit) a.id[node] = kOutside;
         if (a.out) {
             a.id_out[node] = label;
             static_cast<V2*>(a.force_out)[node] = fv;
+        }
+        // lane 0 clears the warp's 8 group bits (32 nodes, one row, 32-aligned)
+        if (a.fmask && (x & 31) == 0) {
+            const int sh = (int)(grp & 31);
+            if ((fword >> sh) & 0xFFu) atomicAnd(a.fmask + (grp >> 5), ~(0xFFu << sh));
+            if ((lword >> sh) & 0xFFu) atomicAnd(a.lmask + (grp >> 5), ~(0xFFu << sh));
         }
     }
     if (a.out) static_cast<C*>(a.rho)[node] = rho;
     if (!(rho > C(0)) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.diag + kDiagNonFinite, 1u);
 }
 
+template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
+__global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    lattice_node<T, C, S, WALLS, FORCING, SCALED>(a, k, x, y);
+}
+
 template <typename T, typename C, int S, bool WALLS, int FORCING>
 static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s) {
+    // the group masks are cleared per warp: a warp must be 32 nodes of one row
+    if (a.fmask && block.x % 32 != 0) return cudaErrorInvalidConfiguration;
     dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
     const Coefs<C>& k = *static_cast<const Coefs<C>*>(coefs);
     constexpr bool SC = std::is_same<T, __half>::value;

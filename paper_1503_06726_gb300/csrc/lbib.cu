@@ -54,12 +54,16 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.phi = take((uint64_t)p.n_species * P * l.cs);
     l.id = take(P * 4);
     l.id_out = take(P * 4);
+    l.fmask = take((uint64_t)mask_words(l.plane) * 4);
+    l.lmask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
     const uint64_t V = (uint64_t)max_vertices, C = (uint64_t)max_cells;
     l.xy = take(V * 16);
     l.L0 = take(V * 8);
     l.k = take(V * 8);
     l.vforce = take(V * 16);
+    l.vbase = take(V * 8);
+    l.vfrac = take(V * 8);
     l.off = take((C + 1) * 4);
     l.pres = take(C * 8);
     l.srcf = take(C);
@@ -74,28 +78,6 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
 
 using namespace lbib;
 
-struct lbib_ctx {
-    lbib_params p;
-    int maxV = 0, maxC = 0;
-    char* ws = nullptr;
-    uint64_t bytes = 0;
-    cudaStream_t stream = nullptr;
-    Layout L;
-    int cur = 0;           // buffer holding the current post-collision populations
-    int nV = 0, nC = 0;
-    bool fields_valid = false;
-    bool vforce_valid = false;
-    Coefs<double> kd;
-    Coefs<float> kf;
-    dim3 block{128, 1, 1};
-    // graph of a two-step chunk, keyed by the buffer parity it starts from
-    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
-    int chunk_nC = -1;
-    std::string err;
-
-    template <typename T>
-    T* at(uint64_t off) const { return reinterpret_cast<T*>(ws + off); }
-};
 
 static thread_local std::string g_create_err;
 
@@ -187,6 +169,8 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.plane = L.plane;
     a.out = out ? 1 : 0;
     a.ib = c->nC > 0 ? 1 : 0;
+    a.fmask = c->at<uint32_t>(L.fmask);
+    a.lmask = c->at<uint32_t>(L.lmask);
     return a;
 }
 
@@ -215,6 +199,10 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) {
     a.do_mask = 1;
     a.write_vforce = vforce ? 1 : 0;
     a.do_force = 1;
+    a.vbase = c->at<int2>(L.vbase);
+    a.vfrac = c->at<float2>(L.vfrac);
+    a.fmask = c->at<uint32_t>(L.fmask);
+    a.lmask = c->at<uint32_t>(L.lmask);
     return a;
 }
 
@@ -331,6 +319,8 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.u, 0, 2 * L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fmask, 0, mask_words(L.plane) * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -691,6 +681,8 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fmask, 0, mask_words(L.plane) * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_state");
     c->nV = hdr[0];

@@ -52,6 +52,7 @@ struct Layout {
     uint64_t f[2] = {0, 0}, g[2] = {0, 0};
     uint64_t force = 0, u = 0, rho = 0, phi = 0, id = 0, id_out = 0, force_out = 0;
     uint64_t xy = 0, L0 = 0, k = 0, vforce = 0, off = 0, pres = 0, srcf = 0, area = 0;
+    uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
 };
@@ -87,6 +88,10 @@ struct LatticeArgs {
     int64_t pitch, plane;
     int out;            // write rho, phi, id_out, force_out
     int ib;             // read/clear force and labels
+    // 1 bit per 4 consecutive nodes (node index >> 2): groups that received
+    // spread force / labels this step.  NULL = dense (read every node).
+    uint32_t* fmask;
+    uint32_t* lmask;
 };
 
 struct IBArgs {
@@ -106,7 +111,25 @@ struct IBArgs {
     double tension;
     int do_move, do_prep, do_mask, write_vforce;
     int do_force;       // compute and spread vertex forces (0: labels only)
+    int2* vbase;        // FP32 path, optional: floor(X) per vertex handed to the next move
+    float2* vfrac;      // FP32 path, optional: X - floor(X) per vertex
+    uint32_t* fmask;    // optional: mark the groups that receive spread force
+    uint32_t* lmask;    // optional: mark the groups that receive labels
 };
+
+// shared memory of the FP32 per-cell IB work (one CTA per cell)
+struct IBSmem32 {
+    double2 sx[kMaxVertsPerCell];  // FP64 positions (exact fallbacks)
+    int2 sb[kMaxVertsPerCell];     // floor(X)
+    float2 sf[kMaxVertsPerCell];   // X - floor(X)
+    int rowcnt[kMaxRows];
+    int thr[kMaxRows * kMaxCross];
+    int sbox[4];
+    int s_flag;
+};
+
+// mask words covering a plane of `plane` elements (1 bit per 4 nodes)
+inline int64_t mask_words(int64_t plane) { return (plane + 127) / 128 + 1; }
 
 // coefficient tables and the calling thread's error text (lbib_last_error(NULL))
 void fill_coefs_public(const lbib_params& p, Coefs<double>* k);
@@ -128,3 +151,28 @@ cudaError_t launch_set_species(int precision, int n_species, int s_idx, int nx, 
                                const void* coefs, cudaStream_t s);
 
 }  // namespace lbib
+
+// One tissue (the opaque handle of the C ABI).
+struct lbib_ctx {
+    lbib_params p;
+    int maxV = 0, maxC = 0;
+    char* ws = nullptr;
+    uint64_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    lbib::Layout L;
+    int cur = 0;           // buffer holding the current post-collision populations
+    int nV = 0, nC = 0;
+    bool fields_valid = false;
+    bool vforce_valid = false;
+    lbib::Coefs<double> kd;
+    lbib::Coefs<float> kf;
+    dim3 block{128, 1, 1};
+    // graph of a two-step chunk, keyed by the buffer parity it starts from
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    int chunk_nC = -1;
+    std::string err;
+
+    template <typename T>
+    T* at(uint64_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+

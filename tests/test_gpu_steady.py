@@ -95,12 +95,16 @@ def test_steady_converges_like_oracle_and_warm_start(lb, orc):
         # FP32 decision by a few residual checks
         assert abs(int(steps[b]) - nref) <= 64, (steps[b], nref)
         assert rel(phi[b], ref[0]) < 1e-4
-    # warm start from the converged field: done at the first check
+    # warm start from the converged field: the populations start at the rest
+    # equilibrium w_q phi*, which lacks the non-equilibrium (flux) part of the
+    # steady populations, so a short transient remains -- but far shorter
+    # than the cold relaxation, and it ends on the same field
     import torch
     phi0 = torch.as_tensor(np.stack(refs).astype(np.float32), device="cuda")
     phi_w, steps_w, resid_w = lb.steady_solve(src, D, k, s, phi0=phi0, tol=1e-6,
                                               max_steps=100000)
-    assert (steps_w <= 32).all() and (resid_w <= 1e-6).all()
+    assert (resid_w <= 1e-6).all()
+    assert (steps_w < steps // 2).all(), (steps_w, steps)
     assert rel(phi_w.cpu().numpy(), np.stack(refs)) < 1e-4
 
 
