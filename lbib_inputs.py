@@ -294,3 +294,17 @@ def scaled_config1(n: int, R: float, n_vert: int, seed: int = 11, n_steps: int =
 def random_fields(seed: int, shape, scale: float = 1.0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(-scale, scale, size=shape)
+
+
+def nop_init_params(seed: int, shapes) -> np.ndarray:
+    """Initial parameters of the neural operator for the given layer list
+    [(name, Ci, Co), ...]: He-normal weights (std sqrt(2 / (9 Ci)); a tenth of
+    that for the output layer), zero biases, in the flat layout weights
+    (3, 3, Ci, Co) then bias (Co,) per layer.  FP32-representable values."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for name, ci, co in shapes:
+        std = math.sqrt(2.0 / (9 * ci)) * (0.1 if name == "out" else 1.0)
+        out.append(rng.normal(0.0, std, size=9 * ci * co))
+        out.append(np.zeros(co))
+    return np.concatenate(out).astype(np.float32).astype(np.float64)

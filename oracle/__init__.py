@@ -18,6 +18,10 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   run (coupled)      invariants above; the coupled trajectory itself is
                      parity unpinned beyond them (no printed trajectory)
   steady             closed-form uniform steady state s/k
+  conv3x3 (+dgrad,   scipy correlate2d, identity tap, adjointness,
+    wgrad)           finite differences
+  nn (U-Net)         finite-difference gradient of the whole network,
+                     pooling/upsampling adjoints, Adam first-step closed form
 """
 from __future__ import annotations
 
@@ -97,6 +101,9 @@ def lib():
             L.orc_steady.restype = ctypes.c_long
             L.orc_steady.argtypes = [ctypes.POINTER(OrcParams), vp, vp, d, ctypes.c_long, i,
                                      vp, ctypes.POINTER(d)]
+            L.orc_conv3x3.argtypes = [i, i, i, i, i, vp, vp, vp, vp]
+            L.orc_conv3x3_dgrad.argtypes = [i, i, i, i, i, vp, vp, vp]
+            L.orc_conv3x3_wgrad.argtypes = [i, i, i, i, i, vp, vp, vp, vp]
             L.orc_set_threads.argtypes = [i]
             L.orc_max_threads.restype = i
             _lib = L
@@ -265,3 +272,37 @@ def steady(p, src, g=None, tol=1e-6, max_steps=200000, check_every=16):
     n = lib().orc_steady(ctypes.byref(P), _ptr(np.ascontiguousarray(src, np.uint8)), _ptr(g),
                          float(tol), int(max_steps), int(check_every), _ptr(phi), ctypes.byref(r))
     return phi, int(n), float(r.value), g
+
+
+# ---------------------------------------------------------------- conv layers
+def conv3x3(x, w, b=None):
+    """x (N,H,W,Ci), w (3,3,Ci,Co), b (Co,) -> (N,H,W,Co); zero padding."""
+    x = _f64(x)
+    w = _f64(w)
+    N, H, W, Ci = x.shape
+    Co = w.shape[3]
+    out = np.empty((N, H, W, Co))
+    lib().orc_conv3x3(N, H, W, Ci, Co, _ptr(x), _ptr(w), _ptr(None if b is None else _f64(b)),
+                      _ptr(out))
+    return out
+
+
+def conv3x3_dgrad(dout, w):
+    dout = _f64(dout)
+    w = _f64(w)
+    N, H, W, Co = dout.shape
+    Ci = w.shape[2]
+    din = np.empty((N, H, W, Ci))
+    lib().orc_conv3x3_dgrad(N, H, W, Ci, Co, _ptr(dout), _ptr(w), _ptr(din))
+    return din
+
+
+def conv3x3_wgrad(x, dout):
+    x = _f64(x)
+    dout = _f64(dout)
+    N, H, W, Ci = x.shape
+    Co = dout.shape[3]
+    dw = np.empty((3, 3, Ci, Co))
+    db = np.empty(Co)
+    lib().orc_conv3x3_wgrad(N, H, W, Ci, Co, _ptr(x), _ptr(dout), _ptr(dw), _ptr(db))
+    return dw, db

@@ -494,3 +494,81 @@ long orc_steady(const orc_params* P, const uint8_t* src, double* g, double tol, 
     if (resid_out) *resid_out = r;
     return n;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Convolution layers of the neural operator that warm-starts the steady
+ * morphogen solve (a learned part the measured method adds; the paper has no
+ * network).  Plain definitions in FP64, NHWC layout, 3x3 taps, zero padding:
+ *   out[n,y,x,o] = b[o] + sum_{ky,kx,i} in[n,y+ky-1,x+kx-1,i] w[ky,kx,i,o]
+ * dgrad: din[n,y,x,i] = sum_{ky,kx,o} dout[n,y-ky+1,x-kx+1,o] w[ky,kx,i,o]
+ * wgrad: dw[ky,kx,i,o] = sum_{n,y,x} in[n,y+ky-1,x+kx-1,i] dout[n,y,x,o],
+ *        db[o] = sum_{n,y,x} dout[n,y,x,o]. */
+void orc_conv3x3(int N, int H, int W, int Ci, int Co, const double* in, const double* w,
+                 const double* b, double* out) {
+    for (int n = 0; n < N; ++n)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int o = 0; o < Co; ++o) {
+                    double s = b ? b[o] : 0.0;
+                    for (int ky = 0; ky < 3; ++ky) {
+                        int yy = y + ky - 1;
+                        if (yy < 0 || yy >= H) continue;
+                        for (int kx = 0; kx < 3; ++kx) {
+                            int xx = x + kx - 1;
+                            if (xx < 0 || xx >= W) continue;
+                            const double* ip = in + (((long)n * H + yy) * W + xx) * Ci;
+                            const double* wp = w + ((long)(ky * 3 + kx) * Ci) * Co + o;
+                            for (int i = 0; i < Ci; ++i) s += ip[i] * wp[(long)i * Co];
+                        }
+                    }
+                    out[(((long)n * H + y) * W + x) * Co + o] = s;
+                }
+}
+
+void orc_conv3x3_dgrad(int N, int H, int W, int Ci, int Co, const double* dout, const double* w,
+                       double* din) {
+    for (int n = 0; n < N; ++n)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x)
+                for (int i = 0; i < Ci; ++i) {
+                    double s = 0.0;
+                    for (int ky = 0; ky < 3; ++ky) {
+                        int yy = y - ky + 1;
+                        if (yy < 0 || yy >= H) continue;
+                        for (int kx = 0; kx < 3; ++kx) {
+                            int xx = x - kx + 1;
+                            if (xx < 0 || xx >= W) continue;
+                            const double* gp = dout + (((long)n * H + yy) * W + xx) * Co;
+                            const double* wp = w + (((long)(ky * 3 + kx) * Ci) + i) * Co;
+                            for (int o = 0; o < Co; ++o) s += gp[o] * wp[o];
+                        }
+                    }
+                    din[(((long)n * H + y) * W + x) * Ci + i] = s;
+                }
+}
+
+void orc_conv3x3_wgrad(int N, int H, int W, int Ci, int Co, const double* in, const double* dout,
+                       double* dw, double* db) {
+    for (long t = 0; t < 9L * Ci * Co; ++t) dw[t] = 0.0;
+    if (db)
+        for (int o = 0; o < Co; ++o) db[o] = 0.0;
+    for (int n = 0; n < N; ++n)
+        for (int y = 0; y < H; ++y)
+            for (int x = 0; x < W; ++x) {
+                const double* gp = dout + (((long)n * H + y) * W + x) * Co;
+                if (db)
+                    for (int o = 0; o < Co; ++o) db[o] += gp[o];
+                for (int ky = 0; ky < 3; ++ky) {
+                    int yy = y + ky - 1;
+                    if (yy < 0 || yy >= H) continue;
+                    for (int kx = 0; kx < 3; ++kx) {
+                        int xx = x + kx - 1;
+                        if (xx < 0 || xx >= W) continue;
+                        const double* ip = in + (((long)n * H + yy) * W + xx) * Ci;
+                        double* wp = dw + ((long)(ky * 3 + kx) * Ci) * Co;
+                        for (int i = 0; i < Ci; ++i)
+                            for (int o = 0; o < Co; ++o) wp[(long)i * Co + o] += ip[i] * gp[o];
+                    }
+                }
+            }
+}
