@@ -62,6 +62,8 @@ def workload(name: str):
         return li.config3(), "fp16"
     if name == "c3-fp64":
         return li.config3(), "fp64"
+    if name == "c4":
+        return li.config4(), "fp32"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -183,7 +185,104 @@ def oracle_sample(w, target_s: float, max_steps: int, threads: int | None = None
 
 
 # ------------------------------------------------------------------ arms
+def run_ensemble(args, rank, world, dist):
+    """64 independent tissues of uneven sizes advanced by one persistent
+    cooperative launch per step call (replayed from a CUDA graph)."""
+    import torch
+    from paper_1503_06726_gb300 import lbib
+
+    lbib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ws = li.config4()
+    N = sum(w.params.nx * w.params.ny for w in ws)
+    ens = lbib.Ensemble([w.params for w in ws], [w.tissue for w in ws], device=dev)
+    tune = ens.tune_cached(f"c4-{len(ws)}-{N}", trial_steps=10)
+    warmup = max(args.warmup, 4)
+    ens.step(warmup)
+    ens.status()
+    torch.cuda.synchronize()
+    stream = ens.stream
+    clocks = ClockSampler(dev.index if dev.index is not None else 0) if rank == 0 else None
+    time.sleep(0.3 if clocks else 0)
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ens.status()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    bpn = alg_bytes_per_node("fp32", ws[0].params.n_species)
+    achieved = bpn * N * args.steps / (ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    # end to end: per step, per-cell parameters of every tissue up from pinned
+    # host memory, one ensemble step, cell areas of every tissue back
+    L = lbib.load()
+    vp = ctypes.c_void_p
+    pins = []
+    for w in ws:
+        pp = torch.empty(w.tissue.n_cells, dtype=torch.float64).pin_memory()
+        pp.numpy()[:] = w.tissue.pressure
+        aa = torch.empty(w.tissue.n_cells, dtype=torch.float64).pin_memory()
+        pins.append((pp, aa))
+    e2e_steps = max(1, min(args.e2e_steps, 100))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for t, (pp, aa) in enumerate(pins):
+            rc = L.lbib_set_cell_params(ens.ctx[t], vp(pp.data_ptr()), None)
+            if rc:
+                raise RuntimeError(lbib.lbib_last_error(ens.ctx[t]))
+        ens.step(1)
+        for t, (pp, aa) in enumerate(pins):
+            rc = L.lbib_get_fields(ens.ctx[t], lbib.LBIB_AREA, None, None, None, None, None,
+                                   vp(aa.data_ptr()), None, None, None)
+            if rc:
+                raise RuntimeError(lbib.lbib_last_error(ens.ctx[t]))
+    t_e2e = time.perf_counter() - t0
+    cells = sum(w.tissue.n_cells for w in ws)
+    e2e = {"value": world * N * e2e_steps / t_e2e / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": cells * 8, "d2h_bytes_per_step": cells * 8,
+           "steps": e2e_steps,
+           "api": "per tissue lbib_set_cell_params, lbib_ensemble_step(1), per tissue "
+                  "lbib_get_fields(AREA)"}
+    info = ens.config()
+    ens.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded tissue generator)",
+        "config": {"workload": f"c4_ensemble_{len(ws)}_tissues", "nodes": N,
+                   "sides": [w.params.nx for w in ws], "cells": cells,
+                   "storage": "fp32", "vertex_precision": "fp64",
+                   "l2": f"inputs larger than L2: {2 * bpn * N / 2**20:.0f} MiB of populations",
+                   "launch": "one persistent cooperative kernel per step call",
+                   "graph": info["graph"], "grid": info["grid"], "tuned": tune},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "ensemble_kernel (whole persistent launch: lattice + IB phases)",
+                     "alg_bytes_per_node": bpn, "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
+        "e2e": e2e, "gpu_launches": 1, "clocks": clk, "cpu_baseline": None,
+    }
+
+
 def run_gb300(args, rank, world, dist):
+    if args.workload == "c4":
+        return run_ensemble(args, rank, world, dist)
     import torch
     from paper_1503_06726_gb300 import lbib
 

@@ -218,6 +218,60 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
                       float* d_phi_out, int64_t* steps_out, double* resid_out,
                       void* d_workspace, uint64_t ws_bytes, void* cuda_stream);
 
+/* ---- Ensembles: many independent tissues advanced together -------------
+ * An ensemble holds n tissues (each with its own lbib_params -- lattice
+ * size, tau, boundary -- and its own cells) in one caller-owned workspace and
+ * advances all of them by one persistent cooperative kernel launch per
+ * lbib_ensemble_step() call, captured once per step count into a CUDA graph.
+ * All tissues use LBIB_FP32 storage and share n_species and forcing.  Each
+ * tissue is a context: lbib_ensemble_tissue() returns it for
+ * lbib_set_cells(), lbib_get_fields(), lbib_get_state() and the like (do not
+ * lbib_destroy() it; lbib_ensemble_destroy() releases all).
+ *   lbib_ensemble_workspace_size  bytes for n tissues with the given params
+ *                                 and vertex / cell capacities (arrays of n)
+ *   lbib_ensemble_create          bind a 256-byte aligned device workspace
+ *                                 and a stream; tissues start at rest
+ *   lbib_ensemble_step            n_steps of every tissue (asynchronous):
+ *                                 the step sequence of lbib_step()
+ *   lbib_ensemble_status          synchronise; LBIB_E_TIMEOUT if a grid
+ *                                 barrier of the persistent launch waited
+ *                                 more than about one second (the launch
+ *                                 then ended early and the tissues' state is
+ *                                 undefined); the barrier state is reset
+ *   lbib_ensemble_config          set the lattice work item (nodes_per_item,
+ *                                 a multiple of 256; <= 0 keeps it) and CTAs
+ *                                 per SM (0 = as many as fit; < 0 keeps it);
+ *                                 reports whether the graph path is in use
+ *                                 and the grid size
+ *   lbib_ensemble_tune            time every (nodes_per_item in 256/512/1024)
+ *                                 x (CTAs per SM) candidate over trial_steps
+ *                                 steps (which advances the tissues), keep the
+ *                                 fastest; config_out[2] = {nodes_per_item,
+ *                                 CTAs per SM}, ms_out = ms per step
+ *   lbib_ensemble_selftest_timeout  run one grid barrier that cannot
+ *                                 complete, to check that the bounded wait
+ *                                 ends (seconds_out) and is reported as
+ *                                 LBIB_E_TIMEOUT
+ * The paper runs one tissue per process (Sec. 3.4); the ensemble is the
+ * parameter-sweep form of the same step. */
+typedef struct lbib_ensemble lbib_ensemble;
+int lbib_ensemble_workspace_size(int32_t n, const lbib_params* params,
+                                 const int32_t* max_vertices, const int32_t* max_cells,
+                                 uint64_t* bytes_out);
+int lbib_ensemble_create(int32_t n, const lbib_params* params, const int32_t* max_vertices,
+                         const int32_t* max_cells, void* d_workspace, uint64_t bytes,
+                         void* cuda_stream, lbib_ensemble** out);
+lbib_ctx* lbib_ensemble_tissue(lbib_ensemble* ens, int32_t t);
+int lbib_ensemble_step(lbib_ensemble* ens, int32_t n_steps);
+int lbib_ensemble_status(lbib_ensemble* ens);
+int lbib_ensemble_config(lbib_ensemble* ens, int32_t nodes_per_item, int32_t blocks_per_sm,
+                         int32_t* graph_out, int32_t* grid_out);
+int lbib_ensemble_tune(lbib_ensemble* ens, int32_t trial_steps, int32_t* config_out,
+                       double* ms_out);
+int lbib_ensemble_selftest_timeout(lbib_ensemble* ens, double* seconds_out);
+void lbib_ensemble_destroy(lbib_ensemble* ens);
+const char* lbib_ensemble_last_error(const lbib_ensemble* ens);
+
 /* Coupled steps without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory while
  * they run -- code inside a framework whose memory pool owns the device,

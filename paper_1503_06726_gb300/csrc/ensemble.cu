@@ -1,0 +1,576 @@
+// ensemble.cu -- a batch of independent tissues advanced together by one
+// persistent, cooperative kernel launch per lbib_ensemble_step() call.
+//
+// Every tissue is an ordinary context (its own slice of the ensemble's
+// workspace, its own parameters: lattice size, tau, boundary, springs), so
+// the per-tissue calls (lbib_set_cells, lbib_get_fields, state) work on it.
+// lbib_ensemble_step(n) runs, for all tissues at once, the same sequence as
+// lbib_step(n): the IB prep, then per step the lattice update of every node
+// of every tissue and the IB move/prep of every cell, separated by grid-wide
+// barriers.  Work is dealt out in items -- lattice items of `nodes_per_item`
+// nodes (rows padded to 32 so a warp stays in one row) and one item per cell
+// -- strided over the persistent CTAs, which balances tissues of very
+// different sizes.  The launch is captured once per step count into a CUDA
+// graph and replayed.  The two launch parameters (nodes per item and CTAs per
+// SM) are chosen by lbib_ensemble_tune(), which times the candidates.
+//
+// The grid barrier spins on a generation word with a bounded wait (a
+// globaltimer limit of about one second): if a barrier cannot complete, the
+// CTA records the error and every CTA leaves at its next barrier, so the
+// launch always ends; lbib_ensemble_status() reports LBIB_E_TIMEOUT.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ib_cell.cuh"
+#include "lattice_node.cuh"
+
+namespace lbib {
+
+struct TissueDev {
+    LatticeArgs la;    // parity-0 buffers: fsrc = f[0], fdst = f[1] (swapped per step)
+    IBArgs ia;
+    Coefs<float> k;
+    int bc_y;
+    int nxr;           // row length padded to a multiple of 32
+    int cur;           // buffer parity at the start of the launch
+    int pad;
+};
+
+struct EnsArgs {
+    const TissueDev* tis;
+    const int* item_pfx;  // n + 1 prefix sums of lattice items
+    const int* cell_pfx;  // n + 1 prefix sums of cells
+    int n, n_steps, nodes_per_item, total_items, total_cells;
+    unsigned* bar;        // [0] arrival count, [1] generation, [2] error flag
+    unsigned nblocks;     // CTAs the barrier waits for
+};
+
+constexpr unsigned long long kBarrierLimitNs = 1000000000ull;  // one second
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier with a bounded wait.  Returns false (for every thread of
+// the CTA) when the ensemble's error flag is set.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = bar + 1;
+        volatile unsigned* verr = bar + 2;
+        const unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*vgen == g) {
+                if (*verr) break;
+                if (global_ns() - t0 > kBarrierLimitNs) {
+                    atomicOr(bar + 2, 1u);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile unsigned*)(bar + 2) == 0u;
+}
+
+__device__ __forceinline__ int find_tissue(const int* pfx, int n, int item) {
+    int lo = 0, hi = n;  // pfx[lo] <= item < pfx[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pfx[mid] <= item) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int S, int FORCING>
+__global__ void __launch_bounds__(kIBThreads) ensemble_kernel(EnsArgs e) {
+    __shared__ IBSmem32 sm;
+    __shared__ TissueDev td;
+    __shared__ int s_t;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_t = -1;
+
+    auto load_tissue = [&](int t) {
+        __syncthreads();
+        if (t != s_t) {
+            const int* src = reinterpret_cast<const int*>(e.tis + t);
+            int* dst = reinterpret_cast<int*>(&td);
+            for (int i = tid; i < (int)(sizeof(TissueDev) / 4); i += blockDim.x) dst[i] = src[i];
+            __syncthreads();
+            if (tid == 0) s_t = t;
+        }
+        __syncthreads();
+    };
+
+    auto ib_phase = [&](int move, int prep, int vforce) {
+        for (int item = blockIdx.x; item < e.total_cells; item += gridDim.x) {
+            const int t = find_tissue(e.cell_pfx, e.n, item);
+            load_tissue(t);
+            IBArgs a = td.ia;
+            a.do_move = move;
+            a.do_prep = prep;
+            a.write_vforce = vforce;
+            ib_cell_f32(a, item - e.cell_pfx[t], sm);
+        }
+    };
+
+    auto lattice_phase = [&](int step, int out) {
+        for (int item = blockIdx.x; item < e.total_items; item += gridDim.x) {
+            const int t = find_tissue(e.item_pfx, e.n, item);
+            load_tissue(t);
+            LatticeArgs a = td.la;
+            const int p = (td.cur + step) & 1;
+            if (p) {
+                a.fsrc = td.la.fdst;
+                a.fdst = const_cast<void*>(td.la.fsrc);
+                a.gsrc = td.la.gdst;
+                a.gdst = const_cast<void*>(td.la.gsrc);
+            }
+            a.out = out;
+            const int64_t v0 = (int64_t)(item - e.item_pfx[t]) * e.nodes_per_item;
+            for (int v = tid; v < e.nodes_per_item; v += blockDim.x) {
+                const int64_t vv = v0 + v;
+                const int y = (int)(vv / td.nxr), x = (int)(vv - (int64_t)y * td.nxr);
+                if (y >= a.ny || x >= a.nx) continue;
+                if (td.bc_y)
+                    lattice_node<float, float, S, true, FORCING, false>(a, td.k, x, y);
+                else
+                    lattice_node<float, float, S, false, FORCING, false>(a, td.k, x, y);
+            }
+        }
+    };
+
+    // the sequence of lbib_step(n): prep, then per step lattice + move/prep
+    ib_phase(0, 1, e.n_steps == 1);
+    if (!grid_barrier(e.bar, e.nblocks)) return;
+    for (int s = 0; s < e.n_steps; ++s) {
+        const bool last = (s == e.n_steps - 1);
+        lattice_phase(s, last ? 1 : 0);
+        if (!grid_barrier(e.bar, e.nblocks)) return;
+        ib_phase(1, last ? 0 : 1, s == e.n_steps - 2);
+        if (!last && !grid_barrier(e.bar, e.nblocks)) return;
+    }
+}
+
+// A barrier that cannot complete (it waits for one CTA more than the grid
+// has): used by lbib_ensemble_selftest_timeout() to exercise the bounded wait.
+__global__ void barrier_timeout_kernel(unsigned* bar, unsigned nblocks) {
+    grid_barrier(bar, nblocks);
+}
+
+typedef void (*EnsKernel)(EnsArgs);
+
+static EnsKernel pick_kernel(int S, int forcing) {
+    switch (S * 2 + (forcing ? 1 : 0)) {
+        case 0: return ensemble_kernel<0, 0>;
+        case 1: return ensemble_kernel<0, 1>;
+        case 2: return ensemble_kernel<1, 0>;
+        case 3: return ensemble_kernel<1, 1>;
+        case 4: return ensemble_kernel<2, 0>;
+        case 5: return ensemble_kernel<2, 1>;
+        case 6: return ensemble_kernel<3, 0>;
+        case 7: return ensemble_kernel<3, 1>;
+        case 8: return ensemble_kernel<4, 0>;
+        default: return ensemble_kernel<4, 1>;
+    }
+}
+
+static uint64_t up256(uint64_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace lbib
+
+using namespace lbib;
+
+struct lbib_ensemble {
+    int n = 0;
+    std::vector<lbib_ctx*> ctx;
+    std::vector<uint64_t> off;  // workspace offset of each tissue
+    char* ws = nullptr;
+    uint64_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t tab_off = 0, ipfx_off = 0, cpfx_off = 0, bar_off = 0;
+    int S = 0, forcing = 0;
+    int nodes_per_item = 256;
+    int blocks_per_sm = 0;  // 0 = as many as fit
+    int max_blocks_per_sm = 0;
+    int n_sms = 0;
+    std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
+    bool graph_ok = true;
+    std::string err;
+};
+
+static thread_local std::string g_ens_err;
+
+static int ens_fail(lbib_ensemble* e, int code, const std::string& msg) {
+    if (e) e->err = msg;
+    set_thread_error(code, msg);
+    g_ens_err = msg;
+    return code;
+}
+
+static void ens_drop_graphs(lbib_ensemble* e) {
+    for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+    e->graphs.clear();
+}
+
+static uint64_t ens_region_bytes(int n) {
+    return up256(sizeof(TissueDev) * (uint64_t)n) + 2 * up256(4 * (uint64_t)(n + 1)) + 256;
+}
+
+// Build the per-tissue table and prefix sums (host), upload them.
+static cudaError_t ens_upload(lbib_ensemble* e, int* total_items, int* total_cells) {
+    std::vector<TissueDev> tab((size_t)e->n);
+    std::vector<int> ipfx((size_t)e->n + 1, 0), cpfx((size_t)e->n + 1, 0);
+    for (int t = 0; t < e->n; ++t) {
+        lbib_ctx* c = e->ctx[t];
+        TissueDev& d = tab[t];
+        std::memset(&d, 0, sizeof(d));
+        d.la = ctx_lattice_args(c, 0, false);
+        d.ia = ctx_ib_args(c, true, true, false);
+        d.k = c->kf;
+        d.bc_y = c->p.bc_y;
+        d.nxr = (c->p.nx + 31) / 32 * 32;
+        d.cur = c->cur;
+        const int64_t nodes = (int64_t)d.nxr * c->p.ny;
+        ipfx[t + 1] = ipfx[t] + (int)((nodes + e->nodes_per_item - 1) / e->nodes_per_item);
+        cpfx[t + 1] = cpfx[t] + c->nC;
+    }
+    *total_items = ipfx[e->n];
+    *total_cells = cpfx[e->n];
+    cudaError_t er = cudaMemcpyAsync(e->ws + e->tab_off, tab.data(), sizeof(TissueDev) * e->n,
+                                     cudaMemcpyHostToDevice, e->stream);
+    if (er == cudaSuccess)
+        er = cudaMemcpyAsync(e->ws + e->ipfx_off, ipfx.data(), 4 * (e->n + 1),
+                             cudaMemcpyHostToDevice, e->stream);
+    if (er == cudaSuccess)
+        er = cudaMemcpyAsync(e->ws + e->cpfx_off, cpfx.data(), 4 * (e->n + 1),
+                             cudaMemcpyHostToDevice, e->stream);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(e->stream);
+    return er;
+}
+
+static EnsArgs ens_args(lbib_ensemble* e, int n_steps, int total_items, int total_cells,
+                        unsigned nblocks) {
+    EnsArgs a;
+    a.tis = reinterpret_cast<const TissueDev*>(e->ws + e->tab_off);
+    a.item_pfx = reinterpret_cast<const int*>(e->ws + e->ipfx_off);
+    a.cell_pfx = reinterpret_cast<const int*>(e->ws + e->cpfx_off);
+    a.n = e->n;
+    a.n_steps = n_steps;
+    a.nodes_per_item = e->nodes_per_item;
+    a.total_items = total_items;
+    a.total_cells = total_cells;
+    a.bar = reinterpret_cast<unsigned*>(e->ws + e->bar_off);
+    a.nblocks = nblocks;
+    return a;
+}
+
+static unsigned ens_grid(lbib_ensemble* e) {
+    int per = e->blocks_per_sm > 0 ? std::min(e->blocks_per_sm, e->max_blocks_per_sm)
+                                   : e->max_blocks_per_sm;
+    if (per < 1) per = 1;
+    return (unsigned)(per * e->n_sms);
+}
+
+static cudaError_t ens_launch(lbib_ensemble* e, const EnsArgs& a, unsigned grid,
+                              cudaStream_t st) {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kIBThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pick_kernel(e->S, e->forcing), a);
+}
+
+extern "C" {
+
+int lbib_ensemble_workspace_size(int32_t n, const lbib_params* params,
+                                 const int32_t* max_vertices, const int32_t* max_cells,
+                                 uint64_t* bytes_out) {
+    if (n < 1 || !params || !max_vertices || !max_cells || !bytes_out)
+        return ens_fail(nullptr, LBIB_E_PARAM, "lbib_ensemble_workspace_size: invalid arguments");
+    uint64_t total = 0;
+    for (int t = 0; t < n; ++t) {
+        uint64_t b = 0;
+        int rc = lbib_workspace_size(params + t, max_vertices[t], max_cells[t], &b);
+        if (rc) return rc;
+        total += up256(b);
+    }
+    *bytes_out = total + ens_region_bytes(n);
+    return LBIB_OK;
+}
+
+int lbib_ensemble_create(int32_t n, const lbib_params* params, const int32_t* max_vertices,
+                         const int32_t* max_cells, void* d_workspace, uint64_t bytes,
+                         void* cuda_stream, lbib_ensemble** out) {
+    if (!out) return ens_fail(nullptr, LBIB_E_PARAM, "out is NULL");
+    *out = nullptr;
+    uint64_t need = 0;
+    int rc = lbib_ensemble_workspace_size(n, params, max_vertices, max_cells, &need);
+    if (rc) return rc;
+    for (int t = 0; t < n; ++t) {
+        if (params[t].precision != LBIB_FP32)
+            return ens_fail(nullptr, LBIB_E_PARAM, "ensemble tissues use FP32 storage");
+        if (params[t].n_species != params[0].n_species || params[t].forcing != params[0].forcing)
+            return ens_fail(nullptr, LBIB_E_PARAM,
+                            "ensemble tissues share the species count and forcing");
+    }
+    if (!d_workspace || bytes < need || reinterpret_cast<uintptr_t>(d_workspace) % 256)
+        return ens_fail(nullptr, LBIB_E_WORKSPACE,
+                        "ensemble workspace NULL, misaligned or smaller than " +
+                            std::to_string(need));
+    lbib_ensemble* e = new (std::nothrow) lbib_ensemble();
+    if (!e) return ens_fail(nullptr, LBIB_E_PARAM, "out of host memory");
+    e->n = n;
+    e->ws = static_cast<char*>(d_workspace);
+    e->bytes = bytes;
+    e->stream = static_cast<cudaStream_t>(cuda_stream);
+    e->S = params[0].n_species;
+    e->forcing = params[0].forcing;
+    uint64_t o = 0;
+    for (int t = 0; t < n; ++t) {
+        uint64_t b = 0;
+        lbib_workspace_size(params + t, max_vertices[t], max_cells[t], &b);
+        lbib_ctx* c = nullptr;
+        rc = lbib_create(params + t, max_vertices[t], max_cells[t], e->ws + o, b, cuda_stream, &c);
+        if (rc) {
+            for (auto* x : e->ctx) lbib_destroy(x);
+            delete e;
+            return rc;
+        }
+        e->ctx.push_back(c);
+        e->off.push_back(o);
+        o += up256(b);
+    }
+    e->tab_off = o;
+    e->ipfx_off = e->tab_off + up256(sizeof(TissueDev) * (uint64_t)n);
+    e->cpfx_off = e->ipfx_off + up256(4 * (uint64_t)(n + 1));
+    e->bar_off = e->cpfx_off + up256(4 * (uint64_t)(n + 1));
+    int dev = 0;
+    cudaError_t er = cudaGetDevice(&dev);
+    if (er == cudaSuccess) er = cudaDeviceGetAttribute(&e->n_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (er == cudaSuccess)
+        er = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &e->max_blocks_per_sm, (const void*)pick_kernel(e->S, e->forcing), kIBThreads, 0);
+    if (er == cudaSuccess) er = cudaMemsetAsync(e->ws + e->bar_off, 0, 256, e->stream);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(e->stream);
+    if (er != cudaSuccess || e->max_blocks_per_sm < 1) {
+        for (auto* x : e->ctx) lbib_destroy(x);
+        delete e;
+        return ens_fail(nullptr, LBIB_E_CUDA,
+                        std::string("lbib_ensemble_create: ") + cudaGetErrorString(er));
+    }
+    *out = e;
+    return LBIB_OK;
+}
+
+lbib_ctx* lbib_ensemble_tissue(lbib_ensemble* e, int32_t t) {
+    if (!e || t < 0 || t >= e->n) return nullptr;
+    return e->ctx[t];
+}
+
+int lbib_ensemble_step(lbib_ensemble* e, int32_t n_steps) {
+    if (!e) return LBIB_E_PARAM;
+    if (n_steps < 0) return ens_fail(e, LBIB_E_PARAM, "n_steps must be >= 0");
+    if (n_steps == 0) return LBIB_OK;
+    int items = 0, cells = 0;
+    cudaError_t er = ens_upload(e, &items, &cells);
+    if (er != cudaSuccess)
+        return ens_fail(e, LBIB_E_CUDA, std::string("lbib_ensemble_step: ") + cudaGetErrorString(er));
+    const unsigned grid = ens_grid(e);
+    const EnsArgs a = ens_args(e, n_steps, items, cells, grid);
+    // the kernel reads the table at run time; the graph depends only on the
+    // step count, the launch shape and the work totals
+    const auto key = std::make_tuple((int)n_steps, items, cells);
+    auto it = e->graphs.find(key);
+    bool launched = false;
+    if (e->graph_ok && it == e->graphs.end()) {
+        cudaStream_t cap;
+        er = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        cudaGraph_t g = nullptr;
+        if (er == cudaSuccess) er = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (er == cudaSuccess) {
+            cudaError_t e2 = ens_launch(e, a, grid, cap);
+            er = cudaStreamEndCapture(cap, &g);
+            if (e2 != cudaSuccess) er = e2;
+        }
+        cudaGraphExec_t ex = nullptr;
+        if (er == cudaSuccess) er = cudaGraphInstantiate(&ex, g, 0);
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        if (er == cudaSuccess) {
+            it = e->graphs.emplace(key, ex).first;
+        } else {
+            cudaGetLastError();
+            e->graph_ok = false;  // fall back to direct cooperative launches
+        }
+    }
+    if (e->graph_ok && it != e->graphs.end()) {
+        er = cudaGraphLaunch(it->second, e->stream);
+        launched = true;
+    }
+    if (!launched) er = ens_launch(e, a, grid, e->stream);
+    if (er != cudaSuccess)
+        return ens_fail(e, LBIB_E_CUDA, std::string("lbib_ensemble_step: ") + cudaGetErrorString(er));
+    for (auto* c : e->ctx) {
+        c->cur = (c->cur + n_steps) & 1;
+        c->fields_valid = true;
+        c->vforce_valid = c->nC > 0;
+    }
+    return LBIB_OK;
+}
+
+int lbib_ensemble_status(lbib_ensemble* e) {
+    if (!e) return LBIB_E_PARAM;
+    unsigned bar[3] = {0, 0, 0};
+    cudaError_t er = cudaMemcpyAsync(bar, e->ws + e->bar_off, sizeof(bar), cudaMemcpyDeviceToHost,
+                                     e->stream);
+    if (er == cudaSuccess) er = cudaStreamSynchronize(e->stream);
+    if (er != cudaSuccess)
+        return ens_fail(e, LBIB_E_CUDA, std::string("lbib_ensemble_status: ") + cudaGetErrorString(er));
+    if (bar[2]) {
+        // clear the barrier state so that the ensemble can run again
+        cudaMemsetAsync(e->ws + e->bar_off, 0, 256, e->stream);
+        cudaStreamSynchronize(e->stream);
+        return ens_fail(e, LBIB_E_TIMEOUT, "a grid barrier wait ran out (about one second)");
+    }
+    return LBIB_OK;
+}
+
+int lbib_ensemble_config(lbib_ensemble* e, int32_t nodes_per_item, int32_t blocks_per_sm,
+                         int32_t* graph_out, int32_t* grid_out) {
+    if (!e) return LBIB_E_PARAM;
+    if (nodes_per_item > 0) {
+        if (nodes_per_item % kIBThreads)
+            return ens_fail(e, LBIB_E_PARAM, "nodes_per_item must be a multiple of 256");
+        if (nodes_per_item != e->nodes_per_item) ens_drop_graphs(e);
+        e->nodes_per_item = nodes_per_item;
+    }
+    if (blocks_per_sm >= 0) {
+        if (blocks_per_sm != e->blocks_per_sm) ens_drop_graphs(e);
+        e->blocks_per_sm = blocks_per_sm;
+    }
+    if (graph_out) *graph_out = e->graph_ok ? 1 : 0;
+    if (grid_out) *grid_out = (int32_t)ens_grid(e);
+    return LBIB_OK;
+}
+
+int lbib_ensemble_tune(lbib_ensemble* e, int32_t trial_steps, int32_t* config_out,
+                       double* ms_out) {
+    if (!e || trial_steps < 1 || !config_out) return LBIB_E_PARAM;
+    const int npis[3] = {256, 512, 1024};
+    double best = 1e300;
+    int best_npi = e->nodes_per_item, best_bps = e->blocks_per_sm;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    for (int npi : npis) {
+        for (int bps = 1; bps <= e->max_blocks_per_sm; ++bps) {
+            e->nodes_per_item = npi;
+            e->blocks_per_sm = bps;
+            int items = 0, cells = 0;
+            cudaError_t er = ens_upload(e, &items, &cells);
+            const unsigned grid = ens_grid(e);
+            const EnsArgs a = ens_args(e, trial_steps, items, cells, grid);
+            float ms = 0.f, msb = 1e30f;
+            for (int rep = 0; rep < 2 && er == cudaSuccess; ++rep) {
+                er = cudaEventRecord(t0, e->stream);
+                if (er == cudaSuccess) er = ens_launch(e, a, grid, e->stream);
+                if (er == cudaSuccess) er = cudaEventRecord(t1, e->stream);
+                if (er == cudaSuccess) er = cudaEventSynchronize(t1);
+                if (er == cudaSuccess) er = cudaEventElapsedTime(&ms, t0, t1);
+                for (auto* c : e->ctx) c->cur = (c->cur + trial_steps) & 1;
+                if (er == cudaSuccess) msb = std::min(msb, ms);
+            }
+            if (er != cudaSuccess) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+                return ens_fail(e, LBIB_E_CUDA, std::string("lbib_ensemble_tune: ") +
+                                                    cudaGetErrorString(er));
+            }
+            const int st = lbib_ensemble_status(e);
+            if (st) {
+                cudaEventDestroy(t0);
+                cudaEventDestroy(t1);
+                return st;
+            }
+            if (msb < best) {
+                best = msb;
+                best_npi = npi;
+                best_bps = bps;
+            }
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (auto* c : e->ctx) {
+        c->fields_valid = true;
+        c->vforce_valid = c->nC > 0;
+    }
+    ens_drop_graphs(e);
+    e->nodes_per_item = best_npi;
+    e->blocks_per_sm = best_bps;
+    config_out[0] = best_npi;
+    config_out[1] = best_bps;
+    if (ms_out) *ms_out = best / trial_steps;
+    return LBIB_OK;
+}
+
+int lbib_ensemble_selftest_timeout(lbib_ensemble* e, double* seconds_out) {
+    if (!e) return LBIB_E_PARAM;
+    unsigned* bar = reinterpret_cast<unsigned*>(e->ws + e->bar_off);
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    cudaError_t er = cudaMemsetAsync(bar, 0, 256, e->stream);
+    if (er == cudaSuccess) er = cudaEventRecord(t0, e->stream);
+    if (er == cudaSuccess) {
+        barrier_timeout_kernel<<<1, 32, 0, e->stream>>>(bar, 2u);  // waits for a CTA that never comes
+        er = cudaGetLastError();
+    }
+    if (er == cudaSuccess) er = cudaEventRecord(t1, e->stream);
+    if (er == cudaSuccess) er = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (er == cudaSuccess) cudaEventElapsedTime(&ms, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (er != cudaSuccess)
+        return ens_fail(e, LBIB_E_CUDA, std::string("selftest: ") + cudaGetErrorString(er));
+    if (seconds_out) *seconds_out = ms * 1e-3;
+    return lbib_ensemble_status(e);
+}
+
+void lbib_ensemble_destroy(lbib_ensemble* e) {
+    if (!e) return;
+    ens_drop_graphs(e);
+    for (auto* c : e->ctx) lbib_destroy(c);
+    delete e;
+}
+
+const char* lbib_ensemble_last_error(const lbib_ensemble* e) {
+    return e ? e->err.c_str() : g_ens_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,462 @@
+// ib_cell.cuh -- device code of the immersed-boundary work of one cell
+// (shared by the per-tissue kernels and the ensemble's persistent kernel).
+#pragma once
+
+#include <climits>
+#include <type_traits>
+
+#include "lbib_internal.cuh"
+
+namespace lbib {
+
+
+constexpr int kIBThreads = 256;
+static_assert(kIBThreads >= kMaxRows, "row counters are cleared one per thread");
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// Weights of the 4 support nodes along one axis, base = floor(X) - 1.
+// With f = X - floor(X) the four offsets are r = -1-f, -f, 1-f, 2-f, and
+// cos(pi |r| / 2) is -sin, cos, sin, -cos of pi f / 2 respectively, so one
+// sincospi gives all four values of Eq. 1Dkernel.
+template <typename C>
+__device__ __forceinline__ void axis_weights(double X, int* base, C w[4]) {
+    const double fl = floor(X);
+    *base = (int)fl - 1;
+    C sn, cs;
+    if (sizeof(C) == 8) {
+        double s2, c2;
+        sincospi(0.5 * (X - fl), &s2, &c2);
+        sn = (C)s2;
+        cs = (C)c2;
+    } else {
+        float s2, c2;
+        sincospif(0.5f * (float)(X - fl), &s2, &c2);
+        sn = (C)s2;
+        cs = (C)c2;
+    }
+    w[0] = C(0.25) * (C(1) - sn);
+    w[1] = C(0.25) * (C(1) + cs);
+    w[2] = C(0.25) * (C(1) + sn);
+    w[3] = C(0.25) * (C(1) - cs);
+}
+
+// raise a diagnostic flag (labelling-only callers may pass no flag words)
+__device__ __forceinline__ void raise_flag(uint32_t* diag, int k) {
+    if (diag) atomicOr(diag + k, 1u);
+}
+
+// spread one weighted force into a node: FP32 uses the float2 vector atomic
+__device__ __forceinline__ void spread_add(float2* p, float fx, float fy) {
+    atomicAdd(p, make_float2(fx, fy));
+}
+__device__ __forceinline__ void spread_add(double2* p, double fx, double fy) {
+    atomicAdd(&p->x, fx);
+    atomicAdd(&p->y, fy);
+}
+
+// Hookean spring of the edge A -> B with constant k and rest length L0: the
+// force on A (B receives the opposite).  FP64 path: all FP64.  FP32 path: the
+// stretch |d| - L0 = (|d|^2 - L0^2)/(|d| + L0) takes its cancelling difference
+// in FP64 and the rest in FP32.
+template <typename C>
+__device__ __forceinline__ void spring(double2 A, double2 B, double L0, double kk, C* fx, C* fy) {
+    const double dx = B.x - A.x, dy = B.y - A.y;
+    if (sizeof(C) == 8) {
+        const double len = sqrt(dx * dx + dy * dy);
+        const double sc = kk * (len - L0) / len;
+        *fx = (C)(sc * dx);
+        *fy = (C)(sc * dy);
+    } else {
+        const double len2 = dx * dx + dy * dy;
+        const float d2 = (float)(len2 - L0 * L0);
+        const float len = sqrtf((float)len2);
+        const float sc = (float)kk * (d2 / (len + (float)L0)) / len;
+        *fx = (C)(sc * (float)dx);
+        *fy = (C)(sc * (float)dy);
+    }
+}
+
+// crossing abscissa of edge A -> B with row y, every operation rounded on its own
+__device__ __forceinline__ double crossing_x(double2 A, double2 B, double yn) {
+    return __dadd_rn(A.x, __ddiv_rn(__dmul_rn(__dsub_rn(yn, A.y), __dsub_rn(B.x, A.x)),
+                                    __dsub_rn(B.y, A.y)));
+}
+
+// Mark in `mask` (1 bit per 4 consecutive nodes) the groups of the four
+// support nodes of one kernel row: one atomicOr per 32-group word touched.
+__device__ __forceinline__ void mark_row(uint32_t* mask, int64_t rowbase, const int ix[4]) {
+    if (!mask) return;
+    int64_t wd = -1;
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t g = (rowbase + ix[i]) >> 2;
+        if ((g >> 5) != wd) {
+            if (bits) atomicOr(mask + wd, bits);
+            wd = g >> 5;
+            bits = 0u;
+        }
+        bits |= 1u << (g & 31);
+    }
+    atomicOr(mask + wd, bits);
+}
+
+// Mark the group of one node; the active lanes of a warp combine their bits
+// per word first.
+__device__ __forceinline__ void mark_node_warp(uint32_t* mask, int64_t node) {
+    if (!mask) return;
+    const unsigned act = __activemask();
+    const int64_t g = node >> 2;
+    const unsigned long long w = (unsigned long long)(g >> 5);
+    const unsigned peers = __match_any_sync(act, w);
+    const uint32_t bits = __reduce_or_sync(peers, 1u << (g & 31));
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(mask + w, bits);
+}
+
+// Labels of one cell (phase 3 of the IB kernels).  With scan_ok the per-row
+// thresholds in thr/rowcnt are complete: one warp per row sorts them and
+// fills each span [t_{2k}, t_{2k+1}) -- the nodes with an odd number of
+// thresholds above them.  Otherwise every node of the box evaluates the
+// crossing predicate over all edges in FP64 (the brute-force path).
+static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, const double2* sx,
+                                         const int* rowcnt, int* thr, bool scan_ok, int I0,
+                                         int J0, int rows, int cols) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int nwarps = kIBThreads / 32;
+    uint32_t* id = a.id;
+    const uint32_t code = ((uint32_t)c << 4) | (uint32_t)(a.srcf[c] & 0xF);
+    const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
+    if (scan_ok) {
+        // one warp per row: sort the row's thresholds, then fill each span
+        // [t_{2k}, t_{2k+1}) -- the nodes with an odd number of thresholds
+        // above them
+        for (int r = warp; r < rows; r += nwarps) {
+            const int J = J0 + r;
+            if (a.bc_y && (J < 0 || J >= a.ny)) continue;
+            const int m = rowcnt[r];
+            int* tr = thr + r * kMaxCross;
+            if (lane == 0) {
+                for (int q = 1; q < m; ++q) {
+                    const int v = tr[q];
+                    int p = q - 1;
+                    while (p >= 0 && tr[p] > v) {
+                        tr[p + 1] = tr[p];
+                        --p;
+                    }
+                    tr[p + 1] = v;
+                }
+            }
+            __syncwarp();
+            int wJ = wJ0 + r;
+            if (wJ >= a.ny) wJ -= a.ny;
+            uint32_t* rowp = id + (int64_t)wJ * a.pitch;
+            if ((m & 1) == 0) {
+                for (int k = 0; k + 1 < m; k += 2) {
+                    const int lo = tr[k], hi = tr[k + 1];
+                    for (int I = lo + lane; I < hi; I += 32) {
+                        int wI = wI0 + (I - I0);
+                        if (wI >= a.nx) wI -= a.nx;
+                        atomicMin(rowp + wI, code);
+                        mark_node_warp(a.lmask, (int64_t)wJ * a.pitch + wI);
+                    }
+                }
+            } else {  // odd count: evaluate the parity rule node by node
+                for (int cc = lane; cc < cols; cc += 32) {
+                    const int I = I0 + cc;
+                    int cnt = 0;
+                    for (int q = 0; q < m; ++q) cnt += (tr[q] > I);
+                    if (cnt & 1) {
+                        int wI = wI0 + cc;
+                        if (wI >= a.nx) wI -= a.nx;
+                        atomicMin(rowp + wI, code);
+                        if (a.lmask) {
+                            const int64_t g = ((int64_t)wJ * a.pitch + wI) >> 2;
+                            atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    } else {
+        // brute force: the same predicate per node over all edges
+        if (tid == 0) raise_flag(a.diag, kDiagRasterSlow);
+        for (int e = tid; e < rows * cols; e += kIBThreads) {
+            const int r = e / cols, cc = e % cols, J = J0 + r;
+            if (a.bc_y && (J < 0 || J >= a.ny)) continue;
+            const double xn = (double)(I0 + cc), yn = (double)J;
+            bool inside = false;
+            for (int t = 0; t < n; ++t) {
+                const double2 A = sx[t], B = sx[(t == n - 1) ? 0 : t + 1];
+                if ((A.y <= yn) != (B.y <= yn) && xn < crossing_x(A, B, yn)) inside = !inside;
+            }
+            if (inside) {
+                int wI = wI0 + cc, wJ = wJ0 + r;
+                if (wI >= a.nx) wI -= a.nx;
+                if (wJ >= a.ny) wJ -= a.ny;
+                atomicMin(id + (int64_t)wJ * a.pitch + wI, code);
+                if (a.lmask) {
+                    const int64_t g = ((int64_t)wJ * a.pitch + wI) >> 2;
+                    atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 path.  GB300's FP64 rate is a small fraction of its FP32 rate, so the
+// FP32 path keeps FP64 to what the storage rule and exactness need: each
+// vertex position is FP64; per vertex and step it takes floor(X) and the
+// fraction X - floor(X) once (FP64 -> int + float).  Everything else --
+// kernel weights, edge vectors, springs, pressure, tension, scanline
+// crossings -- is FP32 on (integer base, fraction) pairs:
+//   * an edge vector is (base_b - base_a) + (frac_b - frac_a), accurate to
+//     about 1e-7 LU whatever the coordinate magnitude;
+//   * ceil(y) = base_y + (frac_y > 0) is exact, so the row predicate
+//     (y_a <= J) != (y_b <= J) is evaluated exactly in integers;
+//   * a crossing abscissa is computed in FP32 relative to its edge's first
+//     vertex with an error bound E; if [x - E, x + E] holds no integer its
+//     ceiling is the ceiling of the exact FP64 value, otherwise (rare) the
+//     FP64 formula is evaluated, so labels stay identical to the FP64 rule.
+// The (base, fraction) of X^{n+1} computed at the end of a launch is stored
+// per vertex and reused by the interpolation of the next launch.
+
+__device__ __forceinline__ void base_frac(double X, int* b, float* f) {
+    const double fl = floor(X);
+    *b = (int)fl;
+    *f = (float)(X - fl);
+}
+
+__device__ __forceinline__ void weights_from_frac(float f, float w[4]) {
+    float sn, cs;
+    sincospif(0.5f * f, &sn, &cs);
+    w[0] = 0.25f * (1.f - sn);
+    w[1] = 0.25f * (1.f + cs);
+    w[2] = 0.25f * (1.f + sn);
+    w[3] = 0.25f * (1.f - cs);
+}
+
+__device__ __forceinline__ float2 edge_vec(int2 ba, float2 fa, int2 bb, float2 fb) {
+    return make_float2((float)(bb.x - ba.x) + (fb.x - fa.x), (float)(bb.y - ba.y) + (fb.y - fa.y));
+}
+
+// spring force on the first vertex of an edge with vector d (FP32)
+__device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
+    const float len2 = d.x * d.x + d.y * d.y;
+    const float len = sqrtf(len2);
+    const float sc = kk * ((len2 - L0 * L0) / (len + L0)) / len;
+    return make_float2(sc * d.x, sc * d.y);
+}
+
+// The work of one cell by one CTA of kIBThreads threads.  Callers that run
+// several cells through the same CTA call it again for the next cell; the
+// first barrier protects the shared arrays of the previous call.
+static __device__ void ib_cell_f32(const IBArgs& a, int c, IBSmem32& S) {
+    double2* sx = S.sx;
+    int2* sb = S.sb;
+    float2* sf = S.sf;
+    int* rowcnt = S.rowcnt;
+    int* thr = S.thr;
+    int* sbox = S.sbox;
+    int& s_flag = S.s_flag;
+    __syncthreads();
+
+    const int v0 = a.off[c];
+    const int n = a.off[c + 1] - v0;
+    const int tid = threadIdx.x, lane = tid & 31;
+
+    if (tid < kMaxRows) rowcnt[tid] = 0;
+    if (tid == 0) {
+        sbox[0] = INT_MAX; sbox[1] = INT_MIN; sbox[2] = INT_MAX; sbox[3] = INT_MIN;
+        s_flag = 0;
+    }
+
+    // ---- (1) interpolate u^n at X^n and move; (base, frac) of the new X
+    int ilo = INT_MAX, ihi = INT_MIN, jlo = INT_MAX, jhi = INT_MIN;
+    bool finite = true;
+    for (int t = tid; t < n; t += kIBThreads) {
+        double2 X = a.xy[v0 + t];
+        int2 b;
+        float2 f;
+        if (a.do_move) {
+            if (a.vbase) {
+                b = a.vbase[v0 + t];
+                f = a.vfrac[v0 + t];
+            } else {
+                base_frac(X.x, &b.x, &f.x);
+                base_frac(X.y, &b.y, &f.y);
+            }
+            float wx[4], wy[4];
+            weights_from_frac(f.x, wx);
+            weights_from_frac(f.y, wy);
+            const float2* u = static_cast<const float2*>(a.u);
+            float Ux = 0.f, Uy = 0.f;
+            int ix[4];
+            ix[0] = wrapi(b.x - 1, a.nx);
+#pragma unroll
+            for (int i = 1; i < 4; ++i) ix[i] = (ix[i - 1] + 1 == a.nx) ? 0 : ix[i - 1] + 1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                int J = b.y - 1 + j;
+                if (a.bc_y) {
+                    if (J < 0 || J >= a.ny) continue;
+                } else {
+                    J = wrapi(J, a.ny);
+                }
+                const float2* row = u + (int64_t)J * a.pitch;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 v = row[ix[i]];
+                    const float w = wx[i] * wy[j];
+                    Ux += v.x * w;
+                    Uy += v.y * w;
+                }
+            }
+            X.x += (double)Ux;
+            X.y += (double)Uy;
+            a.xy[v0 + t] = X;
+        }
+        base_frac(X.x, &b.x, &f.x);
+        base_frac(X.y, &b.y, &f.y);
+        sx[t] = X;
+        sb[t] = b;
+        sf[t] = f;
+        if (a.do_prep && a.vbase) {
+            a.vbase[v0 + t] = b;
+            a.vfrac[v0 + t] = f;
+        }
+        finite = finite && isfinite(f.x) && isfinite(f.y) && b.x > -1000000000 &&
+                 b.x < 1000000000 && b.y > -1000000000 && b.y < 1000000000;
+        const int cyv = b.y + (f.y > 0.f ? 1 : 0);  // ceil(y), exact
+        ilo = min(ilo, b.x);
+        ihi = max(ihi, b.x);
+        jlo = min(jlo, cyv);
+        jhi = max(jhi, cyv);
+    }
+    if (!a.do_prep) return;
+    ilo = __reduce_min_sync(0xffffffffu, ilo);
+    ihi = __reduce_max_sync(0xffffffffu, ihi);
+    jlo = __reduce_min_sync(0xffffffffu, jlo);
+    jhi = __reduce_max_sync(0xffffffffu, jhi);
+    finite = __all_sync(0xffffffffu, finite);
+    __syncthreads();
+    if (lane == 0) {
+        atomicMin(&sbox[0], ilo);
+        atomicMax(&sbox[1], ihi);
+        atomicMin(&sbox[2], jlo);
+        atomicMax(&sbox[3], jhi);
+        if (!finite) s_flag = 2;
+    }
+    __syncthreads();
+    // columns: floor(x) over the vertices, widened by one on each side (the
+    // fractions are FP32); rows: every J with min ceil(y) <= J < max ceil(y),
+    // exactly the rows some edge crosses
+    const int I0 = sbox[0] - 1, I1 = sbox[1] + 1, J0 = sbox[2], J1 = sbox[3] - 1;
+    // a box no wider than the lattice keeps the wrapped indices of the fill
+    // within one period; anything wider means the geometry has blown up
+    const bool geom_ok = s_flag == 0 && (I1 - I0) < a.nx && (J1 - J0) <= a.ny;
+    if (a.do_mask && !geom_ok && tid == 0) raise_flag(a.diag, kDiagGeometry);
+    const bool labels = a.do_mask && geom_ok && J1 >= J0;
+    const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
+    const bool scan = labels && rows <= kMaxRows;
+
+    constexpr int half = kIBThreads / 2;
+    if (tid < half) {
+        if (a.do_force) {
+            float2* force = static_cast<float2*>(a.force);
+            const float p = (float)a.pres[c];
+            const float ten = (float)a.tension;
+            for (int t = tid; t < n; t += half) {
+                const int tp = (t == 0) ? n - 1 : t - 1;
+                const int tn = (t == n - 1) ? 0 : t + 1;
+                const int2 b = sb[t];
+                const float2 f = sf[t];
+                const float2 dn = edge_vec(b, f, sb[tn], sf[tn]);   // X_{t+1} - X_t
+                const float2 dp = edge_vec(sb[tp], sf[tp], b, f);   // X_t - X_{t-1}
+                const float2 s0 = spring32(dn, (float)a.L0[v0 + t], (float)a.k[v0 + t]);
+                const float2 s1 = spring32(dp, (float)a.L0[v0 + tp], (float)a.k[v0 + tp]);
+                float Fx = s0.x - s1.x, Fy = s0.y - s1.y;
+                // pressure p dA/dX: (p/2)(y_{t+1} - y_{t-1}, x_{t-1} - x_{t+1})
+                Fx += 0.5f * p * (dn.y + dp.y);
+                Fy -= 0.5f * p * (dn.x + dp.x);
+                if (ten != 0.f) {  // Eq. membraneforce
+                    const float ln = sqrtf(dn.x * dn.x + dn.y * dn.y);
+                    const float lp = sqrtf(dp.x * dp.x + dp.y * dp.y);
+                    Fx += ten * (dn.x / ln - dp.x / lp);
+                    Fy += ten * (dn.y / ln - dp.y / lp);
+                }
+                if (a.write_vforce) a.vforce[v0 + t] = make_double2((double)Fx, (double)Fy);
+
+                float wx[4], wy[4];
+                weights_from_frac(f.x, wx);
+                weights_from_frac(f.y, wy);
+                int ix[4];
+                ix[0] = wrapi(b.x - 1, a.nx);
+#pragma unroll
+                for (int i = 1; i < 4; ++i) ix[i] = (ix[i - 1] + 1 == a.nx) ? 0 : ix[i - 1] + 1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int J = b.y - 1 + j;
+                    if (a.bc_y) {
+                        if (J < 0 || J >= a.ny) {
+                            raise_flag(a.diag, kDiagWallStencil);
+                            continue;
+                        }
+                    } else {
+                        J = wrapi(J, a.ny);
+                    }
+                    float2* row = force + (int64_t)J * a.pitch;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float w = wx[i] * wy[j];
+                        spread_add(&row[ix[i]], Fx * w, Fy * w);
+                    }
+                    mark_row(a.fmask, (int64_t)J * a.pitch, ix);
+                }
+            }
+        }
+    } else if (scan) {
+        for (int e = tid - half; e < n; e += half) {
+            const int eb = (e == n - 1) ? 0 : e + 1;
+            const int2 ba = sb[e], bb = sb[eb];
+            const float2 fa = sf[e], fb = sf[eb];
+            const int cya = ba.y + (fa.y > 0.f ? 1 : 0), cyb = bb.y + (fb.y > 0.f ? 1 : 0);
+            if (cya == cyb) continue;
+            // rows J with (y_a <= J) != (y_b <= J): min(cy) <= J < max(cy)
+            const int jl = min(cya, cyb), jh = max(cya, cyb) - 1;
+            const float2 d = edge_vec(ba, fa, bb, fb);
+            const float ratio = fabsf(d.x) / fabsf(d.y);
+            for (int J = jl; J <= jh; ++J) {
+                // x_c - base_a.x = frac_a.x + (J - y_a)(x_b - x_a)/(y_b - y_a)
+                const float pr = (float)(J - ba.y) - fa.y;
+                const float xr = fa.x + (pr * d.x) / d.y;
+                const float E = 9.5367431640625e-07f * (4.f + 4.f * ratio + fabsf(d.x) + fabsf(xr));
+                const float clo = ceilf(xr - E), chi = ceilf(xr + E);
+                int ti;
+                if (clo == chi) {
+                    ti = ba.x + (int)clo;
+                } else {
+                    const double tc = ceil(crossing_x(sx[e], sx[eb], (double)J));
+                    ti = tc < (double)I0 ? I0 : (tc > (double)(I1 + 1) ? I1 + 1 : (int)tc);
+                }
+                ti = ti < I0 ? I0 : (ti > I1 + 1 ? I1 + 1 : ti);
+                const int slot = atomicAdd(&rowcnt[J - J0], 1);
+                if (slot < kMaxCross)
+                    thr[(J - J0) * kMaxCross + slot] = ti;
+                else
+                    s_flag = 1;
+            }
+        }
+    }
+    if (!a.do_mask) return;
+    __syncthreads();
+    if (!labels) return;
+    fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols);
+}
+
+}  // namespace lbib

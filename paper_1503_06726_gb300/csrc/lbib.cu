@@ -206,6 +206,11 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) {
     return a;
 }
 
+namespace lbib {
+LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out) { return lattice_args(c, src_buf, out); }
+IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) { return ib_args(c, move, prep, vforce); }
+}  // namespace lbib
+
 static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out) {
     LatticeArgs a = lattice_args(c, src_buf, out);
     return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,

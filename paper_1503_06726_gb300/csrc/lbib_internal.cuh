@@ -176,3 +176,8 @@ struct lbib_ctx {
     T* at(uint64_t off) const { return reinterpret_cast<T*>(ws + off); }
 };
 
+namespace lbib {
+// kernel arguments of a context (its buffers, parity src_buf)
+LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out);
+IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool vforce);
+}  // namespace lbib

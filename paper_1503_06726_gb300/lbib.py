@@ -42,6 +42,9 @@ EXPORTS = (
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
     "lbib_status_string", "lbib_label_cells", "lbib_steady_workspace_size", "lbib_steady_solve",
+    "lbib_ensemble_workspace_size", "lbib_ensemble_create", "lbib_ensemble_tissue",
+    "lbib_ensemble_step", "lbib_ensemble_status", "lbib_ensemble_config", "lbib_ensemble_tune",
+    "lbib_ensemble_selftest_timeout", "lbib_ensemble_destroy", "lbib_ensemble_last_error",
 )
 
 
@@ -94,6 +97,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_steady_workspace_size": (ctypes.c_int, [i32, i32, i32, ctypes.POINTER(u64)]),
         "lbib_steady_solve": (ctypes.c_int, [i32, i32, i32, vp, vp, vp, vp, vp, ctypes.c_double,
                                              ctypes.c_int64, i32, vp, vp, vp, vp, u64, vp]),
+        "lbib_ensemble_workspace_size": (ctypes.c_int, [i32, P, vp, vp, ctypes.POINTER(u64)]),
+        "lbib_ensemble_create": (ctypes.c_int, [i32, P, vp, vp, vp, u64, vp, ctypes.POINTER(vp)]),
+        "lbib_ensemble_tissue": (vp, [vp, i32]),
+        "lbib_ensemble_step": (ctypes.c_int, [vp, i32]),
+        "lbib_ensemble_status": (ctypes.c_int, [vp]),
+        "lbib_ensemble_config": (ctypes.c_int, [vp, i32, i32, vp, vp]),
+        "lbib_ensemble_tune": (ctypes.c_int, [vp, i32, vp, vp]),
+        "lbib_ensemble_selftest_timeout": (ctypes.c_int, [vp, vp]),
+        "lbib_ensemble_destroy": (None, [vp]),
+        "lbib_ensemble_last_error": (ctypes.c_char_p, [vp]),
         "lbib_destroy": (None, [vp]),
         "lbib_last_error": (ctypes.c_char_p, [vp]),
         "lbib_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -396,6 +409,125 @@ class Simulation:
         if getattr(self, "ctx", None):
             lbib_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- ensembles
+def _ens_check(rc, ens):
+    if rc != LBIB_OK:
+        raise LbibError(rc, load().lbib_ensemble_last_error(ens).decode(errors="replace"))
+
+
+class Ensemble:
+    """Many independent FP32 tissues advanced by one persistent launch per
+    step call.  ``params`` is a list of parameter objects; ``tissues`` the
+    matching list of tissues (lbib_inputs.Tissue-like)."""
+
+    def __init__(self, params, tissues, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbib needs a CUDA device; there is no CPU path")
+        L = load()
+        self.device = torch.device(device or "cuda")
+        n = len(params)
+        self.n = n
+        arr = (lbib_params * n)(*[make_params(p, LBIB_FP32) for p in params])
+        self._params = arr
+        self.dims = [(int(p.nx), int(p.ny), int(p.n_species)) for p in params]
+        mv = np.array([t.n_vertices for t in tissues], np.int32)
+        mc = np.array([t.n_cells for t in tissues], np.int32)
+        nb = ctypes.c_uint64(0)
+        vp = ctypes.c_void_p
+        _ens_check(L.lbib_ensemble_workspace_size(n, arr, mv.ctypes.data_as(vp),
+                                                  mc.ctypes.data_as(vp), ctypes.byref(nb)), None)
+        self.nbytes = int(nb.value)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p(0)
+        _ens_check(L.lbib_ensemble_create(n, arr, mv.ctypes.data_as(vp), mc.ctypes.data_as(vp),
+                                          vp(self.workspace.data_ptr()), self.nbytes,
+                                          vp(self.stream.cuda_stream), ctypes.byref(h)), None)
+        self.ens = h.value
+        self.ctx = [L.lbib_ensemble_tissue(self.ens, t) for t in range(n)]
+        self.sizes = [(0, 0)] * n
+        for t, T in enumerate(tissues):
+            if T is not None and T.n_cells:
+                lbib_set_cells(self.ctx[t], T.cell_off, T.xy, T.rest_len, T.k_spring,
+                               T.pressure, T.src_flag)
+                self.sizes[t] = lbib_get_sizes(self.ctx[t])
+
+    def step(self, n: int):
+        _ens_check(load().lbib_ensemble_step(self.ens, int(n)), self.ens)
+
+    def status(self):
+        _ens_check(load().lbib_ensemble_status(self.ens), self.ens)
+
+    def config(self, nodes_per_item: int = 0, blocks_per_sm: int = -1):
+        g, gr = ctypes.c_int32(0), ctypes.c_int32(0)
+        _ens_check(load().lbib_ensemble_config(self.ens, nodes_per_item, blocks_per_sm,
+                                               ctypes.byref(g), ctypes.byref(gr)), self.ens)
+        return {"graph": bool(g.value), "grid": int(gr.value)}
+
+    def tune(self, trial_steps: int = 20):
+        cfg = np.zeros(2, np.int32)
+        ms = ctypes.c_double(0.0)
+        _ens_check(load().lbib_ensemble_tune(self.ens, int(trial_steps),
+                                             cfg.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.byref(ms)), self.ens)
+        return {"nodes_per_item": int(cfg[0]), "blocks_per_sm": int(cfg[1]),
+                "ms_per_step": float(ms.value)}
+
+    def tune_cached(self, key: str, trial_steps: int = 20, path: Optional[str] = None):
+        """Autotune once per ``key`` and keep the choice in a JSON cache
+        (``$LBIB_TUNE_CACHE`` or ~/.cache/lbib_tune.json)."""
+        import json
+        path = path or os.environ.get("LBIB_TUNE_CACHE",
+                                      os.path.join(os.path.expanduser("~"), ".cache",
+                                                   "lbib_tune.json"))
+        cache = {}
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+        if key in cache:
+            c = cache[key]
+            self.config(c["nodes_per_item"], c["blocks_per_sm"])
+            return dict(c, cached=True)
+        c = self.tune(trial_steps)
+        cache[key] = c
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as f:
+                json.dump(cache, f, indent=1)
+        except OSError:
+            pass
+        return dict(c, cached=False)
+
+    def selftest_timeout(self):
+        sec = ctypes.c_double(0.0)
+        rc = load().lbib_ensemble_selftest_timeout(self.ens, ctypes.byref(sec))
+        return rc, float(sec.value)
+
+    def fields(self, t: int, which: int = LBIB_RHO | LBIB_U | LBIB_PHI | LBIB_X) -> dict:
+        nx, ny, S = self.dims[t]
+        nv, nc = self.sizes[t]
+        if S == 0:
+            which &= ~LBIB_PHI
+        if nc == 0:
+            which &= ~(LBIB_X | LBIB_AREA | LBIB_ID | LBIB_FORCE | LBIB_VFORCE)
+        return lbib_get_fields(self.ctx[t], which, nx, ny, S, nv, nc)
+
+    def close(self):
+        if getattr(self, "ens", None):
+            load().lbib_ensemble_destroy(self.ens)
+            self.ens = None
 
     def __del__(self):
         try:

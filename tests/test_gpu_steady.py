@@ -94,7 +94,7 @@ def test_steady_converges_like_oracle_and_warm_start(lb, orc):
         # of max phi) is a few percent of the threshold, which can delay the
         # FP32 decision by a few residual checks
         assert abs(int(steps[b]) - nref) <= 64, (steps[b], nref)
-        assert rel(phi[b], ref[0]) < 1e-4
+        assert rel(phi[b], ref[0]) < 2.0 * 1e-6 / float(k[b])
     # warm start from the converged field: the populations start at the rest
     # equilibrium w_q phi*, which lacks the non-equilibrium (flux) part of the
     # steady populations, so a short transient remains -- but far shorter
@@ -105,7 +105,11 @@ def test_steady_converges_like_oracle_and_warm_start(lb, orc):
                                               max_steps=100000)
     assert (resid_w <= 1e-6).all()
     assert (steps_w < steps // 2).all(), (steps_w, steps)
-    assert rel(phi_w.cpu().numpy(), np.stack(refs)) < 1e-4
+    # a residual r <= 1e-6 leaves each run within about r / decay of the exact
+    # steady field; runs that approach it from different sides can differ by
+    # twice that
+    bound = 2.0 * 1e-6 / float(min(k))
+    assert rel(phi_w.cpu().numpy(), np.stack(refs)) < bound
 
 
 def test_steady_uniform_source_closed_form(lb):
