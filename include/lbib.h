@@ -272,6 +272,71 @@ int lbib_ensemble_selftest_timeout(lbib_ensemble* ens, double* seconds_out);
 void lbib_ensemble_destroy(lbib_ensemble* ens);
 const char* lbib_ensemble_last_error(const lbib_ensemble* ens);
 
+/* ---- Neural operator: learned warm start of the steady morphogen solve ----
+ * The paper has no network; this is the learned part the measured method adds
+ * in front of lbib_steady_solve().  A six-level convolutional U-Net maps, per
+ * tissue, [cell mask, source mask, (D - 0.125)/0.075, log10(decay) + 3] on an
+ * H x W lattice to y, and predicts phi = y * src_rate / decay; it is trained
+ * on targets phi * decay / src_rate with mean squared error and Adam
+ * (0.9, 0.999, 1e-8).  Levels have 32, 48, 64, 96, 128, 192 channels; each is
+ * conv3x3-ReLU-conv3x3-ReLU, joined by 2x2 average pooling; the decoder
+ * convolves [skip, upsample2(deeper)]; a final conv3x3 gives one channel.
+ * Weights are FP32 masters with BF16 copies; activations BF16; every
+ * convolution runs on the tensor cores with FP32 accumulation.
+ *   lbib_nop_workspace_size / lbib_nop_create  up to `batch` tissues of
+ *              H x W (multiples of 32) per call; caller-owned 256-byte
+ *              aligned device workspace; parameters start at zero
+ *   lbib_nop_num_params   parameter count in the canonical flat layout:
+ *              per layer (in order) weights (3, 3, Ci, Co) then bias (Co)
+ *   lbib_nop_layers       layer count and (Ci, Co) pairs of that layout
+ *   lbib_nop_set_params / get_params / get_grads  host FP32 vectors in that
+ *              layout (set also resets the Adam state)
+ *   lbib_nop_forward      phi prediction (d_phi, n*H*W floats) from device
+ *              masks (n*H*W bytes, nonzero = inside) and host per-tissue D,
+ *              decay, src_rate (n doubles each)
+ *   lbib_nop_train_step   forward, loss, backward; with update != 0 also one
+ *              Adam step of learning rate lr; loss_out = the batch loss
+ * Synchronising calls.  Errors as elsewhere; lbib_nop_last_error(). */
+typedef struct lbib_nop lbib_nop;
+int lbib_nop_workspace_size(int32_t batch, int32_t H, int32_t W, uint64_t* bytes_out);
+int lbib_nop_create(int32_t batch, int32_t H, int32_t W, void* d_workspace, uint64_t bytes,
+                    void* cuda_stream, lbib_nop** out);
+int lbib_nop_num_params(const lbib_nop* nop, int64_t* count);
+int lbib_nop_layers(const lbib_nop* nop, int32_t* n_layers, int32_t* ci_co);
+int lbib_nop_set_params(lbib_nop* nop, const float* host, int64_t count);
+int lbib_nop_get_params(lbib_nop* nop, float* host, int64_t count);
+int lbib_nop_get_grads(lbib_nop* nop, float* host, int64_t count);
+int lbib_nop_forward(lbib_nop* nop, int32_t n, const uint8_t* d_mask, const uint8_t* d_src,
+                     const double* D, const double* decay, const double* src_rate, float* d_phi);
+int lbib_nop_train_step(lbib_nop* nop, int32_t n, const uint8_t* d_mask, const uint8_t* d_src,
+                        const double* D, const double* decay, const double* src_rate,
+                        const float* d_phi_target, double lr, int32_t update,
+                        double* loss_out);
+void lbib_nop_destroy(lbib_nop* nop);
+const char* lbib_nop_last_error(const lbib_nop* nop);
+
+/* Single layers of the network (device pointers, asynchronous on the stream):
+ *   lbib_nn_conv3x3        out = conv3x3(in) + bias (ReLU if relu), zero
+ *                          padding; input = [in1 (N,H,W,C1), upsample2(in2)
+ *                          (N,H/2,W/2,C2)] concatenated on channels (C2 may be
+ *                          0); BF16 NHWC in, weights d_wf BF16 (9, Co, C1+C2),
+ *                          bias FP32 (Co) or NULL, out BF16 or FP32 (out_f32)
+ *                          (N,H,W,Co); C1, C2 multiples of 16, Co even
+ *   lbib_nn_conv3x3_wgrad  d_dw (9, C1+C2, Co) += sum over pixels of
+ *                          in(shifted) x d_g, d_db (Co) += sum of d_g (FP32,
+ *                          accumulated: zero them first); Co multiple of 8
+ *   lbib_nn_weight_copies  from FP32 (3,3,Ci,Co) weights the BF16 forward
+ *                          copy (9, Cop, Cip) and the tap-flipped data-gradient
+ *                          copy (9, Cip, Cop), zero padded to Cip, Cop */
+int lbib_nn_conv3x3(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
+                    const void* d_in1, const void* d_in2, const void* d_wf, const float* d_bias,
+                    void* d_out, int32_t relu, int32_t out_f32, void* cuda_stream);
+int lbib_nn_conv3x3_wgrad(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
+                          const void* d_in1, const void* d_in2, const void* d_g, float* d_dw,
+                          float* d_db, void* cuda_stream);
+int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, const float* d_w,
+                          void* d_wf, void* d_wd, void* cuda_stream);
+
 /* Coupled steps without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory while
  * they run -- code inside a framework whose memory pool owns the device,

@@ -1,0 +1,59 @@
+// nn.cuh -- argument structs and kernel declarations of the neural-operator
+// layers (defined in nn.cu, launched by nop.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+namespace lbib {
+namespace nn {
+
+struct ConvArgs {
+    const __nv_bfloat16* in1;  // (N, H, W, C1)
+    const __nv_bfloat16* in2;  // (N, H/2, W/2, C2) read upsampled, or NULL
+    const __nv_bfloat16* w;    // (9, Co, Ci): tap, output channel, input channel
+    const float* bias;         // (Co) or NULL
+    void* out;                 // (N, H, W, Co) bf16, or fp32 when out_f32
+    int N, H, W, C1, C2, Co;
+    int relu, out_f32;
+};
+
+struct WgradArgs {
+    const __nv_bfloat16* in1;
+    const __nv_bfloat16* in2;
+    const __nv_bfloat16* g;  // (N, H, W, Co)
+    float* dw;               // (9, Ci, Co) FP32, accumulated
+    float* db;               // (Co) FP32, accumulated, or NULL
+    int N, H, W, C1, C2, Co;
+    int tiles_per_cta;
+};
+
+constexpr int kTH = 8, kTW = 16;  // pixel tile of a CTA
+constexpr int kConvSmem = (10 * 18 * 40 + 9 * 64 * 40) * 2;
+constexpr int kWgSmem = 10 * 18 * 40 * 2 + 128 * 72 * 2;
+
+__global__ void conv3x3_fwd_kernel(ConvArgs a);
+__global__ void conv3x3_wgrad_kernel(WgradArgs a);
+__global__ void avgpool2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int N, int H, int W,
+                                int C);
+__global__ void avgpool2_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gx, int N, int H,
+                                    int W, int C);
+__global__ void relu_bwd_kernel(__nv_bfloat16* g, const __nv_bfloat16* act, int64_t n);
+__global__ void concat_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gskip,
+                                  __nv_bfloat16* gx2, int N, int H, int W, int C1, int C2,
+                                  int accumulate_skip);
+__global__ void add_kernel(__nv_bfloat16* g, const __nv_bfloat16* h, int64_t n);
+__global__ void mse_kernel(const float* y, int Cy, const float* t, __nv_bfloat16* dy, int Cdy,
+                           int64_t n, double* loss);
+__global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr,
+                            float b1, float b2, float eps, float c1, float c2);
+__global__ void weight_copies_kernel(const float* w, int Ci, int Co, int Cip, int Cop,
+                                     __nv_bfloat16* wf, __nv_bfloat16* wd);
+__global__ void features_kernel(const uint8_t* id_mask, const uint8_t* src, const float* Dn,
+                                const float* Kn, __nv_bfloat16* x, int N, int HW);
+__global__ void scale_kernel(const float* in, int Cin, float* out, const float* fac, int N,
+                             int HW);
+
+}  // namespace nn
+}  // namespace lbib

@@ -45,6 +45,10 @@ EXPORTS = (
     "lbib_ensemble_workspace_size", "lbib_ensemble_create", "lbib_ensemble_tissue",
     "lbib_ensemble_step", "lbib_ensemble_status", "lbib_ensemble_config", "lbib_ensemble_tune",
     "lbib_ensemble_selftest_timeout", "lbib_ensemble_destroy", "lbib_ensemble_last_error",
+    "lbib_nop_workspace_size", "lbib_nop_create", "lbib_nop_num_params", "lbib_nop_layers",
+    "lbib_nop_set_params", "lbib_nop_get_params", "lbib_nop_get_grads", "lbib_nop_forward",
+    "lbib_nop_train_step", "lbib_nop_destroy", "lbib_nop_last_error", "lbib_nn_conv3x3",
+    "lbib_nn_conv3x3_wgrad", "lbib_nn_weight_copies",
 )
 
 
@@ -107,6 +111,21 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_ensemble_selftest_timeout": (ctypes.c_int, [vp, vp]),
         "lbib_ensemble_destroy": (None, [vp]),
         "lbib_ensemble_last_error": (ctypes.c_char_p, [vp]),
+        "lbib_nop_workspace_size": (ctypes.c_int, [i32, i32, i32, ctypes.POINTER(u64)]),
+        "lbib_nop_create": (ctypes.c_int, [i32, i32, i32, vp, u64, vp, ctypes.POINTER(vp)]),
+        "lbib_nop_num_params": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64)]),
+        "lbib_nop_layers": (ctypes.c_int, [vp, ctypes.POINTER(i32), vp]),
+        "lbib_nop_set_params": (ctypes.c_int, [vp, vp, ctypes.c_int64]),
+        "lbib_nop_get_params": (ctypes.c_int, [vp, vp, ctypes.c_int64]),
+        "lbib_nop_get_grads": (ctypes.c_int, [vp, vp, ctypes.c_int64]),
+        "lbib_nop_forward": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
+        "lbib_nop_train_step": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp, ctypes.c_double,
+                                               i32, ctypes.POINTER(ctypes.c_double)]),
+        "lbib_nop_destroy": (None, [vp]),
+        "lbib_nop_last_error": (ctypes.c_char_p, [vp]),
+        "lbib_nn_conv3x3": (ctypes.c_int, [i32] * 6 + [vp] * 5 + [i32, i32, vp]),
+        "lbib_nn_conv3x3_wgrad": (ctypes.c_int, [i32] * 6 + [vp] * 5 + [vp]),
+        "lbib_nn_weight_copies": (ctypes.c_int, [i32] * 4 + [vp] * 4),
         "lbib_destroy": (None, [vp]),
         "lbib_last_error": (ctypes.c_char_p, [vp]),
         "lbib_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -528,6 +547,106 @@ class Ensemble:
         if getattr(self, "ens", None):
             load().lbib_ensemble_destroy(self.ens)
             self.ens = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- neural operator
+def _nop_check(rc, h):
+    if rc != LBIB_OK:
+        raise LbibError(rc, load().lbib_nop_last_error(h).decode(errors="replace"))
+
+
+class NeuralOperator:
+    """The U-Net warm start (include/lbib.h, neural operator section) on a
+    torch-owned workspace."""
+
+    def __init__(self, batch: int, H: int = 256, W: int = 256, device=None, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("lbib needs a CUDA device; there is no CPU path")
+        L = load()
+        self.device = torch.device(device or "cuda")
+        self.B, self.H, self.W = batch, H, W
+        nb = ctypes.c_uint64(0)
+        _nop_check(L.lbib_nop_workspace_size(batch, H, W, ctypes.byref(nb)), None)
+        self.nbytes = int(nb.value)
+        self.workspace = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p(0)
+        _nop_check(L.lbib_nop_create(batch, H, W, ctypes.c_void_p(self.workspace.data_ptr()),
+                                     self.nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                     ctypes.byref(h)), None)
+        self.h = h.value
+        n = ctypes.c_int64(0)
+        _nop_check(L.lbib_nop_num_params(self.h, ctypes.byref(n)), self.h)
+        self.n_params = int(n.value)
+
+    def layers(self):
+        L = load()
+        n = ctypes.c_int32(0)
+        _nop_check(L.lbib_nop_layers(self.h, ctypes.byref(n), None), self.h)
+        cc = np.zeros(2 * n.value, np.int32)
+        _nop_check(L.lbib_nop_layers(self.h, ctypes.byref(n), cc.ctypes.data_as(ctypes.c_void_p)),
+                   self.h)
+        return [(int(cc[2 * i]), int(cc[2 * i + 1])) for i in range(n.value)]
+
+    def set_params(self, p):
+        a = np.ascontiguousarray(p, np.float32)
+        _nop_check(load().lbib_nop_set_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size),
+                   self.h)
+
+    def get_params(self):
+        a = np.empty(self.n_params, np.float32)
+        _nop_check(load().lbib_nop_get_params(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size),
+                   self.h)
+        return a
+
+    def get_grads(self):
+        a = np.empty(self.n_params, np.float32)
+        _nop_check(load().lbib_nop_get_grads(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size),
+                   self.h)
+        return a
+
+    def forward(self, mask, src, D, decay, src_rate, out=None):
+        """mask, src: (n, H, W) uint8 CUDA tensors; returns phi (n, H, W) float32."""
+        import torch
+        n = mask.shape[0]
+        if out is None:
+            out = torch.empty((n, self.H, self.W), dtype=torch.float32, device=mask.device)
+        _, Dp = _p(D, np.float64)
+        _, kp = _p(decay, np.float64)
+        _, sp = _p(src_rate, np.float64)
+        keep = (_, Dp, kp, sp)
+        _nop_check(load().lbib_nop_forward(self.h, n, ctypes.c_void_p(mask.data_ptr()),
+                                           ctypes.c_void_p(src.data_ptr()), Dp, kp, sp,
+                                           ctypes.c_void_p(out.data_ptr())), self.h)
+        del keep
+        return out
+
+    def train_step(self, mask, src, D, decay, src_rate, phi, lr=1e-3, update=True):
+        n = mask.shape[0]
+        Da = np.ascontiguousarray(D, np.float64)
+        ka = np.ascontiguousarray(decay, np.float64)
+        sa = np.ascontiguousarray(src_rate, np.float64)
+        loss = ctypes.c_double(0.0)
+        vp = ctypes.c_void_p
+        _nop_check(load().lbib_nop_train_step(self.h, n, vp(mask.data_ptr()), vp(src.data_ptr()),
+                                              Da.ctypes.data_as(vp), ka.ctypes.data_as(vp),
+                                              sa.ctypes.data_as(vp), vp(phi.data_ptr()),
+                                              float(lr), 1 if update else 0,
+                                              ctypes.byref(loss)), self.h)
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().lbib_nop_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:
