@@ -280,9 +280,94 @@ def run_ensemble(args, rank, world, dist):
     }
 
 
+def warm_start_sample(args, dev):
+    """The second half of the metric at a bounded size: train the neural
+    operator on --ws-train cold-solved 256^2 tissues for --ws-epochs epochs and
+    compare warm vs cold time to r <= 1e-6 on --ws-test held-out seeds.  The
+    full-size run (20k pairs, 1k seeds) is --workload c5."""
+    import torch
+    from paper_1503_06726_gb300 import lbib, warmstart as wsm
+    H = 256
+    t0 = time.perf_counter()
+    data = wsm.make_dataset([li.steady_tissue(s, n=H) for s in range(5, 5 + args.ws_train)],
+                            H, H, batch=256)
+    net = lbib.NeuralOperator(16, H, H, device=dev)
+    layers = net.layers()
+    shapes = [(f"layer{i}", ci, co) for i, (ci, co) in enumerate(layers[:-1])]
+    shapes.append(("out",) + tuple(layers[-1]))
+    net.set_params(li.nop_init_params(5, shapes))
+    losses = wsm.train(net, data, epochs=args.ws_epochs, batch=16, lr=1e-3, lr_end=5e-5)
+    del data
+    rows = wsm.evaluate(net, [li.steady_tissue(s, n=H) for s in range(1000, 1000 + args.ws_test)],
+                        H, H)
+    net.close()
+    torch.cuda.synchronize()
+    summ = wsm.summarize(rows)
+    summ.update({"train_pairs": args.ws_train, "epochs": args.ws_epochs,
+                 "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+                 "seconds": time.perf_counter() - t0,
+                 "note": "bounded sample; --workload c5 is the full 20k-pair / 1k-seed run"})
+    return summ
+
+
+def run_warmstart(args, rank, world, dist):
+    """256^2 steady morphogen solves: the neural operator is trained on pairs
+    the LB solver generates (cold solves of --c5-train random tissues), then
+    on --c5-test held-out seeds each tissue is solved to r <= 1e-6 from a cold
+    start and from the network's prediction (inference included)."""
+    import torch
+    from paper_1503_06726_gb300 import lbib, warmstart as wsm
+
+    lbib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    H = 256
+    t0 = time.perf_counter()
+    train_items = [li.steady_tissue(s, n=H) for s in range(5, 5 + args.c5_train)]
+    data = wsm.make_dataset(train_items, H, H, batch=256)
+    t_data = time.perf_counter() - t0
+    net = lbib.NeuralOperator(args.c5_batch, H, H, device=dev)
+    layers = net.layers()
+    shapes = [(f"layer{i}", ci, co) for i, (ci, co) in enumerate(layers[:-1])]
+    shapes.append(("out",) + tuple(layers[-1]))
+    net.set_params(li.nop_init_params(5, shapes))
+    n_params = net.n_params
+    t0 = time.perf_counter()
+    losses = wsm.train(net, data, epochs=args.c5_epochs, batch=args.c5_batch, lr=1e-3,
+                       lr_end=5e-5)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+    test_items = [li.steady_tissue(s, n=H) for s in range(1000, 1000 + args.c5_test)]
+    rows = wsm.evaluate(net, test_items, H, H)
+    summ = wsm.summarize(rows)
+    n_train_steps = args.c5_epochs * (args.c5_train // args.c5_batch)
+    train_flop = 3 * 9.7e9 * args.c5_batch * n_train_steps
+    net.close()
+    if rank != 0:
+        return None
+    return {
+        "metric": "time-to-steady morphogen (warm vs cold) at resid 1e-6",
+        "value": summ["warm_ms_mean"], "unit": "ms per tissue (warm start, inference included)",
+        "higher_is_better": False, "n_gpus": world, "steps": summ["n"], "warmup": 0,
+        "ms_per_step": summ["warm_ms_mean"], "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 network, f32 relaxation", "data": "synthetic (seeded tissue generator)",
+        "config": {"workload": "c5_warm_start_256x256", "train_pairs": args.c5_train,
+                   "test_seeds": args.c5_test, "epochs": args.c5_epochs,
+                   "batch": args.c5_batch, "params": n_params},
+        "warm_vs_cold": summ,
+        "training": {"data_seconds": t_data, "train_seconds": t_train,
+                     "loss_first_epoch": losses[0], "loss_last_epoch": losses[-1],
+                     "approx_tflops": train_flop / t_train / 1e12},
+        "cpu_baseline": None,
+    }
+
+
 def run_gb300(args, rank, world, dist):
     if args.workload == "c4":
         return run_ensemble(args, rank, world, dist)
+    if args.workload == "c5":
+        return run_warmstart(args, rank, world, dist)
     import torch
     from paper_1503_06726_gb300 import lbib
 
@@ -378,6 +463,9 @@ def run_gb300(args, rank, world, dist):
     # both population buffers (= the algorithmic bytes of one launch) plus the
     # force, velocity and label planes
     ws = alg_bytes + N * (2 * 4 * (2 if prec == "fp64" else 1) * 2 + 4)
+    warm = None
+    if world == 1 and not args.no_warm_start:
+        warm = warm_start_sample(args, dev)
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -394,6 +482,7 @@ def run_gb300(args, rank, world, dist):
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "ib_launch_ms": ib_ms / (n_prof + 1)},
         "e2e": e2e,
+        "warm_start": warm,
         "gpu_launches": 2 * args.steps + 1,
         "clocks": clk,
         "cpu_baseline": cpu,
@@ -434,6 +523,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true")
+    ap.add_argument("--ws-train", type=int, default=2000)
+    ap.add_argument("--ws-epochs", type=int, default=4)
+    ap.add_argument("--ws-test", type=int, default=64)
+    ap.add_argument("--c5-train", type=int, default=20000)
+    ap.add_argument("--c5-test", type=int, default=1000)
+    ap.add_argument("--c5-epochs", type=int, default=8)
+    ap.add_argument("--c5-batch", type=int, default=16)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

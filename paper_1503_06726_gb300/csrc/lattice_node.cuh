@@ -50,7 +50,7 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
 // The update of one node (x, y).  The lane of the calling thread within its
 // warp must match x modulo 32 (the group masks are cleared per warp).
 template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
-__device__ __forceinline__ void lattice_node(const LatticeArgs& a, const Coefs<C>& k, int x,
+__device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C>& k, int x,
                                              int y) {
     using St = Store<T, C>;
     using V2 = typename Vec2<C>::T;
