@@ -99,11 +99,20 @@ __device__ __forceinline__ int find_tissue(const int* pfx, int n, int item) {
 }
 
 template <int S, int FORCING>
-__global__ void __launch_bounds__(kIBThreads) ensemble_kernel(EnsArgs e) {
+__global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
     __shared__ IBSmem32 sm;
     __shared__ TissueDev td;
     __shared__ int s_t;
     const int tid = threadIdx.x;
+    IBShared32 view;
+    view.sx = sm.sx;
+    view.sb = sm.sb;
+    view.sf = sm.sf;
+    view.rowcnt = sm.rowcnt;
+    view.thr = sm.thr;
+    view.sbox = sm.sbox;
+    view.s_flag = &sm.s_flag;
+    view.maxv = kMaxVertsPerCell;
     if (tid == 0) s_t = -1;
 
     auto load_tissue = [&](int t) {
@@ -126,7 +135,7 @@ __global__ void __launch_bounds__(kIBThreads) ensemble_kernel(EnsArgs e) {
             a.do_move = move;
             a.do_prep = prep;
             a.write_vforce = vforce;
-            ib_cell_f32(a, item - e.cell_pfx[t], sm);
+            ib_cell_f32<kIBThreads>(a, item - e.cell_pfx[t], view);
         }
     };
 

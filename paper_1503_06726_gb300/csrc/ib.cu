@@ -202,17 +202,38 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
 }
 
 
-__global__ void __launch_bounds__(kIBThreads) ib_cell_kernel_f32(IBArgs a) {
-    __shared__ IBSmem32 S;
-    ib_cell_f32(a, blockIdx.x, S);
+// FP32 path: dynamic shared memory sized for the largest cell, NT threads
+template <int NT>
+__global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
+    extern __shared__ __align__(16) unsigned char ib_smem[];
+    IBShared32 S;
+    int* fixed = reinterpret_cast<int*>(ib_smem);
+    S.rowcnt = fixed;
+    S.thr = fixed + kMaxRows;
+    S.sbox = S.thr + kMaxRows * kMaxCross;
+    S.s_flag = S.sbox + 4;
+    S.sx = reinterpret_cast<double2*>(ib_smem + kIBSmemFixed);
+    S.sb = reinterpret_cast<int2*>(S.sx + maxv);
+    S.sf = reinterpret_cast<float2*>(S.sb + maxv);
+    S.maxv = maxv;
+    ib_cell_f32<NT>(a, blockIdx.x, S);
 }
 
-cudaError_t launch_ib(int precision, const IBArgs& a, cudaStream_t s) {
+cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s) {
     if (a.n_cells <= 0) return cudaSuccess;
-    if (precision == LBIB_FP64)
+    if (precision == LBIB_FP64) {
         ib_cell_kernel<double><<<a.n_cells, kIBThreads, 0, s>>>(a);
-    else
-        ib_cell_kernel_f32<<<a.n_cells, kIBThreads, 0, s>>>(a);
+    } else {
+        // small, numerous cells: 128-thread CTAs and shared memory sized to
+        // the largest cell let many more CTAs be resident per SM
+        int maxv = maxv_cell < 3 ? 3 : (maxv_cell > kMaxVertsPerCell ? kMaxVertsPerCell : maxv_cell);
+        maxv = (maxv + 7) / 8 * 8;
+        const size_t smem = kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
+        if (maxv <= 128 && a.n_cells >= 2048)
+            ib_cell_kernel_f32<128><<<a.n_cells, 128, smem, s>>>(a, maxv);
+        else
+            ib_cell_kernel_f32<256><<<a.n_cells, 256, smem, s>>>(a, maxv);
+    }
     return cudaGetLastError();
 }
 

@@ -10,7 +10,7 @@
 namespace lbib {
 
 
-constexpr int kIBThreads = 256;
+constexpr int kIBThreads = 256;  // CTA of the FP64 path and the persistent ensemble
 static_assert(kIBThreads >= kMaxRows, "row counters are cleared one per thread");
 
 __device__ __forceinline__ int wrapi(int a, int n) {
@@ -117,6 +117,20 @@ __device__ __forceinline__ void mark_node_warp(uint32_t* mask, int64_t node) {
     if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(mask + w, bits);
 }
 
+// Mark the groups of the nodes [s, e) of one row (no wrap inside the range)
+// in `mask`: lanes take one 32-group word each.
+__device__ __forceinline__ void mark_range(uint32_t* mask, int64_t rowbase, int s, int e,
+                                           int lane) {
+    if (!mask || e <= s) return;
+    const int64_t ga = (rowbase + s) >> 2, gb = (rowbase + e - 1) >> 2;
+    for (int64_t w = (ga >> 5) + lane; w <= (gb >> 5); w += 32) {
+        const unsigned lo = (w == (ga >> 5)) ? (unsigned)(ga & 31) : 0u;
+        const unsigned hi = (w == (gb >> 5)) ? (unsigned)(gb & 31) : 31u;
+        const uint32_t bits = ((2u << hi) - 1u) & ~((1u << lo) - 1u);
+        atomicOr(mask + w, bits);
+    }
+}
+
 // Labels of one cell (phase 3 of the IB kernels).  With scan_ok the per-row
 // thresholds in thr/rowcnt are complete: one warp per row sorts them and
 // fills each span [t_{2k}, t_{2k+1}) -- the nodes with an odd number of
@@ -126,7 +140,7 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
                                          const int* rowcnt, int* thr, bool scan_ok, int I0,
                                          int J0, int rows, int cols) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int nwarps = kIBThreads / 32;
+    const int nwarps = blockDim.x >> 5;
     uint32_t* id = a.id;
     const uint32_t code = ((uint32_t)c << 4) | (uint32_t)(a.srcf[c] & 0xF);
     const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
@@ -161,7 +175,18 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
                         int wI = wI0 + (I - I0);
                         if (wI >= a.nx) wI -= a.nx;
                         atomicMin(rowp + wI, code);
-                        mark_node_warp(a.lmask, (int64_t)wJ * a.pitch + wI);
+                    }
+                    if (hi > lo) {  // the span's groups, split where it wraps
+                        int ws = wI0 + (lo - I0);
+                        if (ws >= a.nx) ws -= a.nx;
+                        const int len = hi - lo;
+                        const int64_t rb = (int64_t)wJ * a.pitch;
+                        if (ws + len <= a.nx) {
+                            mark_range(a.lmask, rb, ws, ws + len, lane);
+                        } else {
+                            mark_range(a.lmask, rb, ws, a.nx, lane);
+                            mark_range(a.lmask, rb, 0, ws + len - a.nx, lane);
+                        }
                     }
                 }
             } else {  // odd count: evaluate the parity rule node by node
@@ -185,7 +210,7 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
     } else {
         // brute force: the same predicate per node over all edges
         if (tid == 0) raise_flag(a.diag, kDiagRasterSlow);
-        for (int e = tid; e < rows * cols; e += kIBThreads) {
+        for (int e = tid; e < rows * cols; e += blockDim.x) {
             const int r = e / cols, cc = e % cols, J = J0 + r;
             if (a.bc_y && (J < 0 || J >= a.ny)) continue;
             const double xn = (double)(I0 + cc), yn = (double)J;
@@ -253,27 +278,54 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
     return make_float2(sc * d.x, sc * d.y);
 }
 
-// The work of one cell by one CTA of kIBThreads threads.  Callers that run
-// several cells through the same CTA call it again for the next cell; the
-// first barrier protects the shared arrays of the previous call.
-static __device__ void ib_cell_f32(const IBArgs& a, int c, IBSmem32& S) {
+// The work of one cell by one CTA of NT threads.  Callers that run several
+// cells through the same CTA call it again for the next cell; the first
+// barrier protects the shared arrays of the previous call.
+template <int NT>
+static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) {
+    static_assert(NT >= kMaxRows && NT % 64 == 0, "CTA size");
+    constexpr int kIBThreads = NT;
     double2* sx = S.sx;
     int2* sb = S.sb;
     float2* sf = S.sf;
     int* rowcnt = S.rowcnt;
     int* thr = S.thr;
     int* sbox = S.sbox;
-    int& s_flag = S.s_flag;
+    int& s_flag = *S.s_flag;
     __syncthreads();
 
     const int v0 = a.off[c];
     const int n = a.off[c + 1] - v0;
     const int tid = threadIdx.x, lane = tid & 31;
+    if (n > S.maxv) {  // cannot happen for callers that size maxv from the cells
+        if (tid == 0) raise_flag(a.diag, kDiagGeometry);
+        return;
+    }
 
     if (tid < kMaxRows) rowcnt[tid] = 0;
     if (tid == 0) {
         sbox[0] = INT_MAX; sbox[1] = INT_MIN; sbox[2] = INT_MAX; sbox[3] = INT_MIN;
         s_flag = 0;
+    }
+
+    // spring data of the vertices this thread will handle in phase 2 (the
+    // first half of the CTA), loaded now so that phase 2 waits on no load
+    constexpr int half = kIBThreads / 2;
+    float pL0[2] = {0.f, 0.f}, pk[2] = {0.f, 0.f}, pL0p[2] = {0.f, 0.f}, pkp[2] = {0.f, 0.f};
+    float ppres = 0.f;
+    if (a.do_prep && a.do_force && tid < half) {
+        ppres = (float)a.pres[c];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int t = tid + r * half;
+            if (t < n) {
+                const int tp = (t == 0) ? n - 1 : t - 1;
+                pL0[r] = (float)a.L0[v0 + t];
+                pk[r] = (float)a.k[v0 + t];
+                pL0p[r] = (float)a.L0[v0 + tp];
+                pkp[r] = (float)a.k[v0 + tp];
+            }
+        }
     }
 
     // ---- (1) interpolate u^n at X^n and move; (base, frac) of the new X
@@ -365,21 +417,25 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, IBSmem32& S) {
     const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
     const bool scan = labels && rows <= kMaxRows;
 
-    constexpr int half = kIBThreads / 2;
     if (tid < half) {
         if (a.do_force) {
             float2* force = static_cast<float2*>(a.force);
-            const float p = (float)a.pres[c];
+            const float p = ppres;
             const float ten = (float)a.tension;
-            for (int t = tid; t < n; t += half) {
+            for (int t = tid, r = 0; t < n; t += half, ++r) {
                 const int tp = (t == 0) ? n - 1 : t - 1;
                 const int tn = (t == n - 1) ? 0 : t + 1;
                 const int2 b = sb[t];
                 const float2 f = sf[t];
                 const float2 dn = edge_vec(b, f, sb[tn], sf[tn]);   // X_{t+1} - X_t
                 const float2 dp = edge_vec(sb[tp], sf[tp], b, f);   // X_t - X_{t-1}
-                const float2 s0 = spring32(dn, (float)a.L0[v0 + t], (float)a.k[v0 + t]);
-                const float2 s1 = spring32(dp, (float)a.L0[v0 + tp], (float)a.k[v0 + tp]);
+                // prefetched for the first two vertices of this thread
+                const float L0t = r == 0 ? pL0[0] : (r == 1 ? pL0[1] : (float)a.L0[v0 + t]);
+                const float kt = r == 0 ? pk[0] : (r == 1 ? pk[1] : (float)a.k[v0 + t]);
+                const float L0p = r == 0 ? pL0p[0] : (r == 1 ? pL0p[1] : (float)a.L0[v0 + tp]);
+                const float kp = r == 0 ? pkp[0] : (r == 1 ? pkp[1] : (float)a.k[v0 + tp]);
+                const float2 s0 = spring32(dn, L0t, kt);
+                const float2 s1 = spring32(dp, L0p, kp);
                 float Fx = s0.x - s1.x, Fy = s0.y - s1.y;
                 // pressure p dA/dX: (p/2)(y_{t+1} - y_{t-1}, x_{t-1} - x_{t+1})
                 Fx += 0.5f * p * (dn.y + dp.y);

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k)
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    lattice_node<T, C, S, WALLS, FORCING, SCALED>(a, k, x, y);
+    LBIB_LATTICE_NODE_BODY
 }
 
 template <typename T, typename C, int S, bool WALLS, int FORCING>

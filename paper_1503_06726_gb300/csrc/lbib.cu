@@ -11,6 +11,7 @@
 // Between two steps the move of step n and the prep of step n+1 are one
 // launch, so a step costs two launches.  A chunk of two steps (one full A/B
 // buffer cycle) is captured once into a CUDA graph and replayed.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -219,7 +220,7 @@ static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out) {
 
 static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool vforce) {
     if (c->nC == 0) return cudaSuccess;
-    return launch_ib(c->p.precision, ib_args(c, move, prep, vforce), c->stream);
+    return launch_ib(c->p.precision, ib_args(c, move, prep, vforce), c->maxv_cell, c->stream);
 }
 
 static void drop_graphs(lbib_ctx* c) {
@@ -402,6 +403,9 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_cells");
     c->nV = V;
     c->nC = n_cells;
+    c->maxv_cell = 0;
+    for (int ci = 0; ci < n_cells; ++ci)
+        c->maxv_cell = std::max(c->maxv_cell, cell_off[ci + 1] - cell_off[ci]);
     c->vforce_valid = false;
     drop_graphs(c);
     return LBIB_OK;
@@ -692,6 +696,12 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_state");
     c->nV = hdr[0];
     c->nC = hdr[1];
+    {   // the largest cell, from the cell offsets of the state
+        const int32_t* off = reinterpret_cast<const int32_t*>(
+            h + 16 + 9 * P + (uint64_t)5 * c->p.n_species * P + (uint64_t)c->maxV * 32);
+        c->maxv_cell = 0;
+        for (int ci = 0; ci < c->nC; ++ci) c->maxv_cell = std::max(c->maxv_cell, off[ci + 1] - off[ci]);
+    }
     c->fields_valid = false;
     c->vforce_valid = false;
     drop_graphs(c);

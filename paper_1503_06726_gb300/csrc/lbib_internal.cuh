@@ -117,7 +117,24 @@ struct IBArgs {
     uint32_t* lmask;    // optional: mark the groups that receive labels
 };
 
-// shared memory of the FP32 per-cell IB work (one CTA per cell)
+// shared memory of the FP32 per-cell IB work (one CTA per cell), as pointers
+// into the CTA's shared memory; the vertex arrays hold `maxv` entries
+struct IBShared32 {
+    double2* sx;  // FP64 positions (exact fallbacks)
+    int2* sb;     // floor(X)
+    float2* sf;   // X - floor(X)
+    int* rowcnt;  // kMaxRows
+    int* thr;     // kMaxRows * kMaxCross
+    int* sbox;    // 4
+    int* s_flag;  // 1
+    int maxv;
+};
+
+// fixed part of the FP32 IB kernel's dynamic shared memory (bytes, 16-aligned)
+constexpr int kIBSmemFixed = ((kMaxRows + kMaxRows * kMaxCross + 4 + 1) * 4 + 15) / 16 * 16;
+constexpr int kIBSmemPerVertex = 16 + 8 + 8;
+
+// a static shared-memory block for the largest cells (the persistent kernel)
 struct IBSmem32 {
     double2 sx[kMaxVertsPerCell];  // FP64 positions (exact fallbacks)
     int2 sb[kMaxVertsPerCell];     // floor(X)
@@ -140,7 +157,8 @@ int set_thread_error(int code, const std::string& msg);
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
                            const LatticeArgs& a, const void* coefs, dim3 block,
                            cudaStream_t s);
-cudaError_t launch_ib(int precision, const IBArgs& a, cudaStream_t s);
+// maxv_cell: the largest vertex count of a cell (sizes shared memory and the CTA)
+cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s);
 cudaError_t launch_areas(const double2* xy, const int32_t* off, int n_cells, double* area,
                          cudaStream_t s);
 cudaError_t launch_init_populations(int precision, int n_species, int nx, int ny,
@@ -162,6 +180,7 @@ struct lbib_ctx {
     lbib::Layout L;
     int cur = 0;           // buffer holding the current post-collision populations
     int nV = 0, nC = 0;
+    int maxv_cell = 0;     // largest vertex count of a cell
     bool fields_valid = false;
     bool vforce_valid = false;
     lbib::Coefs<double> kd;

@@ -146,7 +146,7 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     if (e == cudaSuccess && n_cells > 0) {
         ia.do_move = 0;
         ia.do_prep = 1;
-        e = launch_ib(params->precision, ia, st);
+        e = launch_ib(params->precision, ia, kMaxVertsPerCell, st);
     }
     for (int left = n_steps; left > 0 && e == cudaSuccess; --left) {
         la.fsrc = fbuf[cur];
@@ -158,7 +158,7 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
         if (e == cudaSuccess && n_cells > 0) {
             ia.do_move = 1;
             ia.do_prep = left > 1 ? 1 : 0;
-            e = launch_ib(params->precision, ia, st);
+            e = launch_ib(params->precision, ia, kMaxVertsPerCell, st);
         }
         cur = 1 - cur;
     }

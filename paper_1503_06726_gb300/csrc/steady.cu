@@ -204,7 +204,7 @@ int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
         a.do_prep = 1;
         a.do_mask = 1;
         a.do_force = 0;
-        e = launch_ib(LBIB_FP32, a, st);
+        e = launch_ib(LBIB_FP32, a, kMaxVertsPerCell, st);
     }
     if (e == cudaSuccess) {
         labels_to_ids<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
