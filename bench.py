@@ -19,6 +19,12 @@ Printed JSON line (rank 0):
               cell areas back to pinned host memory;
   cpu_baseline the FP64 oracle on the host cores on a bounded sample.
 
+Other workloads (--workload): c3-fp32, c3-fp16, c3-fp64 (the 4096^2
+periodic tissue of 9,801 cells with FP32 / FP16-shifted / FP64 storage);
+c3-precision (that tissue with all three storages, errors against FP64);
+c4 (64 independent tissues in one persistent launch); c5 (the learned warm
+start of the steady morphogen solve, warm vs cold).
+
 --impl reference times the FP64 oracle (the reference arm of this build)
 on the same workload and metric.
 """
@@ -363,7 +369,76 @@ def run_warmstart(args, rank, world, dist):
     }
 
 
+def run_precision(args, rank, world, dist):
+    """The 4096^2 precision sweep: the same tissue advanced --prec-steps
+    steps with FP64, FP32 and FP16-shifted population storage; velocity,
+    concentration and vertex errors of the FP32/FP16 runs against the FP64
+    run (the FP64 GPU path matches the FP64 oracle to 1e-10), and the per-cell
+    area drift of every run."""
+    import torch
+    from paper_1503_06726_gb300 import lbib
+
+    lbib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = li.config3()
+    p, T = w.params, w.tissue
+    n = args.prec_steps
+    which = lbib.LBIB_U | lbib.LBIB_PHI | lbib.LBIB_X | lbib.LBIB_AREA
+    res, secs = {}, {}
+    area0 = None
+    for name, prec in (("fp64", lbib.LBIB_FP64), ("fp32", lbib.LBIB_FP32),
+                       ("fp16", lbib.LBIB_FP16)):
+        sim = lbib.Simulation(p, prec, T.n_vertices, T.n_cells, device=dev)
+        sim.set_cells(T)
+        if area0 is None:
+            area0 = sim.fields(lbib.LBIB_AREA)["area"]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(n)
+        torch.cuda.synchronize()
+        secs[name] = time.perf_counter() - t0
+        res[name] = sim.fields(which)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+    ref = res["fp64"]
+    umax = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
+    pmax = np.abs(ref["phi"]).max()
+
+    def errs(r):
+        du = max(np.abs(r["ux"] - ref["ux"]).max(), np.abs(r["uy"] - ref["uy"]).max())
+        return {"u_rel_linf": float(du / umax),
+                "phi_rel_linf": float(np.abs(r["phi"] - ref["phi"]).max() / pmax),
+                "x_abs_linf_lu": float(np.abs(r["xy"] - ref["xy"]).max()),
+                "area_rel_linf_vs_fp64": float(np.abs(r["area"] - ref["area"]).max() /
+                                               np.abs(ref["area"]).max())}
+
+    def drift(r):
+        d = (r["area"] - area0) / area0
+        return {"mean": float(d.mean()), "max_abs": float(np.abs(d).max())}
+
+    if rank != 0:
+        return None
+    return {
+        "metric": "precision-path error vs FP64 storage after the stated steps",
+        "value": errs(res["fp32"])["u_rel_linf"], "unit": "relative L-inf of u (FP32 storage)",
+        "higher_is_better": False, "n_gpus": world, "steps": n, "warmup": 0,
+        "ms_per_step": secs["fp32"] * 1e3 / n, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 arithmetic; f64/f32/f16-shifted storage",
+        "data": "synthetic (seeded tissue generator)",
+        "config": workload_config(w, "fp64/fp32/fp16"),
+        "errors_vs_fp64": {"fp32": errs(res["fp32"]), "fp16": errs(res["fp16"])},
+        "area_drift": {k: drift(v) for k, v in res.items()},
+        "field_scale": {"u_max": float(umax), "phi_max": float(pmax)},
+        "seconds": secs,
+        "cpu_baseline": None,
+    }
+
+
 def run_gb300(args, rank, world, dist):
+    if args.workload == "c3-precision":
+        return run_precision(args, rank, world, dist)
     if args.workload == "c4":
         return run_ensemble(args, rank, world, dist)
     if args.workload == "c5":
@@ -531,6 +606,7 @@ def main():
     ap.add_argument("--c5-test", type=int, default=1000)
     ap.add_argument("--c5-epochs", type=int, default=8)
     ap.add_argument("--c5-batch", type=int, default=16)
+    ap.add_argument("--prec-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

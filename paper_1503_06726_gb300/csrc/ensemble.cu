@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
             a.do_move = move;
             a.do_prep = prep;
             a.write_vforce = vforce;
-            ib_cell_f32<kIBThreads>(a, item - e.cell_pfx[t], view);
+            ib_cell_f32<kIBThreads, false>(a, item - e.cell_pfx[t], view);
         }
     };
 

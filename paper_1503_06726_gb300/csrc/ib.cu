@@ -37,10 +37,14 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
     __shared__ int s_flag;   // 1: a scanline row overflowed, 2: geometry not finite
 
     const int c = blockIdx.x;
-    const int v0 = a.off[c];
-    const int n = a.off[c + 1] - v0;
+    const int v0 = __ldcg(a.off + c);
+    const int n = __ldcg(a.off + c + 1) - v0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int nwarps = kIBThreads / 32;
+    // everything below reads the u plane of the lattice launch just before
+    // (programmatic launch) or writes what it reads
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (tid < kMaxRows) rowcnt[tid] = 0;
     if (tid == 0) {
@@ -216,25 +220,24 @@ __global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
     S.sb = reinterpret_cast<int2*>(S.sx + maxv);
     S.sf = reinterpret_cast<float2*>(S.sb + maxv);
     S.maxv = maxv;
-    ib_cell_f32<NT>(a, blockIdx.x, S);
+    ib_cell_f32<NT, true>(a, blockIdx.x, S);
 }
 
-cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s) {
+cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s, bool pdl) {
     if (a.n_cells <= 0) return cudaSuccess;
-    if (precision == LBIB_FP64) {
-        ib_cell_kernel<double><<<a.n_cells, kIBThreads, 0, s>>>(a);
-    } else {
-        // small, numerous cells: 128-thread CTAs and shared memory sized to
-        // the largest cell let many more CTAs be resident per SM
-        int maxv = maxv_cell < 3 ? 3 : (maxv_cell > kMaxVertsPerCell ? kMaxVertsPerCell : maxv_cell);
-        maxv = (maxv + 7) / 8 * 8;
-        const size_t smem = kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
-        if (maxv <= 128 && a.n_cells >= 2048)
-            ib_cell_kernel_f32<128><<<a.n_cells, 128, smem, s>>>(a, maxv);
-        else
-            ib_cell_kernel_f32<256><<<a.n_cells, 256, smem, s>>>(a, maxv);
-    }
-    return cudaGetLastError();
+    if (precision == LBIB_FP64)
+        return launch_kernel(ib_cell_kernel<double>, dim3(a.n_cells), dim3(kIBThreads), 0, s, pdl,
+                             a);
+    // small, numerous cells: 128-thread CTAs and shared memory sized to the
+    // largest cell let many more CTAs be resident per SM
+    int maxv = maxv_cell < 3 ? 3 : (maxv_cell > kMaxVertsPerCell ? kMaxVertsPerCell : maxv_cell);
+    maxv = (maxv + 7) / 8 * 8;
+    const size_t smem = kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
+    if (maxv <= 128 && a.n_cells >= 2048)
+        return launch_kernel(ib_cell_kernel_f32<128>, dim3(a.n_cells), dim3(128), smem, s, pdl, a,
+                             maxv);
+    return launch_kernel(ib_cell_kernel_f32<256>, dim3(a.n_cells), dim3(256), smem, s, pdl, a,
+                         maxv);
 }
 
 // Per-cell shoelace area relative to the first vertex, FP64 (computeAreas).

@@ -280,8 +280,11 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 
 // The work of one cell by one CTA of NT threads.  Callers that run several
 // cells through the same CTA call it again for the next cell; the first
-// barrier protects the shared arrays of the previous call.
-template <int NT>
+// barrier protects the shared arrays of the previous call.  GRIDDEP: the
+// caller is a kernel of its own (programmatic launch after a lattice launch):
+// the cell's constant data and its vertex state (written by the IB launch two
+// launches back) are loaded through L2 before the wait, the u plane after it.
+template <int NT, bool GRIDDEP>
 static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) {
     static_assert(NT >= kMaxRows && NT % 64 == 0, "CTA size");
     constexpr int kIBThreads = NT;
@@ -294,10 +297,14 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
     int& s_flag = *S.s_flag;
     __syncthreads();
 
-    const int v0 = a.off[c];
-    const int n = a.off[c + 1] - v0;
+    const int v0 = __ldcg(a.off + c);
+    const int n = __ldcg(a.off + c + 1) - v0;
     const int tid = threadIdx.x, lane = tid & 31;
     if (n > S.maxv) {  // cannot happen for callers that size maxv from the cells
+        if (GRIDDEP) {
+            griddep_wait();
+            griddep_launch_dependents();
+        }
         if (tid == 0) raise_flag(a.diag, kDiagGeometry);
         return;
     }
@@ -314,31 +321,46 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
     float pL0[2] = {0.f, 0.f}, pk[2] = {0.f, 0.f}, pL0p[2] = {0.f, 0.f}, pkp[2] = {0.f, 0.f};
     float ppres = 0.f;
     if (a.do_prep && a.do_force && tid < half) {
-        ppres = (float)a.pres[c];
+        ppres = (float)__ldcg(a.pres + c);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int t = tid + r * half;
             if (t < n) {
                 const int tp = (t == 0) ? n - 1 : t - 1;
-                pL0[r] = (float)a.L0[v0 + t];
-                pk[r] = (float)a.k[v0 + t];
-                pL0p[r] = (float)a.L0[v0 + tp];
-                pkp[r] = (float)a.k[v0 + tp];
+                pL0[r] = (float)__ldcg(a.L0 + v0 + t);
+                pk[r] = (float)__ldcg(a.k + v0 + t);
+                pL0p[r] = (float)__ldcg(a.L0 + v0 + tp);
+                pkp[r] = (float)__ldcg(a.k + v0 + tp);
             }
         }
+    }
+    // the vertex state of this thread's first vertex
+    double2 X0 = make_double2(0.0, 0.0);
+    int2 b0 = make_int2(0, 0);
+    float2 f0 = make_float2(0.f, 0.f);
+    if (tid < n) {
+        X0 = __ldcg(a.xy + v0 + tid);
+        if (a.do_move && a.vbase) {
+            b0 = __ldcg(a.vbase + v0 + tid);
+            f0 = __ldcg(a.vfrac + v0 + tid);
+        }
+    }
+    if (GRIDDEP) {
+        griddep_wait();
+        griddep_launch_dependents();
     }
 
     // ---- (1) interpolate u^n at X^n and move; (base, frac) of the new X
     int ilo = INT_MAX, ihi = INT_MIN, jlo = INT_MAX, jhi = INT_MIN;
     bool finite = true;
     for (int t = tid; t < n; t += kIBThreads) {
-        double2 X = a.xy[v0 + t];
+        double2 X = (t == tid) ? X0 : a.xy[v0 + t];
         int2 b;
         float2 f;
         if (a.do_move) {
             if (a.vbase) {
-                b = a.vbase[v0 + t];
-                f = a.vfrac[v0 + t];
+                b = (t == tid) ? b0 : a.vbase[v0 + t];
+                f = (t == tid) ? f0 : a.vfrac[v0 + t];
             } else {
                 base_frac(X.x, &b.x, &f.x);
                 base_frac(X.y, &b.y, &f.y);

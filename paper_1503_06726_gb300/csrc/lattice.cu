@@ -27,55 +27,69 @@
 
 namespace lbib {
 
+// CTAs of 128 threads.  FP32/FP16 storage with up to two species is held to
+// 48 registers so that 10 CTAs (40 warps) fit per SM -- more loads in flight,
+// measured faster at 1024^2; more species keep 64 registers (no spills).
+template <typename T, int S>
+struct LatticeOccupancy {
+    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (S <= 2 ? 10 : 8);
+};
+constexpr int kLatticeThreads = 128;
+
 template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
-__global__ void __launch_bounds__(256) lattice_kernel(LatticeArgs a, Coefs<C> k) {
+__global__ void __launch_bounds__(kLatticeThreads, LatticeOccupancy<T, S>::kMinBlocks)
+    lattice_kernel(LatticeArgs a, Coefs<C> k) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
+    constexpr bool GRIDDEP = true;
     LBIB_LATTICE_NODE_BODY
 }
 
 template <typename T, typename C, int S, bool WALLS, int FORCING>
-static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s) {
+static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s,
+                           bool pdl) {
     // the group masks are cleared per warp: a warp must be 32 nodes of one row
     if (a.fmask && block.x % 32 != 0) return cudaErrorInvalidConfiguration;
+    if (block.x * block.y * block.z > (unsigned)kLatticeThreads) return cudaErrorInvalidConfiguration;
     dim3 grid((a.nx + block.x - 1) / block.x, (a.ny + block.y - 1) / block.y);
     const Coefs<C>& k = *static_cast<const Coefs<C>*>(coefs);
     constexpr bool SC = std::is_same<T, __half>::value;
-    lattice_kernel<T, C, S, WALLS, FORCING, SC><<<grid, block, 0, s>>>(a, k);
-    return cudaGetLastError();
+    return launch_kernel(lattice_kernel<T, C, S, WALLS, FORCING, SC>, grid, block, 0, s, pdl, a,
+                         k);
 }
 
 template <typename T, typename C, int S>
 static cudaError_t launch2(int bc_y, int forcing, const LatticeArgs& a, const void* coefs,
-                           dim3 block, cudaStream_t s) {
+                           dim3 block, cudaStream_t s, bool pdl) {
     if (bc_y) {
-        return forcing ? launch3<T, C, S, true, 1>(a, coefs, block, s)
-                       : launch3<T, C, S, true, 0>(a, coefs, block, s);
+        return forcing ? launch3<T, C, S, true, 1>(a, coefs, block, s, pdl)
+                       : launch3<T, C, S, true, 0>(a, coefs, block, s, pdl);
     }
-    return forcing ? launch3<T, C, S, false, 1>(a, coefs, block, s)
-                   : launch3<T, C, S, false, 0>(a, coefs, block, s);
+    return forcing ? launch3<T, C, S, false, 1>(a, coefs, block, s, pdl)
+                   : launch3<T, C, S, false, 0>(a, coefs, block, s, pdl);
 }
 
 template <typename T, typename C>
 static cudaError_t launch1(int n_species, int bc_y, int forcing, const LatticeArgs& a,
-                           const void* coefs, dim3 block, cudaStream_t s) {
+                           const void* coefs, dim3 block, cudaStream_t s, bool pdl) {
     switch (n_species) {
-        case 0: return launch2<T, C, 0>(bc_y, forcing, a, coefs, block, s);
-        case 1: return launch2<T, C, 1>(bc_y, forcing, a, coefs, block, s);
-        case 2: return launch2<T, C, 2>(bc_y, forcing, a, coefs, block, s);
-        case 3: return launch2<T, C, 3>(bc_y, forcing, a, coefs, block, s);
-        default: return launch2<T, C, 4>(bc_y, forcing, a, coefs, block, s);
+        case 0: return launch2<T, C, 0>(bc_y, forcing, a, coefs, block, s, pdl);
+        case 1: return launch2<T, C, 1>(bc_y, forcing, a, coefs, block, s, pdl);
+        case 2: return launch2<T, C, 2>(bc_y, forcing, a, coefs, block, s, pdl);
+        case 3: return launch2<T, C, 3>(bc_y, forcing, a, coefs, block, s, pdl);
+        default: return launch2<T, C, 4>(bc_y, forcing, a, coefs, block, s, pdl);
     }
 }
 
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
-                           const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s) {
+                           const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s,
+                           bool pdl) {
     if (precision == LBIB_FP64)
-        return launch1<double, double>(n_species, bc_y, forcing, a, coefs, block, s);
+        return launch1<double, double>(n_species, bc_y, forcing, a, coefs, block, s, pdl);
     if (precision == LBIB_FP32)
-        return launch1<float, float>(n_species, bc_y, forcing, a, coefs, block, s);
-    return launch1<__half, float>(n_species, bc_y, forcing, a, coefs, block, s);
+        return launch1<float, float>(n_species, bc_y, forcing, a, coefs, block, s, pdl);
+    return launch1<__half, float>(n_species, bc_y, forcing, a, coefs, block, s, pdl);
 }
 
 // ---------------------------------------------------------------------------

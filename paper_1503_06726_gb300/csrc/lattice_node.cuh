@@ -13,17 +13,17 @@ template <typename T, typename C>
 struct Store;
 template <>
 struct Store<double, double> {
-    static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
+    static __device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <>
 struct Store<float, float> {
-    static __device__ __forceinline__ float ld(const float* p) { return __ldg(p); }
+    static __device__ __forceinline__ float ld(const float* p) { return __ldcg(p); }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <>
 struct Store<__half, float> {
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldcg(p)); }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -53,8 +53,11 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
 // The body is a macro so that the standalone kernel expands it directly on its
 // kernel parameters (a separate inlined function measured 17% slower there,
 // with identical memory traffic); the ensemble's device function expands the
-// same text.  It uses the names a (LatticeArgs), k (Coefs<C>), x, y and the
-// template parameters T, C, S, WALLS, FORCING, SCALED.
+// same text.  It uses the names a (LatticeArgs), k (Coefs<C>), x, y, the
+// template parameters T, C, S, WALLS, FORCING, SCALED and a constexpr bool
+// GRIDDEP: with it the population loads (written by the lattice launch two
+// launches back, read through L2) are issued before the programmatic wait on
+// the IB kernel whose force, label and mask planes the rest reads.
 #define LBIB_LATTICE_NODE_BODY \
  \
     using St = Store<T, C>; \
@@ -99,6 +102,12 @@ _Pragma("unroll") \
             pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, lo_wall, \
                                hi_wall, g[s]); \
     } \
+    /* the IB kernel launched just before wrote the force, label and mask */ \
+    /* planes: wait for it, then let the next IB launch start */ \
+    if (GRIDDEP) { \
+        griddep_wait(); \
+        griddep_launch_dependents(); \
+    } \
     /* spread force and labels: only the 4-node groups the IB kernel marked */ \
     V2 fv; \
     fv.x = C(0); \
@@ -120,16 +129,23 @@ _Pragma("unroll") \
         if (lhit) label = a.id[node]; \
     } \
  \
-    /* ---- moments (Sec. 6.1) with the half-force velocity shift (Guo) */ \
-    if (SCALED) { \
-_Pragma("unroll") \
-        for (int q = 0; q < 9; ++q) d[q] *= k.fscale[q]; \
-    } \
+    /* ---- moments (Sec. 6.1) with the half-force velocity shift (Guo).  With */ \
+    /* scaled storage s_q = d_q / (w_q sigma) the moments weight the stored */ \
+    /* values (w_1..w_4 and w_5..w_8 are equal) and d_q is never formed. */ \
     const C Fx = k.bfx + fv.x, Fy = k.bfy + fv.y; \
-    const C drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8]; \
+    C drho, jx, jy; \
+    if (SCALED) { \
+        const C sA = k.fscale[0], sB = k.fscale[1], sC = k.fscale[5]; \
+        drho = sA * d[0] + sB * ((d[1] + d[2]) + (d[3] + d[4])) + \
+               sC * ((d[5] + d[6]) + (d[7] + d[8])); \
+        jx = sB * (d[1] - d[3]) + sC * ((d[5] - d[6]) + (d[8] - d[7])); \
+        jy = sB * (d[2] - d[4]) + sC * ((d[5] + d[6]) - (d[7] + d[8])); \
+    } else { \
+        drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8]; \
+        jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]); \
+        jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]); \
+    } \
     const C rho = k.rho0 + drho; \
-    const C jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]); \
-    const C jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]); \
     const C irho = C(1) / rho; \
     C ux, uy; \
     if (FORCING == LBIB_GUO) { \
@@ -142,52 +158,74 @@ _Pragma("unroll") \
     const C usq15 = C(1.5) * (ux * ux + uy * uy); \
     const C uF = ux * Fx + uy * Fy; \
  \
-    /* ---- collide and store the fluid */ \
+    /* ---- collide and store the fluid, opposite directions together: with */ \
+    /* A = drho + rho (9/2 (v.u)^2 - 3/2 u.u), B = 3 rho v.u and the forcing */ \
+    /* split into its even part Ce and odd part Co, */ \
+    /*   d*_q = (1 - omega) d_q + w (omega A + Ce) + w (omega B + Co) */ \
+    /* and the opposite direction flips the sign of the odd terms.  Scaled */ \
+    /* storage replaces the factor w by 1/sigma. */ \
     T* G = static_cast<T*>(a.fdst); \
+    { \
+        const C e0 = SCALED ? k.isig : C(w9(0)); \
+        C ev = k.omega * (drho - rho * usq15); \
+        if (FORCING == LBIB_GUO) ev -= k.pref * (C(3) * uF); \
+        St::st(G + node, k.omc * d[0] + e0 * ev); \
+    } \
 _Pragma("unroll") \
-    for (int q = 0; q < 9; ++q) { \
-        const C w = C(w9(q)); \
-        const C cu = C(cx(q)) * ux + C(cy(q)) * uy; \
-        const C cF = C(cx(q)) * Fx + C(cy(q)) * Fy; \
-        const C deq = w * (drho + rho * (C(3) * cu + C(4.5) * cu * cu - usq15)); \
-        C Sq; \
-        if (FORCING == LBIB_GUO) \
-            Sq = k.pref * w * (C(3) * (cF - uF) + C(9) * cu * cF); \
-        else \
-            Sq = C(3) * w * cF; \
-        C dn = d[q] + k.omega * (deq - d[q]) + Sq; \
-        if (SCALED) dn *= k.finv[q]; \
-        St::st(G + q * P + node, dn); \
+    for (int q = 1; q < 9; ++q) { \
+        if (q == 1 || q == 2 || q == 5 || q == 6) { \
+            const int o = q + 2; /* opposite of 1, 2, 5, 6 */ \
+            const C ew = SCALED ? k.isig : C(w9(q)); \
+            const C cu = C(cx(q)) * ux + C(cy(q)) * uy; \
+            const C cF = C(cx(q)) * Fx + C(cy(q)) * Fy; \
+            C ev = k.omega * (drho + rho * (C(4.5) * cu * cu - usq15)); \
+            C od = k.omega * (rho * (C(3) * cu)); \
+            if (FORCING == LBIB_GUO) { \
+                ev += k.pref * (C(9) * cu * cF - C(3) * uF); \
+                od += k.pref * (C(3) * cF); \
+            } else { \
+                od += C(3) * cF; \
+            } \
+            ev *= ew; \
+            od *= ew; \
+            St::st(G + q * P + node, k.omc * d[q] + (ev + od)); \
+            St::st(G + o * P + node, k.omc * d[o] + (ev - od)); \
+        } \
     } \
  \
-    /* ---- species (D2Q5): react and collide with the fluid u */ \
+    /* ---- species (D2Q5): react and collide with the fluid u, opposite */ \
+    /* directions together: g*_q = (1 - omega_D) g_q + w (omega_D phi + R) */ \
+    /* + w omega_D phi 3 v.u (scaled storage: 1/sigma_g for w) */ \
     if (S > 0) { \
         const uint32_t bits = (label == kOutside) ? 0u : (label & 0xFu); \
         T* Go = static_cast<T*>(a.gdst); \
         C ph[S > 0 ? S : 1]; \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
-            if (SCALED) { \
-_Pragma("unroll") \
-                for (int q = 0; q < 5; ++q) g[s][q] *= k.gscale[q]; \
-            } \
-            ph[s] = ((g[s][0] + g[s][1]) + (g[s][2] + g[s][3])) + g[s][4]; \
+            if (SCALED) \
+                ph[s] = k.gscale[0] * g[s][0] + \
+                        k.gscale[1] * ((g[s][1] + g[s][2]) + (g[s][3] + g[s][4])); \
+            else \
+                ph[s] = ((g[s][0] + g[s][1]) + (g[s][2] + g[s][3])) + g[s][4]; \
         } \
+        const C cux = ux, cuy = uy; \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
             C R = ((bits >> s) & 1u) ? k.srate[s] : C(0); \
 _Pragma("unroll") \
             for (int b = 0; b < S; ++b) R += k.K[s][b] * ph[b]; \
             T* B = Go + (int64_t)s * 5 * P; \
-_Pragma("unroll") \
-            for (int q = 0; q < 5; ++q) { \
-                const C w = C(w5(q)); \
-                const C cu = C(cx(q)) * ux + C(cy(q)) * uy; \
-                const C geq = ph[s] * w * (C(1) + C(3) * cu); \
-                C gn = g[s][q] + k.omegaD[s] * (geq - g[s][q]) + w * R; \
-                if (SCALED) gn *= k.ginv[q]; \
-                St::st(B + q * P + node, gn); \
-            } \
+            const C ev = k.omegaD[s] * ph[s] + R; \
+            const C od = k.omegaD[s] * ph[s] * C(3); \
+            const C eA = SCALED ? k.isig_g : C(w5(0)); \
+            const C eB = SCALED ? k.isig_g : C(w5(1)); \
+            const C evB = eB * ev; \
+            const C ox = eB * od * cux, oy = eB * od * cuy; \
+            St::st(B + node, k.omcD[s] * g[s][0] + eA * ev); \
+            St::st(B + 1 * P + node, k.omcD[s] * g[s][1] + (evB + ox)); \
+            St::st(B + 3 * P + node, k.omcD[s] * g[s][3] + (evB - ox)); \
+            St::st(B + 2 * P + node, k.omcD[s] * g[s][2] + (evB + oy)); \
+            St::st(B + 4 * P + node, k.omcD[s] * g[s][4] + (evB - oy)); \
             if (a.out) static_cast<C*>(a.phi)[(int64_t)s * P + node] = ph[s]; \
         } \
     } \
@@ -226,6 +264,7 @@ _Pragma("unroll") \
 template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
                                              int y) {
+    constexpr bool GRIDDEP = false;
     LBIB_LATTICE_NODE_BODY
 }
 

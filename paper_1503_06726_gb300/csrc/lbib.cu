@@ -113,12 +113,14 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
     std::memset(k, 0, sizeof(*k));
     k->rho0 = (C)p.rho0;
     k->omega = (C)(1.0 / p.tau);
+    k->omc = (C)(1.0 - 1.0 / p.tau);
     k->pref = (C)(1.0 - 0.5 / p.tau);
     k->bfx = (C)p.body_force[0];
     k->bfy = (C)p.body_force[1];
     for (int s = 0; s < kMaxSpecies; ++s) {
         double tauD = 3.0 * p.D[s] + 0.5;
         k->omegaD[s] = (C)(s < p.n_species ? 1.0 / tauD : 0.0);
+        k->omcD[s] = (C)(s < p.n_species ? 1.0 - 1.0 / tauD : 1.0);
         k->srate[s] = (C)p.src_rate[s];
         for (int b = 0; b < kMaxSpecies; ++b)
             k->K[s][b] = (C)(p.react[s][b] - (s == b ? p.decay[s] : 0.0));
@@ -126,6 +128,8 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
     const double sf = p.fp16_scale > 0 ? p.fp16_scale : std::ldexp(1.0, -10);
     const double sg = p.fp16_scale_species > 0 ? p.fp16_scale_species : std::ldexp(1.0, -8);
     const bool scaled = p.precision == LBIB_FP16;
+    k->isig = (C)(scaled ? 1.0 / sf : 1.0);
+    k->isig_g = (C)(scaled ? 1.0 / sg : 1.0);
     for (int q = 0; q < 9; ++q) {
         k->fscale[q] = (C)(scaled ? w9(q) * sf : 1.0);
         k->finv[q] = (C)(scaled ? 1.0 / (w9(q) * sf) : 1.0);
@@ -212,15 +216,20 @@ LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out) { return lattic
 IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) { return ib_args(c, move, prep, vforce); }
 }  // namespace lbib
 
-static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out) {
+// pdl: programmatic launch, allowed only when the previous launch on the
+// stream is the other kernel of the step (an IB launch before a lattice
+// launch and vice versa): each kernel's early loads rely on the launch two
+// back having completed, which the other kernel's wait guarantees.
+static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl = false) {
     LatticeArgs a = lattice_args(c, src_buf, out);
     return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,
-                          coefs_of(c), c->block, c->stream);
+                          coefs_of(c), c->block, c->stream, pdl && c->nC > 0);
 }
 
-static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool vforce) {
+static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool vforce, bool pdl = false) {
     if (c->nC == 0) return cudaSuccess;
-    return launch_ib(c->p.precision, ib_args(c, move, prep, vforce), c->maxv_cell, c->stream);
+    return launch_ib(c->p.precision, ib_args(c, move, prep, vforce), c->maxv_cell, c->stream,
+                     pdl);
 }
 
 static void drop_graphs(lbib_ctx* c) {
@@ -233,12 +242,13 @@ static void drop_graphs(lbib_ctx* c) {
 }
 
 // two full steps starting from buffer parity `par`, ending with the prep of
-// the following step: [lat(par), ib move+prep, lat(1-par), ib move+prep]
+// the following step: [lat(par), ib move+prep, lat(1-par), ib move+prep];
+// inside the graph each launch after the first is programmatic
 static cudaError_t enqueue_chunk(lbib_ctx* c, int par) {
     cudaError_t e = enqueue_lattice(c, par, false);
-    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false);
-    if (e == cudaSuccess) e = enqueue_lattice(c, 1 - par, false);
-    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, true);
+    if (e == cudaSuccess) e = enqueue_lattice(c, 1 - par, false, true);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, true);
     return e;
 }
 
@@ -456,16 +466,22 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     int left = n_steps;
     // full two-step chunks through the graph, keeping the last two steps apart
     // (they write the vertex forces and the output fields)
+    bool graphed = false;
     while (e == cudaSuccess && left > 3) {
         cudaGraphExec_t g;
         e = get_chunk_graph(c, c->cur, &g);
         if (e == cudaSuccess) e = cudaGraphLaunch(g, c->stream);
+        graphed = true;
         left -= 2;
     }
+    // the remaining steps as single launches: a launch that directly follows
+    // the other kernel of the step (not a graph) is programmatic
+    bool follows_kernel = ib && !graphed;
     while (e == cudaSuccess && left > 0) {
         const bool last = (left == 1);
-        e = enqueue_lattice(c, c->cur, last);
-        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, !last, left == 2);
+        e = enqueue_lattice(c, c->cur, last, follows_kernel);
+        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, !last, left == 2, true);
+        follows_kernel = ib;
         c->cur = 1 - c->cur;
         --left;
     }

@@ -69,6 +69,9 @@ struct Coefs {
     C srate[kMaxSpecies];
     C fscale[9], finv[9];       // stored = (f - w rho0) * finv; dev = stored * fscale
     C gscale[5], ginv[5];
+    C omc;                      // 1 - omega
+    C omcD[kMaxSpecies];        // 1 - omega_D
+    C isig, isig_g;             // 1/sigma, 1/sigma_g of scaled (FP16) storage, else 1
 };
 
 struct LatticeArgs {
@@ -145,6 +148,40 @@ struct IBSmem32 {
     int s_flag;
 };
 
+// Programmatic dependent launch.  A kernel launched with the programmatic
+// stream-serialization attribute may start while the previous kernel of its
+// stream is still running.  griddep_wait() blocks the calling thread until
+// that kernel has completed and its writes are visible;
+// griddep_launch_dependents() lets the next such kernel of the stream start
+// once every CTA of this grid has issued it or exited.  Both are no-ops for a
+// kernel launched without the attribute.  Kernels of the coupled step call
+// them in this order, so a kernel starts only after the kernel two launches
+// back has completed: before its wait it may read what that kernel (or any
+// earlier one) wrote, through L2 (`ld.global.cg`), and nothing else.
+__device__ __forceinline__ void griddep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// launch `kern` on stream s, with programmatic serialization when pdl is set
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t s, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // mask words covering a plane of `plane` elements (1 bit per 4 nodes)
 inline int64_t mask_words(int64_t plane) { return (plane + 127) / 128 + 1; }
 
@@ -154,11 +191,14 @@ void fill_coefs_public(const lbib_params& p, Coefs<float>* k);
 int set_thread_error(int code, const std::string& msg);
 
 // launchers (return cudaError_t of the launch)
+// pdl: launch with programmatic serialization (the previous kernel of the
+// stream must be the other kernel of the coupled step)
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
                            const LatticeArgs& a, const void* coefs, dim3 block,
-                           cudaStream_t s);
+                           cudaStream_t s, bool pdl = false);
 // maxv_cell: the largest vertex count of a cell (sizes shared memory and the CTA)
-cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s);
+cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s,
+                      bool pdl = false);
 cudaError_t launch_areas(const double2* xy, const int32_t* off, int n_cells, double* area,
                          cudaStream_t s);
 cudaError_t launch_init_populations(int precision, int n_species, int nx, int ny,
