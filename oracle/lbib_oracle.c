@@ -150,10 +150,14 @@ void orc_cell_areas(int nc, const int32_t* off, const double* xy, double* area) 
  * the polygons).  Reading: a node belongs to a cell when its centre is inside
  * the polygon by the crossing-number rule, half-open in y -- an edge a->b
  * crosses the row of the node when (y_a <= y) != (y_b <= y), and counts when
- * x < x_a + (y - y_a)(x_b - x_a)/(y_b - y_a).  On overlap the lower cell index
- * wins.  Coordinates are unwrapped; the node index is taken modulo the
- * periodic sizes, rows outside a walled domain are skipped.
- * id[N]: 0 outside, c+1 inside cell c.  src[N]: src_flag of that cell. */
+ * x < x_a + (y - y_a)(x_b - x_a)/(y_b - y_a).  The paper gives no rule for
+ * overlapping polygons (its cells partition the tissue); reading taken: the
+ * node's domainID is the lower cell index, and the node receives the sources
+ * of every cell that contains it (the bitwise OR of their source flags).
+ * Coordinates are unwrapped; the node index is taken modulo the periodic
+ * sizes, rows outside a walled domain are skipped.
+ * id[N]: 0 outside, c+1 for the lowest cell c containing the node.
+ * src[N]: OR of the src_flag of the cells containing the node. */
 void orc_rasterize(int nx, int ny, int bc_y, int nc, const int32_t* off, const double* xy,
                    const uint8_t* src_flag, int32_t* id, uint8_t* src) {
     long N = (long)nx * ny;
@@ -183,10 +187,8 @@ void orc_rasterize(int nx, int ny, int bc_y, int nc, const int32_t* off, const d
                 }
                 if (!inside) continue;
                 long idx = (long)wrap(J, ny) * nx + wrap(I, nx);
-                if (id[idx] == 0) {
-                    id[idx] = c + 1;
-                    src[idx] = src_flag[c];
-                }
+                if (id[idx] == 0) id[idx] = c + 1;
+                src[idx] |= src_flag[c];
             }
         }
     }
