@@ -82,6 +82,8 @@ extern "C" {
  *                R_s = sum_b react[s][b] phi_b - decay[s] phi_s
  *                      + src_rate[s] * [the node lies in a cell whose
  *                                       src_flag has bit s set]
+ *                (a node inside several overlapping cells takes the sources
+ *                of all of them; the paper's cells do not overlap)
  *   forcing      LBIB_GUO or LBIB_HE_PAPER
  *   precision    LBIB_FP64, LBIB_FP32 or LBIB_FP16
  *   fp16_scale   sigma of the FP16 fluid storage (default 2^-10 when 0)
@@ -154,7 +156,7 @@ int lbib_step(lbib_ctx* ctx, int32_t n_steps);
  * nx*ny), LBIB_U (ux, uy), LBIB_PHI (phi, n_species*nx*ny), LBIB_X (xy,
  * 2*V, the current vertex positions), LBIB_AREA (area, n_cells, FP64
  * shoelace of the current polygons), LBIB_ID (id, nx*ny int32: 0 outside,
- * c+1 inside cell c, as used by the last step), LBIB_FORCE (force, 2*nx*ny
+ * c+1 for the lowest cell c containing the node in the last step), LBIB_FORCE (force, 2*nx*ny
  * interleaved fx, fy spread in the last step) and LBIB_VFORCE (vforce, 2*V
  * vertex forces of the last step).  Lattice fields need at least one step
  * since create (else LBIB_E_STATE).  Unused pointers may be NULL. */
@@ -183,11 +185,13 @@ int lbib_set_state(lbib_ctx* ctx, const void* host, uint64_t bytes);
 /* Label lattice nodes by cell (Fig. 2: the domainID of the lattice nodes is
  * set from the polygons), on the device, without a context.  A node belongs to
  * a cell when its centre is inside the polygon by the crossing-number rule,
- * half-open in y; on overlap the lower cell index wins.
+ * half-open in y; on overlap the lower cell index is the node's label and
+ * the node carries the source flags of every cell containing it.
  *   nx, ny, bc_y              lattice (bc_y 1: rows outside [0, ny) dropped)
  *   n_cells, d_cell_off, d_xy, d_src_flag   device arrays as lbib_set_cells()
  *   d_id       out, nx*ny int32 (dense, row-major): 0 outside, c+1 in cell c
- *   d_src      out (may be NULL), nx*ny bytes: src_flag of the node's cell
+ *   d_src      out (may be NULL), nx*ny bytes: OR of the src_flag of the cells
+ *              containing the node
  *   cuda_stream  stream to enqueue on (asynchronous)
  * Returns LBIB_OK, LBIB_E_PARAM or LBIB_E_CUDA (lbib_last_error(NULL)). */
 int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
@@ -345,8 +349,8 @@ int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, cons
  * lbib_step() on state the caller already owns and calls no cudaMalloc,
  * cudaFree or other allocating routine.
  *
- * The intermediate planes (second population buffer, spread force, labels,
- * velocity, diagnostic words) live in one static device array of 4 MiB
+ * The intermediate planes (second population buffer, spread force, source
+ * bits, velocity, diagnostic words) live in one static device array of 4 MiB
  * inside the library; every GPU that loads the library holds it until the
  * process exits.  Lattices whose planes do not fit are rejected with
  * LBIB_E_WORKSPACE (with FP64 storage and one species, 64x64 needs about

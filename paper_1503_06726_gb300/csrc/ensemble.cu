@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
             a.do_move = move;
             a.do_prep = prep;
             a.write_vforce = vforce;
+            a.do_ids = vforce;  // the prep of the output step writes the labels too
             ib_cell_f32<kIBThreads, false>(a, item - e.cell_pfx[t], view);
         }
     };

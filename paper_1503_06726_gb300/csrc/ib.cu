@@ -115,8 +115,11 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
     // Labels need a finite box no wider than the lattice; otherwise the
     // geometry has blown up: flag it and leave the labels empty so that every
     // loop below stays bounded by the lattice size.
-    const bool labels = a.do_mask && s_flag == 0 && (I1 - I0) <= a.nx && (J1 - J0) <= a.ny;
-    if (a.do_mask && !labels && tid == 0) raise_flag(a.diag, kDiagGeometry);
+    const bool geom_ok = s_flag == 0 && (I1 - I0) <= a.nx && (J1 - J0) <= a.ny;
+    if (a.do_mask && !geom_ok && tid == 0) raise_flag(a.diag, kDiagGeometry);
+    // the cell is labelled when the caller wants the packed labels or the cell
+    // has source bits to deposit
+    const bool labels = a.do_mask && geom_ok && (a.do_ids || (a.src && (a.srcf[c] & 0xF)));
     const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
     const bool scan = labels && rows <= kMaxRows;
 
@@ -198,9 +201,8 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
             }
         }
     }
-    if (!a.do_mask) return;
+    if (!labels) return;  // uniform over the CTA
     __syncthreads();
-    if (!labels) return;
 
     fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols);
 }

@@ -135,14 +135,49 @@ __device__ __forceinline__ void mark_range(uint32_t* mask, int64_t rowbase, int 
 // thresholds in thr/rowcnt are complete: one warp per row sorts them and
 // fills each span [t_{2k}, t_{2k+1}) -- the nodes with an odd number of
 // thresholds above them.  Otherwise every node of the box evaluates the
-// crossing predicate over all edges in FP64 (the brute-force path).
+// crossing predicate over all edges in FP64 (the brute-force path).  Every
+// inside node receives, with a.do_ids, the packed label (atomicMin: the lower
+// cell index wins) and, when the cell has source bits, those bits in the
+// source plane (atomicOr: a node inside several cells gets all their sources).
+// OR the source bits into the source plane at one node
+__device__ __forceinline__ void src_or_node(const IBArgs& a, int64_t node, uint32_t bits) {
+    if (a.src_words) {
+        atomicOr(static_cast<uint32_t*>(a.src) + node, bits);
+    } else {
+        unsigned int* w = reinterpret_cast<unsigned int*>(static_cast<uint8_t*>(a.src) + (node & ~3ll));
+        atomicOr(w, bits << (8 * (int)(node & 3)));
+    }
+}
+
+// OR the source bits into the bytes [s, e) of one row of the byte plane (row
+// start 8-byte aligned): one 64-bit atomic per 8 nodes, lanes take words
+__device__ __forceinline__ void src_or_range(uint8_t* row, int s, int e, uint32_t bits, int lane) {
+    if (e <= s) return;
+    const unsigned long long rep = 0x0101010101010101ull * (unsigned long long)bits;
+    unsigned long long* wrow = reinterpret_cast<unsigned long long*>(row);
+    for (int w = (s >> 3) + lane; w <= ((e - 1) >> 3); w += 32) {
+        const int a0 = max(s - 8 * w, 0), a1 = min(e - 8 * w, 8);
+        const unsigned long long m =
+            (a1 - a0 == 8) ? ~0ull : (((1ull << (8 * (a1 - a0))) - 1ull) << (8 * a0));
+        atomicOr(wrow + w, rep & m);
+    }
+}
+
+__device__ __forceinline__ void label_node(const IBArgs& a, int64_t node, uint32_t code,
+                                           uint32_t bits) {
+    if (a.do_ids) atomicMin(a.id + node, code);
+    if (bits) src_or_node(a, node, bits);
+}
+
 static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, const double2* sx,
                                          const int* rowcnt, int* thr, bool scan_ok, int I0,
                                          int J0, int rows, int cols) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nwarps = blockDim.x >> 5;
-    uint32_t* id = a.id;
-    const uint32_t code = ((uint32_t)c << 4) | (uint32_t)(a.srcf[c] & 0xF);
+    // source bits go to the source plane only when the caller gave one
+    const uint32_t cbits = (uint32_t)(a.srcf[c] & 0xF);
+    const uint32_t bits = a.src ? cbits : 0u;
+    const uint32_t code = ((uint32_t)c << 4) | cbits;
     const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
     if (scan_ok) {
         // one warp per row: sort the row's thresholds, then fill each span
@@ -167,25 +202,37 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
             __syncwarp();
             int wJ = wJ0 + r;
             if (wJ >= a.ny) wJ -= a.ny;
-            uint32_t* rowp = id + (int64_t)wJ * a.pitch;
+            const int64_t rb = (int64_t)wJ * a.pitch;
             if ((m & 1) == 0) {
                 for (int k = 0; k + 1 < m; k += 2) {
                     const int lo = tr[k], hi = tr[k + 1];
-                    for (int I = lo + lane; I < hi; I += 32) {
-                        int wI = wI0 + (I - I0);
-                        if (wI >= a.nx) wI -= a.nx;
-                        atomicMin(rowp + wI, code);
+                    // byte plane: whole words per lane below; word plane: per node
+                    const uint32_t nbits = a.src_words ? bits : 0u;
+                    if (a.do_ids || nbits) {
+                        for (int I = lo + lane; I < hi; I += 32) {
+                            int wI = wI0 + (I - I0);
+                            if (wI >= a.nx) wI -= a.nx;
+                            label_node(a, rb + wI, code, nbits);
+                        }
                     }
-                    if (hi > lo) {  // the span's groups, split where it wraps
+                    if (hi > lo) {  // the span's words and groups, split where it wraps
                         int ws = wI0 + (lo - I0);
                         if (ws >= a.nx) ws -= a.nx;
                         const int len = hi - lo;
-                        const int64_t rb = (int64_t)wJ * a.pitch;
-                        if (ws + len <= a.nx) {
-                            mark_range(a.lmask, rb, ws, ws + len, lane);
-                        } else {
-                            mark_range(a.lmask, rb, ws, a.nx, lane);
-                            mark_range(a.lmask, rb, 0, ws + len - a.nx, lane);
+                        const int e1 = ws + len <= a.nx ? ws + len : a.nx;
+                        const int e2 = ws + len - a.nx;  // > 0 when the span wraps
+                        if (a.do_ids) {
+                            mark_range(a.lmask, rb, ws, e1, lane);
+                            if (e2 > 0) mark_range(a.lmask, rb, 0, e2, lane);
+                        }
+                        if (bits) {
+                            if (!a.src_words) {
+                                uint8_t* row = static_cast<uint8_t*>(a.src) + rb;
+                                src_or_range(row, ws, e1, bits, lane);
+                                if (e2 > 0) src_or_range(row, 0, e2, bits, lane);
+                            }
+                            mark_range(a.smask, rb, ws, e1, lane);
+                            if (e2 > 0) mark_range(a.smask, rb, 0, e2, lane);
                         }
                     }
                 }
@@ -197,11 +244,10 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
                     if (cnt & 1) {
                         int wI = wI0 + cc;
                         if (wI >= a.nx) wI -= a.nx;
-                        atomicMin(rowp + wI, code);
-                        if (a.lmask) {
-                            const int64_t g = ((int64_t)wJ * a.pitch + wI) >> 2;
-                            atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
-                        }
+                        label_node(a, rb + wI, code, bits);
+                        const int64_t g = (rb + wI) >> 2;
+                        if (a.do_ids && a.lmask) atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
+                        if (bits && a.smask) atomicOr(a.smask + (g >> 5), 1u << (g & 31));
                     }
                 }
             }
@@ -223,11 +269,11 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
                 int wI = wI0 + cc, wJ = wJ0 + r;
                 if (wI >= a.nx) wI -= a.nx;
                 if (wJ >= a.ny) wJ -= a.ny;
-                atomicMin(id + (int64_t)wJ * a.pitch + wI, code);
-                if (a.lmask) {
-                    const int64_t g = ((int64_t)wJ * a.pitch + wI) >> 2;
-                    atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
-                }
+                const int64_t node = (int64_t)wJ * a.pitch + wI;
+                label_node(a, node, code, bits);
+                const int64_t g = node >> 2;
+                if (a.do_ids && a.lmask) atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
+                if (bits && a.smask) atomicOr(a.smask + (g >> 5), 1u << (g & 31));
             }
         }
     }
@@ -435,7 +481,10 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
     // within one period; anything wider means the geometry has blown up
     const bool geom_ok = s_flag == 0 && (I1 - I0) < a.nx && (J1 - J0) <= a.ny;
     if (a.do_mask && !geom_ok && tid == 0) raise_flag(a.diag, kDiagGeometry);
-    const bool labels = a.do_mask && geom_ok && J1 >= J0;
+    // the cell is labelled when the caller wants the packed labels or the cell
+    // has source bits to deposit
+    const bool labels =
+        a.do_mask && geom_ok && J1 >= J0 && (a.do_ids || (a.src && (a.srcf[c] & 0xF)));
     const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
     const bool scan = labels && rows <= kMaxRows;
 
@@ -531,9 +580,8 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
             }
         }
     }
-    if (!a.do_mask) return;
+    if (!labels) return;  // uniform over the CTA
     __syncthreads();
-    if (!labels) return;
     fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols);
 }
 

@@ -27,12 +27,12 @@
 
 namespace lbib {
 
-// CTAs of 128 threads.  FP32/FP16 storage with up to two species is held to
-// 48 registers so that 10 CTAs (40 warps) fit per SM -- more loads in flight,
-// measured faster at 1024^2; more species keep 64 registers (no spills).
+// CTAs of 128 threads.  FP32/FP16 storage is held to 48 registers with one
+// species (10 CTAs, 40 warps per SM: more loads in flight, measured faster),
+// 56 with two (9 CTAs; 48 spilled) and 64 with more (8 CTAs, no spills).
 template <typename T, int S>
 struct LatticeOccupancy {
-    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (S <= 2 ? 10 : 8);
+    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (S <= 1 ? 10 : (S == 2 ? 9 : 8));
 };
 constexpr int kLatticeThreads = 128;
 

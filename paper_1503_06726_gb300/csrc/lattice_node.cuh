@@ -108,25 +108,34 @@ _Pragma("unroll") \
         griddep_wait(); \
         griddep_launch_dependents(); \
     } \
-    /* spread force and labels: only the 4-node groups the IB kernel marked */ \
+    /* spread force, labels and source bits: only the 4-node groups the IB */ \
+    /* kernel marked (labels are written only before an output step) */ \
     V2 fv; \
     fv.x = C(0); \
     fv.y = C(0); \
-    uint32_t label = kOutside; \
-    bool fhit = false, lhit = false; \
-    uint32_t fword = 0u, lword = 0u; \
+    uint32_t label = kOutside, sbits = 0u; \
+    bool fhit = false, lhit = false, shit = false; \
+    /* for lane 0: which masks hold bits of this warp's 8 groups */ \
+    uint32_t clear = 0u; \
     const int64_t grp = node >> 2; \
     if (a.ib) { \
         if (a.fmask) { \
-            fword = a.fmask[grp >> 5]; \
-            lword = a.lmask[grp >> 5]; \
-            fhit = (fword >> (grp & 31)) & 1u; \
-            lhit = (lword >> (grp & 31)) & 1u; \
+            const int sh = (int)(grp & 31); \
+            const uint32_t fw = a.fmask[grp >> 5] >> sh; \
+            const uint32_t lw = a.lmask[grp >> 5] >> sh; \
+            const uint32_t sw = a.smask[grp >> 5] >> sh; \
+            fhit = fw & 1u; \
+            lhit = lw & 1u; \
+            shit = sw & 1u; \
+            clear = ((fw & 0xFFu) ? 1u : 0u) | ((lw & 0xFFu) ? 2u : 0u) | \
+                    ((sw & 0xFFu) ? 4u : 0u); \
         } else { \
-            fhit = lhit = true; \
+            fhit = shit = true; \
+            lhit = a.id != nullptr; \
         } \
         if (fhit) fv = static_cast<const V2*>(a.force)[node]; \
         if (lhit) label = a.id[node]; \
+        if (shit) sbits = a.src[node]; \
     } \
  \
     /* ---- moments (Sec. 6.1) with the half-force velocity shift (Guo).  With */ \
@@ -197,7 +206,7 @@ _Pragma("unroll") \
     /* directions together: g*_q = (1 - omega_D) g_q + w (omega_D phi + R) */ \
     /* + w omega_D phi 3 v.u (scaled storage: 1/sigma_g for w) */ \
     if (S > 0) { \
-        const uint32_t bits = (label == kOutside) ? 0u : (label & 0xFu); \
+        const uint32_t bits = sbits & 0xFu; \
         T* Go = static_cast<T*>(a.gdst); \
         C ph[S > 0 ? S : 1]; \
 _Pragma("unroll") \
@@ -232,7 +241,8 @@ _Pragma("unroll") \
  \
     /* ---- velocity where the interpolation will read it (the groups that */ \
     /* received force: the kernel support of the same vertex positions) or */ \
-    /* everywhere on an output step; resets; outputs */ \
+    /* everywhere on an output step; resets (after the compute: stores placed */ \
+    /* before it measured 3x slower); outputs; the group masks */ \
     if (a.out || fhit) { \
         V2 uv; \
         uv.x = ux; \
@@ -247,15 +257,17 @@ _Pragma("unroll") \
             static_cast<V2*>(a.force)[node] = z; \
         } \
         if (lhit) a.id[node] = kOutside; \
+        if (shit) a.src[node] = 0; \
         if (a.out) { \
             a.id_out[node] = label; \
             static_cast<V2*>(a.force_out)[node] = fv; \
         } \
         /* lane 0 clears the warp's 8 group bits (32 nodes, one row, 32-aligned) */ \
-        if (a.fmask && (threadIdx.x & 31) == 0) { \
+        if (clear && (threadIdx.x & 31) == 0) { \
             const int sh = (int)(grp & 31); \
-            if ((fword >> sh) & 0xFFu) atomicAnd(a.fmask + (grp >> 5), ~(0xFFu << sh)); \
-            if ((lword >> sh) & 0xFFu) atomicAnd(a.lmask + (grp >> 5), ~(0xFFu << sh)); \
+            if (clear & 1u) atomicAnd(a.fmask + (grp >> 5), ~(0xFFu << sh)); \
+            if (clear & 2u) atomicAnd(a.lmask + (grp >> 5), ~(0xFFu << sh)); \
+            if (clear & 4u) atomicAnd(a.smask + (grp >> 5), ~(0xFFu << sh)); \
         } \
     } \
     if (a.out) static_cast<C*>(a.rho)[node] = rho; \

@@ -57,6 +57,8 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.id_out = take(P * 4);
     l.fmask = take((uint64_t)mask_words(l.plane) * 4);
     l.lmask = take((uint64_t)mask_words(l.plane) * 4);
+    l.src = take(align_up(P, 8));  // one byte per node
+    l.smask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
     const uint64_t V = (uint64_t)max_vertices, C = (uint64_t)max_cells;
     l.xy = take(V * 16);
@@ -155,6 +157,7 @@ static const void* coefs_of(const lbib_ctx* c) {
 
 static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     LatticeArgs a;
+    std::memset(&a, 0, sizeof(a));
     const Layout& L = c->L;
     a.fsrc = c->ws + L.f[src_buf];
     a.fdst = c->ws + L.f[1 - src_buf];
@@ -176,11 +179,16 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.ib = c->nC > 0 ? 1 : 0;
     a.fmask = c->at<uint32_t>(L.fmask);
     a.lmask = c->at<uint32_t>(L.lmask);
+    a.src = c->at<uint8_t>(L.src);
+    a.smask = c->at<uint32_t>(L.smask);
     return a;
 }
 
-static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) {
+// out_next: the prep is for the output step (vertex forces and labels are
+// written for the caller)
+static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
     IBArgs a;
+    std::memset(&a, 0, sizeof(a));
     const Layout& L = c->L;
     a.xy = c->at<double2>(L.xy);
     a.L0 = c->at<double>(L.L0);
@@ -202,18 +210,23 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) {
     a.do_move = move ? 1 : 0;
     a.do_prep = prep ? 1 : 0;
     a.do_mask = 1;
-    a.write_vforce = vforce ? 1 : 0;
+    a.write_vforce = out_next ? 1 : 0;
+    a.do_ids = out_next ? 1 : 0;
     a.do_force = 1;
     a.vbase = c->at<int2>(L.vbase);
     a.vfrac = c->at<float2>(L.vfrac);
     a.fmask = c->at<uint32_t>(L.fmask);
     a.lmask = c->at<uint32_t>(L.lmask);
+    a.src = c->at<uint8_t>(L.src);
+    a.smask = c->at<uint32_t>(L.smask);
     return a;
 }
 
 namespace lbib {
 LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out) { return lattice_args(c, src_buf, out); }
-IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool vforce) { return ib_args(c, move, prep, vforce); }
+IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
+    return ib_args(c, move, prep, out_next);
+}
 }  // namespace lbib
 
 // pdl: programmatic launch, allowed only when the previous launch on the
@@ -226,9 +239,10 @@ static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl 
                           coefs_of(c), c->block, c->stream, pdl && c->nC > 0);
 }
 
-static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool vforce, bool pdl = false) {
+static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next,
+                              bool pdl = false) {
     if (c->nC == 0) return cudaSuccess;
-    return launch_ib(c->p.precision, ib_args(c, move, prep, vforce), c->maxv_cell, c->stream,
+    return launch_ib(c->p.precision, ib_args(c, move, prep, out_next), c->maxv_cell, c->stream,
                      pdl);
 }
 
@@ -337,6 +351,8 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.src, 0, align_up(L.plane, 8), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.smask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -708,6 +724,8 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.src, 0, align_up(L.plane, 8), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.smask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_state");
     c->nV = hdr[0];

@@ -52,7 +52,7 @@ struct Layout {
     uint64_t f[2] = {0, 0}, g[2] = {0, 0};
     uint64_t force = 0, u = 0, rho = 0, phi = 0, id = 0, id_out = 0, force_out = 0;
     uint64_t xy = 0, L0 = 0, k = 0, vforce = 0, off = 0, pres = 0, srcf = 0, area = 0;
-    uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0;
+    uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0, src = 0, smask = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
 };
@@ -80,7 +80,10 @@ struct LatticeArgs {
     const void* gsrc;
     void* gdst;
     void* force;        // interleaved (fx, fy) per node, compute type; read then cleared
-    uint32_t* id;       // packed labels (cell << 4 | src bits), kOutside = none; read then cleared
+    uint32_t* id;       // packed labels (cell << 4 | src bits), kOutside = none; read then
+                        // cleared (written by the IB prep of an output step only); may be NULL
+    uint8_t* src;       // source bits of the node (OR over the cells containing it), one
+                        // byte per node; read then cleared
     void* u;            // interleaved (ux, uy) per node, compute type (written)
     void* rho;          // written when out
     void* phi;          // S planes, written when out
@@ -92,9 +95,11 @@ struct LatticeArgs {
     int out;            // write rho, phi, id_out, force_out
     int ib;             // read/clear force and labels
     // 1 bit per 4 consecutive nodes (node index >> 2): groups that received
-    // spread force / labels this step.  NULL = dense (read every node).
+    // spread force / labels / source bits this step.  fmask NULL = dense
+    // (read every node).
     uint32_t* fmask;
     uint32_t* lmask;
+    uint32_t* smask;
 };
 
 struct IBArgs {
@@ -118,6 +123,11 @@ struct IBArgs {
     float2* vfrac;      // FP32 path, optional: X - floor(X) per vertex
     uint32_t* fmask;    // optional: mark the groups that receive spread force
     uint32_t* lmask;    // optional: mark the groups that receive labels
+    void* src;          // optional source-bits plane (OR of the cells' bits): one byte per
+                        // node, rows 8-byte aligned; with src_words one uint32 per node
+    uint32_t* smask;    // optional: mark the groups that receive source bits
+    int do_ids;         // write the packed labels into `id` (else only source bits)
+    int src_words;
 };
 
 // shared memory of the FP32 per-cell IB work (one CTA per cell), as pointers
@@ -238,5 +248,5 @@ struct lbib_ctx {
 namespace lbib {
 // kernel arguments of a context (its buffers, parity src_buf)
 LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out);
-IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool vforce);
+IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next);
 }  // namespace lbib

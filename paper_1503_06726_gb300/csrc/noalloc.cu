@@ -6,7 +6,7 @@
 // or host code running inside a CUDA graph capture.  For them this file
 // provides lbib_step_noalloc(), which runs the same kernels as lbib_step() on
 // state buffers the caller already owns, and keeps every intermediate plane
-// (the second population buffer, the spread force, the cell labels, the
+// (the second population buffer, the spread force, the source bits, the
 // velocity and the diagnostic words) in one file-scope static device array
 // of kScratchBytes.  Every GPU that loads the library holds that array until
 // the process exits.
@@ -72,14 +72,14 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
         return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: missing buffer");
     if (n_steps == 0) return LBIB_OK;
 
-    // scratch plan: second population buffer, force, velocity, labels, diag
+    // scratch plan: second population buffer, force, velocity, source bits, diag
     const uint64_t P = (uint64_t)L.plane;
     const uint64_t o_f2 = 0;
     const uint64_t o_g2 = up256(o_f2 + 9 * P * L.es);
     const uint64_t o_force = up256(o_g2 + (uint64_t)5 * params->n_species * P * L.es);
     const uint64_t o_u = up256(o_force + 2 * P * L.cs);
-    const uint64_t o_id = up256(o_u + 2 * P * L.cs);
-    const uint64_t o_diag = up256(o_id + 4 * P);
+    const uint64_t o_src = up256(o_u + 2 * P * L.cs);
+    const uint64_t o_diag = up256(o_src + P);
     const uint64_t need = up256(o_diag + kDiagWords * 4);
     if (need > kScratchBytes)
         return set_thread_error(LBIB_E_WORKSPACE,
@@ -102,7 +102,7 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
 
     // the scratch keeps the previous call's contents: reset what must start empty
     e = cudaMemsetAsync(sc + o_force, 0, 2 * P * L.cs, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(sc + o_id, 0xFF, 4 * P, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc + o_src, 0, P, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc + o_diag, 0, kDiagWords * 4, st);
 
     void* fbuf[2] = {d_f, sc + o_f2};
@@ -110,7 +110,8 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     LatticeArgs la;
     std::memset(&la, 0, sizeof(la));
     la.force = sc + o_force;
-    la.id = reinterpret_cast<uint32_t*>(sc + o_id);
+    la.id = nullptr;  // no output step: only source bits are labelled
+    la.src = reinterpret_cast<uint8_t*>(sc + o_src);
     la.u = sc + o_u;
     la.diag = reinterpret_cast<uint32_t*>(sc + o_diag);
     la.nx = params->nx;
@@ -129,7 +130,9 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     ia.srcf = d_src_flag;
     ia.vforce = nullptr;
     ia.force = sc + o_force;
-    ia.id = la.id;
+    ia.id = nullptr;
+    ia.src = la.src;
+    ia.do_ids = 0;
     ia.u = la.u;
     ia.diag = la.diag;
     ia.nx = params->nx;

@@ -204,7 +204,17 @@ int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
         a.do_prep = 1;
         a.do_mask = 1;
         a.do_force = 0;
+        // packed labels (cell << 4 | bits, the lower cell index wins) ...
+        a.do_ids = 1;
         e = launch_ib(LBIB_FP32, a, kMaxVertsPerCell, st);
+        // ... then every containing cell ORs its source bits into the low bits
+        if (e == cudaSuccess) {
+            a.do_ids = 0;
+            a.id = nullptr;
+            a.src = d_id;
+            a.src_words = 1;
+            e = launch_ib(LBIB_FP32, a, kMaxVertsPerCell, st);
+        }
     }
     if (e == cudaSuccess) {
         labels_to_ids<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(
