@@ -209,8 +209,14 @@ int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
  *   d_phi0      batch*nx*ny floats (device): populations start at the rest
  *               equilibrium g_q = w_q phi0 (a warm start); NULL = cold start
  *               from zero
+ *               A warm-started tissue falls back to the cold start (populations
+ *               reset to zero, its step count running on) when its residual is
+ *               not finite, or when after 64 checks it is not below the residual
+ *               of its first check.
  *   d_phi_out   batch*nx*ny floats (device): phi of the final state
  *   steps_out, resid_out  host arrays of batch: steps taken, last residual
+ *   fallback_out  host array of batch int32 (may be NULL): 1 where the warm
+ *               start was abandoned for the cold one
  *   d_workspace, ws_bytes  device scratch of lbib_steady_workspace_size()
  *               bytes, 256-byte aligned, owned by the caller
  * FP32 storage and arithmetic.  Synchronises the stream.  Returns LBIB_OK,
@@ -220,7 +226,8 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
                       const double* D, const double* decay, const double* src_rate,
                       const float* d_phi0, double tol, int64_t max_steps, int32_t check_every,
                       float* d_phi_out, int64_t* steps_out, double* resid_out,
-                      void* d_workspace, uint64_t ws_bytes, void* cuda_stream);
+                      int32_t* fallback_out, void* d_workspace, uint64_t ws_bytes,
+                      void* cuda_stream);
 
 /* ---- Ensembles: many independent tissues advanced together -------------
  * An ensemble holds n tissues (each with its own lbib_params -- lattice

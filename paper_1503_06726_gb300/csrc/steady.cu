@@ -99,6 +99,10 @@ __global__ void __launch_bounds__(256) steady_residual(const float* G0, int64_t 
         const int64_t o = (int64_t)b * nx * ny + (int64_t)y * nx + x;
         d = fabsf(phi - phi_prev[o]);
         pm = fabsf(phi);
+        // a non-finite value counts as +inf (fmaxf would drop a NaN), so the
+        // tissue's residual becomes inf / inf = NaN and never passes the test
+        if (!isfinite(d)) d = INFINITY;
+        if (!isfinite(pm)) pm = INFINITY;
         phi_out[o] = phi;
     }
 #pragma unroll
@@ -113,21 +117,64 @@ __global__ void __launch_bounds__(256) steady_residual(const float* G0, int64_t 
     }
 }
 
-// per tissue: r = dmax / pmax; freeze converged tissues, reset the maxima
-__global__ void steady_decide(int batch, int64_t n, double tol, int* active, unsigned* dmax,
+// Warm-start fallback: a tissue started from a prediction goes back to the
+// cold start (g = 0) when its residual is not finite, or when after this many
+// checks it is not below the residual of its first check (the prediction has
+// not brought the relaxation closer); its step count runs on.
+constexpr int kFallbackChecks = 64;
+
+struct SteadyState {
+    int* active;
+    int* warm;        // still watched: on the warm start, fewer than kFallbackChecks checks
+    int* grow;        // checks so far (warm only)
+    int* fellback;    // the warm start was abandoned
+    int* reset;       // restart from g = 0 after this check
+    float* prevr;     // residual of the first check
+};
+
+// per tissue: r = dmax / pmax; freeze converged tissues, reset the maxima,
+// abandon failing warm starts
+__global__ void steady_decide(int batch, int64_t n, double tol, SteadyState S, unsigned* dmax,
                               unsigned* pmax, long long* steps, double* resid, int* n_active) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= batch || !active[b]) return;
+    if (b >= batch) return;
+    S.reset[b] = 0;
+    if (!S.active[b]) return;
     const float d = __uint_as_float(dmax[b]), p = __uint_as_float(pmax[b]);
     const double r = p > 0.f ? (double)d / (double)p : (d > 0.f ? INFINITY : 0.0);
     resid[b] = r;
     steps[b] = n;
     dmax[b] = 0u;
     pmax[b] = 0u;
+    if (S.warm[b]) {
+        const bool finite = isfinite(r);
+        const int c = ++S.grow[b];
+        if (c == 1) S.prevr[b] = (float)r;
+        if (!finite || (c >= kFallbackChecks && !(r < (double)S.prevr[b]))) {
+            S.warm[b] = 0;
+            S.fellback[b] = 1;
+            S.reset[b] = 1;
+            resid[b] = INFINITY;
+            return;
+        }
+        if (c >= kFallbackChecks) S.warm[b] = 0;  // the prediction has helped: stop watching
+    }
     if (r <= tol) {
-        active[b] = 0;
+        S.active[b] = 0;
         atomicSub(n_active, 1);
     }
+}
+
+// the cold start for the tissues that abandoned their warm start
+__global__ void steady_reset(int nx, int64_t pitch, int64_t plane, int64_t tstride,
+                             const int* reset, float* g) {
+    const int b = blockIdx.z;
+    if (!reset[b]) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= nx) return;
+    float* G = g + (int64_t)b * tstride;
+    for (int q = 0; q < 5; ++q) G[q * plane + (int64_t)y * pitch + x] = 0.f;
 }
 
 __global__ void steady_init(int batch, int nx, int ny, int64_t pitch, int64_t plane,
@@ -144,6 +191,7 @@ __global__ void steady_init(int batch, int nx, int ny, int64_t pitch, int64_t pl
 struct SteadyLayout {
     int64_t pitch, plane, tstride;
     uint64_t g[2], phi_prev, coef, active, dmax, pmax, steps, resid, nact, total;
+    uint64_t warm, grow, fellback, reset, prevr;
 };
 
 static SteadyLayout steady_layout(int nx, int ny, int batch) {
@@ -168,6 +216,11 @@ static SteadyLayout steady_layout(int nx, int ny, int batch) {
     L.steps = take(B * 8);
     L.resid = take(B * 8);
     L.nact = take(4);
+    L.warm = take(B * 4);
+    L.grow = take(B * 4);
+    L.fellback = take(B * 4);
+    L.reset = take(B * 4);
+    L.prevr = take(B * 4);
     L.total = o;
     return L;
 }
@@ -238,7 +291,8 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
                       const double* D, const double* decay, const double* src_rate,
                       const float* d_phi0, double tol, int64_t max_steps, int32_t check_every,
                       float* d_phi_out, int64_t* steps_out, double* resid_out,
-                      void* d_workspace, uint64_t ws_bytes, void* cuda_stream) {
+                      int32_t* fallback_out, void* d_workspace, uint64_t ws_bytes,
+                      void* cuda_stream) {
     if (nx < 8 || ny < 8 || batch < 1 || batch > 65535 || !d_src || !D || !decay ||
         !src_rate || !d_phi_out || !steps_out || !resid_out || check_every < 1 ||
         max_steps < 0 || !(tol >= 0.0))
@@ -265,6 +319,13 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
     long long* steps = reinterpret_cast<long long*>(ws + L.steps);
     double* resid = reinterpret_cast<double*>(ws + L.resid);
     int* nact = reinterpret_cast<int*>(ws + L.nact);
+    SteadyState S;
+    S.active = active;
+    S.warm = reinterpret_cast<int*>(ws + L.warm);
+    S.grow = reinterpret_cast<int*>(ws + L.grow);
+    S.fellback = reinterpret_cast<int*>(ws + L.fellback);
+    S.reset = reinterpret_cast<int*>(ws + L.reset);
+    S.prevr = reinterpret_cast<float*>(ws + L.prevr);
     std::vector<int> ones((size_t)batch, 1);
     std::vector<double> infs((size_t)batch, INFINITY);
     cudaError_t e = cudaMemcpyAsync(cf, coef.data(), coef.size() * 4, cudaMemcpyHostToDevice, st);
@@ -276,6 +337,14 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
     if (e == cudaSuccess) e = cudaMemsetAsync(dmax, 0, (size_t)batch * 4, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(pmax, 0, (size_t)batch * 4, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(nact, &batch, 4, cudaMemcpyHostToDevice, st);
+    // a warm start is watched for the fallback; a cold start is not
+    if (e == cudaSuccess && d_phi0)
+        e = cudaMemcpyAsync(S.warm, ones.data(), (size_t)batch * 4, cudaMemcpyHostToDevice, st);
+    else if (e == cudaSuccess)
+        e = cudaMemsetAsync(S.warm, 0, (size_t)batch * 4, st);
+    for (int* z : {S.grow, S.fellback, S.reset})
+        if (e == cudaSuccess) e = cudaMemsetAsync(z, 0, (size_t)batch * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.prevr, 0, (size_t)batch * 4, st);
     const dim3 blk(128), grd((nx + 127) / 128, ny, batch);
     if (e == cudaSuccess) {
         steady_init<<<grd, blk, 0, st>>>(batch, nx, ny, L.pitch, L.plane, L.tstride, d_phi0, g[0]);
@@ -313,7 +382,12 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
                 e = cudaGetLastError();
                 if (e == cudaSuccess) {
                     steady_decide<<<(batch + 127) / 128, 128, 0, st>>>(
-                        batch, n, tol, active, dmax, pmax, steps, resid, nact);
+                        batch, n, tol, S, dmax, pmax, steps, resid, nact);
+                    e = cudaGetLastError();
+                }
+                if (e == cudaSuccess && d_phi0) {
+                    steady_reset<<<grd, blk, 0, st>>>(nx, L.pitch, L.plane, L.tstride, S.reset,
+                                                      g[cur]);
                     e = cudaGetLastError();
                 }
             }
@@ -336,6 +410,9 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
         e = cudaMemcpyAsync(hs.data(), steps, (size_t)batch * 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(resid_out, resid, (size_t)batch * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && fallback_out)
+        e = cudaMemcpyAsync(fallback_out, S.fellback, (size_t)batch * 4, cudaMemcpyDeviceToHost,
+                            st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return set_thread_error(LBIB_E_CUDA, std::string("lbib_steady_solve: ") +

@@ -100,7 +100,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_label_cells": (ctypes.c_int, [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp]),
         "lbib_steady_workspace_size": (ctypes.c_int, [i32, i32, i32, ctypes.POINTER(u64)]),
         "lbib_steady_solve": (ctypes.c_int, [i32, i32, i32, vp, vp, vp, vp, vp, ctypes.c_double,
-                                             ctypes.c_int64, i32, vp, vp, vp, vp, u64, vp]),
+                                             ctypes.c_int64, i32, vp, vp, vp, vp, vp, u64, vp]),
         "lbib_ensemble_workspace_size": (ctypes.c_int, [i32, P, vp, vp, ctypes.POINTER(u64)]),
         "lbib_ensemble_create": (ctypes.c_int, [i32, P, vp, vp, vp, u64, vp, ctypes.POINTER(vp)]),
         "lbib_ensemble_tissue": (vp, [vp, i32]),
@@ -306,24 +306,28 @@ def lbib_steady_workspace_size(nx: int, ny: int, batch: int) -> int:
 
 def lbib_steady_solve(nx, ny, batch, d_src, D, decay, src_rate, d_phi0, tol, max_steps,
                       check_every, d_phi_out, d_workspace, ws_bytes, stream):
-    """Returns (steps, resid) host arrays; d_* are raw device addresses."""
+    """Returns (steps, resid, fallback) host arrays; d_* are raw device
+    addresses.  fallback[b] = 1 where a warm start was abandoned."""
     vp = ctypes.c_void_p
     D_, Dp = _p(D, np.float64)
     k_, kp = _p(decay, np.float64)
     s_, sp = _p(src_rate, np.float64)
     steps = np.zeros(batch, np.int64)
     resid = np.zeros(batch, np.float64)
+    fallback = np.zeros(batch, np.int32)
     _check(load().lbib_steady_solve(nx, ny, batch, vp(d_src), Dp, kp, sp, vp(d_phi0 or None),
                                     float(tol), int(max_steps), int(check_every), vp(d_phi_out),
                                     steps.ctypes.data_as(vp), resid.ctypes.data_as(vp),
-                                    vp(d_workspace), int(ws_bytes), vp(stream)))
-    return steps, resid
+                                    fallback.ctypes.data_as(vp), vp(d_workspace), int(ws_bytes),
+                                    vp(stream)))
+    return steps, resid, fallback
 
 
 def steady_solve(src, D, decay, src_rate, phi0=None, tol=1e-6, max_steps=200000,
-                 check_every=16, stream=None):
+                 check_every=16, stream=None, with_fallback=False):
     """Convenience wrapper on torch CUDA tensors: src (B, ny, nx) uint8,
-    phi0 (B, ny, nx) float32 or None.  Returns (phi, steps, resid)."""
+    phi0 (B, ny, nx) float32 or None.  Returns (phi, steps, resid), plus the
+    per-tissue fallback flags with with_fallback."""
     import torch
     B, ny, nx = src.shape
     ws_n = lbib_steady_workspace_size(nx, ny, B)
@@ -332,9 +336,11 @@ def steady_solve(src, D, decay, src_rate, phi0=None, tol=1e-6, max_steps=200000,
     st = (stream or torch.cuda.current_stream(src.device)).cuda_stream
     src = src.contiguous()
     p0 = None if phi0 is None else phi0.contiguous().float()
-    steps, resid = lbib_steady_solve(nx, ny, B, src.data_ptr(), D, decay, src_rate,
-                                     None if p0 is None else p0.data_ptr(), tol, max_steps,
-                                     check_every, out.data_ptr(), ws.data_ptr(), ws_n, st)
+    steps, resid, fb = lbib_steady_solve(nx, ny, B, src.data_ptr(), D, decay, src_rate,
+                                         None if p0 is None else p0.data_ptr(), tol, max_steps,
+                                         check_every, out.data_ptr(), ws.data_ptr(), ws_n, st)
+    if with_fallback:
+        return out, steps, resid, fb
     return out, steps, resid
 
 

@@ -10,7 +10,8 @@ only holds device memory):
   * ``train``: minibatch Adam on the neural operator
     (``lbib_nop_train_step``);
   * ``evaluate``: per tissue, steps and wall time to the residual from a cold
-    start and from the network's prediction (inference time included).
+    start and from the network's prediction (inference time included), and
+    whether the solve abandoned the prediction for the cold start.
 """
 from __future__ import annotations
 
@@ -139,14 +140,15 @@ def evaluate(net: "lbib.NeuralOperator", items, H: int = 256, W: int = 256, tol:
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         p0 = net.forward(m, sr, D[i:i + 1], k[i:i + 1], s[i:i + 1])
-        pw, sw, rw = lbib.steady_solve(sr, D[i:i + 1], k[i:i + 1], s[i:i + 1], phi0=p0,
-                                       tol=tol, max_steps=max_steps)
+        pw, sw, rw, fb = lbib.steady_solve(sr, D[i:i + 1], k[i:i + 1], s[i:i + 1], phi0=p0,
+                                           tol=tol, max_steps=max_steps, with_fallback=True)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         a = pc.cpu().numpy()
         b = pw.cpu().numpy()
         rows.append({"cold_steps": int(sc[0]), "warm_steps": int(sw[0]),
                      "cold_s": t1 - t0, "warm_s": t2 - t1,
+                     "fallback": int(fb[0]),
                      "gap": float(np.abs(a - b).max() / max(np.abs(a).max(), 1e-30)),
                      "pred_err": float(np.abs(p0.cpu().numpy() - a).max() /
                                        max(np.abs(a).max(), 1e-30))})
@@ -168,4 +170,5 @@ def summarize(rows):
         "step_ratio_mean": float((cs / np.maximum(ws, 1)).mean()),
         "pred_rel_linf_median": float(np.median(pe)),
         "warm_faster_fraction": float((wt < ct).mean()),
+        "fallbacks": int(sum(r["fallback"] for r in rows)),
     }

@@ -112,6 +112,48 @@ def test_steady_converges_like_oracle_and_warm_start(lb, orc):
     assert rel(phi_w.cpu().numpy(), np.stack(refs)) < bound
 
 
+def test_warm_start_falls_back_on_a_nonfinite_prediction(lb, orc):
+    """A prediction holding NaN or inf is abandoned for the cold start at the
+    first residual check (16 steps) and then relaxes exactly like a cold run
+    started 16 steps later; a sound prediction is kept."""
+    import torch
+    Ps, srcs, src, D, k, s = _batch([1008, 1009, 1010], orc)
+    cold, steps_c, resid_c = lb.steady_solve(src, D, k, s, tol=1e-6, max_steps=100000)
+    phi0 = cold.clone()
+    phi0[1] = float("nan")
+    phi0[2, 5:9, 5:9] = float("inf")
+    warm, steps_w, resid_w, fb = lb.steady_solve(src, D, k, s, phi0=phi0, tol=1e-6,
+                                                 max_steps=100000, with_fallback=True)
+    assert list(fb) == [0, 1, 1]
+    assert (resid_w <= 1e-6).all()
+    assert steps_w[0] < steps_c[0] // 2
+    for b in (1, 2):
+        assert steps_w[b] == steps_c[b] + 16
+        assert torch.equal(warm[b], cold[b])
+    _, _, _, fb_cold = lb.steady_solve(src, D, k, s, tol=1e-6, max_steps=100000,
+                                       with_fallback=True)
+    assert not fb_cold.any()
+
+
+def test_cold_and_warm_within_residual_bound_of_converged_field(lb, orc):
+    """The true error at r <= tol: a contraction whose slowest mode decays by
+    (1 - decay) per step ends within r / decay of its fixed point.  Reference:
+    the FP64 oracle relaxed to r <= 1e-12."""
+    import torch
+    P, T = li.steady_tissue(1011, n=64)
+    P.decay[0] = 5e-3
+    _, src = orc.rasterize(P.nx, P.ny, P.bc_y, T.cell_off, T.xy, T.src_flag)
+    ref, nref, rref, _ = orc.steady(P, src, tol=1e-12, max_steps=200000)
+    assert rref <= 1e-12
+    dsrc = torch.as_tensor(src[None], device="cuda")
+    args = ([P.D[0]], [P.decay[0]], [P.src_rate[0]])
+    cold, _, rc = lb.steady_solve(dsrc, *args, tol=1e-6, max_steps=200000)
+    warm, _, rw = lb.steady_solve(dsrc, *args, phi0=0.5 * cold, tol=1e-6, max_steps=200000)
+    bound = 1e-6 / P.decay[0] + 2e-5   # plus the FP32 rounding floor
+    assert rel(cold[0].cpu().numpy(), ref[0]) < bound
+    assert rel(warm[0].cpu().numpy(), ref[0]) < bound
+
+
 def test_steady_uniform_source_closed_form(lb):
     """All nodes are sources: the steady field is src_rate / decay."""
     import torch
