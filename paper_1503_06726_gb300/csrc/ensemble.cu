@@ -46,6 +46,7 @@ struct EnsArgs {
     const int* item_pfx;  // n + 1 prefix sums of lattice items
     const int* cell_pfx;  // n + 1 prefix sums of cells
     int n, n_steps, nodes_per_item, total_items, total_cells;
+    int maxv;             // vertex arrays of each cell slot in shared memory
     unsigned* bar;        // [0] arrival count, [1] generation, [2] error flag
     unsigned nblocks;     // CTAs the barrier waits for
 };
@@ -98,21 +99,36 @@ __device__ __forceinline__ int find_tissue(const int* pfx, int n, int item) {
     return lo;
 }
 
+// The IB phase runs two cells at a time per CTA, one per 128-thread half with
+// its own named barrier and its own slot of dynamic shared memory (fixed part
+// + maxv vertices): the per-cell work is a chain of dependent steps, so more
+// cells in flight per SM shorten the phase.
+constexpr int kEnsCellThreads = kIBThreads / 2;
+
+__host__ __device__ inline size_t ens_cell_smem(int maxv) {
+    return (size_t)kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
+}
+
 template <int S, int FORCING>
 __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
-    __shared__ IBSmem32 sm;
+    extern __shared__ __align__(16) unsigned char ens_smem[];
     __shared__ TissueDev td;
     __shared__ int s_t;
     const int tid = threadIdx.x;
+    const int half = tid / kEnsCellThreads, htid = tid % kEnsCellThreads;
     IBShared32 view;
-    view.sx = sm.sx;
-    view.sb = sm.sb;
-    view.sf = sm.sf;
-    view.rowcnt = sm.rowcnt;
-    view.thr = sm.thr;
-    view.sbox = sm.sbox;
-    view.s_flag = &sm.s_flag;
-    view.maxv = kMaxVertsPerCell;
+    {
+        unsigned char* base = ens_smem + (size_t)half * ens_cell_smem(e.maxv);
+        int* fixed = reinterpret_cast<int*>(base);
+        view.rowcnt = fixed;
+        view.thr = fixed + kMaxRows;
+        view.sbox = view.thr + kMaxRows * kMaxCross;
+        view.s_flag = view.sbox + 4;
+        view.sx = reinterpret_cast<double2*>(base + kIBSmemFixed);
+        view.sb = reinterpret_cast<int2*>(view.sx + e.maxv);
+        view.sf = reinterpret_cast<float2*>(view.sb + e.maxv);
+        view.maxv = e.maxv;
+    }
     if (tid == 0) s_t = -1;
 
     auto load_tissue = [&](int t) {
@@ -128,15 +144,14 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
     };
 
     auto ib_phase = [&](int move, int prep, int vforce) {
-        for (int item = blockIdx.x; item < e.total_cells; item += gridDim.x) {
+        for (int item = blockIdx.x * 2 + half; item < e.total_cells; item += gridDim.x * 2) {
             const int t = find_tissue(e.cell_pfx, e.n, item);
-            load_tissue(t);
-            IBArgs a = td.ia;
+            IBArgs a = e.tis[t].ia;
             a.do_move = move;
             a.do_prep = prep;
             a.write_vforce = vforce;
             a.do_ids = vforce;  // the prep of the output step writes the labels too
-            ib_cell_f32<kIBThreads, false>(a, item - e.cell_pfx[t], view);
+            ib_cell_f32<kEnsCellThreads, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
         }
     };
 
@@ -220,6 +235,7 @@ struct lbib_ensemble {
     int blocks_per_sm = 0;  // 0 = as many as fit
     int max_blocks_per_sm = 0;
     int n_sms = 0;
+    int maxv = 0;           // vertex slots per cell in shared memory (largest cell)
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     bool graph_ok = true;
     std::string err;
@@ -244,7 +260,32 @@ static uint64_t ens_region_bytes(int n) {
 }
 
 // Build the per-tissue table and prefix sums (host), upload them.
+// Shared memory per CTA follows the largest cell of the ensemble; when it
+// changes, the CTAs that fit per SM and the captured graphs change with it.
+static cudaError_t ens_fit_cells(lbib_ensemble* e) {
+    int mv = 8;
+    for (auto* c : e->ctx) mv = std::max(mv, c->maxv_cell);
+    mv = std::min((mv + 7) / 8 * 8, kMaxVertsPerCell);
+    if (mv == e->maxv && e->max_blocks_per_sm > 0) return cudaSuccess;
+    const size_t smem = 2 * ens_cell_smem(mv);
+    const void* k = (const void*)pick_kernel(e->S, e->forcing);
+    cudaError_t er = cudaSuccess;
+    if (smem > 48 * 1024)
+        er = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    if (er == cudaSuccess)
+        er = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kIBThreads, smem);
+    if (er != cudaSuccess) return er;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    ens_drop_graphs(e);
+    e->maxv = mv;
+    e->max_blocks_per_sm = per;
+    return cudaSuccess;
+}
+
 static cudaError_t ens_upload(lbib_ensemble* e, int* total_items, int* total_cells) {
+    cudaError_t fe = ens_fit_cells(e);
+    if (fe != cudaSuccess) return fe;
     std::vector<TissueDev> tab((size_t)e->n);
     std::vector<int> ipfx((size_t)e->n + 1, 0), cpfx((size_t)e->n + 1, 0);
     for (int t = 0; t < e->n; ++t) {
@@ -288,6 +329,7 @@ static EnsArgs ens_args(lbib_ensemble* e, int n_steps, int total_items, int tota
     a.total_cells = total_cells;
     a.bar = reinterpret_cast<unsigned*>(e->ws + e->bar_off);
     a.nblocks = nblocks;
+    a.maxv = e->maxv;
     return a;
 }
 
@@ -304,7 +346,7 @@ static cudaError_t ens_launch(lbib_ensemble* e, const EnsArgs& a, unsigned grid,
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kIBThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = 2 * ens_cell_smem(a.maxv);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -381,9 +423,7 @@ int lbib_ensemble_create(int32_t n, const lbib_params* params, const int32_t* ma
     int dev = 0;
     cudaError_t er = cudaGetDevice(&dev);
     if (er == cudaSuccess) er = cudaDeviceGetAttribute(&e->n_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (er == cudaSuccess)
-        er = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &e->max_blocks_per_sm, (const void*)pick_kernel(e->S, e->forcing), kIBThreads, 0);
+    if (er == cudaSuccess) er = ens_fit_cells(e);
     if (er == cudaSuccess) er = cudaMemsetAsync(e->ws + e->bar_off, 0, 256, e->stream);
     if (er == cudaSuccess) er = cudaStreamSynchronize(e->stream);
     if (er != cudaSuccess || e->max_blocks_per_sm < 1) {

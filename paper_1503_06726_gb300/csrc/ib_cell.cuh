@@ -171,9 +171,9 @@ __device__ __forceinline__ void label_node(const IBArgs& a, int64_t node, uint32
 
 static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, const double2* sx,
                                          const int* rowcnt, int* thr, bool scan_ok, int I0,
-                                         int J0, int rows, int cols) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nwarps = blockDim.x >> 5;
+                                         int J0, int rows, int cols, int tid, int nthreads) {
+    const int lane = tid & 31, warp = tid >> 5;
+    const int nwarps = nthreads >> 5;
     // source bits go to the source plane only when the caller gave one
     const uint32_t cbits = (uint32_t)(a.srcf[c] & 0xF);
     const uint32_t bits = a.src ? cbits : 0u;
@@ -256,7 +256,7 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
     } else {
         // brute force: the same predicate per node over all edges
         if (tid == 0) raise_flag(a.diag, kDiagRasterSlow);
-        for (int e = tid; e < rows * cols; e += blockDim.x) {
+        for (int e = tid; e < rows * cols; e += nthreads) {
             const int r = e / cols, cc = e % cols, J = J0 + r;
             if (a.bc_y && (J < 0 || J >= a.ny)) continue;
             const double xn = (double)(I0 + cc), yn = (double)J;
@@ -277,6 +277,14 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
             }
         }
     }
+}
+
+// Barrier of the NT threads that work on one cell: `bar` 0 with a CTA of NT
+// threads, or a named barrier of its own for each NT-thread part of a larger
+// CTA that works on several cells at once.
+template <int NT>
+__device__ __forceinline__ void cell_sync(int bar) {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "n"(NT) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -324,14 +332,16 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
     return make_float2(sc * d.x, sc * d.y);
 }
 
-// The work of one cell by one CTA of NT threads.  Callers that run several
-// cells through the same CTA call it again for the next cell; the first
-// barrier protects the shared arrays of the previous call.  GRIDDEP: the
+// The work of one cell by NT threads (thread index tid, barrier bar: the
+// whole CTA, or one part of it).  Callers that run several cells through the
+// same threads call it again for the next cell; the first barrier protects the
+// shared arrays of the previous call.  GRIDDEP: the
 // caller is a kernel of its own (programmatic launch after a lattice launch):
 // the cell's constant data and its vertex state (written by the IB launch two
 // launches back) are loaded through L2 before the wait, the u plane after it.
 template <int NT, bool GRIDDEP>
-static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) {
+static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, int tid,
+                                   int bar) {
     static_assert(NT >= kMaxRows && NT % 64 == 0, "CTA size");
     constexpr int kIBThreads = NT;
     double2* sx = S.sx;
@@ -341,11 +351,11 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
     int* thr = S.thr;
     int* sbox = S.sbox;
     int& s_flag = *S.s_flag;
-    __syncthreads();
+    cell_sync<NT>(bar);
 
     const int v0 = __ldcg(a.off + c);
     const int n = __ldcg(a.off + c + 1) - v0;
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int lane = tid & 31;
     if (n > S.maxv) {  // cannot happen for callers that size maxv from the cells
         if (GRIDDEP) {
             griddep_wait();
@@ -464,7 +474,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
     jlo = __reduce_min_sync(0xffffffffu, jlo);
     jhi = __reduce_max_sync(0xffffffffu, jhi);
     finite = __all_sync(0xffffffffu, finite);
-    __syncthreads();
+    cell_sync<NT>(bar);
     if (lane == 0) {
         atomicMin(&sbox[0], ilo);
         atomicMax(&sbox[1], ihi);
@@ -472,7 +482,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
         atomicMax(&sbox[3], jhi);
         if (!finite) s_flag = 2;
     }
-    __syncthreads();
+    cell_sync<NT>(bar);
     // columns: floor(x) over the vertices, widened by one on each side (the
     // fractions are FP32); rows: every J with min ceil(y) <= J < max ceil(y),
     // exactly the rows some edge crosses
@@ -581,8 +591,8 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S) 
         }
     }
     if (!labels) return;  // uniform over the CTA
-    __syncthreads();
-    fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols);
+    cell_sync<NT>(bar);
+    fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols, tid, NT);
 }
 
 }  // namespace lbib
