@@ -168,6 +168,24 @@ def recorded_traffic(workload_name: str):
     return None
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over the ranks of the process group (x itself without
+    one): every rank's time counts, the job ends with its slowest rank."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(world: int, nodes: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput of `world` independent replicas of `nodes`
+    lattice nodes each, all advanced `steps` steps in `seconds` (the max over
+    ranks)."""
+    return world * nodes * steps / seconds / 1e6
+
+
 def oracle_sample(w, target_s: float, max_steps: int, threads: int | None = None):
     """Time the FP64 oracle on the workload: whole coupled steps until
     target_s of CPU time or max_steps.  Returns (mlups, steps, seconds, cores)."""
@@ -224,11 +242,8 @@ def run_ensemble(args, rank, world, dist):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop() if clocks else None
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ms, dist, dev)
+    value = replica_mlups(world, N, args.steps, ms * 1e-3)
     bpn = alg_bytes_per_node("fp32", ws[0].params.n_species)
     achieved = bpn * N * args.steps / (ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
@@ -256,9 +271,9 @@ def run_ensemble(args, rank, world, dist):
                                    vp(aa.data_ptr()), None, None, None)
             if rc:
                 raise RuntimeError(lbib.lbib_last_error(ens.ctx[t]))
-    t_e2e = time.perf_counter() - t0
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
     cells = sum(w.tissue.n_cells for w in ws)
-    e2e = {"value": world * N * e2e_steps / t_e2e / 1e6, "unit": UNIT,
+    e2e = {"value": replica_mlups(world, N, e2e_steps, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": cells * 8, "d2h_bytes_per_step": cells * 8,
            "steps": e2e_steps,
            "api": "per tissue lbib_set_cell_params, lbib_ensemble_step(1), per tissue "
@@ -476,12 +491,9 @@ def run_gb300(args, rank, world, dist):
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop() if clocks else None
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     ms_per_step = ms / args.steps
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    value = replica_mlups(world, N, args.steps, ms * 1e-3)
 
     # profiled pass: the same steps, every launch bracketed by events
     n_prof = max(10, min(args.steps, 400))
@@ -517,12 +529,8 @@ def run_gb300(args, rank, world, dist):
                                      None)
         if rc:
             raise RuntimeError(lbib.lbib_last_error(sim.ctx))
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * N * e2e_steps / t_e2e / 1e6, "unit": UNIT,
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": replica_mlups(world, N, e2e_steps, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": T.n_cells * 9, "d2h_bytes_per_step": T.n_vertices * 16 + T.n_cells * 8,
            "steps": e2e_steps,
            "api": "lbib_set_cell_params + lbib_step(1) + lbib_get_fields(X|AREA) per step"}
