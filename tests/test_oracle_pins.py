@@ -337,6 +337,28 @@ def test_poiseuille(orc, tau):
         assert np.abs(u - exact).max() < 2e-2 * exact.max()
 
 
+def test_poiseuille_paper_forcing(orc):
+    """The paper's force term 3 w v.F with u = sum f v / rho (no half-force
+    shift): the same discrete curvature -g/nu, and at tau = 1/2 + sqrt(3)/4
+    the measured u plus half the force equals the closed-form parabola."""
+    nx, ny, gF = 4, 16, 1e-6
+    tau = 0.5 + math.sqrt(3.0) / 4.0
+    p = _params(nx, ny, tau=tau, bc=li.BC_WALLS, forcing=1)
+    nu = (tau - 0.5) / 3
+    f, g = orc.equilibrium_state(p)
+    fx = np.full((ny, nx), gF)
+    fy = np.zeros((ny, nx))
+    for _ in range(8000):
+        f, g, rho, ux, uy, _ = orc.lattice_step(p, f, g, fx, fy)
+    u = ux[:, 0]
+    y = np.arange(ny)
+    exact = gF / (2 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    curv = u[2:] - 2 * u[1:-1] + u[:-2]
+    assert np.allclose(curv, -gF / nu, rtol=1e-8)
+    assert np.abs(u + 0.5 * gF / rho[:, 0] - exact).max() < 1e-6 * exact.max()
+    assert np.abs(u - exact).max() > 1e-3 * exact.max()   # the half-force shift is missing
+
+
 def _taylor_green_error(orc, N, tau=0.8, u0=1e-3):
     p = _params(N, N, tau=tau)
     nu = (tau - 0.5) / 3
