@@ -204,6 +204,35 @@ def test_config2_full_size_first_steps(lb, orc):
     assert np.abs(got["xy"] - ref.xy).max() < 1e-6
 
 
+def test_config2_full_size_graph_path(lb, orc):
+    """The benchmarked 1024^2 configuration over 7 steps: two two-step CUDA
+    graph chunks with programmatic launches between the kernels, then the
+    single-launch tail, against the FP64 oracle within the FP32 bounds."""
+    w = li.config2()
+    ref = orc.run(w.params, w.tissue, 7)
+    got = gpu_run(lb, w, 7, lb.LBIB_FP32, which=1 | 2 | 4 | 8)
+    assert max(rel(got["ux"], ref.ux), rel(got["uy"], ref.uy)) < 1e-4
+    assert rel(got["phi"], ref.phi) < 1e-5
+    assert np.abs(got["xy"] - ref.xy).max() < 1e-6
+
+
+def test_config3_full_size_fp32_fp16(lb, orc):
+    """The 4096^2 precision-sweep tissue (9,801 cells, the 128-thread IB
+    kernel) over 5 steps (one graph chunk) in FP32 and FP16 storage against
+    the FP64 oracle: labels bit-exact after the first step, fields within the
+    FP32 and FP16 bounds."""
+    w = li.config3()
+    ref1 = orc.run(w.params, w.tissue, 1)
+    got1 = gpu_run(lb, w, 1, lb.LBIB_FP32, which=32)
+    assert np.array_equal(got1["id"], ref1.id)
+    ref = orc.run(w.params, w.tissue, 5)
+    for prec, tu, tp, tx in ((lb.LBIB_FP32, 1e-4, 1e-5, 1e-6), (lb.LBIB_FP16, 3e-2, 1e-2, 1e-3)):
+        got = gpu_run(lb, w, 5, prec, which=1 | 2 | 4 | 8)
+        assert max(rel(got["ux"], ref.ux), rel(got["uy"], ref.uy)) < tu
+        assert rel(got["phi"], ref.phi) < tp
+        assert np.abs(got["xy"] - ref.xy).max() < tx
+
+
 # ------------------------------------------------------------------ state, errors
 def test_state_roundtrip_bitwise(lb):
     w = li.config1()
