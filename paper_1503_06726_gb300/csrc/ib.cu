@@ -236,6 +236,9 @@ cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_
     int maxv = maxv_cell < 3 ? 3 : (maxv_cell > kMaxVertsPerCell ? kMaxVertsPerCell : maxv_cell);
     maxv = (maxv + 7) / 8 * 8;
     const size_t smem = kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
+    if (maxv <= 64 && a.n_cells >= 2048)
+        return launch_kernel(ib_cell_kernel_f32<64>, dim3(a.n_cells), dim3(64), smem, s, pdl, a,
+                             maxv);
     if (maxv <= 128 && a.n_cells >= 2048)
         return launch_kernel(ib_cell_kernel_f32<128>, dim3(a.n_cells), dim3(128), smem, s, pdl, a,
                              maxv);

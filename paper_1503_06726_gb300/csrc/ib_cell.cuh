@@ -342,7 +342,7 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 template <int NT, bool GRIDDEP>
 static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, int tid,
                                    int bar) {
-    static_assert(NT >= kMaxRows && NT % 64 == 0, "CTA size");
+    static_assert(NT % 64 == 0, "CTA size");
     constexpr int kIBThreads = NT;
     double2* sx = S.sx;
     int2* sb = S.sb;
@@ -365,7 +365,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
         return;
     }
 
-    if (tid < kMaxRows) rowcnt[tid] = 0;
+    for (int r = tid; r < kMaxRows; r += NT) rowcnt[r] = 0;
     if (tid == 0) {
         sbox[0] = INT_MAX; sbox[1] = INT_MIN; sbox[2] = INT_MAX; sbox[3] = INT_MIN;
         s_flag = 0;
