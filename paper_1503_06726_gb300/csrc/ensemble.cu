@@ -47,6 +47,7 @@ struct EnsArgs {
     const int* cell_pfx;  // n + 1 prefix sums of cells
     int n, n_steps, nodes_per_item, total_items, total_cells;
     int maxv;             // vertex arrays of each cell slot in shared memory
+    int cell_threads;     // threads per cell in the IB phase (64 or 128)
     unsigned* bar;        // [0] arrival count, [1] generation, [2] error flag
     unsigned nblocks;     // CTAs the barrier waits for
 };
@@ -99,11 +100,12 @@ __device__ __forceinline__ int find_tissue(const int* pfx, int n, int item) {
     return lo;
 }
 
-// The IB phase runs two cells at a time per CTA, one per 128-thread half with
-// its own named barrier and its own slot of dynamic shared memory (fixed part
-// + maxv vertices): the per-cell work is a chain of dependent steps, so more
-// cells in flight per SM shorten the phase.
-constexpr int kEnsCellThreads = kIBThreads / 2;
+// The IB phase runs several cells at a time per CTA: two per CTA (128-thread
+// halves), or four (64-thread quarters) when no cell has more than 64
+// vertices, each group with its own named barrier and its own slot of dynamic
+// shared memory (fixed part + maxv vertices).  The per-cell work is a chain of
+// dependent steps, so more cells in flight per SM shorten the phase.
+__host__ __device__ inline int ens_cell_threads(int maxv) { return maxv <= 64 ? 64 : 128; }
 
 __host__ __device__ inline size_t ens_cell_smem(int maxv) {
     return (size_t)kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
@@ -115,7 +117,8 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
     __shared__ TissueDev td;
     __shared__ int s_t;
     const int tid = threadIdx.x;
-    const int half = tid / kEnsCellThreads, htid = tid % kEnsCellThreads;
+    const int cgroups = kIBThreads / e.cell_threads;
+    const int half = tid / e.cell_threads, htid = tid % e.cell_threads;
     IBShared32 view;
     {
         unsigned char* base = ens_smem + (size_t)half * ens_cell_smem(e.maxv);
@@ -144,14 +147,18 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
     };
 
     auto ib_phase = [&](int move, int prep, int vforce) {
-        for (int item = blockIdx.x * 2 + half; item < e.total_cells; item += gridDim.x * 2) {
+        for (int item = blockIdx.x * cgroups + half; item < e.total_cells;
+             item += gridDim.x * cgroups) {
             const int t = find_tissue(e.cell_pfx, e.n, item);
             IBArgs a = e.tis[t].ia;
             a.do_move = move;
             a.do_prep = prep;
             a.write_vforce = vforce;
             a.do_ids = vforce;  // the prep of the output step writes the labels too
-            ib_cell_f32<kEnsCellThreads, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
+            if (e.cell_threads == 64)
+                ib_cell_f32<64, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
+            else
+                ib_cell_f32<128, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
         }
     };
 
@@ -267,7 +274,7 @@ static cudaError_t ens_fit_cells(lbib_ensemble* e) {
     for (auto* c : e->ctx) mv = std::max(mv, c->maxv_cell);
     mv = std::min((mv + 7) / 8 * 8, kMaxVertsPerCell);
     if (mv == e->maxv && e->max_blocks_per_sm > 0) return cudaSuccess;
-    const size_t smem = 2 * ens_cell_smem(mv);
+    const size_t smem = (size_t)(kIBThreads / ens_cell_threads(mv)) * ens_cell_smem(mv);
     const void* k = (const void*)pick_kernel(e->S, e->forcing);
     cudaError_t er = cudaSuccess;
     if (smem > 48 * 1024)
@@ -330,6 +337,7 @@ static EnsArgs ens_args(lbib_ensemble* e, int n_steps, int total_items, int tota
     a.bar = reinterpret_cast<unsigned*>(e->ws + e->bar_off);
     a.nblocks = nblocks;
     a.maxv = e->maxv;
+    a.cell_threads = ens_cell_threads(e->maxv);
     return a;
 }
 
@@ -346,7 +354,7 @@ static cudaError_t ens_launch(lbib_ensemble* e, const EnsArgs& a, unsigned grid,
     std::memset(&cfg, 0, sizeof(cfg));
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kIBThreads);
-    cfg.dynamicSmemBytes = 2 * ens_cell_smem(a.maxv);
+    cfg.dynamicSmemBytes = (size_t)(kIBThreads / a.cell_threads) * ens_cell_smem(a.maxv);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
