@@ -135,7 +135,11 @@ int lbib_set_cells(lbib_ctx* ctx, int32_t n_cells, const int32_t* cell_off, cons
 
 /* Update the per-cell pressure and source flags of the current cells (the
  * inputs a host-side biology step changes between time steps).  Either
- * pointer may be NULL to keep that array. */
+ * pointer may be NULL to keep that array.  The arrays are copied into a
+ * pinned staging buffer owned by the context and uploaded asynchronously on
+ * the context stream, ordered before the next step; the caller may reuse
+ * them as soon as the call returns.  The call waits only for the previous
+ * call's upload to have left the staging buffer. */
 int lbib_set_cell_params(lbib_ctx* ctx, const double* pressure, const uint8_t* src_flag);
 
 /* Set the populations of species s to the rest equilibrium g_q = w_q phi of

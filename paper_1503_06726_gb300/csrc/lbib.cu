@@ -355,8 +355,12 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.smask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && max_cells > 0)
+        e = cudaHostAlloc(reinterpret_cast<void**>(&c->hstage), (size_t)max_cells * 9,
+                          cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->hstage_done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete c;
+        lbib_destroy(c);
         return cuda_fail(nullptr, e, "lbib_create");
     }
     *out = c;
@@ -439,15 +443,26 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
 
 int lbib_set_cell_params(lbib_ctx* c, const double* pressure, const uint8_t* src_flag) {
     if (!c) return LBIB_E_PARAM;
+    if (c->nC == 0 || (!pressure && !src_flag)) return LBIB_OK;
+    // the host arrays are copied into the context's pinned staging buffer
+    // (free again once the previous upload has run) and uploaded
+    // asynchronously on the context stream: the caller may reuse them at once
     cudaError_t e = cudaSuccess;
-    if (pressure && c->nC > 0)
-        e = cudaMemcpyAsync(c->ws + c->L.pres, pressure, (size_t)c->nC * 8, cudaMemcpyHostToDevice,
+    if (c->hstage_pending) e = cudaEventSynchronize(c->hstage_done);
+    const size_t nc = (size_t)c->nC;
+    if (e == cudaSuccess && pressure) {
+        std::memcpy(c->hstage, pressure, nc * 8);
+        e = cudaMemcpyAsync(c->ws + c->L.pres, c->hstage, nc * 8, cudaMemcpyHostToDevice,
                             c->stream);
-    if (e == cudaSuccess && src_flag && c->nC > 0)
-        e = cudaMemcpyAsync(c->ws + c->L.srcf, src_flag, (size_t)c->nC, cudaMemcpyHostToDevice,
+    }
+    if (e == cudaSuccess && src_flag) {
+        std::memcpy(c->hstage + nc * 8, src_flag, nc);
+        e = cudaMemcpyAsync(c->ws + c->L.srcf, c->hstage + nc * 8, nc, cudaMemcpyHostToDevice,
                             c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->hstage_done, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_cell_params");
+    c->hstage_pending = true;
     return LBIB_OK;
 }
 
@@ -556,94 +571,81 @@ int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double
         return fail(c, LBIB_E_STATE, "no completed step since the last create or reset");
     if ((which & (LBIB_ID | LBIB_FORCE)) && c->nC == 0)
         return fail(c, LBIB_E_STATE, "labels and spread force need cells");
+    if ((which & LBIB_VFORCE) && c->nV > 0 && !c->vforce_valid)
+        return fail(c, LBIB_E_STATE, "no vertex forces computed yet");
     const Layout& L = c->L;
     const int nx = c->p.nx, ny = c->p.ny, S = c->p.n_species;
     const size_t N = (size_t)nx * ny;
     cudaError_t e = cudaSuccess;
-    // Each requested plane is copied raw (storage pitch, compute type) to host
-    // memory and converted there, so no device scratch is needed.
-    std::vector<char> raw;
-    auto fetch = [&](uint64_t off, size_t bytes) -> const char* {
+    // Every copy is enqueued first and the stream synchronised once.  Lattice
+    // planes are copied raw (storage pitch, compute type) to host memory and
+    // converted there, so no device scratch is needed; vertex data and areas
+    // go straight to the caller's buffers.
+    std::vector<char> r_rho, r_u, r_phi, r_id, r_force;
+    auto fetch = [&](std::vector<char>& raw, uint64_t off, size_t bytes) {
         raw.resize(bytes);
-        e = cudaMemcpyAsync(raw.data(), c->ws + off, bytes, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        return raw.data();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(raw.data(), c->ws + off, bytes, cudaMemcpyDeviceToHost, c->stream);
     };
-    auto val = [&](const char* base, int64_t idx) -> double {
-        return c->L.cs == 8 ? reinterpret_cast<const double*>(base)[idx]
-                            : (double)reinterpret_cast<const float*>(base)[idx];
-    };
-    if (which & LBIB_RHO) {
-        const char* b = fetch(L.rho, (size_t)L.plane * L.cs);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) rho[(size_t)y * nx + x] = val(b, (int64_t)y * L.pitch + x);
+    if (which & LBIB_RHO) fetch(r_rho, L.rho, (size_t)L.plane * L.cs);
+    if (which & LBIB_U) fetch(r_u, L.u, (size_t)2 * L.plane * L.cs);
+    if ((which & LBIB_PHI) && S > 0) fetch(r_phi, L.phi, (size_t)S * L.plane * L.cs);
+    if (which & LBIB_ID) fetch(r_id, L.id_out, (size_t)L.plane * 4);
+    if (which & LBIB_FORCE) fetch(r_force, L.force_out, (size_t)2 * L.plane * L.cs);
+    if ((which & LBIB_X) && c->nV > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(xy, c->ws + L.xy, (size_t)c->nV * 16, cudaMemcpyDeviceToHost, c->stream);
+    if ((which & LBIB_VFORCE) && c->nV > 0 && e == cudaSuccess)
+        e = cudaMemcpyAsync(vforce, c->ws + L.vforce, (size_t)c->nV * 16, cudaMemcpyDeviceToHost,
+                            c->stream);
+    if ((which & LBIB_AREA) && c->nC > 0 && e == cudaSuccess) {
+        e = launch_areas(c->at<double2>(L.xy), c->at<int32_t>(L.off), c->nC, c->at<double>(L.area),
+                         c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(area, c->ws + L.area, (size_t)c->nC * 8, cudaMemcpyDeviceToHost,
+                                c->stream);
     }
-    if (which & LBIB_U) {
-        const char* b = fetch(L.u, (size_t)2 * L.plane * L.cs);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    // the device-side diagnostics
+    uint32_t diag[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(diag, c->ws + L.diag, sizeof(diag), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+
+    auto val = [&](const std::vector<char>& raw, int64_t idx) -> double {
+        return c->L.cs == 8 ? reinterpret_cast<const double*>(raw.data())[idx]
+                            : (double)reinterpret_cast<const float*>(raw.data())[idx];
+    };
+    if (which & LBIB_RHO)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) rho[(size_t)y * nx + x] = val(r_rho, (int64_t)y * L.pitch + x);
+    if (which & LBIB_U)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 int64_t n = (int64_t)y * L.pitch + x;
-                if (ux) ux[(size_t)y * nx + x] = val(b, 2 * n);
-                if (uy) uy[(size_t)y * nx + x] = val(b, 2 * n + 1);
+                if (ux) ux[(size_t)y * nx + x] = val(r_u, 2 * n);
+                if (uy) uy[(size_t)y * nx + x] = val(r_u, 2 * n + 1);
             }
-    }
-    if ((which & LBIB_PHI) && S > 0) {
-        const char* b = fetch(L.phi, (size_t)S * L.plane * L.cs);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    if ((which & LBIB_PHI) && S > 0)
         for (int s = 0; s < S; ++s)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x)
                     phi[(size_t)s * N + (size_t)y * nx + x] =
-                        val(b, (int64_t)s * L.plane + (int64_t)y * L.pitch + x);
-    }
+                        val(r_phi, (int64_t)s * L.plane + (int64_t)y * L.pitch + x);
     if (which & LBIB_ID) {
-        const char* b = fetch(L.id_out, (size_t)L.plane * 4);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
-        const uint32_t* v = reinterpret_cast<const uint32_t*>(b);
+        const uint32_t* v = reinterpret_cast<const uint32_t*>(r_id.data());
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 uint32_t t = v[(int64_t)y * L.pitch + x];
                 id[(size_t)y * nx + x] = (t == kOutside) ? 0 : (int32_t)(t >> 4) + 1;
             }
     }
-    if (which & LBIB_FORCE) {
-        const char* b = fetch(L.force_out, (size_t)2 * L.plane * L.cs);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
+    if (which & LBIB_FORCE)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 int64_t n = (int64_t)y * L.pitch + x;
-                force[2 * ((size_t)y * nx + x)] = val(b, 2 * n);
-                force[2 * ((size_t)y * nx + x) + 1] = val(b, 2 * n + 1);
+                force[2 * ((size_t)y * nx + x)] = val(r_force, 2 * n);
+                force[2 * ((size_t)y * nx + x) + 1] = val(r_force, 2 * n + 1);
             }
-    }
-    if ((which & LBIB_X) && c->nV > 0) {
-        e = cudaMemcpyAsync(xy, c->ws + L.xy, (size_t)c->nV * 16, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
-    }
-    if ((which & LBIB_VFORCE) && c->nV > 0) {
-        if (!c->vforce_valid) return fail(c, LBIB_E_STATE, "no vertex forces computed yet");
-        e = cudaMemcpyAsync(vforce, c->ws + L.vforce, (size_t)c->nV * 16, cudaMemcpyDeviceToHost,
-                            c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
-    }
-    if ((which & LBIB_AREA) && c->nC > 0) {
-        e = launch_areas(c->at<double2>(L.xy), c->at<int32_t>(L.off), c->nC, c->at<double>(L.area),
-                         c->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(area, c->ws + L.area, (size_t)c->nC * 8, cudaMemcpyDeviceToHost,
-                                c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
-    }
-    // surface the device-side diagnostics
-    uint32_t diag[4] = {0, 0, 0, 0};
-    e = cudaMemcpyAsync(diag, c->ws + L.diag, sizeof(diag), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_fields");
     if (diag[kDiagNonFinite])
         return fail(c, LBIB_E_NONFINITE, "a non-finite density or velocity was produced");
     if (diag[kDiagGeometry])
@@ -745,6 +747,11 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
 void lbib_destroy(lbib_ctx* c) {
     if (!c) return;
     drop_graphs(c);
+    if (c->hstage_done) {
+        cudaEventSynchronize(c->hstage_done);
+        cudaEventDestroy(c->hstage_done);
+    }
+    if (c->hstage) cudaFreeHost(c->hstage);
     delete c;
 }
 

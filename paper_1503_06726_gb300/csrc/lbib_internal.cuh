@@ -239,6 +239,11 @@ struct lbib_ctx {
     // graph of a two-step chunk, keyed by the buffer parity it starts from
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
     int chunk_nC = -1;
+    // pinned staging of lbib_set_cell_params (pressure then source flags), and
+    // the event of its last upload (the buffer is reused once that is done)
+    char* hstage = nullptr;
+    cudaEvent_t hstage_done = nullptr;
+    bool hstage_pending = false;
     std::string err;
 
     template <typename T>
