@@ -560,7 +560,9 @@ def run_gb300(args, rank, world, dist):
             "graph": "two-step CUDA graph chunks"}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
-                     "kernel": "lattice_kernel", "alg_bytes_per_launch": alg_bytes,
+                     "kernel": ("lattice_pair_kernel (two nodes per thread)"
+                                if prec == "fp16" and w.params.nx % 2 == 0 else "lattice_kernel"),
+                     "alg_bytes_per_launch": alg_bytes,
                      "alg_bytes_per_node": bpn, "launch_ms": lat_avg,
                      "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "ib_launch_ms": ib_ms / (n_prof + 1)},

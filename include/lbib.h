@@ -20,8 +20,9 @@
  *   - Host pointers passed in are read before the call returns; the caller
  *     keeps ownership.  Host output buffers are caller-allocated.
  *   - Work is enqueued on the CUDA stream given to lbib_create().
- *     lbib_step() is asynchronous; lbib_set_*() and lbib_get_*() synchronise
- *     that stream before they return.
+ *     lbib_step() and lbib_set_cell_params() are asynchronous; the other
+ *     lbib_set_*() and lbib_get_*() calls synchronise that stream before
+ *     they return.
  *   - A context must not be used from two host threads at once.
  *   - Every call returns LBIB_OK (0) or a negative LBIB_E_* code; no call
  *     aborts or throws.  lbib_last_error() gives a one-line reason.
@@ -132,6 +133,16 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
 int lbib_set_cells(lbib_ctx* ctx, int32_t n_cells, const int32_t* cell_off, const double* xy,
                    const double* rest_len, const double* k_spring, const double* pressure,
                    const uint8_t* src_flag);
+
+/* Choose how many lattice nodes one thread of the lattice update handles.
+ * 2 (the default) lets FP16 storage update two adjacent nodes per thread,
+ * moving every population as one 32-bit word of two halves, whenever the
+ * lattice width nx is even; 1 forces one node per thread.  FP32 and FP64
+ * storage always use one node per thread.  Both give the same arithmetic
+ * (the collision of Sec. 6.1, Eq. bgkequation, node by node); the setting
+ * exists to compare and time the two.  LBIB_E_PARAM for other values.  Waits
+ * for the context stream when the choice changes. */
+int lbib_set_lattice_variant(lbib_ctx* ctx, int32_t nodes_per_thread);
 
 /* Update the per-cell pressure and source flags of the current cells (the
  * inputs a host-side biology step changes between time steps).  Either

@@ -28,6 +28,7 @@
 
 #include "ib_cell.cuh"
 #include "lattice_node.cuh"
+#include "lbib_ctx.cuh"
 
 namespace lbib {
 

@@ -273,6 +273,98 @@ _Pragma("unroll") \
     if (a.out) static_cast<C*>(a.rho)[node] = rho; \
     if (!(rho > C(0)) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.diag + kDiagNonFinite, 1u);
 
+// The collision of one node in registers: the arithmetic of the fused update
+// above, operation for operation, without its loads and stores.  d and g hold
+// the pulled populations in their stored form and are overwritten with the
+// post-collision stored values; rho, u and the species fields are returned.
+template <typename C, int S, int FORCING, bool SCALED>
+__device__ __forceinline__ void collide_node(const Coefs<C>& k, C (&d)[9],
+                                             C (&g)[S > 0 ? S : 1][5], C fvx, C fvy,
+                                             uint32_t sbits, C& rho, C& ux, C& uy,
+                                             C (&ph)[S > 0 ? S : 1]) {
+    const C Fx = k.bfx + fvx, Fy = k.bfy + fvy;
+    C drho, jx, jy;
+    if (SCALED) {
+        const C sA = k.fscale[0], sB = k.fscale[1], sC = k.fscale[5];
+        drho = sA * d[0] + sB * ((d[1] + d[2]) + (d[3] + d[4])) +
+               sC * ((d[5] + d[6]) + (d[7] + d[8]));
+        jx = sB * (d[1] - d[3]) + sC * ((d[5] - d[6]) + (d[8] - d[7]));
+        jy = sB * (d[2] - d[4]) + sC * ((d[5] + d[6]) - (d[7] + d[8]));
+    } else {
+        drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+        jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
+        jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+    }
+    rho = k.rho0 + drho;
+    const C irho = C(1) / rho;
+    if (FORCING == LBIB_GUO) {
+        ux = (jx + C(0.5) * Fx) * irho;
+        uy = (jy + C(0.5) * Fy) * irho;
+    } else {
+        ux = jx * irho;
+        uy = jy * irho;
+    }
+    const C usq15 = C(1.5) * (ux * ux + uy * uy);
+    const C uF = ux * Fx + uy * Fy;
+    {
+        const C e0 = SCALED ? k.isig : C(w9(0));
+        C ev = k.omega * (drho - rho * usq15);
+        if (FORCING == LBIB_GUO) ev -= k.pref * (C(3) * uF);
+        d[0] = k.omc * d[0] + e0 * ev;
+    }
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+        if (q == 1 || q == 2 || q == 5 || q == 6) {
+            const int o = q + 2;
+            const C ew = SCALED ? k.isig : C(w9(q));
+            const C cu = C(cx(q)) * ux + C(cy(q)) * uy;
+            const C cF = C(cx(q)) * Fx + C(cy(q)) * Fy;
+            C ev = k.omega * (drho + rho * (C(4.5) * cu * cu - usq15));
+            C od = k.omega * (rho * (C(3) * cu));
+            if (FORCING == LBIB_GUO) {
+                ev += k.pref * (C(9) * cu * cF - C(3) * uF);
+                od += k.pref * (C(3) * cF);
+            } else {
+                od += C(3) * cF;
+            }
+            ev *= ew;
+            od *= ew;
+            const C dq = k.omc * d[q] + (ev + od);
+            const C doo = k.omc * d[o] + (ev - od);
+            d[q] = dq;
+            d[o] = doo;
+        }
+    }
+    if (S > 0) {
+        const uint32_t bits = sbits & 0xFu;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            if (SCALED)
+                ph[s] = k.gscale[0] * g[s][0] +
+                        k.gscale[1] * ((g[s][1] + g[s][2]) + (g[s][3] + g[s][4]));
+            else
+                ph[s] = ((g[s][0] + g[s][1]) + (g[s][2] + g[s][3])) + g[s][4];
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            C R = ((bits >> s) & 1u) ? k.srate[s] : C(0);
+#pragma unroll
+            for (int b = 0; b < S; ++b) R += k.K[s][b] * ph[b];
+            const C ev = k.omegaD[s] * ph[s] + R;
+            const C od = k.omegaD[s] * ph[s] * C(3);
+            const C eA = SCALED ? k.isig_g : C(w5(0));
+            const C eB = SCALED ? k.isig_g : C(w5(1));
+            const C evB = eB * ev;
+            const C ox = eB * od * ux, oy = eB * od * uy;
+            g[s][0] = k.omcD[s] * g[s][0] + eA * ev;
+            g[s][1] = k.omcD[s] * g[s][1] + (evB + ox);
+            g[s][3] = k.omcD[s] * g[s][3] + (evB - ox);
+            g[s][2] = k.omcD[s] * g[s][2] + (evB + oy);
+            g[s][4] = k.omcD[s] * g[s][4] + (evB - oy);
+        }
+    }
+}
+
 template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
                                              int y) {

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "lbib_ctx.cuh"
 #include "lbib_internal.cuh"
 
 namespace lbib {
@@ -236,7 +237,7 @@ IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
 static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl = false) {
     LatticeArgs a = lattice_args(c, src_buf, out);
     return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,
-                          coefs_of(c), c->block, c->stream, pdl && c->nC > 0);
+                          coefs_of(c), c->block, c->stream, pdl && c->nC > 0, c->lattice_pairs);
 }
 
 static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next,
@@ -438,6 +439,21 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
         c->maxv_cell = std::max(c->maxv_cell, cell_off[ci + 1] - cell_off[ci]);
     c->vforce_valid = false;
     drop_graphs(c);
+    return LBIB_OK;
+}
+
+int lbib_set_lattice_variant(lbib_ctx* c, int32_t nodes_per_thread) {
+    if (!c) return LBIB_E_PARAM;
+    if (nodes_per_thread != 1 && nodes_per_thread != 2)
+        return fail(c, LBIB_E_PARAM, "nodes_per_thread must be 1 or 2");
+    const bool pairs = nodes_per_thread == 2;
+    if (pairs != c->lattice_pairs) {
+        // the captured step graphs hold the other kernel
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_lattice_variant");
+        drop_graphs(c);
+        c->lattice_pairs = pairs;
+    }
     return LBIB_OK;
 }
 

@@ -1,0 +1,44 @@
+// Host-side state of one tissue (the opaque handle of the C ABI), kept apart
+// from the kernel headers: no kernel reads it.
+#pragma once
+
+#include <string>
+
+#include "lbib_internal.cuh"
+
+// One tissue (the opaque handle of the C ABI).
+struct lbib_ctx {
+    lbib_params p;
+    int maxV = 0, maxC = 0;
+    char* ws = nullptr;
+    uint64_t bytes = 0;
+    cudaStream_t stream = nullptr;
+    lbib::Layout L;
+    int cur = 0;           // buffer holding the current post-collision populations
+    int nV = 0, nC = 0;
+    int maxv_cell = 0;     // largest vertex count of a cell
+    bool fields_valid = false;
+    bool vforce_valid = false;
+    lbib::Coefs<double> kd;
+    lbib::Coefs<float> kf;
+    dim3 block{128, 1, 1};
+    bool lattice_pairs = true;  // FP16 storage: two nodes per thread where possible
+    // graph of a two-step chunk, keyed by the buffer parity it starts from
+    cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    int chunk_nC = -1;
+    // pinned staging of lbib_set_cell_params (pressure then source flags), and
+    // the event of its last upload (the buffer is reused once that is done)
+    char* hstage = nullptr;
+    cudaEvent_t hstage_done = nullptr;
+    bool hstage_pending = false;
+    std::string err;
+
+    template <typename T>
+    T* at(uint64_t off) const { return reinterpret_cast<T*>(ws + off); }
+};
+
+namespace lbib {
+// kernel arguments of a context (its buffers, parity src_buf)
+LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out);
+IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next);
+}  // namespace lbib

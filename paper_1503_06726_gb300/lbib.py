@@ -38,7 +38,8 @@ PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
 
 # every symbol declared in include/lbib.h
 EXPORTS = (
-    "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_cell_params",
+    "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_lattice_variant",
+    "lbib_set_cell_params",
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
     "lbib_status_string", "lbib_label_cells", "lbib_steady_workspace_size", "lbib_steady_solve",
@@ -88,6 +89,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_create": (ctypes.c_int, [P, i32, i32, vp, u64, vp, ctypes.POINTER(vp)]),
         "lbib_set_cells": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "lbib_set_cell_params": (ctypes.c_int, [vp, vp, vp]),
+        "lbib_set_lattice_variant": (ctypes.c_int, [vp, i32]),
         "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
         "lbib_step": (ctypes.c_int, [vp, i32]),
         "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
@@ -203,6 +205,10 @@ def lbib_set_cells(ctx, cell_off, xy, rest_len=None, k_spring=None, pressure=Non
     pr, pr_p = _p(pressure, np.float64)
     sf, sf_p = _p(src_flag, np.uint8)
     _check(load().lbib_set_cells(ctx, len(off) - 1, off_p, xy_p, L0_p, k_p, pr_p, sf_p), ctx)
+
+
+def lbib_set_lattice_variant(ctx, nodes_per_thread: int):
+    _check(load().lbib_set_lattice_variant(ctx, int(nodes_per_thread)), ctx)
 
 
 def lbib_set_cell_params(ctx, pressure=None, src_flag=None):
@@ -405,6 +411,9 @@ class Simulation:
 
     def set_cell_params(self, pressure=None, src_flag=None):
         lbib_set_cell_params(self.ctx, pressure, src_flag)
+
+    def set_lattice_variant(self, nodes_per_thread: int):
+        lbib_set_lattice_variant(self.ctx, nodes_per_thread)
 
     def set_species(self, s: int, phi):
         lbib_set_species(self.ctx, s, phi)
