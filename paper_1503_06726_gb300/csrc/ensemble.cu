@@ -296,11 +296,18 @@ static cudaError_t ens_upload(lbib_ensemble* e, int* total_items, int* total_cel
     if (fe != cudaSuccess) return fe;
     std::vector<TissueDev> tab((size_t)e->n);
     std::vector<int> ipfx((size_t)e->n + 1, 0), cpfx((size_t)e->n + 1, 0);
+    // the tissues stream through one L2: their summed planes decide the
+    // population load policy
+    int64_t planes = 0;
+    for (int t = 0; t < e->n; ++t) planes += e->ctx[t]->L.plane;
+    const int l2_first =
+        e->n > 0 && lattice_l2_first(LBIB_FP32, e->ctx[0]->p.n_species, planes) ? 1 : 0;
     for (int t = 0; t < e->n; ++t) {
         lbib_ctx* c = e->ctx[t];
         TissueDev& d = tab[t];
         std::memset(&d, 0, sizeof(d));
         d.la = ctx_lattice_args(c, 0, false);
+        d.la.l2_first = l2_first;
         d.ia = ctx_ib_args(c, true, true, false);
         d.k = c->kf;
         d.bc_y = c->p.bc_y;

@@ -51,7 +51,7 @@ __device__ __forceinline__ void raise_flag(uint32_t* diag, int k) {
 
 // spread one weighted force into a node: FP32 uses the float2 vector atomic
 __device__ __forceinline__ void spread_add(float2* p, float fx, float fy) {
-    atomicAdd(p, make_float2(fx, fy));
+    red_keep(p, fx, fy);
 }
 __device__ __forceinline__ void spread_add(double2* p, double fx, double fy) {
     atomicAdd(&p->x, fx);

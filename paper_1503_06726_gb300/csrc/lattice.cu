@@ -64,7 +64,9 @@ struct PairOccupancy {
     static constexpr int kMinBlocks = S <= 1 ? 8 : (S == 2 ? 6 : (S == 3 ? 5 : 4));
 };
 
-__device__ __forceinline__ uint32_t ldw(const uint32_t* p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ldw(const uint32_t* p, uint64_t pol) {
+    return ld_stream(p, pol);
+}
 
 // the pair (x0 - 1, x0) from the aligned word a = (x0, x0 + 1) and e, the
 // word (x0 - 2, x0 - 1) loaded by the lanes with own_l set
@@ -121,39 +123,40 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     const int64_t q0 = (r0 + xr) >> 1, qm = (rm + xr) >> 1, qp = (rp + xr) >> 1;
 
     // ---- every population word first (written two launches back: L2 path)
+    const uint64_t pol = a.l2_first ? l2_evict_first() : l2_evict_normal();
     const uint32_t* F = static_cast<const uint32_t*>(a.fsrc);
     uint32_t r[9], e[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) r[q] = e[q] = 0u;
     if (valid) {
-        r[0] = ldw(F + w);
-        r[1] = ldw(F + 1 * P2 + w);
-        r[3] = ldw(F + 3 * P2 + w);
-        r[2] = lo_wall ? ldw(F + 4 * P2 + w) : ldw(F + 2 * P2 + wm);
-        r[4] = hi_wall ? ldw(F + 2 * P2 + w) : ldw(F + 4 * P2 + wp);
+        r[0] = ldw(F + w, pol);
+        r[1] = ldw(F + 1 * P2 + w, pol);
+        r[3] = ldw(F + 3 * P2 + w, pol);
+        r[2] = lo_wall ? ldw(F + 4 * P2 + w, pol) : ldw(F + 2 * P2 + wm, pol);
+        r[4] = hi_wall ? ldw(F + 2 * P2 + w, pol) : ldw(F + 4 * P2 + wp, pol);
         if (lo_wall) {  // half-way bounce-back at y = -1/2
-            r[5] = ldw(F + 7 * P2 + w);
-            r[6] = ldw(F + 8 * P2 + w);
+            r[5] = ldw(F + 7 * P2 + w, pol);
+            r[6] = ldw(F + 8 * P2 + w, pol);
         } else {
-            r[5] = ldw(F + 5 * P2 + wm);
-            r[6] = ldw(F + 6 * P2 + wm);
+            r[5] = ldw(F + 5 * P2 + wm, pol);
+            r[6] = ldw(F + 6 * P2 + wm, pol);
         }
         if (hi_wall) {  // at y = ny - 1/2
-            r[7] = ldw(F + 5 * P2 + w);
-            r[8] = ldw(F + 6 * P2 + w);
+            r[7] = ldw(F + 5 * P2 + w, pol);
+            r[8] = ldw(F + 6 * P2 + w, pol);
         } else {
-            r[7] = ldw(F + 7 * P2 + wp);
-            r[8] = ldw(F + 8 * P2 + wp);
+            r[7] = ldw(F + 7 * P2 + wp, pol);
+            r[8] = ldw(F + 8 * P2 + wp, pol);
         }
         if (own_l) {
-            e[1] = ldw(F + 1 * P2 + l0);
-            if (!lo_wall) e[5] = ldw(F + 5 * P2 + lm);
-            if (!hi_wall) e[8] = ldw(F + 8 * P2 + lp);
+            e[1] = ldw(F + 1 * P2 + l0, pol);
+            if (!lo_wall) e[5] = ldw(F + 5 * P2 + lm, pol);
+            if (!hi_wall) e[8] = ldw(F + 8 * P2 + lp, pol);
         }
         if (own_r) {
-            e[3] = ldw(F + 3 * P2 + q0);
-            if (!lo_wall) e[6] = ldw(F + 6 * P2 + qm);
-            if (!hi_wall) e[7] = ldw(F + 7 * P2 + qp);
+            e[3] = ldw(F + 3 * P2 + q0, pol);
+            if (!lo_wall) e[6] = ldw(F + 6 * P2 + qm, pol);
+            if (!hi_wall) e[7] = ldw(F + 7 * P2 + qp, pol);
         }
     }
     uint32_t rg[SS][5], eg[SS][2];
@@ -167,13 +170,13 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             const uint32_t* B = Gi + (int64_t)s * 5 * P2;
-            rg[s][0] = ldw(B + w);
-            rg[s][1] = ldw(B + 1 * P2 + w);
-            rg[s][3] = ldw(B + 3 * P2 + w);
-            rg[s][2] = lo_wall ? ldw(B + 4 * P2 + w) : ldw(B + 2 * P2 + wm);
-            rg[s][4] = hi_wall ? ldw(B + 2 * P2 + w) : ldw(B + 4 * P2 + wp);
-            if (own_l) eg[s][0] = ldw(B + 1 * P2 + l0);
-            if (own_r) eg[s][1] = ldw(B + 3 * P2 + q0);
+            rg[s][0] = ldw(B + w, pol);
+            rg[s][1] = ldw(B + 1 * P2 + w, pol);
+            rg[s][3] = ldw(B + 3 * P2 + w, pol);
+            rg[s][2] = lo_wall ? ldw(B + 4 * P2 + w, pol) : ldw(B + 2 * P2 + wm, pol);
+            rg[s][4] = hi_wall ? ldw(B + 2 * P2 + w, pol) : ldw(B + 4 * P2 + wp, pol);
+            if (own_l) eg[s][0] = ldw(B + 1 * P2 + l0, pol);
+            if (own_r) eg[s][1] = ldw(B + 3 * P2 + q0, pol);
         }
     }
     // the IB kernel launched just before wrote the force, label and mask
@@ -276,9 +279,9 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     }
 
     // velocity where the interpolation will read it, resets, outputs, masks
-    if (a.out || fhit) static_cast<float4*>(a.u)[node >> 1] = make_float4(uxA, uyA, uxB, uyB);
+    if (a.out || fhit) st_keep(static_cast<float4*>(a.u) + (node >> 1), make_float4(uxA, uyA, uxB, uyB));
     if (a.ib) {
-        if (fhit) static_cast<float4*>(a.force)[node >> 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fhit) st_keep(static_cast<float4*>(a.force) + (node >> 1), make_float4(0.f, 0.f, 0.f, 0.f));
         if (lhit) reinterpret_cast<uint2*>(a.id)[node >> 1] = make_uint2(kOutside, kOutside);
         if (shit) reinterpret_cast<unsigned short*>(a.src)[node >> 1] = 0;
         if (a.out) {
@@ -342,6 +345,18 @@ static cudaError_t launch1(int n_species, int bc_y, int forcing, const LatticeAr
         case 3: return launch2<T, C, 3>(bc_y, forcing, a, coefs, block, s, pdl, pairs);
         default: return launch2<T, C, 4>(bc_y, forcing, a, coefs, block, s, pdl, pairs);
     }
+}
+
+bool lattice_l2_first(int precision, int n_species, int64_t plane) {
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int es = precision == LBIB_FP64 ? 8 : (precision == LBIB_FP32 ? 4 : 2);
+    const double bytes = 2.0 * (9 + 5 * n_species) * (double)plane * es;
+    return bytes <= 1.5 * (double)l2;
 }
 
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,

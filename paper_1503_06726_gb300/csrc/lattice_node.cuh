@@ -13,17 +13,24 @@ template <typename T, typename C>
 struct Store;
 template <>
 struct Store<double, double> {
-    static __device__ __forceinline__ double ld(const double* p) { return __ldcg(p); }
+    static __device__ __forceinline__ double ld(const double* p, uint64_t pol) {
+        return ld_stream(p, pol);
+    }
     static __device__ __forceinline__ void st(double* p, double v) { *p = v; }
 };
 template <>
 struct Store<float, float> {
-    static __device__ __forceinline__ float ld(const float* p) { return __ldcg(p); }
+    static __device__ __forceinline__ float ld(const float* p, uint64_t pol) {
+        return ld_stream(p, pol);
+    }
     static __device__ __forceinline__ void st(float* p, float v) { *p = v; }
 };
 template <>
 struct Store<__half, float> {
-    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(__ldcg(p)); }
+    static __device__ __forceinline__ float ld(const __half* p, uint64_t pol) {
+        return __half2float(
+            __ushort_as_half(ld_stream(reinterpret_cast<const unsigned short*>(p), pol)));
+    }
     static __device__ __forceinline__ void st(__half* p, float v) { *p = __float2half_rn(v); }
 };
 
@@ -38,13 +45,13 @@ struct Vec2<float> { using T = float2; };
 template <typename T, typename C, bool WALLS>
 __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64_t r0, int64_t rm,
                                       int64_t rp, int x, int xm, int xp, bool lo, bool hi,
-                                      C g[5]) {
+                                      uint64_t pol, C g[5]) {
     using St = Store<T, C>;
-    g[0] = St::ld(B + node);
-    g[1] = St::ld(B + 1 * P + r0 + xm);
-    g[3] = St::ld(B + 3 * P + r0 + xp);
-    g[2] = (WALLS && lo) ? St::ld(B + 4 * P + node) : St::ld(B + 2 * P + rm + x);
-    g[4] = (WALLS && hi) ? St::ld(B + 2 * P + node) : St::ld(B + 4 * P + rp + x);
+    g[0] = St::ld(B + node, pol);
+    g[1] = St::ld(B + 1 * P + r0 + xm, pol);
+    g[3] = St::ld(B + 3 * P + r0 + xp, pol);
+    g[2] = (WALLS && lo) ? St::ld(B + 4 * P + node, pol) : St::ld(B + 2 * P + rm + x, pol);
+    g[4] = (WALLS && hi) ? St::ld(B + 2 * P + node, pol) : St::ld(B + 4 * P + rp + x, pol);
 }
 
 // The update of one node (x, y).  Callers map the 32 lanes of a warp to 32
@@ -79,20 +86,21 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
     /* that a thread has all its DRAM requests in flight at once */ \
     const T* F = static_cast<const T*>(a.fsrc); \
     C d[9]; \
-    pull5<T, C, WALLS>(F, P, node, r0, rm, rp, x, xm, xp, lo_wall, hi_wall, d); \
+    const uint64_t pol = a.l2_first ? l2_evict_first() : l2_evict_normal(); \
+    pull5<T, C, WALLS>(F, P, node, r0, rm, rp, x, xm, xp, lo_wall, hi_wall, pol, d); \
     if (lo_wall) {  /* half-way bounce-back: v_y = +1 populations reflect off y = -1/2 */ \
-        d[5] = St::ld(F + 7 * P + node); \
-        d[6] = St::ld(F + 8 * P + node); \
+        d[5] = St::ld(F + 7 * P + node, pol); \
+        d[6] = St::ld(F + 8 * P + node, pol); \
     } else { \
-        d[5] = St::ld(F + 5 * P + rm + xm); \
-        d[6] = St::ld(F + 6 * P + rm + xp); \
+        d[5] = St::ld(F + 5 * P + rm + xm, pol); \
+        d[6] = St::ld(F + 6 * P + rm + xp, pol); \
     } \
     if (hi_wall) {  /* v_y = -1 populations reflect off y = ny - 1/2 */ \
-        d[7] = St::ld(F + 5 * P + node); \
-        d[8] = St::ld(F + 6 * P + node); \
+        d[7] = St::ld(F + 5 * P + node, pol); \
+        d[8] = St::ld(F + 6 * P + node, pol); \
     } else { \
-        d[7] = St::ld(F + 7 * P + rp + xp); \
-        d[8] = St::ld(F + 8 * P + rp + xm); \
+        d[7] = St::ld(F + 7 * P + rp + xp, pol); \
+        d[8] = St::ld(F + 8 * P + rp + xm, pol); \
     } \
     C g[S > 0 ? S : 1][5]; \
     { \
@@ -100,7 +108,7 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) \
             pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, lo_wall, \
-                               hi_wall, g[s]); \
+                               hi_wall, pol, g[s]); \
     } \
     /* the IB kernel launched just before wrote the force, label and mask */ \
     /* planes: wait for it, then let the next IB launch start */ \
@@ -247,14 +255,14 @@ _Pragma("unroll") \
         V2 uv; \
         uv.x = ux; \
         uv.y = uy; \
-        static_cast<V2*>(a.u)[node] = uv; \
+        st_keep(static_cast<V2*>(a.u) + node, uv); \
     } \
     if (a.ib) { \
         if (fhit) { \
             V2 z; \
             z.x = C(0); \
             z.y = C(0); \
-            static_cast<V2*>(a.force)[node] = z; \
+            st_keep(static_cast<V2*>(a.force) + node, z); \
         } \
         if (lhit) a.id[node] = kOutside; \
         if (shit) a.src[node] = 0; \

@@ -178,6 +178,7 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.plane = L.plane;
     a.out = out ? 1 : 0;
     a.ib = c->nC > 0 ? 1 : 0;
+    a.l2_first = c->l2_first ? 1 : 0;
     a.fmask = c->at<uint32_t>(L.fmask);
     a.lmask = c->at<uint32_t>(L.lmask);
     a.src = c->at<uint8_t>(L.src);
@@ -345,6 +346,7 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     c->L = L;
     fill_coefs(c->p, &c->kd);
     fill_coefs(c->p, &c->kf);
+    c->l2_first = lattice_l2_first(c->p.precision, c->p.n_species, L.plane);
     e = launch_init_populations(c->p.precision, c->p.n_species, c->p.nx, c->p.ny, L.pitch,
                                 L.plane, c->ws + L.f[0], c->ws + L.g[0], c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);

@@ -120,6 +120,7 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     la.plane = L.plane;
     la.out = 0;
     la.ib = n_cells > 0 ? 1 : 0;
+    la.l2_first = lattice_l2_first(params->precision, params->n_species, L.plane) ? 1 : 0;
     IBArgs ia;
     std::memset(&ia, 0, sizeof(ia));
     ia.xy = reinterpret_cast<double2*>(d_xy);
