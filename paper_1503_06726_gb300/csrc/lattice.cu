@@ -56,12 +56,14 @@ __global__ void __launch_bounds__(kLatticeThreads, LatticeOccupancy<T, S>::kMinB
 // neighbouring halves of the thread's own aligned word and of the adjacent
 // lane's (a warp shuffle); the first and the last lane of a warp, and the
 // last pair of a row, load the word beyond the warp themselves (periodic in
-// x).  The arithmetic is collide_node, the same as the one-node update.
-// Register budget of the pair kernel (CTAs of 128 threads per SM): 64 with
-// at most one species, 80 with two, 96 with three, 128 with four (no spills).
+// x).  Both nodes collide at once in packed FP32 arithmetic (collide_node
+// on float2), per node the same operations as the one-node update.
+// Register budget of the pair kernel (CTAs of 128 threads per SM; the packed
+// values of two nodes take register pairs): 64 without species, 72 with one,
+// 102 with two, 128 with three or four (no spills).
 template <int S>
 struct PairOccupancy {
-    static constexpr int kMinBlocks = S <= 1 ? 8 : (S == 2 ? 6 : (S == 3 ? 5 : 4));
+    static constexpr int kMinBlocks = S == 0 ? 8 : (S == 1 ? 7 : (S == 2 ? 5 : 4));
 };
 
 __device__ __forceinline__ uint32_t ldw(const uint32_t* p, uint64_t pol) {
@@ -81,14 +83,8 @@ __device__ __forceinline__ uint32_t pair_from_right(uint32_t a, uint32_t e, bool
     return __funnelshift_r(a, own_r ? e : dn, 16);
 }
 
-__device__ __forceinline__ float lo_half(uint32_t w) {
-    return __half2float(__ushort_as_half((unsigned short)(w & 0xFFFFu)));
-}
-__device__ __forceinline__ float hi_half(uint32_t w) {
-    return __half2float(__ushort_as_half((unsigned short)(w >> 16)));
-}
-__device__ __forceinline__ uint32_t pack_halves(float lo, float hi) {
-    const __half2 h = __floats2half2_rn(lo, hi);
+__device__ __forceinline__ uint32_t pack_halves(float2 v) {
+    const __half2 h = __float22half2_rn(v);
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
@@ -235,51 +231,38 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
         if (shit) sb2 = reinterpret_cast<const unsigned short*>(a.src)[node >> 1];
     }
 
-    // ---- the two collisions
-    C d[9], g[SS][5], ph[SS];
-    C rhoA, uxA, uyA, dA[9], gA[SS][5], phA[SS];
+    // ---- the collision of both nodes at once (packed FP32: x = node x0,
+    // y = node x0 + 1)
+    float2 d[9], g[SS][5], ph[SS], rho, ux, uy;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) d[q] = lo_half(r[q]);
-#pragma unroll
-    for (int s = 0; s < SS; ++s)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) g[s][q] = lo_half(rg[s][q]);
-    collide_node<C, S, FORCING, true>(k, d, g, fv.x, fv.y, sb2 & 0xFFu, rhoA, uxA, uyA, ph);
-#pragma unroll
-    for (int q = 0; q < 9; ++q) dA[q] = d[q];
-#pragma unroll
-    for (int s = 0; s < SS; ++s) {
-        phA[s] = ph[s];
-#pragma unroll
-        for (int q = 0; q < 5; ++q) gA[s][q] = g[s][q];
-    }
-    C rhoB, uxB, uyB;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) d[q] = hi_half(r[q]);
+    for (int q = 0; q < 9; ++q) d[q] = __half22float2(*reinterpret_cast<const __half2*>(&r[q]));
 #pragma unroll
     for (int s = 0; s < SS; ++s)
 #pragma unroll
-        for (int q = 0; q < 5; ++q) g[s][q] = hi_half(rg[s][q]);
-    collide_node<C, S, FORCING, true>(k, d, g, fv.z, fv.w, sb2 >> 8, rhoB, uxB, uyB, ph);
+        for (int q = 0; q < 5; ++q)
+            g[s][q] = __half22float2(*reinterpret_cast<const __half2*>(&rg[s][q]));
+    collide_node<float2, S, FORCING, true>(k, d, g, make_float2(fv.x, fv.z),
+                                           make_float2(fv.y, fv.w), sb2 & 0xFFu, sb2 >> 8, rho,
+                                           ux, uy, ph);
 
     uint32_t* G = static_cast<uint32_t*>(a.fdst);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) G[q * P2 + w] = pack_halves(dA[q], d[q]);
+    for (int q = 0; q < 9; ++q) G[q * P2 + w] = pack_halves(d[q]);
     if (S > 0) {
         uint32_t* Go = static_cast<uint32_t*>(a.gdst);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q)
-                Go[(int64_t)(s * 5 + q) * P2 + w] = pack_halves(gA[s][q], g[s][q]);
+            for (int q = 0; q < 5; ++q) Go[(int64_t)(s * 5 + q) * P2 + w] = pack_halves(g[s][q]);
             if (a.out)
                 reinterpret_cast<float2*>(static_cast<C*>(a.phi) + (int64_t)s * a.plane)[node >> 1] =
-                    make_float2(phA[s], ph[s]);
+                    ph[s];
         }
     }
 
     // velocity where the interpolation will read it, resets, outputs, masks
-    if (a.out || fhit) st_keep(static_cast<float4*>(a.u) + (node >> 1), make_float4(uxA, uyA, uxB, uyB));
+    if (a.out || fhit)
+        st_keep(static_cast<float4*>(a.u) + (node >> 1), make_float4(ux.x, uy.x, ux.y, uy.y));
     if (a.ib) {
         if (fhit) st_keep(static_cast<float4*>(a.force) + (node >> 1), make_float4(0.f, 0.f, 0.f, 0.f));
         if (lhit) reinterpret_cast<uint2*>(a.id)[node >> 1] = make_uint2(kOutside, kOutside);
@@ -296,9 +279,9 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
             if (clear & 4u) atomicAnd(a.smask + (grp >> 5), ~(0xFFFFu << sh));
         }
     }
-    if (a.out) reinterpret_cast<float2*>(a.rho)[node >> 1] = make_float2(rhoA, rhoB);
-    if (!(rhoA > 0.f) || !isfinite(uxA) || !isfinite(uyA) || !(rhoB > 0.f) || !isfinite(uxB) ||
-        !isfinite(uyB))
+    if (a.out) reinterpret_cast<float2*>(a.rho)[node >> 1] = rho;
+    if (!(rho.x > 0.f) || !isfinite(ux.x) || !isfinite(uy.x) || !(rho.y > 0.f) ||
+        !isfinite(ux.y) || !isfinite(uy.y))
         atomicOr(a.diag + kDiagNonFinite, 1u);
 }
 

@@ -146,103 +146,19 @@ _Pragma("unroll") \
         if (shit) sbits = a.src[node]; \
     } \
  \
-    /* ---- moments (Sec. 6.1) with the half-force velocity shift (Guo).  With */ \
-    /* scaled storage s_q = d_q / (w_q sigma) the moments weight the stored */ \
-    /* values (w_1..w_4 and w_5..w_8 are equal) and d_q is never formed. */ \
-    const C Fx = k.bfx + fv.x, Fy = k.bfy + fv.y; \
-    C drho, jx, jy; \
-    if (SCALED) { \
-        const C sA = k.fscale[0], sB = k.fscale[1], sC = k.fscale[5]; \
-        drho = sA * d[0] + sB * ((d[1] + d[2]) + (d[3] + d[4])) + \
-               sC * ((d[5] + d[6]) + (d[7] + d[8])); \
-        jx = sB * (d[1] - d[3]) + sC * ((d[5] - d[6]) + (d[8] - d[7])); \
-        jy = sB * (d[2] - d[4]) + sC * ((d[5] + d[6]) - (d[7] + d[8])); \
-    } else { \
-        drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8]; \
-        jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]); \
-        jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]); \
-    } \
-    const C rho = k.rho0 + drho; \
-    const C irho = C(1) / rho; \
-    C ux, uy; \
-    if (FORCING == LBIB_GUO) { \
-        ux = (jx + C(0.5) * Fx) * irho; \
-        uy = (jy + C(0.5) * Fy) * irho; \
-    } else { \
-        ux = jx * irho; \
-        uy = jy * irho; \
-    } \
-    const C usq15 = C(1.5) * (ux * ux + uy * uy); \
-    const C uF = ux * Fx + uy * Fy; \
- \
-    /* ---- collide and store the fluid, opposite directions together: with */ \
-    /* A = drho + rho (9/2 (v.u)^2 - 3/2 u.u), B = 3 rho v.u and the forcing */ \
-    /* split into its even part Ce and odd part Co, */ \
-    /*   d*_q = (1 - omega) d_q + w (omega A + Ce) + w (omega B + Co) */ \
-    /* and the opposite direction flips the sign of the odd terms.  Scaled */ \
-    /* storage replaces the factor w by 1/sigma. */ \
+    /* ---- the collision (collide_node), then the stores */ \
+    C rho, ux, uy; \
+    C ph[S > 0 ? S : 1]; \
+    collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph); \
     T* G = static_cast<T*>(a.fdst); \
-    { \
-        const C e0 = SCALED ? k.isig : C(w9(0)); \
-        C ev = k.omega * (drho - rho * usq15); \
-        if (FORCING == LBIB_GUO) ev -= k.pref * (C(3) * uF); \
-        St::st(G + node, k.omc * d[0] + e0 * ev); \
-    } \
 _Pragma("unroll") \
-    for (int q = 1; q < 9; ++q) { \
-        if (q == 1 || q == 2 || q == 5 || q == 6) { \
-            const int o = q + 2; /* opposite of 1, 2, 5, 6 */ \
-            const C ew = SCALED ? k.isig : C(w9(q)); \
-            const C cu = C(cx(q)) * ux + C(cy(q)) * uy; \
-            const C cF = C(cx(q)) * Fx + C(cy(q)) * Fy; \
-            C ev = k.omega * (drho + rho * (C(4.5) * cu * cu - usq15)); \
-            C od = k.omega * (rho * (C(3) * cu)); \
-            if (FORCING == LBIB_GUO) { \
-                ev += k.pref * (C(9) * cu * cF - C(3) * uF); \
-                od += k.pref * (C(3) * cF); \
-            } else { \
-                od += C(3) * cF; \
-            } \
-            ev *= ew; \
-            od *= ew; \
-            St::st(G + q * P + node, k.omc * d[q] + (ev + od)); \
-            St::st(G + o * P + node, k.omc * d[o] + (ev - od)); \
-        } \
-    } \
- \
-    /* ---- species (D2Q5): react and collide with the fluid u, opposite */ \
-    /* directions together: g*_q = (1 - omega_D) g_q + w (omega_D phi + R) */ \
-    /* + w omega_D phi 3 v.u (scaled storage: 1/sigma_g for w) */ \
+    for (int q = 0; q < 9; ++q) St::st(G + q * P + node, d[q]); \
     if (S > 0) { \
-        const uint32_t bits = sbits & 0xFu; \
         T* Go = static_cast<T*>(a.gdst); \
-        C ph[S > 0 ? S : 1]; \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
-            if (SCALED) \
-                ph[s] = k.gscale[0] * g[s][0] + \
-                        k.gscale[1] * ((g[s][1] + g[s][2]) + (g[s][3] + g[s][4])); \
-            else \
-                ph[s] = ((g[s][0] + g[s][1]) + (g[s][2] + g[s][3])) + g[s][4]; \
-        } \
-        const C cux = ux, cuy = uy; \
 _Pragma("unroll") \
-        for (int s = 0; s < S; ++s) { \
-            C R = ((bits >> s) & 1u) ? k.srate[s] : C(0); \
-_Pragma("unroll") \
-            for (int b = 0; b < S; ++b) R += k.K[s][b] * ph[b]; \
-            T* B = Go + (int64_t)s * 5 * P; \
-            const C ev = k.omegaD[s] * ph[s] + R; \
-            const C od = k.omegaD[s] * ph[s] * C(3); \
-            const C eA = SCALED ? k.isig_g : C(w5(0)); \
-            const C eB = SCALED ? k.isig_g : C(w5(1)); \
-            const C evB = eB * ev; \
-            const C ox = eB * od * cux, oy = eB * od * cuy; \
-            St::st(B + node, k.omcD[s] * g[s][0] + eA * ev); \
-            St::st(B + 1 * P + node, k.omcD[s] * g[s][1] + (evB + ox)); \
-            St::st(B + 3 * P + node, k.omcD[s] * g[s][3] + (evB - ox)); \
-            St::st(B + 2 * P + node, k.omcD[s] * g[s][2] + (evB + oy)); \
-            St::st(B + 4 * P + node, k.omcD[s] * g[s][4] + (evB - oy)); \
+            for (int q = 0; q < 5; ++q) St::st(Go + (int64_t)(s * 5 + q) * P + node, g[s][q]); \
             if (a.out) static_cast<C*>(a.phi)[(int64_t)s * P + node] = ph[s]; \
         } \
     } \
@@ -281,94 +197,168 @@ _Pragma("unroll") \
     if (a.out) static_cast<C*>(a.rho)[node] = rho; \
     if (!(rho > C(0)) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.diag + kDiagNonFinite, 1u);
 
-// The collision of one node in registers: the arithmetic of the fused update
-// above, operation for operation, without its loads and stores.  d and g hold
-// the pulled populations in their stored form and are overwritten with the
-// post-collision stored values; rho, u and the species fields are returned.
-template <typename C, int S, int FORCING, bool SCALED>
-__device__ __forceinline__ void collide_node(const Coefs<C>& k, C (&d)[9],
-                                             C (&g)[S > 0 ? S : 1][5], C fvx, C fvy,
-                                             uint32_t sbits, C& rho, C& ux, C& uy,
-                                             C (&ph)[S > 0 ? S : 1]) {
-    const C Fx = k.bfx + fvx, Fy = k.bfy + fvy;
-    C drho, jx, jy;
+// Explicit round-to-nearest operations on the value of one node (float,
+// double) or of two nodes at once (float2: the packed FP32 instructions of
+// sm_100 and later, which per component are the float operation).  The
+// collision is written with them, so a node gets bit-identical results
+// whichever form evaluates it, and the compiler neither re-associates nor
+// contracts it.
+template <typename V>
+struct Lane;
+template <>
+struct Lane<float> {
+    using S = float;
+    static __device__ __forceinline__ float c(float s) { return s; }
+    static __device__ __forceinline__ float sel(bool a, bool, float v) { return a ? v : 0.f; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) {
+        return __fmaf_rn(a, b, c);
+    }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+};
+template <>
+struct Lane<float2> {
+    using S = float;
+    static __device__ __forceinline__ float2 c(float s) { return make_float2(s, s); }
+    static __device__ __forceinline__ float2 sel(bool a, bool b, float v) {
+        return make_float2(a ? v : 0.f, b ? v : 0.f);
+    }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+        return __fadd2_rn(a, make_float2(-b.x, -b.y));
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) {
+        return __ffma2_rn(a, b, c);
+    }
+    static __device__ __forceinline__ float2 rcp(float2 a) {
+        return make_float2(__frcp_rn(a.x), __frcp_rn(a.y));
+    }
+};
+template <>
+struct Lane<double> {
+    using S = double;
+    static __device__ __forceinline__ double c(double s) { return s; }
+    static __device__ __forceinline__ double sel(bool a, bool, double v) { return a ? v : 0.0; }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) {
+        return __fma_rn(a, b, c);
+    }
+    static __device__ __forceinline__ double rcp(double a) { return __drcp_rn(a); }
+};
+
+// The collision of one node (or two, V = float2) in registers, Sec. 6.1 in
+// deviation form:
+//   rho = rho0 + sum d,  u = (sum d v + F/2) / rho  (Guo; the paper's term: no F/2)
+//   with A = omega drho, W = omega rho, for a direction q and its opposite q':
+//   d*_q  = (1 - omega) d_q  + w (E + 3 W v.u + Co)
+//   d*_q' = (1 - omega) d_q' + w (E - 3 W v.u - Co)
+//   E = A + W (9/2 (v.u)^2 - 3/2 u.u) + Ce
+//   Guo: Ce = pref (9 (v.u)(v.F) - 3 u.F), Co = 3 pref v.F;  paper: Ce = 0, Co = 3 v.F
+// and every species (D2Q5) with phi = sum g, R = reaction + source:
+//   g*_q = (1 - omega_D) g_q + w (omega_D phi + R) + w 3 omega_D phi v.u
+// Scaled storage (FP16) keeps s_q = d_q / (w_q sigma): the moments weight the
+// stored values and 1/sigma replaces w.  d and g enter as the pulled stored
+// values and leave as the post-collision stored values; bitsA / bitsB are the
+// source bits of the node(s).
+template <typename V, int S, int FORCING, bool SCALED>
+__device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k, V (&d)[9],
+                                             V (&g)[S > 0 ? S : 1][5], V fvx, V fvy,
+                                             uint32_t bitsA, uint32_t bitsB, V& rho, V& ux,
+                                             V& uy, V (&ph)[S > 0 ? S : 1]) {
+    using L = Lane<V>;
+    using C = typename L::S;
+    const V Fx = L::add(L::c(k.bfx), fvx), Fy = L::add(L::c(k.bfy), fvy);
+    V drho, jx, jy;
     if (SCALED) {
-        const C sA = k.fscale[0], sB = k.fscale[1], sC = k.fscale[5];
-        drho = sA * d[0] + sB * ((d[1] + d[2]) + (d[3] + d[4])) +
-               sC * ((d[5] + d[6]) + (d[7] + d[8]));
-        jx = sB * (d[1] - d[3]) + sC * ((d[5] - d[6]) + (d[8] - d[7]));
-        jy = sB * (d[2] - d[4]) + sC * ((d[5] + d[6]) - (d[7] + d[8]));
+        const V sB = L::c(k.fscale[1]), sC = L::c(k.fscale[5]);
+        const V a14 = L::add(L::add(d[1], d[2]), L::add(d[3], d[4]));
+        const V a58 = L::add(L::add(d[5], d[6]), L::add(d[7], d[8]));
+        drho = L::fma(L::c(k.fscale[0]), d[0], L::fma(sB, a14, L::mul(sC, a58)));
+        jx = L::fma(sB, L::sub(d[1], d[3]),
+                    L::mul(sC, L::add(L::sub(d[5], d[6]), L::sub(d[8], d[7]))));
+        jy = L::fma(sB, L::sub(d[2], d[4]),
+                    L::mul(sC, L::sub(L::add(d[5], d[6]), L::add(d[7], d[8]))));
     } else {
-        drho = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-        jx = (d[1] - d[3]) + (d[5] - d[6]) + (d[8] - d[7]);
-        jy = (d[2] - d[4]) + (d[5] + d[6]) - (d[7] + d[8]);
+        drho = L::add(L::add(L::add(L::add(d[0], d[1]), L::add(d[2], d[3])),
+                             L::add(L::add(d[4], d[5]), L::add(d[6], d[7]))),
+                      d[8]);
+        jx = L::add(L::add(L::sub(d[1], d[3]), L::sub(d[5], d[6])), L::sub(d[8], d[7]));
+        jy = L::sub(L::add(L::sub(d[2], d[4]), L::add(d[5], d[6])), L::add(d[7], d[8]));
     }
-    rho = k.rho0 + drho;
-    const C irho = C(1) / rho;
+    rho = L::add(L::c(k.rho0), drho);
+    const V irho = L::rcp(rho);
     if (FORCING == LBIB_GUO) {
-        ux = (jx + C(0.5) * Fx) * irho;
-        uy = (jy + C(0.5) * Fy) * irho;
+        ux = L::mul(L::fma(L::c(C(0.5)), Fx, jx), irho);
+        uy = L::mul(L::fma(L::c(C(0.5)), Fy, jy), irho);
     } else {
-        ux = jx * irho;
-        uy = jy * irho;
+        ux = L::mul(jx, irho);
+        uy = L::mul(jy, irho);
     }
-    const C usq15 = C(1.5) * (ux * ux + uy * uy);
-    const C uF = ux * Fx + uy * Fy;
-    {
-        const C e0 = SCALED ? k.isig : C(w9(0));
-        C ev = k.omega * (drho - rho * usq15);
-        if (FORCING == LBIB_GUO) ev -= k.pref * (C(3) * uF);
-        d[0] = k.omc * d[0] + e0 * ev;
-    }
+    const V nusq = L::mul(L::c(C(-1.5)), L::fma(ux, ux, L::mul(uy, uy)));  // -3/2 u.u
+    const V A = L::mul(L::c(k.omega), drho);
+    const V W = L::mul(L::c(k.omega), rho);
+    const V W3 = L::mul(L::c(C(3)), W);
+    const V W45 = L::mul(L::c(C(4.5)), W);
+    V E0 = L::fma(W, nusq, A);  // the even part common to every direction
+    if (FORCING == LBIB_GUO)
+        E0 = L::fma(L::c(C(-3) * k.pref), L::fma(ux, Fx, L::mul(uy, Fy)), E0);
+    const V omc = L::c(k.omc);
+    d[0] = L::fma(L::c(SCALED ? k.isig : C(w9(0))), E0, L::mul(omc, d[0]));
 #pragma unroll
     for (int q = 1; q < 9; ++q) {
         if (q == 1 || q == 2 || q == 5 || q == 6) {
-            const int o = q + 2;
-            const C ew = SCALED ? k.isig : C(w9(q));
-            const C cu = C(cx(q)) * ux + C(cy(q)) * uy;
-            const C cF = C(cx(q)) * Fx + C(cy(q)) * Fy;
-            C ev = k.omega * (drho + rho * (C(4.5) * cu * cu - usq15));
-            C od = k.omega * (rho * (C(3) * cu));
+            const int o = q + 2;  // opposite of 1, 2, 5, 6
+            const V ew = L::c(SCALED ? k.isig : C(w9(q)));
+            // v.u and v.F of v = (1,0), (0,1), (1,1), (-1,1)
+            const V cu = q == 1 ? ux : (q == 2 ? uy : (q == 5 ? L::add(ux, uy) : L::sub(uy, ux)));
+            const V cF = q == 1 ? Fx : (q == 2 ? Fy : (q == 5 ? L::add(Fx, Fy) : L::sub(Fy, Fx)));
+            V ev = L::fma(W45, L::mul(cu, cu), E0);
+            V od = L::mul(W3, cu);
             if (FORCING == LBIB_GUO) {
-                ev += k.pref * (C(9) * cu * cF - C(3) * uF);
-                od += k.pref * (C(3) * cF);
+                ev = L::fma(L::c(C(9) * k.pref), L::mul(cu, cF), ev);
+                od = L::fma(L::c(C(3) * k.pref), cF, od);
             } else {
-                od += C(3) * cF;
+                od = L::fma(L::c(C(3)), cF, od);
             }
-            ev *= ew;
-            od *= ew;
-            const C dq = k.omc * d[q] + (ev + od);
-            const C doo = k.omc * d[o] + (ev - od);
+            const V dq = L::fma(ew, L::add(ev, od), L::mul(omc, d[q]));
+            const V dqo = L::fma(ew, L::sub(ev, od), L::mul(omc, d[o]));
             d[q] = dq;
-            d[o] = doo;
+            d[o] = dqo;
         }
     }
     if (S > 0) {
-        const uint32_t bits = sbits & 0xFu;
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             if (SCALED)
-                ph[s] = k.gscale[0] * g[s][0] +
-                        k.gscale[1] * ((g[s][1] + g[s][2]) + (g[s][3] + g[s][4]));
+                ph[s] = L::fma(L::c(k.gscale[0]), g[s][0],
+                               L::mul(L::c(k.gscale[1]),
+                                      L::add(L::add(g[s][1], g[s][2]), L::add(g[s][3], g[s][4]))));
             else
-                ph[s] = ((g[s][0] + g[s][1]) + (g[s][2] + g[s][3])) + g[s][4];
+                ph[s] = L::add(L::add(L::add(g[s][0], g[s][1]), L::add(g[s][2], g[s][3])),
+                               g[s][4]);
         }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            C R = ((bits >> s) & 1u) ? k.srate[s] : C(0);
+            V R = L::sel((bitsA >> s) & 1u, (bitsB >> s) & 1u, k.srate[s]);
 #pragma unroll
-            for (int b = 0; b < S; ++b) R += k.K[s][b] * ph[b];
-            const C ev = k.omegaD[s] * ph[s] + R;
-            const C od = k.omegaD[s] * ph[s] * C(3);
+            for (int b = 0; b < S; ++b) R = L::fma(L::c(k.K[s][b]), ph[b], R);
+            const V ev = L::fma(L::c(k.omegaD[s]), ph[s], R);
             const C eA = SCALED ? k.isig_g : C(w5(0));
             const C eB = SCALED ? k.isig_g : C(w5(1));
-            const C evB = eB * ev;
-            const C ox = eB * od * ux, oy = eB * od * uy;
-            g[s][0] = k.omcD[s] * g[s][0] + eA * ev;
-            g[s][1] = k.omcD[s] * g[s][1] + (evB + ox);
-            g[s][3] = k.omcD[s] * g[s][3] + (evB - ox);
-            g[s][2] = k.omcD[s] * g[s][2] + (evB + oy);
-            g[s][4] = k.omcD[s] * g[s][4] + (evB - oy);
+            const V evB = L::mul(L::c(eB), ev);
+            const V o3 = L::mul(L::c(C(3) * eB * k.omegaD[s]), ph[s]);
+            const V ox = L::mul(o3, ux), oy = L::mul(o3, uy);
+            const V omcD = L::c(k.omcD[s]);
+            g[s][0] = L::fma(L::c(eA), ev, L::mul(omcD, g[s][0]));
+            g[s][1] = L::fma(omcD, g[s][1], L::add(evB, ox));
+            g[s][3] = L::fma(omcD, g[s][3], L::sub(evB, ox));
+            g[s][2] = L::fma(omcD, g[s][2], L::add(evB, oy));
+            g[s][4] = L::fma(omcD, g[s][4], L::sub(evB, oy));
         }
     }
 }
