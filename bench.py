@@ -154,18 +154,36 @@ def lattice_kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload_name: str):
-    """DRAM bytes per lattice launch from the committed ncu summary, if it
-    was taken on the current lattice kernel source."""
+def ensemble_kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("ensemble.cu", "ib_cell.cuh", "lattice_node.cuh", "lbib_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1503_06726_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload_name: str, key: str = "dram_bytes_per_launch", sha=None):
+    """DRAM bytes per launch (or per step) from the committed ncu summary, if
+    it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "lattice_kernel_traffic.json")
     try:
         d = json.load(open(path))
         e = d.get(workload_name)
-        if e and e.get("kernel_sha") == lattice_kernel_hash():
-            return float(e["dram_bytes_per_launch"])
+        if e and e.get("kernel_sha") == (sha or lattice_kernel_hash()):
+            return float(e[key])
     except Exception:
         pass
     return None
+
+
+def fp64_flops_per_node(n_species: int, forcing: int) -> int:
+    """FP64 operations of the collision of one node as written (add, sub,
+    mul and reciprocal count 1, fma 2): force 2, moments 26, common even
+    part 18, four direction pairs 72, each species 25 + 2 S; the paper's
+    forcing term instead of Guo's drops 4 + 5 + 4 x 3."""
+    f = 2 + 26 + 18 + 72 + n_species * (25 + 2 * n_species)
+    if forcing == 1:
+        f -= 4 + 5 + 12
+    return f
 
 
 def max_over_ranks(x: float, dist, device) -> float:
@@ -294,7 +312,10 @@ def run_ensemble(args, rank, world, dist):
                    "launch": "one persistent cooperative kernel per step call",
                    "graph": info["graph"], "grid": info["grid"], "tuned": tune},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (lambda t: t * args.steps if t is not None else None)(
+                         recorded_traffic("c4-per-step", "dram_bytes_per_step",
+                                          ensemble_kernel_hash())),
                      "kernel": "ensemble_kernel (whole persistent launch: lattice + IB phases)",
                      "alg_bytes_per_node": bpn, "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
         "e2e": e2e, "gpu_launches": 1, "clocks": clk, "cpu_baseline": None,
@@ -549,6 +570,25 @@ def run_gb300(args, rank, world, dist):
     warm = None
     if world == 1 and not args.no_warm_start:
         warm = warm_start_sample(args, dev)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
+            "kernel": ("lattice_pair_kernel (two nodes per thread)"
+                       if prec == "fp16" and w.params.nx % 2 == 0 else "lattice_kernel"),
+            "alg_bytes_per_launch": alg_bytes,
+            "alg_bytes_per_node": bpn, "launch_ms": lat_avg,
+            "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+            "ib_launch_ms": ib_ms / (n_prof + 1)}
+    if prec == "fp64":
+        # GB300's FP64 rate, not HBM, bounds this kernel: report it against the
+        # FP64 peak (nominal 1.25 TFLOP/s = 152 SMs x 2.07 GHz x 2 FP64 FMA per
+        # SM per clock x 2), with the HBM figures kept beside it
+        fpn = fp64_flops_per_node(p.n_species, p.forcing)
+        gflops = fpn * N / (lat_avg * 1e-3) / 1e9
+        roof = dict(roof, bound="alu", achieved=gflops, peak=1250.0, unit="GFLOP/s",
+                    frac=gflops / 1250.0, alg_flops_per_node=fpn,
+                    peak_kind="nominal FP64 (no measured FP64 peak on this pool)",
+                    hbm={"achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak})
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -558,14 +598,7 @@ def run_gb300(args, rank, world, dist):
             "l2": f"inputs larger than L2: {ws / 2**20:.0f} MiB working set > 129 MiB L2, no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "graph": "two-step CUDA graph chunks"}),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": recorded_traffic(args.workload),
-                     "kernel": ("lattice_pair_kernel (two nodes per thread)"
-                                if prec == "fp16" and w.params.nx % 2 == 0 else "lattice_kernel"),
-                     "alg_bytes_per_launch": alg_bytes,
-                     "alg_bytes_per_node": bpn, "launch_ms": lat_avg,
-                     "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                     "ib_launch_ms": ib_ms / (n_prof + 1)},
+        "roofline": roof,
         "e2e": e2e,
         "warm_start": warm,
         "gpu_launches": 2 * args.steps + 1,
