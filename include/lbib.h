@@ -72,7 +72,9 @@ extern "C" {
 
 /* The global configuration of Sec. 3.1 (simulation size, viscosity through
  * tau, diffusion coefficients) plus the reaction terms of the species.
- *   nx, ny       lattice size (x periodic; y periodic or walls), >= 8 each
+ *   nx, ny       lattice size (x periodic; y periodic or walls), >= 8 each;
+ *                a plane (nx rounded up to a multiple of 64, times ny) must
+ *                hold fewer than 2^31 nodes (kernels index planes in 32 bits)
  *   bc_y         0: periodic in y; 1: half-way bounce-back walls at y = -1/2
  *                and y = ny - 1/2 for the fluid and the species
  *   n_species    0..4 D2Q5 species

@@ -42,16 +42,18 @@ template <>
 struct Vec2<float> { using T = float2; };
 
 // Pull the 5 populations of one D2Q5 set (or the first 5 of D2Q9) at a node.
+// Addresses are a plane base (the same for every thread) plus a 32-bit index
+// within the plane (a plane holds fewer than 2^31 elements).
 template <typename T, typename C, bool WALLS>
-__device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64_t r0, int64_t rm,
-                                      int64_t rp, int x, int xm, int xp, bool lo, bool hi,
-                                      uint64_t pol, C g[5]) {
+__device__ __forceinline__ void pull5(const T* B, int64_t P, int node, int r0, int rm, int rp,
+                                      int x, int xm, int xp, bool lo, bool hi, uint64_t pol,
+                                      C g[5]) {
     using St = Store<T, C>;
     g[0] = St::ld(B + node, pol);
-    g[1] = St::ld(B + 1 * P + r0 + xm, pol);
-    g[3] = St::ld(B + 3 * P + r0 + xp, pol);
-    g[2] = (WALLS && lo) ? St::ld(B + 4 * P + node, pol) : St::ld(B + 2 * P + rm + x, pol);
-    g[4] = (WALLS && hi) ? St::ld(B + 2 * P + node, pol) : St::ld(B + 4 * P + rp + x, pol);
+    g[1] = St::ld((B + 1 * P) + (r0 + xm), pol);
+    g[3] = St::ld((B + 3 * P) + (r0 + xp), pol);
+    g[2] = (WALLS && lo) ? St::ld((B + 4 * P) + node, pol) : St::ld((B + 2 * P) + (rm + x), pol);
+    g[4] = (WALLS && hi) ? St::ld((B + 2 * P) + node, pol) : St::ld((B + 4 * P) + (rp + x), pol);
 }
 
 // The update of one node (x, y).  Callers map the 32 lanes of a warp to 32
@@ -77,10 +79,10 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
     const bool hi_wall = WALLS && (y == a.ny - 1); \
     const int ym = (y == 0) ? a.ny - 1 : y - 1; \
     const int yp = (y == a.ny - 1) ? 0 : y + 1; \
-    const int64_t r0 = (int64_t)y * a.pitch; \
-    const int64_t rm = (int64_t)ym * a.pitch; \
-    const int64_t rp = (int64_t)yp * a.pitch; \
-    const int64_t node = r0 + x; \
+    const int r0 = y * (int)a.pitch; \
+    const int rm = ym * (int)a.pitch; \
+    const int rp = yp * (int)a.pitch; \
+    const int node = r0 + x; \
  \
     /* ---- every load of the node first (all independent, read-only path), so */ \
     /* that a thread has all its DRAM requests in flight at once */ \
@@ -89,18 +91,18 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int64_t node, int64
     const uint64_t pol = a.l2_first ? l2_evict_first() : l2_evict_normal(); \
     pull5<T, C, WALLS>(F, P, node, r0, rm, rp, x, xm, xp, lo_wall, hi_wall, pol, d); \
     if (lo_wall) {  /* half-way bounce-back: v_y = +1 populations reflect off y = -1/2 */ \
-        d[5] = St::ld(F + 7 * P + node, pol); \
-        d[6] = St::ld(F + 8 * P + node, pol); \
+        d[5] = St::ld((F + 7 * P) + node, pol); \
+        d[6] = St::ld((F + 8 * P) + node, pol); \
     } else { \
-        d[5] = St::ld(F + 5 * P + rm + xm, pol); \
-        d[6] = St::ld(F + 6 * P + rm + xp, pol); \
+        d[5] = St::ld((F + 5 * P) + (rm + xm), pol); \
+        d[6] = St::ld((F + 6 * P) + (rm + xp), pol); \
     } \
     if (hi_wall) {  /* v_y = -1 populations reflect off y = ny - 1/2 */ \
-        d[7] = St::ld(F + 5 * P + node, pol); \
-        d[8] = St::ld(F + 6 * P + node, pol); \
+        d[7] = St::ld((F + 5 * P) + node, pol); \
+        d[8] = St::ld((F + 6 * P) + node, pol); \
     } else { \
-        d[7] = St::ld(F + 7 * P + rp + xp, pol); \
-        d[8] = St::ld(F + 8 * P + rp + xm, pol); \
+        d[7] = St::ld((F + 7 * P) + (rp + xp), pol); \
+        d[8] = St::ld((F + 8 * P) + (rp + xm), pol); \
     } \
     C g[S > 0 ? S : 1][5]; \
     { \
@@ -125,7 +127,7 @@ _Pragma("unroll") \
     bool fhit = false, lhit = false, shit = false; \
     /* for lane 0: which masks hold bits of this warp's 8 groups */ \
     uint32_t clear = 0u; \
-    const int64_t grp = node >> 2; \
+    const int grp = node >> 2; \
     if (a.ib) { \
         if (a.fmask) { \
             const int sh = (int)(grp & 31); \
@@ -152,14 +154,14 @@ _Pragma("unroll") \
     collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph); \
     T* G = static_cast<T*>(a.fdst); \
 _Pragma("unroll") \
-    for (int q = 0; q < 9; ++q) St::st(G + q * P + node, d[q]); \
+    for (int q = 0; q < 9; ++q) St::st((G + q * P) + node, d[q]); \
     if (S > 0) { \
         T* Go = static_cast<T*>(a.gdst); \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
 _Pragma("unroll") \
-            for (int q = 0; q < 5; ++q) St::st(Go + (int64_t)(s * 5 + q) * P + node, g[s][q]); \
-            if (a.out) static_cast<C*>(a.phi)[(int64_t)s * P + node] = ph[s]; \
+            for (int q = 0; q < 5; ++q) St::st((Go + (int64_t)(s * 5 + q) * P) + node, g[s][q]); \
+            if (a.out) (static_cast<C*>(a.phi) + (int64_t)s * P)[node] = ph[s]; \
         } \
     } \
  \

@@ -39,6 +39,8 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     // planes are padded by 1.5 KiB (six 256-byte blocks) so that the 9 + 5S
     // streams of one node do not sit at a power-of-two distance from each other
     l.plane = l.pitch * p.ny + 1536 / l.es;
+    // the kernels index within a plane with 32-bit integers
+    if (l.plane > (int64_t)0x7FFFFFFF) return false;
     const uint64_t P = (uint64_t)l.plane;
     uint64_t o = 0;
     auto take = [&](uint64_t bytes) {
