@@ -27,12 +27,14 @@
 
 namespace lbib {
 
-// CTAs of 128 threads.  FP32/FP16 storage is held to 48 registers with one
-// species (10 CTAs, 40 warps per SM: more loads in flight, measured faster),
-// 56 with two (9 CTAs; 48 spilled) and 64 with more (8 CTAs, no spills).
+// CTAs of 128 threads.  FP32/FP16 storage is held to 40 registers with at
+// most one species (12 CTAs, 48 warps per SM: more loads in flight), 48 with
+// two (10 CTAs) and 64 with more (8 CTAs), none of them spilling since the
+// in-plane indices are 32-bit (4096^2: 327 -> 311 us; 1024^2, two species:
+// 28.6 -> 27.8 us against 48 / 56 registers).
 template <typename T, int S>
 struct LatticeOccupancy {
-    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (S <= 1 ? 10 : (S == 2 ? 9 : 8));
+    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (S <= 1 ? 12 : (S == 2 ? 10 : 8));
 };
 constexpr int kLatticeThreads = 128;
 
