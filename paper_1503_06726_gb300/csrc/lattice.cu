@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kLatticeThreads, LatticeOccupancy<T, S>::kMinB
 // 102 with two, 128 with three or four (no spills).
 template <int S>
 struct PairOccupancy {
-    static constexpr int kMinBlocks = S == 0 ? 8 : (S == 1 ? 7 : (S == 2 ? 5 : 4));
+    static constexpr int kMinBlocks = S == 0 ? 8 : (S == 1 ? 7 : (S == 2 ? 6 : 4));
 };
 
 __device__ __forceinline__ uint32_t ldw(const uint32_t* p, uint64_t pol) {
@@ -108,17 +108,19 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     const int ym = (y == 0) ? a.ny - 1 : y - 1;
     const int yp = (y == a.ny - 1) ? 0 : y + 1;
     const int64_t P2 = a.plane >> 1;  // words per plane
-    const int64_t r0 = (int64_t)y * a.pitch;
-    const int64_t rm = (int64_t)ym * a.pitch;
-    const int64_t rp = (int64_t)yp * a.pitch;
-    const int64_t node = r0 + x0;
-    const int64_t w = node >> 1, wm = (rm + x0) >> 1, wp = (rp + x0) >> 1;
+    // in-plane indices are 32-bit (a plane holds fewer than 2^31 nodes); the
+    // plane bases (F + q * P2 and so on) are the same for every thread
+    const int r0 = y * (int)a.pitch;
+    const int rm = ym * (int)a.pitch;
+    const int rp = yp * (int)a.pitch;
+    const int node = r0 + x0;
+    const int w = node >> 1, wm = (rm + x0) >> 1, wp = (rp + x0) >> 1;
     const int xl = (x0 == 0) ? a.nx - 2 : x0 - 2;
     const int xr = (x0 + 2 >= a.nx) ? 0 : x0 + 2;
     const bool own_l = valid && lane == 0;
     const bool own_r = valid && (lane == 31 || x0 + 2 >= a.nx);
-    const int64_t l0 = (r0 + xl) >> 1, lm = (rm + xl) >> 1, lp = (rp + xl) >> 1;
-    const int64_t q0 = (r0 + xr) >> 1, qm = (rm + xr) >> 1, qp = (rp + xr) >> 1;
+    const int l0 = (r0 + xl) >> 1, lm = (rm + xl) >> 1, lp = (rp + xl) >> 1;
+    const int q0 = (r0 + xr) >> 1, qm = (rm + xr) >> 1, qp = (rp + xr) >> 1;
 
     // ---- every population word first (written two launches back: L2 path)
     const uint64_t pol = a.l2_first ? l2_evict_first() : l2_evict_normal();
@@ -128,33 +130,33 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     for (int q = 0; q < 9; ++q) r[q] = e[q] = 0u;
     if (valid) {
         r[0] = ldw(F + w, pol);
-        r[1] = ldw(F + 1 * P2 + w, pol);
-        r[3] = ldw(F + 3 * P2 + w, pol);
-        r[2] = lo_wall ? ldw(F + 4 * P2 + w, pol) : ldw(F + 2 * P2 + wm, pol);
-        r[4] = hi_wall ? ldw(F + 2 * P2 + w, pol) : ldw(F + 4 * P2 + wp, pol);
+        r[1] = ldw((F + 1 * P2) + w, pol);
+        r[3] = ldw((F + 3 * P2) + w, pol);
+        r[2] = lo_wall ? ldw((F + 4 * P2) + w, pol) : ldw((F + 2 * P2) + wm, pol);
+        r[4] = hi_wall ? ldw((F + 2 * P2) + w, pol) : ldw((F + 4 * P2) + wp, pol);
         if (lo_wall) {  // half-way bounce-back at y = -1/2
-            r[5] = ldw(F + 7 * P2 + w, pol);
-            r[6] = ldw(F + 8 * P2 + w, pol);
+            r[5] = ldw((F + 7 * P2) + w, pol);
+            r[6] = ldw((F + 8 * P2) + w, pol);
         } else {
-            r[5] = ldw(F + 5 * P2 + wm, pol);
-            r[6] = ldw(F + 6 * P2 + wm, pol);
+            r[5] = ldw((F + 5 * P2) + wm, pol);
+            r[6] = ldw((F + 6 * P2) + wm, pol);
         }
         if (hi_wall) {  // at y = ny - 1/2
-            r[7] = ldw(F + 5 * P2 + w, pol);
-            r[8] = ldw(F + 6 * P2 + w, pol);
+            r[7] = ldw((F + 5 * P2) + w, pol);
+            r[8] = ldw((F + 6 * P2) + w, pol);
         } else {
-            r[7] = ldw(F + 7 * P2 + wp, pol);
-            r[8] = ldw(F + 8 * P2 + wp, pol);
+            r[7] = ldw((F + 7 * P2) + wp, pol);
+            r[8] = ldw((F + 8 * P2) + wp, pol);
         }
         if (own_l) {
-            e[1] = ldw(F + 1 * P2 + l0, pol);
-            if (!lo_wall) e[5] = ldw(F + 5 * P2 + lm, pol);
-            if (!hi_wall) e[8] = ldw(F + 8 * P2 + lp, pol);
+            e[1] = ldw((F + 1 * P2) + l0, pol);
+            if (!lo_wall) e[5] = ldw((F + 5 * P2) + lm, pol);
+            if (!hi_wall) e[8] = ldw((F + 8 * P2) + lp, pol);
         }
         if (own_r) {
-            e[3] = ldw(F + 3 * P2 + q0, pol);
-            if (!lo_wall) e[6] = ldw(F + 6 * P2 + qm, pol);
-            if (!hi_wall) e[7] = ldw(F + 7 * P2 + qp, pol);
+            e[3] = ldw((F + 3 * P2) + q0, pol);
+            if (!lo_wall) e[6] = ldw((F + 6 * P2) + qm, pol);
+            if (!hi_wall) e[7] = ldw((F + 7 * P2) + qp, pol);
         }
     }
     uint32_t rg[SS][5], eg[SS][2];
@@ -169,12 +171,12 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
         for (int s = 0; s < S; ++s) {
             const uint32_t* B = Gi + (int64_t)s * 5 * P2;
             rg[s][0] = ldw(B + w, pol);
-            rg[s][1] = ldw(B + 1 * P2 + w, pol);
-            rg[s][3] = ldw(B + 3 * P2 + w, pol);
-            rg[s][2] = lo_wall ? ldw(B + 4 * P2 + w, pol) : ldw(B + 2 * P2 + wm, pol);
-            rg[s][4] = hi_wall ? ldw(B + 2 * P2 + w, pol) : ldw(B + 4 * P2 + wp, pol);
-            if (own_l) eg[s][0] = ldw(B + 1 * P2 + l0, pol);
-            if (own_r) eg[s][1] = ldw(B + 3 * P2 + q0, pol);
+            rg[s][1] = ldw((B + 1 * P2) + w, pol);
+            rg[s][3] = ldw((B + 3 * P2) + w, pol);
+            rg[s][2] = lo_wall ? ldw((B + 4 * P2) + w, pol) : ldw((B + 2 * P2) + wm, pol);
+            rg[s][4] = hi_wall ? ldw((B + 2 * P2) + w, pol) : ldw((B + 4 * P2) + wp, pol);
+            if (own_l) eg[s][0] = ldw((B + 1 * P2) + l0, pol);
+            if (own_r) eg[s][1] = ldw((B + 3 * P2) + q0, pol);
         }
     }
     // the IB kernel launched just before wrote the force, label and mask
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     uint32_t sb2 = 0u;
     bool fhit = false, lhit = false, shit = false;
     uint32_t clear = 0u;  // lane 0: which masks hold bits of the warp's 16 groups
-    const int64_t grp = node >> 2;
+    const int grp = node >> 2;
     if (a.ib) {
         if (a.fmask) {
             const int sh = (int)(grp & 31);
@@ -249,13 +251,13 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
 
     uint32_t* G = static_cast<uint32_t*>(a.fdst);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) G[q * P2 + w] = pack_halves(d[q]);
+    for (int q = 0; q < 9; ++q) (G + q * P2)[w] = pack_halves(d[q]);
     if (S > 0) {
         uint32_t* Go = static_cast<uint32_t*>(a.gdst);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) Go[(int64_t)(s * 5 + q) * P2 + w] = pack_halves(g[s][q]);
+            for (int q = 0; q < 5; ++q) (Go + (int64_t)(s * 5 + q) * P2)[w] = pack_halves(g[s][q]);
             if (a.out)
                 reinterpret_cast<float2*>(static_cast<C*>(a.phi) + (int64_t)s * a.plane)[node >> 1] =
                     ph[s];
