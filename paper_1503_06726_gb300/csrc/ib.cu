@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
     if (!labels) return;  // uniform over the CTA
     __syncthreads();
 
-    fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols, threadIdx.x,
+    fill_labels_call(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols, threadIdx.x,
                 kIBThreads);
 }
 
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
     S.sb = reinterpret_cast<int2*>(S.sx + maxv);
     S.sf = reinterpret_cast<float2*>(S.sb + maxv);
     S.maxv = maxv;
-    ib_cell_f32<NT, true>(a, blockIdx.x, S, threadIdx.x, 0);
+    ib_cell_f32<NT, true, NT == 256>(a, blockIdx.x, S, threadIdx.x, 0);
 }
 
 cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s, bool pdl) {

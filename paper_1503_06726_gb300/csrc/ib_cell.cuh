@@ -169,7 +169,7 @@ __device__ __forceinline__ void label_node(const IBArgs& a, int64_t node, uint32
     if (bits) src_or_node(a, node, bits);
 }
 
-static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, const double2* sx,
+static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, int n, const double2* sx,
                                          const int* rowcnt, int* thr, bool scan_ok, int I0,
                                          int J0, int rows, int cols, int tid, int nthreads) {
     const int lane = tid & 31, warp = tid >> 5;
@@ -279,6 +279,15 @@ static __device__ __noinline__ void fill_labels(const IBArgs& a, int c, int n, c
     }
 }
 
+// out of line: keeps the register budget of the callers that hold more state
+// (the ensemble's persistent kernel)
+static __device__ __noinline__ void fill_labels_call(const IBArgs& a, int c, int n,
+                                                     const double2* sx, const int* rowcnt,
+                                                     int* thr, bool scan_ok, int I0, int J0,
+                                                     int rows, int cols, int tid, int nthreads) {
+    fill_labels_body(a, c, n, sx, rowcnt, thr, scan_ok, I0, J0, rows, cols, tid, nthreads);
+}
+
 // Barrier of the NT threads that work on one cell: `bar` 0 with a CTA of NT
 // threads, or a named barrier of its own for each NT-thread part of a larger
 // CTA that works on several cells at once.
@@ -339,7 +348,11 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 // caller is a kernel of its own (programmatic launch after a lattice launch):
 // the cell's constant data and its vertex state (written by the IB launch two
 // launches back) are loaded through L2 before the wait, the u plane after it.
-template <int NT, bool GRIDDEP>
+// INLINE_FILL: the label fill inlined (the 256-thread kernel: no spills, no
+// parameter reads through a pointer; 1024^2 step 40.9 -> 38.4 us) or called
+// out of line (the small-CTA kernels keep 64 registers, 16 CTAs per SM, and
+// the ensemble's persistent kernel its budget)
+template <int NT, bool GRIDDEP, bool INLINE_FILL = true>
 static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, int tid,
                                    int bar) {
     static_assert(NT % 64 == 0, "CTA size");
@@ -439,12 +452,33 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                     J = wrapi(J, a.ny);
                 }
                 const float2* row = u + (int64_t)J * a.pitch;
+                // the four nodes of the row, 16 bytes per load where aligned
+                float2 v[4];
+                if (ix[3] == ix[0] + 3) {
+                    const float2* r0 = row + ix[0];
+                    if ((ix[0] & 1) == 0) {
+                        const float4 p0 = *reinterpret_cast<const float4*>(r0);
+                        const float4 p1 = *reinterpret_cast<const float4*>(r0 + 2);
+                        v[0] = make_float2(p0.x, p0.y);
+                        v[1] = make_float2(p0.z, p0.w);
+                        v[2] = make_float2(p1.x, p1.y);
+                        v[3] = make_float2(p1.z, p1.w);
+                    } else {
+                        const float4 p1 = *reinterpret_cast<const float4*>(r0 + 1);
+                        v[0] = r0[0];
+                        v[1] = make_float2(p1.x, p1.y);
+                        v[2] = make_float2(p1.z, p1.w);
+                        v[3] = r0[3];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v[i] = row[ix[i]];
+                }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float2 v = row[ix[i]];
                     const float w = wx[i] * wy[j];
-                    Ux += v.x * w;
-                    Uy += v.y * w;
+                    Ux += v[i].x * w;
+                    Uy += v[i].y * w;
                 }
             }
             X.x += (double)Ux;
@@ -548,10 +582,29 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                         J = wrapi(J, a.ny);
                     }
                     float2* row = force + (int64_t)J * a.pitch;
+                    float cx4[4], cy4[4];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float w = wx[i] * wy[j];
-                        spread_add(&row[ix[i]], Fx * w, Fy * w);
+                        cx4[i] = Fx * w;
+                        cy4[i] = Fy * w;
+                    }
+                    // the four nodes of the row: two 16-byte reductions when
+                    // the row starts on an even node, 8 + 16 + 8 bytes when it
+                    // starts on an odd one, one per node across the periodic seam
+                    if (ix[3] == ix[0] + 3) {
+                        float2* r0 = row + ix[0];
+                        if ((ix[0] & 1) == 0) {
+                            red_keep2(r0, cx4[0], cy4[0], cx4[1], cy4[1]);
+                            red_keep2(r0 + 2, cx4[2], cy4[2], cx4[3], cy4[3]);
+                        } else {
+                            red_keep(r0, cx4[0], cy4[0]);
+                            red_keep2(r0 + 1, cx4[1], cy4[1], cx4[2], cy4[2]);
+                            red_keep(r0 + 3, cx4[3], cy4[3]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) spread_add(&row[ix[i]], cx4[i], cy4[i]);
                     }
                     mark_row(a.fmask, (int64_t)J * a.pitch, ix);
                 }
@@ -592,7 +645,12 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
     }
     if (!labels) return;  // uniform over the CTA
     cell_sync<NT>(bar);
-    fill_labels(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols, tid, NT);
+    if (INLINE_FILL)
+        fill_labels_body(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols, tid,
+                         NT);
+    else
+        fill_labels_call(a, c, n, sx, rowcnt, thr, scan && s_flag == 0, I0, J0, rows, cols, tid,
+                         NT);
 }
 
 }  // namespace lbib

@@ -239,10 +239,16 @@ __device__ __forceinline__ void st_keep(float4* p, float4 v) {
                  :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(l2_evict_last())
                  : "memory");
 }
-// accumulation into the force plane, evict-last
+// accumulation into the force plane, evict-last: one node (8 bytes) or two
+// adjacent nodes (16 bytes, p 16-byte aligned) per operation
 __device__ __forceinline__ void red_keep(float2* p, float x, float y) {
     asm volatile("red.global.add.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
                  :: "l"(p), "f"(x), "f"(y), "l"(l2_evict_last()) : "memory");
+}
+__device__ __forceinline__ void red_keep2(float2* p, float x0, float y0, float x1, float y1) {
+    asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(p), "f"(x0), "f"(y0), "f"(x1), "f"(y1), "l"(l2_evict_last())
+                 : "memory");
 }
 
 // launch `kern` on stream s, with programmatic serialization when pdl is set
