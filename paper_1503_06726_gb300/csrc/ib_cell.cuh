@@ -120,10 +120,10 @@ __device__ __forceinline__ void mark_node_warp(uint32_t* mask, int64_t node) {
 // Mark the groups of the nodes [s, e) of one row (no wrap inside the range)
 // in `mask`: lanes take one 32-group word each.
 __device__ __forceinline__ void mark_range(uint32_t* mask, int64_t rowbase, int s, int e,
-                                           int lane) {
+                                           int lane, int step = 32) {
     if (!mask || e <= s) return;
     const int64_t ga = (rowbase + s) >> 2, gb = (rowbase + e - 1) >> 2;
-    for (int64_t w = (ga >> 5) + lane; w <= (gb >> 5); w += 32) {
+    for (int64_t w = (ga >> 5) + lane; w <= (gb >> 5); w += step) {
         const unsigned lo = (w == (ga >> 5)) ? (unsigned)(ga & 31) : 0u;
         const unsigned hi = (w == (gb >> 5)) ? (unsigned)(gb & 31) : 31u;
         const uint32_t bits = ((2u << hi) - 1u) & ~((1u << lo) - 1u);
@@ -151,11 +151,12 @@ __device__ __forceinline__ void src_or_node(const IBArgs& a, int64_t node, uint3
 
 // OR the source bits into the bytes [s, e) of one row of the byte plane (row
 // start 8-byte aligned): one 64-bit atomic per 8 nodes, lanes take words
-__device__ __forceinline__ void src_or_range(uint8_t* row, int s, int e, uint32_t bits, int lane) {
+__device__ __forceinline__ void src_or_range(uint8_t* row, int s, int e, uint32_t bits, int lane,
+                                             int step = 32) {
     if (e <= s) return;
     const unsigned long long rep = 0x0101010101010101ull * (unsigned long long)bits;
     unsigned long long* wrow = reinterpret_cast<unsigned long long*>(row);
-    for (int w = (s >> 3) + lane; w <= ((e - 1) >> 3); w += 32) {
+    for (int w = (s >> 3) + lane; w <= ((e - 1) >> 3); w += step) {
         const int a0 = max(s - 8 * w, 0), a1 = min(e - 8 * w, 8);
         const unsigned long long m =
             (a1 - a0 == 8) ? ~0ull : (((1ull << (8 * (a1 - a0))) - 1ull) << (8 * a0));
@@ -179,6 +180,60 @@ static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, 
     const uint32_t bits = a.src ? cbits : 0u;
     const uint32_t code = ((uint32_t)c << 4) | cbits;
     const int wI0 = wrapi(I0, a.nx), wJ0 = wrapi(J0, a.ny);
+    if (scan_ok && !a.do_ids && !a.src_words && a.src) {
+        // source bits only (every step between outputs): one thread per row,
+        // so all rows of the cell at once, each span a few 8-byte ORs
+        for (int r = tid; r < rows; r += nthreads) {
+            const int J = J0 + r;
+            if (a.bc_y && (J < 0 || J >= a.ny)) continue;
+            const int m = rowcnt[r];
+            int* tr = thr + r * kMaxCross;
+            for (int q = 1; q < m; ++q) {
+                const int v = tr[q];
+                int p = q - 1;
+                while (p >= 0 && tr[p] > v) {
+                    tr[p + 1] = tr[p];
+                    --p;
+                }
+                tr[p + 1] = v;
+            }
+            int wJ = wJ0 + r;
+            if (wJ >= a.ny) wJ -= a.ny;
+            const int64_t rb = (int64_t)wJ * a.pitch;
+            uint8_t* row = static_cast<uint8_t*>(a.src) + rb;
+            if ((m & 1) == 0) {
+                for (int k = 0; k + 1 < m; k += 2) {
+                    const int lo = tr[k], hi = tr[k + 1];
+                    if (hi <= lo) continue;
+                    int ws = wI0 + (lo - I0);
+                    if (ws >= a.nx) ws -= a.nx;
+                    const int len = hi - lo;
+                    const int e1 = ws + len <= a.nx ? ws + len : a.nx;
+                    const int e2 = ws + len - a.nx;  // > 0 when the span wraps
+                    src_or_range(row, ws, e1, bits, 0, 1);
+                    mark_range(a.smask, rb, ws, e1, 0, 1);
+                    if (e2 > 0) {
+                        src_or_range(row, 0, e2, bits, 0, 1);
+                        mark_range(a.smask, rb, 0, e2, 0, 1);
+                    }
+                }
+            } else {  // odd count: the parity rule node by node
+                for (int cc = 0; cc < cols; ++cc) {
+                    const int I = I0 + cc;
+                    int cnt = 0;
+                    for (int q = 0; q < m; ++q) cnt += (tr[q] > I);
+                    if (cnt & 1) {
+                        int wI = wI0 + cc;
+                        if (wI >= a.nx) wI -= a.nx;
+                        label_node(a, rb + wI, code, bits);
+                        const int64_t g = (rb + wI) >> 2;
+                        if (a.smask) atomicOr(a.smask + (g >> 5), 1u << (g & 31));
+                    }
+                }
+            }
+        }
+        return;
+    }
     if (scan_ok) {
         // one warp per row: sort the row's thresholds, then fill each span
         // [t_{2k}, t_{2k+1}) -- the nodes with an odd number of thresholds
