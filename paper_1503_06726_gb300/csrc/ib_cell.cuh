@@ -439,17 +439,20 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
         s_flag = 0;
     }
 
-    // spring data of the vertices this thread will handle in phase 2 (the
-    // first half of the CTA), loaded now so that phase 2 waits on no load
+    // spring data of the vertices this thread will handle in phase 2, loaded
+    // now so that phase 2 waits on no load: vertex tid (every thread: the whole
+    // CTA computes forces when the cell is not labelled) and vertex tid + half
+    // (the first half, which alone computes forces while the second half
+    // scans the rows of a labelled cell)
     constexpr int half = kIBThreads / 2;
     float pL0[2] = {0.f, 0.f}, pk[2] = {0.f, 0.f}, pL0p[2] = {0.f, 0.f}, pkp[2] = {0.f, 0.f};
     float ppres = 0.f;
-    if (a.do_prep && a.do_force && tid < half) {
+    if (a.do_prep && a.do_force) {
         ppres = (float)__ldcg(a.pres + c);
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int t = tid + r * half;
-            if (t < n) {
+            if (t < n && (r == 0 || tid < half)) {
                 const int tp = (t == 0) ? n - 1 : t - 1;
                 pL0[r] = (float)__ldcg(a.L0 + v0 + t);
                 pk[r] = (float)__ldcg(a.k + v0 + t);
@@ -587,12 +590,13 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
     const int rows = J1 - J0 + 1, cols = I1 - I0 + 1;
     const bool scan = labels && rows <= kMaxRows;
 
-    if (tid < half) {
+    if (tid < half || !scan) {  // forces: the first half, or all threads without a scan
         if (a.do_force) {
             float2* force = static_cast<float2*>(a.force);
             const float p = ppres;
             const float ten = (float)a.tension;
-            for (int t = tid, r = 0; t < n; t += half, ++r) {
+            const int stride = scan ? half : kIBThreads;
+            for (int t = tid, r = 0; t < n; t += stride, ++r) {
                 const int tp = (t == 0) ? n - 1 : t - 1;
                 const int tn = (t == n - 1) ? 0 : t + 1;
                 const int2 b = sb[t];
@@ -600,10 +604,11 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                 const float2 dn = edge_vec(b, f, sb[tn], sf[tn]);   // X_{t+1} - X_t
                 const float2 dp = edge_vec(sb[tp], sf[tp], b, f);   // X_t - X_{t-1}
                 // prefetched for the first two vertices of this thread
-                const float L0t = r == 0 ? pL0[0] : (r == 1 ? pL0[1] : (float)a.L0[v0 + t]);
-                const float kt = r == 0 ? pk[0] : (r == 1 ? pk[1] : (float)a.k[v0 + t]);
-                const float L0p = r == 0 ? pL0p[0] : (r == 1 ? pL0p[1] : (float)a.L0[v0 + tp]);
-                const float kp = r == 0 ? pkp[0] : (r == 1 ? pkp[1] : (float)a.k[v0 + tp]);
+                const bool pre1 = r == 1 && stride == half;  // tid + half, prefetched
+                const float L0t = r == 0 ? pL0[0] : (pre1 ? pL0[1] : (float)a.L0[v0 + t]);
+                const float kt = r == 0 ? pk[0] : (pre1 ? pk[1] : (float)a.k[v0 + t]);
+                const float L0p = r == 0 ? pL0p[0] : (pre1 ? pL0p[1] : (float)a.L0[v0 + tp]);
+                const float kp = r == 0 ? pkp[0] : (pre1 ? pkp[1] : (float)a.k[v0 + tp]);
                 const float2 s0 = spring32(dn, L0t, kt);
                 const float2 s1 = spring32(dp, L0p, kp);
                 float Fx = s0.x - s1.x, Fy = s0.y - s1.y;
