@@ -23,7 +23,9 @@ Other workloads (--workload): c3-fp32, c3-fp16, c3-fp64 (the 4096^2
 periodic tissue of 9,801 cells with FP32 / FP16-shifted / FP64 storage);
 c3-precision (that tissue with all three storages, errors against FP64);
 c4 (64 independent tissues in one persistent launch); c5 (the learned warm
-start of the steady morphogen solve, warm vs cold).
+start of the steady morphogen solve, warm vs cold); case4 (the immersed-
+boundary leakage study: area loss under constant membrane tension at four
+refinements and its order of convergence).
 
 --impl reference times the FP64 oracle (the reference arm of this build)
 on the same workload and metric.
@@ -472,7 +474,58 @@ def run_precision(args, rank, world, dist):
     }
 
 
+def run_case4(args, rank, world, dist):
+    """The immersed-boundary leakage study (validation Case IV): relative area
+    loss of a circular cell under constant membrane tension at four lattice
+    refinements, and the observed order of convergence."""
+    import math
+    import torch
+    from paper_1503_06726_gb300 import lbib
+
+    lbib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    levels, nodes_steps, t_gpu = [], 0, 0.0
+    for k in range(4):
+        w = li.case4(k, args.case4_max_length)
+        T = w.tissue
+        sim = lbib.Simulation(w.params, lbib.LBIB_FP32, T.n_vertices, T.n_cells, device=dev)
+        sim.set_cells(T)
+        sim.step(1)
+        a0 = float(sim.fields(lbib.LBIB_AREA)["area"][0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(w.n_steps - 1)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        a1 = float(sim.fields(lbib.LBIB_AREA)["area"][0])
+        sim.close()
+        nodes_steps += w.params.nx * w.params.ny * (w.n_steps - 1)
+        t_gpu += dt
+        levels.append({"lattice": w.params.nx, "diameter": 10 * 2 ** k, "vertices": T.n_vertices,
+                       "steps": w.n_steps, "tension_lb": w.params.tension,
+                       "area_loss_rel": (a0 - a1) / a0, "seconds": dt})
+    loss = [lv["area_loss_rel"] for lv in levels]
+    orders = [math.log2(loss[k] / loss[k + 1]) for k in range(3)]
+    if rank != 0:
+        return None
+    return {
+        "metric": "IB leakage: observed order of the relative area loss (validation Case IV)",
+        "value": orders[-1], "unit": "order (two finest lattices)", "n_gpus": world,
+        "steps": sum(lv["steps"] for lv in levels), "warmup": 1,
+        "ms_per_step": None, "higher_is_better": None, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (one circular cell, no random input)",
+        "config": {"workload": "case4_dia10-80_lattice100-800", "max_length": args.case4_max_length,
+                   "bc": "periodic (the study's outflow boundary is out of scope)"},
+        "orders": orders, "levels": levels,
+        "paper": {"order": "about 1", "two_finest": 0.9891},
+        "mlups": nodes_steps / t_gpu / 1e6,
+    }
+
+
 def run_gb300(args, rank, world, dist):
+    if args.workload == "case4":
+        return run_case4(args, rank, world, dist)
     if args.workload == "c3-precision":
         return run_precision(args, rank, world, dist)
     if args.workload == "c4":
@@ -650,6 +703,7 @@ def main():
     ap.add_argument("--c5-epochs", type=int, default=8)
     ap.add_argument("--c5-batch", type=int, default=16)
     ap.add_argument("--prec-steps", type=int, default=2000)
+    ap.add_argument("--case4-max-length", type=float, default=0.5)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -291,6 +291,24 @@ def scaled_config1(n: int, R: float, n_vert: int, seed: int = 11, n_steps: int =
     return Workload(f"c1s_{n}", P, T, n_steps, seed)
 
 
+def case4(level: int, max_length: float = 0.5) -> Workload:
+    """The immersed-boundary leakage study (Sec. 8 validation, Case IV): a
+    circular cell under the constant membrane tension of Eq. membraneforce,
+    no mass source, tau 1, no species.  Level k refines the lattice by 2^k:
+    domain 100*2^k, cell diameter 10*2^k lattice units (the DIA values of the
+    study's figure), T = 1e4*4^k steps and phi_m = 1e-3/2^k in LB units (the
+    study's table: dt ~ dx^2, F^LB ~ dx).  Vertices are max_length lattice
+    units apart (the study's MAXLENGTH); the lattice is periodic in place of
+    the study's outflow boundary."""
+    N = 100 * 2 ** level
+    D = 10.0 * 2 ** level
+    P = LatticeParams(nx=N, ny=N, bc_y=BC_PERIODIC, tau=1.0, rho0=1.0, n_species=0)
+    P.tension = 1e-3 / 2 ** level
+    n_vert = int(math.ceil(math.pi * D / max_length))
+    T = make_tissue([(N / 2.0, N / 2.0)], [D / 2.0], n_vert, 0.0, 0.0, [0])
+    return Workload(f"case4_level{level}_{N}x{N}_dia{int(D)}", P, T, 10000 * 4 ** level, 0)
+
+
 def random_fields(seed: int, shape, scale: float = 1.0) -> np.ndarray:
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.uniform(-scale, scale, size=shape)
