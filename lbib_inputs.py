@@ -50,6 +50,12 @@ class LatticeParams:
     src_rate: List[float] = dataclasses.field(default_factory=lambda: [0.0] * 4)
     forcing: int = 0          # 0 = Guo forcing, 1 = the paper's simple term
     fp16_scale: float = 2.0 ** -10
+    tension: float = 0.0      # constant membrane tension phi_m (Eq. membraneforce)
+    # reaction model: 0 linear (react, decay); 1 Schnakenberg on species 0
+    # (receptor R) and 1 (ligand L) with schnak = (gamma, a, b)
+    reaction: int = 0
+    schnak: List[float] = dataclasses.field(default_factory=lambda: [0.0, 0.0, 0.0])
+    noflux: int = 0           # bit s: species s confined to its domain
 
 
 @dataclasses.dataclass

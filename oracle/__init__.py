@@ -18,6 +18,11 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   run (coupled)      invariants above; the coupled trajectory itself is
                      parity unpinned beyond them (no printed trajectory)
   steady             closed-form uniform steady state s/k
+  Schnakenberg       homogeneous fixed point (a+b, b/(a+b)^2), linearised
+    reaction         map I + J of a uniform perturbation (Jacobian by hand)
+  no-flux domains    per-domain mass conservation of a confined species (a
+                     free one moves mass), relaxation to the domain mean,
+                     one label everywhere = no confinement (bit-exact)
   conv3x3 (+dgrad,   scipy correlate2d, identity tap, adjointness,
     wgrad)           finite differences
   nn (U-Net)         finite-difference gradient of the whole network,
@@ -60,7 +65,8 @@ class OrcParams(ctypes.Structure):
                 ("rho0", ctypes.c_double), ("D", ctypes.c_double * 4),
                 ("decay", ctypes.c_double * 4), ("react", (ctypes.c_double * 4) * 4),
                 ("src_rate", ctypes.c_double * 4), ("forcing", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("react_model", ctypes.c_int32), ("noflux", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("schnak", ctypes.c_double * 3)]
 
 
 def _P(p) -> OrcParams:
@@ -74,6 +80,11 @@ def _P(p) -> OrcParams:
         for b in range(4):
             o.react[s][b] = float(p.react[s][b])
     o.forcing = int(p.forcing)
+    o.react_model = int(getattr(p, "reaction", 0))
+    o.noflux = int(getattr(p, "noflux", 0))
+    sk = getattr(p, "schnak", (0.0, 0.0, 0.0))
+    for q in range(3):
+        o.schnak[q] = float(sk[q])
     return o
 
 
@@ -93,11 +104,11 @@ def lib():
             L.orc_rasterize.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
             L.orc_spread.argtypes = [i, i, i, i, vp, vp, vp, vp]
             L.orc_interp.argtypes = [i, i, i, i, vp, vp, vp, vp]
-            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 11
-            L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 6
+            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 12
+            L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 7
             L.orc_run.restype = i
             L.orc_run.argtypes = ([ctypes.POINTER(OrcParams), i, vp, vp, vp, vp, vp, d, vp, i]
-                                  + [vp] * 11)
+                                  + [vp] * 12)
             L.orc_steady.restype = ctypes.c_long
             L.orc_steady.argtypes = [ctypes.POINTER(OrcParams), vp, vp, d, ctypes.c_long, i,
                                      vp, ctypes.POINTER(d)]
@@ -185,8 +196,13 @@ def equilibrium_state(p):
     return f, g
 
 
-def lattice_step(p, f, g, fx=None, fy=None, src=None):
-    """One stream+collide update.  Returns (f_out, g_out, rho, ux, uy, phi)."""
+def _dom(dom):
+    return None if dom is None else np.ascontiguousarray(dom, np.int32)
+
+
+def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None):
+    """One stream+collide update.  Returns (f_out, g_out, rho, ux, uy, phi).
+    dom: static domain labels (ny, nx) for the species confined by p.noflux."""
     P = _P(p)
     f = _f64(f)
     g = _f64(g) if p.n_species else np.zeros(1)
@@ -200,11 +216,11 @@ def lattice_step(p, f, g, fx=None, fy=None, src=None):
                            _ptr(None if fx is None else _f64(fx)),
                            _ptr(None if fy is None else _f64(fy)),
                            _ptr(None if src is None else np.ascontiguousarray(src, np.uint8)),
-                           _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi))
+                           _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi), _ptr(_dom(dom)))
     return fo, go, rho, ux, uy, phi[: p.n_species]
 
 
-def species_step(p, g, src=None, ux=None, uy=None):
+def species_step(p, g, src=None, ux=None, uy=None, dom=None):
     P = _P(p)
     g = _f64(g)
     go = np.empty_like(g)
@@ -213,7 +229,7 @@ def species_step(p, g, src=None, ux=None, uy=None):
                            _ptr(None if ux is None else _f64(ux)),
                            _ptr(None if uy is None else _f64(uy)),
                            _ptr(None if src is None else np.ascontiguousarray(src, np.uint8)),
-                           _ptr(phi))
+                           _ptr(phi), _ptr(_dom(dom)))
     return go, phi
 
 
@@ -221,9 +237,10 @@ class RunResult:
     pass
 
 
-def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0):
+def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=None):
     """n coupled steps from (f, g, xy) (default: rest state and tissue.xy).
-    Returns a RunResult with the final state and the last step's fields."""
+    Returns a RunResult with the final state and the last step's fields.
+    dom: static domain labels (ny, nx) for the species confined by p.noflux."""
     P = _P(p)
     N = p.nx * p.ny
     if f is None or g is None:
@@ -249,7 +266,8 @@ def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0):
                        _ptr(_f64(tissue.k_spring)), _ptr(_f64(tissue.pressure)), float(tension),
                        _ptr(np.ascontiguousarray(tissue.src_flag, np.uint8)), int(n_steps),
                        _ptr(f), _ptr(g), _ptr(r.rho), _ptr(r.ux), _ptr(r.uy), _ptr(r.phi),
-                       _ptr(r.id), _ptr(r.src), _ptr(r.fx), _ptr(r.fy), _ptr(r.Fv))
+                       _ptr(r.id), _ptr(r.src), _ptr(r.fx), _ptr(r.fy), _ptr(r.Fv),
+                       _ptr(_dom(dom)))
     if rc != 0:
         raise MemoryError("oracle run failed to allocate")
     r.f = f

@@ -32,7 +32,10 @@ typedef struct {
     double tau, rho0;
     double D[4], decay[4], react[4][4], src_rate[4];
     int32_t forcing;           /* 0 Guo et al. 2002, 1 the paper's simple term (Eq. bgkequation) */
+    int32_t react_model;       /* 0 linear (react, decay); 1 Schnakenberg on species 0 and 1 */
+    int32_t noflux;            /* bit s: species s is confined to its domain (no-flux membranes) */
     int32_t pad;
+    double schnak[3];          /* gamma, a, b of the Schnakenberg reaction */
 } orc_params;
 
 /* D2Q9 velocities: v0 = 0; v1..v4 = (cos, sin)(pi(i-1)/2); v5..v8 the diagonals
@@ -261,6 +264,52 @@ static double pull(const double* post, const int* opp, int q, int i, int j, int 
     return post[(long)q * N + (long)sj * nx + si];
 }
 
+/* Species streaming with the membrane no-flux condition.  Reading c26: the
+ * paper's no-flux boundary for reaction-advection-diffusion (Sec. 6.1,
+ * approximating the missing populations by equilibria with interpolated
+ * momentum) is stated too briefly to reproduce; a species confined to its
+ * domain is instead reflected by half-way bounce-back on every lattice link
+ * whose two nodes carry different domain labels: the population that would
+ * arrive across the membrane is the opposite population of the same node,
+ * so nothing crosses the membrane and the species' mass in each domain is
+ * conserved.  dom: one label per node (any value; equal labels = one
+ * domain), NULL = no confinement. */
+static double pull_species(const double* post, const int* opp, int q, int i, int j, int nx,
+                           int ny, int bc_y, const int32_t* dom, int confined) {
+    if (!confined || !dom || q == 0) return pull(post, opp, q, i, j, nx, ny, bc_y);
+    long N = (long)nx * ny;
+    int si = wrap(i - CX[q], nx), sj = j - CY[q];
+    if (sj < 0 || sj >= ny) {
+        if (bc_y == 1) return post[(long)opp[q] * N + (long)j * nx + i];
+        sj = wrap(sj, ny);
+    }
+    if (dom[(long)sj * nx + si] != dom[(long)j * nx + i])
+        return post[(long)opp[q] * N + (long)j * nx + i];
+    return post[(long)q * N + (long)sj * nx + si];
+}
+
+/* The reaction rate of species s at a node (reading c10: evaluated on the
+ * pre-collision phi of the node, added after collision):
+ *   react_model 0:  R_s = sum_b react[s][b] phi_b - decay[s] phi_s
+ *   react_model 1:  the Schnakenberg system of the Turing-patterning example
+ *                   (Sec. 5), receptor R = species 0, ligand L = species 1:
+ *                   R_0 = gamma (a - R + R^2 L),  R_1 = gamma (b - R^2 L);
+ *                   further species linear as above
+ * plus src_rate[s] at nodes inside a source cell of species s. */
+static double reaction(const orc_params* P, int s, const double* phi, int S, uint8_t srcbits) {
+    double R;
+    if (P->react_model == 1 && S >= 2 && s < 2) {
+        double r2l = phi[0] * phi[0] * phi[1];
+        R = s == 0 ? P->schnak[0] * (P->schnak[1] - phi[0] + r2l)
+                   : P->schnak[0] * (P->schnak[2] - r2l);
+    } else {
+        R = -P->decay[s] * phi[s];
+        for (int b = 0; b < S; ++b) R += P->react[s][b] * phi[b];
+    }
+    if ((srcbits >> s) & 1) R += P->src_rate[s];
+    return R;
+}
+
 /* One lattice update: stream, then collide (Sec. 6.1).
  * Fluid, Eq. bgkequation with the equilibrium of Eq. standardequilibrium read
  * as the standard second-order polynomial
@@ -284,7 +333,7 @@ static double pull(const double* post, const int* opp, int q, int i, int j, int 
 void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost_out,
                       const double* gpost_in, double* gpost_out, const double* fx,
                       const double* fy, const uint8_t* src, double* rho_out, double* ux_out,
-                      double* uy_out, double* phi_out) {
+                      double* uy_out, double* phi_out, const int32_t* dom) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     double tau = P->tau;
@@ -331,14 +380,13 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
             for (int s = 0; s < S; ++s) {
                 phi[s] = 0.0;
                 for (int q = 0; q < 5; ++q) {
-                    g[s][q] = pull(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny, P->bc_y);
+                    g[s][q] = pull_species(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny,
+                                           P->bc_y, dom, (P->noflux >> s) & 1);
                     phi[s] += g[s][q];
                 }
             }
             for (int s = 0; s < S; ++s) {
-                double R = -P->decay[s] * phi[s];
-                for (int b = 0; b < S; ++b) R += P->react[s][b] * phi[b];
-                if (src && ((src[idx] >> s) & 1)) R += P->src_rate[s];
+                double R = reaction(P, s, phi, S, src ? src[idx] : 0);
                 double tauD = 3.0 * P->D[s] + 0.5;
                 for (int q = 0; q < 5; ++q) {
                     double vu = CX[q] * ux + CY[q] * uy;
@@ -356,7 +404,7 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
  * NULL): the D2Q5 part of orc_lattice_step, used by the steady solve. */
 void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost_out,
                       const double* ux_in, const double* uy_in, const uint8_t* src,
-                      double* phi_out) {
+                      double* phi_out, const int32_t* dom) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     static const int OPP5[5] = {0, 3, 4, 1, 2};
@@ -369,14 +417,13 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
             for (int s = 0; s < S; ++s) {
                 phi[s] = 0.0;
                 for (int q = 0; q < 5; ++q) {
-                    g[s][q] = pull(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny, P->bc_y);
+                    g[s][q] = pull_species(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny,
+                                           P->bc_y, dom, (P->noflux >> s) & 1);
                     phi[s] += g[s][q];
                 }
             }
             for (int s = 0; s < S; ++s) {
-                double R = -P->decay[s] * phi[s];
-                for (int b = 0; b < S; ++b) R += P->react[s][b] * phi[b];
-                if (src && ((src[idx] >> s) & 1)) R += P->src_rate[s];
+                double R = reaction(P, s, phi, S, src ? src[idx] : 0);
                 double tauD = 3.0 * P->D[s] + 0.5;
                 for (int q = 0; q < 5; ++q) {
                     double vu = CX[q] * ux + CY[q] * uy;
@@ -401,11 +448,12 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
  * State in/out: xy (V,2), f (9 planes, post-collision), g (5S planes).
  * Outputs of the last step (any may be NULL): rho, ux, uy, phi (S planes),
  * id, src, fx, fy (the spread force), Fv (V,2 vertex forces).
- * tension: constant membrane tension magnitude (0 = off). */
+ * tension: constant membrane tension magnitude (0 = off).  dom: static domain
+ * labels for the confined species (NULL = none; see pull_species). */
 int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const double* L0,
             const double* k, const double* p, double tension, const uint8_t* src_flag,
             int n_steps, double* f, double* g, double* rho, double* ux, double* uy, double* phi,
-            int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv) {
+            int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv, const int32_t* dom) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     int V = nc > 0 ? off[nc] : 0;
@@ -431,7 +479,7 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
         for (long t = 0; t < N; ++t) { Fx[t] = 0.0; Fy[t] = 0.0; }
         if (V > 0) orc_spread(nx, ny, P->bc_y, V, xy, F, Fx, Fy);
         orc_lattice_step(P, fa, fb, ga, gb, Fx, Fy, lsrc, last ? rho : NULL, Ux, Uy,
-                         last ? phi : NULL);
+                         last ? phi : NULL, dom);
         if (V > 0) {
             orc_interp(nx, ny, P->bc_y, V, xy, Ux, Uy, U);
             if (last && Fv) memcpy(Fv, F, sizeof(double) * 2 * V);
@@ -473,12 +521,12 @@ long orc_steady(const orc_params* P, const uint8_t* src, double* g, double tol, 
     long n = 0;
     while (n < max_steps) {
         int check = ((n + 1) % check_every) == 0;
-        orc_species_step(P, ga, gb, NULL, NULL, src, p0);
+        orc_species_step(P, ga, gb, NULL, NULL, src, p0, NULL);
         double* t = ga; ga = gb; gb = t;
         ++n;
         if (check) {
             /* phi^{n+1}: the zeroth moment of the populations just streamed */
-            orc_species_step(P, ga, gb, NULL, NULL, src, p1);
+            orc_species_step(P, ga, gb, NULL, NULL, src, p1, NULL);
             double dmax = 0.0, pmax = 0.0;
             for (long x = 0; x < S * N; ++x) {
                 double d = fabs(p1[x] - p0[x]);
@@ -490,7 +538,7 @@ long orc_steady(const orc_params* P, const uint8_t* src, double* g, double tol, 
         }
     }
     /* phi of the final state */
-    orc_species_step(P, ga, gb, NULL, NULL, src, phi);
+    orc_species_step(P, ga, gb, NULL, NULL, src, phi, NULL);
     if (ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
     free(g2); free(p0); free(p1);
     if (resid_out) *resid_out = r;
