@@ -56,6 +56,11 @@ extern "C" {
 #define LBIB_FP32 1   /* FP32 storage of f - w rho0 (shifted), FP32 arithmetic */
 #define LBIB_FP16 2   /* FP16 storage of (f - w rho0)/(w sigma), FP32 arithmetic */
 
+/* reaction model of the species */
+#define LBIB_REACT_LINEAR 0        /* R_s = sum_b react[s][b] phi_b - decay[s] phi_s */
+#define LBIB_REACT_SCHNAKENBERG 1  /* species 0, 1 = receptor R, ligand L (Sec. 4.2):
+                                      R_0 = gamma (a - R + R^2 L), R_1 = gamma (b - R^2 L) */
+
 /* body-force scheme */
 #define LBIB_GUO 0        /* Guo, Zheng & Shi 2002: u = (sum f v + F/2)/rho */
 #define LBIB_HE_PAPER 1   /* the paper's term of Eq. bgkequation, 3 w_i v_i.F */
@@ -95,7 +100,17 @@ extern "C" {
  *   tension      constant membrane tension phi_m of Eq. membraneforce added
  *                to every vertex (0 = off)
  *   body_force   uniform body force density (fx, fy) added at every node on
- *                top of the spread cell forces (e.g. a channel driving force) */
+ *                top of the spread cell forces (e.g. a channel driving force)
+ *   reaction     LBIB_REACT_LINEAR, or LBIB_REACT_SCHNAKENBERG (needs two
+ *                or more species; species 0 and 1 take the Schnakenberg
+ *                rates of the Turing-patterning example, Sec. 4.2, with
+ *                schnak = {gamma, a, b}; further species stay linear; the
+ *                src_rate sources add to every species)
+ *   noflux_mask  bit s: species s is confined to its domain: it does not
+ *                cross the boundaries between the domains set with
+ *                lbib_set_domains() (half-way bounce-back on every lattice
+ *                link between nodes of different domains, the membrane
+ *                no-flux condition of Sec. 6.1); 0 = no domain plane */
 typedef struct lbib_params {
     int32_t nx, ny, bc_y, n_species;
     double tau, rho0;
@@ -104,6 +119,8 @@ typedef struct lbib_params {
     double fp16_scale, fp16_scale_species;
     double tension;
     double body_force[2];
+    int32_t reaction, noflux_mask;
+    double schnak[3];
 } lbib_params;
 
 typedef struct lbib_ctx lbib_ctx;
@@ -135,6 +152,16 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
 int lbib_set_cells(lbib_ctx* ctx, int32_t n_cells, const int32_t* cell_off, const double* xy,
                    const double* rest_len, const double* k_spring, const double* pressure,
                    const uint8_t* src_flag);
+
+/* Set the static domains of the confined species (noflux_mask): labels is a
+ * host array of nx*ny int32, row-major in j, one label per node (any values;
+ * neighbouring nodes with different labels are separated by a membrane; the
+ * paper's static cellular domain is the cell index inside cells and one
+ * common label outside).  NULL: one domain everywhere (nothing confined).
+ * The domain plane lives in the workspace and is read by every lattice
+ * update; it is zero (one domain) until set.  LBIB_E_STATE when the context
+ * was created with noflux_mask 0.  Synchronises the context stream. */
+int lbib_set_domains(lbib_ctx* ctx, const int32_t* labels);
 
 /* Choose how many lattice nodes one thread of the lattice update handles.
  * 2 (the default) lets FP16 storage update two adjacent nodes per thread,

@@ -56,6 +56,27 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int node, int r0, i
     g[4] = (WALLS && hi) ? St::ld((B + 2 * P) + node, pol) : St::ld((B + 4 * P) + (rp + x), pol);
 }
 
+// The D2Q5 pull of a species confined to its domain (the membrane no-flux
+// condition, Sec. 6.1, as half-way bounce-back): a population whose source
+// node lies in another domain (label in dom) is the opposite population of
+// the node itself, so nothing crosses a domain boundary.
+template <typename T, typename C, bool WALLS>
+__device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int32_t* dom,
+                                               int node, int r0, int rm, int rp, int x, int xm,
+                                               int xp, bool lo, bool hi, uint64_t pol,
+                                               C g[5]) {
+    using St = Store<T, C>;
+    const int32_t d0 = dom[node];
+    const bool bl = dom[r0 + xm] != d0, br = dom[r0 + xp] != d0;
+    const bool bd = (WALLS && lo) || dom[rm + x] != d0;
+    const bool bu = (WALLS && hi) || dom[rp + x] != d0;
+    g[0] = St::ld(B + node, pol);
+    g[1] = bl ? St::ld((B + 3 * P) + node, pol) : St::ld((B + 1 * P) + (r0 + xm), pol);
+    g[3] = br ? St::ld((B + 1 * P) + node, pol) : St::ld((B + 3 * P) + (r0 + xp), pol);
+    g[2] = bd ? St::ld((B + 4 * P) + node, pol) : St::ld((B + 2 * P) + (rm + x), pol);
+    g[4] = bu ? St::ld((B + 2 * P) + node, pol) : St::ld((B + 4 * P) + (rp + x), pol);
+}
+
 // The update of one node (x, y).  Callers map the 32 lanes of a warp to 32
 // consecutive nodes of one row starting at a multiple of 32 (lane = x mod
 // 32): lane 0 clears the warp's group-mask bits.
@@ -108,9 +129,14 @@ __device__ __forceinline__ void pull5(const T* B, int64_t P, int node, int r0, i
     { \
         const T* Gi = static_cast<const T*>(a.gsrc); \
 _Pragma("unroll") \
-        for (int s = 0; s < S; ++s) \
-            pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, lo_wall, \
-                               hi_wall, pol, g[s]); \
+        for (int s = 0; s < S; ++s) { \
+            if (a.dom && ((a.noflux >> s) & 1)) \
+                pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
+                                            x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
+            else \
+                pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, \
+                                   lo_wall, hi_wall, pol, g[s]); \
+        } \
     } \
     /* the IB kernel launched just before wrote the force, label and mask */ \
     /* planes: wait for it, then let the next IB launch start */ \
@@ -347,8 +373,17 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             V R = L::sel((bitsA >> s) & 1u, (bitsB >> s) & 1u, k.srate[s]);
+            if (S >= 2 && s < 2 && k.react_model == LBIB_REACT_SCHNAKENBERG) {
+                // receptor R = species 0, ligand L = species 1 (Sec. 4.2):
+                // gamma (a - R + R^2 L) and gamma (b - R^2 L)
+                const V r2l = L::mul(L::mul(ph[0], ph[0]), ph[1]);
+                const V rate = s == 0 ? L::add(L::sub(L::c(k.sa), ph[0]), r2l)
+                                      : L::sub(L::c(k.sb), r2l);
+                R = L::fma(L::c(k.sgamma), rate, R);
+            } else {
 #pragma unroll
-            for (int b = 0; b < S; ++b) R = L::fma(L::c(k.K[s][b]), ph[b], R);
+                for (int b = 0; b < S; ++b) R = L::fma(L::c(k.K[s][b]), ph[b], R);
+            }
             const V ev = L::fma(L::c(k.omegaD[s]), ph[s], R);
             const C eA = SCALED ? k.isig_g : C(w5(0));
             const C eB = SCALED ? k.isig_g : C(w5(1));

@@ -63,6 +63,7 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.src = take(align_up(P, 8));  // one byte per node
     l.smask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
+    if (p.noflux_mask) l.dom = take(P * 4);
     const uint64_t V = (uint64_t)max_vertices, C = (uint64_t)max_cells;
     l.xy = take(V * 16);
     l.L0 = take(V * 8);
@@ -110,6 +111,18 @@ static int check_params(const lbib_params* p, std::string* why) {
     if (p->forcing != LBIB_GUO && p->forcing != LBIB_HE_PAPER) { *why = "unknown forcing"; return LBIB_E_PARAM; }
     if (p->precision < LBIB_FP64 || p->precision > LBIB_FP16) { *why = "unknown precision"; return LBIB_E_PARAM; }
     if (p->fp16_scale < 0 || p->fp16_scale_species < 0) { *why = "fp16 scales must be >= 0"; return LBIB_E_PARAM; }
+    if (p->reaction != LBIB_REACT_LINEAR && p->reaction != LBIB_REACT_SCHNAKENBERG) {
+        *why = "unknown reaction model"; return LBIB_E_PARAM;
+    }
+    if (p->reaction == LBIB_REACT_SCHNAKENBERG &&
+        (p->n_species < 2 || !std::isfinite(p->schnak[0]) || !std::isfinite(p->schnak[1]) ||
+         !std::isfinite(p->schnak[2]))) {
+        *why = "the Schnakenberg reaction needs two species and finite gamma, a, b";
+        return LBIB_E_PARAM;
+    }
+    if (p->noflux_mask < 0 || p->noflux_mask >= (1 << p->n_species)) {
+        *why = "noflux_mask names a species that does not exist"; return LBIB_E_PARAM;
+    }
     return LBIB_OK;
 }
 
@@ -130,6 +143,10 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
         for (int b = 0; b < kMaxSpecies; ++b)
             k->K[s][b] = (C)(p.react[s][b] - (s == b ? p.decay[s] : 0.0));
     }
+    k->react_model = p.reaction;
+    k->sgamma = (C)p.schnak[0];
+    k->sa = (C)p.schnak[1];
+    k->sb = (C)p.schnak[2];
     const double sf = p.fp16_scale > 0 ? p.fp16_scale : std::ldexp(1.0, -10);
     const double sg = p.fp16_scale_species > 0 ? p.fp16_scale_species : std::ldexp(1.0, -8);
     const bool scaled = p.precision == LBIB_FP16;
@@ -181,6 +198,10 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.out = out ? 1 : 0;
     a.ib = c->nC > 0 ? 1 : 0;
     a.l2_first = c->l2_first ? 1 : 0;
+    if (c->p.noflux_mask) {
+        a.dom = c->at<int32_t>(L.dom);
+        a.noflux = c->p.noflux_mask;
+    }
     a.fmask = c->at<uint32_t>(L.fmask);
     a.lmask = c->at<uint32_t>(L.lmask);
     a.src = c->at<uint8_t>(L.src);
@@ -358,6 +379,8 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.src, 0, align_up(L.plane, 8), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.smask, 0, mask_words(L.plane) * 4, c->stream);
+    if (e == cudaSuccess && params->noflux_mask)
+        e = cudaMemsetAsync(c->ws + L.dom, 0, L.plane * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && max_cells > 0)
@@ -443,6 +466,22 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
         c->maxv_cell = std::max(c->maxv_cell, cell_off[ci + 1] - cell_off[ci]);
     c->vforce_valid = false;
     drop_graphs(c);
+    return LBIB_OK;
+}
+
+int lbib_set_domains(lbib_ctx* c, const int32_t* labels) {
+    if (!c) return LBIB_E_PARAM;
+    if (!c->p.noflux_mask) return fail(c, LBIB_E_STATE, "the context has no confined species");
+    const Layout& L = c->L;
+    cudaError_t e;
+    if (labels)
+        e = cudaMemcpy2DAsync(c->ws + L.dom, (size_t)L.pitch * 4, labels, (size_t)c->p.nx * 4,
+                              (size_t)c->p.nx * 4, (size_t)c->p.ny, cudaMemcpyHostToDevice,
+                              c->stream);
+    else
+        e = cudaMemsetAsync(c->ws + L.dom, 0, L.plane * 4, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_domains");
     return LBIB_OK;
 }
 

@@ -53,6 +53,7 @@ struct Layout {
     uint64_t force = 0, u = 0, rho = 0, phi = 0, id = 0, id_out = 0, force_out = 0;
     uint64_t xy = 0, L0 = 0, k = 0, vforce = 0, off = 0, pres = 0, srcf = 0, area = 0;
     uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0, src = 0, smask = 0;
+    uint64_t dom = 0;          // domain labels of the confined species (noflux_mask != 0)
     uint64_t diag = 0;
     uint64_t total = 0;
 };
@@ -72,6 +73,8 @@ struct Coefs {
     C omc;                      // 1 - omega
     C omcD[kMaxSpecies];        // 1 - omega_D
     C isig, isig_g;             // 1/sigma, 1/sigma_g of scaled (FP16) storage, else 1
+    int react_model;            // LBIB_REACT_LINEAR or LBIB_REACT_SCHNAKENBERG
+    C sgamma, sa, sb;           // Schnakenberg gamma, a, b
 };
 
 struct LatticeArgs {
@@ -95,6 +98,8 @@ struct LatticeArgs {
     int out;            // write rho, phi, id_out, force_out
     int ib;             // read/clear force and labels
     int l2_first;       // population loads evict-first in L2 (else normal)
+    const int32_t* dom; // domain label per node (pitch layout), NULL = none
+    int noflux;         // bit s: species s bounces back between different domains
     // 1 bit per 4 consecutive nodes (node index >> 2): groups that received
     // spread force / labels / source bits this step.  fmask NULL = dense
     // (read every node).

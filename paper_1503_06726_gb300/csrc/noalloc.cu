@@ -66,6 +66,12 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     for (int s = 0; s < params->n_species; ++s)
         if (!(params->D[s] > 0.0))
             return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: D must be > 0");
+    if (params->noflux_mask)
+        return set_thread_error(LBIB_E_PARAM,
+                                "lbib_step_noalloc: confined species need a context's domain plane");
+    if (params->reaction != LBIB_REACT_LINEAR &&
+        !(params->reaction == LBIB_REACT_SCHNAKENBERG && params->n_species >= 2))
+        return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: invalid reaction model");
     if (!d_f || (params->n_species > 0 && !d_g) ||
         (n_cells > 0 && (!d_cell_off || !d_xy || !d_rest_len || !d_k_spring || !d_pressure ||
                          !d_src_flag)))

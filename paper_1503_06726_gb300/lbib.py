@@ -31,6 +31,7 @@ LBIB_E_STATE = -7
 
 LBIB_FP64, LBIB_FP32, LBIB_FP16 = 0, 1, 2
 LBIB_GUO, LBIB_HE_PAPER = 0, 1
+LBIB_REACT_LINEAR, LBIB_REACT_SCHNAKENBERG = 0, 1
 LBIB_RHO, LBIB_U, LBIB_PHI, LBIB_X = 1, 2, 4, 8
 LBIB_AREA, LBIB_ID, LBIB_FORCE, LBIB_VFORCE = 16, 32, 64, 128
 
@@ -39,6 +40,7 @@ PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
 # every symbol declared in include/lbib.h
 EXPORTS = (
     "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_lattice_variant",
+    "lbib_set_domains",
     "lbib_set_cell_params",
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
@@ -68,6 +70,8 @@ class lbib_params(ctypes.Structure):
         ("forcing", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("fp16_scale", ctypes.c_double), ("fp16_scale_species", ctypes.c_double),
         ("tension", ctypes.c_double), ("body_force", ctypes.c_double * 2),
+        ("reaction", ctypes.c_int32), ("noflux_mask", ctypes.c_int32),
+        ("schnak", ctypes.c_double * 3),
     ]
 
 
@@ -90,6 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_set_cells": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "lbib_set_cell_params": (ctypes.c_int, [vp, vp, vp]),
         "lbib_set_lattice_variant": (ctypes.c_int, [vp, i32]),
+        "lbib_set_domains": (ctypes.c_int, [vp, vp]),
         "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
         "lbib_step": (ctypes.c_int, [vp, i32]),
         "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
@@ -178,6 +183,11 @@ def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
     o.tension = float(getattr(p, "tension", 0.0) or 0.0)
     bf = getattr(p, "body_force", (0.0, 0.0)) or (0.0, 0.0)
     o.body_force[0], o.body_force[1] = float(bf[0]), float(bf[1])
+    o.reaction = int(getattr(p, "reaction", 0) or 0)
+    o.noflux_mask = int(getattr(p, "noflux", 0) or 0)
+    sk = getattr(p, "schnak", (0.0, 0.0, 0.0)) or (0.0, 0.0, 0.0)
+    for q in range(3):
+        o.schnak[q] = float(sk[q])
     return o
 
 
@@ -205,6 +215,12 @@ def lbib_set_cells(ctx, cell_off, xy, rest_len=None, k_spring=None, pressure=Non
     pr, pr_p = _p(pressure, np.float64)
     sf, sf_p = _p(src_flag, np.uint8)
     _check(load().lbib_set_cells(ctx, len(off) - 1, off_p, xy_p, L0_p, k_p, pr_p, sf_p), ctx)
+
+
+def lbib_set_domains(ctx, labels=None):
+    """labels: (ny, nx) int32 domain of every node, or None (one domain)."""
+    a, a_p = _p(labels, np.int32)
+    _check(load().lbib_set_domains(ctx, a_p), ctx)
 
 
 def lbib_set_lattice_variant(ctx, nodes_per_thread: int):
@@ -411,6 +427,9 @@ class Simulation:
 
     def set_cell_params(self, pressure=None, src_flag=None):
         lbib_set_cell_params(self.ctx, pressure, src_flag)
+
+    def set_domains(self, labels=None):
+        lbib_set_domains(self.ctx, labels)
 
     def set_lattice_variant(self, nodes_per_thread: int):
         lbib_set_lattice_variant(self.ctx, nodes_per_thread)

@@ -1,0 +1,160 @@
+"""GPU parity of the Schnakenberg reaction (Sec. 4.2) and of confined species
+(the membrane no-flux condition, Sec. 6.1, read as half-way bounce-back
+between domains; reading c26) against the FP64 oracle.
+
+  - static cellular domain, fluid at rest, receptor confined, ligand free,
+    Schnakenberg kinetics from a perturbed homogeneous state: FP64 storage
+    within 1e-10 (relative L-infinity on phi) and FP32 within 1e-5 after 300
+    steps; FP16 shifted storage (one node per thread: confined species read
+    their neighbours' domains) within 5e-3 after 30 steps.  FP16 stores the
+    species undeviated with 4.9e-4 relative precision, and near this
+    Turing-unstable state the kinetics amplify its rounding (measured 2.0e-3
+    after 30 steps, 7.4e-2 after 300 with the receptor confined, 1.4e-2
+    without; 7.8e-3 after 300 steps with confinement and no reaction), so
+    the FP16 check stops before the amplification dominates;
+  - the confined species keeps its mass in every domain on the GPU (FP64,
+    no reaction, 1e-12 relative);
+  - moving cells with static domains (the coupled step, walls, sources):
+    FP64 within 1e-10 after 60 steps;
+  - lbib_set_domains needs a context created with confined species.
+"""
+import numpy as np
+import pytest
+
+import lbib_inputs as li
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1503_06726_gb300 import build, lbib
+    build.build()
+    lbib.load()
+    return lbib
+
+
+def rel(a, b):
+    d = np.abs(np.asarray(a) - np.asarray(b)).max()
+    s = np.abs(np.asarray(b)).max()
+    return float(d / s) if s > 0 else float(d)
+
+
+def _domains(nx, ny):
+    """Static cellular domain: the labels of a hexagonal tissue (cell index
+    + 1 inside, 0 outside), from the oracle's rasterisation."""
+    w = li.config2(nx=nx, ny=ny, n_cells_side=4)
+    import oracle
+    oracle.build()
+    idp, _ = oracle.rasterize(nx, ny, 0, w.tissue.cell_off, w.tissue.xy, w.tissue.src_flag)
+    return idp.astype(np.int32)
+
+
+def _schnak_params(nx, ny, noflux=1, reaction=1):
+    p = li.LatticeParams(nx=nx, ny=ny, tau=1.0, rho0=1.0, n_species=2)
+    p.D[0], p.D[1] = 0.05, 0.4
+    p.reaction = reaction
+    p.schnak = [0.02, 0.1, 0.9]
+    p.noflux = noflux
+    return p
+
+
+def _empty_tissue():
+    return li.Tissue(np.zeros(1, np.int32), np.zeros((0, 2)), np.zeros(0), np.zeros(0),
+                     np.zeros(0), np.zeros(0, np.uint8))
+
+
+def _initial_phi(p, seed):
+    a, b = p.schnak[1], p.schnak[2]
+    rng = np.random.default_rng(seed)
+    R = (a + b) * (1.0 + 0.05 * rng.uniform(-1, 1, size=(p.ny, p.nx)))
+    L = b / (a + b) ** 2 * (1.0 + 0.05 * rng.uniform(-1, 1, size=(p.ny, p.nx)))
+    return np.stack([R, L])
+
+
+def _gpu_species_run(lb, p, prec, dom, phi0, n):
+    sim = lb.Simulation(p, prec, 0, 0)
+    sim.set_domains(dom)
+    for s in range(p.n_species):
+        sim.set_species(s, phi0[s])
+    sim.step(n)
+    out = sim.fields(lb.LBIB_PHI | lb.LBIB_U)
+    sim.close()
+    return out
+
+
+def _oracle_species_run(orc, p, dom, phi0, n):
+    W5 = np.array([1 / 3] + [1 / 6] * 4)
+    g = np.concatenate([np.stack([W5[q] * phi0[s] for q in range(5)]) for s in range(2)])
+    r = orc.run(p, _empty_tissue(), n, g=g, dom=dom)
+    return r
+
+
+@pytest.mark.parametrize("prec,n,tol", [("fp64", 300, 1e-10), ("fp32", 300, 1e-5),
+                                        ("fp16", 30, 5e-3)])
+def test_schnakenberg_static_domains_vs_oracle(lb, orc, prec, n, tol):
+    nx, ny = 96, 80
+    p = _schnak_params(nx, ny)
+    dom = _domains(nx, ny)
+    phi0 = _initial_phi(p, 11)
+    ref = _oracle_species_run(orc, p, dom, phi0, n)
+    got = _gpu_species_run(lb, p, lb.PRECISIONS[prec], dom, phi0, n)
+    e0, e1 = rel(got["phi"][0], ref.phi[0]), rel(got["phi"][1], ref.phi[1])
+    print(f"{prec}: R {e0:.2e}  L {e1:.2e}")
+    assert e0 < tol and e1 < tol
+    assert np.abs(got["ux"]).max() < 1e-12 and np.abs(got["uy"]).max() < 1e-12
+
+
+def test_confined_species_keeps_domain_mass(lb):
+    nx, ny = 96, 80
+    p = _schnak_params(nx, ny, noflux=1, reaction=0)
+    dom = _domains(nx, ny)
+    rng = np.random.default_rng(12)
+    phi0 = rng.uniform(0.2, 1.0, size=(2, ny, nx))
+    got = _gpu_species_run(lb, p, lb.LBIB_FP64, dom, phi0, 400)
+    labels = np.unique(dom)
+    s0 = np.array([phi0[0][dom == k].sum() for k in labels])
+    s1 = np.array([got["phi"][0][dom == k].sum() for k in labels])
+    assert np.abs(s1 - s0).max() < 1e-12 * s0.max()
+    # the free ligand does move mass between domains
+    f0 = np.array([phi0[1][dom == k].sum() for k in labels])
+    f1 = np.array([got["phi"][1][dom == k].sum() for k in labels])
+    assert np.abs(f1 - f0).max() > 1e-3 * f0.max()
+
+
+def test_moving_cells_with_static_domains_fp64(lb, orc):
+    w = li.config2(nx=96, ny=80, n_cells_side=3)
+    p = w.params
+    p.reaction = 1
+    p.schnak = [0.01, 0.1, 0.9]
+    p.noflux = 1
+    T = w.tissue
+    idp, _ = orc.rasterize(p.nx, p.ny, p.bc_y, T.cell_off, T.xy, T.src_flag)
+    dom = idp.astype(np.int32)
+    n = 60
+    ref = orc.run(p, T, n, dom=dom)
+    sim = lb.Simulation(p, lb.LBIB_FP64, T.n_vertices, T.n_cells)
+    sim.set_cells(T)
+    sim.set_domains(dom)
+    sim.step(n)
+    got = sim.fields(1 | 2 | 4 | 8)
+    sim.close()
+    assert max(rel(got["ux"], ref.ux), rel(got["uy"], ref.uy)) < 1e-10
+    assert rel(got["phi"], ref.phi) < 1e-10
+    assert np.abs(got["xy"] - ref.xy).max() < 1e-10
+
+
+def test_set_domains_needs_confined_species(lb):
+    p = _schnak_params(32, 24, noflux=0)
+    sim = lb.Simulation(p, lb.LBIB_FP32, 0, 0)
+    with pytest.raises(lb.LbibError):
+        sim.set_domains(np.zeros((24, 32), np.int32))
+    sim.close()
+    p = _schnak_params(32, 24, noflux=1)
+    sim = lb.Simulation(p, lb.LBIB_FP32, 0, 0)
+    sim.set_domains(np.zeros((24, 32), np.int32))
+    sim.set_domains(None)
+    sim.close()
