@@ -298,7 +298,7 @@ def scaled_config1(n: int, R: float, n_vert: int, seed: int = 11, n_steps: int =
 
 
 def case4(level: int, max_length: float = 0.5) -> Workload:
-    """The immersed-boundary leakage study (Sec. 8 validation, Case IV): a
+    """The immersed-boundary leakage study (validation Case IV, Sec. 6.3): a
     circular cell under the constant membrane tension of Eq. membraneforce,
     no mass source, tau 1, no species.  Level k refines the lattice by 2^k:
     domain 100*2^k, cell diameter 10*2^k lattice units (the DIA values of the
@@ -313,6 +313,58 @@ def case4(level: int, max_length: float = 0.5) -> Workload:
     n_vert = int(math.ceil(math.pi * D / max_length))
     T = make_tissue([(N / 2.0, N / 2.0)], [D / 2.0], n_vert, 0.0, 0.0, [0])
     return Workload(f"case4_level{level}_{N}x{N}_dia{int(D)}", P, T, 10000 * 4 ** level, 0)
+
+
+def voronoi_domains(nx: int, ny: int, spacing: float, seed: int) -> np.ndarray:
+    """A static cellular domain: the periodic Voronoi tiling of a jittered
+    grid of centres (spacing lattice units, +-spacing/4 jitter); label of a
+    node = index of its nearest centre (int32, shape (ny, nx))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gx, gy = max(1, int(round(nx / spacing))), max(1, int(round(ny / spacing)))
+    sx, sy = nx / gx, ny / gy
+    cx = (np.arange(gx)[None, :] + 0.5) * sx + rng.uniform(-sx / 4, sx / 4, size=(gy, gx))
+    cy = (np.arange(gy)[:, None] + 0.5) * sy + rng.uniform(-sy / 4, sy / 4, size=(gy, gx))
+    X, Y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))
+    ci = np.floor(X / sx).astype(np.int64)
+    cj = np.floor(Y / sy).astype(np.int64)
+    best = np.full((ny, nx), np.inf)
+    lab = np.zeros((ny, nx), np.int32)
+    for dj in (-1, 0, 1):       # the nearest centre lies in a neighbouring grid cell
+        for di in (-1, 0, 1):
+            i2, j2 = (ci + di) % gx, (cj + dj) % gy
+            dx = X - cx[j2, i2]
+            dy = Y - cy[j2, i2]
+            dx -= nx * np.round(dx / nx)
+            dy -= ny * np.round(dy / ny)
+            d2 = dx * dx + dy * dy
+            m = d2 < best
+            best[m] = d2[m]
+            lab[m] = (j2 * gx + i2)[m].astype(np.int32)
+    return lab
+
+
+def turing(seed: int = 6, n: int = 1024, n_steps: int = 2000) -> Workload:
+    """The Turing example on a static cellular domain (Sec. 4.2, Fig. 5C):
+    n^2 periodic lattice at rest (tau 1), receptor R (species 0, D = 0.05,
+    confined to its cell) and ligand L (species 1, D = 0.4, free) with the
+    Schnakenberg rates gamma = 0.02, a = 0.1, b = 0.9 in LB units, cells of a
+    periodic Voronoi tiling of spacing n/20 (400 cells at 1024^2), starting
+    from the homogeneous state with +-5 % seeded noise.  Attributes domains
+    (labels) and phi0 (initial fields) ride on the workload."""
+    P = LatticeParams(nx=n, ny=n, bc_y=BC_PERIODIC, tau=1.0, rho0=1.0, n_species=2)
+    P.D[0], P.D[1] = 0.05, 0.4
+    P.reaction = 1
+    P.schnak = [0.02, 0.1, 0.9]
+    P.noflux = 1
+    T = Tissue(np.zeros(1, np.int32), np.zeros((0, 2)), np.zeros(0), np.zeros(0),
+               np.zeros(0), np.zeros(0, np.uint8))
+    w = Workload(f"turing_{n}x{n}_static_voronoi", P, T, n_steps, seed)
+    w.domains = voronoi_domains(n, n, n / 20.0, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))
+    a, b = P.schnak[1], P.schnak[2]
+    w.phi0 = np.stack([(a + b) * (1 + 0.05 * rng.uniform(-1, 1, size=(n, n))),
+                       b / (a + b) ** 2 * (1 + 0.05 * rng.uniform(-1, 1, size=(n, n)))])
+    return w
 
 
 def random_fields(seed: int, shape, scale: float = 1.0) -> np.ndarray:
