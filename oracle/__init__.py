@@ -20,6 +20,9 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   steady             closed-form uniform steady state s/k
   Schnakenberg       homogeneous fixed point (a+b, b/(a+b)^2), linearised
     reaction         map I + J of a uniform perturbation (Jacobian by hand)
+  junctions          two facing polygons: partners and force k (g - l0) across
+                     a gap g by construction, nothing beyond l_max, the
+                     periodic image, equal and opposite forces of mutual pairs
   no-flux domains    per-domain mass conservation of a confined species (a
                      free one moves mass), relaxation to the domain mean,
                      one label everywhere = no confinement (bit-exact)
@@ -66,7 +69,10 @@ class OrcParams(ctypes.Structure):
                 ("decay", ctypes.c_double * 4), ("react", (ctypes.c_double * 4) * 4),
                 ("src_rate", ctypes.c_double * 4), ("forcing", ctypes.c_int32),
                 ("react_model", ctypes.c_int32), ("noflux", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("schnak", ctypes.c_double * 3)]
+                ("pad", ctypes.c_int32), ("schnak", ctypes.c_double * 3),
+                ("junction_k", ctypes.c_double), ("junction_l0", ctypes.c_double),
+                ("junction_lmax", ctypes.c_double), ("junction_period", ctypes.c_int32),
+                ("pad2", ctypes.c_int32)]
 
 
 def _P(p) -> OrcParams:
@@ -85,6 +91,10 @@ def _P(p) -> OrcParams:
     sk = getattr(p, "schnak", (0.0, 0.0, 0.0))
     for q in range(3):
         o.schnak[q] = float(sk[q])
+    o.junction_k = float(getattr(p, "junction_k", 0.0))
+    o.junction_l0 = float(getattr(p, "junction_l0", 0.0))
+    o.junction_lmax = float(getattr(p, "junction_lmax", 0.0))
+    o.junction_period = int(getattr(p, "junction_period", 0))
     return o
 
 
@@ -101,6 +111,8 @@ def lib():
             L.orc_polygon_forces.argtypes = [i, vp, vp, vp, vp, vp, vp]
             L.orc_tension_forces.argtypes = [i, vp, vp, d, vp]
             L.orc_cell_areas.argtypes = [i, vp, vp, vp]
+            L.orc_junction_partners.argtypes = [i, i, i, i, vp, vp, d, vp]
+            L.orc_junction_forces.argtypes = [i, i, i, i, vp, vp, d, d, d, vp]
             L.orc_rasterize.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
             L.orc_spread.argtypes = [i, i, i, i, vp, vp, vp, vp]
             L.orc_interp.argtypes = [i, i, i, i, vp, vp, vp, vp]
@@ -149,6 +161,24 @@ def polygon_forces(cell_off, xy, L0, k, p, tension: float = 0.0) -> np.ndarray:
                              _ptr(_f64(p)), _ptr(F))
     if tension:
         lib().orc_tension_forces(len(off) - 1, _ptr(off), _ptr(xy), float(tension), _ptr(F))
+    return F
+
+
+def junction_partners(nx, ny, bc_y, cell_off, xy, lmax) -> np.ndarray:
+    off = np.ascontiguousarray(cell_off, np.int32)
+    xy = _f64(xy)
+    partner = np.zeros(xy.shape[0], np.int32)
+    lib().orc_junction_partners(nx, ny, bc_y, len(off) - 1, _ptr(off), _ptr(xy), float(lmax),
+                                _ptr(partner))
+    return partner
+
+
+def junction_forces(nx, ny, bc_y, xy, partner, k, l0, lmax) -> np.ndarray:
+    xy = _f64(xy)
+    F = np.zeros_like(xy)
+    lib().orc_junction_forces(nx, ny, bc_y, xy.shape[0], _ptr(xy),
+                              _ptr(np.ascontiguousarray(partner, np.int32)), float(k), float(l0),
+                              float(lmax), _ptr(F))
     return F
 
 

@@ -36,6 +36,9 @@ typedef struct {
     int32_t noflux;            /* bit s: species s is confined to its domain (no-flux membranes) */
     int32_t pad;
     double schnak[3];          /* gamma, a, b of the Schnakenberg reaction */
+    double junction_k, junction_l0, junction_lmax;   /* Eq. celljunctionforce */
+    int32_t junction_period;   /* renew the junctions every this many steps (0 = none) */
+    int32_t pad2;
 } orc_params;
 
 /* D2Q9 velocities: v0 = 0; v1..v4 = (cos, sin)(pi(i-1)/2); v5..v8 the diagonals
@@ -127,6 +130,58 @@ void orc_tension_forces(int nc, const int32_t* off, const double* xy, double phi
             double la = sqrt(ax * ax + ay * ay), lb = sqrt(bx * bx + by * by);
             F[2 * l] += phim * (ax / la + bx / lb);
             F[2 * l + 1] += phim * (ay / la + by / lb);
+        }
+    }
+}
+
+/* Cell junctions, Eq. celljunctionforce (Sec. 3.2.4).  Reading c28: when
+ * the junctions are renewed, every membrane point i takes as partner the
+ * closest membrane point j of another cell with |x_j - x_i| < l_max
+ * (distance in FP64 with the periodic minimum image in x, and in y unless
+ * there are walls; ties to the lower index), or none; between renewals the
+ * partners are kept and the force is evaluated from the current positions:
+ *   F_i += k_j (x_j - x_i)/|x_j - x_i| (|x_j - x_i| - l_0)  if |x_j - x_i| < l_max.
+ * The force acts on i only, as the equation states. */
+static void min_image(double* dx, double* dy, int nx, int ny, int bc_y) {
+    *dx -= (double)nx * round(*dx / (double)nx);
+    if (bc_y == 0) *dy -= (double)ny * round(*dy / (double)ny);
+}
+
+void orc_junction_partners(int nx, int ny, int bc_y, int nc, const int32_t* off,
+                           const double* xy, double lmax, int32_t* partner) {
+    int V = nc > 0 ? off[nc] : 0;
+    int32_t* cell = (int32_t*)malloc(sizeof(int32_t) * (V > 0 ? V : 1));
+    for (int c = 0; c < nc; ++c)
+        for (int l = off[c]; l < off[c + 1]; ++l) cell[l] = c;
+    for (int i = 0; i < V; ++i) {
+        int best = -1;
+        double bd2 = lmax * lmax;
+        for (int j = 0; j < V; ++j) {
+            if (cell[j] == cell[i]) continue;
+            double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
+            min_image(&dx, &dy, nx, ny, bc_y);
+            double d2 = dx * dx + dy * dy;
+            if (d2 < bd2) {  /* j ascending: a tie keeps the lower index */
+                bd2 = d2;
+                best = j;
+            }
+        }
+        partner[i] = best;
+    }
+    free(cell);
+}
+
+void orc_junction_forces(int nx, int ny, int bc_y, int nv, const double* xy,
+                         const int32_t* partner, double k, double l0, double lmax, double* F) {
+    for (int i = 0; i < nv; ++i) {
+        int j = partner[i];
+        if (j < 0) continue;
+        double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
+        min_image(&dx, &dy, nx, ny, bc_y);
+        double L = sqrt(dx * dx + dy * dy);
+        if (L < lmax && L > 0.0) {
+            F[2 * i] += k * dx / L * (L - l0);
+            F[2 * i + 1] += k * dy / L * (L - l0);
         }
     }
 }
@@ -292,7 +347,7 @@ static double pull_species(const double* post, const int* opp, int q, int i, int
  * pre-collision phi of the node, added after collision):
  *   react_model 0:  R_s = sum_b react[s][b] phi_b - decay[s] phi_s
  *   react_model 1:  the Schnakenberg system of the Turing-patterning example
- *                   (Sec. 5), receptor R = species 0, ligand L = species 1:
+ *                   (Sec. 4.2), receptor R = species 0, ligand L = species 1:
  *                   R_0 = gamma (a - R + R^2 L),  R_1 = gamma (b - R^2 L);
  *                   further species linear as above
  * plus src_rate[s] at nodes inside a source cell of species s. */
@@ -467,7 +522,9 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
     double* U = (double*)malloc(sizeof(double) * 2 * (V > 0 ? V : 1));
     int32_t* lid = (int32_t*)malloc(sizeof(int32_t) * N);
     uint8_t* lsrc = (uint8_t*)malloc(N);
-    if (!f2 || !g2 || !Fx || !Fy || !Ux || !Uy || !F || !U || !lid || !lsrc) return -1;
+    int32_t* partner = (int32_t*)malloc(sizeof(int32_t) * (V > 0 ? V : 1));
+    if (!f2 || !g2 || !Fx || !Fy || !Ux || !Uy || !F || !U || !lid || !lsrc || !partner) return -1;
+    for (int l = 0; l < V; ++l) partner[l] = -1;
     double *fa = f, *fb = f2, *ga = g, *gb = g2;
     for (int n = 0; n < n_steps; ++n) {
         int last = (n == n_steps - 1);
@@ -475,6 +532,12 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
         if (V > 0) {
             orc_polygon_forces(nc, off, xy, L0, k, p, F);
             if (tension != 0.0) orc_tension_forces(nc, off, xy, tension, F);
+            if (P->junction_period > 0) {
+                if (n % P->junction_period == 0)
+                    orc_junction_partners(nx, ny, P->bc_y, nc, off, xy, P->junction_lmax, partner);
+                orc_junction_forces(nx, ny, P->bc_y, V, xy, partner, P->junction_k,
+                                    P->junction_l0, P->junction_lmax, F);
+            }
         }
         for (long t = 0; t < N; ++t) { Fx[t] = 0.0; Fy[t] = 0.0; }
         if (V > 0) orc_spread(nx, ny, P->bc_y, V, xy, F, Fx, Fy);
@@ -500,7 +563,7 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
     if (fa != f) memcpy(f, fa, sizeof(double) * 9 * N);
     if (S > 0 && ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
     free(f2); free(g2); free(Fx); free(Fy); free(Ux); free(Uy); free(F); free(U);
-    free(lid); free(lsrc);
+    free(lid); free(lsrc); free(partner);
     return 0;
 }
 
