@@ -110,7 +110,18 @@ extern "C" {
  *                cross the boundaries between the domains set with
  *                lbib_set_domains() (half-way bounce-back on every lattice
  *                link between nodes of different domains, the membrane
- *                no-flux condition of Sec. 6.1); 0 = no domain plane */
+ *                no-flux condition of Sec. 6.1); 0 = no domain plane
+ *   junction_k, junction_l0, junction_lmax, junction_period
+ *                cell junctions (Eq. celljunctionforce, Sec. 3.2.4): every
+ *                junction_period steps (counted from lbib_set_cells or
+ *                lbib_set_state; 0 = no junctions) each vertex takes as
+ *                partner the closest vertex of another cell closer than
+ *                junction_lmax (periodic minimum image, ties to the lower
+ *                index); every step it receives the force
+ *                junction_k (d/|d|)(|d| - junction_l0), d = X_partner - X,
+ *                while |d| < junction_lmax.  Steps with junctions move the
+ *                vertices and compute the forces in separate launches and
+ *                are not captured in graphs. */
 typedef struct lbib_params {
     int32_t nx, ny, bc_y, n_species;
     double tau, rho0;
@@ -121,6 +132,8 @@ typedef struct lbib_params {
     double body_force[2];
     int32_t reaction, noflux_mask;
     double schnak[3];
+    double junction_k, junction_l0, junction_lmax;
+    int32_t junction_period, junction_pad;
 } lbib_params;
 
 typedef struct lbib_ctx lbib_ctx;

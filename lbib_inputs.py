@@ -56,6 +56,12 @@ class LatticeParams:
     reaction: int = 0
     schnak: List[float] = dataclasses.field(default_factory=lambda: [0.0, 0.0, 0.0])
     noflux: int = 0           # bit s: species s confined to its domain
+    # cell junctions (Eq. celljunctionforce): spring constant, rest length,
+    # cutoff, renewal period in steps (0 = none)
+    junction_k: float = 0.0
+    junction_l0: float = 0.0
+    junction_lmax: float = 0.0
+    junction_period: int = 0
 
 
 @dataclasses.dataclass

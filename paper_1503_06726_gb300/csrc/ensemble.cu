@@ -401,6 +401,9 @@ int lbib_ensemble_create(int32_t n, const lbib_params* params, const int32_t* ma
     for (int t = 0; t < n; ++t) {
         if (params[t].precision != LBIB_FP32)
             return ens_fail(nullptr, LBIB_E_PARAM, "ensemble tissues use FP32 storage");
+        if (params[t].junction_period > 0)
+            return ens_fail(nullptr, LBIB_E_PARAM,
+                            "ensemble tissues have no cell junctions (they need separate launches)");
         if (params[t].n_species != params[0].n_species || params[t].forcing != params[0].forcing)
             return ens_fail(nullptr, LBIB_E_PARAM,
                             "ensemble tissues share the species count and forcing");

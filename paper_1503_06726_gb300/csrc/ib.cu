@@ -149,6 +149,11 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
                 Fx += ten * (ux_ / la + vx_ / lb);
                 Fy += ten * (uy_ / la + vy_ / lb);
             }
+            if (a.jpartner) {  // Eq. celljunctionforce (a launch without the move)
+                const double2 J = junction_force64(a, X, a.jpartner[v0 + t]);
+                Fx += (C)J.x;
+                Fy += (C)J.y;
+            }
             if (a.write_vforce) a.vforce[v0 + t] = make_double2((double)Fx, (double)Fy);
 
             int bxi, byi;

@@ -44,6 +44,35 @@ __device__ __forceinline__ void axis_weights(double X, int* base, C w[4]) {
     w[3] = C(0.25) * (C(1) - cs);
 }
 
+// Cell junction force on a vertex at X with partner vertex j (Eq.
+// celljunctionforce): k (d/|d|)(|d| - l0) for d = X_j - X (periodic minimum
+// image), zero without a partner or beyond l_max.  The partner's position is
+// read from the vertex array, so the calling launch must not be moving the
+// vertices.
+__device__ __forceinline__ double2 junction_d(const IBArgs& a, double2 X, int j) {
+    const double2 Xj = a.xy[j];
+    double dx = Xj.x - X.x, dy = Xj.y - X.y;
+    dx -= (double)a.nx * round(dx / (double)a.nx);
+    if (!a.bc_y) dy -= (double)a.ny * round(dy / (double)a.ny);
+    return make_double2(dx, dy);
+}
+__device__ __forceinline__ float2 junction_force32(const IBArgs& a, double2 X, int j) {
+    if (j < 0) return make_float2(0.f, 0.f);
+    const double2 d = junction_d(a, X, j);
+    const float dx = (float)d.x, dy = (float)d.y;
+    const float L = sqrtf(dx * dx + dy * dy);
+    if (!(L < (float)a.jlmax) || !(L > 0.f)) return make_float2(0.f, 0.f);
+    const float s = (float)a.jk * (L - (float)a.jl0) / L;
+    return make_float2(s * dx, s * dy);
+}
+__device__ __forceinline__ double2 junction_force64(const IBArgs& a, double2 X, int j) {
+    if (j < 0) return make_double2(0.0, 0.0);
+    const double2 d = junction_d(a, X, j);
+    const double L = sqrt(d.x * d.x + d.y * d.y);
+    if (!(L < a.jlmax) || !(L > 0.0)) return make_double2(0.0, 0.0);
+    return make_double2(a.jk * d.x / L * (L - a.jl0), a.jk * d.y / L * (L - a.jl0));
+}
+
 // raise a diagnostic flag (labelling-only callers may pass no flag words)
 __device__ __forceinline__ void raise_flag(uint32_t* diag, int k) {
     if (diag) atomicOr(diag + k, 1u);
@@ -620,6 +649,11 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                     const float lp = sqrtf(dp.x * dp.x + dp.y * dp.y);
                     Fx += ten * (dn.x / ln - dp.x / lp);
                     Fy += ten * (dn.y / ln - dp.y / lp);
+                }
+                if (a.jpartner) {  // Eq. celljunctionforce (a launch without the move)
+                    const float2 J = junction_force32(a, sx[t], a.jpartner[v0 + t]);
+                    Fx += J.x;
+                    Fy += J.y;
                 }
                 if (a.write_vforce) a.vforce[v0 + t] = make_double2((double)Fx, (double)Fy);
 

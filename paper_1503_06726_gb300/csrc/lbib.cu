@@ -64,6 +64,15 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.smask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
     if (p.noflux_mask) l.dom = take(P * 4);
+    if (p.junction_period > 0 && max_cells > 0) {
+        // bins at least l_max wide (with a margin against rounding at their edges)
+        const double bw = p.junction_lmax * 1.0001;
+        l.jnbx = std::max(1, (int)std::floor(p.nx / bw));
+        l.jnby = std::max(1, (int)std::floor(p.ny / bw));
+        l.jpartner = take((uint64_t)max_vertices * 4);
+        l.jcell = take((uint64_t)max_vertices * 4);
+        l.jbins = take((uint64_t)l.jnbx * l.jnby * (1 + kJunctionBinCap) * 4);
+    }
     const uint64_t V = (uint64_t)max_vertices, C = (uint64_t)max_cells;
     l.xy = take(V * 16);
     l.L0 = take(V * 8);
@@ -122,6 +131,14 @@ static int check_params(const lbib_params* p, std::string* why) {
     }
     if (p->noflux_mask < 0 || p->noflux_mask >= (1 << p->n_species)) {
         *why = "noflux_mask names a species that does not exist"; return LBIB_E_PARAM;
+    }
+    if (p->junction_period < 0 ||
+        (p->junction_period > 0 &&
+         (!(p->junction_lmax > 0.0) || !std::isfinite(p->junction_lmax) ||
+          !std::isfinite(p->junction_k) || !(p->junction_l0 >= 0.0) ||
+          p->junction_lmax * 3.0 > std::min(p->nx, p->ny)))) {
+        *why = "junctions need period >= 0, 0 < l_max <= min(nx, ny)/3, finite k, l0 >= 0";
+        return LBIB_E_PARAM;
     }
     return LBIB_OK;
 }
@@ -215,6 +232,13 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
     IBArgs a;
     std::memset(&a, 0, sizeof(a));
     const Layout& L = c->L;
+    if (c->p.junction_period > 0 && prep && !move && L.jpartner) {
+        // the partners' positions are read while no vertex moves
+        a.jpartner = c->at<int32_t>(L.jpartner);
+        a.jk = c->p.junction_k;
+        a.jl0 = c->p.junction_l0;
+        a.jlmax = c->p.junction_lmax;
+    }
     a.xy = c->at<double2>(L.xy);
     a.L0 = c->at<double>(L.L0);
     a.k = c->at<double>(L.k);
@@ -319,6 +343,64 @@ static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out) {
     }
     *out = c->chunk[par];
     return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Steps with cell junctions.  The prep of step n needs the positions X^n of
+// every cell (the partners of a cell's vertices belong to other cells), so
+// the move of step n - 1 and the prep of step n run as separate launches,
+// with the renewal of the partners between them when n is a multiple of
+// the period.  Launched one by one (no graph): the renewal is decided on the
+// host from the step count.
+static cudaError_t junction_renew_if_due(lbib_ctx* c) {
+    if (c->nstep % c->p.junction_period != 0) return cudaSuccess;
+    const Layout& L = c->L;
+    JunctionArgs j;
+    std::memset(&j, 0, sizeof(j));
+    j.xy = c->at<double2>(L.xy);
+    j.vcell = c->at<int32_t>(L.jcell);
+    j.partner = c->at<int32_t>(L.jpartner);
+    j.bins = c->at<int>(L.jbins);
+    j.diag = c->at<uint32_t>(L.diag);
+    j.nv = c->nV;
+    j.nx = c->p.nx;
+    j.ny = c->p.ny;
+    j.bc_y = c->p.bc_y;
+    j.nbx = L.jnbx;
+    j.nby = L.jnby;
+    j.wbx = (double)c->p.nx / L.jnbx;
+    j.wby = (double)c->p.ny / L.jnby;
+    j.lmax = c->p.junction_lmax;
+    return launch_junction_renew(j, c->stream);
+}
+
+static cudaError_t run_with_junctions(lbib_ctx* c, int n_steps) {
+    cudaError_t e = junction_renew_if_due(c);
+    if (e == cudaSuccess) e = enqueue_ib(c, false, true, n_steps == 1);
+    for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
+        const bool last = (i == n_steps - 1);
+        e = enqueue_lattice(c, c->cur, last);
+        if (e == cudaSuccess) e = enqueue_ib(c, true, false, false);  // move
+        c->cur = 1 - c->cur;
+        ++c->nstep;
+        if (e == cudaSuccess && !last) {
+            e = junction_renew_if_due(c);
+            if (e == cudaSuccess) e = enqueue_ib(c, false, true, i == n_steps - 2);
+        }
+    }
+    return e;
+}
+
+// the cell index of every vertex, for the junction search
+static cudaError_t upload_vertex_cells(lbib_ctx* c, int n_cells, const int32_t* cell_off) {
+    if (!c->L.jcell || n_cells <= 0) return cudaSuccess;
+    std::vector<int32_t> vc((size_t)cell_off[n_cells]);
+    for (int ci = 0; ci < n_cells; ++ci)
+        for (int l = cell_off[ci]; l < cell_off[ci + 1]; ++l) vc[(size_t)l] = ci;
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->L.jcell, vc.data(), vc.size() * 4,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // vc is a host temporary
+    return e;
 }
 
 extern "C" {
@@ -458,7 +540,9 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
                                 c->stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = upload_vertex_cells(c, n_cells, cell_off);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_cells");
+    c->nstep = 0;
     c->nV = V;
     c->nC = n_cells;
     c->maxv_cell = 0;
@@ -551,6 +635,13 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     if (n_steps == 0) return LBIB_OK;
     cudaError_t e = cudaSuccess;
     const bool ib = c->nC > 0;
+    if (ib && c->p.junction_period > 0) {
+        e = run_with_junctions(c, n_steps);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
+        c->fields_valid = true;
+        c->vforce_valid = true;
+        return LBIB_OK;
+    }
     // prep of the first step (labels, forces, spreading from X^n)
     if (ib) e = enqueue_ib(c, false, true, n_steps == 1);
     int left = n_steps;
@@ -584,6 +675,8 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
 int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
     if (!c || !ms_out) return LBIB_E_PARAM;
     if (n_steps <= 0) return fail(c, LBIB_E_PARAM, "n_steps must be > 0");
+    if (c->nC > 0 && c->p.junction_period > 0)
+        return fail(c, LBIB_E_STATE, "profiled steps do not cover cell junctions");
     const bool ib = c->nC > 0;
     // one event before and after every launch: 2 per launch
     const int n_launch = n_steps + (ib ? n_steps + 1 : 0);
@@ -796,7 +889,10 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
             h + 16 + 9 * P + (uint64_t)5 * c->p.n_species * P + (uint64_t)c->maxV * 32);
         c->maxv_cell = 0;
         for (int ci = 0; ci < c->nC; ++ci) c->maxv_cell = std::max(c->maxv_cell, off[ci + 1] - off[ci]);
+        cudaError_t ev = upload_vertex_cells(c, c->nC, off);
+        if (ev != cudaSuccess) return cuda_fail(c, ev, "lbib_set_state");
     }
+    c->nstep = 0;
     c->fields_valid = false;
     c->vforce_valid = false;
     drop_graphs(c);

@@ -23,6 +23,7 @@ struct lbib_ctx {
     lbib::Coefs<float> kf;
     dim3 block{128, 1, 1};
     bool lattice_pairs = true;  // FP16 storage: two nodes per thread where possible
+    int64_t nstep = 0;          // steps since lbib_set_cells / lbib_set_state (junction renewal)
     bool l2_first = false;      // population loads evict-first (lattice nearly fits in L2)
     // graph of a two-step chunk, keyed by the buffer parity it starts from
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};

@@ -41,6 +41,7 @@ enum Diag : int {
     kDiagWallStencil = 1, // an IB stencil node fell outside a walled domain (dropped)
     kDiagRasterSlow = 2,  // a cell used the brute-force labelling path
     kDiagGeometry = 3,    // a cell's bounding box became non-finite or wider than the lattice
+    kDiagJunctionBin = 4, // a junction search bin overflowed (its extra vertices were skipped)
     kDiagWords = 64
 };
 
@@ -54,6 +55,9 @@ struct Layout {
     uint64_t xy = 0, L0 = 0, k = 0, vforce = 0, off = 0, pres = 0, srcf = 0, area = 0;
     uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0, src = 0, smask = 0;
     uint64_t dom = 0;          // domain labels of the confined species (noflux_mask != 0)
+    // cell junctions (junction_period > 0): partner and cell of every vertex, bins
+    uint64_t jpartner = 0, jcell = 0, jbins = 0;
+    int jnbx = 0, jnby = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
 };
@@ -134,6 +138,23 @@ struct IBArgs {
     uint32_t* smask;    // optional: mark the groups that receive source bits
     int do_ids;         // write the packed labels into `id` (else only source bits)
     int src_words;
+    // cell junctions (Eq. celljunctionforce): the partner vertex of each
+    // vertex (-1 none), NULL = no junctions; spring constant, rest length, cutoff
+    const int32_t* jpartner;
+    double jk, jl0, jlmax;
+};
+
+// renewal of the cell junctions: vertices binned into an nbx x nby grid of
+// bins at least lmax wide, kJunctionBinCap slots each (slot 0: the count)
+constexpr int kJunctionBinCap = 32;
+struct JunctionArgs {
+    const double2* xy;
+    const int32_t* vcell;   // cell index of every vertex
+    int32_t* partner;
+    int* bins;
+    uint32_t* diag;
+    int nv, nx, ny, bc_y, nbx, nby;
+    double wbx, wby, lmax;
 };
 
 // shared memory of the FP32 per-cell IB work (one CTA per cell), as pointers
@@ -297,6 +318,8 @@ cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_
                       bool pdl = false);
 cudaError_t launch_areas(const double2* xy, const int32_t* off, int n_cells, double* area,
                          cudaStream_t s);
+// junction partners from the current vertex positions (bins cleared, filled, searched)
+cudaError_t launch_junction_renew(const JunctionArgs& j, cudaStream_t s);
 cudaError_t launch_init_populations(int precision, int n_species, int nx, int ny,
                                     int64_t pitch, int64_t plane, void* f, void* g,
                                     cudaStream_t s);

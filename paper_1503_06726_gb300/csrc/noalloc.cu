@@ -69,6 +69,9 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     if (params->noflux_mask)
         return set_thread_error(LBIB_E_PARAM,
                                 "lbib_step_noalloc: confined species need a context's domain plane");
+    if (params->junction_period > 0)
+        return set_thread_error(LBIB_E_PARAM,
+                                "lbib_step_noalloc: cell junctions need a context");
     if (params->reaction != LBIB_REACT_LINEAR &&
         !(params->reaction == LBIB_REACT_SCHNAKENBERG && params->n_species >= 2))
         return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: invalid reaction model");

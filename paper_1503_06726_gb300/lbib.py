@@ -72,6 +72,9 @@ class lbib_params(ctypes.Structure):
         ("tension", ctypes.c_double), ("body_force", ctypes.c_double * 2),
         ("reaction", ctypes.c_int32), ("noflux_mask", ctypes.c_int32),
         ("schnak", ctypes.c_double * 3),
+        ("junction_k", ctypes.c_double), ("junction_l0", ctypes.c_double),
+        ("junction_lmax", ctypes.c_double), ("junction_period", ctypes.c_int32),
+        ("junction_pad", ctypes.c_int32),
     ]
 
 
@@ -188,6 +191,10 @@ def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
     sk = getattr(p, "schnak", (0.0, 0.0, 0.0)) or (0.0, 0.0, 0.0)
     for q in range(3):
         o.schnak[q] = float(sk[q])
+    o.junction_k = float(getattr(p, "junction_k", 0.0) or 0.0)
+    o.junction_l0 = float(getattr(p, "junction_l0", 0.0) or 0.0)
+    o.junction_lmax = float(getattr(p, "junction_lmax", 0.0) or 0.0)
+    o.junction_period = int(getattr(p, "junction_period", 0) or 0)
     return o
 
 

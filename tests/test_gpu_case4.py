@@ -1,4 +1,4 @@
-"""Immersed-boundary leakage (the paper's validation Case IV, Sec. 8).
+"""Immersed-boundary leakage (the paper's validation Case IV, Sec. 6.3).
 
 A circular cell under a constant membrane tension (Eq. membraneforce) and no
 mass source shrinks because the discrete delta kernel is not divergence-free:

@@ -1,5 +1,5 @@
 """Oracle pins for the Schnakenberg reaction (the Turing-patterning example,
-Sec. 5) and the membrane no-flux condition of confined species (Sec. 6.1,
+Sec. 4.2) and the membrane no-flux condition of confined species (Sec. 6.1,
 read as half-way bounce-back across domain boundaries; reading c26).
 
 What fixes each result (none of it retypes the oracle's update):
