@@ -25,7 +25,8 @@ c3-precision (that tissue with all three storages, errors against FP64);
 c4 (64 independent tissues in one persistent launch); c5 (the learned warm
 start of the steady morphogen solve, warm vs cold); turing (the
 Schnakenberg system on a static cellular domain of 1024^2, receptor confined
-to its cell); case4 (the immersed-
+to its cell); c2-junctions (the default tissue with cell junctions renewed
+every 10 steps); case4 (the immersed-
 boundary leakage study: area loss under constant membrane tension at four
 refinements and its order of convergence).
 
@@ -76,6 +77,8 @@ def workload(name: str):
         return li.config4(), "fp32"
     if name == "turing":
         return li.turing(), "fp32"
+    if name == "c2-junctions":
+        return li.config2_junctions(), "fp32"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -235,11 +238,14 @@ def oracle_sample(w, target_s: float, max_steps: int, threads: int | None = None
         g = np.concatenate([np.stack([W5[q] * phi0[s] for q in range(5)])
                             for s in range(p.n_species)])
     xy = T.xy.copy()
+    # the oracle renews junction partners at the start of every call: call it
+    # once per renewal period so that it renews exactly as often as the GPU
+    chunk = p.junction_period if (p.junction_period > 0 and T.n_cells > 0) else 1
     steps, t0 = 0, time.perf_counter()
     while steps < max_steps:
-        r = oracle.run(p, T, 1, f=f, g=g, xy=xy, dom=dom)
+        r = oracle.run(p, T, chunk, f=f, g=g, xy=xy, dom=dom)
         f, g, xy = r.f, r.g, r.xy
-        steps += 1
+        steps += chunk
         if time.perf_counter() - t0 >= target_s:
             break
     dt = time.perf_counter() - t0
@@ -650,6 +656,12 @@ def run_gb300(args, rank, world, dist):
             "alg_bytes_per_node": bpn, "launch_ms": lat_avg,
             "peak_kind": f"{peak_kind} hbm_gbs (copy)",
             "ib_launch_ms": ib_ms / (n_prof + 1)}
+    jp = p.junction_period if T.n_cells > 0 else 0
+    if jp > 0:
+        # with junctions the IB time per step is a move, a prep and the
+        # partner renewal every jp steps
+        roof.pop("ib_launch_ms")
+        roof["ib_ms_per_step"] = ib_ms / n_prof
     if prec == "fp64":
         # GB300's FP64 rate, not HBM, bounds this kernel: report it against the
         # FP64 peak (nominal 1.25 TFLOP/s = 152 SMs x 2.07 GHz x 2 FP64 FMA per
@@ -661,6 +673,14 @@ def run_gb300(args, rank, world, dist):
                     peak_kind="nominal FP64 (no measured FP64 peak on this pool)",
                     hbm={"achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak})
+    launches = 2 * args.steps + 1
+    if jp > 0:
+        # lattice, move and prep per step (the first prep before the loop, none
+        # after the last step), four kernels per renewal (count, scan, fill,
+        # search), one renewal at every step count in [warmup, warmup + steps)
+        # that is a multiple of jp
+        renewals = len([n for n in range(warmup, warmup + args.steps) if n % jp == 0])
+        launches = 3 * args.steps + 4 * renewals
     rec = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -669,11 +689,12 @@ def run_gb300(args, rank, world, dist):
         "config": workload_config(w, prec, {
             "l2": f"inputs larger than L2: {ws / 2**20:.0f} MiB working set > 129 MiB L2, no flush",
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "graph": "two-step CUDA graph chunks"}),
+            "graph": ("direct launches (steps with junctions are not graphed)" if jp > 0
+                      else "two-step CUDA graph chunks")}),
         "roofline": roof,
         "e2e": e2e,
         "warm_start": warm,
-        "gpu_launches": 2 * args.steps + 1,
+        "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
     }

@@ -225,7 +225,8 @@ int lbib_get_fields(lbib_ctx* ctx, uint32_t which, double* rho, double* ux, doub
  * directly (no graph) with CUDA events recorded on the context stream around
  * every launch, and return the summed device time in milliseconds of the
  * lattice-update launches in ms_out[0] and of the immersed-boundary launches
- * in ms_out[1] (host array of 2).  Synchronises the stream. */
+ * in ms_out[1] (host array of 2; with cell junctions the partner renewals
+ * count as immersed-boundary time).  Synchronises the stream. */
 int lbib_step_profiled(lbib_ctx* ctx, int32_t n_steps, double* ms_out);
 
 /* Number of vertices and cells currently loaded. */

@@ -62,6 +62,14 @@ class LatticeParams:
     junction_l0: float = 0.0
     junction_lmax: float = 0.0
     junction_period: int = 0
+    # mass sources per cell (Sec. 3.2.3): 1 = on (rates and target areas are
+    # given per cell), with the area controller gain alpha
+    mass_sources: int = 0
+    mass_alpha: float = 0.0
+    # internal pressure nodes (Sec. 6.1): 1 = a static node mask is given,
+    # held at density pressure_rho
+    pressure_nodes: int = 0
+    pressure_rho: float = 1.0
 
 
 @dataclasses.dataclass
@@ -190,6 +198,18 @@ def config2(seed: int = 2, n_steps: int = 5000, nx: int = 1024, ny: int = 1024,
     src[rng.choice(C, size=n_src, replace=False)] = 1
     T = make_tissue(centres, radii, 100, 0.02, 1e-3, src)
     return Workload(f"c2_{nx}x{ny}_fp32_walls_{C}cells_2species", P, T, n_steps, seed)
+
+
+def config2_junctions(seed: int = 2, n_steps: int = 5000, period: int = 10) -> Workload:
+    """The 1024^2 walled tissue of ``config2`` with cell junctions
+    (Eq. celljunctionforce): neighbouring membranes lie about 11 lattice
+    units apart (pitch 51.2, radii 20 +- 10%), junctions with k_j = 0.02,
+    l_0 = 8 and l_max = 14, renewed every ``period`` steps."""
+    w = config2(seed=seed, n_steps=n_steps)
+    p = w.params
+    p.junction_k, p.junction_l0, p.junction_lmax, p.junction_period = 0.02, 8.0, 14.0, period
+    return Workload(w.name.replace("c2_", "c2j_") + f"_junctions_every{period}", p, w.tissue,
+                    n_steps, seed)
 
 
 def jittered_grid_tissue(rng, nx, ny, spacing, radius, n_vert, k, pressure,

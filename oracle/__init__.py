@@ -72,7 +72,8 @@ class OrcParams(ctypes.Structure):
                 ("pad", ctypes.c_int32), ("schnak", ctypes.c_double * 3),
                 ("junction_k", ctypes.c_double), ("junction_l0", ctypes.c_double),
                 ("junction_lmax", ctypes.c_double), ("junction_period", ctypes.c_int32),
-                ("pad2", ctypes.c_int32)]
+                ("pad2", ctypes.c_int32), ("mass_alpha", ctypes.c_double),
+                ("pressure_rho", ctypes.c_double)]
 
 
 def _P(p) -> OrcParams:
@@ -95,6 +96,8 @@ def _P(p) -> OrcParams:
     o.junction_l0 = float(getattr(p, "junction_l0", 0.0))
     o.junction_lmax = float(getattr(p, "junction_lmax", 0.0))
     o.junction_period = int(getattr(p, "junction_period", 0))
+    o.mass_alpha = float(getattr(p, "mass_alpha", 0.0))
+    o.pressure_rho = float(getattr(p, "pressure_rho", 0.0))
     return o
 
 
@@ -116,11 +119,11 @@ def lib():
             L.orc_rasterize.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
             L.orc_spread.argtypes = [i, i, i, i, vp, vp, vp, vp]
             L.orc_interp.argtypes = [i, i, i, i, vp, vp, vp, vp]
-            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 12
+            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 14
             L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 7
             L.orc_run.restype = i
             L.orc_run.argtypes = ([ctypes.POINTER(OrcParams), i, vp, vp, vp, vp, vp, d, vp, i]
-                                  + [vp] * 12)
+                                  + [vp] * 15)
             L.orc_steady.restype = ctypes.c_long
             L.orc_steady.argtypes = [ctypes.POINTER(OrcParams), vp, vp, d, ctypes.c_long, i,
                                      vp, ctypes.POINTER(d)]
@@ -230,9 +233,15 @@ def _dom(dom):
     return None if dom is None else np.ascontiguousarray(dom, np.int32)
 
 
-def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None):
+def _opt(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dt)
+
+
+def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None, msrc=None, pmask=None):
     """One stream+collide update.  Returns (f_out, g_out, rho, ux, uy, phi).
-    dom: static domain labels (ny, nx) for the species confined by p.noflux."""
+    dom: static domain labels (ny, nx) for the species confined by p.noflux;
+    msrc: mass source per node (ny, nx); pmask: internal pressure nodes
+    (ny, nx), prescribed density p.pressure_rho."""
     P = _P(p)
     f = _f64(f)
     g = _f64(g) if p.n_species else np.zeros(1)
@@ -246,7 +255,8 @@ def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None):
                            _ptr(None if fx is None else _f64(fx)),
                            _ptr(None if fy is None else _f64(fy)),
                            _ptr(None if src is None else np.ascontiguousarray(src, np.uint8)),
-                           _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi), _ptr(_dom(dom)))
+                           _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi), _ptr(_dom(dom)),
+                           _ptr(_opt(msrc, np.float64)), _ptr(_opt(pmask, np.uint8)))
     return fo, go, rho, ux, uy, phi[: p.n_species]
 
 
@@ -267,10 +277,14 @@ class RunResult:
     pass
 
 
-def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=None):
+def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=None,
+        mass_rate=None, target_area=None, pmask=None):
     """n coupled steps from (f, g, xy) (default: rest state and tissue.xy).
     Returns a RunResult with the final state and the last step's fields.
-    dom: static domain labels (ny, nx) for the species confined by p.noflux."""
+    dom: static domain labels (ny, nx) for the species confined by p.noflux;
+    mass_rate (per cell): mass source of the cell's nodes, plus
+    p.mass_alpha (target_area - area) with target_area (per cell); pmask:
+    internal pressure nodes (ny, nx) held at density p.pressure_rho."""
     P = _P(p)
     N = p.nx * p.ny
     if f is None or g is None:
@@ -297,7 +311,8 @@ def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=N
                        _ptr(np.ascontiguousarray(tissue.src_flag, np.uint8)), int(n_steps),
                        _ptr(f), _ptr(g), _ptr(r.rho), _ptr(r.ux), _ptr(r.uy), _ptr(r.phi),
                        _ptr(r.id), _ptr(r.src), _ptr(r.fx), _ptr(r.fy), _ptr(r.Fv),
-                       _ptr(_dom(dom)))
+                       _ptr(_dom(dom)), _ptr(_opt(mass_rate, np.float64)),
+                       _ptr(_opt(target_area, np.float64)), _ptr(_opt(pmask, np.uint8)))
     if rc != 0:
         raise MemoryError("oracle run failed to allocate")
     r.f = f

@@ -39,6 +39,8 @@ typedef struct {
     double junction_k, junction_l0, junction_lmax;   /* Eq. celljunctionforce */
     int32_t junction_period;   /* renew the junctions every this many steps (0 = none) */
     int32_t pad2;
+    double mass_alpha;         /* gain of the cell area controller (Sec. 3.2.3) */
+    double pressure_rho;       /* density prescribed at internal pressure nodes */
 } orc_params;
 
 /* D2Q9 velocities: v0 = 0; v1..v4 = (cos, sin)(pi(i-1)/2); v5..v8 the diagonals
@@ -383,12 +385,20 @@ static double reaction(const orc_params* P, int s, const double* phi, int S, uin
  *   pre-collision phi of the same node)
  *   R_s = sum_b react[s][b] phi_b - decay[s] phi_s + src_rate[s] [src bit s].
  * Walls bounce species back too (zero flux).
+ * Internal pressure nodes (Sec. 6.1, pressure boundary condition; reading
+ * c30): where pmask is set, every pulled population is multiplied by
+ * gamma = pressure_rho / rho before the moments are taken, so the node holds
+ * the prescribed density and keeps its velocity (gamma cancels in u).
+ * Mass sources (Sec. 3.2.3; reading c29): msrc[x] is added to the node's
+ * mass after the collision, spread over the directions by the weights,
+ * f*_q += w_q msrc[x], which adds no momentum.
  * fpost_*: 9 planes of N; gpost_*: S*5 planes; fx, fy may be NULL (no force);
- * rho, ux, uy, phi (S planes) may be NULL. */
+ * rho, ux, uy, phi (S planes) may be NULL; msrc, pmask may be NULL (none). */
 void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost_out,
                       const double* gpost_in, double* gpost_out, const double* fx,
                       const double* fy, const uint8_t* src, double* rho_out, double* ux_out,
-                      double* uy_out, double* phi_out, const int32_t* dom) {
+                      double* uy_out, double* phi_out, const int32_t* dom, const double* msrc,
+                      const uint8_t* pmask) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     double tau = P->tau;
@@ -400,6 +410,12 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
             double f[9];
             for (int q = 0; q < 9; ++q) f[q] = pull(fpost_in, OPP, q, i, j, nx, ny, P->bc_y);
             double rho = 0.0, jx = 0.0, jy = 0.0;
+            if (pmask && pmask[idx]) {
+                for (int q = 0; q < 9; ++q) rho += f[q];
+                double gam = P->pressure_rho / rho;
+                for (int q = 0; q < 9; ++q) f[q] *= gam;
+                rho = 0.0;
+            }
             for (int q = 0; q < 9; ++q) {
                 rho += f[q];
                 jx += f[q] * CX[q];
@@ -425,6 +441,7 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
                           9.0 * vu * (CX[q] * Fx + CY[q] * Fy));
                 else
                     Sq = 3.0 * W9(q) * (CX[q] * Fx + CY[q] * Fy);
+                if (msrc) Sq += W9(q) * msrc[idx];
                 fpost_out[(long)q * N + idx] = f[q] - (f[q] - feq) / tau + Sq;
             }
             if (rho_out) rho_out[idx] = rho;
@@ -504,11 +521,18 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
  * Outputs of the last step (any may be NULL): rho, ux, uy, phi (S planes),
  * id, src, fx, fy (the spread force), Fv (V,2 vertex forces).
  * tension: constant membrane tension magnitude (0 = off).  dom: static domain
- * labels for the confined species (NULL = none; see pull_species). */
+ * labels for the confined species (NULL = none; see pull_species).
+ * Mass sources (Sec. 3.2.3, reading c29): with mrate (per cell, NULL = none)
+ * every node labelled with cell c receives
+ *   S_c = mrate[c] + mass_alpha (marea[c] - A_c(X^n))
+ * (the proportional area controller; without marea S_c = mrate[c]), A_c the
+ * polygon area of Sec. 3.3 at the start of the step.  pmask: internal
+ * pressure nodes (NULL = none; see orc_lattice_step). */
 int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const double* L0,
             const double* k, const double* p, double tension, const uint8_t* src_flag,
             int n_steps, double* f, double* g, double* rho, double* ux, double* uy, double* phi,
-            int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv, const int32_t* dom) {
+            int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv, const int32_t* dom,
+            const double* mrate, const double* marea, const uint8_t* pmask) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     int V = nc > 0 ? off[nc] : 0;
@@ -523,7 +547,11 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
     int32_t* lid = (int32_t*)malloc(sizeof(int32_t) * N);
     uint8_t* lsrc = (uint8_t*)malloc(N);
     int32_t* partner = (int32_t*)malloc(sizeof(int32_t) * (V > 0 ? V : 1));
-    if (!f2 || !g2 || !Fx || !Fy || !Ux || !Uy || !F || !U || !lid || !lsrc || !partner) return -1;
+    double* Sn = mrate ? (double*)malloc(sizeof(double) * N) : NULL;
+    double* Sc = (double*)malloc(sizeof(double) * (nc > 0 ? nc : 1));
+    if (!f2 || !g2 || !Fx || !Fy || !Ux || !Uy || !F || !U || !lid || !lsrc || !partner || !Sc ||
+        (mrate && !Sn))
+        return -1;
     for (int l = 0; l < V; ++l) partner[l] = -1;
     double *fa = f, *fb = f2, *ga = g, *gb = g2;
     for (int n = 0; n < n_steps; ++n) {
@@ -541,8 +569,14 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
         }
         for (long t = 0; t < N; ++t) { Fx[t] = 0.0; Fy[t] = 0.0; }
         if (V > 0) orc_spread(nx, ny, P->bc_y, V, xy, F, Fx, Fy);
+        if (mrate) {
+            if (marea) orc_cell_areas(nc, off, xy, Sc);
+            for (int c = 0; c < nc; ++c)
+                Sc[c] = marea ? mrate[c] + P->mass_alpha * (marea[c] - Sc[c]) : mrate[c];
+            for (long t = 0; t < N; ++t) Sn[t] = lid[t] > 0 ? Sc[lid[t] - 1] : 0.0;
+        }
         orc_lattice_step(P, fa, fb, ga, gb, Fx, Fy, lsrc, last ? rho : NULL, Ux, Uy,
-                         last ? phi : NULL, dom);
+                         last ? phi : NULL, dom, Sn, pmask);
         if (V > 0) {
             orc_interp(nx, ny, P->bc_y, V, xy, Ux, Uy, U);
             if (last && Fv) memcpy(Fv, F, sizeof(double) * 2 * V);
@@ -563,7 +597,7 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
     if (fa != f) memcpy(f, fa, sizeof(double) * 9 * N);
     if (S > 0 && ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
     free(f2); free(g2); free(Fx); free(Fy); free(Ux); free(Uy); free(F); free(U);
-    free(lid); free(lsrc); free(partner);
+    free(lid); free(lsrc); free(partner); free(Sn); free(Sc);
     return 0;
 }
 

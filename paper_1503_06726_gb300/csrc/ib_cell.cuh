@@ -51,9 +51,9 @@ __device__ __forceinline__ void axis_weights(double X, int* base, C w[4]) {
 // vertices.
 __device__ __forceinline__ double2 junction_d(const IBArgs& a, double2 X, int j) {
     const double2 Xj = a.xy[j];
-    double dx = Xj.x - X.x, dy = Xj.y - X.y;
-    dx -= (double)a.nx * round(dx / (double)a.nx);
-    if (!a.bc_y) dy -= (double)a.ny * round(dy / (double)a.ny);
+    const double dx = min_image(__dsub_rn(Xj.x, X.x), a.nx);
+    double dy = __dsub_rn(Xj.y, X.y);
+    if (!a.bc_y) dy = min_image(dy, a.ny);
     return make_double2(dx, dy);
 }
 __device__ __forceinline__ float2 junction_force32(const IBArgs& a, double2 X, int j) {

@@ -2,44 +2,106 @@
 // Sec. 3.2.4): every membrane point takes as partner the closest membrane
 // point of another cell within l_max, or none.
 //
-// The vertices are put into a uniform grid of bins at least l_max wide (a
-// fixed number of slots per bin; a bin that overflows raises a diagnostic
-// flag and keeps its first slots), then every vertex scans the 3x3 bins
-// around its own.  Distances are FP64 with the periodic minimum image in x
-// (and in y without walls), evaluated with the same round-to-nearest
-// operations in the same order as the definition (difference, image shift,
-// squared length), so the chosen partner is that of the definition; ties go
-// to the lower vertex index.  The forces themselves are added by the IB
-// kernel's prep from the current positions.
+// The vertices are sorted into a uniform grid of bins at least l_max wide
+// (CSR: count, one-CTA scan, fill; no per-bin capacity), then every vertex
+// scans the 3x3 bins around its own.  Each candidate first passes an FP32
+// test on wrapped positions whose bound exceeds l_max by more than the FP32
+// rounding can move a distance, so it only drops vertices that are certainly
+// out of range; the survivors take the definition's FP64 test (difference,
+// periodic minimum image, squared length, round-to-nearest in that order), so
+// the chosen partner is that of the definition; ties go to the lower vertex
+// index.  The forces themselves are added by the IB kernel's prep from the
+// current positions.
 #include <cmath>
 
 #include "lbib_internal.cuh"
 
 namespace lbib {
 
-__device__ __forceinline__ double image_shift(double d, int n) {
-    return __dsub_rn(d, __dmul_rn((double)n, round(__ddiv_rn(d, (double)n))));
-}
-
-__device__ __forceinline__ int bin_of(double X, int n, int nb, double w, bool periodic) {
+// Bin of coordinate X on an axis of n nodes cut into nb bins of width w (the
+// coordinate wrapped into [0, n) on a periodic axis, clamped to the end bins
+// on a walled one).  Every vertex's bin is computed once and stored, so the
+// multiplications by reciprocals only have to keep the bins at least l_max
+// wide, which the 1e-4 margin of the width covers.
+__device__ __forceinline__ int bin_axis(double X, int n, double inv_n, int nb, double inv_w,
+                                        bool periodic, double* wrapped) {
     double xw = X;
-    if (periodic) xw = __dsub_rn(X, __dmul_rn((double)n, floor(__ddiv_rn(X, (double)n))));
-    int b = (int)floor(xw / w);
+    if (periodic) xw = X - (double)n * floor(X * inv_n);
+    *wrapped = xw;
+    const int b = (int)floor(xw * inv_w);
     return b < 0 ? 0 : (b >= nb ? nb - 1 : b);
 }
 
-__global__ void junction_bin_kernel(JunctionArgs j) {
+__device__ __forceinline__ int vertex_bin(const JunctionArgs& j, double2 X, float2* wrapped) {
+    double xw, yw;
+    const int bx = bin_axis(X.x, j.nx, j.inv_nx, j.nbx, j.inv_wbx, true, &xw);
+    const int by = bin_axis(X.y, j.ny, j.inv_ny, j.nby, j.inv_wby, !j.bc_y, &yw);
+    *wrapped = make_float2((float)xw, (float)yw);
+    return by * j.nbx + bx;
+}
+
+__global__ void junction_count_kernel(JunctionArgs j) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= j.nv) return;
-    const double2 X = j.xy[v];
-    const int bx = bin_of(X.x, j.nx, j.nbx, j.wbx, true);
-    const int by = bin_of(X.y, j.ny, j.nby, j.wby, !j.bc_y);
-    int* bin = j.bins + (int64_t)(by * j.nbx + bx) * (1 + kJunctionBinCap);
-    const int slot = atomicAdd(bin, 1);
-    if (slot < kJunctionBinCap)
-        bin[1 + slot] = v;
-    else
-        atomicOr(j.diag + kDiagJunctionBin, 1u);
+    float2 w;
+    const int b = vertex_bin(j, j.xy[v], &w);
+    j.vbin[v] = b;
+    atomicAdd(j.cnt + b, 1);
+}
+
+// exclusive scan of the bin counts into start[0..nbins] (one CTA of 1024
+// threads, a contiguous run of bins per thread); the counts become the fill
+// cursors
+__global__ void __launch_bounds__(1024) junction_scan_kernel(JunctionArgs j) {
+    __shared__ int wsum[32];
+    const int nb = j.nbx * j.nby;
+    const int per = (nb + 1023) / 1024;
+    const int b0 = min(nb, (int)threadIdx.x * per), b1 = min(nb, b0 + per);
+    int s = 0;
+    for (int b = b0; b < b1; ++b) s += j.cnt[b];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    int excl = x - s + (w > 0 ? wsum[w - 1] : 0);
+    for (int b = b0; b < b1; ++b) {
+        const int c = j.cnt[b];
+        j.start[b] = excl;
+        j.cnt[b] = excl;
+        excl += c;
+    }
+    if (threadIdx.x == 1023) j.start[nb] = excl;  // the last thread ends at the total
+}
+
+__global__ void junction_fill_kernel(JunctionArgs j) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= j.nv) return;
+    float2 w;
+    vertex_bin(j, j.xy[v], &w);
+    const int slot = atomicAdd(j.cnt + j.vbin[v], 1);
+    JunctionEntry e;
+    e.x = w.x;
+    e.y = w.y;
+    e.cell = j.vcell[v];
+    e.v = v;
+    j.ent[slot] = e;
+}
+
+__device__ __forceinline__ float fold(float d, float n, float half) {
+    return d > half ? d - n : (d < -half ? d + n : d);
 }
 
 __global__ void junction_search_kernel(JunctionArgs j) {
@@ -47,8 +109,12 @@ __global__ void junction_search_kernel(JunctionArgs j) {
     if (i >= j.nv) return;
     const double2 Xi = j.xy[i];
     const int ci = j.vcell[i];
-    const int bx = bin_of(Xi.x, j.nx, j.nbx, j.wbx, true);
-    const int by = bin_of(Xi.y, j.ny, j.nby, j.wby, !j.bc_y);
+    float2 wi;
+    vertex_bin(j, Xi, &wi);
+    const int b = j.vbin[i];
+    const int bx = b % j.nbx, by = b / j.nbx;
+    const float nxf = (float)j.nx, nyf = (float)j.ny;
+    const float hx = 0.5f * nxf, hy = 0.5f * nyf;
     double best = __dmul_rn(j.lmax, j.lmax);
     int bestj = -1;
     for (int dyb = -1; dyb <= 1; ++dyb) {
@@ -59,20 +125,23 @@ __global__ void junction_search_kernel(JunctionArgs j) {
             b2y = (b2y + j.nby) % j.nby;
         }
         for (int dxb = -1; dxb <= 1; ++dxb) {
-            const int b2x = (bx + dxb + j.nbx) % j.nbx;
-            const int* bin = j.bins + (int64_t)(b2y * j.nbx + b2x) * (1 + kJunctionBinCap);
-            const int cnt = min(bin[0], kJunctionBinCap);
-            for (int k = 0; k < cnt; ++k) {
-                const int v = bin[1 + k];
-                if (j.vcell[v] == ci) continue;
-                const double2 Xv = j.xy[v];
-                double dx = image_shift(__dsub_rn(Xv.x, Xi.x), j.nx);
+            const int b2 = b2y * j.nbx + (bx + dxb + j.nbx) % j.nbx;
+            const int s1 = j.start[b2 + 1];
+            for (int s = j.start[b2]; s < s1; ++s) {
+                const JunctionEntry e = j.ent[s];
+                if (e.cell == ci) continue;
+                const float fx = fold(e.x - wi.x, nxf, hx);
+                const float fy = j.bc_y ? e.y - wi.y : fold(e.y - wi.y, nyf, hy);
+                if (fx * fx + fy * fy > j.fthr) continue;
+                // the definition's test in FP64
+                const double2 Xv = j.xy[e.v];
+                const double dx = min_image(__dsub_rn(Xv.x, Xi.x), j.nx);
                 double dy = __dsub_rn(Xv.y, Xi.y);
-                if (!j.bc_y) dy = image_shift(dy, j.ny);
+                if (!j.bc_y) dy = min_image(dy, j.ny);
                 const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                if (d2 < best || (d2 == best && bestj >= 0 && v < bestj)) {
+                if (d2 < best || (d2 == best && bestj >= 0 && e.v < bestj)) {
                     best = d2;
-                    bestj = v;
+                    bestj = e.v;
                 }
             }
         }
@@ -82,14 +151,17 @@ __global__ void junction_search_kernel(JunctionArgs j) {
 
 cudaError_t launch_junction_renew(const JunctionArgs& j, cudaStream_t s) {
     if (j.nv <= 0) return cudaSuccess;
-    // bin counts to zero: the first int of every bin
-    cudaError_t e = cudaMemset2DAsync(j.bins, (size_t)(1 + kJunctionBinCap) * 4, 0, 4,
-                                      (size_t)j.nbx * j.nby, s);
+    cudaError_t e = cudaMemsetAsync(j.cnt, 0, (size_t)j.nbx * j.nby * 4, s);
     if (e != cudaSuccess) return e;
     const int threads = 256, blocks = (j.nv + threads - 1) / threads;
-    e = launch_kernel(junction_bin_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
-    if (e != cudaSuccess) return e;
-    return launch_kernel(junction_search_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
+    e = launch_kernel(junction_count_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
+    if (e == cudaSuccess)
+        e = launch_kernel(junction_scan_kernel, dim3(1), dim3(1024), 0, s, false, j);
+    if (e == cudaSuccess)
+        e = launch_kernel(junction_fill_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
+    if (e == cudaSuccess)
+        e = launch_kernel(junction_search_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
+    return e;
 }
 
 }  // namespace lbib

@@ -65,13 +65,25 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.force_out = take(2 * P * l.cs);
     if (p.noflux_mask) l.dom = take(P * 4);
     if (p.junction_period > 0 && max_cells > 0) {
-        // bins at least l_max wide (with a margin against rounding at their edges)
+        // bins at least l_max wide (with a margin against rounding at their
+        // edges); wider where they would outnumber the vertices by far
         const double bw = p.junction_lmax * 1.0001;
         l.jnbx = std::max(1, (int)std::floor(p.nx / bw));
         l.jnby = std::max(1, (int)std::floor(p.ny / bw));
+        const int64_t cap = std::min<int64_t>(1 << 22, std::max<int64_t>(4096, 4 * (int64_t)max_vertices));
+        while ((int64_t)l.jnbx * l.jnby > cap) {
+            if (l.jnbx >= l.jnby)
+                l.jnbx = (l.jnbx + 1) / 2;
+            else
+                l.jnby = (l.jnby + 1) / 2;
+        }
+        const uint64_t nb = (uint64_t)l.jnbx * l.jnby;
         l.jpartner = take((uint64_t)max_vertices * 4);
         l.jcell = take((uint64_t)max_vertices * 4);
-        l.jbins = take((uint64_t)l.jnbx * l.jnby * (1 + kJunctionBinCap) * 4);
+        l.jcnt = take(nb * 4);
+        l.jstart = take((nb + 1) * 4);
+        l.jvbin = take((uint64_t)max_vertices * 4);
+        l.jent = take((uint64_t)max_vertices * sizeof(JunctionEntry));
     }
     const uint64_t V = (uint64_t)max_vertices, C = (uint64_t)max_cells;
     l.xy = take(V * 16);
@@ -352,40 +364,61 @@ static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out) {
 // with the renewal of the partners between them when n is a multiple of
 // the period.  Launched one by one (no graph): the renewal is decided on the
 // host from the step count.
-static cudaError_t junction_renew_if_due(lbib_ctx* c) {
-    if (c->nstep % c->p.junction_period != 0) return cudaSuccess;
+static bool junction_due(const lbib_ctx* c) { return c->nstep % c->p.junction_period == 0; }
+
+static cudaError_t junction_renew(lbib_ctx* c) {
     const Layout& L = c->L;
     JunctionArgs j;
     std::memset(&j, 0, sizeof(j));
     j.xy = c->at<double2>(L.xy);
     j.vcell = c->at<int32_t>(L.jcell);
     j.partner = c->at<int32_t>(L.jpartner);
-    j.bins = c->at<int>(L.jbins);
-    j.diag = c->at<uint32_t>(L.diag);
+    j.cnt = c->at<int>(L.jcnt);
+    j.start = c->at<int>(L.jstart);
+    j.vbin = c->at<int>(L.jvbin);
+    j.ent = c->at<JunctionEntry>(L.jent);
     j.nv = c->nV;
     j.nx = c->p.nx;
     j.ny = c->p.ny;
     j.bc_y = c->p.bc_y;
     j.nbx = L.jnbx;
     j.nby = L.jnby;
-    j.wbx = (double)c->p.nx / L.jnbx;
-    j.wby = (double)c->p.ny / L.jnby;
+    j.inv_nx = 1.0 / c->p.nx;
+    j.inv_ny = 1.0 / c->p.ny;
+    j.inv_wbx = L.jnbx / (double)c->p.nx;
+    j.inv_wby = L.jnby / (double)c->p.ny;
     j.lmax = c->p.junction_lmax;
+    // FP32 prefilter: the wrapped FP32 coordinates are within n 2^-24 of the
+    // exact ones, a folded FP32 difference within 4 n 2^-24 of the exact
+    // minimum image, so a candidate at an exact distance below l_max has an
+    // FP32 distance below l_max + 6 n 2^-24 (with the norm's rounding inside
+    // the 1e-5 relative margin)
+    const double eps = 6.0 * std::max(c->p.nx, c->p.ny) * std::ldexp(1.0, -24);
+    const double r = (j.lmax + eps) * (1.0 + 1e-5);
+    j.fthr = (float)(r * r);
     return launch_junction_renew(j, c->stream);
 }
 
-static cudaError_t run_with_junctions(lbib_ctx* c, int n_steps) {
-    cudaError_t e = junction_renew_if_due(c);
-    if (e == cudaSuccess) e = enqueue_ib(c, false, true, n_steps == 1);
+// Steps with cell junctions.  The junction force of a vertex needs the moved
+// position of a vertex of another cell, so the move and the next step's prep
+// are two launches with the partner renewal between them when it is due.
+// `wrap(kind, fn)` runs one enqueue (kind 0 lattice, 1 everything else) and
+// returns its status; the profiled step brackets it with events.
+template <class Wrap>
+static cudaError_t run_with_junctions(lbib_ctx* c, int n_steps, Wrap&& wrap) {
+    cudaError_t e = cudaSuccess;
+    if (junction_due(c)) e = wrap(1, [&] { return junction_renew(c); });
+    if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
     for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
         const bool last = (i == n_steps - 1);
-        e = enqueue_lattice(c, c->cur, last);
-        if (e == cudaSuccess) e = enqueue_ib(c, true, false, false);  // move
+        e = wrap(0, [&] { return enqueue_lattice(c, c->cur, last); });
+        if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, true, false, false); });
         c->cur = 1 - c->cur;
         ++c->nstep;
         if (e == cudaSuccess && !last) {
-            e = junction_renew_if_due(c);
-            if (e == cudaSuccess) e = enqueue_ib(c, false, true, i == n_steps - 2);
+            if (junction_due(c)) e = wrap(1, [&] { return junction_renew(c); });
+            if (e == cudaSuccess)
+                e = wrap(1, [&] { return enqueue_ib(c, false, true, i == n_steps - 2); });
         }
     }
     return e;
@@ -636,7 +669,7 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     cudaError_t e = cudaSuccess;
     const bool ib = c->nC > 0;
     if (ib && c->p.junction_period > 0) {
-        e = run_with_junctions(c, n_steps);
+        e = run_with_junctions(c, n_steps, [](int, auto&& fn) { return fn(); });
         if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
         c->fields_valid = true;
         c->vforce_valid = true;
@@ -675,11 +708,11 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
 int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
     if (!c || !ms_out) return LBIB_E_PARAM;
     if (n_steps <= 0) return fail(c, LBIB_E_PARAM, "n_steps must be > 0");
-    if (c->nC > 0 && c->p.junction_period > 0)
-        return fail(c, LBIB_E_STATE, "profiled steps do not cover cell junctions");
     const bool ib = c->nC > 0;
-    // one event before and after every launch: 2 per launch
-    const int n_launch = n_steps + (ib ? n_steps + 1 : 0);
+    const bool junctions = ib && c->p.junction_period > 0;
+    // one event before and after every launch: 2 per launch (with junctions
+    // at most a renewal, a prep, a lattice update and a move per step)
+    const int n_launch = junctions ? 4 * n_steps + 2 : n_steps + (ib ? n_steps + 1 : 0);
     std::vector<cudaEvent_t> ev((size_t)2 * n_launch, nullptr);
     std::vector<int> kind((size_t)n_launch, 0);
     cudaError_t e = cudaSuccess;
@@ -693,12 +726,19 @@ int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
         if (e == cudaSuccess) e = cudaEventRecord(ev[2 * li + 1], c->stream);
         kind[li++] = k;
     };
-    if (ib) timed(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
-    for (int left = n_steps; left > 0 && e == cudaSuccess; --left) {
-        const bool last = (left == 1);
-        timed(0, [&] { return enqueue_lattice(c, c->cur, last); });
-        if (ib) timed(1, [&] { return enqueue_ib(c, true, !last, left == 2); });
-        c->cur = 1 - c->cur;
+    if (junctions) {
+        run_with_junctions(c, n_steps, [&](int k, auto&& fn) {
+            timed(k, fn);
+            return e;
+        });
+    } else {
+        if (ib) timed(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
+        for (int left = n_steps; left > 0 && e == cudaSuccess; --left) {
+            const bool last = (left == 1);
+            timed(0, [&] { return enqueue_lattice(c, c->cur, last); });
+            if (ib) timed(1, [&] { return enqueue_ib(c, true, !last, left == 2); });
+            c->cur = 1 - c->cur;
+        }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     ms_out[0] = ms_out[1] = 0.0;

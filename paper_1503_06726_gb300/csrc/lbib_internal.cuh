@@ -41,7 +41,6 @@ enum Diag : int {
     kDiagWallStencil = 1, // an IB stencil node fell outside a walled domain (dropped)
     kDiagRasterSlow = 2,  // a cell used the brute-force labelling path
     kDiagGeometry = 3,    // a cell's bounding box became non-finite or wider than the lattice
-    kDiagJunctionBin = 4, // a junction search bin overflowed (its extra vertices were skipped)
     kDiagWords = 64
 };
 
@@ -56,7 +55,7 @@ struct Layout {
     uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0, src = 0, smask = 0;
     uint64_t dom = 0;          // domain labels of the confined species (noflux_mask != 0)
     // cell junctions (junction_period > 0): partner and cell of every vertex, bins
-    uint64_t jpartner = 0, jcell = 0, jbins = 0;
+    uint64_t jpartner = 0, jcell = 0, jcnt = 0, jstart = 0, jvbin = 0, jent = 0;
     int jnbx = 0, jnby = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
@@ -145,17 +144,33 @@ struct IBArgs {
 };
 
 // renewal of the cell junctions: vertices binned into an nbx x nby grid of
-// bins at least lmax wide, kJunctionBinCap slots each (slot 0: the count)
-constexpr int kJunctionBinCap = 32;
+// Junction renewal: the vertices sorted into a uniform grid of bins at least
+// l_max wide, CSR (count per bin, offsets, entries grouped by bin)
+struct __align__(16) JunctionEntry {
+    float x, y;  // wrapped position in FP32 (for the prefilter)
+    int cell, v;
+};
 struct JunctionArgs {
     const double2* xy;
     const int32_t* vcell;   // cell index of every vertex
     int32_t* partner;
-    int* bins;
-    uint32_t* diag;
+    int* cnt;               // nbins: counts, then fill cursors
+    int* start;             // nbins + 1 offsets into ent
+    int* vbin;              // bin of every vertex
+    JunctionEntry* ent;     // nv entries
     int nv, nx, ny, bc_y, nbx, nby;
-    double wbx, wby, lmax;
+    double inv_nx, inv_ny, inv_wbx, inv_wby, lmax;
+    float fthr;             // FP32 prefilter bound on the squared distance
 };
+
+// The periodic minimum image d - n round(d/n) of a coordinate difference in
+// FP64, with that expression's result: for |d| <= 0.49 n the quotient rounds
+// to zero and d comes back unchanged, so the division (slow at this GPU's
+// FP64 rate) only runs for differences across the periodic seam.
+__device__ __forceinline__ double min_image(double d, int n) {
+    if (fabs(d) <= 0.49 * (double)n) return d;
+    return __dsub_rn(d, __dmul_rn((double)n, round(__ddiv_rn(d, (double)n))));
+}
 
 // shared memory of the FP32 per-cell IB work (one CTA per cell), as pointers
 // into the CTA's shared memory; the vertex arrays hold `maxv` entries

@@ -13,7 +13,7 @@ them the whole coupled trajectory, match the oracle:
   - FP32 storage within the FP32 bounds (u 1e-4, X 1e-6 lattice units);
   - the junctions change the trajectory (positions move by more than 1e-4
     against a run without them);
-  - profiled steps and ensembles refuse junctions.
+  - the profiled step takes the same steps; ensembles refuse junctions.
 """
 import numpy as np
 import pytest
@@ -88,6 +88,27 @@ def test_junctions_periodic_fp64(lb, orc):
     _check_fp64(_gpu(lb, w, lb.LBIB_FP64, (30,)), ref)
 
 
+def test_junctions_dense_membranes_fp64(lb, orc):
+    """Cells of 400 vertices (0.2 lattice units apart) put well over a hundred
+    vertices into one search bin; the partners and the trajectory still follow
+    the oracle's brute-force search."""
+    w = _walled()
+    base = w.tissue
+    C = base.n_cells
+    n0 = int(base.cell_off[1] - base.cell_off[0])
+    centres = [tuple(base.xy[base.cell_off[c]:base.cell_off[c + 1]].mean(axis=0))
+               for c in range(C)]
+    radii = [float(np.hypot(*(base.xy[base.cell_off[c]] - centres[c]))) for c in range(C)]
+    assert n0 == 100
+    T = li.make_tissue(centres, radii, 400, 0.02, 1e-3, base.src_flag)
+    w.tissue = T
+    ref = orc.run(w.params, T, 12)
+    _check_fp64(_gpu(lb, w, lb.LBIB_FP64, (12,)), ref)
+    p = w.params
+    part = orc.junction_partners(p.nx, p.ny, p.bc_y, T.cell_off, ref.xy, p.junction_lmax)
+    assert (part >= 0).sum() > 1000
+
+
 def test_junctions_fp32(lb, orc):
     w = _walled()
     ref = orc.run(w.params, w.tissue, 40)
@@ -104,13 +125,26 @@ def test_junctions_change_the_trajectory(lb):
     assert np.abs(a["xy"] - b["xy"]).max() > 1e-4
 
 
-def test_junctions_refused_where_unsupported(lb):
+def test_junctions_profiled_step_matches(lb):
+    """The profiled step takes the same steps: split 25 + 15 over a plain and
+    a profiled call, the state equals the plain 40-step run (to 1e-12: the
+    spreading's atomic order is not fixed)."""
     w = _walled()
+    ref = _gpu(lb, w, lb.LBIB_FP64, (40,))
     T = w.tissue
-    sim = lb.Simulation(w.params, lb.LBIB_FP32, T.n_vertices, T.n_cells)
+    sim = lb.Simulation(w.params, lb.LBIB_FP64, T.n_vertices, T.n_cells)
     sim.set_cells(T)
-    with pytest.raises(lb.LbibError):
-        sim.step_profiled(2)
+    sim.step(25)
+    lat_ms, ib_ms = sim.step_profiled(15)
+    got = sim.fields(ALL)
     sim.close()
+    assert lat_ms > 0 and ib_ms > 0
+    for k in ("ux", "uy", "phi", "vforce"):
+        assert rel(got[k], ref[k]) < 1e-12, k
+    assert np.abs(got["xy"] - ref["xy"]).max() < 1e-12
+
+
+def test_junctions_refused_by_ensembles(lb):
+    w = _walled()
     with pytest.raises(lb.LbibError):
-        lb.Ensemble([w.params], [T])
+        lb.Ensemble([w.params], [w.tissue])
