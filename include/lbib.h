@@ -121,7 +121,24 @@ extern "C" {
  *                junction_k (d/|d|)(|d| - junction_l0), d = X_partner - X,
  *                while |d| < junction_lmax.  Steps with junctions move the
  *                vertices and compute the forces in separate launches and
- *                are not captured in graphs. */
+ *                are not captured in graphs.
+ *   mass_sources, mass_alpha
+ *                1 = per-cell mass sources (Sec. 3.2.3): every step each
+ *                node labelled with cell c (the lowest cell containing it)
+ *                gains S_c = rate_c + mass_alpha (A0_c - A_c) of fluid mass,
+ *                added after the collision as w_q S_c in every direction (no
+ *                momentum); A_c is the polygon area at the start of the
+ *                step, rate_c and the set points A0_c come from
+ *                lbib_set_mass_sources (the controller term only once set
+ *                points are given).  The cells are labelled every step.
+ *   pressure_nodes, pressure_rho
+ *                1 = internal pressure nodes (Sec. 6.1): before the
+ *                collision every population of a node flagged by
+ *                lbib_set_pressure_nodes is multiplied by
+ *                pressure_rho / rho, so the node holds the prescribed
+ *                density (pressure rho/3) and keeps its velocity; such
+ *                nodes take up or give off mass (the sink of growing
+ *                tissues).  pressure_rho > 0. */
 typedef struct lbib_params {
     int32_t nx, ny, bc_y, n_species;
     double tau, rho0;
@@ -134,6 +151,8 @@ typedef struct lbib_params {
     double schnak[3];
     double junction_k, junction_l0, junction_lmax;
     int32_t junction_period, junction_pad;
+    int32_t mass_sources, pressure_nodes;
+    double mass_alpha, pressure_rho;
 } lbib_params;
 
 typedef struct lbib_ctx lbib_ctx;
@@ -175,6 +194,22 @@ int lbib_set_cells(lbib_ctx* ctx, int32_t n_cells, const int32_t* cell_off, cons
  * update; it is zero (one domain) until set.  LBIB_E_STATE when the context
  * was created with noflux_mask 0.  Synchronises the context stream. */
 int lbib_set_domains(lbib_ctx* ctx, const int32_t* labels);
+
+/* Set the per-cell mass sources (mass_sources): rate (host, n_cells doubles,
+ * NULL = 0) is the constant part of each cell's source, target_area (host,
+ * n_cells doubles, NULL = controller off) the set points A0_c of the
+ * proportional area controller S_c = rate_c + mass_alpha (A0_c - A_c)
+ * (Sec. 3.2.3).  Both are copied; they apply from the next step on and stay
+ * until set again.  LBIB_E_STATE when the context was created with
+ * mass_sources 0.  Synchronises the context stream. */
+int lbib_set_mass_sources(lbib_ctx* ctx, const double* rate, const double* target_area);
+
+/* Set the internal pressure nodes (pressure_nodes): mask is a host array of
+ * nx*ny bytes, row-major in j, nonzero = the node is held at pressure_rho
+ * (Sec. 6.1).  NULL clears every node.  The plane lives in the workspace and
+ * is zero until set.  LBIB_E_STATE when the context was created with
+ * pressure_nodes 0.  Synchronises the context stream. */
+int lbib_set_pressure_nodes(lbib_ctx* ctx, const uint8_t* mask);
 
 /* Choose how many lattice nodes one thread of the lattice update handles.
  * 2 (the default) lets FP16 storage update two adjacent nodes per thread,

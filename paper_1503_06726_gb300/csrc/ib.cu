@@ -111,6 +111,10 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
         if (!finite) s_flag = 2;
     }
     __syncthreads();
+    if (a.msrc_out && warp == 0) {  // the cell's mass source (Sec. 3.2.3)
+        const double a_c = cell_area_warp(sx, n, lane);
+        if (lane == 0) static_cast<C*>(a.msrc_out)[c] = (C)mass_source(a, c, a_c);
+    }
     const int I0 = sbox[0], I1 = sbox[1], J0 = sbox[2], J1 = sbox[3];
     // Labels need a finite box no wider than the lattice; otherwise the
     // geometry has blown up: flag it and leave the labels empty so that every

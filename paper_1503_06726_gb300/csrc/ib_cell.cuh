@@ -73,6 +73,28 @@ __device__ __forceinline__ double2 junction_force64(const IBArgs& a, double2 X, 
     return make_double2(a.jk * d.x / L * (L - a.jl0), a.jk * d.y / L * (L - a.jl0));
 }
 
+// Shoelace area of a polygon held in shared memory, taken about its first
+// vertex (Sec. 3.3), summed by one warp in FP64; every lane returns it.
+__device__ __forceinline__ double cell_area_warp(const double2* sx, int n, int lane) {
+    const double2 X0 = sx[0];
+    double acc = 0.0;
+    for (int t = lane; t < n; t += 32) {
+        const double2 A = sx[t], B = sx[t + 1 == n ? 0 : t + 1];
+        const double xl = A.x - X0.x, yl = A.y - X0.y, xm = B.x - X0.x, ym = B.y - X0.y;
+        acc += xl * ym - xm * yl;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return 0.5 * acc;
+}
+
+// the mass source of cell c for the step (Sec. 3.2.3): the constant rate plus
+// the proportional area controller when target areas are set
+__device__ __forceinline__ double mass_source(const IBArgs& a, int c, double area) {
+    const double r = a.mrate ? a.mrate[c] : 0.0;
+    return a.marea ? r + a.malpha * (a.marea[c] - area) : r;
+}
+
 // raise a diagnostic flag (labelling-only callers may pass no flag words)
 __device__ __forceinline__ void raise_flag(uint32_t* diag, int k) {
     if (diag) atomicOr(diag + k, 1u);
@@ -604,6 +626,12 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
         if (!finite) s_flag = 2;
     }
     cell_sync<NT>(bar);
+    if (a.msrc_out && tid < 32) {
+        // mass source of the cell (Sec. 3.2.3): S_c = rate + alpha (A0 - A_c),
+        // A_c the shoelace area of the moved polygon about its first vertex
+        const double a_c = cell_area_warp(sx, n, lane);
+        if (lane == 0) static_cast<float*>(a.msrc_out)[c] = (float)mass_source(a, c, a_c);
+    }
     // columns: floor(x) over the vertices, widened by one on each side (the
     // fractions are FP32); rows: every J with min ceil(y) <= J < max ceil(y),
     // exactly the rows some edge crosses

@@ -177,7 +177,12 @@ _Pragma("unroll") \
     /* ---- the collision (collide_node), then the stores */ \
     C rho, ux, uy; \
     C ph[S > 0 ? S : 1]; \
-    collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph); \
+    /* the cell's mass source at labelled nodes; internal pressure nodes */ \
+    C ms = C(0); \
+    if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
+    const bool pn = a.pnode && a.pnode[node] != 0; \
+    collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph, \
+                                        a.msrc != nullptr, ms, pn); \
     T* G = static_cast<T*>(a.fdst); \
 _Pragma("unroll") \
     for (int q = 0; q < 9; ++q) St::st((G + q * P) + node, d[q]); \
@@ -297,7 +302,9 @@ template <typename V, int S, int FORCING, bool SCALED>
 __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k, V (&d)[9],
                                              V (&g)[S > 0 ? S : 1][5], V fvx, V fvy,
                                              uint32_t bitsA, uint32_t bitsB, V& rho, V& ux,
-                                             V& uy, V (&ph)[S > 0 ? S : 1]) {
+                                             V& uy, V (&ph)[S > 0 ? S : 1],
+                                             bool mass_on = false, V ms = V(),
+                                             bool pnode = false) {
     using L = Lane<V>;
     using C = typename L::S;
     const V Fx = L::add(L::c(k.bfx), fvx), Fy = L::add(L::c(k.bfy), fvy);
@@ -318,6 +325,20 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
         jx = L::add(L::add(L::sub(d[1], d[3]), L::sub(d[5], d[6])), L::sub(d[8], d[7]));
         jy = L::sub(L::add(L::sub(d[2], d[4]), L::add(d[5], d[6])), L::add(d[7], d[8]));
     }
+    if (pnode) {
+        // internal pressure node (Sec. 6.1): every population scaled by
+        // gamma = rho_p / rho, so the node holds rho_p and keeps u; on the
+        // deviations d = f - w rho0 (scaled: / (w sigma)) that is
+        // d <- gamma d + (gamma - 1) w rho0 (scaled: (gamma - 1) rho0 / sigma)
+        const V gam = L::mul(L::c(k.prho), L::rcp(L::add(L::c(k.rho0), drho)));
+        const V gm1 = L::sub(gam, L::c(C(1)));
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            d[q] = L::fma(gam, d[q], L::mul(gm1, L::c(SCALED ? k.rho0 * k.isig : C(w9(q)) * k.rho0)));
+        drho = L::c(k.prho - k.rho0);
+        jx = L::mul(gam, jx);
+        jy = L::mul(gam, jy);
+    }
     rho = L::add(L::c(k.rho0), drho);
     const V irho = L::rcp(rho);
     if (FORCING == LBIB_GUO) {
@@ -335,6 +356,8 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
     V E0 = L::fma(W, nusq, A);  // the even part common to every direction
     if (FORCING == LBIB_GUO)
         E0 = L::fma(L::c(C(-3) * k.pref), L::fma(ux, Fx, L::mul(uy, Fy)), E0);
+    // mass source (Sec. 3.2.3): w_q S added to every direction, no momentum
+    if (mass_on) E0 = L::add(E0, ms);
     const V omc = L::c(k.omc);
     d[0] = L::fma(L::c(SCALED ? k.isig : C(w9(0))), E0, L::mul(omc, d[0]));
 #pragma unroll

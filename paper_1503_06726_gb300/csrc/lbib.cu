@@ -64,6 +64,12 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.smask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
     if (p.noflux_mask) l.dom = take(P * 4);
+    if (p.mass_sources && max_cells > 0) {
+        l.mrate = take((uint64_t)max_cells * 8);
+        l.marea = take((uint64_t)max_cells * 8);
+        l.msrc = take((uint64_t)max_cells * 8);
+    }
+    if (p.pressure_nodes) l.pnode = take(align_up(P, 8));
     if (p.junction_period > 0 && max_cells > 0) {
         // bins at least l_max wide (with a margin against rounding at their
         // edges); wider where they would outnumber the vertices by far
@@ -152,6 +158,14 @@ static int check_params(const lbib_params* p, std::string* why) {
         *why = "junctions need period >= 0, 0 < l_max <= min(nx, ny)/3, finite k, l0 >= 0";
         return LBIB_E_PARAM;
     }
+    if ((p->mass_sources != 0 && p->mass_sources != 1) || !std::isfinite(p->mass_alpha)) {
+        *why = "mass_sources must be 0 or 1 and mass_alpha finite"; return LBIB_E_PARAM;
+    }
+    if ((p->pressure_nodes != 0 && p->pressure_nodes != 1) ||
+        (p->pressure_nodes && (!(p->pressure_rho > 0.0) || !std::isfinite(p->pressure_rho)))) {
+        *why = "pressure_nodes must be 0 or 1 and pressure_rho finite and > 0";
+        return LBIB_E_PARAM;
+    }
     return LBIB_OK;
 }
 
@@ -176,6 +190,7 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
     k->sgamma = (C)p.schnak[0];
     k->sa = (C)p.schnak[1];
     k->sb = (C)p.schnak[2];
+    k->prho = (C)(p.pressure_nodes ? p.pressure_rho : p.rho0);
     const double sf = p.fp16_scale > 0 ? p.fp16_scale : std::ldexp(1.0, -10);
     const double sg = p.fp16_scale_species > 0 ? p.fp16_scale_species : std::ldexp(1.0, -8);
     const bool scaled = p.precision == LBIB_FP16;
@@ -235,6 +250,8 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.lmask = c->at<uint32_t>(L.lmask);
     a.src = c->at<uint8_t>(L.src);
     a.smask = c->at<uint32_t>(L.smask);
+    if (c->p.mass_sources && c->nC > 0) a.msrc = c->ws + L.msrc;
+    if (c->p.pressure_nodes) a.pnode = c->at<uint8_t>(L.pnode);
     return a;
 }
 
@@ -280,6 +297,15 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
     a.lmask = c->at<uint32_t>(L.lmask);
     a.src = c->at<uint8_t>(L.src);
     a.smask = c->at<uint32_t>(L.smask);
+    if (c->p.mass_sources && prep && L.msrc) {
+        // S_c for the coming lattice update, at every node labelled c: the
+        // labels are needed every step
+        a.msrc_out = c->ws + L.msrc;
+        a.mrate = c->at<double>(L.mrate);
+        a.marea = c->mass_ctrl ? c->at<double>(L.marea) : nullptr;
+        a.malpha = c->p.mass_alpha;
+        a.do_ids = 1;
+    }
     return a;
 }
 
@@ -496,6 +522,11 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.smask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess && params->noflux_mask)
         e = cudaMemsetAsync(c->ws + L.dom, 0, L.plane * 4, c->stream);
+    for (uint64_t off : {L.mrate, L.marea, L.msrc})
+        if (e == cudaSuccess && off)
+            e = cudaMemsetAsync(c->ws + off, 0, (size_t)8 * max_cells, c->stream);
+    if (e == cudaSuccess && params->pressure_nodes)
+        e = cudaMemsetAsync(c->ws + L.pnode, 0, align_up(L.plane, 8), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && max_cells > 0)
@@ -599,6 +630,47 @@ int lbib_set_domains(lbib_ctx* c, const int32_t* labels) {
         e = cudaMemsetAsync(c->ws + L.dom, 0, L.plane * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_domains");
+    return LBIB_OK;
+}
+
+int lbib_set_mass_sources(lbib_ctx* c, const double* rate, const double* target_area) {
+    if (!c) return LBIB_E_PARAM;
+    if (!c->p.mass_sources || !c->L.mrate)
+        return fail(c, LBIB_E_STATE, "the context has no mass sources");
+    const Layout& L = c->L;
+    const size_t nc = (size_t)c->nC;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess && nc > 0) {
+        if (rate)
+            e = cudaMemcpyAsync(c->ws + L.mrate, rate, nc * 8, cudaMemcpyHostToDevice, c->stream);
+        else
+            e = cudaMemsetAsync(c->ws + L.mrate, 0, nc * 8, c->stream);
+    }
+    if (e == cudaSuccess && nc > 0 && target_area)
+        e = cudaMemcpyAsync(c->ws + L.marea, target_area, nc * 8, cudaMemcpyHostToDevice,
+                            c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_mass_sources");
+    if (c->mass_ctrl != (target_area != nullptr)) {
+        drop_graphs(c);  // the captured steps hold the other controller setting
+        c->mass_ctrl = target_area != nullptr;
+    }
+    return LBIB_OK;
+}
+
+int lbib_set_pressure_nodes(lbib_ctx* c, const uint8_t* mask) {
+    if (!c) return LBIB_E_PARAM;
+    if (!c->p.pressure_nodes) return fail(c, LBIB_E_STATE, "the context has no pressure nodes");
+    const Layout& L = c->L;
+    cudaError_t e;
+    if (mask)
+        e = cudaMemcpy2DAsync(c->ws + L.pnode, (size_t)L.pitch, mask, (size_t)c->p.nx,
+                              (size_t)c->p.nx, (size_t)c->p.ny, cudaMemcpyHostToDevice,
+                              c->stream);
+    else
+        e = cudaMemsetAsync(c->ws + L.pnode, 0, L.plane, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_pressure_nodes");
     return LBIB_OK;
 }
 

@@ -56,6 +56,8 @@ struct Layout {
     uint64_t dom = 0;          // domain labels of the confined species (noflux_mask != 0)
     // cell junctions (junction_period > 0): partner and cell of every vertex, bins
     uint64_t jpartner = 0, jcell = 0, jcnt = 0, jstart = 0, jvbin = 0, jent = 0;
+    uint64_t mrate = 0, marea = 0, msrc = 0;  // per-cell mass source data (mass_sources)
+    uint64_t pnode = 0;        // internal pressure nodes, one byte per node (pressure_nodes)
     int jnbx = 0, jnby = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
@@ -78,6 +80,7 @@ struct Coefs {
     C isig, isig_g;             // 1/sigma, 1/sigma_g of scaled (FP16) storage, else 1
     int react_model;            // LBIB_REACT_LINEAR or LBIB_REACT_SCHNAKENBERG
     C sgamma, sa, sb;           // Schnakenberg gamma, a, b
+    C prho;                     // density held at internal pressure nodes
 };
 
 struct LatticeArgs {
@@ -109,6 +112,12 @@ struct LatticeArgs {
     uint32_t* fmask;
     uint32_t* lmask;
     uint32_t* smask;
+    // mass sources (Sec. 3.2.3): S_c of every cell for this step (compute
+    // type, written by the IB prep), added at the nodes labelled c; NULL = none
+    const void* msrc;
+    // internal pressure nodes (Sec. 6.1): one byte per node (pitch layout),
+    // nonzero = populations rescaled to the density prho; NULL = none
+    const uint8_t* pnode;
 };
 
 struct IBArgs {
@@ -141,9 +150,15 @@ struct IBArgs {
     // vertex (-1 none), NULL = no junctions; spring constant, rest length, cutoff
     const int32_t* jpartner;
     double jk, jl0, jlmax;
+    // mass sources (Sec. 3.2.3): the prep writes S_c = mrate[c] +
+    // malpha (marea[c] - A_c) (A_c the polygon area after the move; without
+    // marea S_c = mrate[c]) to msrc_out[c] in the lattice compute type; NULL = none
+    void* msrc_out;
+    const double* mrate;
+    const double* marea;
+    double malpha;
 };
 
-// renewal of the cell junctions: vertices binned into an nbx x nby grid of
 // Junction renewal: the vertices sorted into a uniform grid of bins at least
 // l_max wide, CSR (count per bin, offsets, entries grouped by bin)
 struct __align__(16) JunctionEntry {

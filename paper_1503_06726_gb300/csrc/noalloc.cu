@@ -72,6 +72,9 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     if (params->junction_period > 0)
         return set_thread_error(LBIB_E_PARAM,
                                 "lbib_step_noalloc: cell junctions need a context");
+    if (params->mass_sources || params->pressure_nodes)
+        return set_thread_error(LBIB_E_PARAM,
+                                "lbib_step_noalloc: mass sources and pressure nodes need a context");
     if (params->reaction != LBIB_REACT_LINEAR &&
         !(params->reaction == LBIB_REACT_SCHNAKENBERG && params->n_species >= 2))
         return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: invalid reaction model");

@@ -40,7 +40,7 @@ PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
 # every symbol declared in include/lbib.h
 EXPORTS = (
     "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_lattice_variant",
-    "lbib_set_domains",
+    "lbib_set_domains", "lbib_set_mass_sources", "lbib_set_pressure_nodes",
     "lbib_set_cell_params",
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
@@ -75,6 +75,8 @@ class lbib_params(ctypes.Structure):
         ("junction_k", ctypes.c_double), ("junction_l0", ctypes.c_double),
         ("junction_lmax", ctypes.c_double), ("junction_period", ctypes.c_int32),
         ("junction_pad", ctypes.c_int32),
+        ("mass_sources", ctypes.c_int32), ("pressure_nodes", ctypes.c_int32),
+        ("mass_alpha", ctypes.c_double), ("pressure_rho", ctypes.c_double),
     ]
 
 
@@ -98,6 +100,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_set_cell_params": (ctypes.c_int, [vp, vp, vp]),
         "lbib_set_lattice_variant": (ctypes.c_int, [vp, i32]),
         "lbib_set_domains": (ctypes.c_int, [vp, vp]),
+        "lbib_set_mass_sources": (ctypes.c_int, [vp, vp, vp]),
+        "lbib_set_pressure_nodes": (ctypes.c_int, [vp, vp]),
         "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
         "lbib_step": (ctypes.c_int, [vp, i32]),
         "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
@@ -195,6 +199,10 @@ def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
     o.junction_l0 = float(getattr(p, "junction_l0", 0.0) or 0.0)
     o.junction_lmax = float(getattr(p, "junction_lmax", 0.0) or 0.0)
     o.junction_period = int(getattr(p, "junction_period", 0) or 0)
+    o.mass_sources = int(getattr(p, "mass_sources", 0) or 0)
+    o.mass_alpha = float(getattr(p, "mass_alpha", 0.0) or 0.0)
+    o.pressure_nodes = int(getattr(p, "pressure_nodes", 0) or 0)
+    o.pressure_rho = float(getattr(p, "pressure_rho", 0.0) or 0.0)
     return o
 
 
@@ -228,6 +236,19 @@ def lbib_set_domains(ctx, labels=None):
     """labels: (ny, nx) int32 domain of every node, or None (one domain)."""
     a, a_p = _p(labels, np.int32)
     _check(load().lbib_set_domains(ctx, a_p), ctx)
+
+
+def lbib_set_mass_sources(ctx, rate=None, target_area=None):
+    """rate, target_area: per-cell float64 arrays, or None."""
+    r, r_p = _p(rate, np.float64)
+    t, t_p = _p(target_area, np.float64)
+    _check(load().lbib_set_mass_sources(ctx, r_p, t_p), ctx)
+
+
+def lbib_set_pressure_nodes(ctx, mask=None):
+    """mask: (ny, nx) uint8, nonzero = pressure node, or None (none)."""
+    m, m_p = _p(mask, np.uint8)
+    _check(load().lbib_set_pressure_nodes(ctx, m_p), ctx)
 
 
 def lbib_set_lattice_variant(ctx, nodes_per_thread: int):
@@ -437,6 +458,12 @@ class Simulation:
 
     def set_domains(self, labels=None):
         lbib_set_domains(self.ctx, labels)
+
+    def set_mass_sources(self, rate=None, target_area=None):
+        lbib_set_mass_sources(self.ctx, rate, target_area)
+
+    def set_pressure_nodes(self, mask=None):
+        lbib_set_pressure_nodes(self.ctx, mask)
 
     def set_lattice_variant(self, nodes_per_thread: int):
         lbib_set_lattice_variant(self.ctx, nodes_per_thread)
