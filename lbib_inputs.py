@@ -341,6 +341,30 @@ def case4(level: int, max_length: float = 0.5) -> Workload:
     return Workload(f"case4_level{level}_{N}x{N}_dia{int(D)}", P, T, 10000 * 4 ** level, 0)
 
 
+def case2(level: int, max_length: float = 0.5) -> Workload:
+    """Validation Case II (Sec. 6.3): a circular cell grown by a constant mass
+    source, uniform over the nodes inside it, no membrane force, tau 1, no
+    species.  Level k: domain 100*2^k, diameter 10*2^k lattice units,
+    T = 1e4*4^k steps (the study's table), per-node source ln 2 / T so that
+    the area doubles by T.  The excess mass leaves through internal pressure
+    nodes at rho0 on the periodic seam (row 0 and column 0), in place of the
+    study's iso-pressure outflow boundary."""
+    N = 100 * 2 ** level
+    D = 10.0 * 2 ** level
+    steps = 10000 * 4 ** level
+    P = LatticeParams(nx=N, ny=N, bc_y=BC_PERIODIC, tau=1.0, rho0=1.0, n_species=0)
+    P.mass_sources = 1
+    P.pressure_nodes, P.pressure_rho = 1, 1.0
+    n_vert = int(math.ceil(math.pi * D / max_length))
+    T = make_tissue([(N / 2.0, N / 2.0)], [D / 2.0], n_vert, 0.0, 0.0, [0])
+    w = Workload(f"case2_level{level}_{N}x{N}_dia{int(D)}", P, T, steps, 0)
+    w.mass_rate = np.array([math.log(2.0) / steps])
+    w.pressure_mask = np.zeros((N, N), np.uint8)
+    w.pressure_mask[0, :] = 1
+    w.pressure_mask[:, 0] = 1
+    return w
+
+
 def voronoi_domains(nx: int, ny: int, spacing: float, seed: int) -> np.ndarray:
     """A static cellular domain: the periodic Voronoi tiling of a jittered
     grid of centres (spacing lattice units, +-spacing/4 jitter); label of a
