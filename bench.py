@@ -26,7 +26,8 @@ c4 (64 independent tissues in one persistent launch); c5 (the learned warm
 start of the steady morphogen solve, warm vs cold); turing (the
 Schnakenberg system on a static cellular domain of 1024^2, receptor confined
 to its cell); c2-junctions (the default tissue with cell junctions renewed
-every 10 steps); case2 (the mass-source growth study: a cell doubling its area
+every 10 steps); c2-growth (the default tissue growing under the area
+controller, pressure nodes along the walls); case2 (the mass-source growth study: a cell doubling its area
 under a uniform source at four refinements); case4 (the immersed-
 boundary leakage study: area loss under constant membrane tension at four
 refinements and its order of convergence).
@@ -80,6 +81,8 @@ def workload(name: str):
         return li.turing(), "fp32"
     if name == "c2-junctions":
         return li.config2_junctions(), "fp32"
+    if name == "c2-growth":
+        return li.config2_growth(), "fp32"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -90,6 +93,10 @@ def prepare(sim, w):
     if getattr(w, "phi0", None) is not None:
         for s in range(w.params.n_species):
             sim.set_species(s, w.phi0[s])
+    if getattr(w, "mass_rate", None) is not None or getattr(w, "target_area", None) is not None:
+        sim.set_mass_sources(getattr(w, "mass_rate", None), getattr(w, "target_area", None))
+    if getattr(w, "pressure_mask", None) is not None:
+        sim.set_pressure_nodes(w.pressure_mask)
 
 
 def workload_config(w, precision, extra=None):
@@ -244,7 +251,10 @@ def oracle_sample(w, target_s: float, max_steps: int, threads: int | None = None
     chunk = p.junction_period if (p.junction_period > 0 and T.n_cells > 0) else 1
     steps, t0 = 0, time.perf_counter()
     while steps < max_steps:
-        r = oracle.run(p, T, chunk, f=f, g=g, xy=xy, dom=dom)
+        r = oracle.run(p, T, chunk, f=f, g=g, xy=xy, dom=dom,
+                       mass_rate=getattr(w, "mass_rate", None),
+                       target_area=getattr(w, "target_area", None),
+                       pmask=getattr(w, "pressure_mask", None))
         f, g, xy = r.f, r.g, r.xy
         steps += chunk
         if time.perf_counter() - t0 >= target_s:

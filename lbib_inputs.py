@@ -197,7 +197,9 @@ def config2(seed: int = 2, n_steps: int = 5000, nx: int = 1024, ny: int = 1024,
     src = np.zeros(C, np.uint8)
     src[rng.choice(C, size=n_src, replace=False)] = 1
     T = make_tissue(centres, radii, 100, 0.02, 1e-3, src)
-    return Workload(f"c2_{nx}x{ny}_fp32_walls_{C}cells_2species", P, T, n_steps, seed)
+    w = Workload(f"c2_{nx}x{ny}_fp32_walls_{C}cells_2species", P, T, n_steps, seed)
+    w.radii = radii
+    return w
 
 
 def config2_junctions(seed: int = 2, n_steps: int = 5000, period: int = 10) -> Workload:
@@ -210,6 +212,28 @@ def config2_junctions(seed: int = 2, n_steps: int = 5000, period: int = 10) -> W
     p.junction_k, p.junction_l0, p.junction_lmax, p.junction_period = 0.02, 8.0, 14.0, period
     return Workload(w.name.replace("c2_", "c2j_") + f"_junctions_every{period}", p, w.tissue,
                     n_steps, seed)
+
+
+def config2_growth(seed: int = 2, n_steps: int = 5000, growth: float = 1.2,
+                   alpha: float = 2e-6) -> Workload:
+    """The 1024^2 walled tissue of ``config2`` growing under the proportional
+    area controller (Sec. 3.2.3): every cell's set point is ``growth`` times
+    its initial polygon area (regular 100-gon), gain alpha; the rows next to
+    the two walls are internal pressure nodes at rho0 that take up the added
+    mass."""
+    w = config2(seed=seed, n_steps=n_steps)
+    p = w.params
+    p.mass_sources, p.mass_alpha = 1, alpha
+    p.pressure_nodes, p.pressure_rho = 1, 1.0
+    n = 100
+    poly_area = 0.5 * n * np.asarray(w.radii) ** 2 * math.sin(2.0 * math.pi / n)
+    w.mass_rate = np.zeros(w.tissue.n_cells)
+    w.target_area = growth * poly_area
+    w.pressure_mask = np.zeros((p.ny, p.nx), np.uint8)
+    w.pressure_mask[0, :] = 1
+    w.pressure_mask[-1, :] = 1
+    w.name = w.name.replace("c2_", "c2g_") + f"_area_controller_x{growth:g}"
+    return w
 
 
 def jittered_grid_tissue(rng, nx, ny, spacing, radius, n_vert, k, pressure,
