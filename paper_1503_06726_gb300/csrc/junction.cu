@@ -4,7 +4,8 @@
 //
 // The vertices are sorted into a uniform grid of bins at least l_max wide
 // (CSR: count, one-CTA scan, fill; no per-bin capacity), then every vertex
-// scans the 3x3 bins around its own.  Each candidate first passes an FP32
+// scans the 3x3 bins around its own with a group of lanes that share its
+// candidates.  Each candidate first passes an FP32
 // test on wrapped positions whose bound exceeds l_max by more than the FP32
 // rounding can move a distance, so it only drops vertices that are certainly
 // out of range; the survivors take the definition's FP64 test (difference,
@@ -104,49 +105,67 @@ __device__ __forceinline__ float fold(float d, float n, float half) {
     return d > half ? d - n : (d < -half ? d + n : d);
 }
 
+// lanes that share one vertex's candidates (an aligned group within a warp)
+constexpr int kSearchLanes = 8;
+
 __global__ void junction_search_kernel(JunctionArgs j) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= j.nv) return;
-    const double2 Xi = j.xy[i];
-    const int ci = j.vcell[i];
-    float2 wi;
-    vertex_bin(j, Xi, &wi);
-    const int b = j.vbin[i];
-    const int bx = b % j.nbx, by = b / j.nbx;
-    const float nxf = (float)j.nx, nyf = (float)j.ny;
-    const float hx = 0.5f * nxf, hy = 0.5f * nyf;
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = (int)(gt / kSearchLanes);
+    const int r = (int)(gt % kSearchLanes);
     double best = __dmul_rn(j.lmax, j.lmax);
     int bestj = -1;
-    for (int dyb = -1; dyb <= 1; ++dyb) {
-        int b2y = by + dyb;
-        if (j.bc_y) {
-            if (b2y < 0 || b2y >= j.nby) continue;
-        } else {
-            b2y = (b2y + j.nby) % j.nby;
-        }
-        for (int dxb = -1; dxb <= 1; ++dxb) {
-            const int b2 = b2y * j.nbx + (bx + dxb + j.nbx) % j.nbx;
-            const int s1 = j.start[b2 + 1];
-            for (int s = j.start[b2]; s < s1; ++s) {
-                const JunctionEntry e = j.ent[s];
-                if (e.cell == ci) continue;
-                const float fx = fold(e.x - wi.x, nxf, hx);
-                const float fy = j.bc_y ? e.y - wi.y : fold(e.y - wi.y, nyf, hy);
-                if (fx * fx + fy * fy > j.fthr) continue;
-                // the definition's test in FP64
-                const double2 Xv = j.xy[e.v];
-                const double dx = min_image(__dsub_rn(Xv.x, Xi.x), j.nx);
-                double dy = __dsub_rn(Xv.y, Xi.y);
-                if (!j.bc_y) dy = min_image(dy, j.ny);
-                const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
-                if (d2 < best || (d2 == best && bestj >= 0 && e.v < bestj)) {
-                    best = d2;
-                    bestj = e.v;
+    if (i < j.nv) {
+        const double2 Xi = j.xy[i];
+        const int ci = j.vcell[i];
+        float2 wi;
+        vertex_bin(j, Xi, &wi);
+        const int b = j.vbin[i];
+        const int bx = b % j.nbx, by = b / j.nbx;
+        const float nxf = (float)j.nx, nyf = (float)j.ny;
+        const float hx = 0.5f * nxf, hy = 0.5f * nyf;
+        for (int dyb = -1; dyb <= 1; ++dyb) {
+            int b2y = by + dyb;
+            if (j.bc_y) {
+                if (b2y < 0 || b2y >= j.nby) continue;
+            } else {
+                b2y = (b2y + j.nby) % j.nby;
+            }
+            for (int dxb = -1; dxb <= 1; ++dxb) {
+                const int b2 = b2y * j.nbx + (bx + dxb + j.nbx) % j.nbx;
+                const int s1 = j.start[b2 + 1];
+                for (int s = j.start[b2] + r; s < s1; s += kSearchLanes) {
+                    const JunctionEntry e = j.ent[s];
+                    if (e.cell == ci) continue;
+                    const float fx = fold(e.x - wi.x, nxf, hx);
+                    const float fy = j.bc_y ? e.y - wi.y : fold(e.y - wi.y, nyf, hy);
+                    if (fx * fx + fy * fy > j.fthr) continue;
+                    // the definition's test in FP64
+                    const double2 Xv = j.xy[e.v];
+                    const double dx = min_image(__dsub_rn(Xv.x, Xi.x), j.nx);
+                    double dy = __dsub_rn(Xv.y, Xi.y);
+                    if (!j.bc_y) dy = min_image(dy, j.ny);
+                    const double d2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                    if (d2 < best || (d2 == best && bestj >= 0 && e.v < bestj)) {
+                        best = d2;
+                        bestj = e.v;
+                    }
                 }
             }
         }
     }
-    j.partner[i] = bestj;
+    // the closest candidate over the vertex's lanes, ties to the lower index
+    // (a found candidate is always strictly closer than l_max, so "none"
+    // never ties with one)
+#pragma unroll
+    for (int o = kSearchLanes / 2; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, bestj, o);
+        if (ob < best || (ob == best && oj >= 0 && (bestj < 0 || oj < bestj))) {
+            best = ob;
+            bestj = oj;
+        }
+    }
+    if (i < j.nv && r == 0) j.partner[i] = bestj;
 }
 
 cudaError_t launch_junction_renew(const JunctionArgs& j, cudaStream_t s) {
@@ -159,8 +178,12 @@ cudaError_t launch_junction_renew(const JunctionArgs& j, cudaStream_t s) {
         e = launch_kernel(junction_scan_kernel, dim3(1), dim3(1024), 0, s, false, j);
     if (e == cudaSuccess)
         e = launch_kernel(junction_fill_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
+    // kSearchLanes lanes per vertex; the block size keeps every group of
+    // lanes inside one warp
+    const int64_t search_blocks = ((int64_t)j.nv * kSearchLanes + threads - 1) / threads;
     if (e == cudaSuccess)
-        e = launch_kernel(junction_search_kernel, dim3(blocks), dim3(threads), 0, s, false, j);
+        e = launch_kernel(junction_search_kernel, dim3((unsigned)search_blocks), dim3(threads), 0,
+                          s, false, j);
     return e;
 }
 

@@ -430,15 +430,21 @@ static cudaError_t junction_renew(lbib_ctx* c) {
 // are two launches with the partner renewal between them when it is due.
 // `wrap(kind, fn)` runs one enqueue (kind 0 lattice, 1 everything else) and
 // returns its status; the profiled step brackets it with events.
+// With pdl the lattice update (after the prep) and the move (after the
+// update) are programmatic launches: the update's early population loads need
+// the previous update finished, which the previous move waited for before the
+// prep (an ordinary launch) could start; the move's early loads of the
+// vertex bases need the prep finished, which the update waits for before it
+// lets the move start.  Preps and renewals stay ordinary launches.
 template <class Wrap>
-static cudaError_t run_with_junctions(lbib_ctx* c, int n_steps, Wrap&& wrap) {
+static cudaError_t run_with_junctions(lbib_ctx* c, int n_steps, bool pdl, Wrap&& wrap) {
     cudaError_t e = cudaSuccess;
     if (junction_due(c)) e = wrap(1, [&] { return junction_renew(c); });
     if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
     for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
         const bool last = (i == n_steps - 1);
-        e = wrap(0, [&] { return enqueue_lattice(c, c->cur, last); });
-        if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, true, false, false); });
+        e = wrap(0, [&] { return enqueue_lattice(c, c->cur, last, pdl); });
+        if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, true, false, false, pdl); });
         c->cur = 1 - c->cur;
         ++c->nstep;
         if (e == cudaSuccess && !last) {
@@ -741,7 +747,7 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     cudaError_t e = cudaSuccess;
     const bool ib = c->nC > 0;
     if (ib && c->p.junction_period > 0) {
-        e = run_with_junctions(c, n_steps, [](int, auto&& fn) { return fn(); });
+        e = run_with_junctions(c, n_steps, true, [](int, auto&& fn) { return fn(); });
         if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
         c->fields_valid = true;
         c->vforce_valid = true;
@@ -799,7 +805,7 @@ int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
         kind[li++] = k;
     };
     if (junctions) {
-        run_with_junctions(c, n_steps, [&](int k, auto&& fn) {
+        run_with_junctions(c, n_steps, false, [&](int k, auto&& fn) {
             timed(k, fn);
             return e;
         });
