@@ -123,7 +123,7 @@ def lib():
             L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 7
             L.orc_run.restype = i
             L.orc_run.argtypes = ([ctypes.POINTER(OrcParams), i, vp, vp, vp, vp, vp, d, vp, i]
-                                  + [vp] * 15)
+                                  + [vp] * 16)
             L.orc_steady.restype = ctypes.c_long
             L.orc_steady.argtypes = [ctypes.POINTER(OrcParams), vp, vp, d, ctypes.c_long, i,
                                      vp, ctypes.POINTER(d)]
@@ -278,13 +278,14 @@ class RunResult:
 
 
 def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=None,
-        mass_rate=None, target_area=None, pmask=None):
+        mass_rate=None, target_area=None, pmask=None, node_source=None):
     """n coupled steps from (f, g, xy) (default: rest state and tissue.xy).
     Returns a RunResult with the final state and the last step's fields.
     dom: static domain labels (ny, nx) for the species confined by p.noflux;
     mass_rate (per cell): mass source of the cell's nodes, plus
     p.mass_alpha (target_area - area) with target_area (per cell); pmask:
-    internal pressure nodes (ny, nx) held at density p.pressure_rho."""
+    internal pressure nodes (ny, nx) held at density p.pressure_rho;
+    node_source: static mass source per node (ny, nx), added to the cells'."""
     P = _P(p)
     N = p.nx * p.ny
     if f is None or g is None:
@@ -312,7 +313,8 @@ def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=N
                        _ptr(f), _ptr(g), _ptr(r.rho), _ptr(r.ux), _ptr(r.uy), _ptr(r.phi),
                        _ptr(r.id), _ptr(r.src), _ptr(r.fx), _ptr(r.fy), _ptr(r.Fv),
                        _ptr(_dom(dom)), _ptr(_opt(mass_rate, np.float64)),
-                       _ptr(_opt(target_area, np.float64)), _ptr(_opt(pmask, np.uint8)))
+                       _ptr(_opt(target_area, np.float64)), _ptr(_opt(pmask, np.uint8)),
+                       _ptr(_opt(node_source, np.float64)))
     if rc != 0:
         raise MemoryError("oracle run failed to allocate")
     r.f = f

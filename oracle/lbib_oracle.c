@@ -526,13 +526,15 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
  * every node labelled with cell c receives
  *   S_c = mrate[c] + mass_alpha (marea[c] - A_c(X^n))
  * (the proportional area controller; without marea S_c = mrate[c]), A_c the
- * polygon area of Sec. 3.3 at the start of the step.  pmask: internal
+ * polygon area of Sec. 3.3 at the start of the step.  nsrc: a static mass
+ * source per node (the field S(x,t) of Fig. 1; NULL = none), added to the
+ * cells' sources (a point source is one node of it).  pmask: internal
  * pressure nodes (NULL = none; see orc_lattice_step). */
 int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const double* L0,
             const double* k, const double* p, double tension, const uint8_t* src_flag,
             int n_steps, double* f, double* g, double* rho, double* ux, double* uy, double* phi,
             int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv, const int32_t* dom,
-            const double* mrate, const double* marea, const uint8_t* pmask) {
+            const double* mrate, const double* marea, const uint8_t* pmask, const double* nsrc) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     int V = nc > 0 ? off[nc] : 0;
@@ -547,10 +549,10 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
     int32_t* lid = (int32_t*)malloc(sizeof(int32_t) * N);
     uint8_t* lsrc = (uint8_t*)malloc(N);
     int32_t* partner = (int32_t*)malloc(sizeof(int32_t) * (V > 0 ? V : 1));
-    double* Sn = mrate ? (double*)malloc(sizeof(double) * N) : NULL;
+    double* Sn = (mrate || nsrc) ? (double*)malloc(sizeof(double) * N) : NULL;
     double* Sc = (double*)malloc(sizeof(double) * (nc > 0 ? nc : 1));
     if (!f2 || !g2 || !Fx || !Fy || !Ux || !Uy || !F || !U || !lid || !lsrc || !partner || !Sc ||
-        (mrate && !Sn))
+        ((mrate || nsrc) && !Sn))
         return -1;
     for (int l = 0; l < V; ++l) partner[l] = -1;
     double *fa = f, *fb = f2, *ga = g, *gb = g2;
@@ -574,7 +576,11 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
             for (int c = 0; c < nc; ++c)
                 Sc[c] = marea ? mrate[c] + P->mass_alpha * (marea[c] - Sc[c]) : mrate[c];
             for (long t = 0; t < N; ++t) Sn[t] = lid[t] > 0 ? Sc[lid[t] - 1] : 0.0;
+        } else if (nsrc) {
+            for (long t = 0; t < N; ++t) Sn[t] = 0.0;
         }
+        if (nsrc)
+            for (long t = 0; t < N; ++t) Sn[t] += nsrc[t];
         orc_lattice_step(P, fa, fb, ga, gb, Fx, Fy, lsrc, last ? rho : NULL, Ux, Uy,
                          last ? phi : NULL, dom, Sn, pmask);
         if (V > 0) {

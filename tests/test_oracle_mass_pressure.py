@@ -15,7 +15,10 @@ What fixes each result (none of it retypes the oracle's update):
     cell grows its area as A0 exp(S t) when the excess mass can leave
     through pressure nodes (here a frame at the periodic seam);
   - the proportional controller S = alpha (A0 - A) brings the cell to its
-    set-point area from below and from above (its fixed point).
+    set-point area from below and from above (its fixed point);
+  - the paper's validation Case I: a point source q at the cell centre grows
+    the area linearly, A(t) = A0 + q t, with a relative error that falls with
+    refinement.
 """
 import math
 
@@ -134,3 +137,26 @@ def test_area_controller_reaches_its_set_point(orc, target_ratio):
                 pmask=_frame(n))
     print(f"target {At:.2f}, reached {r.area[0]:.2f} from {A0:.2f}")
     assert abs(r.area[0] / At - 1.0) < 0.01
+
+
+def _case1_error(orc, n, r, q, T):
+    p = li.LatticeParams(nx=n, ny=n, tau=1.0, rho0=1.0)
+    p.pressure_nodes, p.pressure_rho = 1, 1.0
+    tis = li.make_tissue([(n / 2, n / 2)], [r], 8 * int(r), 0.0, 0.0, [0])
+    A0 = orc.cell_areas(tis.cell_off, tis.xy)[0]
+    ns = np.zeros((n, n))
+    ns[n // 2, n // 2] = q
+    res = orc.run(p, tis, T, pmask=_frame(n), node_source=ns)
+    return res.area[0] / (A0 + q * T) - 1.0
+
+
+def test_point_source_grows_linearly(orc):
+    """Validation Case I: dA/dt = q for a point source of strength q, so
+    A(t) = A0 + q t; refining in diffusive scaling (diameter x2, T x4, q per
+    step fixed) the relative area error falls."""
+    e1 = _case1_error(orc, 64, 8.0, 0.05, 300)
+    e2 = _case1_error(orc, 128, 16.0, 0.05, 1200)
+    order = math.log2(abs(e1) / abs(e2))
+    print(f"relative area error {e1:+.4f} (diameter 16), {e2:+.4f} (32): order {order:.2f}")
+    assert abs(e1) < 0.005 and abs(e2) < abs(e1)
+    assert 0.8 < order < 2.2
