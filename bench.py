@@ -27,8 +27,9 @@ start of the steady morphogen solve, warm vs cold); turing (the
 Schnakenberg system on a static cellular domain of 1024^2, receptor confined
 to its cell); c2-junctions (the default tissue with cell junctions renewed
 every 10 steps); c2-growth (the default tissue growing under the area
-controller, pressure nodes along the walls); case2 (the mass-source growth study: a cell doubling its area
-under a uniform source at four refinements); case4 (the immersed-
+controller, pressure nodes along the walls); case1 / case2 (the mass-source
+growth studies: a cell grown by a point source / doubling its area under a
+uniform source, at four refinements); case4 (the immersed-
 boundary leakage study: area loss under constant membrane tension at four
 refinements and its order of convergence).
 
@@ -558,10 +559,10 @@ def run_case4(args, rank, world, dist):
     }
 
 
-def run_case2(args, rank, world, dist):
-    """Validation Case II: a circular cell grown by a uniform mass source
-    (per-node ln 2 / T) doubles its area by T; relative area error at four
-    lattice refinements and the observed order of convergence."""
+def run_growth_study(args, rank, world, dist, case: int):
+    """Validation Case I (point source at the cell centre, A(T) = A0 + q T)
+    or Case II (uniform per-node source ln 2 / T, A(T) = 2 A0): relative area
+    error at four lattice refinements and the observed order of convergence."""
     import math
     import torch
     from paper_1503_06726_gb300 import lbib
@@ -571,11 +572,14 @@ def run_case2(args, rank, world, dist):
     torch.cuda.set_device(dev)
     levels, nodes_steps, t_gpu = [], 0, 0.0
     for k in range(4):
-        w = li.case2(k)
+        w = li.case1(k) if case == 1 else li.case2(k)
         T = w.tissue
         sim = lbib.Simulation(w.params, lbib.LBIB_FP32, T.n_vertices, T.n_cells, device=dev)
         sim.set_cells(T)
-        sim.set_mass_sources(w.mass_rate)
+        if case == 1:
+            sim.set_node_sources(w.node_source)
+        else:
+            sim.set_mass_sources(w.mass_rate)
         sim.set_pressure_nodes(w.pressure_mask)
         a0 = float(sim.fields(lbib.LBIB_AREA)["area"][0])
         torch.cuda.synchronize()
@@ -587,26 +591,34 @@ def run_case2(args, rank, world, dist):
         sim.close()
         nodes_steps += w.params.nx * w.params.ny * w.n_steps
         t_gpu += dt
-        expect = math.exp(float(w.mass_rate[0]) * w.n_steps)
+        if case == 1:
+            q = float(w.node_source.sum())
+            expect = (a0 + q * w.n_steps) / a0
+        else:
+            q = float(w.mass_rate[0])
+            expect = math.exp(q * w.n_steps)
         levels.append({"lattice": w.params.nx, "diameter": 10 * 2 ** k, "vertices": T.n_vertices,
-                       "steps": w.n_steps, "source_lb": float(w.mass_rate[0]),
-                       "area_ratio": a1 / a0, "expected": expect,
-                       "area_err_rel": a1 / a0 / expect - 1.0, "seconds": dt})
+                       "steps": w.n_steps, "source_lb": q, "area_ratio": a1 / a0,
+                       "expected": expect, "area_err_rel": a1 / a0 / expect - 1.0,
+                       "seconds": dt})
     err = [abs(lv["area_err_rel"]) for lv in levels]
     orders = [math.log2(err[k] / err[k + 1]) for k in range(3)]
     if rank != 0:
         return None
+    what = ("point mass source" if case == 1 else "uniform mass source")
+    paper = ({"order": "about 1 (text); fitted slope -1.80 (figure)", "fitted_slope": -1.80}
+             if case == 1 else {"order": "about 1 (area, finer grids)", "fitted_slope": -0.99})
     return {
-        "metric": "mass-source growth: observed order of the relative area error (validation Case II)",
+        "metric": f"{what} growth: observed order of the relative area error "
+                  f"(validation Case {'I' if case == 1 else 'II'})",
         "value": orders[-1], "unit": "order (two finest lattices)", "n_gpus": world,
         "steps": sum(lv["steps"] for lv in levels), "warmup": 0,
         "ms_per_step": None, "higher_is_better": None, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (one circular cell, no random input)",
-        "config": {"workload": "case2_dia10-80_lattice100-800",
+        "config": {"workload": f"case{case}_dia10-80_lattice100-800",
                    "bc": "periodic with pressure nodes at rho0 on the seam (the study's outflow "
                          "boundary is out of scope)"},
-        "orders": orders, "levels": levels,
-        "paper": {"order": "about 1 (area, finer grids)", "fitted_slope": -0.99},
+        "orders": orders, "levels": levels, "paper": paper,
         "mlups": nodes_steps / t_gpu / 1e6,
     }
 
@@ -614,8 +626,8 @@ def run_case2(args, rank, world, dist):
 def run_gb300(args, rank, world, dist):
     if args.workload == "case4":
         return run_case4(args, rank, world, dist)
-    if args.workload == "case2":
-        return run_case2(args, rank, world, dist)
+    if args.workload in ("case1", "case2"):
+        return run_growth_study(args, rank, world, dist, int(args.workload[-1]))
     if args.workload == "c3-precision":
         return run_precision(args, rank, world, dist)
     if args.workload == "c4":

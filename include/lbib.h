@@ -138,7 +138,11 @@ extern "C" {
  *                pressure_rho / rho, so the node holds the prescribed
  *                density (pressure rho/3) and keeps its velocity; such
  *                nodes take up or give off mass (the sink of growing
- *                tissues).  pressure_rho > 0. */
+ *                tissues).  pressure_rho > 0.
+ *   node_sources 1 = a static mass source per node (the field S(x,t) of
+ *                Fig. 1; a point source is one node of it), set by
+ *                lbib_set_node_sources and added to the cells' sources in
+ *                the same way (w_q S after the collision). */
 typedef struct lbib_params {
     int32_t nx, ny, bc_y, n_species;
     double tau, rho0;
@@ -153,6 +157,7 @@ typedef struct lbib_params {
     int32_t junction_period, junction_pad;
     int32_t mass_sources, pressure_nodes;
     double mass_alpha, pressure_rho;
+    int32_t node_sources, node_pad;
 } lbib_params;
 
 typedef struct lbib_ctx lbib_ctx;
@@ -210,6 +215,13 @@ int lbib_set_mass_sources(lbib_ctx* ctx, const double* rate, const double* targe
  * is zero until set.  LBIB_E_STATE when the context was created with
  * pressure_nodes 0.  Synchronises the context stream. */
 int lbib_set_pressure_nodes(lbib_ctx* ctx, const uint8_t* mask);
+
+/* Set the static mass source per node (node_sources): S is a host array of
+ * nx*ny doubles, row-major in j (mass added per step; negative = sink), kept
+ * in the workspace in the lattice compute type.  NULL clears it.  LBIB_E_STATE
+ * when the context was created with node_sources 0.  Synchronises the
+ * context stream. */
+int lbib_set_node_sources(lbib_ctx* ctx, const double* S);
 
 /* Choose how many lattice nodes one thread of the lattice update handles.
  * 2 (the default) lets FP16 storage update two adjacent nodes per thread,

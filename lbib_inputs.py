@@ -70,6 +70,8 @@ class LatticeParams:
     # held at density pressure_rho
     pressure_nodes: int = 0
     pressure_rho: float = 1.0
+    # a static mass source per node (the field S(x,t) of Fig. 1): 1 = on
+    node_sources: int = 0
 
 
 @dataclasses.dataclass
@@ -363,6 +365,31 @@ def case4(level: int, max_length: float = 0.5) -> Workload:
     n_vert = int(math.ceil(math.pi * D / max_length))
     T = make_tissue([(N / 2.0, N / 2.0)], [D / 2.0], n_vert, 0.0, 0.0, [0])
     return Workload(f"case4_level{level}_{N}x{N}_dia{int(D)}", P, T, 10000 * 4 ** level, 0)
+
+
+def case1(level: int, max_length: float = 0.5) -> Workload:
+    """Validation Case I (Sec. 6.3): a circular cell grown by a constant point
+    mass source at its centre node, no membrane force, tau 1, no species.
+    Level k: domain 100*2^k, diameter 10*2^k lattice units, T = 1e4*4^k steps,
+    source 1e-2 per step (the study's table: S^LB = S^ND dt/dx^2 with
+    S^ND = 1), so that A(T) = A0 + 1e-2 T = A0 (1 + 4/pi).  Pressure nodes at
+    rho0 on the periodic seam take up the excess mass, in place of the
+    study's iso-pressure outflow boundary."""
+    N = 100 * 2 ** level
+    D = 10.0 * 2 ** level
+    steps = 10000 * 4 ** level
+    P = LatticeParams(nx=N, ny=N, bc_y=BC_PERIODIC, tau=1.0, rho0=1.0, n_species=0)
+    P.node_sources = 1
+    P.pressure_nodes, P.pressure_rho = 1, 1.0
+    n_vert = int(math.ceil(math.pi * D / max_length))
+    T = make_tissue([(N / 2.0, N / 2.0)], [D / 2.0], n_vert, 0.0, 0.0, [0])
+    w = Workload(f"case1_level{level}_{N}x{N}_dia{int(D)}", P, T, steps, 0)
+    w.node_source = np.zeros((N, N))
+    w.node_source[N // 2, N // 2] = 1e-2
+    w.pressure_mask = np.zeros((N, N), np.uint8)
+    w.pressure_mask[0, :] = 1
+    w.pressure_mask[:, 0] = 1
+    return w
 
 
 def case2(level: int, max_length: float = 0.5) -> Workload:

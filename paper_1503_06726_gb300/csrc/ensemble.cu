@@ -404,7 +404,8 @@ int lbib_ensemble_create(int32_t n, const lbib_params* params, const int32_t* ma
         if (params[t].junction_period > 0)
             return ens_fail(nullptr, LBIB_E_PARAM,
                             "ensemble tissues have no cell junctions (they need separate launches)");
-        if (params[t].noflux_mask || params[t].mass_sources || params[t].pressure_nodes)
+        if (params[t].noflux_mask || params[t].mass_sources || params[t].pressure_nodes ||
+            params[t].node_sources)
             return ens_fail(nullptr, LBIB_E_PARAM,
                             "ensemble tissues have no domain planes, mass sources or pressure nodes");
         if (params[t].n_species != params[0].n_species || params[t].forcing != params[0].forcing)

@@ -180,9 +180,10 @@ _Pragma("unroll") \
     /* the cell's mass source at labelled nodes; internal pressure nodes */ \
     C ms = C(0); \
     if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
+    if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
     const bool pn = a.pnode && a.pnode[node] != 0; \
     collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph, \
-                                        a.msrc != nullptr, ms, pn); \
+                                        a.msrc != nullptr || a.nsrc != nullptr, ms, pn); \
     T* G = static_cast<T*>(a.fdst); \
 _Pragma("unroll") \
     for (int q = 0; q < 9; ++q) St::st((G + q * P) + node, d[q]); \

@@ -70,6 +70,7 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
         l.msrc = take((uint64_t)max_cells * 8);
     }
     if (p.pressure_nodes) l.pnode = take(align_up(P, 8));
+    if (p.node_sources) l.nsrc = take(P * l.cs);
     if (p.junction_period > 0 && max_cells > 0) {
         // bins at least l_max wide (with a margin against rounding at their
         // edges); wider where they would outnumber the vertices by far
@@ -166,6 +167,9 @@ static int check_params(const lbib_params* p, std::string* why) {
         *why = "pressure_nodes must be 0 or 1 and pressure_rho finite and > 0";
         return LBIB_E_PARAM;
     }
+    if (p->node_sources != 0 && p->node_sources != 1) {
+        *why = "node_sources must be 0 or 1"; return LBIB_E_PARAM;
+    }
     return LBIB_OK;
 }
 
@@ -252,6 +256,7 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.smask = c->at<uint32_t>(L.smask);
     if (c->p.mass_sources && c->nC > 0) a.msrc = c->ws + L.msrc;
     if (c->p.pressure_nodes) a.pnode = c->at<uint8_t>(L.pnode);
+    if (c->p.node_sources) a.nsrc = c->ws + L.nsrc;
     return a;
 }
 
@@ -533,6 +538,8 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
             e = cudaMemsetAsync(c->ws + off, 0, (size_t)8 * max_cells, c->stream);
     if (e == cudaSuccess && params->pressure_nodes)
         e = cudaMemsetAsync(c->ws + L.pnode, 0, align_up(L.plane, 8), c->stream);
+    if (e == cudaSuccess && params->node_sources)
+        e = cudaMemsetAsync(c->ws + L.nsrc, 0, L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.diag, 0, kDiagWords * 4, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess && max_cells > 0)
@@ -677,6 +684,30 @@ int lbib_set_pressure_nodes(lbib_ctx* c, const uint8_t* mask) {
         e = cudaMemsetAsync(c->ws + L.pnode, 0, L.plane, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_pressure_nodes");
+    return LBIB_OK;
+}
+
+int lbib_set_node_sources(lbib_ctx* c, const double* S) {
+    if (!c) return LBIB_E_PARAM;
+    if (!c->p.node_sources) return fail(c, LBIB_E_STATE, "the context has no node sources");
+    const Layout& L = c->L;
+    const size_t nx = (size_t)c->p.nx, ny = (size_t)c->p.ny;
+    cudaError_t e = cudaSuccess;
+    if (!S) {
+        e = cudaMemsetAsync(c->ws + L.nsrc, 0, L.plane * L.cs, c->stream);
+    } else if (L.cs == 8) {
+        e = cudaMemcpy2DAsync(c->ws + L.nsrc, (size_t)L.pitch * 8, S, nx * 8, nx * 8, ny,
+                              cudaMemcpyHostToDevice, c->stream);
+    } else {
+        // FP32 / FP16 storage compute in FP32: convert on the host
+        std::vector<float> f(nx * ny);
+        for (size_t t = 0; t < f.size(); ++t) f[t] = (float)S[t];
+        e = cudaMemcpy2DAsync(c->ws + L.nsrc, (size_t)L.pitch * 4, f.data(), nx * 4, nx * 4, ny,
+                              cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // f is a host temporary
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_node_sources");
     return LBIB_OK;
 }
 

@@ -58,6 +58,7 @@ struct Layout {
     uint64_t jpartner = 0, jcell = 0, jcnt = 0, jstart = 0, jvbin = 0, jent = 0;
     uint64_t mrate = 0, marea = 0, msrc = 0;  // per-cell mass source data (mass_sources)
     uint64_t pnode = 0;        // internal pressure nodes, one byte per node (pressure_nodes)
+    uint64_t nsrc = 0;         // static mass source per node, compute type (node_sources)
     int jnbx = 0, jnby = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
@@ -118,6 +119,9 @@ struct LatticeArgs {
     // internal pressure nodes (Sec. 6.1): one byte per node (pitch layout),
     // nonzero = populations rescaled to the density prho; NULL = none
     const uint8_t* pnode;
+    // static mass source per node (compute type, pitch layout), added to the
+    // cell's; NULL = none
+    const void* nsrc;
 };
 
 struct IBArgs {

@@ -41,6 +41,7 @@ PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
 EXPORTS = (
     "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_lattice_variant",
     "lbib_set_domains", "lbib_set_mass_sources", "lbib_set_pressure_nodes",
+    "lbib_set_node_sources",
     "lbib_set_cell_params",
     "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
@@ -77,6 +78,7 @@ class lbib_params(ctypes.Structure):
         ("junction_pad", ctypes.c_int32),
         ("mass_sources", ctypes.c_int32), ("pressure_nodes", ctypes.c_int32),
         ("mass_alpha", ctypes.c_double), ("pressure_rho", ctypes.c_double),
+        ("node_sources", ctypes.c_int32), ("node_pad", ctypes.c_int32),
     ]
 
 
@@ -102,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_set_domains": (ctypes.c_int, [vp, vp]),
         "lbib_set_mass_sources": (ctypes.c_int, [vp, vp, vp]),
         "lbib_set_pressure_nodes": (ctypes.c_int, [vp, vp]),
+        "lbib_set_node_sources": (ctypes.c_int, [vp, vp]),
         "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
         "lbib_step": (ctypes.c_int, [vp, i32]),
         "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
@@ -203,6 +206,7 @@ def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
     o.mass_alpha = float(getattr(p, "mass_alpha", 0.0) or 0.0)
     o.pressure_nodes = int(getattr(p, "pressure_nodes", 0) or 0)
     o.pressure_rho = float(getattr(p, "pressure_rho", 0.0) or 0.0)
+    o.node_sources = int(getattr(p, "node_sources", 0) or 0)
     return o
 
 
@@ -249,6 +253,12 @@ def lbib_set_pressure_nodes(ctx, mask=None):
     """mask: (ny, nx) uint8, nonzero = pressure node, or None (none)."""
     m, m_p = _p(mask, np.uint8)
     _check(load().lbib_set_pressure_nodes(ctx, m_p), ctx)
+
+
+def lbib_set_node_sources(ctx, S=None):
+    """S: (ny, nx) float64 mass source per node, or None (none)."""
+    a, a_p = _p(S, np.float64)
+    _check(load().lbib_set_node_sources(ctx, a_p), ctx)
 
 
 def lbib_set_lattice_variant(ctx, nodes_per_thread: int):
@@ -464,6 +474,9 @@ class Simulation:
 
     def set_pressure_nodes(self, mask=None):
         lbib_set_pressure_nodes(self.ctx, mask)
+
+    def set_node_sources(self, S=None):
+        lbib_set_node_sources(self.ctx, S)
 
     def set_lattice_variant(self, nodes_per_thread: int):
         lbib_set_lattice_variant(self.ctx, nodes_per_thread)

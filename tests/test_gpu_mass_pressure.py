@@ -10,8 +10,10 @@ c30) against the FP64 oracle.
     FP64 within 1e-10 after 60 steps; FP32 within the FP32 bounds (u 1e-4,
     X 1e-6 lattice units); FP16 shifted storage within its bounds (u 3e-2,
     X 1e-3);
+  - a static per-node source field (random sources and sinks) on top of the
+    cells' sources: FP64 within 1e-10, FP32 within its bounds;
   - the set-up calls need contexts created with the feature; ensembles
-    refuse both features.
+    refuse the features.
 """
 import numpy as np
 import pytest
@@ -124,6 +126,33 @@ def test_area_controller_tissue_reduced(lb, orc, prec, tu, tx):
     assert eu < tu and ex < tx
 
 
+def _with_node_sources(case):
+    p, T, rate, target, pm = case
+    p.node_sources = 1
+    rng = np.random.default_rng(32)
+    ns = 1e-4 * rng.uniform(-1, 1, size=(p.ny, p.nx))
+    return p, T, rate, target, pm, ns
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_node_sources_vs_oracle(lb, orc, prec):
+    p, T, rate, target, pm, ns = _with_node_sources(_tissue())
+    ref = orc.run(p, T, 60, mass_rate=rate, target_area=target, pmask=pm, node_source=ns)
+    sim = lb.Simulation(p, lb.PRECISIONS[prec], T.n_vertices, T.n_cells)
+    sim.set_cells(T)
+    sim.set_mass_sources(rate, target)
+    sim.set_pressure_nodes(pm)
+    sim.set_node_sources(ns)
+    sim.step(60)
+    got = sim.fields(ALL)
+    sim.close()
+    if prec == "fp64":
+        _check_fp64(got, ref)
+    else:
+        assert max(rel(got["ux"], ref.ux), rel(got["uy"], ref.uy)) < 1e-4
+        assert np.abs(got["xy"] - ref.xy).max() < 1e-6
+
+
 def test_setup_calls_need_the_feature(lb):
     w = li.config2(nx=96, ny=80, n_cells_side=3)
     T = w.tissue
@@ -133,8 +162,10 @@ def test_setup_calls_need_the_feature(lb):
         sim.set_mass_sources(np.zeros(T.n_cells))
     with pytest.raises(lb.LbibError):
         sim.set_pressure_nodes(np.zeros((w.params.ny, w.params.nx), np.uint8))
+    with pytest.raises(lb.LbibError):
+        sim.set_node_sources(np.zeros((w.params.ny, w.params.nx)))
     sim.close()
-    for field in ("mass_sources", "pressure_nodes"):
+    for field in ("mass_sources", "pressure_nodes", "node_sources"):
         p = li.config2(nx=96, ny=80, n_cells_side=3).params
         setattr(p, field, 1)
         with pytest.raises(lb.LbibError):
