@@ -72,6 +72,11 @@ class LatticeParams:
     pressure_rho: float = 1.0
     # a static mass source per node (the field S(x,t) of Fig. 1): 1 = on
     node_sources: int = 0
+    # a mass source mass_beta * phi_s inside the cells (s = mass_species)
+    mass_beta: float = 0.0
+    mass_species: int = 0
+    # 1 = the confined species (noflux) follow the cells' labels of each step
+    noflux_dynamic: int = 0
 
 
 @dataclasses.dataclass
@@ -386,6 +391,36 @@ def case1(level: int, max_length: float = 0.5) -> Workload:
     w = Workload(f"case1_level{level}_{N}x{N}_dia{int(D)}", P, T, steps, 0)
     w.node_source = np.zeros((N, N))
     w.node_source[N // 2, N // 2] = 1e-2
+    w.pressure_mask = np.zeros((N, N), np.uint8)
+    w.pressure_mask[0, :] = 1
+    w.pressure_mask[:, 0] = 1
+    return w
+
+
+def case3(level: int, max_length: float = 0.5) -> Workload:
+    """Validation Case III (Sec. 6.3): a circular cell holding one species
+    (concentration 1 at the nodes strictly inside the circle, 0 elsewhere,
+    no production or decay) that the moving membrane confines, and a mass
+    source beta * C at every node inside the cell.  Level k: domain 100*2^k,
+    diameter 10*2^k lattice units, T = 1e4*4^k steps, tau = tau_D = 1 (the
+    study's table), beta = 1 / T (the study's strength 1 C in its time
+    unit), so that the area grows linearly, A(T) = A0 + beta M T with M the
+    conserved species mass.  Pressure nodes at rho0 on the periodic seam take
+    up the excess mass, in place of the study's outflow boundary."""
+    N = 100 * 2 ** level
+    D = 10.0 * 2 ** level
+    steps = 10000 * 4 ** level
+    P = LatticeParams(nx=N, ny=N, bc_y=BC_PERIODIC, tau=1.0, rho0=1.0, n_species=1)
+    P.D[0] = 1.0 / 6.0
+    P.noflux, P.noflux_dynamic = 1, 1
+    P.mass_beta, P.mass_species = 1.0 / steps, 0
+    P.pressure_nodes, P.pressure_rho = 1, 1.0
+    n_vert = int(math.ceil(math.pi * D / max_length))
+    T = make_tissue([(N / 2.0, N / 2.0)], [D / 2.0], n_vert, 0.0, 0.0, [0])
+    w = Workload(f"case3_level{level}_{N}x{N}_dia{int(D)}", P, T, steps, 0)
+    X, Y = np.meshgrid(np.arange(N, dtype=np.float64), np.arange(N, dtype=np.float64))
+    inside = np.hypot(X - N / 2.0, Y - N / 2.0) <= D / 2.0 - 0.1
+    w.phi0 = inside.astype(np.float64)[None]
     w.pressure_mask = np.zeros((N, N), np.uint8)
     w.pressure_mask[0, :] = 1
     w.pressure_mask[:, 0] = 1

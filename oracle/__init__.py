@@ -73,7 +73,8 @@ class OrcParams(ctypes.Structure):
                 ("junction_k", ctypes.c_double), ("junction_l0", ctypes.c_double),
                 ("junction_lmax", ctypes.c_double), ("junction_period", ctypes.c_int32),
                 ("pad2", ctypes.c_int32), ("mass_alpha", ctypes.c_double),
-                ("pressure_rho", ctypes.c_double)]
+                ("pressure_rho", ctypes.c_double), ("mass_beta", ctypes.c_double),
+                ("mass_species", ctypes.c_int32), ("noflux_dynamic", ctypes.c_int32)]
 
 
 def _P(p) -> OrcParams:
@@ -98,6 +99,9 @@ def _P(p) -> OrcParams:
     o.junction_period = int(getattr(p, "junction_period", 0))
     o.mass_alpha = float(getattr(p, "mass_alpha", 0.0))
     o.pressure_rho = float(getattr(p, "pressure_rho", 0.0))
+    o.mass_beta = float(getattr(p, "mass_beta", 0.0))
+    o.mass_species = int(getattr(p, "mass_species", 0))
+    o.noflux_dynamic = int(getattr(p, "noflux_dynamic", 0))
     return o
 
 
@@ -119,7 +123,7 @@ def lib():
             L.orc_rasterize.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
             L.orc_spread.argtypes = [i, i, i, i, vp, vp, vp, vp]
             L.orc_interp.argtypes = [i, i, i, i, vp, vp, vp, vp]
-            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 14
+            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 15
             L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 7
             L.orc_run.restype = i
             L.orc_run.argtypes = ([ctypes.POINTER(OrcParams), i, vp, vp, vp, vp, vp, d, vp, i]
@@ -237,11 +241,13 @@ def _opt(a, dt):
     return None if a is None else np.ascontiguousarray(a, dt)
 
 
-def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None, msrc=None, pmask=None):
+def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None, msrc=None, pmask=None,
+                 lab=None):
     """One stream+collide update.  Returns (f_out, g_out, rho, ux, uy, phi).
     dom: static domain labels (ny, nx) for the species confined by p.noflux;
     msrc: mass source per node (ny, nx); pmask: internal pressure nodes
-    (ny, nx), prescribed density p.pressure_rho."""
+    (ny, nx), prescribed density p.pressure_rho; lab: cell labels (ny, nx),
+    > 0 inside a cell, for the source p.mass_beta phi_s."""
     P = _P(p)
     f = _f64(f)
     g = _f64(g) if p.n_species else np.zeros(1)
@@ -256,7 +262,8 @@ def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None, msrc=None, pmask
                            _ptr(None if fy is None else _f64(fy)),
                            _ptr(None if src is None else np.ascontiguousarray(src, np.uint8)),
                            _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi), _ptr(_dom(dom)),
-                           _ptr(_opt(msrc, np.float64)), _ptr(_opt(pmask, np.uint8)))
+                           _ptr(_opt(msrc, np.float64)), _ptr(_opt(pmask, np.uint8)),
+                           _ptr(_opt(lab, np.int32)))
     return fo, go, rho, ux, uy, phi[: p.n_species]
 
 

@@ -41,6 +41,9 @@ typedef struct {
     int32_t pad2;
     double mass_alpha;         /* gain of the cell area controller (Sec. 3.2.3) */
     double pressure_rho;       /* density prescribed at internal pressure nodes */
+    double mass_beta;          /* mass source beta phi_s inside cells (reading c32) */
+    int32_t mass_species;      /* the species s of that source */
+    int32_t noflux_dynamic;    /* confined species follow the cells' labels of each step */
 } orc_params;
 
 /* D2Q9 velocities: v0 = 0; v1..v4 = (cos, sin)(pi(i-1)/2); v5..v8 the diagonals
@@ -391,14 +394,17 @@ static double reaction(const orc_params* P, int s, const double* phi, int S, uin
  * the prescribed density and keeps its velocity (gamma cancels in u).
  * Mass sources (Sec. 3.2.3; reading c29): msrc[x] is added to the node's
  * mass after the collision, spread over the directions by the weights,
- * f*_q += w_q msrc[x], which adds no momentum.
+ * f*_q += w_q msrc[x], which adds no momentum.  With lab (cell labels, > 0
+ * inside a cell) the source of a node inside a cell gains mass_beta phi_s
+ * (s = mass_species; reading c32: the concentration-proportional source of
+ * the validation Case III, on the pre-collision phi of the node).
  * fpost_*: 9 planes of N; gpost_*: S*5 planes; fx, fy may be NULL (no force);
- * rho, ux, uy, phi (S planes) may be NULL; msrc, pmask may be NULL (none). */
+ * rho, ux, uy, phi (S planes) may be NULL; msrc, pmask, lab may be NULL. */
 void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost_out,
                       const double* gpost_in, double* gpost_out, const double* fx,
                       const double* fy, const uint8_t* src, double* rho_out, double* ux_out,
                       double* uy_out, double* phi_out, const int32_t* dom, const double* msrc,
-                      const uint8_t* pmask) {
+                      const uint8_t* pmask, const int32_t* lab) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     double tau = P->tau;
@@ -409,6 +415,21 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
             long idx = (long)j * nx + i;
             double f[9];
             for (int q = 0; q < 9; ++q) f[q] = pull(fpost_in, OPP, q, i, j, nx, ny, P->bc_y);
+            /* the species' pulled populations and concentrations (needed by
+             * the concentration-proportional mass source) */
+            double g[4][5], phi[4];
+            for (int s = 0; s < S; ++s) {
+                phi[s] = 0.0;
+                for (int q = 0; q < 5; ++q) {
+                    g[s][q] = pull_species(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny,
+                                           P->bc_y, dom, (P->noflux >> s) & 1);
+                    phi[s] += g[s][q];
+                }
+            }
+            const int beta_on = lab && lab[idx] > 0 && P->mass_beta != 0.0 &&
+                                P->mass_species >= 0 && P->mass_species < S;
+            double Sm = msrc ? msrc[idx] : 0.0;
+            if (beta_on) Sm += P->mass_beta * phi[P->mass_species];
             double rho = 0.0, jx = 0.0, jy = 0.0;
             if (pmask && pmask[idx]) {
                 for (int q = 0; q < 9; ++q) rho += f[q];
@@ -441,22 +462,13 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
                           9.0 * vu * (CX[q] * Fx + CY[q] * Fy));
                 else
                     Sq = 3.0 * W9(q) * (CX[q] * Fx + CY[q] * Fy);
-                if (msrc) Sq += W9(q) * msrc[idx];
+                if (msrc || beta_on) Sq += W9(q) * Sm;
                 fpost_out[(long)q * N + idx] = f[q] - (f[q] - feq) / tau + Sq;
             }
             if (rho_out) rho_out[idx] = rho;
             if (ux_out) ux_out[idx] = ux;
             if (uy_out) uy_out[idx] = uy;
 
-            double g[4][5], phi[4];
-            for (int s = 0; s < S; ++s) {
-                phi[s] = 0.0;
-                for (int q = 0; q < 5; ++q) {
-                    g[s][q] = pull_species(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny,
-                                           P->bc_y, dom, (P->noflux >> s) & 1);
-                    phi[s] += g[s][q];
-                }
-            }
             for (int s = 0; s < S; ++s) {
                 double R = reaction(P, s, phi, S, src ? src[idx] : 0);
                 double tauD = 3.0 * P->D[s] + 0.5;
@@ -526,7 +538,11 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
  * every node labelled with cell c receives
  *   S_c = mrate[c] + mass_alpha (marea[c] - A_c(X^n))
  * (the proportional area controller; without marea S_c = mrate[c]), A_c the
- * polygon area of Sec. 3.3 at the start of the step.  nsrc: a static mass
+ * polygon area of Sec. 3.3 at the start of the step; with mass_beta != 0 a
+ * node inside a cell also gains mass_beta phi_s (reading c32).  With
+ * noflux_dynamic the confined species are bounded by the cells' labels of
+ * each step (id: 0 outside, c+1 inside) instead of dom (reading c31: the
+ * membranes move).  nsrc: a static mass
  * source per node (the field S(x,t) of Fig. 1; NULL = none), added to the
  * cells' sources (a point source is one node of it).  pmask: internal
  * pressure nodes (NULL = none; see orc_lattice_step). */
@@ -582,7 +598,8 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
         if (nsrc)
             for (long t = 0; t < N; ++t) Sn[t] += nsrc[t];
         orc_lattice_step(P, fa, fb, ga, gb, Fx, Fy, lsrc, last ? rho : NULL, Ux, Uy,
-                         last ? phi : NULL, dom, Sn, pmask);
+                         last ? phi : NULL, P->noflux_dynamic ? lid : dom, Sn, pmask,
+                         P->mass_beta != 0.0 ? lid : NULL);
         if (V > 0) {
             orc_interp(nx, ny, P->bc_y, V, xy, Ux, Uy, U);
             if (last && Fv) memcpy(Fv, F, sizeof(double) * 2 * V);
