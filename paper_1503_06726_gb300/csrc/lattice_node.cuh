@@ -84,10 +84,13 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
 // kernel parameters (a separate inlined function measured 17% slower there,
 // with identical memory traffic); the ensemble's device function expands the
 // same text.  It uses the names a (LatticeArgs), k (Coefs<C>), x, y, the
-// template parameters T, C, S, WALLS, FORCING, SCALED and a constexpr bool
-// GRIDDEP: with it the population loads (written by the lattice launch two
-// launches back, read through L2) are issued before the programmatic wait on
-// the IB kernel whose force, label and mask planes the rest reads.
+// template parameters T, C, S, WALLS, FORCING, SCALED and two constexpr
+// bools: GRIDDEP, with which the population loads (written by the lattice
+// launch two launches back, read through L2) are issued before the
+// programmatic wait on the IB kernel whose force, label and mask planes the
+// rest reads; EXTRAS, without which the per-context options (domain planes,
+// mass sources, pressure nodes, alternating label planes) are compiled out
+// (the ensemble has none of them and keeps its registers).
 #define LBIB_LATTICE_NODE_BODY \
  \
     using St = Store<T, C>; \
@@ -130,7 +133,7 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
         const T* Gi = static_cast<const T*>(a.gsrc); \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
-            if (a.dom && ((a.noflux >> s) & 1)) \
+            if (EXTRAS && a.dom && ((a.noflux >> s) & 1)) \
                 pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
                                             x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
             else \
@@ -179,11 +182,22 @@ _Pragma("unroll") \
     C ph[S > 0 ? S : 1]; \
     /* the cell's mass source at labelled nodes; internal pressure nodes */ \
     C ms = C(0); \
-    if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
-    if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
-    const bool pn = a.pnode && a.pnode[node] != 0; \
+    bool pn = false, mass_on = false; \
+    if (EXTRAS) { \
+        if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
+        if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
+        /* inside a cell: beta phi_s, the concentration-proportional source */ \
+        if (S > 0 && k.mbeta != C(0) && label != kOutside) { \
+_Pragma("unroll") \
+            for (int s = 0; s < S; ++s) \
+                if (s == k.mspecies) \
+                    ms = Lane<C>::fma(k.mbeta, species_moment<C, SCALED>(k, g[s]), ms); \
+        } \
+        pn = a.pnode && a.pnode[node] != 0; \
+        mass_on = a.msrc != nullptr || a.nsrc != nullptr || k.mbeta != C(0); \
+    } \
     collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph, \
-                                        a.msrc != nullptr || a.nsrc != nullptr, ms, pn); \
+                                        mass_on, ms, pn); \
     T* G = static_cast<T*>(a.fdst); \
 _Pragma("unroll") \
     for (int q = 0; q < 9; ++q) St::st((G + q * P) + node, d[q]); \
@@ -214,7 +228,10 @@ _Pragma("unroll") \
             z.y = C(0); \
             st_keep(static_cast<V2*>(a.force) + node, z); \
         } \
-        if (lhit) a.id[node] = kOutside; \
+        /* labels: read then cleared, or (moving confinement) kept for the */ \
+        /* neighbours' reads while the other label plane is cleared whole */ \
+        if (lhit && !(EXTRAS && a.id_clear)) a.id[node] = kOutside; \
+        if (EXTRAS && a.id_clear) a.id_clear[node] = kOutside; \
         if (shit) a.src[node] = 0; \
         if (a.out) { \
             a.id_out[node] = label; \
@@ -299,6 +316,17 @@ struct Lane<double> {
 // stored values and 1/sigma replaces w.  d and g enter as the pulled stored
 // values and leave as the post-collision stored values; bitsA / bitsB are the
 // source bits of the node(s).
+// concentration of one species from its pulled populations (scaled storage:
+// deviations in units of w sigma_g)
+template <typename V, bool SCALED>
+__device__ __forceinline__ V species_moment(const Coefs<typename Lane<V>::S>& k, const V (&g)[5]) {
+    using L = Lane<V>;
+    if (SCALED)
+        return L::fma(L::c(k.gscale[0]), g[0],
+                      L::mul(L::c(k.gscale[1]), L::add(L::add(g[1], g[2]), L::add(g[3], g[4]))));
+    return L::add(L::add(L::add(g[0], g[1]), L::add(g[2], g[3])), g[4]);
+}
+
 template <typename V, int S, int FORCING, bool SCALED>
 __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k, V (&d)[9],
                                              V (&g)[S > 0 ? S : 1][5], V fvx, V fvy,
@@ -385,15 +413,7 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
     }
     if (S > 0) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
-            if (SCALED)
-                ph[s] = L::fma(L::c(k.gscale[0]), g[s][0],
-                               L::mul(L::c(k.gscale[1]),
-                                      L::add(L::add(g[s][1], g[s][2]), L::add(g[s][3], g[s][4]))));
-            else
-                ph[s] = L::add(L::add(L::add(g[s][0], g[s][1]), L::add(g[s][2], g[s][3])),
-                               g[s][4]);
-        }
+        for (int s = 0; s < S; ++s) ph[s] = species_moment<V, SCALED>(k, g[s]);
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             V R = L::sel((bitsA >> s) & 1u, (bitsB >> s) & 1u, k.srate[s]);
@@ -428,6 +448,7 @@ template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
                                              int y) {
     constexpr bool GRIDDEP = false;
+    constexpr bool EXTRAS = false;  // the ensemble's tissues have none of the options
     LBIB_LATTICE_NODE_BODY
 }
 
