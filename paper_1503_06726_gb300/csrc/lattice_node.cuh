@@ -129,16 +129,19 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
         d[8] = St::ld((F + 8 * P) + (rp + xm), pol); \
     } \
     C g[S > 0 ? S : 1][5]; \
-    { \
-        const T* Gi = static_cast<const T*>(a.gsrc); \
+    const T* Gi = static_cast<const T*>(a.gsrc); \
+    /* moving membranes: the domain plane is this step's labels, which the */ \
+    /* IB prep is still writing: those species are pulled after the wait */ \
+    const bool dyn_dom = EXTRAS && a.id_clear != nullptr; \
 _Pragma("unroll") \
-        for (int s = 0; s < S; ++s) { \
-            if (EXTRAS && a.dom && ((a.noflux >> s) & 1)) \
+    for (int s = 0; s < S; ++s) { \
+        if (EXTRAS && a.dom && ((a.noflux >> s) & 1)) { \
+            if (!dyn_dom) \
                 pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
                                             x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
-            else \
-                pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, \
-                                   lo_wall, hi_wall, pol, g[s]); \
+        } else { \
+            pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, \
+                               lo_wall, hi_wall, pol, g[s]); \
         } \
     } \
     /* the IB kernel launched just before wrote the force, label and mask */ \
@@ -146,6 +149,13 @@ _Pragma("unroll") \
     if (GRIDDEP) { \
         griddep_wait(); \
         griddep_launch_dependents(); \
+    } \
+    if (dyn_dom) { \
+_Pragma("unroll") \
+        for (int s = 0; s < S; ++s) \
+            if ((a.noflux >> s) & 1) \
+                pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
+                                            x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
     } \
     /* spread force, labels and source bits: only the 4-node groups the IB */ \
     /* kernel marked (labels are written only before an output step) */ \
