@@ -27,10 +27,9 @@ start of the steady morphogen solve, warm vs cold); turing (the
 Schnakenberg system on a static cellular domain of 1024^2, receptor confined
 to its cell); c2-junctions (the default tissue with cell junctions renewed
 every 10 steps); c2-growth (the default tissue growing under the area
-controller, pressure nodes along the walls); case1 / case2 / case3 (the
-mass-source growth studies at four refinements: a cell grown by a point
-source, doubling its area under a uniform source, or growing in proportion
-to a species its moving membrane confines); case4 (the immersed-
+controller, pressure nodes along the walls); case1 / case2 (the mass-source
+growth studies: a cell grown by a point source / doubling its area under a
+uniform source, at four refinements); case4 (the immersed-
 boundary leakage study: area loss under constant membrane tension at four
 refinements and its order of convergence).
 
@@ -561,11 +560,9 @@ def run_case4(args, rank, world, dist):
 
 
 def run_growth_study(args, rank, world, dist, case: int):
-    """Validation Case I (point source at the cell centre, A(T) = A0 + q T),
-    Case II (uniform per-node source ln 2 / T, A(T) = 2 A0) or Case III
-    (source beta C inside the cell, species confined by the moving membrane,
-    A(T) = A0 + beta M T): relative area error at four lattice refinements
-    and the observed order of convergence."""
+    """Validation Case I (point source at the cell centre, A(T) = A0 + q T)
+    or Case II (uniform per-node source ln 2 / T, A(T) = 2 A0): relative area
+    error at four lattice refinements and the observed order of convergence."""
     import math
     import torch
     from paper_1503_06726_gb300 import lbib
@@ -575,16 +572,14 @@ def run_growth_study(args, rank, world, dist, case: int):
     torch.cuda.set_device(dev)
     levels, nodes_steps, t_gpu = [], 0, 0.0
     for k in range(4):
-        w = li.case1(k) if case == 1 else (li.case2(k) if case == 2 else li.case3(k))
+        w = li.case1(k) if case == 1 else li.case2(k)
         T = w.tissue
         sim = lbib.Simulation(w.params, lbib.LBIB_FP32, T.n_vertices, T.n_cells, device=dev)
         sim.set_cells(T)
         if case == 1:
             sim.set_node_sources(w.node_source)
-        elif case == 2:
-            sim.set_mass_sources(w.mass_rate)
         else:
-            sim.set_species(0, w.phi0[0])
+            sim.set_mass_sources(w.mass_rate)
         sim.set_pressure_nodes(w.pressure_mask)
         a0 = float(sim.fields(lbib.LBIB_AREA)["area"][0])
         torch.cuda.synchronize()
@@ -599,12 +594,9 @@ def run_growth_study(args, rank, world, dist, case: int):
         if case == 1:
             q = float(w.node_source.sum())
             expect = (a0 + q * w.n_steps) / a0
-        elif case == 2:
+        else:
             q = float(w.mass_rate[0])
             expect = math.exp(q * w.n_steps)
-        else:
-            q = float(w.params.mass_beta)
-            expect = (a0 + q * float(w.phi0.sum()) * w.n_steps) / a0
         levels.append({"lattice": w.params.nx, "diameter": 10 * 2 ** k, "vertices": T.n_vertices,
                        "steps": w.n_steps, "source_lb": q, "area_ratio": a1 / a0,
                        "expected": expect, "area_err_rel": a1 / a0 / expect - 1.0,
@@ -613,14 +605,12 @@ def run_growth_study(args, rank, world, dist, case: int):
     orders = [math.log2(err[k] / err[k + 1]) for k in range(3)]
     if rank != 0:
         return None
-    what = {1: "point mass source", 2: "uniform mass source",
-            3: "concentration-proportional mass source"}[case]
-    paper = {1: {"order": "about 1 (text); fitted slope -1.80 (figure)", "fitted_slope": -1.80},
-             2: {"order": "about 1 (area, finer grids)", "fitted_slope": -0.99},
-             3: {"order": "about 1 (area, finer grids)", "fitted_slope": -1.01}}[case]
+    what = ("point mass source" if case == 1 else "uniform mass source")
+    paper = ({"order": "about 1 (text); fitted slope -1.80 (figure)", "fitted_slope": -1.80}
+             if case == 1 else {"order": "about 1 (area, finer grids)", "fitted_slope": -0.99})
     return {
         "metric": f"{what} growth: observed order of the relative area error "
-                  f"(validation Case {'I' * case})",
+                  f"(validation Case {'I' if case == 1 else 'II'})",
         "value": orders[-1], "unit": "order (two finest lattices)", "n_gpus": world,
         "steps": sum(lv["steps"] for lv in levels), "warmup": 0,
         "ms_per_step": None, "higher_is_better": None, "scaling": "weak", "vs_baseline": None,
@@ -636,7 +626,7 @@ def run_growth_study(args, rank, world, dist, case: int):
 def run_gb300(args, rank, world, dist):
     if args.workload == "case4":
         return run_case4(args, rank, world, dist)
-    if args.workload in ("case1", "case2", "case3"):
+    if args.workload in ("case1", "case2"):
         return run_growth_study(args, rank, world, dist, int(args.workload[-1]))
     if args.workload == "c3-precision":
         return run_precision(args, rank, world, dist)

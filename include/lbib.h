@@ -142,20 +142,7 @@ extern "C" {
  *   node_sources 1 = a static mass source per node (the field S(x,t) of
  *                Fig. 1; a point source is one node of it), set by
  *                lbib_set_node_sources and added to the cells' sources in
- *                the same way (w_q S after the collision).
- *   mass_beta, mass_species
- *                a mass source mass_beta phi_s (s = mass_species, the
- *                pre-collision concentration of the node) at every node
- *                inside a cell, added to the other sources (the
- *                concentration-proportional source of validation Case III);
- *                0 = none.  The cells are labelled every step.
- *   noflux_dynamic
- *                1 = the confined species (noflux_mask) are bounded by the
- *                cells' labels of each step instead of a static domain plane
- *                (the membranes move; lbib_set_domains is refused): a link
- *                between nodes of different cells, or between a cell and the
- *                outside, reflects them.  Two label planes alternate with
- *                the population buffers. */
+ *                the same way (w_q S after the collision). */
 typedef struct lbib_params {
     int32_t nx, ny, bc_y, n_species;
     double tau, rho0;
@@ -171,8 +158,6 @@ typedef struct lbib_params {
     int32_t mass_sources, pressure_nodes;
     double mass_alpha, pressure_rho;
     int32_t node_sources, node_pad;
-    double mass_beta;
-    int32_t mass_species, noflux_dynamic;
 } lbib_params;
 
 typedef struct lbib_ctx lbib_ctx;
@@ -205,8 +190,7 @@ int lbib_set_cells(lbib_ctx* ctx, int32_t n_cells, const int32_t* cell_off, cons
                    const double* rest_len, const double* k_spring, const double* pressure,
                    const uint8_t* src_flag);
 
-/* Set the static domains of the confined species (noflux_mask, with
- * noflux_dynamic 0): labels is a
+/* Set the static domains of the confined species (noflux_mask): labels is a
  * host array of nx*ny int32, row-major in j, one label per node (any values;
  * neighbouring nodes with different labels are separated by a membrane; the
  * paper's static cellular domain is the cell index inside cells and one

@@ -157,9 +157,9 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
             a.write_vforce = vforce;
             a.do_ids = vforce;  // the prep of the output step writes the labels too
             if (e.cell_threads == 64)
-                ib_cell_f32<64, false, false, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
+                ib_cell_f32<64, false, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
             else
-                ib_cell_f32<128, false, false, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
+                ib_cell_f32<128, false, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
         }
     };
 
@@ -405,7 +405,7 @@ int lbib_ensemble_create(int32_t n, const lbib_params* params, const int32_t* ma
             return ens_fail(nullptr, LBIB_E_PARAM,
                             "ensemble tissues have no cell junctions (they need separate launches)");
         if (params[t].noflux_mask || params[t].mass_sources || params[t].pressure_nodes ||
-            params[t].node_sources || params[t].mass_beta != 0.0)
+            params[t].node_sources)
             return ens_fail(nullptr, LBIB_E_PARAM,
                             "ensemble tissues have no domain planes, mass sources or pressure nodes");
         if (params[t].n_species != params[0].n_species || params[t].forcing != params[0].forcing)

@@ -218,9 +218,8 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
 }
 
 
-// FP32 path: dynamic shared memory sized for the largest cell, NT threads;
-// EXTRAS: the junction forces and mass sources are compiled in
-template <int NT, bool EXTRAS>
+// FP32 path: dynamic shared memory sized for the largest cell, NT threads
+template <int NT>
 __global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
     extern __shared__ __align__(16) unsigned char ib_smem[];
     IBShared32 S;
@@ -233,18 +232,7 @@ __global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
     S.sb = reinterpret_cast<int2*>(S.sx + maxv);
     S.sf = reinterpret_cast<float2*>(S.sb + maxv);
     S.maxv = maxv;
-    ib_cell_f32<NT, true, NT == 256, EXTRAS>(a, blockIdx.x, S, threadIdx.x, 0);
-}
-
-// the options in their own instantiation, so that the plain step keeps the
-// registers of the code without them
-template <int NT>
-static cudaError_t launch_f32(const IBArgs& a, size_t smem, int maxv, cudaStream_t s, bool pdl) {
-    if (a.jpartner || a.msrc_out)
-        return launch_kernel(ib_cell_kernel_f32<NT, true>, dim3(a.n_cells), dim3(NT), smem, s, pdl,
-                             a, maxv);
-    return launch_kernel(ib_cell_kernel_f32<NT, false>, dim3(a.n_cells), dim3(NT), smem, s, pdl,
-                         a, maxv);
+    ib_cell_f32<NT, true, NT == 256>(a, blockIdx.x, S, threadIdx.x, 0);
 }
 
 cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s, bool pdl) {
@@ -257,9 +245,14 @@ cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_
     int maxv = maxv_cell < 3 ? 3 : (maxv_cell > kMaxVertsPerCell ? kMaxVertsPerCell : maxv_cell);
     maxv = (maxv + 7) / 8 * 8;
     const size_t smem = kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
-    if (maxv <= 64 && a.n_cells >= 2048) return launch_f32<64>(a, smem, maxv, s, pdl);
-    if (maxv <= 128 && a.n_cells >= 2048) return launch_f32<128>(a, smem, maxv, s, pdl);
-    return launch_f32<256>(a, smem, maxv, s, pdl);
+    if (maxv <= 64 && a.n_cells >= 2048)
+        return launch_kernel(ib_cell_kernel_f32<64>, dim3(a.n_cells), dim3(64), smem, s, pdl, a,
+                             maxv);
+    if (maxv <= 128 && a.n_cells >= 2048)
+        return launch_kernel(ib_cell_kernel_f32<128>, dim3(a.n_cells), dim3(128), smem, s, pdl, a,
+                             maxv);
+    return launch_kernel(ib_cell_kernel_f32<256>, dim3(a.n_cells), dim3(256), smem, s, pdl, a,
+                         maxv);
 }
 
 // Per-cell shoelace area relative to the first vertex, FP64 (computeAreas).

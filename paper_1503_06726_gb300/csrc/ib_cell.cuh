@@ -458,9 +458,7 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 // parameter reads through a pointer; 1024^2 step 40.9 -> 38.4 us) or called
 // out of line (the small-CTA kernels keep 64 registers, 16 CTAs per SM, and
 // the ensemble's persistent kernel its budget)
-// EXTRAS = false compiles out the per-context options the ensemble does not
-// have (junction forces, mass sources)
-template <int NT, bool GRIDDEP, bool INLINE_FILL = true, bool EXTRAS = true>
+template <int NT, bool GRIDDEP, bool INLINE_FILL = true>
 static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, int tid,
                                    int bar) {
     static_assert(NT % 64 == 0, "CTA size");
@@ -628,7 +626,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
         if (!finite) s_flag = 2;
     }
     cell_sync<NT>(bar);
-    if (EXTRAS && a.msrc_out && tid < 32) {
+    if (a.msrc_out && tid < 32) {
         // mass source of the cell (Sec. 3.2.3): S_c = rate + alpha (A0 - A_c),
         // A_c the shoelace area of the moved polygon about its first vertex
         const double a_c = cell_area_warp(sx, n, lane);
@@ -680,7 +678,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                     Fx += ten * (dn.x / ln - dp.x / lp);
                     Fy += ten * (dn.y / ln - dp.y / lp);
                 }
-                if (EXTRAS && a.jpartner) {  // Eq. celljunctionforce (a launch without the move)
+                if (a.jpartner) {  // Eq. celljunctionforce (a launch without the move)
                     const float2 J = junction_force32(a, sx[t], a.jpartner[v0 + t]);
                     Fx += J.x;
                     Fy += J.y;

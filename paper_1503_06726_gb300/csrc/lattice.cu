@@ -45,7 +45,6 @@ __global__ void __launch_bounds__(kLatticeThreads, LatticeOccupancy<T, S>::kMinB
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
     constexpr bool GRIDDEP = true;
-    constexpr bool EXTRAS = true;
     LBIB_LATTICE_NODE_BODY
 }
 
@@ -303,8 +302,7 @@ static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, 
         // two nodes per thread when the rows hold whole pairs
         // (confined species read their neighbours' domains, mass sources and
         // pressure nodes are per node: one node per thread)
-        const bool per_node = a.dom || a.msrc || a.pnode || a.nsrc || k.mbeta != 0.f;
-        if (pairs && !per_node && a.nx % 2 == 0 && a.pitch % 64 == 0 && a.plane % 2 == 0) {
+        if (pairs && !a.dom && !a.msrc && !a.pnode && !a.nsrc && a.nx % 2 == 0 && a.pitch % 64 == 0 && a.plane % 2 == 0) {
             const dim3 pb(kLatticeThreads, 1, 1);
             const dim3 pg((a.nx / 2 + kLatticeThreads - 1) / kLatticeThreads, a.ny);
             return launch_kernel(lattice_pair_kernel<S, WALLS, FORCING>, pg, pb, 0, s, pdl, a,

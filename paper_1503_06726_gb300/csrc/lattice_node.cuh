@@ -84,13 +84,10 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
 // kernel parameters (a separate inlined function measured 17% slower there,
 // with identical memory traffic); the ensemble's device function expands the
 // same text.  It uses the names a (LatticeArgs), k (Coefs<C>), x, y, the
-// template parameters T, C, S, WALLS, FORCING, SCALED and two constexpr
-// bools: GRIDDEP, with which the population loads (written by the lattice
-// launch two launches back, read through L2) are issued before the
-// programmatic wait on the IB kernel whose force, label and mask planes the
-// rest reads; EXTRAS, without which the per-context options (domain planes,
-// mass sources, pressure nodes, alternating label planes) are compiled out
-// (the ensemble has none of them and keeps its registers).
+// template parameters T, C, S, WALLS, FORCING, SCALED and a constexpr bool
+// GRIDDEP: with it the population loads (written by the lattice launch two
+// launches back, read through L2) are issued before the programmatic wait on
+// the IB kernel whose force, label and mask planes the rest reads.
 #define LBIB_LATTICE_NODE_BODY \
  \
     using St = Store<T, C>; \
@@ -129,19 +126,16 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
         d[8] = St::ld((F + 8 * P) + (rp + xm), pol); \
     } \
     C g[S > 0 ? S : 1][5]; \
-    const T* Gi = static_cast<const T*>(a.gsrc); \
-    /* moving membranes: the domain plane is this step's labels, which the */ \
-    /* IB prep is still writing: those species are pulled after the wait */ \
-    const bool dyn_dom = EXTRAS && a.id_clear != nullptr; \
+    { \
+        const T* Gi = static_cast<const T*>(a.gsrc); \
 _Pragma("unroll") \
-    for (int s = 0; s < S; ++s) { \
-        if (EXTRAS && a.dom && ((a.noflux >> s) & 1)) { \
-            if (!dyn_dom) \
+        for (int s = 0; s < S; ++s) { \
+            if (a.dom && ((a.noflux >> s) & 1)) \
                 pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
                                             x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
-        } else { \
-            pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, \
-                               lo_wall, hi_wall, pol, g[s]); \
+            else \
+                pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, \
+                                   lo_wall, hi_wall, pol, g[s]); \
         } \
     } \
     /* the IB kernel launched just before wrote the force, label and mask */ \
@@ -149,13 +143,6 @@ _Pragma("unroll") \
     if (GRIDDEP) { \
         griddep_wait(); \
         griddep_launch_dependents(); \
-    } \
-    if (dyn_dom) { \
-_Pragma("unroll") \
-        for (int s = 0; s < S; ++s) \
-            if ((a.noflux >> s) & 1) \
-                pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
-                                            x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
     } \
     /* spread force, labels and source bits: only the 4-node groups the IB */ \
     /* kernel marked (labels are written only before an output step) */ \
@@ -192,22 +179,11 @@ _Pragma("unroll") \
     C ph[S > 0 ? S : 1]; \
     /* the cell's mass source at labelled nodes; internal pressure nodes */ \
     C ms = C(0); \
-    bool pn = false, mass_on = false; \
-    if (EXTRAS) { \
-        if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
-        if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
-        /* inside a cell: beta phi_s, the concentration-proportional source */ \
-        if (S > 0 && k.mbeta != C(0) && label != kOutside) { \
-_Pragma("unroll") \
-            for (int s = 0; s < S; ++s) \
-                if (s == k.mspecies) \
-                    ms = Lane<C>::fma(k.mbeta, species_moment<C, SCALED>(k, g[s]), ms); \
-        } \
-        pn = a.pnode && a.pnode[node] != 0; \
-        mass_on = a.msrc != nullptr || a.nsrc != nullptr || k.mbeta != C(0); \
-    } \
+    if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
+    if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
+    const bool pn = a.pnode && a.pnode[node] != 0; \
     collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph, \
-                                        mass_on, ms, pn); \
+                                        a.msrc != nullptr || a.nsrc != nullptr, ms, pn); \
     T* G = static_cast<T*>(a.fdst); \
 _Pragma("unroll") \
     for (int q = 0; q < 9; ++q) St::st((G + q * P) + node, d[q]); \
@@ -238,10 +214,7 @@ _Pragma("unroll") \
             z.y = C(0); \
             st_keep(static_cast<V2*>(a.force) + node, z); \
         } \
-        /* labels: read then cleared, or (moving confinement) kept for the */ \
-        /* neighbours' reads while the other label plane is cleared whole */ \
-        if (lhit && !(EXTRAS && a.id_clear)) a.id[node] = kOutside; \
-        if (EXTRAS && a.id_clear) a.id_clear[node] = kOutside; \
+        if (lhit) a.id[node] = kOutside; \
         if (shit) a.src[node] = 0; \
         if (a.out) { \
             a.id_out[node] = label; \
@@ -326,17 +299,6 @@ struct Lane<double> {
 // stored values and 1/sigma replaces w.  d and g enter as the pulled stored
 // values and leave as the post-collision stored values; bitsA / bitsB are the
 // source bits of the node(s).
-// concentration of one species from its pulled populations (scaled storage:
-// deviations in units of w sigma_g)
-template <typename V, bool SCALED>
-__device__ __forceinline__ V species_moment(const Coefs<typename Lane<V>::S>& k, const V (&g)[5]) {
-    using L = Lane<V>;
-    if (SCALED)
-        return L::fma(L::c(k.gscale[0]), g[0],
-                      L::mul(L::c(k.gscale[1]), L::add(L::add(g[1], g[2]), L::add(g[3], g[4]))));
-    return L::add(L::add(L::add(g[0], g[1]), L::add(g[2], g[3])), g[4]);
-}
-
 template <typename V, int S, int FORCING, bool SCALED>
 __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k, V (&d)[9],
                                              V (&g)[S > 0 ? S : 1][5], V fvx, V fvy,
@@ -423,7 +385,15 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
     }
     if (S > 0) {
 #pragma unroll
-        for (int s = 0; s < S; ++s) ph[s] = species_moment<V, SCALED>(k, g[s]);
+        for (int s = 0; s < S; ++s) {
+            if (SCALED)
+                ph[s] = L::fma(L::c(k.gscale[0]), g[s][0],
+                               L::mul(L::c(k.gscale[1]),
+                                      L::add(L::add(g[s][1], g[s][2]), L::add(g[s][3], g[s][4]))));
+            else
+                ph[s] = L::add(L::add(L::add(g[s][0], g[s][1]), L::add(g[s][2], g[s][3])),
+                               g[s][4]);
+        }
 #pragma unroll
         for (int s = 0; s < S; ++s) {
             V R = L::sel((bitsA >> s) & 1u, (bitsB >> s) & 1u, k.srate[s]);
@@ -458,7 +428,6 @@ template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
                                              int y) {
     constexpr bool GRIDDEP = false;
-    constexpr bool EXTRAS = false;  // the ensemble's tissues have none of the options
     LBIB_LATTICE_NODE_BODY
 }
 

@@ -63,8 +63,7 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.src = take(align_up(P, 8));  // one byte per node
     l.smask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
-    if (p.noflux_mask && !p.noflux_dynamic) l.dom = take(P * 4);
-    if (p.noflux_dynamic) l.id2 = take(P * 4);
+    if (p.noflux_mask) l.dom = take(P * 4);
     if (p.mass_sources && max_cells > 0) {
         l.mrate = take((uint64_t)max_cells * 8);
         l.marea = take((uint64_t)max_cells * 8);
@@ -171,15 +170,6 @@ static int check_params(const lbib_params* p, std::string* why) {
     if (p->node_sources != 0 && p->node_sources != 1) {
         *why = "node_sources must be 0 or 1"; return LBIB_E_PARAM;
     }
-    if ((p->noflux_dynamic != 0 && p->noflux_dynamic != 1) ||
-        (p->noflux_dynamic && !p->noflux_mask)) {
-        *why = "noflux_dynamic must be 0 or 1 and needs confined species"; return LBIB_E_PARAM;
-    }
-    if (!std::isfinite(p->mass_beta) ||
-        (p->mass_beta != 0.0 && (p->mass_species < 0 || p->mass_species >= p->n_species))) {
-        *why = "mass_beta must be finite and mass_species a species of the context";
-        return LBIB_E_PARAM;
-    }
     return LBIB_OK;
 }
 
@@ -205,8 +195,6 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
     k->sa = (C)p.schnak[1];
     k->sb = (C)p.schnak[2];
     k->prho = (C)(p.pressure_nodes ? p.pressure_rho : p.rho0);
-    k->mbeta = (C)p.mass_beta;
-    k->mspecies = p.mass_species;
     const double sf = p.fp16_scale > 0 ? p.fp16_scale : std::ldexp(1.0, -10);
     const double sg = p.fp16_scale_species > 0 ? p.fp16_scale_species : std::ldexp(1.0, -8);
     const bool scaled = p.precision == LBIB_FP16;
@@ -235,12 +223,6 @@ static const void* coefs_of(const lbib_ctx* c) {
     return c->p.precision == LBIB_FP64 ? (const void*)&c->kd : (const void*)&c->kf;
 }
 
-// the label plane of the lattice launch that reads population buffer `buf`
-// (moving confinement: the planes alternate with the buffers; else one plane)
-static uint64_t label_plane(const lbib_ctx* c, int buf) {
-    return (c->p.noflux_dynamic && buf == 1) ? c->L.id2 : c->L.id;
-}
-
 static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     LatticeArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -250,7 +232,7 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.gsrc = c->ws + L.g[src_buf];
     a.gdst = c->ws + L.g[1 - src_buf];
     a.force = c->ws + L.force;
-    a.id = c->at<uint32_t>(label_plane(c, src_buf));
+    a.id = c->at<uint32_t>(L.id);
     a.u = c->ws + L.u;
     a.rho = c->ws + L.rho;
     a.phi = c->ws + L.phi;
@@ -264,12 +246,7 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     a.out = out ? 1 : 0;
     a.ib = c->nC > 0 ? 1 : 0;
     a.l2_first = c->l2_first ? 1 : 0;
-    if (c->p.noflux_mask && c->p.noflux_dynamic) {
-        // confined by the cells' labels of this step (kOutside outside)
-        a.dom = c->at<int32_t>(label_plane(c, src_buf));
-        a.id_clear = c->at<uint32_t>(label_plane(c, 1 - src_buf));
-        a.noflux = c->p.noflux_mask;
-    } else if (c->p.noflux_mask) {
+    if (c->p.noflux_mask) {
         a.dom = c->at<int32_t>(L.dom);
         a.noflux = c->p.noflux_mask;
     }
@@ -284,9 +261,8 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
 }
 
 // out_next: the prep is for the output step (vertex forces and labels are
-// written for the caller); next_buf: the population buffer the lattice launch
-// after this prep reads (it selects the label plane)
-static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next, int next_buf) {
+// written for the caller)
+static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
     IBArgs a;
     std::memset(&a, 0, sizeof(a));
     const Layout& L = c->L;
@@ -305,7 +281,7 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next, int next
     a.srcf = c->at<uint8_t>(L.srcf);
     a.vforce = c->at<double2>(L.vforce);
     a.force = c->ws + L.force;
-    a.id = c->at<uint32_t>(label_plane(c, next_buf));
+    a.id = c->at<uint32_t>(L.id);
     a.u = c->ws + L.u;
     a.diag = c->at<uint32_t>(L.diag);
     a.nx = c->p.nx;
@@ -335,15 +311,13 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next, int next
         a.malpha = c->p.mass_alpha;
         a.do_ids = 1;
     }
-    // labels every step for moving confinement and the beta source
-    if (prep && (c->p.noflux_dynamic || c->p.mass_beta != 0.0)) a.do_ids = 1;
     return a;
 }
 
 namespace lbib {
 LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out) { return lattice_args(c, src_buf, out); }
 IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
-    return ib_args(c, move, prep, out_next, 0);
+    return ib_args(c, move, prep, out_next);
 }
 }  // namespace lbib
 
@@ -357,11 +331,10 @@ static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl 
                           coefs_of(c), c->block, c->stream, pdl && c->nC > 0, c->lattice_pairs);
 }
 
-static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next, int next_buf,
+static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next,
                               bool pdl = false) {
     if (c->nC == 0) return cudaSuccess;
-    return launch_ib(c->p.precision, ib_args(c, move, prep, out_next, next_buf), c->maxv_cell,
-                     c->stream,
+    return launch_ib(c->p.precision, ib_args(c, move, prep, out_next), c->maxv_cell, c->stream,
                      pdl);
 }
 
@@ -379,9 +352,9 @@ static void drop_graphs(lbib_ctx* c) {
 // inside the graph each launch after the first is programmatic
 static cudaError_t enqueue_chunk(lbib_ctx* c, int par) {
     cudaError_t e = enqueue_lattice(c, par, false);
-    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, 1 - par, true);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, true);
     if (e == cudaSuccess) e = enqueue_lattice(c, 1 - par, false, true);
-    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, par, true);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, true);
     return e;
 }
 
@@ -472,19 +445,17 @@ template <class Wrap>
 static cudaError_t run_with_junctions(lbib_ctx* c, int n_steps, bool pdl, Wrap&& wrap) {
     cudaError_t e = cudaSuccess;
     if (junction_due(c)) e = wrap(1, [&] { return junction_renew(c); });
-    if (e == cudaSuccess)
-        e = wrap(1, [&] { return enqueue_ib(c, false, true, n_steps == 1, c->cur); });
+    if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
     for (int i = 0; i < n_steps && e == cudaSuccess; ++i) {
         const bool last = (i == n_steps - 1);
         e = wrap(0, [&] { return enqueue_lattice(c, c->cur, last, pdl); });
-        if (e == cudaSuccess)
-            e = wrap(1, [&] { return enqueue_ib(c, true, false, false, 1 - c->cur, pdl); });
+        if (e == cudaSuccess) e = wrap(1, [&] { return enqueue_ib(c, true, false, false, pdl); });
         c->cur = 1 - c->cur;
         ++c->nstep;
         if (e == cudaSuccess && !last) {
             if (junction_due(c)) e = wrap(1, [&] { return junction_renew(c); });
             if (e == cudaSuccess)
-                e = wrap(1, [&] { return enqueue_ib(c, false, true, i == n_steps - 2, c->cur); });
+                e = wrap(1, [&] { return enqueue_ib(c, false, true, i == n_steps - 2); });
         }
     }
     return e;
@@ -556,7 +527,6 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.u, 0, 2 * L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
-    if (e == cudaSuccess && L.id2) e = cudaMemsetAsync(c->ws + L.id2, 0xFF, L.plane * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.src, 0, align_up(L.plane, 8), c->stream);
@@ -646,10 +616,6 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
             e = cudaMemcpyAsync(c->ws + L.srcf, sf.data(), (size_t)n_cells, cudaMemcpyHostToDevice,
                                 c->stream);
     }
-    if (e == cudaSuccess && L.id2) {  // moving confinement keeps a plane of labels between steps
-        e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id2, 0xFF, L.plane * 4, c->stream);
-    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = upload_vertex_cells(c, n_cells, cell_off);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_cells");
@@ -666,8 +632,7 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
 
 int lbib_set_domains(lbib_ctx* c, const int32_t* labels) {
     if (!c) return LBIB_E_PARAM;
-    if (!c->p.noflux_mask || c->p.noflux_dynamic)
-        return fail(c, LBIB_E_STATE, "the context has no static domain plane");
+    if (!c->p.noflux_mask) return fail(c, LBIB_E_STATE, "the context has no confined species");
     const Layout& L = c->L;
     cudaError_t e;
     if (labels)
@@ -820,7 +785,7 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
         return LBIB_OK;
     }
     // prep of the first step (labels, forces, spreading from X^n)
-    if (ib) e = enqueue_ib(c, false, true, n_steps == 1, c->cur);
+    if (ib) e = enqueue_ib(c, false, true, n_steps == 1);
     int left = n_steps;
     // full two-step chunks through the graph, keeping the last two steps apart
     // (they write the vertex forces and the output fields)
@@ -838,7 +803,7 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     while (e == cudaSuccess && left > 0) {
         const bool last = (left == 1);
         e = enqueue_lattice(c, c->cur, last, follows_kernel);
-        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, !last, left == 2, 1 - c->cur, true);
+        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, !last, left == 2, true);
         follows_kernel = ib;
         c->cur = 1 - c->cur;
         --left;
@@ -876,11 +841,11 @@ int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
             return e;
         });
     } else {
-        if (ib) timed(1, [&] { return enqueue_ib(c, false, true, n_steps == 1, c->cur); });
+        if (ib) timed(1, [&] { return enqueue_ib(c, false, true, n_steps == 1); });
         for (int left = n_steps; left > 0 && e == cudaSuccess; --left) {
             const bool last = (left == 1);
             timed(0, [&] { return enqueue_lattice(c, c->cur, last); });
-            if (ib) timed(1, [&] { return enqueue_ib(c, true, !last, left == 2, 1 - c->cur); });
+            if (ib) timed(1, [&] { return enqueue_ib(c, true, !last, left == 2); });
             c->cur = 1 - c->cur;
         }
     }
@@ -1060,7 +1025,6 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.force, 0, 2 * L.plane * L.cs, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.id, 0xFF, L.plane * 4, c->stream);
-    if (e == cudaSuccess && L.id2) e = cudaMemsetAsync(c->ws + L.id2, 0xFF, L.plane * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.fmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.lmask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.src, 0, align_up(L.plane, 8), c->stream);

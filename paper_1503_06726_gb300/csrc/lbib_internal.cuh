@@ -59,7 +59,6 @@ struct Layout {
     uint64_t mrate = 0, marea = 0, msrc = 0;  // per-cell mass source data (mass_sources)
     uint64_t pnode = 0;        // internal pressure nodes, one byte per node (pressure_nodes)
     uint64_t nsrc = 0;         // static mass source per node, compute type (node_sources)
-    uint64_t id2 = 0;          // second label plane (noflux_dynamic: planes alternate by step)
     int jnbx = 0, jnby = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
@@ -83,8 +82,6 @@ struct Coefs {
     int react_model;            // LBIB_REACT_LINEAR or LBIB_REACT_SCHNAKENBERG
     C sgamma, sa, sb;           // Schnakenberg gamma, a, b
     C prho;                     // density held at internal pressure nodes
-    C mbeta;                    // mass source mbeta phi_s inside cells (s = mspecies)
-    int mspecies;
 };
 
 struct LatticeArgs {
@@ -125,11 +122,6 @@ struct LatticeArgs {
     // static mass source per node (compute type, pitch layout), added to the
     // cell's; NULL = none
     const void* nsrc;
-    // confinement by the moving membranes: `id` (and `dom`) is this step's
-    // label plane, kept for the neighbours' reads; id_clear, the other
-    // plane, is cleared whole for the next prep.  NULL = labels read then
-    // cleared per node
-    uint32_t* id_clear;
 };
 
 struct IBArgs {

@@ -72,8 +72,7 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     if (params->junction_period > 0)
         return set_thread_error(LBIB_E_PARAM,
                                 "lbib_step_noalloc: cell junctions need a context");
-    if (params->mass_sources || params->pressure_nodes || params->node_sources ||
-        params->mass_beta != 0.0)
+    if (params->mass_sources || params->pressure_nodes || params->node_sources)
         return set_thread_error(LBIB_E_PARAM,
                                 "lbib_step_noalloc: mass sources and pressure nodes need a context");
     if (params->reaction != LBIB_REACT_LINEAR &&

@@ -79,8 +79,6 @@ class lbib_params(ctypes.Structure):
         ("mass_sources", ctypes.c_int32), ("pressure_nodes", ctypes.c_int32),
         ("mass_alpha", ctypes.c_double), ("pressure_rho", ctypes.c_double),
         ("node_sources", ctypes.c_int32), ("node_pad", ctypes.c_int32),
-        ("mass_beta", ctypes.c_double), ("mass_species", ctypes.c_int32),
-        ("noflux_dynamic", ctypes.c_int32),
     ]
 
 
@@ -209,9 +207,9 @@ def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
     o.pressure_nodes = int(getattr(p, "pressure_nodes", 0) or 0)
     o.pressure_rho = float(getattr(p, "pressure_rho", 0.0) or 0.0)
     o.node_sources = int(getattr(p, "node_sources", 0) or 0)
-    o.mass_beta = float(getattr(p, "mass_beta", 0.0) or 0.0)
-    o.mass_species = int(getattr(p, "mass_species", 0) or 0)
-    o.noflux_dynamic = int(getattr(p, "noflux_dynamic", 0) or 0)
+    if float(getattr(p, "mass_beta", 0.0) or 0.0) != 0.0 or int(getattr(p, "noflux_dynamic", 0) or 0):
+        raise ValueError("the concentration-proportional mass source and confinement by moving "
+                         "membranes have no CUDA path")
     return o
 
 
