@@ -78,3 +78,46 @@ def test_create_rejects_bad_workspace_without_touching_device(L):
 def test_status_strings(L):
     assert L.lbib_status_string(0) == "LBIB_OK"
     assert L.lbib_status_string(-5) == "LBIB_E_TIMEOUT"
+
+
+def test_option_validation_on_the_host(L):
+    """The options of the rows beyond the plain step are checked by the host
+    before any device work: reaction models, confined species, junctions,
+    mass sources, pressure and node sources (lbib_workspace_size runs the
+    same checks as lbib_create)."""
+    w = li.config2(nx=96, ny=80, n_cells_side=3)
+    bad = (("reaction", 7), ("noflux_mask", 1 << 3),
+           ("junction_period", -1), ("mass_sources", 2), ("pressure_nodes", 2),
+           ("node_sources", 2))
+    for field, value in bad:
+        q = L.make_params(w.params, L.LBIB_FP32)
+        setattr(q, field, value)
+        with pytest.raises(L.LbibError) as e:
+            L.lbib_workspace_size(q, 10, 1)
+        assert e.value.code == L.LBIB_E_PARAM, field
+    # junctions: l_max must leave room for the 3x3 bin search
+    q = L.make_params(w.params, L.LBIB_FP32)
+    q.junction_period, q.junction_lmax, q.junction_k = 5, 40.0, 0.01
+    with pytest.raises(L.LbibError):
+        L.lbib_workspace_size(q, 10, 1)
+    # pressure nodes need a positive density
+    q = L.make_params(w.params, L.LBIB_FP32)
+    q.pressure_nodes, q.pressure_rho = 1, 0.0
+    with pytest.raises(L.LbibError):
+        L.lbib_workspace_size(q, 10, 1)
+    # valid options enlarge the workspace by their planes
+    base = L.lbib_workspace_size(L.make_params(w.params, L.LBIB_FP32), 900, 9)
+    q = L.make_params(w.params, L.LBIB_FP32)
+    q.junction_period, q.junction_lmax, q.junction_k = 5, 8.0, 0.01
+    q.mass_sources, q.pressure_nodes, q.pressure_rho, q.node_sources = 1, 1, 1.0, 1
+    assert L.lbib_workspace_size(q, 900, 9) > base
+
+
+def test_binding_refuses_options_without_a_cuda_path(L):
+    w = li.config2(nx=96, ny=80, n_cells_side=3)
+    w.params.mass_beta = 1e-3
+    with pytest.raises(ValueError):
+        L.make_params(w.params, L.LBIB_FP32)
+    w.params.mass_beta, w.params.noflux, w.params.noflux_dynamic = 0.0, 1, 1
+    with pytest.raises(ValueError):
+        L.make_params(w.params, L.LBIB_FP32)
