@@ -255,6 +255,16 @@ int lbib_set_species(lbib_ctx* ctx, int32_t s, const double* phi);
  * LBIB_E_NONFINITE. */
 int lbib_step(lbib_ctx* ctx, int32_t n_steps);
 
+/* Advance n_steps coupled steps exactly like lbib_step() (the same kernels,
+ * the same arithmetic and the same state afterwards) without the output
+ * work of the last step: no step writes the density, velocity, species,
+ * label, force or vertex-force output planes, so every step is an ordinary
+ * one and all but at most one are replayed from CUDA graphs.  Afterwards
+ * lbib_get_fields() serves LBIB_X and LBIB_AREA; the other fields need an
+ * lbib_step() call first (LBIB_E_STATE).  With cell junctions this is
+ * lbib_step().  Asynchronous on the context stream. */
+int lbib_advance(lbib_ctx* ctx, int32_t n_steps);
+
 /* Copy fields of the last completed step to host buffers (doubles unless
  * stated), synchronising the stream.  `which` is a mask of LBIB_RHO (rho,
  * nx*ny), LBIB_U (ux, uy), LBIB_PHI (phi, n_species*nx*ny), LBIB_X (xy,
@@ -263,7 +273,7 @@ int lbib_step(lbib_ctx* ctx, int32_t n_steps);
  * c+1 for the lowest cell c containing the node in the last step), LBIB_FORCE (force, 2*nx*ny
  * interleaved fx, fy spread in the last step) and LBIB_VFORCE (vforce, 2*V
  * vertex forces of the last step).  Lattice fields need at least one step
- * since create (else LBIB_E_STATE).  Unused pointers may be NULL. */
+ * since create, the last one by lbib_step() (else LBIB_E_STATE).  Unused pointers may be NULL. */
 int lbib_get_fields(lbib_ctx* ctx, uint32_t which, double* rho, double* ux, double* uy,
                     double* phi, double* xy, double* area, int32_t* id, double* force,
                     double* vforce);
@@ -455,11 +465,10 @@ int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, cons
 
 /* Coupled steps without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory while
- * they run -- code inside a framework whose memory pool owns the device,
- * plug-ins that must keep the device footprint fixed after start-up, or host
- * code that runs while a CUDA graph is being captured.  It runs the kernels of
- * lbib_step() on state the caller already owns and calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * they run -- code inside a framework whose memory pool owns the device, or
+ * plug-ins that must keep the device footprint fixed after start-up.  It runs
+ * the kernels of lbib_step() on state the caller already owns and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  *
  * The intermediate planes (second population buffer, spread force, source
  * bits, velocity, diagnostic words) live in one static device array of 4 MiB
@@ -471,14 +480,21 @@ int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, cons
  * host threads) race and give wrong results, so serialise them.  Each call
  * resets the planes that must start empty.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture begins.  The call
- * synchronises `cuda_stream` before it returns.
+ * current.  The call reads the diagnostic words back and synchronises
+ * `cuda_stream` before it returns, so that stream must not be capturing a
+ * graph when it is called.
  *
  * Arguments (device pointers, on the current device):
- *   params      as for lbib_create(); params->precision selects the storage
+ *   params      as for lbib_create() (the same checks); params->precision
+ *               selects the storage; confined species, junctions, mass
+ *               sources, pressure nodes and node sources are refused
+ *               (LBIB_E_PARAM: they need a context's planes)
  *   n_cells, d_cell_off, d_xy (in/out, 2*V), d_rest_len, d_k_spring (V),
  *               d_pressure (n_cells), d_src_flag (n_cells): as lbib_set_cells()
- *               but already on the device and complete (no NULL defaults)
+ *               but already on the device and complete (no NULL defaults);
+ *               the offsets are not read on the host, so a cell with fewer
+ *               than 3 or more than 1024 vertices is skipped on the device
+ *               and reported as LBIB_E_NONFINITE (geometry flag)
  *   d_f         9 population planes, d_g 5*n_species planes (in/out), in the
  *               library's storage layout: element bytes b = 8 / 4 / 2 for
  *               FP64 / FP32 / FP16, row pitch = nx rounded up to a multiple
@@ -486,6 +502,8 @@ int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, cons
  *               values stored as the deviations f - w rho0 (FP16: divided by
  *               w sigma) -- the population section of lbib_get_state(); all
  *               zero bytes is the rest state
+ *   alignment   d_f, d_g and d_xy 16 bytes; d_rest_len, d_k_spring,
+ *               d_pressure 8 bytes; d_cell_off 4 bytes (else LBIB_E_PARAM)
  *   n_steps     steps to advance; the result is always left in d_f, d_g
  *   cuda_stream cudaStream_t as void* (NULL = legacy default stream)
  * Returns LBIB_OK, LBIB_E_PARAM, LBIB_E_WORKSPACE (lattice too large for the

@@ -45,6 +45,13 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
     // (programmatic launch) or writes what it reads
     griddep_wait();
     griddep_launch_dependents();
+    // the shared arrays hold kMaxVertsPerCell vertices and a polygon needs
+    // three; callers that pass device offsets unchecked (the allocation-free
+    // step) get the geometry flag instead of an access past sx
+    if (n > kMaxVertsPerCell || n < 3) {
+        if (tid == 0) raise_flag(a.diag, kDiagGeometry);
+        return;
+    }
 
     if (tid < kMaxRows) rowcnt[tid] = 0;
     if (tid == 0) {

@@ -475,7 +475,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
     const int v0 = __ldcg(a.off + c);
     const int n = __ldcg(a.off + c + 1) - v0;
     const int lane = tid & 31;
-    if (n > S.maxv) {  // cannot happen for callers that size maxv from the cells
+    if (n > S.maxv || n < 3) {  // cannot happen for callers that size maxv from the cells
         if (GRIDDEP) {
             griddep_wait();
             griddep_launch_dependents();

@@ -213,6 +213,7 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
 namespace lbib {
 void fill_coefs_public(const lbib_params& p, Coefs<double>* k) { fill_coefs(p, k); }
 void fill_coefs_public(const lbib_params& p, Coefs<float>* k) { fill_coefs(p, k); }
+int check_params_public(const lbib_params* p, std::string* why) { return check_params(p, why); }
 int set_thread_error(int code, const std::string& msg) {
     g_create_err = msg;
     return code;
@@ -339,28 +340,36 @@ static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next,
 }
 
 static void drop_graphs(lbib_ctx* c) {
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (c->chunk[i]) {
             cudaGraphExecDestroy(c->chunk[i]);
             c->chunk[i] = nullptr;
         }
+        if (c->tail[i]) {
+            cudaGraphExecDestroy(c->tail[i]);
+            c->tail[i] = nullptr;
+        }
+    }
     c->chunk_nC = -1;
 }
 
 // two full steps starting from buffer parity `par`, ending with the prep of
 // the following step: [lat(par), ib move+prep, lat(1-par), ib move+prep];
 // inside the graph each launch after the first is programmatic
-static cudaError_t enqueue_chunk(lbib_ctx* c, int par) {
+// tail: the second IB launch only moves (no prep for a following step)
+static cudaError_t enqueue_chunk(lbib_ctx* c, int par, bool tail = false) {
     cudaError_t e = enqueue_lattice(c, par, false);
     if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, true);
     if (e == cudaSuccess) e = enqueue_lattice(c, 1 - par, false, true);
-    if (e == cudaSuccess) e = enqueue_ib(c, true, true, false, true);
+    if (e == cudaSuccess) e = enqueue_ib(c, true, !tail, false, true);
     return e;
 }
 
-static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out) {
+static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out,
+                                   bool tail = false) {
     if (c->chunk_nC != c->nC) drop_graphs(c);
-    if (!c->chunk[par]) {
+    cudaGraphExec_t* slot = tail ? &c->tail[par] : &c->chunk[par];
+    if (!*slot) {
         cudaStream_t cap;
         cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         if (e != cudaSuccess) return e;
@@ -369,7 +378,7 @@ static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out) {
         cudaGraph_t g = nullptr;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e2 = enqueue_chunk(c, par);
+            cudaError_t e2 = enqueue_chunk(c, par, tail);
             e = cudaStreamEndCapture(cap, &g);
             if (e2 != cudaSuccess) e = e2;
         }
@@ -379,12 +388,12 @@ static cudaError_t get_chunk_graph(lbib_ctx* c, int par, cudaGraphExec_t* out) {
             if (g) cudaGraphDestroy(g);
             return e;
         }
-        e = cudaGraphInstantiate(&c->chunk[par], g, 0);
+        e = cudaGraphInstantiate(slot, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return e;
         c->chunk_nC = c->nC;
     }
-    *out = c->chunk[par];
+    *out = *slot;
     return cudaSuccess;
 }
 
@@ -811,6 +820,37 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
     c->fields_valid = true;
     c->vforce_valid = ib;
+    return LBIB_OK;
+}
+
+int lbib_advance(lbib_ctx* c, int32_t n_steps) {
+    if (!c) return LBIB_E_PARAM;
+    if (n_steps < 0) return fail(c, LBIB_E_PARAM, "n_steps must be >= 0");
+    if (n_steps == 0) return LBIB_OK;
+    const bool ib = c->nC > 0;
+    // steps with junctions are launched one by one anyway
+    if (ib && c->p.junction_period > 0) return lbib_step(c, n_steps);
+    cudaError_t e = cudaSuccess;
+    if (ib) e = enqueue_ib(c, false, true, false);
+    int left = n_steps;
+    // an odd count starts with one directly launched step (programmatic after
+    // the prep); its IB launch moves, and preps unless it is the only step
+    if (left % 2 == 1) {
+        if (e == cudaSuccess) e = enqueue_lattice(c, c->cur, false, ib);
+        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, left > 1, false, true);
+        c->cur = 1 - c->cur;
+        --left;
+    }
+    while (e == cudaSuccess && left > 0) {
+        cudaGraphExec_t g;
+        e = get_chunk_graph(c, c->cur, &g, left == 2);
+        if (e == cudaSuccess) e = cudaGraphLaunch(g, c->stream);
+        left -= 2;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_advance");
+    // the lattice fields, labels and vertex forces of the last step were not written
+    c->fields_valid = false;
+    c->vforce_valid = false;
     return LBIB_OK;
 }
 

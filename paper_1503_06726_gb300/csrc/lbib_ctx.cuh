@@ -28,6 +28,9 @@ struct lbib_ctx {
     bool l2_first = false;      // population loads evict-first (lattice nearly fits in L2)
     // graph of a two-step chunk, keyed by the buffer parity it starts from
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
+    // the same two steps whose last IB launch only moves (the end of an
+    // lbib_advance call), keyed the same way
+    cudaGraphExec_t tail[2] = {nullptr, nullptr};
     int chunk_nC = -1;
     // pinned staging of lbib_set_cell_params (pressure then source flags), and
     // the event of its last upload (the buffer is reused once that is done)

@@ -334,6 +334,8 @@ inline int64_t mask_words(int64_t plane) { return (plane + 127) / 128 + 1; }
 // coefficient tables and the calling thread's error text (lbib_last_error(NULL))
 void fill_coefs_public(const lbib_params& p, Coefs<double>* k);
 void fill_coefs_public(const lbib_params& p, Coefs<float>* k);
+// the parameter checks of lbib_create (LBIB_OK or LBIB_E_PARAM with the reason)
+int check_params_public(const lbib_params* p, std::string* why);
 int set_thread_error(int code, const std::string& msg);
 
 // launchers (return cudaError_t of the launch)

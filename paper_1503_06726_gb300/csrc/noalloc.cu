@@ -2,14 +2,15 @@
 //
 // Some callers are not allowed to call cudaMalloc (or any allocator) while
 // they run: code inside a framework whose memory pool owns the whole device,
-// plug-ins that must not change the device's memory footprint after start-up,
-// or host code running inside a CUDA graph capture.  For them this file
-// provides lbib_step_noalloc(), which runs the same kernels as lbib_step() on
-// state buffers the caller already owns, and keeps every intermediate plane
-// (the second population buffer, the spread force, the source bits, the
-// velocity and the diagnostic words) in one file-scope static device array
-// of kScratchBytes.  Every GPU that loads the library holds that array until
-// the process exits.
+// or plug-ins that must not change the device's memory footprint after
+// start-up.  For them this file provides lbib_step_noalloc(), which runs the
+// same kernels as lbib_step() on state buffers the caller already owns, and
+// keeps every intermediate plane (the second population buffer, the spread
+// force, the source bits, the velocity and the diagnostic words) in one
+// file-scope static device array of kScratchBytes.  Every GPU that loads the
+// library holds that array until the process exits.  The call reads the
+// diagnostic words back and synchronises its stream before it returns, so it
+// must not be called while that stream is being captured into a graph.
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -58,14 +59,12 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
                                  const double* d_rest_len, const double* d_k_spring,
                                  const double* d_pressure, const uint8_t* d_src_flag, void* d_f,
                                  void* d_g, int32_t n_steps, void* cuda_stream) {
+    std::string why;
+    if (check_params_public(params, &why) != LBIB_OK)
+        return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: " + why);
     Layout L;
-    if (!params || !make_layout(*params, 0, 0, &L) || !(params->tau > 0.5) || n_steps < 0 ||
-        n_cells < 0 || params->bc_y < 0 || params->bc_y > 1 ||
-        (params->forcing != LBIB_GUO && params->forcing != LBIB_HE_PAPER))
+    if (!make_layout(*params, 0, 0, &L) || n_steps < 0 || n_cells < 0)
         return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: invalid parameters");
-    for (int s = 0; s < params->n_species; ++s)
-        if (!(params->D[s] > 0.0))
-            return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: D must be > 0");
     if (params->noflux_mask)
         return set_thread_error(LBIB_E_PARAM,
                                 "lbib_step_noalloc: confined species need a context's domain plane");
@@ -75,13 +74,21 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     if (params->mass_sources || params->pressure_nodes || params->node_sources)
         return set_thread_error(LBIB_E_PARAM,
                                 "lbib_step_noalloc: mass sources and pressure nodes need a context");
-    if (params->reaction != LBIB_REACT_LINEAR &&
-        !(params->reaction == LBIB_REACT_SCHNAKENBERG && params->n_species >= 2))
-        return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: invalid reaction model");
     if (!d_f || (params->n_species > 0 && !d_g) ||
         (n_cells > 0 && (!d_cell_off || !d_xy || !d_rest_len || !d_k_spring || !d_pressure ||
                          !d_src_flag)))
         return set_thread_error(LBIB_E_PARAM, "lbib_step_noalloc: missing buffer");
+    // the kernels move populations, positions and constants in vector and
+    // word accesses of these sizes
+    auto misaligned = [](const void* p, uintptr_t a) {
+        return p && reinterpret_cast<uintptr_t>(p) % a != 0;
+    };
+    if (misaligned(d_f, 16) || misaligned(d_g, 16) || misaligned(d_xy, 16) ||
+        misaligned(d_rest_len, 8) || misaligned(d_k_spring, 8) || misaligned(d_pressure, 8) ||
+        misaligned(d_cell_off, 4))
+        return set_thread_error(LBIB_E_PARAM,
+                                "lbib_step_noalloc: d_f, d_g, d_xy need 16-byte alignment, "
+                                "d_rest_len, d_k_spring, d_pressure 8 bytes, d_cell_off 4 bytes");
     if (n_steps == 0) return LBIB_OK;
 
     // scratch plan: second population buffer, force, velocity, source bits, diag

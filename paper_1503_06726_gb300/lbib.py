@@ -43,7 +43,7 @@ EXPORTS = (
     "lbib_set_domains", "lbib_set_mass_sources", "lbib_set_pressure_nodes",
     "lbib_set_node_sources",
     "lbib_set_cell_params",
-    "lbib_set_species", "lbib_step", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
+    "lbib_set_species", "lbib_step", "lbib_advance", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
     "lbib_status_string", "lbib_label_cells", "lbib_steady_workspace_size", "lbib_steady_solve",
     "lbib_ensemble_workspace_size", "lbib_ensemble_create", "lbib_ensemble_tissue",
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_set_node_sources": (ctypes.c_int, [vp, vp]),
         "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
         "lbib_step": (ctypes.c_int, [vp, i32]),
+        "lbib_advance": (ctypes.c_int, [vp, i32]),
         "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
         "lbib_get_fields": (ctypes.c_int, [vp, u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "lbib_get_sizes": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
@@ -281,6 +282,10 @@ def lbib_set_species(ctx, s: int, phi):
 
 def lbib_step(ctx, n_steps: int):
     _check(load().lbib_step(ctx, int(n_steps)), ctx)
+
+
+def lbib_advance(ctx, n_steps: int) -> None:
+    _check(load().lbib_advance(ctx, int(n_steps)), ctx)
 
 
 def lbib_step_profiled(ctx, n_steps: int):
@@ -489,6 +494,10 @@ class Simulation:
 
     def step(self, n: int = 1):
         lbib_step(self.ctx, n)
+
+    def advance(self, n: int = 1):
+        """n steps without the output work of the last one (lbib_advance)."""
+        lbib_advance(self.ctx, n)
 
     def step_profiled(self, n: int):
         return lbib_step_profiled(self.ctx, n)

@@ -1,14 +1,17 @@
 """The allocation-free entry point, lbib_step_noalloc, against lbib_step.
 
 Callers that may not allocate device memory while they run (a framework's
-memory pool owns the device, a plug-in must keep its footprint fixed, or the
-host thread is capturing a CUDA graph) use lbib_step_noalloc with buffers
-they already own; its intermediate planes live in a static device array in
-the library.  This test gives it the same state as a context, runs two calls
-in a row and compares populations and vertex positions with the context's
-lbib_step after each call, at the FP64 parity tolerance used elsewhere
-(relative L-infinity 1e-10).  It lives in its own file that pytest collects
-last, and it holds its own state, so it passes alone or after other tests.
+memory pool owns the device, or a plug-in must keep its footprint fixed) use
+lbib_step_noalloc with buffers they already own; its intermediate planes live
+in a static device array in the library.  These tests give it the same state
+as a context, run two calls in a row and compare populations and vertex
+positions with the context's lbib_step after each call: FP64 storage at the
+FP64 parity tolerance used elsewhere (relative L-infinity 1e-10), FP32
+storage at the tolerance of the ensemble-against-single-tissue test (the same
+kernels, only the atomic order of the spreading differs: populations 1e-5
+relative, positions 1e-9 LU).  The call synchronises its stream, so the
+stream is idle when it returns.  The file is collected last and holds its own
+state, so it passes alone or after the other tests.
 """
 import numpy as np
 import pytest
@@ -31,9 +34,9 @@ def _split_state(blob, w, es, plane):
     return f, g, xy
 
 
-def _lattice(raw, n_planes, plane, pitch, nx, ny):
+def _lattice(raw, n_planes, plane, pitch, nx, ny, dtype=np.float64):
     """The nx*ny nodes of each plane (row and plane padding are never written)."""
-    v = raw.view(np.float64)
+    v = raw.view(dtype).astype(np.float64)
     return np.stack([v[q * plane:q * plane + pitch * ny].reshape(ny, pitch)[:, :nx]
                      for q in range(n_planes)])
 
@@ -43,7 +46,7 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / s) if s > 0 else float(np.abs(a - b).max())
 
 
-def test_noalloc_matches_context_two_calls():
+def _two_calls(precision, tol_pop, tol_xy):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
@@ -54,12 +57,13 @@ def test_noalloc_matches_context_two_calls():
     w = li.config1()
     T = w.tissue
     p = w.params
-    cp = lbib.make_params(p, lbib.LBIB_FP64)
-    es = 8
+    cp = lbib.make_params(p, precision)
+    es = 8 if precision == lbib.LBIB_FP64 else 4
+    dt = np.float64 if es == 8 else np.float32
     pitch = (p.nx + 63) // 64 * 64
     plane = pitch * p.ny + 1536 // es
 
-    sim = lbib.Simulation(p, lbib.LBIB_FP64, T.n_vertices, T.n_cells)
+    sim = lbib.Simulation(p, precision, T.n_vertices, T.n_cells)
     sim.set_cells(T)
     f0, g0, xy0 = _split_state(sim.get_state(), w, es, plane)
     assert np.array_equal(xy0, T.xy)
@@ -73,23 +77,34 @@ def test_noalloc_matches_context_two_calls():
     d_k = torch.from_numpy(T.k_spring.copy()).to(dev)
     d_p = torch.from_numpy(T.pressure.copy()).to(dev)
     d_s = torch.from_numpy(T.src_flag.astype(np.uint8)).to(dev)
-    stream = torch.cuda.current_stream().cuda_stream
+    cs = torch.cuda.current_stream()
     torch.cuda.synchronize()
 
     for n in (3, 4):   # two calls in a row, odd then even step counts
         lbib.lbib_step_noalloc(cp, T.n_cells, d_off.data_ptr(), d_xy.data_ptr(),
                                d_L0.data_ptr(), d_k.data_ptr(), d_p.data_ptr(), d_s.data_ptr(),
-                               d_f.data_ptr(), d_g.data_ptr(), n, stream)
+                               d_f.data_ptr(), d_g.data_ptr(), n, cs.cuda_stream)
+        assert cs.query(), "the call returns with its stream idle"
         sim.step(n)
         fr, gr, xyr = _split_state(sim.get_state(), w, es, plane)
         S = p.n_species
-        fn = _lattice(d_f.cpu().numpy(), 9, plane, pitch, p.nx, p.ny)
-        gn = _lattice(d_g.cpu().numpy(), 5 * S, plane, pitch, p.nx, p.ny)
-        assert _rel(fn, _lattice(fr, 9, plane, pitch, p.nx, p.ny)) < 1e-10
-        assert _rel(gn, _lattice(gr, 5 * S, plane, pitch, p.nx, p.ny)) < 1e-10
+        fn = _lattice(d_f.cpu().numpy(), 9, plane, pitch, p.nx, p.ny, dt)
+        gn = _lattice(d_g.cpu().numpy(), 5 * S, plane, pitch, p.nx, p.ny, dt)
+        assert _rel(fn, _lattice(fr, 9, plane, pitch, p.nx, p.ny, dt)) < tol_pop
+        assert _rel(gn, _lattice(gr, 5 * S, plane, pitch, p.nx, p.ny, dt)) < tol_pop
         assert np.abs(fn).max() > 0 and np.abs(gn).max() > 0
-        assert np.abs(d_xy.cpu().numpy() - xyr).max() < 1e-12
+        assert np.abs(d_xy.cpu().numpy() - xyr).max() < tol_xy
     sim.close()
+
+
+def test_noalloc_matches_context_two_calls():
+    from paper_1503_06726_gb300 import lbib
+    _two_calls(lbib.LBIB_FP64, 1e-10, 1e-12)
+
+
+def test_noalloc_fp32_matches_context_two_calls():
+    from paper_1503_06726_gb300 import lbib
+    _two_calls(lbib.LBIB_FP32, 1e-5, 1e-9)
 
 
 def test_noalloc_rejects_oversized_lattice():
