@@ -56,6 +56,9 @@ class LatticeParams:
     reaction: int = 0
     schnak: List[float] = dataclasses.field(default_factory=lambda: [0.0, 0.0, 0.0])
     noflux: int = 0           # bit s: species s confined to its domain
+    # membrane no-flux scheme of the confined species: 0 the equilibrium
+    # closure of Sec. 6.1, 1 half-way bounce-back (an option, not the paper's)
+    noflux_scheme: int = 0
     # cell junctions (Eq. celljunctionforce): spring constant, rest length,
     # cutoff, renewal period in steps (0 = none)
     junction_k: float = 0.0

@@ -23,9 +23,16 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
   junctions          two facing polygons: partners and force k (g - l0) across
                      a gap g by construction, nothing beyond l_max, the
                      periodic image, equal and opposite forces of mutual pairs
-  no-flux domains    per-domain mass conservation of a confined species (a
-                     free one moves mass), relaxation to the domain mean,
-                     one label everywhere = no confinement (bit-exact)
+  no-flux closure    the paper's equilibrium closure (Sec. 6.1): closed form
+    (scheme 0)       for a linear density and a given momentum, the thin-
+                     domain fallbacks, rotation and mirror invariance, uniform
+                     domains as a fixed point with an empty domain staying
+                     empty, first-order convergence to the closed-form
+                     Neumann profile with no steady leak, first-order decay
+                     of the transient leak with straight membranes
+  bounce-back        per-domain mass conservation of a confined species (a
+    (scheme 1)       free one moves mass), relaxation to the domain mean;
+                     either scheme: one label everywhere = no confinement
   conv3x3 (+dgrad,   scipy correlate2d, identity tap, adjointness,
     wgrad)           finite differences
   nn (U-Net)         finite-difference gradient of the whole network,
@@ -69,7 +76,7 @@ class OrcParams(ctypes.Structure):
                 ("decay", ctypes.c_double * 4), ("react", (ctypes.c_double * 4) * 4),
                 ("src_rate", ctypes.c_double * 4), ("forcing", ctypes.c_int32),
                 ("react_model", ctypes.c_int32), ("noflux", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("schnak", ctypes.c_double * 3),
+                ("noflux_scheme", ctypes.c_int32), ("schnak", ctypes.c_double * 3),
                 ("junction_k", ctypes.c_double), ("junction_l0", ctypes.c_double),
                 ("junction_lmax", ctypes.c_double), ("junction_period", ctypes.c_int32),
                 ("pad2", ctypes.c_int32), ("mass_alpha", ctypes.c_double),
@@ -90,6 +97,7 @@ def _P(p) -> OrcParams:
     o.forcing = int(p.forcing)
     o.react_model = int(getattr(p, "reaction", 0))
     o.noflux = int(getattr(p, "noflux", 0))
+    o.noflux_scheme = int(getattr(p, "noflux_scheme", 0) or 0)
     sk = getattr(p, "schnak", (0.0, 0.0, 0.0))
     for q in range(3):
         o.schnak[q] = float(sk[q])
@@ -123,11 +131,12 @@ def lib():
             L.orc_rasterize.argtypes = [i, i, i, i, vp, vp, vp, vp, vp]
             L.orc_spread.argtypes = [i, i, i, i, vp, vp, vp, vp]
             L.orc_interp.argtypes = [i, i, i, i, vp, vp, vp, vp]
-            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 15
-            L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 7
+            L.orc_lattice_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 17
+            L.orc_species_step.argtypes = [ctypes.POINTER(OrcParams)] + [vp] * 9
+            L.orc_species_moments.argtypes = [ctypes.POINTER(OrcParams), vp, vp]
             L.orc_run.restype = i
             L.orc_run.argtypes = ([ctypes.POINTER(OrcParams), i, vp, vp, vp, vp, vp, d, vp, i]
-                                  + [vp] * 16)
+                                  + [vp] * 17)
             L.orc_steady.restype = ctypes.c_long
             L.orc_steady.argtypes = [ctypes.POINTER(OrcParams), vp, vp, d, ctypes.c_long, i,
                                      vp, ctypes.POINTER(d)]
@@ -241,13 +250,33 @@ def _opt(a, dt):
     return None if a is None else np.ascontiguousarray(a, dt)
 
 
+def species_moments(p, g):
+    """Density and momentum (phi, jx, jy) of every species from populations
+    g at the same node: (3S, ny, nx).  The moments a run starts from."""
+    P = _P(p)
+    mom = np.empty((3 * p.n_species, p.ny, p.nx))
+    lib().orc_species_moments(ctypes.byref(P), _ptr(_f64(g)), _ptr(mom))
+    return mom
+
+
+def _mom_in(p, g, mom, dom):
+    """The previous step's species moments for the no-flux closure (only
+    needed with confined species): given, or those of g."""
+    if not (p.n_species and int(getattr(p, "noflux", 0)) and dom is not None):
+        return None
+    return species_moments(p, g) if mom is None else _f64(mom)
+
+
 def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None, msrc=None, pmask=None,
-                 lab=None):
+                 lab=None, mom=None, mom_out=None):
     """One stream+collide update.  Returns (f_out, g_out, rho, ux, uy, phi).
     dom: static domain labels (ny, nx) for the species confined by p.noflux;
     msrc: mass source per node (ny, nx); pmask: internal pressure nodes
     (ny, nx), prescribed density p.pressure_rho; lab: cell labels (ny, nx),
-    > 0 inside a cell, for the source p.mass_beta phi_s."""
+    > 0 inside a cell, for the source p.mass_beta phi_s.  mom: the species
+    moments of the previous step (3S, ny, nx) for the no-flux closure
+    (default: those of g); mom_out (3S, ny, nx), if given, receives this
+    step's."""
     P = _P(p)
     f = _f64(f)
     g = _f64(g) if p.n_species else np.zeros(1)
@@ -257,26 +286,31 @@ def lattice_step(p, f, g, fx=None, fy=None, src=None, dom=None, msrc=None, pmask
     ux = np.empty_like(rho)
     uy = np.empty_like(rho)
     phi = np.empty((max(p.n_species, 1), p.ny, p.nx))
+    mi = _mom_in(p, g, mom, dom)
     lib().orc_lattice_step(ctypes.byref(P), _ptr(f), _ptr(fo), _ptr(g), _ptr(go),
                            _ptr(None if fx is None else _f64(fx)),
                            _ptr(None if fy is None else _f64(fy)),
                            _ptr(None if src is None else np.ascontiguousarray(src, np.uint8)),
                            _ptr(rho), _ptr(ux), _ptr(uy), _ptr(phi), _ptr(_dom(dom)),
                            _ptr(_opt(msrc, np.float64)), _ptr(_opt(pmask, np.uint8)),
-                           _ptr(_opt(lab, np.int32)))
+                           _ptr(_opt(lab, np.int32)), _ptr(mi), _ptr(mom_out))
     return fo, go, rho, ux, uy, phi[: p.n_species]
 
 
-def species_step(p, g, src=None, ux=None, uy=None, dom=None):
+def species_step(p, g, src=None, ux=None, uy=None, dom=None, mom=None, mom_out=None):
+    """One D2Q5 update of every species with a frozen velocity (u = 0 when
+    ux, uy are None).  Returns (g_out, phi).  dom, mom, mom_out as for
+    lattice_step."""
     P = _P(p)
     g = _f64(g)
     go = np.empty_like(g)
     phi = np.empty((p.n_species, p.ny, p.nx))
+    mi = _mom_in(p, g, mom, dom)
     lib().orc_species_step(ctypes.byref(P), _ptr(g), _ptr(go),
                            _ptr(None if ux is None else _f64(ux)),
                            _ptr(None if uy is None else _f64(uy)),
                            _ptr(None if src is None else np.ascontiguousarray(src, np.uint8)),
-                           _ptr(phi), _ptr(_dom(dom)))
+                           _ptr(phi), _ptr(_dom(dom)), _ptr(mi), _ptr(mom_out))
     return go, phi
 
 
@@ -285,14 +319,17 @@ class RunResult:
 
 
 def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=None,
-        mass_rate=None, target_area=None, pmask=None, node_source=None):
+        mass_rate=None, target_area=None, pmask=None, node_source=None, mom=None):
     """n coupled steps from (f, g, xy) (default: rest state and tissue.xy).
     Returns a RunResult with the final state and the last step's fields.
     dom: static domain labels (ny, nx) for the species confined by p.noflux;
     mass_rate (per cell): mass source of the cell's nodes, plus
     p.mass_alpha (target_area - area) with target_area (per cell); pmask:
     internal pressure nodes (ny, nx) held at density p.pressure_rho;
-    node_source: static mass source per node (ny, nx), added to the cells'."""
+    node_source: static mass source per node (ny, nx), added to the cells';
+    mom: the species moments of the previous step (3S, ny, nx) for the no-flux
+    closure of confined species (default: those of the initial g); the
+    result's r.mom carries them on to a following call."""
     P = _P(p)
     N = p.nx * p.ny
     if f is None or g is None:
@@ -314,6 +351,9 @@ def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=N
     r.fy = np.zeros_like(r.rho)
     V = xy.shape[0]
     r.Fv = np.zeros((max(V, 1), 2))
+    r.mom = None
+    if p.n_species and int(getattr(p, "noflux", 0)):
+        r.mom = species_moments(p, g) if mom is None else _f64(mom).copy()
     rc = lib().orc_run(ctypes.byref(P), len(off) - 1, _ptr(off), _ptr(xy), _ptr(_f64(tissue.rest_len)),
                        _ptr(_f64(tissue.k_spring)), _ptr(_f64(tissue.pressure)), float(tension),
                        _ptr(np.ascontiguousarray(tissue.src_flag, np.uint8)), int(n_steps),
@@ -321,7 +361,7 @@ def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=N
                        _ptr(r.id), _ptr(r.src), _ptr(r.fx), _ptr(r.fy), _ptr(r.Fv),
                        _ptr(_dom(dom)), _ptr(_opt(mass_rate, np.float64)),
                        _ptr(_opt(target_area, np.float64)), _ptr(_opt(pmask, np.uint8)),
-                       _ptr(_opt(node_source, np.float64)))
+                       _ptr(_opt(node_source, np.float64)), _ptr(r.mom))
     if rc != 0:
         raise MemoryError("oracle run failed to allocate")
     r.f = f

@@ -34,7 +34,7 @@ typedef struct {
     int32_t forcing;           /* 0 Guo et al. 2002, 1 the paper's simple term (Eq. bgkequation) */
     int32_t react_model;       /* 0 linear (react, decay); 1 Schnakenberg on species 0 and 1 */
     int32_t noflux;            /* bit s: species s is confined to its domain (no-flux membranes) */
-    int32_t pad;
+    int32_t noflux_scheme;     /* 0: the equilibrium closure of Sec. 6.1; 1: half-way bounce-back */
     double schnak[3];          /* gamma, a, b of the Schnakenberg reaction */
     double junction_k, junction_l0, junction_lmax;   /* Eq. celljunctionforce */
     int32_t junction_period;   /* renew the junctions every this many steps (0 = none) */
@@ -324,18 +324,50 @@ static double pull(const double* post, const int* opp, int q, int i, int j, int 
     return post[(long)q * N + (long)sj * nx + si];
 }
 
-/* Species streaming with the membrane no-flux condition.  Reading c26: the
- * paper's no-flux boundary for reaction-advection-diffusion (Sec. 6.1,
- * approximating the missing populations by equilibria with interpolated
- * momentum) is stated too briefly to reproduce; a species confined to its
- * domain is instead reflected by half-way bounce-back on every lattice link
- * whose two nodes carry different domain labels: the population that would
- * arrive across the membrane is the opposite population of the same node,
- * so nothing crosses the membrane and the species' mass in each domain is
- * conserved.  dom: one label per node (any value; equal labels = one
- * domain), NULL = no confinement. */
-static double pull_species(const double* post, const int* opp, int q, int i, int j, int nx,
-                           int ny, int bc_y, const int32_t* dom, int confined) {
+/* Species streaming with the membrane no-flux condition (Sec. 6.1,
+ * "No-flux Boundary Condition for Reaction-Advection-Diffusion Equations").
+ * A species confined to its domain (labels dom, one per node; equal labels =
+ * one domain) does not take the population that would arrive at x along v_q
+ * from a node x - v_q of another domain: that population is missing.
+ *
+ * Scheme 0, the paper's (reading c26): the missing population is the D2Q5
+ * equilibrium w_q (phi + 3 v_q . j) of a density and a momentum (first
+ * moment j = sum_k v_k g_k) obtained from the fluid of the domain:
+ *   - the momentum is interpolated linearly between the fluid node
+ *     y1 = x + v_q (in the direction the missing population travels) and
+ *     zero at the wall point; the membrane sits at the half-way point
+ *     x - v_q/2 of the crossing link (the static domain plane carries no
+ *     finer position), so x lies at distance 1/2 from the wall and y1 at
+ *     3/2: j(x) = (1/2)/(3/2) j(y1) = j(y1)/3;
+ *   - the density is extrapolated linearly from the fluid nodes y1 and
+ *     y2 = x + 2 v_q: phi(x) = 2 phi(y1) - phi(y2);
+ *   - the densities and momenta of the fluid nodes are those of the
+ *     previous step (mom: phi, jx, jy of the pulled populations before the
+ *     collision, per node), so no population of the step depends on
+ *     another one of the same step;
+ *   - where y2 is not in the domain (or beyond a wall) the density is
+ *     taken from y1 alone (zeroth order); where y1 is not in the domain
+ *     either, the momentum is zero (walls on both sides of x) and the
+ *     density is the node's own of the previous step.
+ * The closure is first order in space, as the paper states for it, and it
+ * does not conserve each domain's mass exactly.
+ * Scheme 1 (not the paper's; kept as an option): half-way bounce-back, the
+ * missing population is the opposite population of x itself, so nothing
+ * crosses the membrane and each domain keeps its mass exactly.
+ * Membranes that move (noflux_dynamic, reading c31) always use scheme 1.
+ * Walls in y bounce back first (reading c13). */
+static int in_domain(const int32_t* dom, int i, int j, int nx, int ny, int bc_y, int32_t d0) {
+    if (j < 0 || j >= ny) {
+        if (bc_y == 1) return 0;
+        j = wrap(j, ny);
+    }
+    return dom[(long)j * nx + wrap(i, nx)] == d0;
+}
+
+static double pull_species(const orc_params* P, const double* post, const int* opp, int q,
+                           int i, int j, const int32_t* dom, int confined, const double* mom,
+                           int s) {
+    int nx = P->nx, ny = P->ny, bc_y = P->bc_y;
     if (!confined || !dom || q == 0) return pull(post, opp, q, i, j, nx, ny, bc_y);
     long N = (long)nx * ny;
     int si = wrap(i - CX[q], nx), sj = j - CY[q];
@@ -343,9 +375,53 @@ static double pull_species(const double* post, const int* opp, int q, int i, int
         if (bc_y == 1) return post[(long)opp[q] * N + (long)j * nx + i];
         sj = wrap(sj, ny);
     }
-    if (dom[(long)sj * nx + si] != dom[(long)j * nx + i])
+    int32_t d0 = dom[(long)j * nx + i];
+    if (dom[(long)sj * nx + si] == d0) return post[(long)q * N + (long)sj * nx + si];
+    if (P->noflux_dynamic || P->noflux_scheme == 1 || !mom)
         return post[(long)opp[q] * N + (long)j * nx + i];
-    return post[(long)q * N + (long)sj * nx + si];
+    /* scheme 0: the equilibrium closure */
+    const double* mphi = mom + (long)(3 * s) * N;
+    const double* mjx = mphi + N;
+    const double* mjy = mphi + 2 * N;
+    int in1 = in_domain(dom, i + CX[q], j + CY[q], nx, ny, bc_y, d0);
+    int in2 = in1 && in_domain(dom, i + 2 * CX[q], j + 2 * CY[q], nx, ny, bc_y, d0);
+    long x0 = (long)j * nx + i;
+    long x1 = (long)wrap(j + CY[q], ny) * nx + wrap(i + CX[q], nx);
+    long x2 = (long)wrap(j + 2 * CY[q], ny) * nx + wrap(i + 2 * CX[q], nx);
+    double phih, jh;
+    if (in2) {
+        phih = 2.0 * mphi[x1] - mphi[x2];
+        jh = (CX[q] * mjx[x1] + CY[q] * mjy[x1]) / 3.0;
+    } else if (in1) {
+        phih = mphi[x1];
+        jh = (CX[q] * mjx[x1] + CY[q] * mjy[x1]) / 3.0;
+    } else {
+        phih = mphi[x0];
+        jh = 0.0;
+    }
+    return W5(q) * (phih + 3.0 * jh);
+}
+
+/* Density and momentum of every species from populations g (5S planes) at
+ * the same node (no streaming): mom[3s], mom[3s+1], mom[3s+2] = phi, jx, jy.
+ * The moments a run starts from: those of its initial populations. */
+void orc_species_moments(const orc_params* P, const double* g, double* mom) {
+    long N = (long)P->nx * P->ny;
+    for (int s = 0; s < P->n_species; ++s) {
+        const double* G = g + (long)5 * s * N;
+        double* m = mom + (long)3 * s * N;
+        for (long t = 0; t < N; ++t) {
+            double phi = 0.0, jx = 0.0, jy = 0.0;
+            for (int q = 0; q < 5; ++q) {
+                phi += G[(long)q * N + t];
+                jx += CX[q] * G[(long)q * N + t];
+                jy += CY[q] * G[(long)q * N + t];
+            }
+            m[t] = phi;
+            m[N + t] = jx;
+            m[2 * N + t] = jy;
+        }
+    }
 }
 
 /* The reaction rate of species s at a node (reading c10: evaluated on the
@@ -387,7 +463,8 @@ static double reaction(const orc_params* P, int s, const double* phi, int S, uin
  *   reaction (reading c10: added after collision, evaluated on the
  *   pre-collision phi of the same node)
  *   R_s = sum_b react[s][b] phi_b - decay[s] phi_s + src_rate[s] [src bit s].
- * Walls bounce species back too (zero flux).
+ * Walls bounce species back too (zero flux); the membranes between
+ * domains of a confined species take the no-flux closure (pull_species).
  * Internal pressure nodes (Sec. 6.1, pressure boundary condition; reading
  * c30): where pmask is set, every pulled population is multiplied by
  * gamma = pressure_rho / rho before the moments are taken, so the node holds
@@ -399,12 +476,16 @@ static double reaction(const orc_params* P, int s, const double* phi, int S, uin
  * (s = mass_species; reading c32: the concentration-proportional source of
  * the validation Case III, on the pre-collision phi of the node).
  * fpost_*: 9 planes of N; gpost_*: S*5 planes; fx, fy may be NULL (no force);
- * rho, ux, uy, phi (S planes) may be NULL; msrc, pmask, lab may be NULL. */
+ * rho, ux, uy, phi (S planes) may be NULL; msrc, pmask, lab may be NULL.
+ * mom_in (3S planes: phi, jx, jy per species): the moments of the previous
+ * step for the no-flux closure of the confined species; mom_out receives
+ * this step's (either may be NULL). */
 void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost_out,
                       const double* gpost_in, double* gpost_out, const double* fx,
                       const double* fy, const uint8_t* src, double* rho_out, double* ux_out,
                       double* uy_out, double* phi_out, const int32_t* dom, const double* msrc,
-                      const uint8_t* pmask, const int32_t* lab) {
+                      const uint8_t* pmask, const int32_t* lab, const double* mom_in,
+                      double* mom_out) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     double tau = P->tau;
@@ -421,9 +502,14 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
             for (int s = 0; s < S; ++s) {
                 phi[s] = 0.0;
                 for (int q = 0; q < 5; ++q) {
-                    g[s][q] = pull_species(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny,
-                                           P->bc_y, dom, (P->noflux >> s) & 1);
+                    g[s][q] = pull_species(P, gpost_in + (long)s * 5 * N, OPP5, q, i, j, dom,
+                                           (P->noflux >> s) & 1, mom_in, s);
                     phi[s] += g[s][q];
+                }
+                if (mom_out) {  /* this step's moments, for the next step's closures */
+                    mom_out[(long)(3 * s) * N + idx] = phi[s];
+                    mom_out[(long)(3 * s + 1) * N + idx] = g[s][1] - g[s][3];
+                    mom_out[(long)(3 * s + 2) * N + idx] = g[s][2] - g[s][4];
                 }
             }
             const int beta_on = lab && lab[idx] > 0 && P->mass_beta != 0.0 &&
@@ -488,7 +574,8 @@ void orc_lattice_step(const orc_params* P, const double* fpost_in, double* fpost
  * NULL): the D2Q5 part of orc_lattice_step, used by the steady solve. */
 void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost_out,
                       const double* ux_in, const double* uy_in, const uint8_t* src,
-                      double* phi_out, const int32_t* dom) {
+                      double* phi_out, const int32_t* dom, const double* mom_in,
+                      double* mom_out) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     static const int OPP5[5] = {0, 3, 4, 1, 2};
@@ -501,9 +588,14 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
             for (int s = 0; s < S; ++s) {
                 phi[s] = 0.0;
                 for (int q = 0; q < 5; ++q) {
-                    g[s][q] = pull_species(gpost_in + (long)s * 5 * N, OPP5, q, i, j, nx, ny,
-                                           P->bc_y, dom, (P->noflux >> s) & 1);
+                    g[s][q] = pull_species(P, gpost_in + (long)s * 5 * N, OPP5, q, i, j, dom,
+                                           (P->noflux >> s) & 1, mom_in, s);
                     phi[s] += g[s][q];
+                }
+                if (mom_out) {
+                    mom_out[(long)(3 * s) * N + idx] = phi[s];
+                    mom_out[(long)(3 * s + 1) * N + idx] = g[s][1] - g[s][3];
+                    mom_out[(long)(3 * s + 2) * N + idx] = g[s][2] - g[s][4];
                 }
             }
             for (int s = 0; s < S; ++s) {
@@ -545,12 +637,16 @@ void orc_species_step(const orc_params* P, const double* gpost_in, double* gpost
  * membranes move).  nsrc: a static mass
  * source per node (the field S(x,t) of Fig. 1; NULL = none), added to the
  * cells' sources (a point source is one node of it).  pmask: internal
- * pressure nodes (NULL = none; see orc_lattice_step). */
+ * pressure nodes (NULL = none; see orc_lattice_step).  mom (3S planes,
+ * in/out, may be NULL): the species moments of the previous step that the
+ * no-flux closure reads (pull_species); NULL starts from the moments of the
+ * initial populations. */
 int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const double* L0,
             const double* k, const double* p, double tension, const uint8_t* src_flag,
             int n_steps, double* f, double* g, double* rho, double* ux, double* uy, double* phi,
             int32_t* id, uint8_t* src, double* fx, double* fy, double* Fv, const int32_t* dom,
-            const double* mrate, const double* marea, const uint8_t* pmask, const double* nsrc) {
+            const double* mrate, const double* marea, const uint8_t* pmask, const double* nsrc,
+            double* mom) {
     int nx = P->nx, ny = P->ny, S = P->n_species;
     long N = (long)nx * ny;
     int V = nc > 0 ? off[nc] : 0;
@@ -571,6 +667,17 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
         ((mrate || nsrc) && !Sn))
         return -1;
     for (int l = 0; l < V; ++l) partner[l] = -1;
+    /* the species moments of the previous step, for the no-flux closure:
+     * carried in mom (3S planes) across calls, else those of the initial
+     * populations */
+    double *ma = NULL, *mb = NULL;
+    if (S > 0 && P->noflux) {
+        ma = (double*)malloc(sizeof(double) * 3 * S * N);
+        mb = (double*)malloc(sizeof(double) * 3 * S * N);
+        if (!ma || !mb) return -1;
+        if (mom) memcpy(ma, mom, sizeof(double) * 3 * S * N);
+        else orc_species_moments(P, g, ma);
+    }
     double *fa = f, *fb = f2, *ga = g, *gb = g2;
     for (int n = 0; n < n_steps; ++n) {
         int last = (n == n_steps - 1);
@@ -599,7 +706,7 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
             for (long t = 0; t < N; ++t) Sn[t] += nsrc[t];
         orc_lattice_step(P, fa, fb, ga, gb, Fx, Fy, lsrc, last ? rho : NULL, Ux, Uy,
                          last ? phi : NULL, P->noflux_dynamic ? lid : dom, Sn, pmask,
-                         P->mass_beta != 0.0 ? lid : NULL);
+                         P->mass_beta != 0.0 ? lid : NULL, ma, mb);
         if (V > 0) {
             orc_interp(nx, ny, P->bc_y, V, xy, Ux, Uy, U);
             if (last && Fv) memcpy(Fv, F, sizeof(double) * 2 * V);
@@ -616,7 +723,10 @@ int orc_run(const orc_params* P, int nc, const int32_t* off, double* xy, const d
         double* t;
         t = fa; fa = fb; fb = t;
         t = ga; ga = gb; gb = t;
+        t = ma; ma = mb; mb = t;
     }
+    if (mom && ma) memcpy(mom, ma, sizeof(double) * 3 * S * N);
+    free(ma); free(mb);
     if (fa != f) memcpy(f, fa, sizeof(double) * 9 * N);
     if (S > 0 && ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
     free(f2); free(g2); free(Fx); free(Fy); free(Ux); free(Uy); free(F); free(U);
@@ -641,12 +751,12 @@ long orc_steady(const orc_params* P, const uint8_t* src, double* g, double tol, 
     long n = 0;
     while (n < max_steps) {
         int check = ((n + 1) % check_every) == 0;
-        orc_species_step(P, ga, gb, NULL, NULL, src, p0, NULL);
+        orc_species_step(P, ga, gb, NULL, NULL, src, p0, NULL, NULL, NULL);
         double* t = ga; ga = gb; gb = t;
         ++n;
         if (check) {
             /* phi^{n+1}: the zeroth moment of the populations just streamed */
-            orc_species_step(P, ga, gb, NULL, NULL, src, p1, NULL);
+            orc_species_step(P, ga, gb, NULL, NULL, src, p1, NULL, NULL, NULL);
             double dmax = 0.0, pmax = 0.0;
             for (long x = 0; x < S * N; ++x) {
                 double d = fabs(p1[x] - p0[x]);
@@ -658,7 +768,7 @@ long orc_steady(const orc_params* P, const uint8_t* src, double* g, double tol, 
         }
     }
     /* phi of the final state */
-    orc_species_step(P, ga, gb, NULL, NULL, src, phi, NULL);
+    orc_species_step(P, ga, gb, NULL, NULL, src, phi, NULL, NULL, NULL);
     if (ga != g) memcpy(g, ga, sizeof(double) * 5 * S * N);
     free(g2); free(p0); free(p1);
     if (resid_out) *resid_out = r;

@@ -1,6 +1,7 @@
 """Oracle pins for the Schnakenberg reaction (the Turing-patterning example,
-Sec. 4.2) and the membrane no-flux condition of confined species (Sec. 6.1,
-read as half-way bounce-back across domain boundaries; reading c26).
+Sec. 4.2) and the half-way bounce-back option for confined species
+(noflux_scheme 1; the paper's own no-flux closure of Sec. 6.1 is pinned in
+test_oracle_noflux_closure.py).
 
 What fixes each result (none of it retypes the oracle's update):
   - the homogeneous state R* = a + b, L* = b / (a + b)^2 makes both rates
@@ -10,10 +11,10 @@ What fixes each result (none of it retypes the oracle's update):
     uniform perturbation of the fixed point follows the linear map I + J with
     J the Jacobian of the rates, derived by hand:
         J = gamma [[-1 + 2 R* L*, R*^2], [-2 R* L*, -R*^2]];
-  - a confined species keeps its mass in every domain (no population crosses
-    a domain boundary), relaxes to the domain mean without reaction, and is
-    unaffected when every node carries the same label; a free species moves
-    mass between domains.
+  - a species confined by bounce-back keeps its mass in every domain (no
+    population crosses a domain boundary), relaxes to the domain mean
+    without reaction, and is unaffected when every node carries the same
+    label (under either scheme); a free species moves mass between domains.
 """
 import numpy as np
 import pytest
@@ -22,8 +23,9 @@ import lbib_inputs as li
 
 
 def _params(nx, ny, gamma=0.05, a=0.1, b=0.9, D=(0.1, 0.3), bc_y=li.BC_PERIODIC, noflux=0,
-            reaction=1):
+            reaction=1, scheme=1):
     p = li.LatticeParams(nx=nx, ny=ny, bc_y=bc_y, tau=1.0, rho0=1.0, n_species=2)
+    p.noflux_scheme = scheme
     p.D[0], p.D[1] = D
     p.reaction = reaction
     p.schnak = [gamma, a, b]
@@ -116,16 +118,20 @@ def test_noflux_relaxes_to_domain_mean(orc):
         assert np.abs(phi[0][dom == k] - m).max() < 1e-8 * m
 
 
-def test_noflux_single_domain_is_free(orc):
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_noflux_single_domain_is_free(orc, scheme):
     nx, ny = 16, 12
     rng = np.random.default_rng(7)
     g0 = rng.uniform(0.0, 1.0, size=(10, ny, nx))
     dom = np.zeros((ny, nx), np.int32)
-    pc = _params(nx, ny, noflux=3)
+    pc = _params(nx, ny, noflux=3, scheme=scheme)
     pf = _params(nx, ny, noflux=0)
     gc, gf = g0.copy(), g0.copy()
+    mom = orc.species_moments(pc, gc)
     for _ in range(20):
-        gc, phic = orc.species_step(pc, gc, dom=dom)
+        mo = np.empty_like(mom)
+        gc, phic = orc.species_step(pc, gc, dom=dom, mom=mom, mom_out=mo)
+        mom = mo
         gf, phif = orc.species_step(pf, gf)
     assert np.array_equal(phic, phif)
 

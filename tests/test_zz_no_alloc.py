@@ -36,9 +36,9 @@ def _split_state(blob, w, es, plane):
 
 def _lattice(raw, n_planes, plane, pitch, nx, ny, dtype=np.float64):
     """The nx*ny nodes of each plane (row and plane padding are never written)."""
-    v = raw.view(dtype).astype(np.float64)
+    v = raw.view(dtype)
     return np.stack([v[q * plane:q * plane + pitch * ny].reshape(ny, pitch)[:, :nx]
-                     for q in range(n_planes)])
+                     for q in range(n_planes)]).astype(np.float64)
 
 
 def _rel(a, b):
