@@ -61,6 +61,13 @@ extern "C" {
 #define LBIB_REACT_SCHNAKENBERG 1  /* species 0, 1 = receptor R, ligand L (Sec. 4.2):
                                       R_0 = gamma (a - R + R^2 L), R_1 = gamma (b - R^2 L) */
 
+/* membrane no-flux scheme of the confined species (noflux_mask) */
+#define LBIB_NOFLUX_CLOSURE 0     /* Sec. 6.1: the missing populations are equilibria of a
+                                     density extrapolated from, and a momentum interpolated
+                                     between, the fluid and the wall */
+#define LBIB_NOFLUX_BOUNCEBACK 1  /* half-way bounce-back (exact mass per domain; not the
+                                     paper's condition) */
+
 /* body-force scheme */
 #define LBIB_GUO 0        /* Guo, Zheng & Shi 2002: u = (sum f v + F/2)/rho */
 #define LBIB_HE_PAPER 1   /* the paper's term of Eq. bgkequation, 3 w_i v_i.F */
@@ -108,9 +115,18 @@ extern "C" {
  *                src_rate sources add to every species)
  *   noflux_mask  bit s: species s is confined to its domain: it does not
  *                cross the boundaries between the domains set with
- *                lbib_set_domains() (half-way bounce-back on every lattice
- *                link between nodes of different domains, the membrane
- *                no-flux condition of Sec. 6.1); 0 = no domain plane
+ *                lbib_set_domains(); 0 = no domain plane
+ *   noflux_scheme how a confined species meets a membrane.
+ *                LBIB_NOFLUX_CLOSURE, the paper's no-flux condition (Sec. 6.1):
+ *                a population that would arrive at x along v_q from another
+ *                domain is replaced by the D2Q5 equilibrium
+ *                w_q (phi^ + 3 v_q . j^) with phi^ = 2 phi(x + v_q) -
+ *                phi(x + 2 v_q) (first-order extrapolation) and j^ the first
+ *                moment at x + v_q scaled by 1/3 (first-order interpolation to
+ *                zero at the half-way point of the link), moments of the
+ *                previous step; first order, and each domain's mass is not
+ *                kept exactly.  LBIB_NOFLUX_BOUNCEBACK: half-way bounce-back on
+ *                every link between domains (each domain keeps its mass)
  *   junction_k, junction_l0, junction_lmax, junction_period
  *                cell junctions (Eq. celljunctionforce, Sec. 3.2.4): every
  *                junction_period steps (counted from lbib_set_cells or
@@ -157,7 +173,7 @@ typedef struct lbib_params {
     int32_t junction_period, junction_pad;
     int32_t mass_sources, pressure_nodes;
     double mass_alpha, pressure_rho;
-    int32_t node_sources, node_pad;
+    int32_t node_sources, noflux_scheme;
 } lbib_params;
 
 typedef struct lbib_ctx lbib_ctx;

@@ -23,30 +23,9 @@
 // of the node's cell.
 #include <type_traits>
 
-#include "lattice_node.cuh"
+#include "lattice_kernel.cuh"
 
 namespace lbib {
-
-// CTAs of 128 threads.  FP32/FP16 storage is held to 40 registers with at
-// most one species (12 CTAs, 48 warps per SM: more loads in flight), 48 with
-// two (10 CTAs) and 64 with more (8 CTAs), none of them spilling since the
-// in-plane indices are 32-bit (4096^2: 327 -> 311 us; 1024^2, two species:
-// 28.6 -> 27.8 us against 48 / 56 registers).
-template <typename T, int S>
-struct LatticeOccupancy {
-    static constexpr int kMinBlocks = sizeof(T) == 8 ? 1 : (S <= 1 ? 12 : (S == 2 ? 10 : 8));
-};
-constexpr int kLatticeThreads = 128;
-
-template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
-__global__ void __launch_bounds__(kLatticeThreads, LatticeOccupancy<T, S>::kMinBlocks)
-    lattice_kernel(LatticeArgs a, Coefs<C> k) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    constexpr bool GRIDDEP = true;
-    LBIB_LATTICE_NODE_BODY
-}
 
 // ---------------------------------------------------------------------------
 // FP16 storage, two nodes per thread.  One population of a node is two
@@ -309,8 +288,8 @@ static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, 
                                  k);
         }
     }
-    return launch_kernel(lattice_kernel<T, C, S, WALLS, FORCING, SC>, grid, block, 0, s, pdl, a,
-                         k);
+    return launch_kernel(lattice_kernel<T, C, S, WALLS, FORCING, SC, false>, grid, block, 0, s,
+                         pdl, a, k);
 }
 
 template <typename T, typename C, int S>
@@ -351,6 +330,10 @@ bool lattice_l2_first(int precision, int n_species, int64_t plane) {
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
                            const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s,
                            bool pdl, bool pairs) {
+    // confined species: the kernels with their paths compiled in
+    if (a.dom && n_species > 0)
+        return launch_lattice_confined(precision, n_species, bc_y, forcing, a, coefs, block, s,
+                                       pdl);
     if (precision == LBIB_FP64)
         return launch1<double, double>(n_species, bc_y, forcing, a, coefs, block, s, pdl, pairs);
     if (precision == LBIB_FP32)

@@ -77,6 +77,58 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
     g[4] = bu ? St::ld((B + 2 * P) + node, pol) : St::ld((B + 4 * P) + (rp + x), pol);
 }
 
+// The D2Q5 pull of a species confined by the paper's no-flux closure
+// (Sec. 6.1): a population whose source node lies in another domain (bit q
+// of the node's code) is the equilibrium w_q (phi^ + v_q.j(y1)) of the
+// previous step's moments M (planes phi, jx, jy of the species, compute
+// type): phi^ = 2 phi(y1) - phi(y2) extrapolated along the link from
+// y1 = x + v_q and y2 = x + 2 v_q, the momentum j(y1)/3 interpolated to zero
+// at the half-way wall point (times the 3 of the equilibrium); where y2 (or
+// y1) is not in the domain the density comes from y1 (or the node itself,
+// with no momentum).  Walls bounce back as in pull5.  In stored units:
+// unscaled storage keeps g, FP16 storage g / (w sigma_g) (isg = 1/sigma_g).
+// The moments were written by the lattice launch two launches back: read
+// through L2.
+template <typename T, typename C, bool WALLS, bool SCALED>
+__device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M, uint32_t code,
+                                              int node, int r0, int rm, int rp, int rmm, int rpp,
+                                              int x, int xm, int xp, int xmm, int xpp, bool lo,
+                                              bool hi, uint64_t pol, C isg, C g[5]) {
+    using St = Store<T, C>;
+    g[0] = St::ld(B + node, pol);
+#pragma unroll
+    for (int q = 1; q <= 4; ++q) {
+        if ((code >> (kNcodeMiss + q - 1)) & 1u) {
+            const int i1 = q == 1 ? r0 + xp : (q == 3 ? r0 + xm : (q == 2 ? rp + x : rm + x));
+            const int i2 = q == 1 ? r0 + xpp : (q == 3 ? r0 + xmm : (q == 2 ? rpp + x : rmm + x));
+            const bool in1 = (code >> (kNcodeIn1 + q - 1)) & 1u;
+            const bool in2 = (code >> (kNcodeIn2 + q - 1)) & 1u;
+            const C* Mj = M + (q == 1 || q == 3 ? P : 2 * P);
+            C ph, jc;
+            if (in1) {
+                const C p1 = __ldcg(M + i1);
+                const C j1 = __ldcg(Mj + i1);
+                ph = in2 ? C(2) * p1 - __ldcg(M + i2) : p1;
+                jc = (q == 1 || q == 2) ? j1 : -j1;
+            } else {
+                ph = __ldcg(M + node);
+                jc = C(0);
+            }
+            g[q] = SCALED ? (ph + jc) * isg : C(w5(q)) * (ph + jc);
+        } else if (q == 1) {
+            g[1] = St::ld((B + 1 * P) + (r0 + xm), pol);
+        } else if (q == 3) {
+            g[3] = St::ld((B + 3 * P) + (r0 + xp), pol);
+        } else if (q == 2) {
+            g[2] = (WALLS && lo) ? St::ld((B + 4 * P) + node, pol)
+                                 : St::ld((B + 2 * P) + (rm + x), pol);
+        } else {
+            g[4] = (WALLS && hi) ? St::ld((B + 2 * P) + node, pol)
+                                 : St::ld((B + 4 * P) + (rp + x), pol);
+        }
+    }
+}
+
 // The update of one node (x, y).  Callers map the 32 lanes of a warp to 32
 // consecutive nodes of one row starting at a multiple of 32 (lane = x mod
 // 32): lane 0 clears the warp's group-mask bits.
@@ -84,10 +136,12 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
 // kernel parameters (a separate inlined function measured 17% slower there,
 // with identical memory traffic); the ensemble's device function expands the
 // same text.  It uses the names a (LatticeArgs), k (Coefs<C>), x, y, the
-// template parameters T, C, S, WALLS, FORCING, SCALED and a constexpr bool
-// GRIDDEP: with it the population loads (written by the lattice launch two
-// launches back, read through L2) are issued before the programmatic wait on
-// the IB kernel whose force, label and mask planes the rest reads.
+// template parameters T, C, S, WALLS, FORCING, SCALED and two constexpr
+// bools: GRIDDEP, with which the population loads (written by the lattice
+// launch two launches back, read through L2) are issued before the
+// programmatic wait on the IB kernel whose force, label and mask planes the
+// rest reads; CONF, without which the paths of confined species (domain
+// planes, the no-flux closure and its moments) are compiled out.
 #define LBIB_LATTICE_NODE_BODY \
  \
     using St = Store<T, C>; \
@@ -126,16 +180,33 @@ __device__ __forceinline__ void pull5_confined(const T* B, int64_t P, const int3
         d[8] = St::ld((F + 8 * P) + (rp + xm), pol); \
     } \
     C g[S > 0 ? S : 1][5]; \
+    /* confined species: the node's closure code (the paper's no-flux */ \
+    /* closure) or its domain (half-way bounce-back) */ \
+    uint32_t ncode = 0u; \
+    if (CONF && a.ncode) ncode = a.ncode[node]; \
     { \
         const T* Gi = static_cast<const T*>(a.gsrc); \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
-            if (a.dom && ((a.noflux >> s) & 1)) \
-                pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, rp, \
-                                            x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
-            else \
+            if (CONF && a.dom && ((a.noflux >> s) & 1)) { \
+                if (a.ncode) { \
+                    const int ypp = (y + 2 >= a.ny) ? y + 2 - a.ny : y + 2; \
+                    const int ymm = (y < 2) ? y - 2 + a.ny : y - 2; \
+                    const int xpp = (x + 2 >= a.nx) ? x + 2 - a.nx : x + 2; \
+                    const int xmm = (x < 2) ? x - 2 + a.nx : x - 2; \
+                    pull5_closure<T, C, WALLS, SCALED>( \
+                        Gi + (int64_t)s * 5 * P, P, \
+                        static_cast<const C*>(a.mom_in) + (int64_t)s * 3 * P, ncode, node, r0, \
+                        rm, rp, ymm * (int)a.pitch, ypp * (int)a.pitch, x, xm, xp, xmm, xpp, \
+                        lo_wall, hi_wall, pol, k.isig_g, g[s]); \
+                } else { \
+                    pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, \
+                                                rp, x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
+                } \
+            } else { \
                 pull5<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, node, r0, rm, rp, x, xm, xp, \
                                    lo_wall, hi_wall, pol, g[s]); \
+            } \
         } \
     } \
     /* the IB kernel launched just before wrote the force, label and mask */ \
@@ -182,8 +253,31 @@ _Pragma("unroll") \
     if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
     if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
     const bool pn = a.pnode && a.pnode[node] != 0; \
+    /* the closure reads this node's moments next step: its species fluxes */ \
+    /* before the collision (the densities come out of collide_node) */ \
+    const bool mom_w = CONF && ((ncode >> kNcodeMom) & 1u); \
+    C mjx[S > 0 ? S : 1], mjy[S > 0 ? S : 1]; \
+    if (mom_w) { \
+_Pragma("unroll") \
+        for (int s = 0; s < S; ++s) { \
+            const C gs = SCALED ? k.gscale[1] : C(1); \
+            mjx[s] = gs * (g[s][1] - g[s][3]); \
+            mjy[s] = gs * (g[s][2] - g[s][4]); \
+        } \
+    } \
     collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph, \
                                         a.msrc != nullptr || a.nsrc != nullptr, ms, pn); \
+    if (mom_w) { \
+_Pragma("unroll") \
+        for (int s = 0; s < S; ++s) { \
+            if ((a.noflux >> s) & 1) { \
+                C* Mo = static_cast<C*>(a.mom_out) + (int64_t)s * 3 * P; \
+                Mo[node] = ph[s]; \
+                (Mo + P)[node] = mjx[s]; \
+                (Mo + 2 * P)[node] = mjy[s]; \
+            } \
+        } \
+    } \
     T* G = static_cast<T*>(a.fdst); \
 _Pragma("unroll") \
     for (int q = 0; q < 9; ++q) St::st((G + q * P) + node, d[q]); \
@@ -428,6 +522,7 @@ template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
                                              int y) {
     constexpr bool GRIDDEP = false;
+    constexpr bool CONF = false;  // the ensemble's tissues confine no species
     LBIB_LATTICE_NODE_BODY
 }
 

@@ -64,6 +64,11 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.smask = take((uint64_t)mask_words(l.plane) * 4);
     l.force_out = take(2 * P * l.cs);
     if (p.noflux_mask) l.dom = take(P * 4);
+    if (p.noflux_mask && p.noflux_scheme == LBIB_NOFLUX_CLOSURE) {
+        l.ncode = take(P * 2);
+        l.mom[0] = take((uint64_t)3 * p.n_species * P * l.cs);
+        l.mom[1] = take((uint64_t)3 * p.n_species * P * l.cs);
+    }
     if (p.mass_sources && max_cells > 0) {
         l.mrate = take((uint64_t)max_cells * 8);
         l.marea = take((uint64_t)max_cells * 8);
@@ -150,6 +155,10 @@ static int check_params(const lbib_params* p, std::string* why) {
     }
     if (p->noflux_mask < 0 || p->noflux_mask >= (1 << p->n_species)) {
         *why = "noflux_mask names a species that does not exist"; return LBIB_E_PARAM;
+    }
+    if (p->noflux_scheme != LBIB_NOFLUX_CLOSURE && p->noflux_scheme != LBIB_NOFLUX_BOUNCEBACK) {
+        *why = "noflux_scheme must be LBIB_NOFLUX_CLOSURE or LBIB_NOFLUX_BOUNCEBACK";
+        return LBIB_E_PARAM;
     }
     if (p->junction_period < 0 ||
         (p->junction_period > 0 &&
@@ -250,6 +259,11 @@ static LatticeArgs lattice_args(lbib_ctx* c, int src_buf, bool out) {
     if (c->p.noflux_mask) {
         a.dom = c->at<int32_t>(L.dom);
         a.noflux = c->p.noflux_mask;
+        if (L.ncode) {  // the closure: moments by the parity of the population buffers
+            a.ncode = c->at<uint16_t>(L.ncode);
+            a.mom_in = c->ws + L.mom[src_buf];
+            a.mom_out = c->ws + L.mom[1 - src_buf];
+        }
     }
     a.fmask = c->at<uint32_t>(L.fmask);
     a.lmask = c->at<uint32_t>(L.lmask);
@@ -326,6 +340,18 @@ IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
 // stream is the other kernel of the step (an IB launch before a lattice
 // launch and vice versa): each kernel's early loads rely on the launch two
 // back having completed, which the other kernel's wait guarantees.
+// The no-flux closure reads the species moments of the previous step; after
+// create, lbib_set_species, lbib_set_domains or lbib_set_state there is no
+// previous step, and the moments of the stored populations stand in.
+static cudaError_t ensure_moments(lbib_ctx* c) {
+    if (!c->L.ncode || c->mom_valid) return cudaSuccess;
+    cudaError_t e = launch_species_moments(c->p.precision, c->p.n_species, c->p.nx, c->p.ny,
+                                           c->L.pitch, c->L.plane, c->ws + c->L.g[c->cur],
+                                           c->ws + c->L.mom[c->cur], coefs_of(c), c->stream);
+    if (e == cudaSuccess) c->mom_valid = true;
+    return e;
+}
+
 static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl = false) {
     LatticeArgs a = lattice_args(c, src_buf, out);
     return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,
@@ -542,6 +568,9 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
     if (e == cudaSuccess) e = cudaMemsetAsync(c->ws + L.smask, 0, mask_words(L.plane) * 4, c->stream);
     if (e == cudaSuccess && params->noflux_mask)
         e = cudaMemsetAsync(c->ws + L.dom, 0, L.plane * 4, c->stream);
+    if (e == cudaSuccess && L.ncode)
+        e = launch_make_ncode(c->at<int32_t>(L.dom), c->at<uint16_t>(L.ncode), params->nx,
+                              params->ny, params->bc_y, L.pitch, c->stream);
     for (uint64_t off : {L.mrate, L.marea, L.msrc})
         if (e == cudaSuccess && off)
             e = cudaMemsetAsync(c->ws + off, 0, (size_t)8 * max_cells, c->stream);
@@ -650,8 +679,13 @@ int lbib_set_domains(lbib_ctx* c, const int32_t* labels) {
                               c->stream);
     else
         e = cudaMemsetAsync(c->ws + L.dom, 0, L.plane * 4, c->stream);
+    if (e == cudaSuccess && L.ncode)
+        e = launch_make_ncode(c->at<int32_t>(L.dom), c->at<uint16_t>(L.ncode), c->p.nx, c->p.ny,
+                              c->p.bc_y, L.pitch, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_domains");
+    // the moments were kept where the old closures read them
+    c->mom_valid = false;
     return LBIB_OK;
 }
 
@@ -777,6 +811,7 @@ int lbib_set_species(lbib_ctx* c, int32_t s, const double* phi) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_species");
     c->fields_valid = false;
+    c->mom_valid = false;
     return LBIB_OK;
 }
 
@@ -784,7 +819,8 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     if (!c) return LBIB_E_PARAM;
     if (n_steps < 0) return fail(c, LBIB_E_PARAM, "n_steps must be >= 0");
     if (n_steps == 0) return LBIB_OK;
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = ensure_moments(c);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
     const bool ib = c->nC > 0;
     if (ib && c->p.junction_period > 0) {
         e = run_with_junctions(c, n_steps, true, [](int, auto&& fn) { return fn(); });
@@ -830,8 +866,8 @@ int lbib_advance(lbib_ctx* c, int32_t n_steps) {
     const bool ib = c->nC > 0;
     // steps with junctions are launched one by one anyway
     if (ib && c->p.junction_period > 0) return lbib_step(c, n_steps);
-    cudaError_t e = cudaSuccess;
-    if (ib) e = enqueue_ib(c, false, true, false);
+    cudaError_t e = ensure_moments(c);
+    if (ib && e == cudaSuccess) e = enqueue_ib(c, false, true, false);
     int left = n_steps;
     // an odd count starts with one directly launched step (programmatic after
     // the prep); its IB launch moves, and preps unless it is the only step
@@ -864,7 +900,7 @@ int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
     const int n_launch = junctions ? 4 * n_steps + 2 : n_steps + (ib ? n_steps + 1 : 0);
     std::vector<cudaEvent_t> ev((size_t)2 * n_launch, nullptr);
     std::vector<int> kind((size_t)n_launch, 0);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = ensure_moments(c);
     for (auto& x : ev)
         if (e == cudaSuccess) e = cudaEventCreate(&x);
     int li = 0;
@@ -1003,11 +1039,16 @@ int lbib_get_sizes(const lbib_ctx* c, int32_t* n_vertices, int32_t* n_cells) {
 
 // state: populations of the current buffer (f then g), then xy, L0, k, off,
 // pres, srcf, then a small header {cur-independent}.
+// the no-flux closure's moments of the previous step (part of the state)
+static uint64_t mom_bytes(const lbib_ctx* c) {
+    return c->L.ncode ? (uint64_t)3 * c->p.n_species * c->L.plane * c->L.cs : 0;
+}
+
 static uint64_t state_bytes(const lbib_ctx* c) {
     const Layout& L = c->L;
     uint64_t P = (uint64_t)L.plane * L.es;
     return 16 + 9 * P + (uint64_t)5 * c->p.n_species * P + (uint64_t)c->maxV * 32 +
-           (uint64_t)(c->maxC + 1) * 4 + (uint64_t)c->maxC * 9;
+           (uint64_t)(c->maxC + 1) * 4 + (uint64_t)c->maxC * 9 + mom_bytes(c);
 }
 
 int lbib_state_size(const lbib_ctx* c, uint64_t* bytes_out) {
@@ -1021,6 +1062,10 @@ int lbib_get_state(lbib_ctx* c, void* host, uint64_t bytes) {
     if (bytes < state_bytes(c)) return fail(c, LBIB_E_PARAM, "state buffer too small");
     const Layout& L = c->L;
     char* h = static_cast<char*>(host);
+    {
+        cudaError_t em = ensure_moments(c);
+        if (em != cudaSuccess) return cuda_fail(c, em, "lbib_get_state");
+    }
     int32_t hdr[4] = {c->nV, c->nC, c->p.precision, c->p.n_species};
     std::memcpy(h, hdr, 16);
     uint64_t o = 16, P = (uint64_t)L.plane * L.es;
@@ -1028,7 +1073,7 @@ int lbib_get_state(lbib_ctx* c, void* host, uint64_t bytes) {
         {L.f[c->cur], 9 * P}, {L.g[c->cur], (uint64_t)5 * c->p.n_species * P},
         {L.xy, (uint64_t)c->maxV * 16}, {L.L0, (uint64_t)c->maxV * 8}, {L.k, (uint64_t)c->maxV * 8},
         {L.off, (uint64_t)(c->maxC + 1) * 4}, {L.pres, (uint64_t)c->maxC * 8},
-        {L.srcf, (uint64_t)c->maxC}};
+        {L.srcf, (uint64_t)c->maxC}, {L.mom[c->cur], mom_bytes(c)}};
     cudaError_t e = cudaSuccess;
     for (auto& pc : pieces) {
         if (pc.bytes && e == cudaSuccess)
@@ -1056,7 +1101,7 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
         {L.f[0], 9 * P}, {L.g[0], (uint64_t)5 * c->p.n_species * P},
         {L.xy, (uint64_t)c->maxV * 16}, {L.L0, (uint64_t)c->maxV * 8}, {L.k, (uint64_t)c->maxV * 8},
         {L.off, (uint64_t)(c->maxC + 1) * 4}, {L.pres, (uint64_t)c->maxC * 8},
-        {L.srcf, (uint64_t)c->maxC}};
+        {L.srcf, (uint64_t)c->maxC}, {L.mom[0], mom_bytes(c)}};
     cudaError_t e = cudaSuccess;
     for (auto& pc : pieces) {
         if (pc.bytes && e == cudaSuccess)
@@ -1084,6 +1129,7 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
     c->nstep = 0;
     c->fields_valid = false;
     c->vforce_valid = false;
+    c->mom_valid = true;  // restored with the populations
     drop_graphs(c);
     return LBIB_OK;
 }

@@ -26,6 +26,7 @@ struct lbib_ctx {
     bool lattice_pairs = true;  // FP16 storage: two nodes per thread where possible
     int64_t nstep = 0;          // steps since lbib_set_cells / lbib_set_state (junction renewal)
     bool l2_first = false;      // population loads evict-first (lattice nearly fits in L2)
+    bool mom_valid = false;     // the no-flux closure's moments of buffer `cur` are current
     // graph of a two-step chunk, keyed by the buffer parity it starts from
     cudaGraphExec_t chunk[2] = {nullptr, nullptr};
     // the same two steps whose last IB launch only moves (the end of an

@@ -35,6 +35,15 @@ constexpr int kMaxRows = 128;           // scanline rows per cell (else brute fo
 constexpr int kMaxCross = 8;            // crossings per scanline row (else brute force)
 constexpr uint32_t kOutside = 0xFFFFFFFFu;
 
+// Bits of the 16-bit no-flux closure code of a node (direction q = 1..4 of
+// D2Q5): the population arriving along v_q comes from another domain (not a
+// wall link); x + v_q lies in the node's domain; x + 2 v_q does too; some
+// closure reads this node's moments.
+constexpr int kNcodeMiss = 0;    // bits 0..3
+constexpr int kNcodeIn1 = 4;     // bits 4..7
+constexpr int kNcodeIn2 = 8;     // bits 8..11
+constexpr int kNcodeMom = 12;    // bit 12
+
 // diagnostic words at the start of the diag region
 enum Diag : int {
     kDiagNonFinite = 0,   // a non-finite rho or u was produced
@@ -54,6 +63,10 @@ struct Layout {
     uint64_t xy = 0, L0 = 0, k = 0, vforce = 0, off = 0, pres = 0, srcf = 0, area = 0;
     uint64_t vbase = 0, vfrac = 0, fmask = 0, lmask = 0, src = 0, smask = 0;
     uint64_t dom = 0;          // domain labels of the confined species (noflux_mask != 0)
+    // the no-flux closure of Sec. 6.1 (noflux_scheme 0): a 16-bit code per
+    // node (kNcode* bits) and the species moments (phi, jx, jy per species,
+    // compute type, plane stride `plane`) of the previous step, by parity
+    uint64_t ncode = 0, mom[2] = {0, 0};
     // cell junctions (junction_period > 0): partner and cell of every vertex, bins
     uint64_t jpartner = 0, jcell = 0, jcnt = 0, jstart = 0, jvbin = 0, jent = 0;
     uint64_t mrate = 0, marea = 0, msrc = 0;  // per-cell mass source data (mass_sources)
@@ -106,7 +119,14 @@ struct LatticeArgs {
     int ib;             // read/clear force and labels
     int l2_first;       // population loads evict-first in L2 (else normal)
     const int32_t* dom; // domain label per node (pitch layout), NULL = none
-    int noflux;         // bit s: species s bounces back between different domains
+    int noflux;         // bit s: species s is confined to its domain
+    // the no-flux closure (Sec. 6.1) of the confined species: the node codes
+    // (NULL: half-way bounce-back on the links between domains instead), the
+    // moments of the previous step (read at the closures) and of this step
+    // (written where the code asks for them); 3 planes per species
+    const uint16_t* ncode;
+    const void* mom_in;
+    void* mom_out;
     // 1 bit per 4 consecutive nodes (node index >> 2): groups that received
     // spread force / labels / source bits this step.  fmask NULL = dense
     // (read every node).
@@ -349,6 +369,11 @@ bool lattice_l2_first(int precision, int n_species, int64_t plane);
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
                            const LatticeArgs& a, const void* coefs, dim3 block,
                            cudaStream_t s, bool pdl = false, bool pairs = true);
+// the same with confined species (a.dom set, n_species >= 1): one node per
+// thread, the confinement paths compiled in (launch_lattice calls it)
+cudaError_t launch_lattice_confined(int precision, int n_species, int bc_y, int forcing,
+                                    const LatticeArgs& a, const void* coefs, dim3 block,
+                                    cudaStream_t s, bool pdl);
 // maxv_cell: the largest vertex count of a cell (sizes shared memory and the CTA)
 cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s,
                       bool pdl = false);
@@ -359,6 +384,14 @@ cudaError_t launch_junction_renew(const JunctionArgs& j, cudaStream_t s);
 cudaError_t launch_init_populations(int precision, int n_species, int nx, int ny,
                                     int64_t pitch, int64_t plane, void* f, void* g,
                                     cudaStream_t s);
+// the closure codes of every node from the domain labels (pitch layout)
+cudaError_t launch_make_ncode(const int32_t* dom, uint16_t* ncode, int nx, int ny, int bc_y,
+                              int64_t pitch, cudaStream_t s);
+// the species moments (phi, jx, jy per species; compute type) of the stored
+// populations g at every node (the moments a run starts from)
+cudaError_t launch_species_moments(int precision, int n_species, int nx, int ny, int64_t pitch,
+                                   int64_t plane, const void* g, void* mom, const void* coefs,
+                                   cudaStream_t s);
 cudaError_t launch_set_species(int precision, int n_species, int s_idx, int nx, int ny,
                                int64_t pitch, int64_t plane, const double* phi, void* g,
                                const void* coefs, cudaStream_t s);

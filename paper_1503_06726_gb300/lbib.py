@@ -32,6 +32,7 @@ LBIB_E_STATE = -7
 LBIB_FP64, LBIB_FP32, LBIB_FP16 = 0, 1, 2
 LBIB_GUO, LBIB_HE_PAPER = 0, 1
 LBIB_REACT_LINEAR, LBIB_REACT_SCHNAKENBERG = 0, 1
+LBIB_NOFLUX_CLOSURE, LBIB_NOFLUX_BOUNCEBACK = 0, 1
 LBIB_RHO, LBIB_U, LBIB_PHI, LBIB_X = 1, 2, 4, 8
 LBIB_AREA, LBIB_ID, LBIB_FORCE, LBIB_VFORCE = 16, 32, 64, 128
 
@@ -78,7 +79,7 @@ class lbib_params(ctypes.Structure):
         ("junction_pad", ctypes.c_int32),
         ("mass_sources", ctypes.c_int32), ("pressure_nodes", ctypes.c_int32),
         ("mass_alpha", ctypes.c_double), ("pressure_rho", ctypes.c_double),
-        ("node_sources", ctypes.c_int32), ("node_pad", ctypes.c_int32),
+        ("node_sources", ctypes.c_int32), ("noflux_scheme", ctypes.c_int32),
     ]
 
 
@@ -208,6 +209,7 @@ def make_params(p, precision: int = LBIB_FP64) -> lbib_params:
     o.pressure_nodes = int(getattr(p, "pressure_nodes", 0) or 0)
     o.pressure_rho = float(getattr(p, "pressure_rho", 0.0) or 0.0)
     o.node_sources = int(getattr(p, "node_sources", 0) or 0)
+    o.noflux_scheme = int(getattr(p, "noflux_scheme", 0) or 0)
     if float(getattr(p, "mass_beta", 0.0) or 0.0) != 0.0 or int(getattr(p, "noflux_dynamic", 0) or 0):
         raise ValueError("the concentration-proportional mass source and confinement by moving "
                          "membranes have no CUDA path")

@@ -1,19 +1,24 @@
 """GPU parity of the Schnakenberg reaction (Sec. 4.2) and of confined species
-(the membrane no-flux condition, Sec. 6.1, read as half-way bounce-back
-between domains; reading c26) against the FP64 oracle.
+against the FP64 oracle, under the paper's no-flux closure (Sec. 6.1: the
+missing populations are equilibria of an extrapolated density and an
+interpolated momentum of the previous step; reading c26) and under the
+half-way bounce-back option.
 
   - static cellular domain, fluid at rest, receptor confined, ligand free,
     Schnakenberg kinetics from a perturbed homogeneous state: FP64 storage
-    within 1e-10 (relative L-infinity on phi) and FP32 within 1e-5 after 300
-    steps; FP16 shifted storage (one node per thread: confined species read
-    their neighbours' domains) within 5e-3 after 30 steps.  FP16 stores the
-    species undeviated with 4.9e-4 relative precision, and near this
-    Turing-unstable state the kinetics amplify its rounding (measured 2.0e-3
-    after 30 steps, 7.4e-2 after 300 with the receptor confined, 1.4e-2
-    without; 7.8e-3 after 300 steps with confinement and no reaction), so
-    the FP16 check stops before the amplification dominates;
-  - the confined species keeps its mass in every domain on the GPU (FP64,
-    no reaction, 1e-12 relative);
+    within 1e-10 (relative L-infinity on phi) under either scheme, FP32
+    within 1e-5 after 300 steps; FP16 shifted storage (one node per thread:
+    confined species read their neighbours' domains) within 5e-3 after 30
+    steps.  FP16 stores the species undeviated with 4.9e-4 relative
+    precision, and near this Turing-unstable state the kinetics amplify its
+    rounding (measured 2.0e-3 after 30 steps, 7.4e-2 after 300 with the
+    receptor confined, 1.4e-2 without), so the FP16 check stops before the
+    amplification dominates;
+  - the closure carries the previous step's moments across calls: split
+    calls, lbib_advance and a state round trip give the one-call result
+    (FP64, 1e-10); a domain that touches the walls too;
+  - under bounce-back the confined species keeps its mass in every domain on
+    the GPU (FP64, no reaction, 1e-12 relative);
   - moving cells with static domains (the coupled step, walls, sources):
     FP64 within 1e-10 after 60 steps;
   - lbib_set_domains needs a context created with confined species.
@@ -53,8 +58,9 @@ def _domains(nx, ny):
     return idp.astype(np.int32)
 
 
-def _schnak_params(nx, ny, noflux=1, reaction=1):
-    p = li.LatticeParams(nx=nx, ny=ny, tau=1.0, rho0=1.0, n_species=2)
+def _schnak_params(nx, ny, noflux=1, reaction=1, scheme=0, bc_y=li.BC_PERIODIC):
+    p = li.LatticeParams(nx=nx, ny=ny, bc_y=bc_y, tau=1.0, rho0=1.0, n_species=2)
+    p.noflux_scheme = scheme
     p.D[0], p.D[1] = 0.05, 0.4
     p.reaction = reaction
     p.schnak = [0.02, 0.1, 0.9]
@@ -75,12 +81,24 @@ def _initial_phi(p, seed):
     return np.stack([R, L])
 
 
-def _gpu_species_run(lb, p, prec, dom, phi0, n):
+def _gpu_species_run(lb, p, prec, dom, phi0, n, calls=None):
+    """n steps (in the given pieces: ('step', k), ('advance', k) or
+    ('state', 0), a get/set state round trip into a new context)."""
     sim = lb.Simulation(p, prec, 0, 0)
     sim.set_domains(dom)
     for s in range(p.n_species):
         sim.set_species(s, phi0[s])
-    sim.step(n)
+    for kind, k in (calls or [("step", n)]):
+        if kind == "step":
+            sim.step(k)
+        elif kind == "advance":
+            sim.advance(k)
+        else:
+            st = sim.get_state()
+            sim.close()
+            sim = lb.Simulation(p, prec, 0, 0)
+            sim.set_domains(dom)
+            sim.set_state(st)
     out = sim.fields(lb.LBIB_PHI | lb.LBIB_U)
     sim.close()
     return out
@@ -93,11 +111,11 @@ def _oracle_species_run(orc, p, dom, phi0, n):
     return r
 
 
-@pytest.mark.parametrize("prec,n,tol", [("fp64", 300, 1e-10), ("fp32", 300, 1e-5),
-                                        ("fp16", 30, 5e-3)])
-def test_schnakenberg_static_domains_vs_oracle(lb, orc, prec, n, tol):
+@pytest.mark.parametrize("prec,n,tol,scheme", [("fp64", 300, 1e-10, 0), ("fp64", 300, 1e-10, 1),
+                                               ("fp32", 300, 1e-5, 0), ("fp16", 30, 5e-3, 0)])
+def test_schnakenberg_static_domains_vs_oracle(lb, orc, prec, n, tol, scheme):
     nx, ny = 96, 80
-    p = _schnak_params(nx, ny)
+    p = _schnak_params(nx, ny, scheme=scheme)
     dom = _domains(nx, ny)
     phi0 = _initial_phi(p, 11)
     ref = _oracle_species_run(orc, p, dom, phi0, n)
@@ -108,9 +126,45 @@ def test_schnakenberg_static_domains_vs_oracle(lb, orc, prec, n, tol):
     assert np.abs(got["ux"]).max() < 1e-12 and np.abs(got["uy"]).max() < 1e-12
 
 
+@pytest.mark.parametrize("calls", [
+    [("step", 7), ("step", 1), ("step", 52)],
+    [("advance", 9), ("step", 20), ("advance", 30), ("step", 1)],
+    [("step", 25), ("state", 0), ("step", 35)],
+])
+def test_closure_across_calls_fp64(lb, orc, calls):
+    nx, ny = 64, 48
+    p = _schnak_params(nx, ny, scheme=0)
+    dom = _domains(nx, ny)
+    phi0 = _initial_phi(p, 21)
+    n = sum(k for _, k in calls)
+    ref = _oracle_species_run(orc, p, dom, phi0, n)
+    got = _gpu_species_run(lb, p, lb.LBIB_FP64, dom, phi0, n, calls)
+    assert rel(got["phi"][0], ref.phi[0]) < 1e-10 and rel(got["phi"][1], ref.phi[1]) < 1e-10
+
+
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_closure_with_walls_fp64(lb, orc, scheme):
+    """Domains that touch the no-slip walls: the wall links reflect, the
+    membrane links take the scheme, and the closure's fluid nodes stop at
+    the walls."""
+    nx, ny = 64, 40
+    p = _schnak_params(nx, ny, scheme=scheme, bc_y=li.BC_WALLS)
+    dom = np.zeros((ny, nx), np.int32)
+    dom[0:14, 10:30] = 1      # on the lower wall
+    dom[30:40, 5:60] = 2      # on the upper wall
+    dom[15:24, 35:37] = 3     # two nodes wide
+    dom[20, 45] = 4           # one node
+    phi0 = _initial_phi(p, 23)
+    ref = _oracle_species_run(orc, p, dom, phi0, 80)
+    got = _gpu_species_run(lb, p, lb.LBIB_FP64, dom, phi0, 80)
+    assert rel(got["phi"][0], ref.phi[0]) < 1e-10 and rel(got["phi"][1], ref.phi[1]) < 1e-10
+
+
 def test_confined_species_keeps_domain_mass(lb):
+    """Half-way bounce-back (the option, not the paper's closure) keeps every
+    domain's mass of the confined species."""
     nx, ny = 96, 80
-    p = _schnak_params(nx, ny, noflux=1, reaction=0)
+    p = _schnak_params(nx, ny, noflux=1, reaction=0, scheme=1)
     dom = _domains(nx, ny)
     rng = np.random.default_rng(12)
     phi0 = rng.uniform(0.2, 1.0, size=(2, ny, nx))
