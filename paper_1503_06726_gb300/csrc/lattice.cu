@@ -369,7 +369,7 @@ __global__ void set_species_kernel(int nx, int ny, int64_t pitch, int64_t plane,
     if (x >= nx || y >= ny) return;
     double v = phi[(int64_t)y * nx + x];
     for (int q = 0; q < 5; ++q) {
-        C gq = C(w5(q) * v);
+        C gq = k.w5c[q == 0 ? 0 : 1] * C(v);
         if (scaled) gq *= k.ginv[q];
         Store<T, C>::st(g + q * plane + (int64_t)y * pitch + x, gq);
     }

@@ -93,7 +93,7 @@ template <typename T, typename C, bool WALLS, bool SCALED>
 __device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M, uint32_t code,
                                               int node, int r0, int rm, int rp, int rmm, int rpp,
                                               int x, int xm, int xp, int xmm, int xpp, bool lo,
-                                              bool hi, uint64_t pol, C isg, C g[5]) {
+                                              bool hi, uint64_t pol, C isg, C wq, C g[5]) {
     using St = Store<T, C>;
     g[0] = St::ld(B + node, pol);
 #pragma unroll
@@ -114,7 +114,7 @@ __device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M,
                 ph = __ldcg(M + node);
                 jc = C(0);
             }
-            g[q] = SCALED ? (ph + jc) * isg : C(w5(q)) * (ph + jc);
+            g[q] = SCALED ? (ph + jc) * isg : wq * (ph + jc);
         } else if (q == 1) {
             g[1] = St::ld((B + 1 * P) + (r0 + xm), pol);
         } else if (q == 3) {
@@ -198,7 +198,7 @@ _Pragma("unroll") \
                         Gi + (int64_t)s * 5 * P, P, \
                         static_cast<const C*>(a.mom_in) + (int64_t)s * 3 * P, ncode, node, r0, \
                         rm, rp, ymm * (int)a.pitch, ypp * (int)a.pitch, x, xm, xp, xmm, xpp, \
-                        lo_wall, hi_wall, pol, k.isig_g, g[s]); \
+                        lo_wall, hi_wall, pol, k.isig_g, k.w5c[1], g[s]); \
                 } else { \
                     pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, \
                                                 rp, x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
@@ -429,7 +429,7 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
         const V gm1 = L::sub(gam, L::c(C(1)));
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-            d[q] = L::fma(gam, d[q], L::mul(gm1, L::c(SCALED ? k.rho0 * k.isig : C(w9(q)) * k.rho0)));
+            d[q] = L::fma(gam, d[q], L::mul(gm1, L::c(SCALED ? k.rho0 * k.isig : k.w9c[q == 0 ? 0 : (q < 5 ? 1 : 2)] * k.rho0)));
         drho = L::c(k.prho - k.rho0);
         jx = L::mul(gam, jx);
         jy = L::mul(gam, jy);
@@ -454,12 +454,12 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
     // mass source (Sec. 3.2.3): w_q S added to every direction, no momentum
     if (mass_on) E0 = L::add(E0, ms);
     const V omc = L::c(k.omc);
-    d[0] = L::fma(L::c(SCALED ? k.isig : C(w9(0))), E0, L::mul(omc, d[0]));
+    d[0] = L::fma(L::c(SCALED ? k.isig : k.w9c[0]), E0, L::mul(omc, d[0]));
 #pragma unroll
     for (int q = 1; q < 9; ++q) {
         if (q == 1 || q == 2 || q == 5 || q == 6) {
             const int o = q + 2;  // opposite of 1, 2, 5, 6
-            const V ew = L::c(SCALED ? k.isig : C(w9(q)));
+            const V ew = L::c(SCALED ? k.isig : k.w9c[q < 5 ? 1 : 2]);
             // v.u and v.F of v = (1,0), (0,1), (1,1), (-1,1)
             const V cu = q == 1 ? ux : (q == 2 ? uy : (q == 5 ? L::add(ux, uy) : L::sub(uy, ux)));
             const V cF = q == 1 ? Fx : (q == 2 ? Fy : (q == 5 ? L::add(Fx, Fy) : L::sub(Fy, Fx)));
@@ -503,8 +503,8 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
                 for (int b = 0; b < S; ++b) R = L::fma(L::c(k.K[s][b]), ph[b], R);
             }
             const V ev = L::fma(L::c(k.omegaD[s]), ph[s], R);
-            const C eA = SCALED ? k.isig_g : C(w5(0));
-            const C eB = SCALED ? k.isig_g : C(w5(1));
+            const C eA = SCALED ? k.isig_g : k.w5c[0];
+            const C eB = SCALED ? k.isig_g : k.w5c[1];
             const V evB = L::mul(L::c(eB), ev);
             const V o3 = L::mul(L::c(C(3) * eB * k.omegaD[s]), ph[s]);
             const V ox = L::mul(o3, ux), oy = L::mul(o3, uy);

@@ -209,13 +209,16 @@ static void fill_coefs(const lbib_params& p, Coefs<C>* k) {
     const bool scaled = p.precision == LBIB_FP16;
     k->isig = (C)(scaled ? 1.0 / sf : 1.0);
     k->isig_g = (C)(scaled ? 1.0 / sg : 1.0);
+    exact_sum_weights<C>(k->w9c, k->w5c);
     for (int q = 0; q < 9; ++q) {
-        k->fscale[q] = (C)(scaled ? w9(q) * sf : 1.0);
-        k->finv[q] = (C)(scaled ? 1.0 / (w9(q) * sf) : 1.0);
+        const double wq = (double)k->w9c[q == 0 ? 0 : (q < 5 ? 1 : 2)];
+        k->fscale[q] = (C)(scaled ? wq * sf : 1.0);
+        k->finv[q] = (C)(scaled ? 1.0 / (wq * sf) : 1.0);
     }
     for (int q = 0; q < 5; ++q) {
-        k->gscale[q] = (C)(scaled ? w5(q) * sg : 1.0);
-        k->ginv[q] = (C)(scaled ? 1.0 / (w5(q) * sg) : 1.0);
+        const double wq = (double)k->w5c[q == 0 ? 0 : 1];
+        k->gscale[q] = (C)(scaled ? wq * sg : 1.0);
+        k->ginv[q] = (C)(scaled ? 1.0 / (wq * sg) : 1.0);
     }
 }
 

@@ -67,9 +67,13 @@ __global__ void __launch_bounds__(256) steady_update(SteadyArgs a) {
     const float R = ((s & 1u) ? a.srate[b] : 0.f) - a.decay[b] * phi;
     const float om = a.omegaD[b];
     float* O = a.gdst + (int64_t)b * a.tstride;
+    // weights that sum to one exactly in FP32 (1 - 4 w1 is exact): the
+    // update creates no mass from their rounding
+    constexpr float w1 = (float)(1.0 / 6.0);
+    constexpr float w0 = 1.0f - 4.0f * w1;
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
-        const float w = (float)w5(q);
+        const float w = q == 0 ? w0 : w1;
         O[q * P + node] = g[q] + om * (phi * w - g[q]) + w * R;
     }
     if (a.store_prev) a.phi_prev[(int64_t)b * a.nx * a.ny + (int64_t)y * a.nx + x] = phi;
@@ -185,7 +189,9 @@ __global__ void steady_init(int batch, int nx, int ny, int64_t pitch, int64_t pl
     if (x >= nx) return;
     const float v = phi0 ? phi0[(int64_t)b * nx * ny + (int64_t)y * nx + x] : 0.f;
     float* G = g + (int64_t)b * tstride;
-    for (int q = 0; q < 5; ++q) G[q * plane + (int64_t)y * pitch + x] = (float)w5(q) * v;
+    constexpr float w1 = (float)(1.0 / 6.0);
+    constexpr float w0 = 1.0f - 4.0f * w1;
+    for (int q = 0; q < 5; ++q) G[q * plane + (int64_t)y * pitch + x] = (q == 0 ? w0 : w1) * v;
 }
 
 struct SteadyLayout {
