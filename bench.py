@@ -467,7 +467,7 @@ def run_precision(args, rank, world, dist):
     w = li.config3()
     p, T = w.params, w.tissue
     n = args.prec_steps
-    which = lbib.LBIB_U | lbib.LBIB_PHI | lbib.LBIB_X | lbib.LBIB_AREA
+    which = lbib.LBIB_U | lbib.LBIB_PHI | lbib.LBIB_X | lbib.LBIB_AREA | lbib.LBIB_ID
     res, secs = {}, {}
     area0 = None
     for name, prec in (("fp64", lbib.LBIB_FP64), ("fp32", lbib.LBIB_FP32),
@@ -488,14 +488,48 @@ def run_precision(args, rank, world, dist):
     ref = res["fp64"]
     umax = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max())
     pmax = np.abs(ref["phi"]).max()
+    # nodes at least three nodes from any membrane (uniform 7x7 label block):
+    # away from the source cells' edges, whose source bits flip between runs
+    # when a node centre lies within the vertex-position error of an edge
+    lab = ref["id"]
+    away = np.ones_like(lab, bool)
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            away &= np.roll(np.roll(lab, dy, 0), dx, 1) == lab
 
     def errs(r):
         du = max(np.abs(r["ux"] - ref["ux"]).max(), np.abs(r["uy"] - ref["uy"]).max())
+        dp = np.abs(r["phi"] - ref["phi"])[0]
         return {"u_rel_linf": float(du / umax),
-                "phi_rel_linf": float(np.abs(r["phi"] - ref["phi"]).max() / pmax),
+                "phi_rel_linf": float(dp.max() / pmax),
+                "phi_rel_linf_away_from_membranes": float(dp[away].max() / pmax),
+                "labels_differ_at_end": int((r["id"] != ref["id"]).sum()),
                 "x_abs_linf_lu": float(np.abs(r["xy"] - ref["xy"]).max()),
                 "area_rel_linf_vs_fp64": float(np.abs(r["area"] - ref["area"]).max() /
                                                np.abs(ref["area"]).max())}
+
+    # the same tissue scaled to 512^2, against the FP64 oracle itself (it
+    # runs the 2000 steps in about a minute on the host cores)
+    ws = li.config3(n=512)
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oref = oracle.run(ws.params, ws.tissue, n)
+    osec = time.perf_counter() - t0
+    oerr = {}
+    for name, prec in (("fp32", lbib.LBIB_FP32), ("fp16", lbib.LBIB_FP16)):
+        sim = lbib.Simulation(ws.params, prec, ws.tissue.n_vertices, ws.tissue.n_cells,
+                              device=dev)
+        sim.set_cells(ws.tissue)
+        sim.step(n)
+        r = sim.fields(which)
+        sim.close()
+        ou = max(np.abs(oref.ux).max(), np.abs(oref.uy).max())
+        oerr[name] = {
+            "u_rel_linf": float(max(np.abs(r["ux"] - oref.ux).max(),
+                                    np.abs(r["uy"] - oref.uy).max()) / ou),
+            "phi_rel_linf": float(np.abs(r["phi"] - oref.phi).max() / np.abs(oref.phi).max()),
+            "x_abs_linf_lu": float(np.abs(r["xy"] - oref.xy).max())}
 
     def drift(r):
         d = (r["area"] - area0) / area0
@@ -512,6 +546,8 @@ def run_precision(args, rank, world, dist):
         "data": "synthetic (seeded tissue generator)",
         "config": workload_config(w, "fp64/fp32/fp16"),
         "errors_vs_fp64": {"fp32": errs(res["fp32"]), "fp16": errs(res["fp16"])},
+        "errors_vs_oracle_512sq": dict(oerr, workload=ws.name, steps=n,
+                                       oracle_seconds=osec),
         "area_drift": {k: drift(v) for k, v in res.items()},
         "field_scale": {"u_max": float(umax), "phi_max": float(pmax)},
         "seconds": secs,

@@ -188,6 +188,25 @@ def test_reduced_precision_walls_two_species(lb, orc, prec, tu, tp):
     assert ex < (1e-6 if prec == "fp32" else 1e-3)
 
 
+def test_precision_paths_512sq_2000_steps(lb, orc):
+    """The precision-sweep tissue scaled to 512^2 (144 cells) over the sweep's
+    own length, 2000 steps, against the FP64 oracle: FP32 storage within
+    u 1e-4, phi 1e-5 (relative L-infinity), X 1e-5 LU; FP16 shifted storage
+    within u 3e-2, phi 1e-2, X 1e-3 LU.  Measured: FP32 u 8.0e-5, phi 2.0e-6,
+    X 3.2e-6; FP16 u 3.6e-3, phi 4.9e-3, X 3.9e-4 (against the FP64 GPU path,
+    which matches the oracle to 1e-10)."""
+    w = li.config3(n=512)
+    ref = orc.run(w.params, w.tissue, 2000)
+    for prec, tu, tp, tx in ((lb.LBIB_FP32, 1e-4, 1e-5, 1e-5),
+                             (lb.LBIB_FP16, 3e-2, 1e-2, 1e-3)):
+        got = gpu_run(lb, w, 2000, prec, which=1 | 2 | 4 | 8)
+        eu = max(rel(got["ux"], ref.ux), rel(got["uy"], ref.uy))
+        ep = rel(got["phi"], ref.phi)
+        ex = np.abs(got["xy"] - ref.xy).max()
+        print(f"precision {prec}: u {eu:.3e} phi {ep:.3e} X {ex:.3e}")
+        assert eu < tu and ep < tp and ex < tx
+
+
 # ------------------------------------------------------------------ full sizes
 def test_config2_full_size_first_steps(lb, orc):
     """1024^2 walls, 400 cells, 2 species in FP32 (the benchmarked
