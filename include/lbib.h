@@ -294,6 +294,23 @@ int lbib_get_fields(lbib_ctx* ctx, uint32_t which, double* rho, double* ux, doub
                     double* phi, double* xy, double* area, int32_t* id, double* force,
                     double* vforce);
 
+/* FP64 conservation sums of the last step's fields (the per-cell and global
+ * budgets beside the per-cell area of Sec. 3.3, computeAreas), computed on
+ * the device from the output of the last lbib_step() (LBIB_E_STATE after
+ * lbib_advance() or before any step) and copied to host buffers;
+ * synchronises the stream:
+ *   global_sums  3 + n_species doubles: sum rho, sum rho ux, sum rho uy and
+ *                sum phi_s over every node (rho u as in LBIB_U: with Guo
+ *                forcing it includes half the node's force)
+ *   cell_sums    may be NULL, n_cells x (1 + n_species) doubles, row c: sum
+ *                rho and sum phi_s over the nodes whose label is cell c (the
+ *                lowest cell containing the node, as LBIB_ID)
+ *   nonfinite    may be NULL: the number of nodes with a non-finite or
+ *                non-positive density or a non-finite velocity or
+ *                concentration
+ * Accumulated in FP64 (atomic order not fixed: sums agree to rounding). */
+int lbib_get_sums(lbib_ctx* ctx, double* global_sums, double* cell_sums, uint32_t* nonfinite);
+
 /* Run n_steps coupled steps like lbib_step(), launching each kernel
  * directly (no graph) with CUDA events recorded on the context stream around
  * every launch, and return the summed device time in milliseconds of the

@@ -17,6 +17,9 @@ Parity status per function (what pins it; see tests/test_oracle_pins.py):
                      variance growth 2Dt
   run (coupled)      invariants above; the coupled trajectory itself is
                      parity unpinned beyond them (no printed trajectory)
+  sums               global mass conserved on a periodic lattice, global
+                     momentum (n - 1/2) N F under a uniform body force F,
+                     per-cell sums adding up to the sum over labelled nodes
   steady             closed-form uniform steady state s/k
   Schnakenberg       homogeneous fixed point (a+b, b/(a+b)^2), linearised
     reaction         map I + J of a uniform perturbation (Jacobian by hand)
@@ -371,6 +374,25 @@ def run(p, tissue, n_steps, f=None, g=None, xy=None, tension: float = 0.0, dom=N
     r.area = cell_areas(off, xy)
     assert N == p.nx * p.ny
     return r
+
+
+def sums(p, r, n_cells):
+    """Conservation sums of a run's last-step fields (Sec. 3.3 computeAreas
+    gives the per-cell area; these are its mass and concentration
+    companions), in FP64: global sum rho, sum rho ux, sum rho uy and sum phi_s
+    over all nodes; per cell c (the nodes whose lowest containing cell is c,
+    id == c + 1) sum rho and sum phi_s.  Returns (glob (3 + S,),
+    cell (n_cells, 1 + S))."""
+    S = p.n_species
+    glob = np.array([r.rho.sum(), (r.rho * r.ux).sum(), (r.rho * r.uy).sum()] +
+                    [r.phi[s].sum() for s in range(S)])
+    cell = np.zeros((n_cells, 1 + S))
+    for c in range(n_cells):
+        m = r.id == c + 1
+        cell[c, 0] = r.rho[m].sum()
+        for s in range(S):
+            cell[c, 1 + s] = r.phi[s][m].sum()
+    return glob, cell
 
 
 def steady(p, src, g=None, tol=1e-6, max_steps=200000, check_every=16):

@@ -108,6 +108,8 @@ bool make_layout(const lbib_params& p, int max_vertices, int max_cells, Layout* 
     l.pres = take(C * 8);
     l.srcf = take(C);
     l.area = take(C * 8);
+    l.sums_bytes = (uint64_t)(4 + kMaxSpecies + C * (1 + kMaxSpecies)) * 8 + 16;
+    l.sums = take(l.sums_bytes);
     l.diag = take(kDiagWords * 4);
     l.total = o;
     *L = l;

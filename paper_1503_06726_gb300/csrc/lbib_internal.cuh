@@ -74,6 +74,8 @@ struct Layout {
     uint64_t pnode = 0;        // internal pressure nodes, one byte per node (pressure_nodes)
     uint64_t nsrc = 0;         // static mass source per node, compute type (node_sources)
     int jnbx = 0, jnby = 0;
+    // FP64 conservation sums (lbib_get_sums): global, per cell, non-finite count
+    uint64_t sums = 0, sums_bytes = 0;
     uint64_t diag = 0;
     uint64_t total = 0;
 };

@@ -44,7 +44,7 @@ EXPORTS = (
     "lbib_set_domains", "lbib_set_mass_sources", "lbib_set_pressure_nodes",
     "lbib_set_node_sources",
     "lbib_set_cell_params",
-    "lbib_set_species", "lbib_step", "lbib_advance", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
+    "lbib_set_species", "lbib_step", "lbib_advance", "lbib_get_sums", "lbib_step_profiled", "lbib_get_fields", "lbib_get_sizes", "lbib_state_size",
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
     "lbib_status_string", "lbib_label_cells", "lbib_steady_workspace_size", "lbib_steady_solve",
     "lbib_ensemble_workspace_size", "lbib_ensemble_create", "lbib_ensemble_tissue",
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lbib_set_species": (ctypes.c_int, [vp, i32, vp]),
         "lbib_step": (ctypes.c_int, [vp, i32]),
         "lbib_advance": (ctypes.c_int, [vp, i32]),
+        "lbib_get_sums": (ctypes.c_int, [vp, vp, vp, vp]),
         "lbib_step_profiled": (ctypes.c_int, [vp, i32, vp]),
         "lbib_get_fields": (ctypes.c_int, [vp, u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "lbib_get_sizes": (ctypes.c_int, [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
@@ -288,6 +289,16 @@ def lbib_step(ctx, n_steps: int):
 
 def lbib_advance(ctx, n_steps: int) -> None:
     _check(load().lbib_advance(ctx, int(n_steps)), ctx)
+
+
+def lbib_get_sums(ctx, n_species: int, n_cells: int):
+    """(global (3 + S,), per cell (n_cells, 1 + S), non-finite node count)."""
+    glob = np.zeros(3 + n_species)
+    cell = np.zeros((max(n_cells, 1), 1 + n_species))
+    bad = ctypes.c_uint32(0)
+    _check(load().lbib_get_sums(ctx, glob.ctypes.data_as(ctypes.c_void_p),
+                                cell.ctypes.data_as(ctypes.c_void_p), ctypes.byref(bad)), ctx)
+    return glob, cell[:n_cells], int(bad.value)
 
 
 def lbib_step_profiled(ctx, n_steps: int):
@@ -496,6 +507,10 @@ class Simulation:
 
     def step(self, n: int = 1):
         lbib_step(self.ctx, n)
+
+    def sums(self):
+        """FP64 conservation sums of the last step (lbib_get_sums)."""
+        return lbib_get_sums(self.ctx, self.n_species, self.n_cells)
 
     def advance(self, n: int = 1):
         """n steps without the output work of the last one (lbib_advance)."""
