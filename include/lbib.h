@@ -50,6 +50,8 @@ extern "C" {
 #define LBIB_E_TIMEOUT (-5)     /* a bounded device-side wait ran out */
 #define LBIB_E_CUDA (-6)        /* a CUDA runtime call failed */
 #define LBIB_E_STATE (-7)       /* call not valid in the context's current state */
+#define LBIB_E_CHECK (-8)       /* checking build only: a kernel access failed its bounds
+                                   or alignment check (it was skipped, not made) */
 
 /* storage precision of the lattice populations */
 #define LBIB_FP64 0   /* FP64 storage, FP64 arithmetic */

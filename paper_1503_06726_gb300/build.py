@@ -17,6 +17,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbib.so")
+# the checking build (-DLBIB_CHECK): every vector, atomic and indexed access of
+# the hot kernels tests its address first, records a failure in the context's
+# diagnostic words and skips the access; selected by LBIB_CHECK=1
+BUILD_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(BUILD_CHECK, "liblbib_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -40,12 +45,17 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=(), check: bool = False) -> str:
+    """Compile the library (check=True: the checking build, -DLBIB_CHECK)."""
+    build_dir = BUILD_CHECK if check else BUILD
+    lib = LIB_CHECK if check else LIB
+    if check:
+        extra = tuple(extra) + ("-DLBIB_CHECK",)
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(ROOT, "include", "lbib.h"))
     srcs = sources()
-    objs = [os.path.join(BUILD, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(build_dir, os.path.basename(s)[:-3] + ".o") for s in srcs]
     nv = nvcc()
 
     def comp(src, obj):
@@ -66,13 +76,14 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for l in logs:
             if l:
                 print(l, file=sys.stderr)
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nv, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         subprocess.run(cmd, check=True, capture_output=True, text=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                check="--check" in sys.argv))

@@ -157,9 +157,11 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
             a.write_vforce = vforce;
             a.do_ids = vforce;  // the prep of the output step writes the labels too
             if (e.cell_threads == 64)
-                ib_cell_f32<64, false, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
+                ib_cell_f32<64, false, false, false>(a, item - e.cell_pfx[t], view, htid,
+                                                     1 + half);
             else
-                ib_cell_f32<128, false, false>(a, item - e.cell_pfx[t], view, htid, 1 + half);
+                ib_cell_f32<128, false, false, false>(a, item - e.cell_pfx[t], view, htid,
+                                                      1 + half);
         }
     };
 

@@ -48,7 +48,10 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
     // the shared arrays hold kMaxVertsPerCell vertices and a polygon needs
     // three; callers that pass device offsets unchecked (the allocation-free
     // step) get the geometry flag instead of an access past sx
-    if (n > kMaxVertsPerCell || n < 3) {
+    const bool vok = LBIB_CHK_INDEX(a.diag, kSiteIbVertex, v0, (int64_t)__ldcg(a.off + a.n_cells)) &&
+                     LBIB_CHK_INDEX(a.diag, kSiteIbVertex, (int64_t)v0 + n - 1,
+                                    (int64_t)__ldcg(a.off + a.n_cells));
+    if (n > kMaxVertsPerCell || n < 3 || !vok) {
         if (tid == 0) raise_flag(a.diag, kDiagGeometry);
         return;
     }
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
                 const V2* row = u + (int64_t)J * a.pitch;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const V2 v = row[ix[i]];
+                    const V2 v = u_ld(a, row + ix[i]);
                     const C w = wx[i] * wy[j];
                     Ux += v.x * w;
                     Uy += v.y * w;
@@ -190,9 +193,9 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const C w = wx[i] * wy[j];
-                    spread_add(&row[ix[i]], Fx * w, Fy * w);
+                    spread_add(a, &row[ix[i]], Fx * w, Fy * w);
                 }
-                mark_row(a.fmask, (int64_t)J * a.pitch, ix);
+                mark_row(a, a.fmask, (int64_t)J * a.pitch, ix);
             }
         }
       }

@@ -101,12 +101,47 @@ __device__ __forceinline__ void raise_flag(uint32_t* diag, int k) {
 }
 
 // spread one weighted force into a node: FP32 uses the float2 vector atomic
-__device__ __forceinline__ void spread_add(float2* p, float fx, float fy) {
-    red_keep(p, fx, fy);
+__device__ __forceinline__ void spread_add(const IBArgs& a, float2* p, float fx, float fy) {
+    const float2* f = static_cast<const float2*>(a.force);
+    if (LBIB_CHK_ACCESS(a.diag, kSiteIbForce, p, 8, f, f + a.plane)) red_keep(p, fx, fy);
 }
-__device__ __forceinline__ void spread_add(double2* p, double fx, double fy) {
-    atomicAdd(&p->x, fx);
-    atomicAdd(&p->y, fy);
+__device__ __forceinline__ void spread_add(const IBArgs& a, double2* p, double fx, double fy) {
+    const double2* f = static_cast<const double2*>(a.force);
+    if (LBIB_CHK_ACCESS(a.diag, kSiteIbForce, p, 16, f, f + a.plane)) {
+        atomicAdd(&p->x, fx);
+        atomicAdd(&p->y, fy);
+    }
+}
+
+// The FP32 path's vector accesses to the force and velocity planes, with the
+// checking build's tests (address inside the plane, aligned to the access).
+__device__ __forceinline__ bool force_ok(const IBArgs& a, const float2* p, int bytes) {
+    const float2* f = static_cast<const float2*>(a.force);
+    return LBIB_CHK_ACCESS(a.diag, kSiteIbForce, p, bytes, f, f + a.plane);
+}
+__device__ __forceinline__ void force_red1(const IBArgs& a, float2* p, float x, float y) {
+    if (force_ok(a, p, 8)) red_keep(p, x, y);
+}
+__device__ __forceinline__ void force_red2(const IBArgs& a, float2* p, float x0, float y0,
+                                           float x1, float y1) {
+    if (force_ok(a, p, 16)) red_keep2(p, x0, y0, x1, y1);
+}
+__device__ __forceinline__ float4 u_ld4(const IBArgs& a, const float2* p) {
+    const float2* u = static_cast<const float2*>(a.u);
+    if (!LBIB_CHK_ACCESS(a.diag, kSiteIbU, p, 16, u, u + a.plane))
+        return make_float4(0.f, 0.f, 0.f, 0.f);
+    return *reinterpret_cast<const float4*>(p);
+}
+template <typename V2>
+__device__ __forceinline__ V2 u_ld(const IBArgs& a, const V2* p) {
+    const V2* u = static_cast<const V2*>(a.u);
+    if (!LBIB_CHK_ACCESS(a.diag, kSiteIbU, p, (int)sizeof(V2), u, u + a.plane)) {
+        V2 z;
+        z.x = 0;
+        z.y = 0;
+        return z;
+    }
+    return *p;
 }
 
 // Hookean spring of the edge A -> B with constant k and rest length L0: the
@@ -139,7 +174,8 @@ __device__ __forceinline__ double crossing_x(double2 A, double2 B, double yn) {
 
 // Mark in `mask` (1 bit per 4 consecutive nodes) the groups of the four
 // support nodes of one kernel row: one atomicOr per 32-group word touched.
-__device__ __forceinline__ void mark_row(uint32_t* mask, int64_t rowbase, const int ix[4]) {
+__device__ __forceinline__ void mark_row(const IBArgs& a, uint32_t* mask, int64_t rowbase,
+                                         const int ix[4]) {
     if (!mask) return;
     int64_t wd = -1;
     uint32_t bits = 0u;
@@ -147,39 +183,34 @@ __device__ __forceinline__ void mark_row(uint32_t* mask, int64_t rowbase, const 
     for (int i = 0; i < 4; ++i) {
         const int64_t g = (rowbase + ix[i]) >> 2;
         if ((g >> 5) != wd) {
-            if (bits) atomicOr(mask + wd, bits);
+            if (bits && LBIB_CHK_INDEX(a.diag, kSiteMask, wd, mask_words(a.plane)))
+                atomicOr(mask + wd, bits);
             wd = g >> 5;
             bits = 0u;
         }
         bits |= 1u << (g & 31);
     }
-    atomicOr(mask + wd, bits);
-}
-
-// Mark the group of one node; the active lanes of a warp combine their bits
-// per word first.
-__device__ __forceinline__ void mark_node_warp(uint32_t* mask, int64_t node) {
-    if (!mask) return;
-    const unsigned act = __activemask();
-    const int64_t g = node >> 2;
-    const unsigned long long w = (unsigned long long)(g >> 5);
-    const unsigned peers = __match_any_sync(act, w);
-    const uint32_t bits = __reduce_or_sync(peers, 1u << (g & 31));
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(mask + w, bits);
+    if (LBIB_CHK_INDEX(a.diag, kSiteMask, wd, mask_words(a.plane))) atomicOr(mask + wd, bits);
 }
 
 // Mark the groups of the nodes [s, e) of one row (no wrap inside the range)
 // in `mask`: lanes take one 32-group word each.
-__device__ __forceinline__ void mark_range(uint32_t* mask, int64_t rowbase, int s, int e,
-                                           int lane, int step = 32) {
+__device__ __forceinline__ void mark_range(const IBArgs& a, uint32_t* mask, int64_t rowbase,
+                                           int s, int e, int lane, int step = 32) {
     if (!mask || e <= s) return;
     const int64_t ga = (rowbase + s) >> 2, gb = (rowbase + e - 1) >> 2;
     for (int64_t w = (ga >> 5) + lane; w <= (gb >> 5); w += step) {
         const unsigned lo = (w == (ga >> 5)) ? (unsigned)(ga & 31) : 0u;
         const unsigned hi = (w == (gb >> 5)) ? (unsigned)(gb & 31) : 31u;
         const uint32_t bits = ((2u << hi) - 1u) & ~((1u << lo) - 1u);
-        atomicOr(mask + w, bits);
+        if (LBIB_CHK_INDEX(a.diag, kSiteMask, w, mask_words(a.plane))) atomicOr(mask + w, bits);
     }
+}
+// one node's group bit in a mask
+__device__ __forceinline__ void mark_node(const IBArgs& a, uint32_t* mask, int64_t node) {
+    const int64_t g = node >> 2;
+    if (mask && LBIB_CHK_INDEX(a.diag, kSiteMask, g >> 5, mask_words(a.plane)))
+        atomicOr(mask + (g >> 5), 1u << (g & 31));
 }
 
 // Labels of one cell (phase 3 of the IB kernels).  With scan_ok the per-row
@@ -193,17 +224,22 @@ __device__ __forceinline__ void mark_range(uint32_t* mask, int64_t rowbase, int 
 // OR the source bits into the source plane at one node
 __device__ __forceinline__ void src_or_node(const IBArgs& a, int64_t node, uint32_t bits) {
     if (a.src_words) {
-        atomicOr(static_cast<uint32_t*>(a.src) + node, bits);
+        uint32_t* w = static_cast<uint32_t*>(a.src) + node;
+        if (LBIB_CHK_ACCESS(a.diag, kSiteIbLabel, w, 4, a.src,
+                            static_cast<uint32_t*>(a.src) + a.plane))
+            atomicOr(w, bits);
     } else {
         unsigned int* w = reinterpret_cast<unsigned int*>(static_cast<uint8_t*>(a.src) + (node & ~3ll));
-        atomicOr(w, bits << (8 * (int)(node & 3)));
+        if (LBIB_CHK_ACCESS(a.diag, kSiteIbLabel, w, 4, a.src,
+                            static_cast<uint8_t*>(a.src) + a.plane))
+            atomicOr(w, bits << (8 * (int)(node & 3)));
     }
 }
 
 // OR the source bits into the bytes [s, e) of one row of the byte plane (row
 // start 8-byte aligned): one 64-bit atomic per 8 nodes, lanes take words
-__device__ __forceinline__ void src_or_range(uint8_t* row, int s, int e, uint32_t bits, int lane,
-                                             int step = 32) {
+__device__ __forceinline__ void src_or_range(const IBArgs& a, uint8_t* row, int s, int e,
+                                             uint32_t bits, int lane, int step = 32) {
     if (e <= s) return;
     const unsigned long long rep = 0x0101010101010101ull * (unsigned long long)bits;
     unsigned long long* wrow = reinterpret_cast<unsigned long long*>(row);
@@ -211,13 +247,16 @@ __device__ __forceinline__ void src_or_range(uint8_t* row, int s, int e, uint32_
         const int a0 = max(s - 8 * w, 0), a1 = min(e - 8 * w, 8);
         const unsigned long long m =
             (a1 - a0 == 8) ? ~0ull : (((1ull << (8 * (a1 - a0))) - 1ull) << (8 * a0));
-        atomicOr(wrow + w, rep & m);
+        if (LBIB_CHK_ACCESS(a.diag, kSiteIbLabel, wrow + w, 8, a.src,
+                            static_cast<uint8_t*>(a.src) + a.plane))
+            atomicOr(wrow + w, rep & m);
     }
 }
 
 __device__ __forceinline__ void label_node(const IBArgs& a, int64_t node, uint32_t code,
                                            uint32_t bits) {
-    if (a.do_ids) atomicMin(a.id + node, code);
+    if (a.do_ids && LBIB_CHK_ACCESS(a.diag, kSiteIbLabel, a.id + node, 4, a.id, a.id + a.plane))
+        atomicMin(a.id + node, code);
     if (bits) src_or_node(a, node, bits);
 }
 
@@ -261,11 +300,11 @@ static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, 
                     const int len = hi - lo;
                     const int e1 = ws + len <= a.nx ? ws + len : a.nx;
                     const int e2 = ws + len - a.nx;  // > 0 when the span wraps
-                    src_or_range(row, ws, e1, bits, 0, 1);
-                    mark_range(a.smask, rb, ws, e1, 0, 1);
+                    src_or_range(a, row, ws, e1, bits, 0, 1);
+                    mark_range(a, a.smask, rb, ws, e1, 0, 1);
                     if (e2 > 0) {
-                        src_or_range(row, 0, e2, bits, 0, 1);
-                        mark_range(a.smask, rb, 0, e2, 0, 1);
+                        src_or_range(a, row, 0, e2, bits, 0, 1);
+                        mark_range(a, a.smask, rb, 0, e2, 0, 1);
                     }
                 }
             } else {  // odd count: the parity rule node by node
@@ -277,8 +316,7 @@ static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, 
                         int wI = wI0 + cc;
                         if (wI >= a.nx) wI -= a.nx;
                         label_node(a, rb + wI, code, bits);
-                        const int64_t g = (rb + wI) >> 2;
-                        if (a.smask) atomicOr(a.smask + (g >> 5), 1u << (g & 31));
+                        mark_node(a, a.smask, rb + wI);
                     }
                 }
             }
@@ -328,17 +366,17 @@ static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, 
                         const int e1 = ws + len <= a.nx ? ws + len : a.nx;
                         const int e2 = ws + len - a.nx;  // > 0 when the span wraps
                         if (a.do_ids) {
-                            mark_range(a.lmask, rb, ws, e1, lane);
-                            if (e2 > 0) mark_range(a.lmask, rb, 0, e2, lane);
+                            mark_range(a, a.lmask, rb, ws, e1, lane);
+                            if (e2 > 0) mark_range(a, a.lmask, rb, 0, e2, lane);
                         }
                         if (bits) {
                             if (!a.src_words) {
                                 uint8_t* row = static_cast<uint8_t*>(a.src) + rb;
-                                src_or_range(row, ws, e1, bits, lane);
-                                if (e2 > 0) src_or_range(row, 0, e2, bits, lane);
+                                src_or_range(a, row, ws, e1, bits, lane);
+                                if (e2 > 0) src_or_range(a, row, 0, e2, bits, lane);
                             }
-                            mark_range(a.smask, rb, ws, e1, lane);
-                            if (e2 > 0) mark_range(a.smask, rb, 0, e2, lane);
+                            mark_range(a, a.smask, rb, ws, e1, lane);
+                            if (e2 > 0) mark_range(a, a.smask, rb, 0, e2, lane);
                         }
                     }
                 }
@@ -351,9 +389,8 @@ static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, 
                         int wI = wI0 + cc;
                         if (wI >= a.nx) wI -= a.nx;
                         label_node(a, rb + wI, code, bits);
-                        const int64_t g = (rb + wI) >> 2;
-                        if (a.do_ids && a.lmask) atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
-                        if (bits && a.smask) atomicOr(a.smask + (g >> 5), 1u << (g & 31));
+                        if (a.do_ids) mark_node(a, a.lmask, rb + wI);
+                        if (bits) mark_node(a, a.smask, rb + wI);
                     }
                 }
             }
@@ -377,9 +414,8 @@ static __device__ __forceinline__ void fill_labels_body(const IBArgs& a, int c, 
                 if (wJ >= a.ny) wJ -= a.ny;
                 const int64_t node = (int64_t)wJ * a.pitch + wI;
                 label_node(a, node, code, bits);
-                const int64_t g = node >> 2;
-                if (a.do_ids && a.lmask) atomicOr(a.lmask + (g >> 5), 1u << (g & 31));
-                if (bits && a.smask) atomicOr(a.smask + (g >> 5), 1u << (g & 31));
+                if (a.do_ids) mark_node(a, a.lmask, node);
+                if (bits) mark_node(a, a.smask, node);
             }
         }
     }
@@ -458,7 +494,9 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 // parameter reads through a pointer; 1024^2 step 40.9 -> 38.4 us) or called
 // out of line (the small-CTA kernels keep 64 registers, 16 CTAs per SM, and
 // the ensemble's persistent kernel its budget)
-template <int NT, bool GRIDDEP, bool INLINE_FILL = true>
+// OPTS = false compiles out the junction forces and mass sources (the
+// ensemble has neither).
+template <int NT, bool GRIDDEP, bool INLINE_FILL = true, bool OPTS = true>
 static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, int tid,
                                    int bar) {
     static_assert(NT % 64 == 0, "CTA size");
@@ -475,7 +513,11 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
     const int v0 = __ldcg(a.off + c);
     const int n = __ldcg(a.off + c + 1) - v0;
     const int lane = tid & 31;
-    if (n > S.maxv || n < 3) {  // cannot happen for callers that size maxv from the cells
+    // the checking build: the cell's vertices inside the vertex arrays
+    const bool vok = LBIB_CHK_INDEX(a.diag, kSiteIbVertex, v0, (int64_t)__ldcg(a.off + a.n_cells)) &&
+                     LBIB_CHK_INDEX(a.diag, kSiteIbVertex, (int64_t)v0 + n - 1,
+                                    (int64_t)__ldcg(a.off + a.n_cells));
+    if (n > S.maxv || n < 3 || !vok) {  // cannot happen for callers that size maxv from the cells
         if (GRIDDEP) {
             griddep_wait();
             griddep_launch_dependents();
@@ -566,22 +608,22 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                 if (ix[3] == ix[0] + 3) {
                     const float2* r0 = row + ix[0];
                     if ((ix[0] & 1) == 0) {
-                        const float4 p0 = *reinterpret_cast<const float4*>(r0);
-                        const float4 p1 = *reinterpret_cast<const float4*>(r0 + 2);
+                        const float4 p0 = u_ld4(a, r0);
+                        const float4 p1 = u_ld4(a, r0 + 2);
                         v[0] = make_float2(p0.x, p0.y);
                         v[1] = make_float2(p0.z, p0.w);
                         v[2] = make_float2(p1.x, p1.y);
                         v[3] = make_float2(p1.z, p1.w);
                     } else {
-                        const float4 p1 = *reinterpret_cast<const float4*>(r0 + 1);
-                        v[0] = r0[0];
+                        const float4 p1 = u_ld4(a, r0 + 1);
+                        v[0] = u_ld(a, r0);
                         v[1] = make_float2(p1.x, p1.y);
                         v[2] = make_float2(p1.z, p1.w);
-                        v[3] = r0[3];
+                        v[3] = u_ld(a, r0 + 3);
                     }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) v[i] = row[ix[i]];
+                    for (int i = 0; i < 4; ++i) v[i] = u_ld(a, row + ix[i]);
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -626,7 +668,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
         if (!finite) s_flag = 2;
     }
     cell_sync<NT>(bar);
-    if (a.msrc_out && tid < 32) {
+    if (OPTS && a.msrc_out && tid < 32) {
         // mass source of the cell (Sec. 3.2.3): S_c = rate + alpha (A0 - A_c),
         // A_c the shoelace area of the moved polygon about its first vertex
         const double a_c = cell_area_warp(sx, n, lane);
@@ -678,7 +720,7 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                     Fx += ten * (dn.x / ln - dp.x / lp);
                     Fy += ten * (dn.y / ln - dp.y / lp);
                 }
-                if (a.jpartner) {  // Eq. celljunctionforce (a launch without the move)
+                if (OPTS && a.jpartner) {  // Eq. celljunctionforce (a launch without the move)
                     const float2 J = junction_force32(a, sx[t], a.jpartner[v0 + t]);
                     Fx += J.x;
                     Fy += J.y;
@@ -717,18 +759,18 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                     if (ix[3] == ix[0] + 3) {
                         float2* r0 = row + ix[0];
                         if ((ix[0] & 1) == 0) {
-                            red_keep2(r0, cx4[0], cy4[0], cx4[1], cy4[1]);
-                            red_keep2(r0 + 2, cx4[2], cy4[2], cx4[3], cy4[3]);
+                            force_red2(a, r0, cx4[0], cy4[0], cx4[1], cy4[1]);
+                            force_red2(a, r0 + 2, cx4[2], cy4[2], cx4[3], cy4[3]);
                         } else {
-                            red_keep(r0, cx4[0], cy4[0]);
-                            red_keep2(r0 + 1, cx4[1], cy4[1], cx4[2], cy4[2]);
-                            red_keep(r0 + 3, cx4[3], cy4[3]);
+                            force_red1(a, r0, cx4[0], cy4[0]);
+                            force_red2(a, r0 + 1, cx4[1], cy4[1], cx4[2], cy4[2]);
+                            force_red1(a, r0 + 3, cx4[3], cy4[3]);
                         }
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) spread_add(&row[ix[i]], cx4[i], cy4[i]);
+                        for (int i = 0; i < 4; ++i) spread_add(a, &row[ix[i]], cx4[i], cy4[i]);
                     }
-                    mark_row(a.fmask, (int64_t)J * a.pitch, ix);
+                    mark_row(a, a.fmask, (int64_t)J * a.pitch, ix);
                 }
             }
         }

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     // shuffles (lanes past the end load and store nothing)
     if (2 * (t - lane) >= a.nx || y >= a.ny) return;
     const int x0 = 2 * t;
-    const bool valid = x0 < a.nx;
+    bool valid = x0 < a.nx;
     const bool lo_wall = WALLS && (y == 0);
     const bool hi_wall = WALLS && (y == a.ny - 1);
     const int ym = (y == 0) ? a.ny - 1 : y - 1;
@@ -100,6 +100,18 @@ __global__ void __launch_bounds__(kLatticeThreads, PairOccupancy<S>::kMinBlocks)
     const bool own_r = valid && (lane == 31 || x0 + 2 >= a.nx);
     const int l0 = (r0 + xl) >> 1, lm = (rm + xl) >> 1, lp = (rp + xl) >> 1;
     const int q0 = (r0 + xr) >> 1, qm = (rm + xr) >> 1, qp = (rp + xr) >> 1;
+    // the checking build: the word indices inside the plane, the 16-byte
+    // accesses of the pair aligned; a lane that fails loads and stores
+    // nothing but still takes part in the warp's shuffles
+    if (valid &&
+        (!LBIB_CHK_INDEX(a.diag, kSitePairIndex,
+                         (int64_t)max(max(max(wm, wp), max(lm, lp)), max(max(qm, qp), w)), P2) ||
+         !LBIB_CHK_ACCESS(a.diag, kSitePairAlign, static_cast<const float4*>(a.u) + (node >> 1),
+                          16, nullptr, nullptr) ||
+         !LBIB_CHK_ACCESS(a.diag, kSitePairAlign, static_cast<const float4*>(a.force) + (node >> 1),
+                          16, nullptr, nullptr) ||
+         !LBIB_CHK_INDEX(a.diag, kSiteMask, (int64_t)(node >> 7), mask_words(a.plane))))
+        valid = false;
 
     // ---- every population word first (written two launches back: L2 path)
     const uint64_t pol = a.l2_first ? l2_evict_first() : l2_evict_normal();

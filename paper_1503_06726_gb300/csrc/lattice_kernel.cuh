@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kLatticeThreads, LatticeOccupancy<T, S, CONF>:
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
     constexpr bool GRIDDEP = true;
+    constexpr bool OPTS = true;
     LBIB_LATTICE_NODE_BODY
 }
 

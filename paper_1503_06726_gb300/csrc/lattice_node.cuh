@@ -93,7 +93,8 @@ template <typename T, typename C, bool WALLS, bool SCALED>
 __device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M, uint32_t code,
                                               int node, int r0, int rm, int rp, int rmm, int rpp,
                                               int x, int xm, int xp, int xmm, int xpp, bool lo,
-                                              bool hi, uint64_t pol, C isg, C wq, C g[5]) {
+                                              bool hi, uint64_t pol, C isg, C wq, C g[5],
+                                              uint32_t* diag) {
     using St = Store<T, C>;
     g[0] = St::ld(B + node, pol);
 #pragma unroll
@@ -101,6 +102,11 @@ __device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M,
         if ((code >> (kNcodeMiss + q - 1)) & 1u) {
             const int i1 = q == 1 ? r0 + xp : (q == 3 ? r0 + xm : (q == 2 ? rp + x : rm + x));
             const int i2 = q == 1 ? r0 + xpp : (q == 3 ? r0 + xmm : (q == 2 ? rpp + x : rmm + x));
+            if (!LBIB_CHK_INDEX(diag, kSiteClosureIndex, i1, P) ||
+                !LBIB_CHK_INDEX(diag, kSiteClosureIndex, i2, P)) {
+                g[q] = C(0);
+                continue;
+            }
             const bool in1 = (code >> (kNcodeIn1 + q - 1)) & 1u;
             const bool in2 = (code >> (kNcodeIn2 + q - 1)) & 1u;
             const C* Mj = M + (q == 1 || q == 3 ? P : 2 * P);
@@ -141,7 +147,9 @@ __device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M,
 // launch two launches back, read through L2) are issued before the
 // programmatic wait on the IB kernel whose force, label and mask planes the
 // rest reads; CONF, without which the paths of confined species (domain
-// planes, the no-flux closure and its moments) are compiled out.
+// planes, the no-flux closure and its moments) are compiled out; OPTS,
+// without which the mass sources, node sources and pressure nodes are
+// (the ensemble has none of them and keeps its registers).
 #define LBIB_LATTICE_NODE_BODY \
  \
     using St = Store<T, C>; \
@@ -158,6 +166,18 @@ __device__ __forceinline__ void pull5_closure(const T* B, int64_t P, const C* M,
     const int rm = ym * (int)a.pitch; \
     const int rp = yp * (int)a.pitch; \
     const int node = r0 + x; \
+    /* the checking build: every pulled index inside the plane, the plane */ \
+    /* bases aligned to their elements */ \
+    if (!LBIB_CHK_INDEX(a.diag, kSiteLatticeIndex, \
+                        (int64_t)(rm > rp ? (rm > r0 ? rm : r0) : (rp > r0 ? rp : r0)) + \
+                            (xm > xp ? (xm > x ? xm : x) : (xp > x ? xp : x)), \
+                        a.plane) || \
+        !LBIB_CHK_ACCESS(a.diag, kSiteLatticeAlign, a.fsrc, (int)sizeof(T), nullptr, nullptr) || \
+        !LBIB_CHK_ACCESS(a.diag, kSiteLatticeAlign, a.fdst, (int)sizeof(T), nullptr, nullptr) || \
+        !LBIB_CHK_ACCESS(a.diag, kSiteLatticeAlign, a.u, (int)sizeof(V2), nullptr, nullptr) || \
+        !LBIB_CHK_ACCESS(a.diag, kSiteLatticeAlign, a.force, (int)sizeof(V2), nullptr, nullptr) || \
+        !LBIB_CHK_INDEX(a.diag, kSiteMask, (int64_t)(node >> 7), mask_words(a.plane))) \
+        return; \
  \
     /* ---- every load of the node first (all independent, read-only path), so */ \
     /* that a thread has all its DRAM requests in flight at once */ \
@@ -198,7 +218,7 @@ _Pragma("unroll") \
                         Gi + (int64_t)s * 5 * P, P, \
                         static_cast<const C*>(a.mom_in) + (int64_t)s * 3 * P, ncode, node, r0, \
                         rm, rp, ymm * (int)a.pitch, ypp * (int)a.pitch, x, xm, xp, xmm, xpp, \
-                        lo_wall, hi_wall, pol, k.isig_g, k.w5c[1], g[s]); \
+                        lo_wall, hi_wall, pol, k.isig_g, k.w5c[1], g[s], a.diag); \
                 } else { \
                     pull5_confined<T, C, WALLS>(Gi + (int64_t)s * 5 * P, P, a.dom, node, r0, rm, \
                                                 rp, x, xm, xp, lo_wall, hi_wall, pol, g[s]); \
@@ -250,9 +270,9 @@ _Pragma("unroll") \
     C ph[S > 0 ? S : 1]; \
     /* the cell's mass source at labelled nodes; internal pressure nodes */ \
     C ms = C(0); \
-    if (a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
-    if (a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
-    const bool pn = a.pnode && a.pnode[node] != 0; \
+    if (OPTS && a.msrc && label != kOutside) ms = static_cast<const C*>(a.msrc)[label >> 4]; \
+    if (OPTS && a.nsrc) ms += static_cast<const C*>(a.nsrc)[node]; \
+    const bool pn = OPTS && a.pnode && a.pnode[node] != 0; \
     /* the closure reads this node's moments next step: its species fluxes */ \
     /* before the collision (the densities come out of collide_node) */ \
     const bool mom_w = CONF && ((ncode >> kNcodeMom) & 1u); \
@@ -266,7 +286,8 @@ _Pragma("unroll") \
         } \
     } \
     collide_node<C, S, FORCING, SCALED>(k, d, g, fv.x, fv.y, sbits, 0u, rho, ux, uy, ph, \
-                                        a.msrc != nullptr || a.nsrc != nullptr, ms, pn); \
+                                        OPTS && (a.msrc != nullptr || a.nsrc != nullptr), ms, \
+                                        pn); \
     if (mom_w) { \
 _Pragma("unroll") \
         for (int s = 0; s < S; ++s) { \
@@ -522,7 +543,10 @@ template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
 __device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
                                              int y) {
     constexpr bool GRIDDEP = false;
-    constexpr bool CONF = false;  // the ensemble's tissues confine no species
+    // the ensemble's tissues confine no species and have no mass sources,
+    // node sources or pressure nodes
+    constexpr bool CONF = false;
+    constexpr bool OPTS = false;
     LBIB_LATTICE_NODE_BODY
 }
 

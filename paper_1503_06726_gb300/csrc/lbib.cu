@@ -309,6 +309,7 @@ static IBArgs ib_args(lbib_ctx* c, bool move, bool prep, bool out_next) {
     a.bc_y = c->p.bc_y;
     a.n_cells = c->nC;
     a.pitch = L.pitch;
+    a.plane = L.plane;
     a.tension = c->p.tension;
     a.do_move = move ? 1 : 0;
     a.do_prep = prep ? 1 : 0;
@@ -987,7 +988,7 @@ int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double
                                 c->stream);
     }
     // the device-side diagnostics
-    uint32_t diag[4] = {0, 0, 0, 0};
+    uint32_t diag[kDiagCheckAddr + 1] = {0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(diag, c->ws + L.diag, sizeof(diag), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1028,6 +1029,14 @@ int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double
                 force[2 * ((size_t)y * nx + x)] = val(r_force, 2 * n);
                 force[2 * ((size_t)y * nx + x) + 1] = val(r_force, 2 * n + 1);
             }
+    if (diag[kDiagCheck]) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg),
+                      "checking build: an access failed its bounds or alignment check "
+                      "(site %u, address low bits 0x%08x) and was skipped",
+                      diag[kDiagCheckSite], diag[kDiagCheckAddr]);
+        return fail(c, LBIB_E_CHECK, msg);
+    }
     if (diag[kDiagNonFinite])
         return fail(c, LBIB_E_NONFINITE, "a non-finite density or velocity was produced");
     if (diag[kDiagGeometry])
@@ -1164,6 +1173,7 @@ const char* lbib_status_string(int status) {
         case LBIB_E_TIMEOUT: return "LBIB_E_TIMEOUT";
         case LBIB_E_CUDA: return "LBIB_E_CUDA";
         case LBIB_E_STATE: return "LBIB_E_STATE";
+        case LBIB_E_CHECK: return "LBIB_E_CHECK";
         default: return "LBIB_E_UNKNOWN";
     }
 }

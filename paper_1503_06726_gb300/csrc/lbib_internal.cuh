@@ -51,8 +51,64 @@ enum Diag : int {
     kDiagWallStencil = 1, // an IB stencil node fell outside a walled domain (dropped)
     kDiagRasterSlow = 2,  // a cell used the brute-force labelling path
     kDiagGeometry = 3,    // a cell's bounding box became non-finite or wider than the lattice
+    kDiagCheck = 4,       // checking build: an access failed its bounds or alignment check
+    kDiagCheckSite = 5,   // checking build: site of the first failed check (CheckSite)
+    kDiagCheckAddr = 6,   // checking build: low 32 bits of its address
     kDiagWords = 64
 };
+
+// Sites of the checking build's access checks (kDiagCheckSite).
+enum CheckSite : uint32_t {
+    kSiteLatticeIndex = 1,  // a pulled population's index outside the plane
+    kSiteLatticeAlign = 2,  // a plane base not aligned to its element
+    kSiteClosureIndex = 3,  // a no-flux closure's moment index outside the plane
+    kSitePairIndex = 4,     // FP16 pair kernel: a word index outside the plane
+    kSitePairAlign = 5,     // FP16 pair kernel: a 16-byte access not aligned
+    kSiteMask = 6,          // a group-mask word outside the mask
+    kSiteIbVertex = 7,      // a vertex index outside the vertex arrays
+    kSiteIbU = 8,           // an interpolation load outside the velocity plane or misaligned
+    kSiteIbForce = 9,       // a spreading reduction outside the force plane or misaligned
+    kSiteIbLabel = 10,      // a label or source write outside its plane or misaligned
+    kSiteIbShared = 11,     // a vertex slot outside the cell's shared arrays
+};
+
+// The checking build (compiled with -DLBIB_CHECK into a library of its own):
+// the kernels test the address of every access that needs an alignment or
+// could leave its array, and an access that fails is skipped (a load reads
+// zero) after the first failure's site and address are recorded in the diag
+// words.  Nothing traps.  The plain build compiles every check to `true`.
+#ifdef LBIB_CHECK
+__device__ __noinline__ inline void check_failed(uint32_t* diag, uint32_t site, const void* p) {
+    if (!diag) return;
+    if (atomicOr(diag + kDiagCheck, 1u) == 0u) {
+        atomicExch(diag + kDiagCheckSite, site);
+        atomicExch(diag + kDiagCheckAddr, (uint32_t)reinterpret_cast<uintptr_t>(p));
+    }
+}
+// p: the access of `bytes` bytes (aligned to `bytes`), inside [lo, hi) when
+// lo is given
+__device__ __forceinline__ bool check_access(uint32_t* diag, uint32_t site, const void* p,
+                                             int bytes, const void* lo, const void* hi) {
+    const char* c = static_cast<const char*>(p);
+    bool ok = (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(bytes - 1)) == 0;
+    if (lo && (c < static_cast<const char*>(lo) || c + bytes > static_cast<const char*>(hi)))
+        ok = false;
+    if (!ok) check_failed(diag, site, p);
+    return ok;
+}
+// an index of an array of n elements
+__device__ __forceinline__ bool check_index(uint32_t* diag, uint32_t site, int64_t i, int64_t n) {
+    const bool ok = i >= 0 && i < n;
+    if (!ok) check_failed(diag, site, reinterpret_cast<const void*>(i));
+    return ok;
+}
+#define LBIB_CHK_ACCESS(diag, site, p, bytes, lo, hi) \
+    ::lbib::check_access((diag), (site), (p), (bytes), (lo), (hi))
+#define LBIB_CHK_INDEX(diag, site, i, n) ::lbib::check_index((diag), (site), (i), (n))
+#else
+#define LBIB_CHK_ACCESS(diag, site, p, bytes, lo, hi) true
+#define LBIB_CHK_INDEX(diag, site, i, n) true
+#endif
 
 // Workspace layout: byte offsets into the caller's device workspace.
 struct Layout {
@@ -194,6 +250,7 @@ struct IBArgs {
     uint32_t* diag;
     int nx, ny, bc_y, n_cells;
     int64_t pitch;
+    int64_t plane;      // elements per plane of the force / u / label / source planes
     double tension;
     int do_move, do_prep, do_mask, write_vforce;
     int do_force;       // compute and spread vertex forces (0: labels only)
@@ -385,7 +442,7 @@ inline cudaError_t launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, 
 }
 
 // mask words covering a plane of `plane` elements (1 bit per 4 nodes)
-inline int64_t mask_words(int64_t plane) { return (plane + 127) / 128 + 1; }
+__host__ __device__ inline int64_t mask_words(int64_t plane) { return (plane + 127) / 128 + 1; }
 
 // coefficient tables and the calling thread's error text (lbib_last_error(NULL))
 void fill_coefs_public(const lbib_params& p, Coefs<double>* k);

@@ -160,6 +160,7 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
     ia.bc_y = params->bc_y;
     ia.n_cells = n_cells;
     ia.pitch = L.pitch;
+    ia.plane = L.plane;
     ia.tension = params->tension;
     ia.do_mask = 1;
     ia.write_vforce = 0;
@@ -192,13 +193,18 @@ extern "C" int lbib_step_noalloc(const lbib_params* params, int32_t n_cells,
             e = cudaMemcpyAsync(d_g, gbuf[1], (size_t)5 * params->n_species * P * L.es,
                                 cudaMemcpyDeviceToDevice, st);
     }
-    uint32_t diag[kDiagGeometry + 1] = {0};
+    uint32_t diag[kDiagCheckAddr + 1] = {0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(diag, sc + o_diag, sizeof(diag), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess)
         return set_thread_error(LBIB_E_CUDA, std::string("lbib_step_noalloc: ") +
                                                  cudaGetErrorString(e));
+    if (diag[kDiagCheck])
+        return set_thread_error(LBIB_E_CHECK,
+                                "lbib_step_noalloc: checking build: an access failed its bounds or "
+                                "alignment check (site " + std::to_string(diag[kDiagCheckSite]) +
+                                    ") and was skipped");
     if (diag[kDiagNonFinite] || diag[kDiagGeometry])
         return set_thread_error(LBIB_E_NONFINITE,
                                 "lbib_step_noalloc: a non-finite value or blown-up cell appeared");

@@ -259,6 +259,7 @@ int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
         a.bc_y = bc_y;
         a.n_cells = n_cells;
         a.pitch = nx;
+        a.plane = (int64_t)nx * ny;
         a.do_move = 0;
         a.do_prep = 1;
         a.do_mask = 1;

@@ -19,6 +19,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "liblbib.so")
+# the checking build (bounds and alignment checks in the kernels), used when
+# the environment sets LBIB_CHECK=1
+LIB_CHECK_PATH = os.path.join(HERE, "_build_check", "liblbib_check.so")
 
 LBIB_OK = 0
 LBIB_E_PARAM = -1
@@ -28,6 +31,7 @@ LBIB_E_NONFINITE = -4
 LBIB_E_TIMEOUT = -5
 LBIB_E_CUDA = -6
 LBIB_E_STATE = -7
+LBIB_E_CHECK = -8
 
 LBIB_FP64, LBIB_FP32, LBIB_FP16 = 0, 1, 2
 LBIB_GUO, LBIB_HE_PAPER = 0, 1
@@ -86,11 +90,18 @@ class lbib_params(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load the CUDA library; raises if it has not been built."""
+def load(path: str = None) -> ctypes.CDLL:
+    """Load the CUDA library; raises if it has not been built.  With
+    LBIB_CHECK=1 in the environment the checking build is built if needed and
+    loaded instead."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_PATH
+        if os.environ.get("LBIB_CHECK") == "1":
+            from . import build as _build
+            path = _build.build(check=True)
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
     L = ctypes.CDLL(path)
