@@ -185,7 +185,7 @@ def peaks():
 
 def lattice_kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("lattice.cu", "lattice_node.cuh", "lbib_internal.cuh"):
+    for f in ("lattice.cu", "lattice_kernel.cuh", "lattice_node.cuh", "lbib_internal.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1503_06726_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
