@@ -498,6 +498,33 @@ int lbib_nn_conv3x3_wgrad(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C
 int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, const float* d_w,
                           void* d_wf, void* d_wd, void* cuda_stream);
 
+/* The same 3x3 convolution on the fifth-generation tensor cores (tcgen05.mma
+ * with the FP32 accumulator in tensor memory, operands staged by the tensor
+ * memory accelerator); the network's training and inference use it for every
+ * layer it supports:
+ *   lbib_nn_conv3x3_tc_supported  1 when the shape is supported: H x W split
+ *                          into tiles of 128 pixels (W a multiple of 128, or
+ *                          W in {16, 32, 64} with H a multiple of 128 / W),
+ *                          C1 >= 16 and C1, C2 multiples of 16, Co >= 1
+ *   lbib_nn_tile_weights_tc  the forward weights d_wf (9, Co, Ci) (as
+ *                          lbib_nn_weight_copies makes them) rearranged into
+ *                          d_wt, the order the kernel's bulk copies load
+ *                          (*elems_out bf16 elements; d_wt NULL: size only)
+ *   lbib_nn_conv3x3_tc     out = conv3x3([in1, upsample2(in2)]) + bias (ReLU
+ *                          if relu) as lbib_nn_conv3x3, with the tiled weights;
+ *                          d_in1, d_in2, d_wt 16-byte aligned; d_err a device
+ *                          word the caller zeroes: nonzero afterwards when a
+ *                          bounded wait of the kernel ran out (the output is
+ *                          then undefined)
+ * The paper has no network; these calls belong to the learned warm start. */
+int lbib_nn_conv3x3_tc_supported(int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co);
+int lbib_nn_tile_weights_tc(int32_t Ci, int32_t Co, const void* d_wf, void* d_wt,
+                            uint64_t* elems_out, void* cuda_stream);
+int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
+                       const void* d_in1, const void* d_in2, const void* d_wt, const float* d_bias,
+                       void* d_out, int32_t relu, int32_t out_f32, uint32_t* d_err,
+                       void* cuda_stream);
+
 /* Coupled steps without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory while
  * they run -- code inside a framework whose memory pool owns the device, or

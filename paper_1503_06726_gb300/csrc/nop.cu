@@ -594,6 +594,51 @@ int lbib_nn_conv3x3(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int
     return LBIB_OK;
 }
 
+int lbib_nn_conv3x3_tc_supported(int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co) {
+    return tc_conv_supported(H, W, C1, C2, Co) ? 1 : 0;
+}
+
+int lbib_nn_tile_weights_tc(int32_t Ci, int32_t Co, const void* d_wf, void* d_wt,
+                            uint64_t* elems_out, void* cuda_stream) {
+    if (Ci < 16 || Ci % 16 || Co < 1)
+        return set_thread_error(LBIB_E_PARAM, "lbib_nn_tile_weights_tc: invalid arguments");
+    if (elems_out) *elems_out = (uint64_t)tc_tiled_weight_elems(Ci, Co);
+    if (!d_wt) return LBIB_OK;
+    if (!d_wf) return set_thread_error(LBIB_E_PARAM, "lbib_nn_tile_weights_tc: d_wf is NULL");
+    cudaError_t e = tc_tile_weights(d_wf, Co, Ci, d_wt, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return set_thread_error(LBIB_E_CUDA, cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
+                       const void* d_in1, const void* d_in2, const void* d_wt, const float* d_bias,
+                       void* d_out, int32_t relu, int32_t out_f32, uint32_t* d_err,
+                       void* cuda_stream) {
+    if (N < 1 || !d_in1 || !d_wt || !d_out || !d_err || (C2 > 0 && !d_in2) ||
+        !tc_conv_supported(H, W, C1, C2, Co))
+        return set_thread_error(LBIB_E_PARAM, "lbib_nn_conv3x3_tc: unsupported shape or arguments");
+    if (reinterpret_cast<uintptr_t>(d_in1) % 16 || reinterpret_cast<uintptr_t>(d_wt) % 16 ||
+        (d_in2 && reinterpret_cast<uintptr_t>(d_in2) % 16))
+        return set_thread_error(LBIB_E_PARAM, "lbib_nn_conv3x3_tc: inputs need 16-byte alignment");
+    nn::ConvArgs a;
+    a.in1 = static_cast<const bf16*>(d_in1);
+    a.in2 = static_cast<const bf16*>(d_in2);
+    a.w = nullptr;
+    a.bias = d_bias;
+    a.out = d_out;
+    a.N = N;
+    a.H = H;
+    a.W = W;
+    a.C1 = C1;
+    a.C2 = C2;
+    a.Co = Co;
+    a.relu = relu;
+    a.out_f32 = out_f32;
+    cudaError_t e = tc_conv3x3(a, d_wt, d_err, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return set_thread_error(LBIB_E_CUDA, cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
 int lbib_nn_conv3x3_wgrad(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
                           const void* d_in1, const void* d_in2, const void* d_g, float* d_dw,
                           float* d_db, void* cuda_stream) {
