@@ -31,6 +31,7 @@ Other workloads (--workload): c2 (the 1024^2 tissue, no-slip walls in y,
 tau 0.8, 400 hexagonally packed 100-vertex cells, two reacting species);
 c3-fp16, c3-fp64 (the default tissue with FP16-shifted / FP64 storage);
 c3-precision (that tissue with all three storages, errors against FP64);
+nn (the neural operator's training step and forward pass, TFLOP/s);
 c4 (64 independent tissues in one persistent launch); c5 (the learned warm
 start of the steady morphogen solve, warm vs cold); turing (the
 Schnakenberg system on a static cellular domain of 1024^2, receptor confined
@@ -452,6 +453,91 @@ def run_warmstart(args, rank, world, dist):
     }
 
 
+def nn_conv_flops(layers, H, W, N):
+    """Algorithmic FLOPs of the U-Net's 3x3 convolutions per sample batch:
+    forward 2 * 9 * Ci * Co * pixels per layer (canonical channels), the
+    data gradient the same except for the input layer, the weight gradient
+    the same.  Layers in the network's order: encoder levels 0..5 (two each),
+    decoder levels 4..0 (two each), the output layer at level 0."""
+    levels = [l for l in range(6) for _ in range(2)] + \
+        [l for l in range(4, -1, -1) for _ in range(2)] + [0]
+    fwd = [2 * 9 * ci * co * (H >> l) * (W >> l) * N for (ci, co), l in zip(layers, levels)]
+    return sum(fwd), sum(fwd) + sum(fwd[1:]) + sum(fwd)
+
+
+def run_nn(args, rank, world, dist):
+    """The neural operator alone: training steps (forward, loss, backward,
+    Adam) and forward passes of the six-level U-Net on 256^2 batches of 16,
+    inputs resident on the device, timed with CUDA events on the network's
+    stream; throughput = the convolutions' algorithmic FLOPs per second
+    against the measured BF16 tensor peak."""
+    import torch
+    from paper_1503_06726_gb300 import lbib
+
+    lbib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    B, H = args.c5_batch, 256
+    net = lbib.NeuralOperator(B, H, H, device=dev)
+    layers = net.layers()
+    shapes = [(f"layer{i}", ci, co) for i, (ci, co) in enumerate(layers[:-1])]
+    shapes.append(("out",) + tuple(layers[-1]))
+    net.set_params(li.nop_init_params(5, shapes))
+    g = torch.Generator(device="cpu").manual_seed(3)
+    mask = (torch.rand((B, H, H), generator=g) < 0.6).to(torch.uint8).to(dev)
+    src = (torch.rand((B, H, H), generator=g) < 0.1).to(torch.uint8).to(dev)
+    phi = torch.rand((B, H, H), generator=g).to(dev)
+    D = np.full(B, 0.1)
+    k = np.full(B, 1e-3)
+    r = np.full(B, 1e-3)
+    fwd_flop, train_flop = nn_conv_flops(layers, H, H, B)
+    st = net.stream
+    for _ in range(max(args.warmup, 3)):
+        net.train_step(mask, src, D, k, r, phi, lr=1e-4)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index if dev.index is not None else 0) if rank == 0 else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(1, args.steps)
+    e0.record(st)
+    for _ in range(n):
+        net.train_step(mask, src, D, k, r, phi, lr=1e-4)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_train = e0.elapsed_time(e1) / n
+    out = torch.empty((B, H, H), dtype=torch.float32, device=dev)
+    e0.record(st)
+    for _ in range(n):
+        net.forward(mask, src, D, k, r, out=out)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_fwd = e0.elapsed_time(e1) / n
+    clk = clocks.stop() if clocks else None
+    net.close()
+    if rank != 0:
+        return None
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("bf16_tflops", 1900.0)
+    tf_train = train_flop / (t_train * 1e-3) / 1e12
+    tf_fwd = fwd_flop / (t_fwd * 1e-3) / 1e12
+    return {
+        "metric": "neural-operator training throughput (3x3 convolutions)",
+        "value": tf_train, "unit": "TFLOP/s", "higher_is_better": True, "n_gpus": world,
+        "steps": n, "warmup": max(args.warmup, 3), "ms_per_step": t_train, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (fp32 accumulation)", "data": "synthetic",
+        "config": {"workload": f"nn_unet_{H}x{H}_batch{B}", "params": net.n_params,
+                   "layers": layers},
+        "training_step_ms": t_train, "forward_ms": t_fwd,
+        "roofline": {"bound": "tensor", "achieved": tf_train, "peak": peak, "unit": "TFLOP/s",
+                     "frac": tf_train / peak, "forward_tflops": tf_fwd,
+                     "forward_frac": tf_fwd / peak,
+                     "alg_flop_per_step": train_flop, "alg_flop_per_forward": fwd_flop,
+                     "peak_kind": "measured bf16_tflops (burst)",
+                     "note": "whole steps: the numerator counts the convolutions only, the "
+                             "time includes the elementwise layers and the host's input "
+                             "staging of every call"},
+        "clocks": clk, "cpu_baseline": None,
+    }
+
+
 def run_precision(args, rank, world, dist):
     """The 4096^2 precision sweep: the same tissue advanced --prec-steps
     steps with FP64, FP32 and FP16-shifted population storage; velocity,
@@ -679,6 +765,8 @@ def run_gb300(args, rank, world, dist):
         return run_ensemble(args, rank, world, dist)
     if args.workload == "c5":
         return run_warmstart(args, rank, world, dist)
+    if args.workload == "nn":
+        return run_nn(args, rank, world, dist)
     import torch
     from paper_1503_06726_gb300 import lbib
 

@@ -46,6 +46,8 @@ struct Layer {
     int64_t coff;    // offset in the canonical flat vector
     bf16* wf;        // (9, cop, cip)
     bf16* wd;        // (9, cip, cop)
+    bf16* wft;       // wf tiled for the tcgen05 convolution
+    bf16* wdt;       // wd tiled for the tcgen05 convolution (the data gradient)
 };
 
 std::vector<Layer> make_layers() {
@@ -58,7 +60,7 @@ std::vector<Layer> make_layers() {
         l.cip = ci < 16 ? 16 : ci;
         l.cop = co < 16 ? 16 : co;
         l.off = l.coff = 0;
-        l.wf = l.wd = nullptr;
+        l.wf = l.wd = l.wft = l.wdt = nullptr;
         L.push_back(l);
     };
     static const char* enc_names[kLevels][2] = {{"enc0a", "enc0b"}, {"enc1a", "enc1b"},
@@ -117,6 +119,7 @@ struct lbib_nop {
     float* dn = nullptr;     // per sample normalised D, decay
     float* kn = nullptr;
     double* loss = nullptr;
+    unsigned* tc_err = nullptr;  // raised by a tcgen05 convolution whose bounded wait ran out
     int64_t t = 0;           // Adam step
     std::string err;
 
@@ -151,7 +154,10 @@ void nop_layout(lbib_nop* n) {
     for (auto& l : n->L) {
         l.wf = n->take<bf16>(9LL * l.cip * l.cop);
         l.wd = n->take<bf16>(9LL * l.cip * l.cop);
+        l.wft = n->take<bf16>(tc_tiled_weight_elems(l.cip, l.cop));
+        l.wdt = n->take<bf16>(tc_tiled_weight_elems(l.cop, l.cip));
     }
+    n->tc_err = n->take<unsigned>(1);
     const int64_t B = n->B;
     int64_t maxg = 0;
     for (int l = 0; l < kLevels; ++l) {
@@ -183,9 +189,11 @@ void nop_layout(lbib_nop* n) {
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// A 3x3 convolution of the network: on the tcgen05 tensor cores (tiled
+// weights wt) wherever the layer's shape allows, else the warp-level kernel.
 cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* in2, int C1, int C2,
-                     int lvl, void* out, int relu, int out_f32, const bf16* w, const float* bias,
-                     int Co, int N) {
+                     int lvl, void* out, int relu, int out_f32, const bf16* w, const bf16* wt,
+                     const float* bias, int Co, int N) {
     nn::ConvArgs a;
     a.in1 = in1;
     a.in2 = in2;
@@ -201,6 +209,7 @@ cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* i
     a.relu = relu;
     a.out_f32 = out_f32;
     (void)l;
+    if (wt && tc_conv_supported(a.H, a.W, C1, C2, Co)) return tc_conv3x3(a, wt, n->tc_err, n->stream);
     const int tiles = ((a.H + kTH - 1) / kTH) * ((a.W + kTW - 1) / kTW);
     dim3 grid(tiles, (Co + 63) / 64, N);
     nn::conv3x3_fwd_kernel<<<grid, 256, kConvSmem, n->stream>>>(a);
@@ -234,6 +243,8 @@ cudaError_t refresh_weights(lbib_nop* n) {
         nn::weight_copies_kernel<<<blocks(cnt), 256, 0, n->stream>>>(n->param + l.off, l.cip, l.cop,
                                                                       l.cip, l.cop, l.wf, l.wd);
         cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = tc_tile_weights(l.wf, l.cop, l.cip, l.wft, n->stream);
+        if (e == cudaSuccess) e = tc_tile_weights(l.wd, l.cip, l.cop, l.wdt, n->stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -278,25 +289,25 @@ cudaError_t forward(lbib_nop* n, int N) {
         const Layer& a = L[li++];
         const Layer& b = L[li++];
         if (e == cudaSuccess)
-            e = conv_fwd(n, a, n->enc_in[l], nullptr, cin, 0, l, n->enc_r1[l], 1, 0, a.wf,
+            e = conv_fwd(n, a, n->enc_in[l], nullptr, cin, 0, l, n->enc_r1[l], 1, 0, a.wf, a.wft,
                          n->param + a.off + 9LL * a.cip * a.cop, a.cop, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, b, n->enc_r1[l], nullptr, kCh[l], 0, l, n->enc_out[l], 1, 0, b.wf,
+            e = conv_fwd(n, b, n->enc_r1[l], nullptr, kCh[l], 0, l, n->enc_out[l], 1, 0, b.wf, b.wft,
                          n->param + b.off + 9LL * b.cip * b.cop, b.cop, N);
     }
     for (int l = kLevels - 2; l >= 0 && e == cudaSuccess; --l) {
         const Layer& a = L[li++];
         const Layer& b = L[li++];
         const bf16* deeper = (l == kLevels - 2) ? n->enc_out[l + 1] : n->dec_out[l + 1];
-        e = conv_fwd(n, a, n->enc_out[l], deeper, kCh[l], kCh[l + 1], l, n->dec_r1[l], 1, 0, a.wf,
+        e = conv_fwd(n, a, n->enc_out[l], deeper, kCh[l], kCh[l + 1], l, n->dec_r1[l], 1, 0, a.wf, a.wft,
                      n->param + a.off + 9LL * a.cip * a.cop, a.cop, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, b, n->dec_r1[l], nullptr, kCh[l], 0, l, n->dec_out[l], 1, 0, b.wf,
+            e = conv_fwd(n, b, n->dec_r1[l], nullptr, kCh[l], 0, l, n->dec_out[l], 1, 0, b.wf, b.wft,
                          n->param + b.off + 9LL * b.cip * b.cop, b.cop, N);
     }
     if (e == cudaSuccess) {
         const Layer& o = L[li];
-        e = conv_fwd(n, o, n->dec_out[0], nullptr, kCh[0], 0, 0, n->y, 0, 1, o.wf,
+        e = conv_fwd(n, o, n->dec_out[0], nullptr, kCh[0], 0, 0, n->y, 0, 1, o.wf, o.wft,
                      n->param + o.off + 9LL * o.cip * o.cop, o.cop, N);
     }
     return e;
@@ -318,7 +329,7 @@ cudaError_t backward(lbib_nop* n, int N) {
     // output layer
     if (e == cudaSuccess) e = conv_wgrad(n, o, n->dec_out[0], nullptr, kCh[0], 0, 0, n->dy, N);
     if (e == cudaSuccess)
-        e = conv_fwd(n, o, n->dy, nullptr, o.cop, 0, 0, n->ga, 0, 0, o.wd, nullptr, o.cip, N);
+        e = conv_fwd(n, o, n->dy, nullptr, o.cop, 0, 0, n->ga, 0, 0, o.wd, o.wdt, nullptr, o.cip, N);
     bf16* g = n->ga;
     bf16* s1 = n->gb;
     bf16* s2 = n->gc;
@@ -329,14 +340,14 @@ cudaError_t backward(lbib_nop* n, int N) {
         relu_bwd(g, n->dec_out[l], N * hw * kCh[l]);
         if (e == cudaSuccess) e = conv_wgrad(n, b, n->dec_r1[l], nullptr, kCh[l], 0, l, g, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, nullptr, kCh[l], N);
+            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, b.wdt, nullptr, kCh[l], N);
         relu_bwd(s1, n->dec_r1[l], N * hw * kCh[l]);
         const bf16* deeper = (l == kLevels - 2) ? n->enc_out[l + 1] : n->dec_out[l + 1];
         if (e == cudaSuccess)
             e = conv_wgrad(n, a, n->enc_out[l], deeper, kCh[l], kCh[l + 1], l, s1, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, a, s1, nullptr, kCh[l], 0, l, s2, 0, 0, a.wd, nullptr,
-                         kCh[l] + kCh[l + 1], N);
+            e = conv_fwd(n, a, s1, nullptr, kCh[l], 0, l, s2, 0, 0, a.wd, a.wdt,
+                         nullptr, kCh[l] + kCh[l + 1], N);
         if (e == cudaSuccess) {
             const int64_t tot = N * hw * kCh[l] + N * (hw / 4) * kCh[l + 1];
             nn::concat_bwd_kernel<<<blocks(tot), 256, 0, n->stream>>>(
@@ -358,12 +369,12 @@ cudaError_t backward(lbib_nop* n, int N) {
         relu_bwd(g, n->enc_out[l], N * hw * kCh[l]);
         if (e == cudaSuccess) e = conv_wgrad(n, b, n->enc_r1[l], nullptr, kCh[l], 0, l, g, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, nullptr, kCh[l], N);
+            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, b.wdt, nullptr, kCh[l], N);
         relu_bwd(s1, n->enc_r1[l], N * hw * kCh[l]);
         const int cin = l == 0 ? 16 : kCh[l - 1];
         if (e == cudaSuccess) e = conv_wgrad(n, a, n->enc_in[l], nullptr, cin, 0, l, s1, N);
         if (l > 0 && e == cudaSuccess) {
-            e = conv_fwd(n, a, s1, nullptr, kCh[l], 0, l, s2, 0, 0, a.wd, nullptr, cin, N);
+            e = conv_fwd(n, a, s1, nullptr, kCh[l], 0, l, s2, 0, 0, a.wd, a.wdt, nullptr, cin, N);
             if (e == cudaSuccess) {
                 const int64_t cnt = N * (int64_t)(n->H >> (l - 1)) * (n->W >> (l - 1)) * cin;
                 nn::avgpool2_bwd_kernel<<<blocks(cnt), 256, 0, n->stream>>>(
@@ -376,6 +387,19 @@ cudaError_t backward(lbib_nop* n, int N) {
 }
 
 bool params_ok(lbib_nop* n) { return n && n->param; }
+
+// After the stream has been synchronised: whether a tcgen05 convolution's
+// bounded wait ran out since the last check (the word is then cleared).
+int tc_status(lbib_nop* n, const char* where) {
+    unsigned h = 0u;
+    cudaError_t e = cudaMemcpy(&h, n->tc_err, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(n->tc_err, 0, 4);
+    if (e != cudaSuccess) return nop_fail(n, LBIB_E_CUDA, cudaGetErrorString(e));
+    if (h)
+        return nop_fail(n, LBIB_E_TIMEOUT,
+                        std::string(where) + ": a tensor-core convolution's wait ran out");
+    return LBIB_OK;
+}
 
 }  // namespace
 
@@ -419,6 +443,7 @@ int lbib_nop_create(int32_t batch, int32_t H, int32_t W, void* d_workspace, uint
         e = cudaFuncSetAttribute(nn::conv3x3_wgrad_kernel,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->param, 0, n->P * 4 * 4, n->stream);  // param, grad, m, v
+    if (e == cudaSuccess) e = cudaMemsetAsync(n->tc_err, 0, 4, n->stream);
     if (e == cudaSuccess) e = refresh_weights(n);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) {
@@ -516,8 +541,9 @@ int lbib_nop_forward(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uint8_
         nn::scale_kernel<<<blocks((int64_t)N * HW), 256, 0, n->stream>>>(n->y, 16, d_phi, n->fac, N, HW);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) return nop_fail(n, LBIB_E_CUDA, cudaGetErrorString(e));
-    return LBIB_OK;
+    return tc_status(n, "lbib_nop_forward");
 }
 
 int lbib_nop_train_step(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uint8_t* d_src,
@@ -554,7 +580,7 @@ int lbib_nop_train_step(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uin
         e = cudaMemcpyAsync(loss_out, n->loss, 8, cudaMemcpyDeviceToHost, n->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) return nop_fail(n, LBIB_E_CUDA, cudaGetErrorString(e));
-    return LBIB_OK;
+    return tc_status(n, "lbib_nop_train_step");
 }
 
 void lbib_nop_destroy(lbib_nop* n) { delete n; }
