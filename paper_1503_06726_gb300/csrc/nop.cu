@@ -190,7 +190,10 @@ void nop_layout(lbib_nop* n) {
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
 // A 3x3 convolution of the network: on the tcgen05 tensor cores (tiled
-// weights wt) wherever the layer's shape allows, else the warp-level kernel.
+// weights wt) for images of rows of 128 pixels or more, where the single
+// halo per tile makes them the faster kernel (1.7 - 2.4x at 256 x 256, even
+// at 128 x 128); narrower levels, where the three kx-shifted halo copies
+// cost more than the warp-level kernel's register tiling, take the latter.
 cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* in2, int C1, int C2,
                      int lvl, void* out, int relu, int out_f32, const bf16* w, const bf16* wt,
                      const float* bias, int Co, int N) {
@@ -209,7 +212,7 @@ cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* i
     a.relu = relu;
     a.out_f32 = out_f32;
     (void)l;
-    if (wt && tc_conv_supported(a.H, a.W, C1, C2, Co)) return tc_conv3x3(a, wt, n->tc_err, n->stream);
+    if (wt && a.W >= 128 && tc_conv_supported(a.H, a.W, C1, C2, Co)) return tc_conv3x3(a, wt, n->tc_err, n->stream);
     const int tiles = ((a.H + kTH - 1) / kTH) * ((a.W + kTW - 1) / kTW);
     dim3 grid(tiles, (Co + 63) / 64, N);
     nn::conv3x3_fwd_kernel<<<grid, 256, kConvSmem, n->stream>>>(a);

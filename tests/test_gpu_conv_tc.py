@@ -6,9 +6,12 @@ Tolerances as for the other layer tests: BF16-exact inputs and weights, so
 only the FP32 accumulation order differs: relative L-infinity 1e-5 in FP32
 output; BF16 output within 8e-3 (one rounding of 2^-8 relative).  The
 kernel's error word stays zero.  Shapes cover every pixel tile (W = 16, 32,
-64: several rows per tile; 128, 256: one row), the decoder's upsampled
-second input, an output wider than one CTA's 192 channels (two tiles), the
-one-channel final layer and the data gradient through flipped weights.
+64: several rows per tile, three kx-shifted halo copies; 128, 256, 640,
+1280: rows of 128 under one halo), one and several accumulators per CTA
+(the larger images leave enough CTAs for 4 accumulators, or 2 at 192
+channels), the decoder's upsampled second input, an output wider than one
+CTA's 192 channels (two tiles), the one-channel final layer and the data
+gradient through flipped weights.
 """
 import numpy as np
 import pytest
@@ -66,6 +69,9 @@ def _weights(lb, w, Ci, Co, st):
     (2, 2, 256, 32, 0, 192),    # two tiles per row, 192 channels in one CTA
     (1, 16, 16, 48, 0, 320),    # two N tiles of 160
     (1, 16, 64, 32, 0, 1),      # the one-channel final layer
+    (2, 128, 640, 16, 16, 48),  # rows of 128, 4 accumulators, upsampled input
+    (1, 64, 1280, 16, 0, 192),  # rows of 128, 2 accumulators of 192 channels
+    (40, 64, 64, 16, 16, 32),   # 2 rows x 64, 4 accumulators, upsampled input
 ])
 def test_tc_conv_matches_oracle_and_mma_sync(lb, orc, N, H, W, C1, C2, Co):
     import torch
