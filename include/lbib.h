@@ -500,16 +500,18 @@ int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, cons
 
 /* The same 3x3 convolution on the fifth-generation tensor cores (tcgen05.mma
  * with the FP32 accumulator in tensor memory, operands staged by the tensor
- * memory accelerator); the network's training and inference use it for every
- * layer it supports:
- *   lbib_nn_conv3x3_tc_supported  1 when the shape is supported: H x W split
- *                          into tiles of 128 pixels (W a multiple of 128, or
- *                          W in {16, 32, 64} with H a multiple of 128 / W),
- *                          C1 >= 16 and C1, C2 multiples of 16, Co >= 1
+ * memory accelerator); the network's training and inference use it for the
+ * levels where it is the faster kernel:
+ *   lbib_nn_conv3x3_tc_supported  1 when the shape is supported: W <= 128 or
+ *                          a multiple of 128; C1 >= 16, C1 and C2 multiples
+ *                          of 16, and C1 a multiple of 32 when C1 + C2 is
+ *                          (the chunk width); H and W even when C2 > 0;
+ *                          Co >= 1
  *   lbib_nn_tile_weights_tc  the forward weights d_wf (9, Co, Ci) (as
  *                          lbib_nn_weight_copies makes them) rearranged into
- *                          d_wt, the order the kernel's bulk copies load
- *                          (*elems_out bf16 elements; d_wt NULL: size only)
+ *                          d_wt, the order and the swizzled layout the
+ *                          kernel's bulk copies load (*elems_out bf16
+ *                          elements; d_wt NULL: size only)
  *   lbib_nn_conv3x3_tc     out = conv3x3([in1, upsample2(in2)]) + bias (ReLU
  *                          if relu) as lbib_nn_conv3x3, with the tiled weights;
  *                          d_in1, d_in2, d_wt 16-byte aligned; d_err a device

@@ -1,33 +1,33 @@
 // conv_tc.cu -- the 3x3 convolutions of the neural operator on the fifth-
 // generation tensor cores: tcgen05.mma (BF16 operands, FP32 accumulation)
-// with the accumulator in tensor memory (TMEM), operands staged in shared
-// memory by the tensor memory accelerator (TMA), one thread issuing the
-// matrix multiplies, mbarriers pacing two pipeline stages.
+// with the accumulators in tensor memory (TMEM), operands staged in shared
+// memory by the tensor memory accelerator (TMA), one thread issuing copies
+// and matrix multiplies, mbarriers pacing up to three pipeline stages.
 //
-// Implicit GEMM: M = output pixels, N = all output channels (rounded up to
-// 16; more than 192 split into equal tiles of at most 192, one per CTA
-// column of the grid), K = 9 taps x input channels, in chunks of 16.  A tap
-// (ky, kx) reads the pixel tile shifted by (ky - 1, kx - 1), and its A
-// operand must be a K-major matrix whose rows (one per output pixel) lie 16
-// bytes apart -- the canonical layout without swizzling (core matrices of 8
-// rows x 16 bytes; the two 8-channel halves of a chunk a fixed offset
-// apart).  Two tile shapes make every tap such a window of the staged halo:
-//   wide images (W a multiple of 128): a CTA takes m image rows of 128
-//   pixels, one accumulator of 128 TMEM lanes per row; the halo holds
-//   (m + 2) rows of 130 pixels, and row j's tap (ky, kx) starts at halo row
-//   j + ky, column kx -- one 4-D TMA box (8 channels x 130 x (m + 2) x 1)
-//   per 8-channel half;
-//   narrow images (W = 16, 32, 64): a CTA takes R = 128 / W whole rows in
-//   one accumulator; the halo is staged three times, copy kx holding columns
-//   kx - 1 .. kx + W - 2, so that tap (ky, kx) is copy kx from row ky on --
-//   one TMA box (8 x W x (R + 2) x 1) per copy and half.
-// The image's zero padding is the TMA's out-of-bounds fill.  The decoder's
-// upsampled half-resolution channels (each value repeated 2 x 2) are staged
-// by the threads with cp.async instead.  The weights are pre-tiled
-// (tile_weights_tc_kernel) into the order the B descriptors read, [N tile]
-// [chunk][tap][half][output channel][8 input channels], so that one bulk
-// copy loads a chunk's weights for all nine taps.  Chunks stream through
-// two or three stages of shared memory.
+// Implicit GEMM: M = output pixels, N = the output channels (rounded up to
+// 16, split into equal tiles of at most 128 -- 192 for 16-channel chunks --
+// one per CTA column of the grid), K = 9 taps x input channels, in chunks of
+// Kc = 32 channels (16 where the channel count is not a multiple of 32).
+//
+// A CTA takes TR image rows of a tile of Wt columns (Wt = W up to 128, else
+// 128) and stages their halo once per chunk: (TR + 2) rows of rs = Wt + 2
+// pixels, one pixel per 2 Kc-byte row of shared memory, swizzled in the 32-
+// or 64-byte pattern of the matching TMA mode -- one 4-D box (Kc channels x
+// rs x (TR + 2) x 1 image), whose out-of-bounds fill is the image's zero
+// padding.  In that layout the pixel at halo position p + ky rs + kx is tap
+// (ky, kx) of output position p, so every tap of an accumulator's 128 output
+// positions is one K-major operand starting ky rs + kx rows further on: the
+// tensor cores read swizzled operands from any row (the swizzle follows the
+// absolute shared-memory address, and the stages are 1024-byte aligned).
+// Accumulators of 128 TMEM lanes:
+//   Wt = 128: one per image row (m = TR), lane = column;
+//   Wt < 128: m = ceil(TR rs / 128) over the row-major halo positions, the
+//   two lanes per row that fall on halo columns discarded.
+// The decoder's upsampled half-resolution channels (each value repeated 2 x
+// 2) are staged by the threads with cp.async into the same swizzled layout.
+// The weights are pre-tiled and pre-swizzled (tile_weights_tc_kernel) into
+// [N tile][chunk][tap][output channel][Kc input channels], so that one bulk
+// copy loads a chunk's weights for all nine taps.
 //
 // Every mbarrier wait is bounded: a wait that runs out raises the error word,
 // the CTA waits (again bounded) for its copies and multiplies in flight,
@@ -47,28 +47,29 @@
 namespace lbib {
 namespace nn {
 
-constexpr int kTcThreads = 128;  // four warps: the accumulator's four lane quarters
+constexpr int kTcThreads = 128;  // four warps: the accumulators' four lane quarters
 constexpr int kTcM = 128;
-constexpr int kTcChunk = 16;     // input channels per K chunk (one MMA per tap)
+constexpr int kTcMaxStages = 3;
 
 struct ConvTcArgs {
     const __nv_bfloat16* in2;  // (N, H/2, W/2, C2), read upsampled, or NULL
-    const __nv_bfloat16* wt;   // tiled weights, [N tiles][nk][9][2][Np][8]
+    const __nv_bfloat16* wt;   // tiled weights, [N tiles][nk][9][Np][Kc] swizzled
     const float* bias;         // (Co) or NULL
     void* out;                 // (N, H, W, Co) bf16, or fp32 when out_f32
     unsigned* err;             // raised when a bounded wait runs out
-    int N, H, W, C1, C2, Co, nk;
+    int N, H, W, C1, C2, Co;
+    int Kc;                    // input channels of a chunk (32 or 16)
+    int swb;                   // bytes of one staged pixel: 2 Kc, the swizzle span
+    int swcode;                // the descriptors' layout code of that swizzle
+    int nk, nk1;               // chunks in all, and from in1
     int Np;                    // output channels of one CTA (N tile)
-    int Wt, R, m;              // tile: m accumulators of R rows x Wt pixels (R * Wt = 128)
-    int wide;                  // 1: one halo of rows of Wt + 2 pixels; 0: three kx copies
-    int rs;                    // halo row stride in pixels (Wt + 2, or Wt)
-    int nc;                    // halo copies (1, or 3)
-    int relu, out_f32;
-    int box_bytes;             // one halo copy of one 8-channel half: (m R + 2) rs 16
-    int copy_bytes;            // box_bytes rounded up to 128 (TMA destinations)
-    int stage_bytes;           // A and B of one chunk, rounded up to 1024
-    int stages;                // 2 or 3
+    int Wt, rs, TR, m, wide;   // tile: TR rows x Wt columns, halo rows of rs pixels
+    int tiles_x, tiles_y;
+    int a_bytes;               // the halo region of a stage (1024-byte multiple)
+    int box_bytes;             // bytes one TMA box delivers: (TR + 2) rs swb
+    int stage_bytes, stages;   // stage: halo + the chunk's weights
     int tmem_cols;             // power of two >= max(32, m Np)
+    int relu, out_f32;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -82,6 +83,12 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void mbar_tx_only(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
     uint32_t ok;
@@ -132,13 +139,23 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-// Shared memory matrix descriptor, K-major without swizzling: start address,
-// the byte distance between the two 16-byte K core matrices of an MMA (lbo)
-// and between consecutive groups of 8 rows (sbo), all in 16-byte units; bits
-// 46-47 hold the descriptor version of this architecture (1).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Shared memory matrix descriptor of a K-major operand in a swizzled layout:
+// start address (16-byte units, bits 0-13), the leading byte offset (unused
+// when one MMA's 16 K elements lie within a swizzled row; 1 by convention,
+// bits 16-29), the byte distance between groups of 8 rows (bits 32-45), the
+// descriptor version of this architecture (bits 46-47 = 1), base offset 0
+// (bits 49-51), and the layout code (bits 61-63: 6 = 32-byte, 4 = 64-byte,
+// 2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t sbo, uint32_t code) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)code << 61);
+}
+// Byte offset, within a 1024-byte aligned region, of the 16-byte piece that
+// the TMA's swizzle of span swb places at the unswizzled offset off: bits 4..
+// of the piece index XOR the bits from 7 on (one bit for 32 bytes, two for 64,
+// three for 128).
+__host__ __device__ __forceinline__ uint32_t swizzle_off(uint32_t off, int swb) {
+    return off ^ (((off >> 7) & (uint32_t)((swb >> 4) - 1)) << 4);
 }
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
 // A and B (bits 7-9 and 10-12 = 1), both K-major, N / 8 in bits 17-22,
@@ -174,27 +191,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int kTcMaxStages = 3;
 
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads)
     conv3x3_tc_kernel(const __grid_constant__ CUtensorMap map1, ConvTcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_done[kTcMaxStages];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_bad, s_committed;
-    // stages at 1024-byte boundaries (TMA destinations need 128)
-    const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
+    // stages at 1024-byte boundaries: the swizzle follows the address bits
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NS = a.stages;
 
-    const int TR = a.m * a.R;  // image rows of the tile
-    const int tiles_x = a.W / a.Wt, tiles_y = a.H / TR;
-    const int n = blockIdx.x / (tiles_x * tiles_y);
-    const int rem = blockIdx.x % (tiles_x * tiles_y);
-    const int y0 = (rem / tiles_x) * TR, x0 = (rem % tiles_x) * a.Wt;
+    const int per_img = a.tiles_x * a.tiles_y;
+    const int n = blockIdx.x / per_img;
+    const int rem = blockIdx.x % per_img;
+    const int y0 = (rem / a.tiles_x) * a.TR, x0 = (rem % a.tiles_x) * a.Wt;
     const int co0 = blockIdx.y * a.Np;  // this CTA's output channels
-    const __nv_bfloat16* wt = a.wt + (int64_t)blockIdx.y * a.nk * 9 * 2 * a.Np * 8;
+    const __nv_bfloat16* wt = a.wt + (int64_t)blockIdx.y * a.nk * 9 * a.Np * a.Kc;
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -217,78 +231,92 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const uint32_t idesc = mma_idesc(kTcM, a.Np);
-    const int a_bytes = 2 * a.nc * a.copy_bytes;
-    const uint32_t b_bytes = 18u * (uint32_t)a.Np * 16u;
-    const int hrows = TR + 2;
-    // thread 0: the chunk whose loads were issued into a stage and not yet
-    // waited for (-1 = none)
+    const uint32_t b_bytes = 9u * (uint32_t)a.Np * (uint32_t)a.swb;
+    const uint32_t sbo = 8u * (uint32_t)a.swb;
+    // thread 0: per stage, the chunk whose copies were issued and not yet
+    // waited for (-1 = none), and whether its arrival (after the threads'
+    // staging of an upsampled chunk) is still owed
     int loading[kTcMaxStages] = {-1, -1, -1};
+    bool owed[kTcMaxStages] = {false, false, false};
 
+    auto issue = [&](int k) {
+        const int s = k % NS;
+        const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
+        const uint32_t fb = smem_u32(&bar_full[s]);
+        if (k < a.nk1) {
+            mbar_expect_tx(fb, b_bytes + (uint32_t)a.box_bytes);
+            tma_load_4d(st, &map1, k * a.Kc, x0 - 1, y0 - 1, n, fb);
+        } else {
+            mbar_tx_only(fb, b_bytes);
+            owed[s] = true;
+        }
+        bulk_load(st + (uint32_t)a.a_bytes, wt + (int64_t)k * 9 * a.Np * a.Kc, b_bytes, fb);
+        loading[s] = k;
+    };
+
+    if (tid == 0)
+        for (int k = 0; k < NS && k < a.nk; ++k) issue(k);
     for (int k = 0; k < a.nk; ++k) {
         const int s = k % NS;
         const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
-        // the stage was read by the multiplies of chunk k - NS
-        if (k >= NS && !mbar_wait(smem_u32(&bar_done[s]), ((k - NS) / NS) & 1)) s_bad = 1;
-        __syncthreads();
-        if (s_bad) break;
-        const int c0 = k * kTcChunk;
-        const bool from1 = c0 < a.C1;
-        if (tid == 0) {
-            const uint32_t fb = smem_u32(&bar_full[s]);
-            mbar_expect_tx(fb, b_bytes + (from1 ? (uint32_t)(2 * a.nc * a.box_bytes) : 0u));
-            if (from1) {
-                for (int h = 0; h < 2; ++h)
-                    for (int cp = 0; cp < a.nc; ++cp)
-                        tma_load_4d(st + (uint32_t)((h * a.nc + cp) * a.copy_bytes), &map1,
-                                    c0 + 8 * h, a.wide ? x0 - 1 : x0 + cp - 1, y0 - 1, n, fb);
-            }
-            bulk_load(st + (uint32_t)a_bytes, wt + (int64_t)k * 9 * 2 * a.Np * 8, b_bytes, fb);
-            loading[s] = k;
-        }
-        if (!from1) {
+        if (k >= a.nk1) {
             // upsampled half-resolution channels: every thread stages 16-byte
-            // pieces (8 channels of one halo pixel), zeros outside the image
-            const int cc = c0 - a.C1;
-            const int per_copy = hrows * a.rs;
-            for (int i = tid; i < 2 * a.nc * per_copy; i += kTcThreads) {
-                const int cp = i / per_copy, hp = i % per_copy;
-                const int h = cp / a.nc, kx = cp % a.nc;
-                const int gy = y0 + hp / a.rs - 1;
-                const int gx = x0 + hp % a.rs - 1 + (a.wide ? 0 : kx);
+            // pieces (8 channels of one halo pixel), zeros outside the image;
+            // the stage is free, its copies having been issued after the
+            // multiplies of chunk k - NS completed
+            const int cc = (k - a.nk1) * a.Kc;
+            const int ppp = a.Kc / 8;
+            const int pieces = (a.TR + 2) * a.rs * ppp;
+            for (int i = tid; i < pieces; i += kTcThreads) {
+                const int hp = i / ppp, q = i % ppp;
+                const int gy = y0 + hp / a.rs - 1, gx = x0 + hp % a.rs - 1;
                 const bool ok = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
                 const __nv_bfloat16* src =
                     ok ? a.in2 + (((int64_t)n * (a.H >> 1) + (gy >> 1)) * (a.W >> 1) + (gx >> 1)) *
-                                     a.C2 + cc + 8 * h
+                                     a.C2 + cc + 8 * q
                        : a.in2;
-                cp_async16_zfill(st + (uint32_t)(cp * a.copy_bytes + hp * 16), src, ok);
+                cp_async16_zfill(st + swizzle_off((uint32_t)(hp * a.swb + q * 16), a.swb), src, ok);
             }
             asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
             // written through the generic proxy, read by the tensor cores
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                mbar_arrive(smem_u32(&bar_full[s]));
+                owed[s] = false;
+            }
         }
-        __syncthreads();
         if (tid == 0) {
             if (!mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
                 s_bad = 1;
             } else {
                 loading[s] = -1;
                 tc_fence_after();
-                const uint32_t lbo = (uint32_t)(a.nc * a.copy_bytes);
+                const uint32_t bst = st + (uint32_t)a.a_bytes;
                 for (int t = 0; t < 9; ++t) {
                     const int ky = t / 3, kx = t % 3;
-                    const uint32_t bad = st + (uint32_t)a_bytes + (uint32_t)(t * 2 * a.Np * 16);
-                    const uint64_t bdesc = smem_desc(bad, (uint32_t)a.Np * 16u, 128u);
-                    for (int j = 0; j < a.m; ++j) {
-                        const int row = j * a.R + ky;
-                        const uint32_t aad =
-                            st + (uint32_t)((a.wide ? 0 : kx) * a.copy_bytes) +
-                            (uint32_t)((row * a.rs + (a.wide ? kx : 0)) * 16);
-                        tc_mma(tmem + (uint32_t)(j * a.Np), smem_desc(aad, lbo, 128u), bdesc,
-                               idesc, (k > 0 || t > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < a.Kc / 16; ++kk) {
+                        const uint64_t bdesc = smem_desc_sw(
+                            bst + (uint32_t)(t * a.Np * a.swb + kk * 32), sbo, (uint32_t)a.swcode);
+                        for (int j = 0; j < a.m; ++j) {
+                            const int row = (a.wide ? j * a.rs : j * kTcM) + ky * a.rs + kx;
+                            const uint64_t adesc = smem_desc_sw(
+                                st + (uint32_t)(row * a.swb + kk * 32), sbo, (uint32_t)a.swcode);
+                            tc_mma(tmem + (uint32_t)(j * a.Np), adesc, bdesc, idesc,
+                                   (k > 0 || t > 0 || kk > 0) ? 1u : 0u);
+                        }
                     }
                 }
                 tc_commit(smem_u32(&bar_done[s]));
                 s_committed = k;
+                // refill the stage of chunk k - 1, whose multiplies ran ahead
+                // of the ones just issued
+                if (k >= 1 && k - 1 + NS < a.nk) {
+                    if (!mbar_wait(smem_u32(&bar_done[(k - 1) % NS]), ((k - 1) / NS) & 1))
+                        s_bad = 1;
+                    else
+                        issue(k - 1 + NS);
+                }
             }
         }
         __syncthreads();
@@ -297,7 +325,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // after an error: the copies still in flight land before the CTA leaves
     if (tid == 0)
         for (int s = 0; s < NS; ++s)
-            if (loading[s] >= 0) mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
+            if (loading[s] >= 0) {
+                if (owed[s]) mbar_arrive(smem_u32(&bar_full[s]));
+                mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
+            }
     __syncthreads();
     // the last commit covers every multiply issued before it
     const int committed = s_committed;
@@ -308,44 +339,47 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (ok) {
         // epilogue: warp w owns lanes 32w .. 32w + 31 of every accumulator
-        const int p = warp * 32 + lane;
+        const int i = warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int j = 0; j < a.m; ++j) {
-            const int gy = y0 + j * a.R + p / a.Wt, gx = x0 + p % a.Wt;
-            const int64_t pix = ((int64_t)n * a.H + gy) * a.W + gx;
+            const int lin = j * kTcM + i;
+            const int r = a.wide ? j : lin / a.rs, c = a.wide ? i : lin % a.rs;
+            const bool valid = c < a.Wt && r < a.TR && y0 + r < a.H;
+            const int64_t pix = ((int64_t)n * a.H + y0 + r) * a.W + x0 + c;
             for (int cl = 0; cl < a.Np; cl += 16) {
                 float v[16];
                 tmem_ld16(trow + (uint32_t)(j * a.Np + cl), v);
+                if (!valid) continue;
                 const int c0 = co0 + cl;
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int co = c0 + i;
+                for (int q = 0; q < 16; ++q) {
+                    const int co = c0 + q;
                     if (co < a.Co) {
-                        if (a.bias) v[i] += a.bias[co];
-                        if (a.relu) v[i] = fmaxf(v[i], 0.f);
+                        if (a.bias) v[q] += a.bias[co];
+                        if (a.relu) v[q] = fmaxf(v[q], 0.f);
                     }
                 }
                 if (a.out_f32) {
                     float* o = static_cast<float*>(a.out) + pix * a.Co;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        if (c0 + i < a.Co) o[c0 + i] = v[i];
+                    for (int q = 0; q < 16; ++q)
+                        if (c0 + q < a.Co) o[c0 + q] = v[q];
                 } else {
                     __nv_bfloat16* o = static_cast<__nv_bfloat16*>(a.out) + pix * a.Co + c0;
                     if (c0 + 16 <= a.Co && (a.Co % 8) == 0) {
                         uint4 w0, w1;
                         __nv_bfloat162 h[8];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i)
-                            h[i] = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+                        for (int q = 0; q < 8; ++q)
+                            h[q] = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
                         std::memcpy(&w0, &h[0], 16);
                         std::memcpy(&w1, &h[4], 16);
                         reinterpret_cast<uint4*>(o)[0] = w0;
                         reinterpret_cast<uint4*>(o)[1] = w1;
                     } else {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (c0 + i < a.Co) o[i] = __float2bfloat16_rn(v[i]);
+                        for (int q = 0; q < 16; ++q)
+                            if (c0 + q < a.Co) o[q] = __float2bfloat16_rn(v[q]);
                     }
                 }
             }
@@ -361,24 +395,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                      : "memory");
 }
 
-// Weights (9, Co, Ci) -> [N tiles][Ci/16 chunks][9 taps][2 halves][Np][8]
-// (Np output channels per tile), zeros for output channels >= Co and input
-// channels >= Ci.
-__global__ void tile_weights_tc_kernel(const __nv_bfloat16* w, int Co, int Ci, int Np, int nk,
-                                       int ntiles, __nv_bfloat16* wt) {
-    const int64_t per_tile = (int64_t)nk * 9 * 2 * Np * 8;
+// Weights (9, Co, Ci) -> [N tiles][Ci / Kc chunks][9 taps][Np output
+// channels][Kc input channels], each output channel's row of 2 Kc bytes
+// swizzled as the TMA would place it in a 1024-byte aligned region (a tap's
+// block of Np rows is a multiple of the swizzle's repeat); zeros for output
+// channels >= Co.
+__global__ void tile_weights_tc_kernel(const __nv_bfloat16* w, int Co, int Ci, int Kc, int Np,
+                                       int nk, int ntiles, __nv_bfloat16* wt) {
+    const int64_t per_tile = (int64_t)nk * 9 * Np * Kc;
     const int64_t total = per_tile * ntiles;
+    const int swb = 2 * Kc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i % per_tile;
         const int tile = (int)(i / per_tile);
-        const int j = (int)(r % 8);
-        const int co = tile * Np + (int)((r / 8) % Np);
-        const int h = (int)((r / (8 * Np)) % 2);
-        const int t = (int)((r / (16 * Np)) % 9);
-        const int k = (int)(r / (144 * (int64_t)Np));
-        const int ci = k * kTcChunk + 8 * h + j;
-        wt[i] = (co < Co && ci < Ci) ? w[((int64_t)t * Co + co) * Ci + ci] : __float2bfloat16(0.f);
+        const int e = (int)(r % Kc);  // element of the unswizzled row
+        const int row = (int)((r / Kc) % Np);
+        const int t = (int)((r / ((int64_t)Kc * Np)) % 9);
+        const int k = (int)(r / ((int64_t)Kc * Np * 9));
+        const int co = tile * Np + row;
+        const int ci = k * Kc + e;
+        const uint32_t off = swizzle_off((uint32_t)(row * swb + e * 2), swb);
+        const int64_t dst = i - e - (int64_t)row * Kc + off / 2;
+        wt[dst] = (co < Co && ci < Ci) ? w[((int64_t)t * Co + co) * Ci + ci] : __float2bfloat16(0.f);
     }
 }
 
@@ -401,18 +440,17 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// pixel tile of an H x W image: R rows of Wt pixels, R * Wt = 128
-static bool tc_tile(int H, int W, int* R, int* Wt) {
-    if (W >= 128) {
-        if (W % 128) return false;
-        *Wt = 128;
-        *R = 1;
-    } else {
-        if (W < 16 || 128 % W) return false;
-        *Wt = W;
-        *R = 128 / W;
-    }
-    return H % *R == 0;
+// input channels of a K chunk: 32 (64-byte swizzle) where the channel count
+// allows, else 16 (32-byte swizzle)
+static int tc_kc(int Ci) { return Ci % 32 == 0 ? 32 : 16; }
+
+// output channels per CTA: all of them (rounded up to 16) up to 128 (192 for
+// 16-channel chunks), else equal tiles of at most that
+static void tc_ntiles(int Co, int Kc, int* ntiles, int* Np) {
+    const int n16 = (Co + 15) / 16;
+    const int per = Kc == 32 ? 8 : 12;
+    *ntiles = (n16 + per - 1) / per;
+    *Np = (n16 + *ntiles - 1) / *ntiles * 16;
 }
 
 static int sm_count() {
@@ -428,67 +466,81 @@ static int sm_count() {
 }
 
 constexpr int kTcSmemMax = 227 * 1024 - 1024;  // dynamic shared memory of one CTA
+constexpr int kTcSmemSM = 228 * 1024;          // shared memory of an SM
+constexpr int kTcMaxAcc = 4;                   // accumulators per CTA
+constexpr int kTcMaxCols = 256;                // TMEM columns per CTA (two CTAs per SM)
 
-// The tile plan: m accumulators per CTA -- the largest of 4, 2, 1 that
-// divides the image rows, fits TMEM (m Np <= 512 columns) and two stages of
-// shared memory, and still leaves two CTAs per SM -- and three stages where
-// they fit.
-static bool tc_plan(int N, int H, int W, int Np, int ntiles, nn::ConvTcArgs* a) {
-    int R, Wt;
-    if (!tc_tile(H, W, &R, &Wt)) return false;
-    a->R = R;
-    a->Wt = Wt;
-    a->wide = Wt == 128 ? 1 : 0;
-    a->rs = a->wide ? Wt + 2 : Wt;
-    a->nc = a->wide ? 1 : 3;
-    for (int m = 4; m >= 1; m /= 2) {
-        if (H % (m * R) || m * Np > 512) continue;
-        const int64_t ctas = (int64_t)N * (H / (m * R)) * (W / Wt) * ntiles;
-        if (m > 1 && ctas < 2 * sm_count()) continue;
-        const int box = (m * R + 2) * a->rs * 16;
-        const int copy = (box + 127) / 128 * 128;
-        const int stage = (2 * a->nc * copy + 18 * Np * 16 + 1023) / 1024 * 1024;
-        if (2 * stage + 1024 > kTcSmemMax) continue;
-        a->m = m;
-        a->box_bytes = box;
-        a->copy_bytes = copy;
-        a->stage_bytes = stage;
-        a->stages = 3 * stage + 1024 <= kTcSmemMax ? 3 : 2;
-        a->tmem_cols = 32;
-        while (a->tmem_cols < m * Np) a->tmem_cols *= 2;
-        return true;
+// The tile plan: TR rows per CTA (m accumulators), chosen for the fraction of
+// useful MMA lanes, of halo rows loaded once and of rows inside the image,
+// as long as two waves of CTAs remain; up to three stages.
+static bool tc_plan(int N, int H, int W, int Np, int ntiles, int nk, nn::ConvTcArgs* a) {
+    a->Wt = W <= 128 ? W : 128;
+    a->rs = a->Wt + 2;
+    a->wide = a->Wt == 128 ? 1 : 0;
+    a->tiles_x = W / a->Wt;
+    const int b_bytes = (9 * Np * a->swb + 1023) / 1024 * 1024;
+    double best = -1.0;
+    for (int TR = 1; TR <= H && TR <= 64; ++TR) {
+        const int m = a->wide ? TR : (TR * a->rs + nn::kTcM - 1) / nn::kTcM;
+        if (m > kTcMaxAcc || m * Np > kTcMaxCols) break;
+        const int rows = a->wide ? (TR + 2) * a->rs : std::max((TR + 2) * a->rs, nn::kTcM * m + 2 * a->rs + 2);
+        const int a_bytes = (rows * a->swb + 1023) / 1024 * 1024;
+        const int stage = a_bytes + b_bytes;
+        int ns = nk == 1 ? 1 : 3;
+        while (ns > 1 && ns * stage + 1024 > kTcSmemMax) --ns;
+        if (ns * stage + 1024 > kTcSmemMax || (nk > 1 && ns < 2)) continue;
+        const int ty = (H + TR - 1) / TR;
+        const int64_t ctas = (int64_t)N * ty * a->tiles_x * ntiles;
+        double score = (double)(TR * a->Wt) / (m * nn::kTcM) * TR / (TR + 2.0) * H / (double)(ty * TR);
+        if (ctas < 2 * sm_count()) score *= (double)ctas / (2 * sm_count());
+        if (score > best + 1e-9) {
+            best = score;
+            a->TR = TR;
+            a->m = m;
+            a->tiles_y = ty;
+            a->a_bytes = a_bytes;
+            a->box_bytes = (TR + 2) * a->rs * a->swb;
+            a->stage_bytes = stage;
+            a->stages = ns;
+        }
     }
-    return false;
-}
-
-// output channels per CTA: all of them (rounded up to 16) up to 192, else
-// equal tiles of at most 192
-static void tc_ntiles(int Co, int* ntiles, int* Np) {
-    const int n16 = (Co + 15) / 16;
-    *ntiles = (n16 + 11) / 12;
-    *Np = (n16 + *ntiles - 1) / *ntiles * 16;
+    if (best < 0) return false;
+    a->tmem_cols = 32;
+    while (a->tmem_cols < a->m * Np) a->tmem_cols *= 2;
+    return true;
 }
 
 int64_t tc_tiled_weight_elems(int Ci, int Co) {
+    const int Kc = tc_kc(Ci);
     int nt, Np;
-    tc_ntiles(Co, &nt, &Np);
-    return (int64_t)nt * ((Ci + nn::kTcChunk - 1) / nn::kTcChunk) * 9 * 2 * Np * 8;
+    tc_ntiles(Co, Kc, &nt, &Np);
+    return (int64_t)nt * (Ci / Kc) * 9 * Np * Kc;
 }
 
 bool tc_conv_supported(int H, int W, int C1, int C2, int Co) {
-    int R, Wt;
-    return tc_tile(H, W, &R, &Wt) && C1 >= 16 && C1 % 16 == 0 && C2 % 16 == 0 && Co >= 1 &&
-           (C2 == 0 || (H % 2 == 0 && W % 2 == 0)) && encode_fn() != nullptr;
+    const int Ci = C1 + C2;
+    if (H < 1 || W < 1 || (W > 128 && W % 128) || C1 < 16 || C1 % 16 || C2 < 0 || C2 % 16 ||
+        Co < 1 || (C2 > 0 && (H % 2 || W % 2)) || C1 % tc_kc(Ci) || encode_fn() == nullptr)
+        return false;
+    nn::ConvTcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.Kc = tc_kc(Ci);
+    a.swb = 2 * a.Kc;
+    int nt, Np;
+    tc_ntiles(Co, a.Kc, &nt, &Np);
+    return tc_plan(1, H, W, Np, nt, Ci / a.Kc, &a);
 }
 
 cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_t s) {
+    const int Kc = tc_kc(Ci);
     int nt, Np;
-    tc_ntiles(Co, &nt, &Np);
-    const int nk = (Ci + nn::kTcChunk - 1) / nn::kTcChunk;
-    const int64_t total = (int64_t)nt * nk * 9 * 2 * Np * 8;
+    tc_ntiles(Co, Kc, &nt, &Np);
+    const int nk = Ci / Kc;
+    const int64_t total = (int64_t)nt * nk * 9 * Np * Kc;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 4096);
     nn::tile_weights_tc_kernel<<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(w), Co, Ci,
-                                                      Np, nk, nt, static_cast<__nv_bfloat16*>(wt));
+                                                      Kc, Np, nk, nt,
+                                                      static_cast<__nv_bfloat16*>(wt));
     return cudaGetLastError();
 }
 
@@ -507,33 +559,41 @@ cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cud
     a.C1 = c.C1;
     a.C2 = c.C2;
     a.Co = c.Co;
+    a.Kc = tc_kc(c.C1 + c.C2);
+    a.swb = 2 * a.Kc;
+    a.swcode = a.Kc == 32 ? 4 : 6;
+    a.nk = (c.C1 + c.C2) / a.Kc;
+    a.nk1 = c.C1 / a.Kc;
     int ntiles = 1;
-    tc_ntiles(c.Co, &ntiles, &a.Np);
-    if (!tc_plan(c.N, c.H, c.W, a.Np, ntiles, &a)) return cudaErrorInvalidValue;
-    a.nk = (c.C1 + c.C2) / nn::kTcChunk;
+    tc_ntiles(c.Co, a.Kc, &ntiles, &a.Np);
+    if (!tc_plan(c.N, c.H, c.W, a.Np, ntiles, a.nk, &a)) return cudaErrorInvalidValue;
     a.relu = c.relu;
     a.out_f32 = c.out_f32;
     // the full-resolution input as a 4-D tensor (channels, x, y, image); one
-    // box is 8 channels x rs pixels x (m R + 2) rows of one image
+    // box is Kc channels x rs pixels x (TR + 2) rows of one image, swizzled
     CUtensorMap map;
     std::memset(&map, 0, sizeof(map));
     cuuint64_t dims[4] = {(cuuint64_t)c.C1, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.N};
     cuuint64_t strides[3] = {(cuuint64_t)c.C1 * 2, (cuuint64_t)c.W * c.C1 * 2,
                              (cuuint64_t)c.H * c.W * c.C1 * 2};
-    cuuint32_t box[4] = {8, (cuuint32_t)a.rs, (cuuint32_t)(a.m * a.R + 2), 1};
+    cuuint32_t box[4] = {(cuuint32_t)a.Kc, (cuuint32_t)a.rs, (cuuint32_t)(a.TR + 2), 1};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4,
                              const_cast<__nv_bfloat16*>(c.in1), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     int smem = a.stages * a.stage_bytes + 1024;
-    // more than half of TMEM: one CTA per SM, so that no allocation waits
-    if (a.tmem_cols > 256) smem = std::max(smem, 120 * 1024);
+    // no more CTAs on an SM than its tensor memory holds, so that no
+    // allocation waits
+    const int by_tmem = 512 / a.tmem_cols;
+    smem = std::max(smem, kTcSmemSM / (by_tmem + 1) - 1024 + 256);
+    smem = std::min(smem, kTcSmemMax);
     cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    const int tiles = c.N * (c.H / (a.m * a.R)) * (c.W / a.Wt);
+    const int tiles = c.N * a.tiles_y * a.tiles_x;
     nn::conv3x3_tc_kernel<<<dim3(tiles, ntiles), nn::kTcThreads, smem, s>>>(map, a);
     return cudaGetLastError();
 }

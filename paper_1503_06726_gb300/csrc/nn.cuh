@@ -59,10 +59,10 @@ __global__ void scale_kernel(const float* in, int Cin, float* out, const float* 
 }  // namespace nn
 
 // The tcgen05 convolution (conv_tc.cu): whether a layer's shape is supported
-// (H x W tiles of 128 pixels with W >= 16, channels multiples of 16, at most
-// 192 output channels), the element count of its tiled weights, the tiling
-// of (9, Co, Ci) weights, and the convolution itself (out as nn::ConvArgs,
-// the tiled weights in place of c.w; err raised when a bounded wait ran out).
+// (W up to 128 or a multiple of 128, channels multiples of 16, C1 a multiple
+// of the chunk width), the element count of its tiled weights, the tiling of
+// (9, Co, Ci) weights, and the convolution itself (out as nn::ConvArgs, the
+// tiled weights in place of c.w; err raised when a bounded wait ran out).
 bool tc_conv_supported(int H, int W, int C1, int C2, int Co);
 int64_t tc_tiled_weight_elems(int Ci, int Co);
 cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_t s);

@@ -5,12 +5,13 @@ warp-level mma.sync kernel of lbib_nn_conv3x3.
 Tolerances as for the other layer tests: BF16-exact inputs and weights, so
 only the FP32 accumulation order differs: relative L-infinity 1e-5 in FP32
 output; BF16 output within 8e-3 (one rounding of 2^-8 relative).  The
-kernel's error word stays zero.  Shapes cover every pixel tile (W = 16, 32,
-64: several rows per tile, three kx-shifted halo copies; 128, 256, 640,
-1280: rows of 128 under one halo), one and several accumulators per CTA
-(the larger images leave enough CTAs for 4 accumulators, or 2 at 192
-channels), the decoder's upsampled second input, an output wider than one
-CTA's 192 channels (two tiles), the one-channel final layer and the data
+kernel's error word stays zero.  Shapes cover tiles of rows of 128 (one
+accumulator per row; W = 128, 256, 640, 1280) and of whole narrower rows
+(accumulators over the row-major halo positions; W = 8 .. 64, and 48, not a
+power of two), one and several accumulators per CTA, tiles that overhang
+the image's last row, 16- and 32-channel chunks (32- and 64-byte
+swizzles), the decoder's upsampled second input in both, an output wider
+than one CTA (two N tiles), the one-channel final layer and the data
 gradient through flipped weights.
 """
 import numpy as np
@@ -62,16 +63,19 @@ def _weights(lb, w, Ci, Co, st):
 
 
 @pytest.mark.parametrize("N,H,W,C1,C2,Co", [
-    (2, 16, 32, 16, 32, 48),    # 4 rows x 32 per tile, upsampled decoder input
-    (1, 32, 16, 32, 0, 64),     # 8 rows x 16
-    (2, 8, 64, 16, 16, 32),     # 2 rows x 64, upsampled
-    (1, 3, 128, 64, 0, 96),     # one row of 128
-    (2, 2, 256, 32, 0, 192),    # two tiles per row, 192 channels in one CTA
+    (2, 16, 32, 16, 32, 48),    # 16-channel chunks, upsampled input, overhanging tile
+    (1, 32, 16, 32, 0, 64),     # 32-channel chunk, narrow rows
+    (2, 8, 64, 16, 32, 32),     # upsampled
+    (1, 3, 128, 64, 0, 96),     # rows of 128, two chunks
+    (2, 2, 256, 32, 0, 192),    # two N tiles of 96, two tiles per row
     (1, 16, 16, 48, 0, 320),    # two N tiles of 160
     (1, 16, 64, 32, 0, 1),      # the one-channel final layer
-    (2, 128, 640, 16, 16, 48),  # rows of 128, 4 accumulators, upsampled input
-    (1, 64, 1280, 16, 0, 192),  # rows of 128, 2 accumulators of 192 channels
-    (40, 64, 64, 16, 16, 32),   # 2 rows x 64, 4 accumulators, upsampled input
+    (4, 8, 8, 32, 0, 64),       # the 8 x 8 level: one tile per image
+    (3, 50, 48, 32, 0, 32),     # W = 48, 50 rows
+    (2, 32, 256, 32, 32, 32),   # upsampled input in a 32-channel chunk
+    (2, 128, 640, 16, 32, 48),  # rows of 128, 4 accumulators, upsampled input
+    (1, 64, 1280, 16, 0, 192),  # rows of 128, 192 channels in one CTA
+    (40, 64, 64, 16, 32, 32),   # 7 rows x 66 halo positions in 4 accumulators
 ])
 def test_tc_conv_matches_oracle_and_mma_sync(lb, orc, N, H, W, C1, C2, Co):
     import torch
@@ -142,7 +146,10 @@ def test_tc_conv_data_gradient(lb, orc):
 
 def test_tc_conv_shape_support(lb):
     L = lb.load()
-    assert L.lbib_nn_conv3x3_tc_supported(8, 8, 32, 0, 32) == 0      # W = 8: below one tile
+    assert L.lbib_nn_conv3x3_tc_supported(16, 192, 32, 0, 32) == 0   # W > 128, not rows of 128
     assert L.lbib_nn_conv3x3_tc_supported(16, 16, 8, 0, 32) == 0     # C1 not a multiple of 16
-    assert L.lbib_nn_conv3x3_tc_supported(2, 32, 16, 0, 32) == 0     # H not a multiple of 4
+    assert L.lbib_nn_conv3x3_tc_supported(16, 16, 16, 16, 32) == 0   # 32-channel chunks, C1 = 16
+    assert L.lbib_nn_conv3x3_tc_supported(15, 16, 32, 16, 32) == 0   # upsampled input, odd H
+    assert L.lbib_nn_conv3x3_tc_supported(8, 8, 32, 0, 32) == 1
+    assert L.lbib_nn_conv3x3_tc_supported(2, 32, 16, 0, 32) == 1
     assert L.lbib_nn_conv3x3_tc_supported(256, 256, 16, 0, 32) == 1
