@@ -77,15 +77,15 @@ def alg_bytes_per_node(precision: str, n_species: int) -> int:
     return 2 * 9 * b + 2 * 5 * n_species * b
 
 
-def workload(name: str):
+def workload(name: str, c3_n: int = 4096):
     if name == "c2":
         return li.config2(), "fp32"
     if name == "c3-fp32":
-        return li.config3(), "fp32"
+        return li.config3(n=c3_n), "fp32"
     if name == "c3-fp16":
-        return li.config3(), "fp16"
+        return li.config3(n=c3_n), "fp16"
     if name == "c3-fp64":
-        return li.config3(), "fp64"
+        return li.config3(n=c3_n), "fp64"
     if name == "c4":
         return li.config4(), "fp32"
     if name == "turing":
@@ -773,7 +773,7 @@ def run_gb300(args, rank, world, dist):
     lbib.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w, prec = workload(args.workload)
+    w, prec = workload(args.workload, args.c3_n)
     p, T = w.params, w.tissue
     N = p.nx * p.ny
     sim = lbib.Simulation(p, lbib.PRECISIONS[prec], T.n_vertices, T.n_cells, device=dev)
@@ -922,7 +922,7 @@ def run_gb300(args, rank, world, dist):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    w, prec = workload(args.workload)
+    w, prec = workload(args.workload, args.c3_n)
     p = w.params
     # bounded sample: at most a minute of whole coupled oracle steps
     max_steps = max(1, args.steps)
@@ -949,6 +949,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3-fp32")
     ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--c3-n", type=int, default=4096,
+                    help="side of the c3 tissue (4096: the configuration; smaller for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
