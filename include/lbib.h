@@ -514,7 +514,7 @@ int lbib_nn_weight_copies(int32_t Ci, int32_t Co, int32_t Cip, int32_t Cop, cons
  *                          elements; d_wt NULL: size only)
  *   lbib_nn_conv3x3_tc     out = conv3x3([in1, upsample2(in2)]) + bias (ReLU
  *                          if relu) as lbib_nn_conv3x3, with the tiled weights;
- *                          d_in1, d_in2, d_wt 16-byte aligned; d_err a device
+ *                          d_in1, d_in2, d_wt, d_out 16-byte aligned; d_err a device
  *                          word the caller zeroes: nonzero afterwards when a
  *                          bounded wait of the kernel ran out (the output is
  *                          then undefined)

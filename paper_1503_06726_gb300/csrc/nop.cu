@@ -647,8 +647,8 @@ int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, 
         !tc_conv_supported(H, W, C1, C2, Co))
         return set_thread_error(LBIB_E_PARAM, "lbib_nn_conv3x3_tc: unsupported shape or arguments");
     if (reinterpret_cast<uintptr_t>(d_in1) % 16 || reinterpret_cast<uintptr_t>(d_wt) % 16 ||
-        (d_in2 && reinterpret_cast<uintptr_t>(d_in2) % 16))
-        return set_thread_error(LBIB_E_PARAM, "lbib_nn_conv3x3_tc: inputs need 16-byte alignment");
+        reinterpret_cast<uintptr_t>(d_out) % 16 || (d_in2 && reinterpret_cast<uintptr_t>(d_in2) % 16))
+        return set_thread_error(LBIB_E_PARAM, "lbib_nn_conv3x3_tc: buffers need 16-byte alignment");
     nn::ConvArgs a;
     a.in1 = static_cast<const bf16*>(d_in1);
     a.in2 = static_cast<const bf16*>(d_in2);
