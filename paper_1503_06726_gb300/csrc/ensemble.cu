@@ -467,6 +467,7 @@ lbib_ctx* lbib_ensemble_tissue(lbib_ensemble* e, int32_t t) {
 }
 
 int lbib_ensemble_step(lbib_ensemble* e, int32_t n_steps) {
+    NvtxRange nvtx_range("lbib_ensemble_step");
     if (!e) return LBIB_E_PARAM;
     if (n_steps < 0) return ens_fail(e, LBIB_E_PARAM, "n_steps must be >= 0");
     if (n_steps == 0) return LBIB_OK;

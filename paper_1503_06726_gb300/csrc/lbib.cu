@@ -359,6 +359,7 @@ static cudaError_t ensure_moments(lbib_ctx* c) {
 }
 
 static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl = false) {
+    NvtxRange nvtx_range("lbib.lattice_update");
     LatticeArgs a = lattice_args(c, src_buf, out);
     return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,
                           coefs_of(c), c->block, c->stream, pdl && c->nC > 0, c->lattice_pairs);
@@ -366,6 +367,7 @@ static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl 
 
 static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next,
                               bool pdl = false) {
+    NvtxRange nvtx_range("lbib.ib_cells");
     if (c->nC == 0) return cudaSuccess;
     return launch_ib(c->p.precision, ib_args(c, move, prep, out_next), c->maxv_cell, c->stream,
                      pdl);
@@ -601,6 +603,7 @@ int lbib_create(const lbib_params* params, int32_t max_vertices, int32_t max_cel
 int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const double* xy,
                    const double* rest_len, const double* k_spring, const double* pressure,
                    const uint8_t* src_flag) {
+    NvtxRange nvtx_range("lbib_set_cells");
     if (!c) return LBIB_E_PARAM;
     if (n_cells < 0 || n_cells > c->maxC) return fail(c, LBIB_E_CELLS, "n_cells exceeds capacity");
     if (n_cells > 0 && (!cell_off || !xy)) return fail(c, LBIB_E_CELLS, "cell_off and xy are required");
@@ -822,6 +825,7 @@ int lbib_set_species(lbib_ctx* c, int32_t s, const double* phi) {
 }
 
 int lbib_step(lbib_ctx* c, int32_t n_steps) {
+    NvtxRange nvtx_range("lbib_step");
     if (!c) return LBIB_E_PARAM;
     if (n_steps < 0) return fail(c, LBIB_E_PARAM, "n_steps must be >= 0");
     if (n_steps == 0) return LBIB_OK;
@@ -866,6 +870,7 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
 }
 
 int lbib_advance(lbib_ctx* c, int32_t n_steps) {
+    NvtxRange nvtx_range("lbib_advance");
     if (!c) return LBIB_E_PARAM;
     if (n_steps < 0) return fail(c, LBIB_E_PARAM, "n_steps must be >= 0");
     if (n_steps == 0) return LBIB_OK;
@@ -948,6 +953,7 @@ int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
 
 int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double* uy, double* phi,
                     double* xy, double* area, int32_t* id, double* force, double* vforce) {
+    NvtxRange nvtx_range("lbib_get_fields");
     if (!c) return LBIB_E_PARAM;
     const uint32_t lattice_bits = LBIB_RHO | LBIB_U | LBIB_PHI | LBIB_ID | LBIB_FORCE;
     if ((which & lattice_bits) && !c->fields_valid)

@@ -4,6 +4,9 @@
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#ifndef LBIB_NO_NVTX
+#include <nvtx3/nvToolsExt.h>
+#endif
 #include <stdint.h>
 
 #include <cmath>
@@ -12,6 +15,27 @@
 #include "../../include/lbib.h"
 
 namespace lbib {
+
+// A named NVTX range over a host call: a profiler's timeline shows each as a
+// span around the launches (or graph launches) it enqueues; without an
+// attached tool a push or pop is a test of one function pointer.  Building
+// with -DLBIB_NO_NVTX removes them.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) {
+#ifndef LBIB_NO_NVTX
+        nvtxRangePushA(name);
+#else
+        (void)name;
+#endif
+    }
+    ~NvtxRange() {
+#ifndef LBIB_NO_NVTX
+        nvtxRangePop();
+#endif
+    }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // D2Q9 velocity set in the order v0 = 0, v1..v4 = axes (cos, sin)(pi(i-1)/2),
 // v5..v8 = diagonals (1,1), (-1,1), (-1,-1), (1,-1)  (Sec. 6.1 footnotes).

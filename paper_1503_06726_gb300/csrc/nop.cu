@@ -197,6 +197,7 @@ inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) /
 cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* in2, int C1, int C2,
                      int lvl, void* out, int relu, int out_f32, const bf16* w, const bf16* wt,
                      const float* bias, int Co, int N) {
+    NvtxRange nvtx_range("nn.conv3x3");
     nn::ConvArgs a;
     a.in1 = in1;
     a.in2 = in2;
@@ -221,6 +222,7 @@ cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* i
 
 cudaError_t conv_wgrad(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* in2, int C1,
                        int C2, int lvl, const bf16* g, int N) {
+    NvtxRange nvtx_range("nn.conv3x3_wgrad");
     nn::WgradArgs a;
     a.in1 = in1;
     a.in2 = in2;
@@ -534,6 +536,7 @@ int lbib_nop_get_grads(lbib_nop* n, float* host, int64_t count) {
 
 int lbib_nop_forward(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uint8_t* d_src,
                      const double* D, const double* decay, const double* src_rate, float* d_phi) {
+    NvtxRange nvtx_range("lbib_nop_forward");
     if (!params_ok(n) || N < 1 || N > n->B || !d_mask || !d_src || !D || !decay || !src_rate ||
         !d_phi)
         return nop_fail(n, LBIB_E_PARAM, "lbib_nop_forward: invalid arguments");
@@ -553,6 +556,7 @@ int lbib_nop_train_step(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uin
                         const double* D, const double* decay, const double* src_rate,
                         const float* d_phi_target, double lr, int32_t update,
                         double* loss_out) {
+    NvtxRange nvtx_range("lbib_nop_train_step");
     if (!params_ok(n) || N < 1 || N > n->B || !d_mask || !d_src || !D || !decay || !src_rate ||
         !d_phi_target)
         return nop_fail(n, LBIB_E_PARAM, "lbib_nop_train_step: invalid arguments");

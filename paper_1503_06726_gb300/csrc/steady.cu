@@ -240,6 +240,7 @@ extern "C" {
 int lbib_label_cells(int32_t nx, int32_t ny, int32_t bc_y, int32_t n_cells,
                      const int32_t* d_cell_off, const double* d_xy, const uint8_t* d_src_flag,
                      int32_t* d_id, uint8_t* d_src, void* cuda_stream) {
+    NvtxRange nvtx_range("lbib_label_cells");
     if (nx < 8 || ny < 8 || bc_y < 0 || bc_y > 1 || n_cells < 0 || !d_id)
         return set_thread_error(LBIB_E_PARAM, "lbib_label_cells: invalid arguments");
     if (n_cells > 0 && (!d_cell_off || !d_xy || !d_src_flag))
@@ -300,6 +301,7 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
                       float* d_phi_out, int64_t* steps_out, double* resid_out,
                       int32_t* fallback_out, void* d_workspace, uint64_t ws_bytes,
                       void* cuda_stream) {
+    NvtxRange nvtx_range("lbib_steady_solve");
     if (nx < 8 || ny < 8 || batch < 1 || batch > 65535 || !d_src || !D || !decay ||
         !src_rate || !d_phi_out || !steps_out || !resid_out || check_every < 1 ||
         max_steps < 0 || !(tol >= 0.0))

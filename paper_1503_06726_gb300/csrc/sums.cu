@@ -158,6 +158,7 @@ using namespace lbib;
 
 extern "C" int lbib_get_sums(lbib_ctx* c, double* global_sums, double* cell_sums,
                              uint32_t* nonfinite) {
+    NvtxRange nvtx_range("lbib_get_sums");
     if (!c || !global_sums) return LBIB_E_PARAM;
     if (!c->fields_valid) {
         c->err = "lbib_get_sums: the last step wrote no output fields (need lbib_step)";

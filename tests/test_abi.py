@@ -121,3 +121,16 @@ def test_binding_refuses_options_without_a_cuda_path(L):
     w.params.mass_beta, w.params.noflux, w.params.noflux_dynamic = 0.0, 1, 1
     with pytest.raises(ValueError):
         L.make_params(w.params, L.LBIB_FP32)
+
+
+def test_nvtx_ranges_are_built_in(L):
+    """The host calls that enqueue device work open named NVTX ranges (a
+    profiler's timeline shows them around their launches); their names are in
+    the library."""
+    from paper_1503_06726_gb300 import build
+    blob = open(build.LIB, "rb").read()
+    for name in (b"lbib_step", b"lbib_advance", b"lbib.lattice_update", b"lbib.ib_cells",
+                 b"lbib_get_fields", b"lbib_get_sums", b"lbib_ensemble_step",
+                 b"lbib_steady_solve", b"lbib_nop_train_step", b"nn.conv3x3",
+                 b"nn.conv3x3_wgrad"):
+        assert name + b"\x00" in blob, name
