@@ -56,6 +56,7 @@ struct ConvTcArgs {
     const __nv_bfloat16* wt;   // tiled weights, [N tiles][nk][9][Np][Kc] swizzled
     const float* bias;         // (Co) or NULL
     void* out;                 // (N, H, W, Co) bf16, or fp32 when out_f32
+    const __nv_bfloat16* gate; // (N, H, W, Co) or NULL: out = 0 where !(gate > 0)
     unsigned* err;             // raised when a bounded wait runs out
     int N, H, W, C1, C2, Co;
     int Kc;                    // input channels of a chunk (32 or 16)
@@ -359,6 +360,26 @@ __global__ void __launch_bounds__(kTcThreads)
                         if (a.relu) v[q] = fmaxf(v[q], 0.f);
                     }
                 }
+                if (a.gate) {
+                    const __nv_bfloat16* gt = a.gate + pix * a.Co + c0;
+                    if (c0 + 16 <= a.Co && (a.Co % 8) == 0) {
+                        __nv_bfloat162 h[8];
+                        const uint4 g0 = __ldg(reinterpret_cast<const uint4*>(gt));
+                        const uint4 g1 = __ldg(reinterpret_cast<const uint4*>(gt) + 1);
+                        std::memcpy(&h[0], &g0, 16);
+                        std::memcpy(&h[4], &g1, 16);
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const float2 f = __bfloat1622float2(h[q]);
+                            if (!(f.x > 0.f)) v[2 * q] = 0.f;
+                            if (!(f.y > 0.f)) v[2 * q + 1] = 0.f;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (c0 + q < a.Co && !(__bfloat162float(gt[q]) > 0.f)) v[q] = 0.f;
+                    }
+                }
                 if (a.out_f32) {
                     float* o = static_cast<float*>(a.out) + pix * a.Co;
 #pragma unroll
@@ -418,6 +439,78 @@ __global__ void tile_weights_tc_kernel(const __nv_bfloat16* w, int Co, int Ci, i
         const uint32_t off = swizzle_off((uint32_t)(row * swb + e * 2), swb);
         const int64_t dst = i - e - (int64_t)row * Kc + off / 2;
         wt[dst] = (co < Co && ci < Ci) ? w[((int64_t)t * Co + co) * Ci + ci] : __float2bfloat16(0.f);
+    }
+}
+
+// The fused weight refresh: for layer blockIdx.y, from its FP32 master
+// weights w (9, Ci, Co): the BF16 forward copy wf (9, Co, Ci), the
+// tap-flipped copy wd (9, Ci, Co) (wd[8 - t][i][o] = w[t][i][o]) and the
+// tcgen05 tilings of both (tile_weights_tc_kernel's layout, element values
+// taken straight from w), in one grid-stride pass per layer.
+struct TileGeom {
+    int Kc, Np, nk, nt;
+};
+__device__ __forceinline__ TileGeom tile_geom(int Ci, int Co) {
+    TileGeom g;
+    g.Kc = Ci % 32 == 0 ? 32 : 16;
+    const int n16 = (Co + 15) / 16;
+    const int per = g.Kc == 32 ? 8 : 12;
+    g.nt = (n16 + per - 1) / per;
+    g.Np = (n16 + g.nt - 1) / g.nt * 16;
+    g.nk = Ci / g.Kc;
+    return g;
+}
+// element i of the tiling of a (9, Co, Ci) array: where it goes (dst) and
+// which (tap, co, ci) of the array it holds; false for padding (co >= Co)
+__device__ __forceinline__ bool tiled_source(int64_t i, int Ci, int Co, const TileGeom& g,
+                                             int64_t* dst, int* t, int* co, int* ci) {
+    const int64_t per_tile = (int64_t)g.nk * 9 * g.Np * g.Kc;
+    const int64_t r = i % per_tile;
+    const int tile = (int)(i / per_tile);
+    const int e = (int)(r % g.Kc);
+    const int row = (int)((r / g.Kc) % g.Np);
+    *t = (int)((r / ((int64_t)g.Kc * g.Np)) % 9);
+    const int k = (int)(r / ((int64_t)g.Kc * g.Np * 9));
+    *co = tile * g.Np + row;
+    *ci = k * g.Kc + e;
+    const int swb = 2 * g.Kc;
+    const uint32_t off = swizzle_off((uint32_t)(row * swb + e * 2), swb);
+    *dst = i - e - (int64_t)row * g.Kc + off / 2;
+    return *co < Co && *ci < Ci;
+}
+__global__ void refresh_weights_kernel(const WeightSet* sets) {
+    const WeightSet ws = sets[blockIdx.y];
+    const int Ci = ws.Ci, Co = ws.Co;
+    const int64_t n_copy = 9LL * Ci * Co;
+    const TileGeom gf = tile_geom(Ci, Co), gd = tile_geom(Co, Ci);
+    const int64_t n_f = ws.wft ? (int64_t)gf.nt * gf.nk * 9 * gf.Np * gf.Kc : 0;
+    const int64_t n_d = ws.wdt ? (int64_t)gd.nt * gd.nk * 9 * gd.Np * gd.Kc : 0;
+    const int64_t total = n_copy + n_f + n_d;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < n_copy) {
+            const int o = (int)(i % Co);
+            const int in = (int)((i / Co) % Ci);
+            const int t = (int)(i / ((int64_t)Co * Ci));
+            const __nv_bfloat16 v = __float2bfloat16(ws.w[i]);
+            ws.wf[((int64_t)t * Co + o) * Ci + in] = v;
+            ws.wd[((int64_t)(8 - t) * Ci + in) * Co + o] = v;
+        } else if (i < n_copy + n_f) {
+            // the forward tiling: the (9, Co, Ci) array is wf
+            int64_t dst;
+            int t, co, ci;
+            const bool in = tiled_source(i - n_copy, Ci, Co, gf, &dst, &t, &co, &ci);
+            ws.wft[dst] = in ? __float2bfloat16(ws.w[((int64_t)t * Ci + ci) * Co + co])
+                             : __float2bfloat16(0.f);
+        } else {
+            // the data-gradient tiling: the (9, Ci, Co) array is wd, whose
+            // output channels are the forward input channels
+            int64_t dst;
+            int t, co, ci;
+            const bool in = tiled_source(i - n_copy - n_f, Co, Ci, gd, &dst, &t, &co, &ci);
+            ws.wdt[dst] = in ? __float2bfloat16(ws.w[((int64_t)(8 - t) * Ci + co) * Co + ci])
+                             : __float2bfloat16(0.f);
+        }
     }
 }
 
@@ -544,6 +637,17 @@ cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_
     return cudaGetLastError();
 }
 
+int64_t weight_set_elems(int Ci, int Co) {
+    return 9LL * Ci * Co + tc_tiled_weight_elems(Ci, Co) + tc_tiled_weight_elems(Co, Ci);
+}
+
+cudaError_t refresh_weight_sets(const WeightSet* d_sets, int n, int64_t max_elems, cudaStream_t s) {
+    if (n < 1) return cudaSuccess;
+    const int bx = (int)std::min<int64_t>((max_elems + 255) / 256, 1024);
+    nn::refresh_weights_kernel<<<dim3(bx, n), 256, 0, s>>>(d_sets);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cudaStream_t s) {
     if (!tc_conv_supported(c.H, c.W, c.C1, c.C2, c.Co)) return cudaErrorInvalidValue;
     nn::ConvTcArgs a;
@@ -552,6 +656,7 @@ cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cud
     a.wt = static_cast<const __nv_bfloat16*>(wt);
     a.bias = c.bias;
     a.out = c.out;
+    a.gate = c.gate;
     a.err = err;
     a.N = c.N;
     a.H = c.H;

@@ -167,6 +167,11 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_fwd_kernel(ConvArgs a) {
                     v0 = fmaxf(v0, 0.f);
                     v1 = fmaxf(v1, 0.f);
                 }
+                if (a.gate) {
+                    const __nv_bfloat16* gt = a.gate + pix * a.Co + co;
+                    if (!(__bfloat162float(gt[0]) > 0.f)) v0 = 0.f;
+                    if (co + 1 < a.Co && !(__bfloat162float(gt[1]) > 0.f)) v1 = 0.f;
+                }
                 if (a.out_f32) {
                     float* o = static_cast<float*>(a.out) + pix * a.Co + co;
                     o[0] = v0;
@@ -309,18 +314,12 @@ __global__ void avgpool2_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gx, i
     gx[i] = __float2bfloat16(0.25f * v);
 }
 
-// g *= (act > 0)
-__global__ void relu_bwd_kernel(__nv_bfloat16* g, const __nv_bfloat16* act, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    if (!(__bfloat162float(act[i]) > 0.f)) g[i] = __float2bfloat16(0.f);
-}
-
 // split the gradient of a concatenation [skip (C1), upsample2(x2) (C2)]:
-// gskip += g[..., :C1]; gx2 (half res) = sum over the 2x2 children of g[..., C1:]
+// gskip += g[..., :C1]; gx2 (half res) = sum over the 2x2 children of g[..., C1:],
+// zero where !(gate2 > 0) when gate2 (x2's ReLU output) is given
 __global__ void concat_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gskip,
-                                  __nv_bfloat16* gx2, int N, int H, int W, int C1, int C2,
-                                  int accumulate_skip) {
+                                  __nv_bfloat16* gx2, const __nv_bfloat16* gate2, int N, int H,
+                                  int W, int C1, int C2, int accumulate_skip) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int C = C1 + C2;
     const int64_t nfull = (int64_t)N * H * W * C1;
@@ -342,13 +341,18 @@ __global__ void concat_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gskip,
         for (int dx = 0; dx < 2; ++dx)
             s += __bfloat162float(
                 g[(((int64_t)n * H + 2 * yo + dy) * W + 2 * xo + dx) * C + C1 + c]);
+    if (gate2 && !(__bfloat162float(gate2[j]) > 0.f)) s = 0.f;
     gx2[j] = __float2bfloat16(s);
 }
 
-// g (bf16) += h (bf16)
-__global__ void add_kernel(__nv_bfloat16* g, const __nv_bfloat16* h, int64_t n) {
+// g (bf16) = g + h where act > 0, else 0 (the sum's ReLU backward)
+__global__ void add_gate_kernel(__nv_bfloat16* g, const __nv_bfloat16* h,
+                                const __nv_bfloat16* act, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) g[i] = __float2bfloat16(__bfloat162float(g[i]) + __bfloat162float(h[i]));
+    if (i >= n) return;
+    g[i] = __bfloat162float(act[i]) > 0.f
+               ? __float2bfloat16(__bfloat162float(g[i]) + __bfloat162float(h[i]))
+               : __float2bfloat16(0.f);
 }
 
 // MSE: loss += sum (y - t)^2 / n; dy = 2 (y - t) / n  (y in channel 0 of Cy)

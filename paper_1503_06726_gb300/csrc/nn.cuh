@@ -16,6 +16,7 @@ struct ConvArgs {
     const __nv_bfloat16* w;    // (9, Co, Ci): tap, output channel, input channel
     const float* bias;         // (Co) or NULL
     void* out;                 // (N, H, W, Co) bf16, or fp32 when out_f32
+    const __nv_bfloat16* gate; // (N, H, W, Co) or NULL: out = 0 where !(gate > 0) (ReLU backward)
     int N, H, W, C1, C2, Co;
     int relu, out_f32;
 };
@@ -40,11 +41,11 @@ __global__ void avgpool2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int N,
                                 int C);
 __global__ void avgpool2_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gx, int N, int H,
                                     int W, int C);
-__global__ void relu_bwd_kernel(__nv_bfloat16* g, const __nv_bfloat16* act, int64_t n);
 __global__ void concat_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gskip,
-                                  __nv_bfloat16* gx2, int N, int H, int W, int C1, int C2,
-                                  int accumulate_skip);
-__global__ void add_kernel(__nv_bfloat16* g, const __nv_bfloat16* h, int64_t n);
+                                  __nv_bfloat16* gx2, const __nv_bfloat16* gate2, int N, int H,
+                                  int W, int C1, int C2, int accumulate_skip);
+__global__ void add_gate_kernel(__nv_bfloat16* g, const __nv_bfloat16* h,
+                                const __nv_bfloat16* act, int64_t n);
 __global__ void mse_kernel(const float* y, int Cy, const float* t, __nv_bfloat16* dy, int Cdy,
                            int64_t n, double* loss);
 __global__ void adam_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr,
@@ -67,4 +68,18 @@ bool tc_conv_supported(int H, int W, int C1, int C2, int Co);
 int64_t tc_tiled_weight_elems(int Ci, int Co);
 cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_t s);
 cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cudaStream_t s);
+
+// One layer of the fused weight refresh: the FP32 master weights w (9, Ci, Co)
+// and the BF16 copies made from them -- the forward copy wf (9, Co, Ci), the
+// tap-flipped data-gradient copy wd (9, Ci, Co) and the tcgen05 tilings of
+// both (wft, wdt).
+struct WeightSet {
+    const float* w;
+    __nv_bfloat16 *wf, *wd, *wft, *wdt;
+    int Ci, Co;
+};
+// All layers' copies in one launch (d_sets: the table in device memory, n
+// entries; max_elems: the largest per-layer element count, for the grid).
+cudaError_t refresh_weight_sets(const WeightSet* d_sets, int n, int64_t max_elems, cudaStream_t s);
+int64_t weight_set_elems(int Ci, int Co);
 }  // namespace lbib

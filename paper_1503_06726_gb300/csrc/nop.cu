@@ -120,6 +120,8 @@ struct lbib_nop {
     float* kn = nullptr;
     double* loss = nullptr;
     unsigned* tc_err = nullptr;  // raised by a tcgen05 convolution whose bounded wait ran out
+    WeightSet* wsets = nullptr;  // per layer: master weights and their BF16 copies (device table)
+    int64_t wsets_max = 0;       // the largest layer's element count over all its copies
     int64_t t = 0;           // Adam step
     std::string err;
 
@@ -158,6 +160,7 @@ void nop_layout(lbib_nop* n) {
         l.wdt = n->take<bf16>(tc_tiled_weight_elems(l.cop, l.cip));
     }
     n->tc_err = n->take<unsigned>(1);
+    n->wsets = n->take<WeightSet>(n->L.size());
     const int64_t B = n->B;
     int64_t maxg = 0;
     for (int l = 0; l < kLevels; ++l) {
@@ -196,7 +199,7 @@ inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) /
 // cost more than the warp-level kernel's register tiling, take the latter.
 cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* in2, int C1, int C2,
                      int lvl, void* out, int relu, int out_f32, const bf16* w, const bf16* wt,
-                     const float* bias, int Co, int N) {
+                     const float* bias, int Co, int N, const bf16* gate = nullptr) {
     NvtxRange nvtx_range("nn.conv3x3");
     nn::ConvArgs a;
     a.in1 = in1;
@@ -212,6 +215,7 @@ cudaError_t conv_fwd(lbib_nop* n, const Layer& l, const bf16* in1, const bf16* i
     a.Co = Co;
     a.relu = relu;
     a.out_f32 = out_f32;
+    a.gate = gate;
     (void)l;
     if (wt && a.W >= 128 && tc_conv_supported(a.H, a.W, C1, C2, Co)) return tc_conv3x3(a, wt, n->tc_err, n->stream);
     const int tiles = ((a.H + kTH - 1) / kTH) * ((a.W + kTW - 1) / kTW);
@@ -242,17 +246,10 @@ cudaError_t conv_wgrad(lbib_nop* n, const Layer& l, const bf16* in1, const bf16*
     return cudaGetLastError();
 }
 
+// The BF16 copies of every layer's weights (forward, tap-flipped, and their
+// tcgen05 tilings) from the FP32 master weights, in one launch.
 cudaError_t refresh_weights(lbib_nop* n) {
-    for (auto& l : n->L) {
-        const int64_t cnt = 9LL * l.cip * l.cop;
-        nn::weight_copies_kernel<<<blocks(cnt), 256, 0, n->stream>>>(n->param + l.off, l.cip, l.cop,
-                                                                      l.cip, l.cop, l.wf, l.wd);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = tc_tile_weights(l.wf, l.cop, l.cip, l.wft, n->stream);
-        if (e == cudaSuccess) e = tc_tile_weights(l.wd, l.cip, l.cop, l.wdt, n->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return refresh_weight_sets(n->wsets, (int)n->L.size(), n->wsets_max, n->stream);
 }
 
 cudaError_t set_inputs(lbib_nop* n, int N, const uint8_t* mask, const uint8_t* src,
@@ -321,11 +318,6 @@ cudaError_t forward(lbib_nop* n, int N) {
 cudaError_t backward(lbib_nop* n, int N) {
     const std::vector<Layer>& L = n->L;
     cudaError_t e = cudaMemsetAsync(n->grad, 0, n->P * 4, n->stream);
-    auto relu_bwd = [&](bf16* g, const bf16* act, int64_t cnt) {
-        if (e != cudaSuccess) return;
-        nn::relu_bwd_kernel<<<blocks(cnt), 256, 0, n->stream>>>(g, act, cnt);
-        e = cudaGetLastError();
-    };
     // layer indices: enc l a/b = 2l, 2l+1; dec l a/b = 12 + 2(4 - l), +1; out = 22
     auto enc = [&](int l, int ab) -> const Layer& { return L[2 * l + ab]; };
     auto dec = [&](int l, int ab) -> const Layer& { return L[12 + 2 * (kLevels - 2 - l) + ab]; };
@@ -333,8 +325,11 @@ cudaError_t backward(lbib_nop* n, int N) {
     const int64_t hw0 = (int64_t)n->H * n->W;
     // output layer
     if (e == cudaSuccess) e = conv_wgrad(n, o, n->dec_out[0], nullptr, kCh[0], 0, 0, n->dy, N);
+    // every ReLU backward is fused into the kernel that produces the gradient
+    // (the data-gradient convolutions, the concatenation split, the skip sum)
     if (e == cudaSuccess)
-        e = conv_fwd(n, o, n->dy, nullptr, o.cop, 0, 0, n->ga, 0, 0, o.wd, o.wdt, nullptr, o.cip, N);
+        e = conv_fwd(n, o, n->dy, nullptr, o.cop, 0, 0, n->ga, 0, 0, o.wd, o.wdt, nullptr, o.cip, N,
+                     n->dec_out[0]);
     bf16* g = n->ga;
     bf16* s1 = n->gb;
     bf16* s2 = n->gc;
@@ -342,11 +337,10 @@ cudaError_t backward(lbib_nop* n, int N) {
         const int64_t hw = (int64_t)(n->H >> l) * (n->W >> l);
         const Layer& a = dec(l, 0);
         const Layer& b = dec(l, 1);
-        relu_bwd(g, n->dec_out[l], N * hw * kCh[l]);
         if (e == cudaSuccess) e = conv_wgrad(n, b, n->dec_r1[l], nullptr, kCh[l], 0, l, g, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, b.wdt, nullptr, kCh[l], N);
-        relu_bwd(s1, n->dec_r1[l], N * hw * kCh[l]);
+            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, b.wdt, nullptr, kCh[l], N,
+                         n->dec_r1[l]);
         const bf16* deeper = (l == kLevels - 2) ? n->enc_out[l + 1] : n->dec_out[l + 1];
         if (e == cudaSuccess)
             e = conv_wgrad(n, a, n->enc_out[l], deeper, kCh[l], kCh[l + 1], l, s1, N);
@@ -355,8 +349,9 @@ cudaError_t backward(lbib_nop* n, int N) {
                          nullptr, kCh[l] + kCh[l + 1], N);
         if (e == cudaSuccess) {
             const int64_t tot = N * hw * kCh[l] + N * (hw / 4) * kCh[l + 1];
+            // g: the gradient of the deeper output, through its ReLU
             nn::concat_bwd_kernel<<<blocks(tot), 256, 0, n->stream>>>(
-                s2, n->gskip[l], g, N, n->H >> l, n->W >> l, kCh[l], kCh[l + 1], 0);
+                s2, n->gskip[l], g, deeper, N, n->H >> l, n->W >> l, kCh[l], kCh[l + 1], 0);
             e = cudaGetLastError();
         }
         (void)hw0;
@@ -367,15 +362,16 @@ cudaError_t backward(lbib_nop* n, int N) {
         const Layer& a = enc(l, 0);
         const Layer& b = enc(l, 1);
         if (l < kLevels - 1) {
-            nn::add_kernel<<<blocks(N * hw * kCh[l]), 256, 0, n->stream>>>(g, n->gskip[l],
-                                                                           N * hw * kCh[l]);
+            // the skip's gradient joins the deeper path's, through the ReLU
+            // (at the deepest level the concatenation split applied it)
+            nn::add_gate_kernel<<<blocks(N * hw * kCh[l]), 256, 0, n->stream>>>(
+                g, n->gskip[l], n->enc_out[l], N * hw * kCh[l]);
             e = cudaGetLastError();
         }
-        relu_bwd(g, n->enc_out[l], N * hw * kCh[l]);
         if (e == cudaSuccess) e = conv_wgrad(n, b, n->enc_r1[l], nullptr, kCh[l], 0, l, g, N);
         if (e == cudaSuccess)
-            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, b.wdt, nullptr, kCh[l], N);
-        relu_bwd(s1, n->enc_r1[l], N * hw * kCh[l]);
+            e = conv_fwd(n, b, g, nullptr, kCh[l], 0, l, s1, 0, 0, b.wd, b.wdt, nullptr, kCh[l], N,
+                         n->enc_r1[l]);
         const int cin = l == 0 ? 16 : kCh[l - 1];
         if (e == cudaSuccess) e = conv_wgrad(n, a, n->enc_in[l], nullptr, cin, 0, l, s1, N);
         if (l > 0 && e == cudaSuccess) {
@@ -449,6 +445,22 @@ int lbib_nop_create(int32_t batch, int32_t H, int32_t W, void* d_workspace, uint
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem);
     if (e == cudaSuccess) e = cudaMemsetAsync(n->param, 0, n->P * 4 * 4, n->stream);  // param, grad, m, v
     if (e == cudaSuccess) e = cudaMemsetAsync(n->tc_err, 0, 4, n->stream);
+    std::vector<WeightSet> sets;
+    for (const Layer& l : n->L) {
+        WeightSet w;
+        w.w = n->param + l.off;
+        w.wf = l.wf;
+        w.wd = l.wd;
+        w.wft = l.wft;
+        w.wdt = l.wdt;
+        w.Ci = l.cip;
+        w.Co = l.cop;
+        sets.push_back(w);
+        n->wsets_max = std::max(n->wsets_max, weight_set_elems(l.cip, l.cop));
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n->wsets, sets.data(), sets.size() * sizeof(WeightSet),
+                            cudaMemcpyHostToDevice, n->stream);
     if (e == cudaSuccess) e = refresh_weights(n);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) {
@@ -615,6 +627,7 @@ int lbib_nn_conv3x3(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int
     a.Co = Co;
     a.relu = relu;
     a.out_f32 = out_f32;
+    a.gate = nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_fwd_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
@@ -667,6 +680,7 @@ int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, 
     a.Co = Co;
     a.relu = relu;
     a.out_f32 = out_f32;
+    a.gate = nullptr;
     cudaError_t e = tc_conv3x3(a, d_wt, d_err, static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return set_thread_error(LBIB_E_CUDA, cudaGetErrorString(e));
     return LBIB_OK;

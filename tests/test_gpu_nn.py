@@ -135,10 +135,15 @@ def _bf16_round(a):
         .astype(np.float64)
 
 
-def test_network_forward_and_gradient_match_oracle(lb, orc):
+@pytest.mark.parametrize("H,n", [
+    (32, 2),    # every level on the warp-level convolution
+    (256, 1),   # 256^2 and 128^2 on the tcgen05 convolution (forward and data
+                # gradient with the fused ReLU backward), the weights re-tiled
+                # by the fused refresh
+])
+def test_network_forward_and_gradient_match_oracle(lb, orc, H, n):
     import torch
     from oracle import nn as onn
-    H, n = 32, 2
     net = lb.NeuralOperator(n, H, H)
     shapes = onn.nop_shapes()
     assert net.layers() == [(ci, co) for _, ci, co in shapes]
