@@ -404,7 +404,7 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
  *                                 per SM (0 = as many as fit; < 0 keeps it);
  *                                 reports whether the graph path is in use
  *                                 and the grid size
- *   lbib_ensemble_tune            time every (nodes_per_item in 256/512/1024)
+ *   lbib_ensemble_tune            time every (nodes_per_item in 256/512/1024/2048/4096)
  *                                 x (CTAs per SM) candidate over trial_steps
  *                                 steps (which advances the tissues), keep the
  *                                 fastest; config_out[2] = {nodes_per_item,

@@ -64,6 +64,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // Grid-wide barrier with a bounded wait.  Returns false (for every thread of
 // the CTA) when the ensemble's error flag is set.
 __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
+    __shared__ unsigned s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile unsigned* vgen = bar + 1;
@@ -86,9 +87,12 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks) {
             }
         }
         __threadfence();
+        // one reading of the error flag for the whole CTA, so that its threads
+        // leave together
+        s_ok = *(volatile unsigned*)(bar + 2) == 0u ? 1u : 0u;
     }
     __syncthreads();
-    return *(volatile unsigned*)(bar + 2) == 0u;
+    return s_ok != 0u;
 }
 
 __device__ __forceinline__ int find_tissue(const int* pfx, int n, int item) {
@@ -556,7 +560,7 @@ int lbib_ensemble_config(lbib_ensemble* e, int32_t nodes_per_item, int32_t block
 int lbib_ensemble_tune(lbib_ensemble* e, int32_t trial_steps, int32_t* config_out,
                        double* ms_out) {
     if (!e || trial_steps < 1 || !config_out) return LBIB_E_PARAM;
-    const int npis[3] = {256, 512, 1024};
+    const int npis[5] = {256, 512, 1024, 2048, 4096};
     double best = 1e300;
     int best_npi = e->nodes_per_item, best_bps = e->blocks_per_sm;
     cudaEvent_t t0, t1;
