@@ -527,6 +527,24 @@ int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, 
                        void* d_out, int32_t relu, int32_t out_f32, uint32_t* d_err,
                        void* cuda_stream);
 
+/* The weight gradient on the tensor cores (tcgen05.mma with MN-major operands:
+ * the pixels are the contraction, the input channels of three tap shifts the
+ * M rows, the output channels the N rows; FP32 accumulators in tensor memory,
+ * added to d_dw with FP32 reductions):
+ *   lbib_nn_conv3x3_wgrad_tc_supported  1 when the shape is supported: W from 16
+ *                          to 128 in multiples of 16, or a multiple of 128;
+ *                          C1 >= 16, C1 and C2 multiples of 16, C1 a multiple of
+ *                          32 when C1 + C2 is; Co a multiple of 16; H and W even
+ *                          when C2 > 0
+ *   lbib_nn_conv3x3_wgrad_tc  as lbib_nn_conv3x3_wgrad (d_dw (9, C1+C2, Co) and
+ *                          d_db (Co, or NULL) accumulated: zero them first);
+ *                          d_in1, d_in2, d_g, d_dw 16-byte aligned; d_err as for
+ *                          lbib_nn_conv3x3_tc */
+int lbib_nn_conv3x3_wgrad_tc_supported(int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co);
+int lbib_nn_conv3x3_wgrad_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
+                             const void* d_in1, const void* d_in2, const void* d_g, float* d_dw,
+                             float* d_db, uint32_t* d_err, void* cuda_stream);
+
 /* Coupled steps without any allocation.  The paper has no counterpart: this
  * entry point exists for callers that may not allocate device memory while
  * they run -- code inside a framework whose memory pool owns the device, or

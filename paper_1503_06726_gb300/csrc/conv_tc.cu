@@ -151,6 +151,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr, uint32_t sbo, ui
     return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) |
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)code << 61);
 }
+// The same for an MN-major operand: the leading byte offset is the distance
+// between M (or N) atoms, the stride byte offset between groups of 8 K rows.
+__device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                                 uint32_t code) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)code << 61);
+}
 // Byte offset, within a 1024-byte aligned region, of the 16-byte piece that
 // the TMA's swizzle of span swb places at the unswizzled offset off: bits 4..
 // of the piece index XOR the bits from 7 on (one bit for 32 bytes, two for 64,
@@ -442,6 +449,256 @@ __global__ void tile_weights_tc_kernel(const __nv_bfloat16* w, int Co, int Ci, i
     }
 }
 
+// ---------------------------------------------------------------------------
+// The weight gradient on the tensor cores: dW[ky][kx][ci][co] = sum over
+// pixels p of X[p + (ky - 1, kx - 1)][ci] G[p][co], a GEMM with the pixels as
+// K.  Both operands are staged as pixel rows (channels contiguous), so they
+// enter the MMA MN-major: A rows (M) are input channels, B rows (N) output
+// channels, K runs down the pixel rows.  The X halo of a tile (TR + 2 rows of
+// rs = Wt + 2 pixels, one Kc-channel chunk, swizzled as in the forward
+// kernel) makes every tap a row-shifted window, and the MN-major A operand
+// puts four such windows side by side: its M atoms (Kc channels each) sit one
+// pixel row apart (LBO = one row), so M = 128 covers the taps kx = 0, 1, 2
+// (and a fourth, unused shift) of one ky for 32 channels -- with 16-channel
+// chunks eight shifts, three of them used.  The K steps walk the tile's image
+// rows 16 pixels at a time (Wt a multiple of 16), so the halo columns never
+// enter: G is staged without halo, 16 output channels per TMA box (32-byte
+// swizzle), its N atoms a region apart.  One accumulator per ky and per
+// "set" of image rows (rows r % sets; more independent accumulation chains
+// in flight), summed at the end and added to dW with FP32 reductions.  A CTA
+// takes one input-channel chunk, one N tile and a range of pixel tiles
+// (split K over CTAs).  Pipeline and bounded waits as the forward kernel.
+struct WgTcArgs {
+    const __nv_bfloat16* in2;  // (N, H/2, W/2, C2), read upsampled, or NULL
+    float* dw;                 // (9, Ci, Co) FP32, accumulated
+    unsigned* err;
+    int N, H, W, C1, C2, Co;
+    int Kc, swx, swcode_x;     // the X chunk: channels, bytes per pixel row, layout code
+    int natoms;                // M atoms of the A operand: 128 / Kc
+    int Np, ng;                // output channels of the N tile, its 16-channel G atoms
+    int Wt, rs, TR, tiles_x, tiles_y, total_tiles;
+    int sk;                    // CTAs sharing one (chunk, N tile): split K
+    int sets;                  // accumulator sets
+    int x_bytes, x_box_bytes;  // the X halo region of a stage, one TMA box
+    int g_atom_bytes;          // one G atom region (TR Wt 32 bytes)
+    int stage_bytes, stages, tmem_cols;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    conv3x3_wgrad_tc_kernel(const __grid_constant__ CUtensorMap mapx,
+                            const __grid_constant__ CUtensorMap mapg, WgTcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_done[kTcMaxStages];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_bad, s_committed;
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int NS = a.stages;
+    const int chunk = blockIdx.y, ntile = blockIdx.z;
+    const int c0 = chunk * a.Kc, co0 = ntile * a.Np;
+    const bool up = c0 >= a.C1;  // the chunk comes from the upsampled input
+    // this CTA's pixel tiles
+    const int t_begin = (int)((int64_t)a.total_tiles * blockIdx.x / a.sk);
+    const int t_end = (int)((int64_t)a.total_tiles * (blockIdx.x + 1) / a.sk);
+    const int nt = t_end - t_begin;
+    const int per_img = a.tiles_x * a.tiles_y;
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&bar_full[s]), 1);
+            mbar_init(smem_u32(&bar_done[s]), 1);
+        }
+        s_bad = 0;
+        s_committed = -1;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_slot)),
+                     "r"(a.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    // M = 128 (the Kc-channel atoms of natoms shifts), N = Np, both MN-major
+    const uint32_t idesc = mma_idesc(kTcM, a.Np) | (1u << 15) | (1u << 16);
+    const uint32_t g_bytes = (uint32_t)a.ng * (uint32_t)a.g_atom_bytes;
+    int loading[kTcMaxStages] = {-1, -1, -1};
+    bool owed[kTcMaxStages] = {false, false, false};
+    uint32_t started = 0u;  // accumulators that hold a first product
+
+    auto tile_xy = [&](int T, int& n, int& y0, int& x0) {
+        n = T / per_img;
+        const int rem = T % per_img;
+        y0 = (rem / a.tiles_x) * a.TR;
+        x0 = (rem % a.tiles_x) * a.Wt;
+    };
+    auto issue = [&](int k) {  // local tile k of this CTA
+        const int s = k % NS;
+        const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
+        const uint32_t fb = smem_u32(&bar_full[s]);
+        int n, y0, x0;
+        tile_xy(t_begin + k, n, y0, x0);
+        if (!up) {
+            mbar_expect_tx(fb, g_bytes + (uint32_t)a.x_box_bytes);
+            tma_load_4d(st, &mapx, c0, x0 - 1, y0 - 1, n, fb);
+        } else {
+            mbar_tx_only(fb, g_bytes);
+            owed[s] = true;
+        }
+        for (int at = 0; at < a.ng; ++at)
+            tma_load_4d(st + (uint32_t)a.x_bytes + (uint32_t)(at * a.g_atom_bytes), &mapg,
+                        co0 + 16 * at, x0, y0, n, fb);
+        loading[s] = k;
+    };
+
+    if (tid == 0)
+        for (int k = 0; k < NS && k < nt; ++k) issue(k);
+    for (int k = 0; k < nt; ++k) {
+        const int s = k % NS;
+        const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
+        if (up) {
+            // the upsampled half-resolution channels, as in the forward kernel
+            int n, y0, x0;
+            tile_xy(t_begin + k, n, y0, x0);
+            const int cc = c0 - a.C1;
+            const int ppp = a.Kc / 8;
+            const int pieces = (a.TR + 2) * a.rs * ppp;
+            for (int i = tid; i < pieces; i += kTcThreads) {
+                const int hp = i / ppp, q = i % ppp;
+                const int gy = y0 + hp / a.rs - 1, gx = x0 + hp % a.rs - 1;
+                const bool ok = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+                const __nv_bfloat16* src =
+                    ok ? a.in2 + (((int64_t)n * (a.H >> 1) + (gy >> 1)) * (a.W >> 1) + (gx >> 1)) *
+                                     a.C2 + cc + 8 * q
+                       : a.in2;
+                cp_async16_zfill(st + swizzle_off((uint32_t)(hp * a.swx + q * 16), a.swx), src, ok);
+            }
+            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                mbar_arrive(smem_u32(&bar_full[s]));
+                owed[s] = false;
+            }
+        }
+        if (tid == 0) {
+            if (!mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
+                s_bad = 1;
+            } else {
+                loading[s] = -1;
+                tc_fence_after();
+                const uint32_t gst = st + (uint32_t)a.x_bytes;
+                for (int r = 0; r < a.TR; ++r) {
+                    const int set = r % a.sets;
+                    for (int k0 = 0; k0 < a.Wt; k0 += 16) {
+                        // G: 16-channel atoms a region apart, 8 pixel rows of 32 bytes
+                        const uint64_t bdesc =
+                            smem_desc_mn(gst + (uint32_t)((r * a.Wt + k0) * 32),
+                                         (uint32_t)a.g_atom_bytes, 256u, 6u);
+                        for (int ky = 0; ky < 3; ++ky) {
+                            const int acc = set * 3 + ky;
+                            const uint64_t adesc = smem_desc_mn(
+                                st + (uint32_t)(((r + ky) * a.rs + k0) * a.swx), (uint32_t)a.swx,
+                                8u * (uint32_t)a.swx, (uint32_t)a.swcode_x);
+                            tc_mma(tmem + (uint32_t)(acc * a.Np), adesc, bdesc, idesc,
+                                   (started >> acc) & 1u);
+                            started |= 1u << acc;
+                        }
+                    }
+                }
+                tc_commit(smem_u32(&bar_done[s]));
+                s_committed = k;
+                if (k >= 1 && k - 1 + NS < nt) {
+                    if (!mbar_wait(smem_u32(&bar_done[(k - 1) % NS]), ((k - 1) / NS) & 1))
+                        s_bad = 1;
+                    else
+                        issue(k - 1 + NS);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_bad) break;
+    }
+    if (tid == 0)
+        for (int s = 0; s < NS; ++s)
+            if (loading[s] >= 0) {
+                if (owed[s]) mbar_arrive(smem_u32(&bar_full[s]));
+                mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
+            }
+    __syncthreads();
+    const int committed = s_committed;
+    bool ok = !s_bad;
+    if (committed >= 0 && !mbar_wait(smem_u32(&bar_done[committed % NS]), (committed / NS) & 1))
+        ok = false;
+    tc_fence_after();
+
+    if (ok && committed >= 0) {
+        // lane m of warp w: A row m = 32 w + lane = (shift j, channel ci)
+        const int m = warp * 32 + lane;
+        const int j = m / a.Kc, ci = m % a.Kc;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int ky = 0; ky < 3; ++ky)
+            for (int cl = 0; cl < a.Np; cl += 16) {
+                float v[16], w[16];
+                __syncwarp();
+                tmem_ld16(trow + (uint32_t)(ky * a.Np + cl), v);
+                for (int set = 1; set < a.sets; ++set) {
+                    __syncwarp();
+                    tmem_ld16(trow + (uint32_t)((set * 3 + ky) * a.Np + cl), w);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) v[q] += w[q];
+                }
+                if (j < 3 && c0 + ci < a.C1 + a.C2) {
+                    float* d = a.dw + ((int64_t)(ky * 3 + j) * (a.C1 + a.C2) + c0 + ci) * a.Co +
+                               co0 + cl;
+                    if (co0 + cl + 16 <= a.Co) {
+                        // four FP32 reductions per instruction (d is 16-byte aligned:
+                        // Co and co0 + cl are multiples of 16)
+#pragma unroll
+                        for (int q = 0; q < 16; q += 4)
+                            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(d + q),
+                                         "f"(v[q]), "f"(v[q + 1]), "f"(v[q + 2]), "f"(v[q + 3])
+                                         : "memory");
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q)
+                            if (co0 + cl + q < a.Co) atomicAdd(d + q, v[q]);
+                    }
+                }
+            }
+    } else if (!ok && tid == 0) {
+        atomicOr(a.err, 1u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(a.tmem_cols)
+                     : "memory");
+}
+
+// db[co] += sum over pixels of g[p][co]: R pixel rows per block at a time, a
+// channel per thread, partial sums reduced in shared memory
+__global__ void bias_grad_kernel(const __nv_bfloat16* g, int64_t npix, int Co, float* db) {
+    extern __shared__ float red[];
+    const int R = blockDim.x / Co;
+    const int c = threadIdx.x % Co, r = threadIdx.x / Co;
+    float acc = 0.f;
+    if (r < R)
+        for (int64_t p = (int64_t)blockIdx.x * R + r; p < npix; p += (int64_t)gridDim.x * R)
+            acc += __bfloat162float(g[p * Co + c]);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    if (r == 0) {
+        for (int k = 1; k < R; ++k) acc += red[k * Co + c];
+        atomicAdd(db + c, acc);
+    }
+}
+
 // The fused weight refresh: for layer blockIdx.y, from its FP32 master
 // weights w (9, Ci, Co): the BF16 forward copy wf (9, Co, Ci), the
 // tap-flipped copy wd (9, Ci, Co) (wd[8 - t][i][o] = w[t][i][o]) and the
@@ -634,6 +891,122 @@ cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_
     nn::tile_weights_tc_kernel<<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(w), Co, Ci,
                                                       Kc, Np, nk, nt,
                                                       static_cast<__nv_bfloat16*>(wt));
+    return cudaGetLastError();
+}
+
+// ---- the weight gradient
+// output channels of one N tile (at most 160: three accumulators of Np
+// columns and more sets where they fit in the 512 TMEM columns)
+static void tcw_ntiles(int Co, int* ntiles, int* Np) {
+    const int n16 = (Co + 15) / 16;
+    *ntiles = (n16 + 9) / 10;
+    *Np = (n16 + *ntiles - 1) / *ntiles * 16;
+}
+
+bool tc_wgrad_supported(int H, int W, int C1, int C2, int Co) {
+    const int Ci = C1 + C2;
+    if (H < 1 || W < 16 || (W <= 128 ? W % 16 : W % 128) || C1 < 16 || C1 % 16 || C2 < 0 ||
+        C2 % 16 || Co < 16 || Co % 16 || (C2 > 0 && (H % 2 || W % 2)) || C1 % tc_kc(Ci) ||
+        encode_fn() == nullptr)
+        return false;
+    return true;
+}
+
+cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t s) {
+    if (!tc_wgrad_supported(w.H, w.W, w.C1, w.C2, w.Co)) return cudaErrorInvalidValue;
+    nn::WgTcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in2 = w.in2;
+    a.dw = w.dw;
+    a.err = err;
+    a.N = w.N;
+    a.H = w.H;
+    a.W = w.W;
+    a.C1 = w.C1;
+    a.C2 = w.C2;
+    a.Co = w.Co;
+    const int Ci = w.C1 + w.C2;
+    a.Kc = tc_kc(Ci);
+    a.swx = 2 * a.Kc;
+    a.swcode_x = a.Kc == 32 ? 4 : 6;
+    a.natoms = nn::kTcM / a.Kc;
+    int ntn = 1;
+    tcw_ntiles(w.Co, &ntn, &a.Np);
+    a.ng = a.Np / 16;
+    a.Wt = w.W <= 128 ? w.W : 128;
+    a.rs = a.Wt + 2;
+    a.tiles_x = w.W / a.Wt;
+    // the tile: TR rows, the largest of 4, 2, 1 whose stage fits twice
+    for (int TR = 4; TR >= 1; TR /= 2) {
+        // halo rows plus the rows the unused shifts of the last K step read
+        const int rows = (TR + 2) * a.rs + a.natoms;
+        const int xb = (rows * a.swx + 1023) / 1024 * 1024;
+        const int gab = TR * a.Wt * 32;
+        const int stage = (xb + a.ng * gab + 1023) / 1024 * 1024;
+        if (2 * stage + 1024 > kTcSmemMax && TR > 1) continue;
+        a.TR = TR;
+        a.x_bytes = xb;
+        a.x_box_bytes = (TR + 2) * a.rs * a.swx;
+        a.g_atom_bytes = gab;
+        a.stage_bytes = stage;
+        a.stages = 3 * stage + 1024 <= kTcSmemMax ? 3 : 2;
+        break;
+    }
+    if (a.stages * a.stage_bytes + 1024 > kTcSmemMax) return cudaErrorInvalidValue;
+    // accumulator sets: as many as TMEM holds (three accumulators of Np
+    // columns each), at most 4 and at most the tile's rows, so that every set
+    // receives products
+    a.sets = std::max(1, std::min(std::min(4, a.TR), 512 / (3 * a.Np)));
+    a.tmem_cols = 32;
+    while (a.tmem_cols < 3 * a.sets * a.Np) a.tmem_cols *= 2;
+    a.tiles_y = (w.H + a.TR - 1) / a.TR;
+    a.total_tiles = w.N * a.tiles_y * a.tiles_x;
+    const int nchunks = Ci / a.Kc;
+    // split K: one wave of CTAs over all (chunk, N tile) pairs (each CTA's
+    // partial sums cost one reduction per weight), at least two tiles each
+    a.sk = std::max(1, std::min(a.total_tiles / 2, sm_count() / (nchunks * ntn)));
+    // tensor maps: the input (channels, x, y, image) and the gradient
+    CUtensorMap mx, mg;
+    std::memset(&mx, 0, sizeof(mx));
+    std::memset(&mg, 0, sizeof(mg));
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)w.C1, (cuuint64_t)w.W, (cuuint64_t)w.H, (cuuint64_t)w.N};
+        cuuint64_t str[3] = {(cuuint64_t)w.C1 * 2, (cuuint64_t)w.W * w.C1 * 2,
+                             (cuuint64_t)w.H * w.W * w.C1 * 2};
+        cuuint32_t box[4] = {(cuuint32_t)a.Kc, (cuuint32_t)a.rs, (cuuint32_t)(a.TR + 2), 1};
+        if (encode_fn()(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w.in1),
+                        dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    {
+        cuuint64_t dims[4] = {(cuuint64_t)w.Co, (cuuint64_t)w.W, (cuuint64_t)w.H, (cuuint64_t)w.N};
+        cuuint64_t str[3] = {(cuuint64_t)w.Co * 2, (cuuint64_t)w.W * w.Co * 2,
+                             (cuuint64_t)w.H * w.W * w.Co * 2};
+        cuuint32_t box[4] = {16, (cuuint32_t)a.Wt, (cuuint32_t)a.TR, 1};
+        if (encode_fn()(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w.g),
+                        dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    int smem = a.stages * a.stage_bytes + 1024;
+    const int by_tmem = 512 / a.tmem_cols;
+    smem = std::min(kTcSmemMax, std::max(smem, kTcSmemSM / (by_tmem + 1) - 1024 + 256));
+    cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_wgrad_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    nn::conv3x3_wgrad_tc_kernel<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !w.db) return e;
+    // the bias gradient: column sums of g
+    const int R = std::max(1, 256 / w.Co);
+    const int64_t npix = (int64_t)w.N * w.H * w.W;
+    const int blocks = (int)std::min<int64_t>((npix + R - 1) / R, 4 * sm_count());
+    nn::bias_grad_kernel<<<blocks, R * w.Co, R * w.Co * 4, s>>>(w.g, npix, w.Co, w.db);
     return cudaGetLastError();
 }
 

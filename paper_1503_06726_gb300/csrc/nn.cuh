@@ -68,6 +68,12 @@ bool tc_conv_supported(int H, int W, int C1, int C2, int Co);
 int64_t tc_tiled_weight_elems(int Ci, int Co);
 cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_t s);
 cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cudaStream_t s);
+// The weight gradient on tcgen05 (conv_tc.cu): whether a layer's shape is
+// supported (W from 16 up to 128 in multiples of 16, or a multiple of 128;
+// channels multiples of 16, C1 a multiple of the chunk width), and the
+// gradient itself (w.dw and w.db accumulated; err as for the convolution).
+bool tc_wgrad_supported(int H, int W, int C1, int C2, int Co);
+cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t s);
 
 // One layer of the fused weight refresh: the FP32 master weights w (9, Ci, Co)
 // and the BF16 copies made from them -- the forward copy wf (9, Co, Ci), the

@@ -239,6 +239,13 @@ cudaError_t conv_wgrad(lbib_nop* n, const Layer& l, const bf16* in1, const bf16*
     a.C1 = C1;
     a.C2 = C2;
     a.Co = l.cop;
+    // the tcgen05 kernel where it measured faster (batch 16): every level from
+    // 64^2 up except the decoder's upsampled-input layers at 128^2 and 256^2,
+    // and the 32^2 layers of 96 or more input channels
+    const int Ci = C1 + C2;
+    const bool tc = tc_wgrad_supported(a.H, a.W, C1, C2, a.Co) &&
+                    ((a.W >= 64 && !(C2 > 0 && a.W >= 128)) || (a.W == 32 && Ci >= 96));
+    if (tc) return tc_conv3x3_wgrad(a, n->tc_err, n->stream);
     const int tiles = ((a.H + kTH - 1) / kTH) * ((a.W + kTW - 1) / kTW) * N;
     a.tiles_per_cta = tiles > 4096 ? 32 : (tiles > 512 ? 8 : 1);
     dim3 grid((tiles + a.tiles_per_cta - 1) / a.tiles_per_cta, (C1 + C2 + 15) / 16, (l.cop + 63) / 64);
@@ -682,6 +689,38 @@ int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, 
     a.out_f32 = out_f32;
     a.gate = nullptr;
     cudaError_t e = tc_conv3x3(a, d_wt, d_err, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return set_thread_error(LBIB_E_CUDA, cudaGetErrorString(e));
+    return LBIB_OK;
+}
+
+int lbib_nn_conv3x3_wgrad_tc_supported(int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co) {
+    return tc_wgrad_supported(H, W, C1, C2, Co) ? 1 : 0;
+}
+
+int lbib_nn_conv3x3_wgrad_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, int32_t Co,
+                             const void* d_in1, const void* d_in2, const void* d_g, float* d_dw,
+                             float* d_db, uint32_t* d_err, void* cuda_stream) {
+    if (N < 1 || !d_in1 || !d_g || !d_dw || !d_err || (C2 > 0 && !d_in2) ||
+        !tc_wgrad_supported(H, W, C1, C2, Co))
+        return set_thread_error(LBIB_E_PARAM,
+                                "lbib_nn_conv3x3_wgrad_tc: unsupported shape or arguments");
+    if (reinterpret_cast<uintptr_t>(d_in1) % 16 || reinterpret_cast<uintptr_t>(d_g) % 16 ||
+        reinterpret_cast<uintptr_t>(d_dw) % 16 || (d_in2 && reinterpret_cast<uintptr_t>(d_in2) % 16))
+        return set_thread_error(LBIB_E_PARAM, "lbib_nn_conv3x3_wgrad_tc: buffers need 16-byte alignment");
+    nn::WgradArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in1 = static_cast<const bf16*>(d_in1);
+    a.in2 = static_cast<const bf16*>(d_in2);
+    a.g = static_cast<const bf16*>(d_g);
+    a.dw = d_dw;
+    a.db = d_db;
+    a.N = N;
+    a.H = H;
+    a.W = W;
+    a.C1 = C1;
+    a.C2 = C2;
+    a.Co = Co;
+    cudaError_t e = tc_conv3x3_wgrad(a, d_err, static_cast<cudaStream_t>(cuda_stream));
     if (e != cudaSuccess) return set_thread_error(LBIB_E_CUDA, cudaGetErrorString(e));
     return LBIB_OK;
 }

@@ -58,7 +58,8 @@ EXPORTS = (
     "lbib_nop_set_params", "lbib_nop_get_params", "lbib_nop_get_grads", "lbib_nop_forward",
     "lbib_nop_train_step", "lbib_nop_destroy", "lbib_nop_last_error", "lbib_nn_conv3x3",
     "lbib_nn_conv3x3_wgrad", "lbib_nn_weight_copies", "lbib_nn_conv3x3_tc_supported",
-    "lbib_nn_tile_weights_tc", "lbib_nn_conv3x3_tc",
+    "lbib_nn_tile_weights_tc", "lbib_nn_conv3x3_tc", "lbib_nn_conv3x3_wgrad_tc_supported",
+    "lbib_nn_conv3x3_wgrad_tc",
 )
 
 
@@ -161,6 +162,8 @@ def load(path: str = None) -> ctypes.CDLL:
         "lbib_nn_conv3x3_tc_supported": (ctypes.c_int, [i32] * 5),
         "lbib_nn_tile_weights_tc": (ctypes.c_int, [i32, i32, vp, vp, ctypes.POINTER(u64), vp]),
         "lbib_nn_conv3x3_tc": (ctypes.c_int, [i32] * 6 + [vp] * 5 + [i32, i32, vp, vp]),
+        "lbib_nn_conv3x3_wgrad_tc_supported": (ctypes.c_int, [i32] * 5),
+        "lbib_nn_conv3x3_wgrad_tc": (ctypes.c_int, [i32] * 6 + [vp] * 7),
         "lbib_destroy": (None, [vp]),
         "lbib_last_error": (ctypes.c_char_p, [vp]),
         "lbib_status_string": (ctypes.c_char_p, [ctypes.c_int]),

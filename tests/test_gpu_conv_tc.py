@@ -153,3 +153,57 @@ def test_tc_conv_shape_support(lb):
     assert L.lbib_nn_conv3x3_tc_supported(8, 8, 32, 0, 32) == 1
     assert L.lbib_nn_conv3x3_tc_supported(2, 32, 16, 0, 32) == 1
     assert L.lbib_nn_conv3x3_tc_supported(256, 256, 16, 0, 32) == 1
+
+
+@pytest.mark.parametrize("N,H,W,C1,C2,Co", [
+    (2, 16, 32, 32, 0, 32),     # whole narrow rows, one 32-channel chunk (64-byte swizzle)
+    (2, 8, 16, 16, 32, 48),     # 16-channel chunks (eight shifts per M), upsampled input
+    (1, 5, 128, 64, 0, 64),     # rows of 128, two chunks, a row tile overhanging the image
+    (1, 4, 256, 32, 32, 192),   # two tiles per row, two N tiles of 96, upsampled 32-channel chunk
+    (4, 64, 64, 48, 0, 16),     # the smallest N tile (four accumulator sets), 48 channels
+])
+def test_tc_wgrad_matches_oracle_and_mma_sync(lb, orc, N, H, W, C1, C2, Co):
+    """The weight gradient on tcgen05 (MN-major operands, the input channels of
+    three tap shifts as M) against the FP64 oracle and the warp-level kernel:
+    BF16-exact inputs, FP32 accumulation in a different order."""
+    import torch
+    from oracle import nn as onn
+    L = lb.load()
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(H, W, C1, C2, Co) == 1
+    Ci = C1 + C2
+    x1 = bf16((N, H, W, C1), 21)
+    x2 = bf16((N, H // 2, W // 2, C2), 22) if C2 else None
+    g = bf16((N, H, W, Co), 23)
+    st = torch.cuda.current_stream().cuda_stream
+    dx1, dg = x1.cuda(), g.cuda()
+    dx2 = x2.cuda() if C2 else None
+    p2 = dx2.data_ptr() if C2 else None
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dw = torch.zeros((9, Ci, Co), dtype=torch.float32, device="cuda")
+    db = torch.zeros(Co, dtype=torch.float32, device="cuda")
+    assert L.lbib_nn_conv3x3_wgrad_tc(N, H, W, C1, C2, Co, dx1.data_ptr(), p2, dg.data_ptr(),
+                                      dw.data_ptr(), db.data_ptr(), err.data_ptr(), st) == 0, \
+        lb.lbib_last_error(None)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    xin = f64(x1) if not C2 else np.concatenate([f64(x1), onn.upsample2(f64(x2))], axis=3)
+    rw, rb = orc.conv3x3_wgrad(xin, f64(g))
+    got = dw.cpu().numpy().reshape(3, 3, Ci, Co)
+    assert np.isfinite(got).all()
+    assert rel_inf(got, rw) < 1e-5
+    assert rel_inf(db.cpu().numpy(), rb) < 1e-5
+    dw2 = torch.zeros((9, Ci, Co), dtype=torch.float32, device="cuda")
+    db2 = torch.zeros(Co, dtype=torch.float32, device="cuda")
+    assert L.lbib_nn_conv3x3_wgrad(N, H, W, C1, C2, Co, dx1.data_ptr(), p2, dg.data_ptr(),
+                                   dw2.data_ptr(), db2.data_ptr(), st) == 0
+    torch.cuda.synchronize()
+    assert rel_inf(got, dw2.cpu().numpy().reshape(3, 3, Ci, Co)) < 1e-5
+
+
+def test_tc_wgrad_shape_support(lb):
+    L = lb.load()
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 8, 32, 0, 32) == 0     # W below 16
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 40, 32, 0, 32) == 0    # W not a multiple of 16
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 32, 32, 0, 40) == 0    # Co not a multiple of 16
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 32, 16, 16, 32) == 0   # 32-channel chunks, C1 = 16
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(256, 256, 16, 0, 32) == 1
