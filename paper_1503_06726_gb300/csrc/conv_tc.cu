@@ -68,8 +68,10 @@ struct ConvTcArgs {
     int tiles_x, tiles_y;
     int a_bytes;               // the halo region of a stage (1024-byte multiple)
     int box_bytes;             // bytes one TMA box delivers: (TR + 2) rs swb
-    int stage_bytes, stages;   // stage: halo + the chunk's weights
+    int stage_bytes, stages;   // stage: halo + the chunk's weights (+ the upsampled box)
     int tmem_cols;             // power of two >= max(32, m Np)
+    int up_rows, up_cols;      // the half-resolution box of an upsampled chunk
+    int up_off, up_box_bytes;  // its place in the stage, the bytes it delivers
     int relu, out_f32;
 };
 
@@ -165,6 +167,27 @@ __device__ __forceinline__ uint64_t smem_desc_mn(uint32_t addr, uint32_t lbo, ui
 __host__ __device__ __forceinline__ uint32_t swizzle_off(uint32_t off, int swb) {
     return off ^ (((off >> 7) & (uint32_t)((swb >> 4) - 1)) << 4);
 }
+
+// The decoder's upsampled channels: the half-resolution box (staged by TMA in
+// the same swizzle, origin at half-resolution pixel ((x0 - 1) >> 1,
+// (y0 - 1) >> 1), up_cols wide) expanded into the halo layout -- halo pixel hp
+// (row hp / rs, column hp % rs of the halo starting at (x0 - 1, y0 - 1))
+// takes half-resolution pixel (gy >> 1, gx >> 1).  Outside the image the box
+// holds the TMA's zero fill, which is the zero padding (H and W are even).
+__device__ __forceinline__ void expand_upsampled(unsigned char* dst, const unsigned char* stg,
+                                                 int halo_rows, int rs, int swb, int x0, int y0,
+                                                 int up_cols, int tid, int nthreads) {
+    const int ppp = swb / 16;
+    const int by = (y0 - 1) >> 1, bx = (x0 - 1) >> 1;
+    for (int i = tid; i < halo_rows * rs * ppp; i += nthreads) {
+        const int hp = i / ppp, q = i % ppp;
+        const int gy = y0 - 1 + hp / rs, gx = x0 - 1 + hp % rs;
+        const int srow = ((gy >> 1) - by) * up_cols + ((gx >> 1) - bx);
+        const uint4 v = *reinterpret_cast<const uint4*>(
+            stg + swizzle_off((uint32_t)(srow * swb + q * 16), swb));
+        *reinterpret_cast<uint4*>(dst + swizzle_off((uint32_t)(hp * swb + q * 16), swb)) = v;
+    }
+}
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
 // A and B (bits 7-9 and 10-12 = 1), both K-major, N / 8 in bits 17-22,
 // M / 16 in bits 24-28.
@@ -201,11 +224,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 
 
 __global__ void __launch_bounds__(kTcThreads)
-    conv3x3_tc_kernel(const __grid_constant__ CUtensorMap map1, ConvTcArgs a) {
+    conv3x3_tc_kernel(const __grid_constant__ CUtensorMap map1,
+                      const __grid_constant__ CUtensorMap map2, ConvTcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_done[kTcMaxStages];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_bad, s_committed;
+    __shared__ int s_bad, s_committed, s_up_ok;
     // stages at 1024-byte boundaries: the swizzle follows the address bits
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -242,10 +266,8 @@ __global__ void __launch_bounds__(kTcThreads)
     const uint32_t b_bytes = 9u * (uint32_t)a.Np * (uint32_t)a.swb;
     const uint32_t sbo = 8u * (uint32_t)a.swb;
     // thread 0: per stage, the chunk whose copies were issued and not yet
-    // waited for (-1 = none), and whether its arrival (after the threads'
-    // staging of an upsampled chunk) is still owed
+    // waited for (-1 = none)
     int loading[kTcMaxStages] = {-1, -1, -1};
-    bool owed[kTcMaxStages] = {false, false, false};
 
     auto issue = [&](int k) {
         const int s = k % NS;
@@ -255,45 +277,44 @@ __global__ void __launch_bounds__(kTcThreads)
             mbar_expect_tx(fb, b_bytes + (uint32_t)a.box_bytes);
             tma_load_4d(st, &map1, k * a.Kc, x0 - 1, y0 - 1, n, fb);
         } else {
-            mbar_tx_only(fb, b_bytes);
-            owed[s] = true;
+            mbar_expect_tx(fb, b_bytes + (uint32_t)a.up_box_bytes);
+            tma_load_4d(st + (uint32_t)a.up_off, &map2, (k - a.nk1) * a.Kc, (x0 - 1) >> 1,
+                        (y0 - 1) >> 1, n, fb);
         }
         bulk_load(st + (uint32_t)a.a_bytes, wt + (int64_t)k * 9 * a.Np * a.Kc, b_bytes, fb);
         loading[s] = k;
     };
 
-    if (tid == 0)
-        for (int k = 0; k < NS && k < a.nk; ++k) issue(k);
-    for (int k = 0; k < a.nk; ++k) {
+    // an upsampled chunk: once its half-resolution box has landed the threads
+    // expand it into the halo (the stage's previous multiplies completed
+    // before its copies were issued); done one chunk ahead, beside the
+    // multiplies of the chunk before
+    auto expand_chunk = [&](int k) {
         const int s = k % NS;
         const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
-        if (k >= a.nk1) {
-            // upsampled half-resolution channels: every thread stages 16-byte
-            // pieces (8 channels of one halo pixel), zeros outside the image;
-            // the stage is free, its copies having been issued after the
-            // multiplies of chunk k - NS completed
-            const int cc = (k - a.nk1) * a.Kc;
-            const int ppp = a.Kc / 8;
-            const int pieces = (a.TR + 2) * a.rs * ppp;
-            for (int i = tid; i < pieces; i += kTcThreads) {
-                const int hp = i / ppp, q = i % ppp;
-                const int gy = y0 + hp / a.rs - 1, gx = x0 + hp % a.rs - 1;
-                const bool ok = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-                const __nv_bfloat16* src =
-                    ok ? a.in2 + (((int64_t)n * (a.H >> 1) + (gy >> 1)) * (a.W >> 1) + (gx >> 1)) *
-                                     a.C2 + cc + 8 * q
-                       : a.in2;
-                cp_async16_zfill(st + swizzle_off((uint32_t)(hp * a.swb + q * 16), a.swb), src, ok);
-            }
-            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-            // written through the generic proxy, read by the tensor cores
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                mbar_arrive(smem_u32(&bar_full[s]));
-                owed[s] = false;
-            }
+        if (tid == 0) {
+            s_up_ok = !s_bad && mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1) ? 1 : 0;
+            if (!s_up_ok) s_bad = 1;
         }
+        __syncthreads();
+        if (s_up_ok && mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
+            unsigned char* gst = smem_raw + (st - smem_u32(smem_raw));
+            expand_upsampled(gst, gst + a.up_off, a.TR + 2, a.rs, a.swb, x0, y0, a.up_cols, tid,
+                             kTcThreads);
+        }
+        // written through the generic proxy, read by the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    };
+
+    if (tid == 0)
+        for (int k = 0; k < NS && k < a.nk; ++k) issue(k);
+    if (a.nk1 == 0) {
+        expand_chunk(0);
+        __syncthreads();
+    }
+    for (int k = 0; k < a.nk && !s_bad; ++k) {
+        const int s = k % NS;
+        const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
         if (tid == 0) {
             if (!mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
                 s_bad = 1;
@@ -327,16 +348,13 @@ __global__ void __launch_bounds__(kTcThreads)
                 }
             }
         }
+        if (k + 1 < a.nk && k + 1 >= a.nk1) expand_chunk(k + 1);
         __syncthreads();
-        if (s_bad) break;
     }
     // after an error: the copies still in flight land before the CTA leaves
     if (tid == 0)
         for (int s = 0; s < NS; ++s)
-            if (loading[s] >= 0) {
-                if (owed[s]) mbar_arrive(smem_u32(&bar_full[s]));
-                mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
-            }
+            if (loading[s] >= 0) mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
     __syncthreads();
     // the last commit covers every multiply issued before it
     const int committed = s_committed;
@@ -482,15 +500,17 @@ struct WgTcArgs {
     int x_bytes, x_box_bytes;  // the X halo region of a stage, one TMA box
     int g_atom_bytes;          // one G atom region (TR Wt 32 bytes)
     int stage_bytes, stages, tmem_cols;
+    int up_rows, up_cols, up_off, up_box_bytes;  // the half-resolution box, as in ConvTcArgs
 };
 
 __global__ void __launch_bounds__(kTcThreads, 1)
     conv3x3_wgrad_tc_kernel(const __grid_constant__ CUtensorMap mapx,
-                            const __grid_constant__ CUtensorMap mapg, WgTcArgs a) {
+                            const __grid_constant__ CUtensorMap mapg,
+                            const __grid_constant__ CUtensorMap mapu, WgTcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_done[kTcMaxStages];
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_bad, s_committed;
+    __shared__ int s_bad, s_committed, s_up_ok;
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NS = a.stages;
@@ -527,7 +547,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t idesc = mma_idesc(kTcM, a.Np) | (1u << 15) | (1u << 16);
     const uint32_t g_bytes = (uint32_t)a.ng * (uint32_t)a.g_atom_bytes;
     int loading[kTcMaxStages] = {-1, -1, -1};
-    bool owed[kTcMaxStages] = {false, false, false};
     uint32_t started = 0u;  // accumulators that hold a first product
 
     auto tile_xy = [&](int T, int& n, int& y0, int& x0) {
@@ -546,8 +565,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_expect_tx(fb, g_bytes + (uint32_t)a.x_box_bytes);
             tma_load_4d(st, &mapx, c0, x0 - 1, y0 - 1, n, fb);
         } else {
-            mbar_tx_only(fb, g_bytes);
-            owed[s] = true;
+            mbar_expect_tx(fb, g_bytes + (uint32_t)a.up_box_bytes);
+            tma_load_4d(st + (uint32_t)a.up_off, &mapu, c0 - a.C1, (x0 - 1) >> 1, (y0 - 1) >> 1,
+                        n, fb);
         }
         for (int at = 0; at < a.ng; ++at)
             tma_load_4d(st + (uint32_t)a.x_bytes + (uint32_t)(at * a.g_atom_bytes), &mapg,
@@ -555,36 +575,35 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         loading[s] = k;
     };
 
-    if (tid == 0)
-        for (int k = 0; k < NS && k < nt; ++k) issue(k);
-    for (int k = 0; k < nt; ++k) {
+    // an upsampled chunk: each tile's half-resolution box expanded into the
+    // halo one tile ahead, beside the multiplies of the tile before
+    auto expand_tile = [&](int k) {
         const int s = k % NS;
         const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
-        if (up) {
-            // the upsampled half-resolution channels, as in the forward kernel
-            int n, y0, x0;
-            tile_xy(t_begin + k, n, y0, x0);
-            const int cc = c0 - a.C1;
-            const int ppp = a.Kc / 8;
-            const int pieces = (a.TR + 2) * a.rs * ppp;
-            for (int i = tid; i < pieces; i += kTcThreads) {
-                const int hp = i / ppp, q = i % ppp;
-                const int gy = y0 + hp / a.rs - 1, gx = x0 + hp % a.rs - 1;
-                const bool ok = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-                const __nv_bfloat16* src =
-                    ok ? a.in2 + (((int64_t)n * (a.H >> 1) + (gy >> 1)) * (a.W >> 1) + (gx >> 1)) *
-                                     a.C2 + cc + 8 * q
-                       : a.in2;
-                cp_async16_zfill(st + swizzle_off((uint32_t)(hp * a.swx + q * 16), a.swx), src, ok);
-            }
-            asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                mbar_arrive(smem_u32(&bar_full[s]));
-                owed[s] = false;
-            }
+        int n, y0, x0;
+        tile_xy(t_begin + k, n, y0, x0);
+        if (tid == 0) {
+            s_up_ok = !s_bad && mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1) ? 1 : 0;
+            if (!s_up_ok) s_bad = 1;
         }
+        __syncthreads();
+        if (s_up_ok && mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
+            unsigned char* gst = smem_raw + (st - smem_u32(smem_raw));
+            expand_upsampled(gst, gst + a.up_off, a.TR + 2, a.rs, a.swx, x0, y0, a.up_cols, tid,
+                             kTcThreads);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    };
+
+    if (tid == 0)
+        for (int k = 0; k < NS && k < nt; ++k) issue(k);
+    if (up && nt > 0) {
+        expand_tile(0);
+        __syncthreads();
+    }
+    for (int k = 0; k < nt && !s_bad; ++k) {
+        const int s = k % NS;
+        const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
         if (tid == 0) {
             if (!mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
                 s_bad = 1;
@@ -620,15 +639,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         }
+        if (up && k + 1 < nt) expand_tile(k + 1);
         __syncthreads();
-        if (s_bad) break;
     }
     if (tid == 0)
         for (int s = 0; s < NS; ++s)
-            if (loading[s] >= 0) {
-                if (owed[s]) mbar_arrive(smem_u32(&bar_full[s]));
-                mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
-            }
+            if (loading[s] >= 0) mbar_wait(smem_u32(&bar_full[s]), (loading[s] / NS) & 1);
     __syncthreads();
     const int committed = s_committed;
     bool ok = !s_bad;
@@ -823,7 +839,8 @@ constexpr int kTcMaxCols = 256;                // TMEM columns per CTA (two CTAs
 // The tile plan: TR rows per CTA (m accumulators), chosen for the fraction of
 // useful MMA lanes, of halo rows loaded once and of rows inside the image,
 // as long as two waves of CTAs remain; up to three stages.
-static bool tc_plan(int N, int H, int W, int Np, int ntiles, int nk, nn::ConvTcArgs* a) {
+static bool tc_plan(int N, int H, int W, int Np, int ntiles, int nk, bool up,
+                    nn::ConvTcArgs* a) {
     a->Wt = W <= 128 ? W : 128;
     a->rs = a->Wt + 2;
     a->wide = a->Wt == 128 ? 1 : 0;
@@ -835,9 +852,15 @@ static bool tc_plan(int N, int H, int W, int Np, int ntiles, int nk, nn::ConvTcA
         if (m > kTcMaxAcc || m * Np > kTcMaxCols) break;
         const int rows = a->wide ? (TR + 2) * a->rs : std::max((TR + 2) * a->rs, nn::kTcM * m + 2 * a->rs + 2);
         const int a_bytes = (rows * a->swb + 1023) / 1024 * 1024;
-        const int stage = a_bytes + b_bytes;
+        // an upsampled chunk's half-resolution box (rows for either parity of y0)
+        const int up_rows = (TR + 3) / 2 + 1, up_cols = a->Wt / 2 + 2;
+        const int up_bytes = up ? (up_rows * up_cols * a->swb + 1023) / 1024 * 1024 : 0;
+        const int stage = a_bytes + b_bytes + up_bytes;
+        // three stages where they fit without costing the second CTA per SM
         int ns = nk == 1 ? 1 : 3;
         while (ns > 1 && ns * stage + 1024 > kTcSmemMax) --ns;
+        if (ns == 3 && 2 * (3 * stage + 2048) > kTcSmemSM && 2 * (2 * stage + 2048) <= kTcSmemSM)
+            ns = 2;
         if (ns * stage + 1024 > kTcSmemMax || (nk > 1 && ns < 2)) continue;
         const int ty = (H + TR - 1) / TR;
         const int64_t ctas = (int64_t)N * ty * a->tiles_x * ntiles;
@@ -852,6 +875,10 @@ static bool tc_plan(int N, int H, int W, int Np, int ntiles, int nk, nn::ConvTcA
             a->box_bytes = (TR + 2) * a->rs * a->swb;
             a->stage_bytes = stage;
             a->stages = ns;
+            a->up_rows = up_rows;
+            a->up_cols = up_cols;
+            a->up_off = a_bytes + b_bytes;
+            a->up_box_bytes = up_rows * up_cols * a->swb;
         }
     }
     if (best < 0) return false;
@@ -878,7 +905,7 @@ bool tc_conv_supported(int H, int W, int C1, int C2, int Co) {
     a.swb = 2 * a.Kc;
     int nt, Np;
     tc_ntiles(Co, a.Kc, &nt, &Np);
-    return tc_plan(1, H, W, Np, nt, Ci / a.Kc, &a);
+    return tc_plan(1, H, W, Np, nt, Ci / a.Kc, C2 > 0, &a);
 }
 
 cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_t s) {
@@ -942,13 +969,20 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
         const int rows = (TR + 2) * a.rs + a.natoms;
         const int xb = (rows * a.swx + 1023) / 1024 * 1024;
         const int gab = TR * a.Wt * 32;
-        const int stage = (xb + a.ng * gab + 1023) / 1024 * 1024;
+        const int up_rows = (TR + 3) / 2 + 1, up_cols = a.Wt / 2 + 2;
+        const int up_off = (xb + a.ng * gab + 1023) / 1024 * 1024;
+        const int up_bytes = w.C2 > 0 ? (up_rows * up_cols * a.swx + 1023) / 1024 * 1024 : 0;
+        const int stage = up_off + up_bytes;
         if (2 * stage + 1024 > kTcSmemMax && TR > 1) continue;
         a.TR = TR;
         a.x_bytes = xb;
         a.x_box_bytes = (TR + 2) * a.rs * a.swx;
         a.g_atom_bytes = gab;
         a.stage_bytes = stage;
+        a.up_rows = up_rows;
+        a.up_cols = up_cols;
+        a.up_off = up_off;
+        a.up_box_bytes = up_rows * up_cols * a.swx;
         a.stages = 3 * stage + 1024 <= kTcSmemMax ? 3 : 2;
         break;
     }
@@ -993,13 +1027,28 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
+    CUtensorMap mu = mx;
+    if (w.C2 > 0) {
+        cuuint64_t dims[4] = {(cuuint64_t)w.C2, (cuuint64_t)(w.W / 2), (cuuint64_t)(w.H / 2),
+                              (cuuint64_t)w.N};
+        cuuint64_t str[3] = {(cuuint64_t)w.C2 * 2, (cuuint64_t)(w.W / 2) * w.C2 * 2,
+                             (cuuint64_t)(w.H / 2) * (w.W / 2) * w.C2 * 2};
+        cuuint32_t box[4] = {(cuuint32_t)a.Kc, (cuuint32_t)a.up_cols, (cuuint32_t)a.up_rows, 1};
+        if (encode_fn()(&mu, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w.in2),
+                        dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     int smem = a.stages * a.stage_bytes + 1024;
     const int by_tmem = 512 / a.tmem_cols;
     smem = std::min(kTcSmemMax, std::max(smem, kTcSmemSM / (by_tmem + 1) - 1024 + 256));
     cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_wgrad_tc_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    nn::conv3x3_wgrad_tc_kernel<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, a);
+    nn::conv3x3_wgrad_tc_kernel<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, mu,
+                                                                                      a);
     e = cudaGetLastError();
     if (e != cudaSuccess || !w.db) return e;
     // the bias gradient: column sums of g
@@ -1044,7 +1093,7 @@ cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cud
     a.nk1 = c.C1 / a.Kc;
     int ntiles = 1;
     tc_ntiles(c.Co, a.Kc, &ntiles, &a.Np);
-    if (!tc_plan(c.N, c.H, c.W, a.Np, ntiles, a.nk, &a)) return cudaErrorInvalidValue;
+    if (!tc_plan(c.N, c.H, c.W, a.Np, ntiles, a.nk, c.C2 > 0, &a)) return cudaErrorInvalidValue;
     a.relu = c.relu;
     a.out_f32 = c.out_f32;
     // the full-resolution input as a 4-D tensor (channels, x, y, image); one
@@ -1062,6 +1111,21 @@ cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cud
                              a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // the half-resolution input (channels, x, y, image); one box is Kc
+    // channels x up_cols x up_rows of one image
+    CUtensorMap map2 = map;
+    if (c.C2 > 0) {
+        cuuint64_t d2[4] = {(cuuint64_t)c.C2, (cuuint64_t)(c.W / 2), (cuuint64_t)(c.H / 2),
+                            (cuuint64_t)c.N};
+        cuuint64_t s2[3] = {(cuuint64_t)c.C2 * 2, (cuuint64_t)(c.W / 2) * c.C2 * 2,
+                            (cuuint64_t)(c.H / 2) * (c.W / 2) * c.C2 * 2};
+        cuuint32_t b2[4] = {(cuuint32_t)a.Kc, (cuuint32_t)a.up_cols, (cuuint32_t)a.up_rows, 1};
+        r = encode_fn()(&map2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(c.in2),
+                        d2, s2, b2, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
     int smem = a.stages * a.stage_bytes + 1024;
     // no more CTAs on an SM than its tensor memory holds, so that no
     // allocation waits
@@ -1072,7 +1136,7 @@ cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cud
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = c.N * a.tiles_y * a.tiles_x;
-    nn::conv3x3_tc_kernel<<<dim3(tiles, ntiles), nn::kTcThreads, smem, s>>>(map, a);
+    nn::conv3x3_tc_kernel<<<dim3(tiles, ntiles), nn::kTcThreads, smem, s>>>(map, map2, a);
     return cudaGetLastError();
 }
 
