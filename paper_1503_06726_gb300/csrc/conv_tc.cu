@@ -223,6 +223,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 }
 
 
+// UP: the layer has upsampled channels (the expansion is compiled only then)
+template <bool UP>
 __global__ void __launch_bounds__(kTcThreads)
     conv3x3_tc_kernel(const __grid_constant__ CUtensorMap map1,
                       const __grid_constant__ CUtensorMap map2, ConvTcArgs a) {
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kTcThreads)
         const int s = k % NS;
         const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
         const uint32_t fb = smem_u32(&bar_full[s]);
-        if (k < a.nk1) {
+        if (!UP || k < a.nk1) {
             mbar_expect_tx(fb, b_bytes + (uint32_t)a.box_bytes);
             tma_load_4d(st, &map1, k * a.Kc, x0 - 1, y0 - 1, n, fb);
         } else {
@@ -308,11 +310,11 @@ __global__ void __launch_bounds__(kTcThreads)
 
     if (tid == 0)
         for (int k = 0; k < NS && k < a.nk; ++k) issue(k);
-    if (a.nk1 == 0) {
+    if (UP && a.nk1 == 0) {
         expand_chunk(0);
         __syncthreads();
     }
-    for (int k = 0; k < a.nk && !s_bad; ++k) {
+    for (int k = 0; k < a.nk; ++k) {
         const int s = k % NS;
         const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
         if (tid == 0) {
@@ -348,8 +350,9 @@ __global__ void __launch_bounds__(kTcThreads)
                 }
             }
         }
-        if (k + 1 < a.nk && k + 1 >= a.nk1) expand_chunk(k + 1);
+        if (UP && k + 1 < a.nk && k + 1 >= a.nk1) expand_chunk(k + 1);
         __syncthreads();
+        if (s_bad) break;
     }
     // after an error: the copies still in flight land before the CTA leaves
     if (tid == 0)
@@ -503,6 +506,7 @@ struct WgTcArgs {
     int up_rows, up_cols, up_off, up_box_bytes;  // the half-resolution box, as in ConvTcArgs
 };
 
+template <bool UP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     conv3x3_wgrad_tc_kernel(const __grid_constant__ CUtensorMap mapx,
                             const __grid_constant__ CUtensorMap mapg,
@@ -516,7 +520,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int NS = a.stages;
     const int chunk = blockIdx.y, ntile = blockIdx.z;
     const int c0 = chunk * a.Kc, co0 = ntile * a.Np;
-    const bool up = c0 >= a.C1;  // the chunk comes from the upsampled input
+    const bool up = UP && c0 >= a.C1;  // the chunk comes from the upsampled input
     // this CTA's pixel tiles
     const int t_begin = (int)((int64_t)a.total_tiles * blockIdx.x / a.sk);
     const int t_end = (int)((int64_t)a.total_tiles * (blockIdx.x + 1) / a.sk);
@@ -601,7 +605,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         expand_tile(0);
         __syncthreads();
     }
-    for (int k = 0; k < nt && !s_bad; ++k) {
+    for (int k = 0; k < nt; ++k) {
         const int s = k % NS;
         const uint32_t st = base + (uint32_t)s * (uint32_t)a.stage_bytes;
         if (tid == 0) {
@@ -641,6 +645,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         if (up && k + 1 < nt) expand_tile(k + 1);
         __syncthreads();
+        if (s_bad) break;
     }
     if (tid == 0)
         for (int s = 0; s < NS; ++s)
@@ -1044,11 +1049,10 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
     int smem = a.stages * a.stage_bytes + 1024;
     const int by_tmem = 512 / a.tmem_cols;
     smem = std::min(kTcSmemMax, std::max(smem, kTcSmemSM / (by_tmem + 1) - 1024 + 256));
-    cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_wgrad_tc_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = w.C2 > 0 ? nn::conv3x3_wgrad_tc_kernel<true> : nn::conv3x3_wgrad_tc_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    nn::conv3x3_wgrad_tc_kernel<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, mu,
-                                                                                      a);
+    kern<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, mu, a);
     e = cudaGetLastError();
     if (e != cudaSuccess || !w.db) return e;
     // the bias gradient: column sums of g
@@ -1132,11 +1136,11 @@ cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cud
     const int by_tmem = 512 / a.tmem_cols;
     smem = std::max(smem, kTcSmemSM / (by_tmem + 1) - 1024 + 256);
     smem = std::min(smem, kTcSmemMax);
-    cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_tc_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = c.C2 > 0 ? nn::conv3x3_tc_kernel<true> : nn::conv3x3_tc_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int tiles = c.N * a.tiles_y * a.tiles_x;
-    nn::conv3x3_tc_kernel<<<dim3(tiles, ntiles), nn::kTcThreads, smem, s>>>(map, map2, a);
+    kern<<<dim3(tiles, ntiles), nn::kTcThreads, smem, s>>>(map, map2, a);
     return cudaGetLastError();
 }
 
