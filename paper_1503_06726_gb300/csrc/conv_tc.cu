@@ -492,6 +492,7 @@ __global__ void tile_weights_tc_kernel(const __nv_bfloat16* w, int Co, int Ci, i
 struct WgTcArgs {
     const __nv_bfloat16* in2;  // (N, H/2, W/2, C2), read upsampled, or NULL
     float* dw;                 // (9, Ci, Co) FP32, accumulated
+    float* db;                 // (Co) FP32, accumulated, or NULL
     unsigned* err;
     int N, H, W, C1, C2, Co;
     int Kc, swx, swcode_x;     // the X chunk: channels, bytes per pixel row, layout code
@@ -552,6 +553,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t g_bytes = (uint32_t)a.ng * (uint32_t)a.g_atom_bytes;
     int loading[kTcMaxStages] = {-1, -1, -1};
     uint32_t started = 0u;  // accumulators that hold a first product
+    // the CTAs of the first chunk also sum the bias gradient, in warps 1 - 3
+    // (warp 0 issues the multiplies): channels tid - 32 and tid + 64 of the N tile
+    const bool dbsum = a.db != nullptr && chunk == 0 && tid >= 32 && tid - 32 < a.Np;
+    float db_acc[2] = {0.f, 0.f};
 
     auto tile_xy = [&](int T, int& n, int& y0, int& x0) {
         n = T / per_img;
@@ -644,6 +649,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
         }
         if (up && k + 1 < nt) expand_tile(k + 1);
+        if (dbsum && !s_bad && mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
+            // the bias gradient: this thread's output channels summed over
+            // the tile's pixel rows of G in shared memory (beside the multiplies)
+            for (int i = 0; i < 2; ++i) {
+                const int c = tid - 32 + 96 * i;
+                if (c >= a.Np) break;
+                const unsigned char* g0 = smem_raw + (st - smem_u32(smem_raw)) + a.x_bytes +
+                                          (c >> 4) * a.g_atom_bytes;
+                const int e = c & 15;
+                float acc = 0.f;
+                for (int p = 0; p < a.TR * a.Wt; ++p)
+                    acc += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(
+                        g0 + swizzle_off((uint32_t)(p * 32 + e * 2), 32)));
+                db_acc[i] += acc;
+            }
+        }
         __syncthreads();
         if (s_bad) break;
     }
@@ -694,30 +715,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else if (!ok && tid == 0) {
         atomicOr(a.err, 1u);
     }
+    if (ok && dbsum)
+        for (int i = 0; i < 2; ++i) {
+            const int c = tid - 32 + 96 * i;
+            if (c < a.Np && co0 + c < a.Co) atomicAdd(a.db + co0 + c, db_acc[i]);
+        }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(a.tmem_cols)
                      : "memory");
-}
-
-// db[co] += sum over pixels of g[p][co]: R pixel rows per block at a time, a
-// channel per thread, partial sums reduced in shared memory
-__global__ void bias_grad_kernel(const __nv_bfloat16* g, int64_t npix, int Co, float* db) {
-    extern __shared__ float red[];
-    const int R = blockDim.x / Co;
-    const int c = threadIdx.x % Co, r = threadIdx.x / Co;
-    float acc = 0.f;
-    if (r < R)
-        for (int64_t p = (int64_t)blockIdx.x * R + r; p < npix; p += (int64_t)gridDim.x * R)
-            acc += __bfloat162float(g[p * Co + c]);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    if (r == 0) {
-        for (int k = 1; k < R; ++k) acc += red[k * Co + c];
-        atomicAdd(db + c, acc);
-    }
 }
 
 // The fused weight refresh: for layer blockIdx.y, from its FP32 master
@@ -950,6 +958,7 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
     std::memset(&a, 0, sizeof(a));
     a.in2 = w.in2;
     a.dw = w.dw;
+    a.db = w.db;
     a.err = err;
     a.N = w.N;
     a.H = w.H;
@@ -1053,13 +1062,6 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     kern<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, mu, a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || !w.db) return e;
-    // the bias gradient: column sums of g
-    const int R = std::max(1, 256 / w.Co);
-    const int64_t npix = (int64_t)w.N * w.H * w.W;
-    const int blocks = (int)std::min<int64_t>((npix + R - 1) / R, 4 * sm_count());
-    nn::bias_grad_kernel<<<blocks, R * w.Co, R * w.Co * 4, s>>>(w.g, npix, w.Co, w.db);
     return cudaGetLastError();
 }
 
