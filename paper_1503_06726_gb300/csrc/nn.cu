@@ -23,6 +23,25 @@
 namespace lbib {
 namespace nn {
 
+// eight BF16 channels (16 bytes) in and out of FP32 registers
+__device__ __forceinline__ void load8(const __nv_bfloat16* p, float v[8]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(h[k]);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+__device__ __forceinline__ void store8(__nv_bfloat16* p, const float v[8]) {
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    *reinterpret_cast<uint4*>(p) = u;
+}
+
 constexpr int TH = kTH, TW = kTW, BM = TH * TW, BN = 64, KC = 32;
 constexpr int HH = TH + 2, HWD = TW + 2;   // halo tile
 constexpr int AST = KC + 8;                // smem row stride (bf16) of halo / weight rows
@@ -289,29 +308,39 @@ __global__ void __launch_bounds__(kConvThreads) conv3x3_wgrad_kernel(WgradArgs a
 // elementwise layers
 __global__ void avgpool2_kernel(const __nv_bfloat16* x, __nv_bfloat16* y, int N, int H, int W,
                                 int C) {
+    // one thread: eight channels of one output pixel (C a multiple of 8)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int Ho = H / 2, Wo = W / 2;
-    if (i >= (int64_t)N * Ho * Wo * C) return;
-    const int c = (int)(i % C);
-    const int64_t p = i / C;
+    const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+    if (i >= (int64_t)N * Ho * Wo * C8) return;
+    const int c = (int)(i % C8) * 8;
+    const int64_t p = i / C8;
     const int xo = (int)(p % Wo), yo = (int)((p / Wo) % Ho), n = (int)(p / ((int64_t)Wo * Ho));
     const int64_t b = (((int64_t)n * H + 2 * yo) * W + 2 * xo) * C + c;
-    const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) +
-                    __bfloat162float(x[b + (int64_t)W * C]) +
-                    __bfloat162float(x[b + (int64_t)W * C + C]);
-    y[i] = __float2bfloat16(0.25f * s);
+    float a[8], bb[8], cc[8], d[8], o[8];
+    load8(x + b, a);
+    load8(x + b + C, bb);
+    load8(x + b + (int64_t)W * C, cc);
+    load8(x + b + (int64_t)W * C + C, d);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = 0.25f * (a[k] + bb[k] + cc[k] + d[k]);
+    store8(y + p * C + c, o);
 }
 
 // gx (full res) = 0.25 * g (half res) at each of the 4 children
 __global__ void avgpool2_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gx, int N, int H,
                                     int W, int C) {
+    // one thread: eight channels of one full-resolution pixel
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (int64_t)N * H * W * C) return;
-    const int c = (int)(i % C);
-    const int64_t p = i / C;
+    const int C8 = C / 8;
+    if (i >= (int64_t)N * H * W * C8) return;
+    const int c = (int)(i % C8) * 8;
+    const int64_t p = i / C8;
     const int x = (int)(p % W), y = (int)((p / W) % H), n = (int)(p / ((int64_t)W * H));
-    const float v = __bfloat162float(g[(((int64_t)n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c]);
-    gx[i] = __float2bfloat16(0.25f * v);
+    float v[8];
+    load8(g + (((int64_t)n * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c, v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] *= 0.25f;
+    store8(gx + p * C + c, v);
 }
 
 // split the gradient of a concatenation [skip (C1), upsample2(x2) (C2)]:
@@ -320,39 +349,61 @@ __global__ void avgpool2_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gx, i
 __global__ void concat_bwd_kernel(const __nv_bfloat16* g, __nv_bfloat16* gskip,
                                   __nv_bfloat16* gx2, const __nv_bfloat16* gate2, int N, int H,
                                   int W, int C1, int C2, int accumulate_skip) {
+    // one thread: eight channels (C1 and C2 multiples of 8)
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int C = C1 + C2;
-    const int64_t nfull = (int64_t)N * H * W * C1;
+    const int C = C1 + C2, C18 = C1 / 8, C28 = C2 / 8;
+    const int64_t nfull = (int64_t)N * H * W * C18;
     if (i < nfull) {
-        const int c = (int)(i % C1);
-        const int64_t p = i / C1;
-        const float v = __bfloat162float(g[p * C + c]);
-        gskip[i] = __float2bfloat16(accumulate_skip ? __bfloat162float(gskip[i]) + v : v);
+        const int c = (int)(i % C18) * 8;
+        const int64_t p = i / C18;
+        float v[8];
+        load8(g + p * C + c, v);
+        if (accumulate_skip) {
+            float s0[8];
+            load8(gskip + p * C1 + c, s0);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = s0[k] + v[k];
+        }
+        store8(gskip + p * C1 + c, v);
         return;
     }
     const int64_t j = i - nfull;
     const int Ho = H / 2, Wo = W / 2;
-    if (j >= (int64_t)N * Ho * Wo * C2) return;
-    const int c = (int)(j % C2);
-    const int64_t p = j / C2;
+    if (j >= (int64_t)N * Ho * Wo * C28) return;
+    const int c = (int)(j % C28) * 8;
+    const int64_t p = j / C28;
     const int xo = (int)(p % Wo), yo = (int)((p / Wo) % Ho), n = (int)(p / ((int64_t)Wo * Ho));
-    float s = 0.f;
+    float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-            s += __bfloat162float(
-                g[(((int64_t)n * H + 2 * yo + dy) * W + 2 * xo + dx) * C + C1 + c]);
-    if (gate2 && !(__bfloat162float(gate2[j]) > 0.f)) s = 0.f;
-    gx2[j] = __float2bfloat16(s);
+        for (int dx = 0; dx < 2; ++dx) {
+            float v[8];
+            load8(g + (((int64_t)n * H + 2 * yo + dy) * W + 2 * xo + dx) * C + C1 + c, v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s8[k] += v[k];
+        }
+    if (gate2) {
+        float gt[8];
+        load8(gate2 + p * C2 + c, gt);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (!(gt[k] > 0.f)) s8[k] = 0.f;
+    }
+    store8(gx2 + p * C2 + c, s8);
 }
 
 // g (bf16) = g + h where act > 0, else 0 (the sum's ReLU backward)
 __global__ void add_gate_kernel(__nv_bfloat16* g, const __nv_bfloat16* h,
                                 const __nv_bfloat16* act, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // one thread: eight elements (n a multiple of 8)
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8;
     if (i >= n) return;
-    g[i] = __bfloat162float(act[i]) > 0.f
-               ? __float2bfloat16(__bfloat162float(g[i]) + __bfloat162float(h[i]))
-               : __float2bfloat16(0.f);
+    float a[8], b[8], t[8];
+    load8(g + i, a);
+    load8(h + i, b);
+    load8(act + i, t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = t[k] > 0.f ? a[k] + b[k] : 0.f;
+    store8(g + i, a);
 }
 
 // MSE: loss += sum (y - t)^2 / n; dy = 2 (y - t) / n  (y in channel 0 of Cy)
@@ -406,12 +457,10 @@ __global__ void features_kernel(const uint8_t* id_mask, const uint8_t* src, cons
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)N * HW) return;
     const int n = (int)(i / HW);
-    __nv_bfloat16* o = x + i * 16;
-    o[0] = __float2bfloat16(id_mask[i] ? 1.f : 0.f);
-    o[1] = __float2bfloat16(src[i] ? 1.f : 0.f);
-    o[2] = __float2bfloat16(Dn[n]);
-    o[3] = __float2bfloat16(Kn[n]);
-    for (int c = 4; c < 16; ++c) o[c] = __float2bfloat16(0.f);
+    float v[8] = {id_mask[i] ? 1.f : 0.f, src[i] ? 1.f : 0.f, Dn[n], Kn[n], 0.f, 0.f, 0.f, 0.f};
+    const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    store8(x + i * 16, v);
+    store8(x + i * 16 + 8, z);
 }
 
 // target y = phi * decay / src_rate; prediction phi = y * src_rate / decay

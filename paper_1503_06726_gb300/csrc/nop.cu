@@ -290,7 +290,7 @@ cudaError_t forward(lbib_nop* n, int N) {
     for (int l = 0; l < kLevels && e == cudaSuccess; ++l) {
         const int64_t hw = (int64_t)(n->H >> l) * (n->W >> l);
         if (l > 0) {
-            nn::avgpool2_kernel<<<blocks(N * hw * kCh[l - 1]), 256, 0, n->stream>>>(
+            nn::avgpool2_kernel<<<blocks(N * hw * kCh[l - 1] / 8), 256, 0, n->stream>>>(
                 n->enc_out[l - 1], n->enc_in[l], N, n->H >> (l - 1), n->W >> (l - 1), kCh[l - 1]);
             e = cudaGetLastError();
         }
@@ -355,7 +355,7 @@ cudaError_t backward(lbib_nop* n, int N) {
             e = conv_fwd(n, a, s1, nullptr, kCh[l], 0, l, s2, 0, 0, a.wd, a.wdt,
                          nullptr, kCh[l] + kCh[l + 1], N);
         if (e == cudaSuccess) {
-            const int64_t tot = N * hw * kCh[l] + N * (hw / 4) * kCh[l + 1];
+            const int64_t tot = (N * hw * kCh[l] + N * (hw / 4) * kCh[l + 1]) / 8;
             // g: the gradient of the deeper output, through its ReLU
             nn::concat_bwd_kernel<<<blocks(tot), 256, 0, n->stream>>>(
                 s2, n->gskip[l], g, deeper, N, n->H >> l, n->W >> l, kCh[l], kCh[l + 1], 0);
@@ -371,7 +371,7 @@ cudaError_t backward(lbib_nop* n, int N) {
         if (l < kLevels - 1) {
             // the skip's gradient joins the deeper path's, through the ReLU
             // (at the deepest level the concatenation split applied it)
-            nn::add_gate_kernel<<<blocks(N * hw * kCh[l]), 256, 0, n->stream>>>(
+            nn::add_gate_kernel<<<blocks(N * hw * kCh[l] / 8), 256, 0, n->stream>>>(
                 g, n->gskip[l], n->enc_out[l], N * hw * kCh[l]);
             e = cudaGetLastError();
         }
@@ -385,7 +385,7 @@ cudaError_t backward(lbib_nop* n, int N) {
             e = conv_fwd(n, a, s1, nullptr, kCh[l], 0, l, s2, 0, 0, a.wd, a.wdt, nullptr, cin, N);
             if (e == cudaSuccess) {
                 const int64_t cnt = N * (int64_t)(n->H >> (l - 1)) * (n->W >> (l - 1)) * cin;
-                nn::avgpool2_bwd_kernel<<<blocks(cnt), 256, 0, n->stream>>>(
+                nn::avgpool2_bwd_kernel<<<blocks(cnt / 8), 256, 0, n->stream>>>(
                     s2, g, N, n->H >> (l - 1), n->W >> (l - 1), cin);
                 e = cudaGetLastError();
             }
