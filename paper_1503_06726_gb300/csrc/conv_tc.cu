@@ -746,22 +746,26 @@ __device__ __forceinline__ TileGeom tile_geom(int Ci, int Co) {
     g.nk = Ci / g.Kc;
     return g;
 }
-// element i of the tiling of a (9, Co, Ci) array: where it goes (dst) and
-// which (tap, co, ci) of the array it holds; false for padding (co >= Co)
+// element i of the tiling of a (9, Co, Ci) array, counted with the output
+// channel (row) fastest or the input channel (e) fastest -- whichever is
+// contiguous in the FP32 source, so that a warp's reads coalesce: where it
+// goes (dst) and which (tap, co, ci) of the array it holds; false for padding
+// (co >= Co)
 __device__ __forceinline__ bool tiled_source(int64_t i, int Ci, int Co, const TileGeom& g,
-                                             int64_t* dst, int* t, int* co, int* ci) {
+                                             bool row_fast, int64_t* dst, int* t, int* co,
+                                             int* ci) {
     const int64_t per_tile = (int64_t)g.nk * 9 * g.Np * g.Kc;
     const int64_t r = i % per_tile;
     const int tile = (int)(i / per_tile);
-    const int e = (int)(r % g.Kc);
-    const int row = (int)((r / g.Kc) % g.Np);
-    *t = (int)((r / ((int64_t)g.Kc * g.Np)) % 9);
-    const int k = (int)(r / ((int64_t)g.Kc * g.Np * 9));
+    const int row = row_fast ? (int)(r % g.Np) : (int)((r / g.Kc) % g.Np);
+    const int e = row_fast ? (int)((r / g.Np) % g.Kc) : (int)(r % g.Kc);
+    *t = (int)((r / ((int64_t)g.Np * g.Kc)) % 9);
+    const int k = (int)(r / ((int64_t)g.Np * g.Kc * 9));
     *co = tile * g.Np + row;
     *ci = k * g.Kc + e;
     const int swb = 2 * g.Kc;
     const uint32_t off = swizzle_off((uint32_t)(row * swb + e * 2), swb);
-    *dst = i - e - (int64_t)row * g.Kc + off / 2;
+    *dst = (int64_t)tile * per_tile + ((int64_t)k * 9 + *t) * g.Np * g.Kc + off / 2;
     return *co < Co && *ci < Ci;
 }
 __global__ void refresh_weights_kernel(const WeightSet* sets) {
@@ -785,7 +789,7 @@ __global__ void refresh_weights_kernel(const WeightSet* sets) {
             // the forward tiling: the (9, Co, Ci) array is wf
             int64_t dst;
             int t, co, ci;
-            const bool in = tiled_source(i - n_copy, Ci, Co, gf, &dst, &t, &co, &ci);
+            const bool in = tiled_source(i - n_copy, Ci, Co, gf, true, &dst, &t, &co, &ci);
             ws.wft[dst] = in ? __float2bfloat16(ws.w[((int64_t)t * Ci + ci) * Co + co])
                              : __float2bfloat16(0.f);
         } else {
@@ -793,7 +797,7 @@ __global__ void refresh_weights_kernel(const WeightSet* sets) {
             // output channels are the forward input channels
             int64_t dst;
             int t, co, ci;
-            const bool in = tiled_source(i - n_copy - n_f, Co, Ci, gd, &dst, &t, &co, &ci);
+            const bool in = tiled_source(i - n_copy - n_f, Co, Ci, gd, false, &dst, &t, &co, &ci);
             ws.wdt[dst] = in ? __float2bfloat16(ws.w[((int64_t)(8 - t) * Ci + co) * Co + ci])
                              : __float2bfloat16(0.f);
         }
