@@ -533,9 +533,8 @@ int lbib_nn_conv3x3_tc(int32_t N, int32_t H, int32_t W, int32_t C1, int32_t C2, 
  * added to d_dw with FP32 reductions):
  *   lbib_nn_conv3x3_wgrad_tc_supported  1 when the shape is supported: W from 16
  *                          to 128 in multiples of 16, or a multiple of 128;
- *                          C1 >= 16, C1 and C2 multiples of 16, C1 a multiple of
- *                          32 when C1 + C2 is; Co a multiple of 16; H and W even
- *                          when C2 > 0
+ *                          C1 >= 16, C1 and C2 multiples of 16, C1 + C2 <= 384;
+ *                          Co a multiple of 16; H and W even when C2 > 0
  *   lbib_nn_conv3x3_wgrad_tc  as lbib_nn_conv3x3_wgrad (d_dw (9, C1+C2, Co) and
  *                          d_db (Co, or NULL) accumulated: zero them first);
  *                          d_in1, d_in2, d_g, d_dw 16-byte aligned; d_err as for

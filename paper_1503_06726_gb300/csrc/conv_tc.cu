@@ -489,14 +489,21 @@ __global__ void tile_weights_tc_kernel(const __nv_bfloat16* w, int Co, int Ci, i
 // in flight), summed at the end and added to dW with FP32 reductions.  A CTA
 // takes one input-channel chunk, one N tile and a range of pixel tiles
 // (split K over CTAs).  Pipeline and bounded waits as the forward kernel.
+constexpr int kTcMaxChunks = 24;  // input-channel chunks of a weight gradient (up to 384 channels)
+
 struct WgTcArgs {
     const __nv_bfloat16* in2;  // (N, H/2, W/2, C2), read upsampled, or NULL
     float* dw;                 // (9, Ci, Co) FP32, accumulated
     float* db;                 // (Co) FP32, accumulated, or NULL
     unsigned* err;
     int N, H, W, C1, C2, Co;
-    int Kc, swx, swcode_x;     // the X chunk: channels, bytes per pixel row, layout code
-    int natoms;                // M atoms of the A operand: 128 / Kc
+    // the input-channel chunks (one per CTA row of the grid): 32 channels where
+    // the input allows, 16 for a remainder; each from in1 or the upsampled in2
+    int nchunks;
+    int ck_c0[kTcMaxChunks];    // first channel within its own input
+    int ck_row[kTcMaxChunks];   // first channel of dW (in1 channels, then in2's)
+    int ck_kc[kTcMaxChunks];    // 32 or 16
+    int ck_up[kTcMaxChunks];    // from in2
     int Np, ng;                // output channels of the N tile, its 16-channel G atoms
     int Wt, rs, TR, tiles_x, tiles_y, total_tiles;
     int sk;                    // CTAs sharing one (chunk, N tile): split K
@@ -509,9 +516,11 @@ struct WgTcArgs {
 
 template <bool UP>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    conv3x3_wgrad_tc_kernel(const __grid_constant__ CUtensorMap mapx,
-                            const __grid_constant__ CUtensorMap mapg,
-                            const __grid_constant__ CUtensorMap mapu, WgTcArgs a) {
+    conv3x3_wgrad_tc_kernel(const __grid_constant__ CUtensorMap mapx32,
+                            const __grid_constant__ CUtensorMap mapx16,
+                            const __grid_constant__ CUtensorMap mapu32,
+                            const __grid_constant__ CUtensorMap mapu16,
+                            const __grid_constant__ CUtensorMap mapg, WgTcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar_full[kTcMaxStages], bar_done[kTcMaxStages];
     __shared__ uint32_t tmem_slot;
@@ -520,8 +529,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int NS = a.stages;
     const int chunk = blockIdx.y, ntile = blockIdx.z;
-    const int c0 = chunk * a.Kc, co0 = ntile * a.Np;
-    const bool up = UP && c0 >= a.C1;  // the chunk comes from the upsampled input
+    const int co0 = ntile * a.Np;
+    // this CTA's chunk: its width (the 64- or 32-byte swizzle, 4 or 8 shifts
+    // in M), its place in its input and in dW
+    const int Kc = a.ck_kc[chunk], swx = 2 * Kc, swcode = Kc == 32 ? 4 : 6;
+    const int c0 = a.ck_c0[chunk], row0 = a.ck_row[chunk];
+    const bool up = UP && a.ck_up[chunk] != 0;  // the chunk comes from the upsampled input
+    const CUtensorMap* mapx = Kc == 32 ? &mapx32 : &mapx16;
+    const CUtensorMap* mapu = Kc == 32 ? &mapu32 : &mapu16;
+    const uint32_t x_box_bytes = (uint32_t)((a.TR + 2) * a.rs * swx);
+    const uint32_t up_box_bytes = (uint32_t)(a.up_rows * a.up_cols * swx);
     // this CTA's pixel tiles
     const int t_begin = (int)((int64_t)a.total_tiles * blockIdx.x / a.sk);
     const int t_end = (int)((int64_t)a.total_tiles * (blockIdx.x + 1) / a.sk);
@@ -571,12 +588,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         int n, y0, x0;
         tile_xy(t_begin + k, n, y0, x0);
         if (!up) {
-            mbar_expect_tx(fb, g_bytes + (uint32_t)a.x_box_bytes);
-            tma_load_4d(st, &mapx, c0, x0 - 1, y0 - 1, n, fb);
+            mbar_expect_tx(fb, g_bytes + x_box_bytes);
+            tma_load_4d(st, mapx, c0, x0 - 1, y0 - 1, n, fb);
         } else {
-            mbar_expect_tx(fb, g_bytes + (uint32_t)a.up_box_bytes);
-            tma_load_4d(st + (uint32_t)a.up_off, &mapu, c0 - a.C1, (x0 - 1) >> 1, (y0 - 1) >> 1,
-                        n, fb);
+            mbar_expect_tx(fb, g_bytes + up_box_bytes);
+            tma_load_4d(st + (uint32_t)a.up_off, mapu, c0, (x0 - 1) >> 1, (y0 - 1) >> 1, n, fb);
         }
         for (int at = 0; at < a.ng; ++at)
             tma_load_4d(st + (uint32_t)a.x_bytes + (uint32_t)(at * a.g_atom_bytes), &mapg,
@@ -598,7 +614,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         __syncthreads();
         if (s_up_ok && mbar_wait(smem_u32(&bar_full[s]), (k / NS) & 1)) {
             unsigned char* gst = smem_raw + (st - smem_u32(smem_raw));
-            expand_upsampled(gst, gst + a.up_off, a.TR + 2, a.rs, a.swx, x0, y0, a.up_cols, tid,
+            expand_upsampled(gst, gst + a.up_off, a.TR + 2, a.rs, swx, x0, y0, a.up_cols, tid,
                              kTcThreads);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -630,8 +646,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         for (int ky = 0; ky < 3; ++ky) {
                             const int acc = set * 3 + ky;
                             const uint64_t adesc = smem_desc_mn(
-                                st + (uint32_t)(((r + ky) * a.rs + k0) * a.swx), (uint32_t)a.swx,
-                                8u * (uint32_t)a.swx, (uint32_t)a.swcode_x);
+                                st + (uint32_t)(((r + ky) * a.rs + k0) * swx), (uint32_t)swx,
+                                8u * (uint32_t)swx, (uint32_t)swcode);
                             tc_mma(tmem + (uint32_t)(acc * a.Np), adesc, bdesc, idesc,
                                    (started >> acc) & 1u);
                             started |= 1u << acc;
@@ -681,7 +697,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (ok && committed >= 0) {
         // lane m of warp w: A row m = 32 w + lane = (shift j, channel ci)
         const int m = warp * 32 + lane;
-        const int j = m / a.Kc, ci = m % a.Kc;
+        const int j = m / Kc, ci = m % Kc;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         for (int ky = 0; ky < 3; ++ky)
             for (int cl = 0; cl < a.Np; cl += 16) {
@@ -694,8 +710,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                     for (int q = 0; q < 16; ++q) v[q] += w[q];
                 }
-                if (j < 3 && c0 + ci < a.C1 + a.C2) {
-                    float* d = a.dw + ((int64_t)(ky * 3 + j) * (a.C1 + a.C2) + c0 + ci) * a.Co +
+                if (j < 3) {
+                    float* d = a.dw + ((int64_t)(ky * 3 + j) * (a.C1 + a.C2) + row0 + ci) * a.Co +
                                co0 + cl;
                     if (co0 + cl + 16 <= a.Co) {
                         // four FP32 reductions per instruction (d is 16-byte aligned:
@@ -948,10 +964,9 @@ static void tcw_ntiles(int Co, int* ntiles, int* Np) {
 }
 
 bool tc_wgrad_supported(int H, int W, int C1, int C2, int Co) {
-    const int Ci = C1 + C2;
     if (H < 1 || W < 16 || (W <= 128 ? W % 16 : W % 128) || C1 < 16 || C1 % 16 || C2 < 0 ||
-        C2 % 16 || Co < 16 || Co % 16 || (C2 > 0 && (H % 2 || W % 2)) || C1 % tc_kc(Ci) ||
-        encode_fn() == nullptr)
+        C2 % 16 || Co < 16 || Co % 16 || (C2 > 0 && (H % 2 || W % 2)) ||
+        (C1 + C2) > 16 * nn::kTcMaxChunks || encode_fn() == nullptr)
         return false;
     return true;
 }
@@ -970,37 +985,47 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
     a.C1 = w.C1;
     a.C2 = w.C2;
     a.Co = w.Co;
-    const int Ci = w.C1 + w.C2;
-    a.Kc = tc_kc(Ci);
-    a.swx = 2 * a.Kc;
-    a.swcode_x = a.Kc == 32 ? 4 : 6;
-    a.natoms = nn::kTcM / a.Kc;
+    // the chunks: 32 channels where the input has them, 16 for a remainder
+    int nchunks = 0;
+    for (int src = 0; src < 2; ++src) {
+        const int C = src == 0 ? w.C1 : w.C2;
+        for (int c = 0; c < C;) {
+            if (nchunks == nn::kTcMaxChunks) return cudaErrorInvalidValue;
+            const int kc = C - c >= 32 ? 32 : 16;
+            a.ck_c0[nchunks] = c;
+            a.ck_row[nchunks] = (src == 0 ? 0 : w.C1) + c;
+            a.ck_kc[nchunks] = kc;
+            a.ck_up[nchunks] = src;
+            ++nchunks;
+            c += kc;
+        }
+    }
+    a.nchunks = nchunks;
     int ntn = 1;
     tcw_ntiles(w.Co, &ntn, &a.Np);
     a.ng = a.Np / 16;
     a.Wt = w.W <= 128 ? w.W : 128;
     a.rs = a.Wt + 2;
     a.tiles_x = w.W / a.Wt;
-    // the tile: TR rows, the largest of 4, 2, 1 whose stage fits twice
+    // the tile: TR rows, the largest of 4, 2, 1 whose stage fits twice; the
+    // halo region holds a 32-channel chunk (64-byte rows) plus the rows the
+    // unused shifts of the last K step read (up to eight, for 16 channels)
     for (int TR = 4; TR >= 1; TR /= 2) {
-        // halo rows plus the rows the unused shifts of the last K step read
-        const int rows = (TR + 2) * a.rs + a.natoms;
-        const int xb = (rows * a.swx + 1023) / 1024 * 1024;
+        const int rows = (TR + 2) * a.rs + 8;
+        const int xb = (rows * 64 + 1023) / 1024 * 1024;
         const int gab = TR * a.Wt * 32;
         const int up_rows = (TR + 3) / 2 + 1, up_cols = a.Wt / 2 + 2;
         const int up_off = (xb + a.ng * gab + 1023) / 1024 * 1024;
-        const int up_bytes = w.C2 > 0 ? (up_rows * up_cols * a.swx + 1023) / 1024 * 1024 : 0;
+        const int up_bytes = w.C2 > 0 ? (up_rows * up_cols * 64 + 1023) / 1024 * 1024 : 0;
         const int stage = up_off + up_bytes;
         if (2 * stage + 1024 > kTcSmemMax && TR > 1) continue;
         a.TR = TR;
         a.x_bytes = xb;
-        a.x_box_bytes = (TR + 2) * a.rs * a.swx;
         a.g_atom_bytes = gab;
         a.stage_bytes = stage;
         a.up_rows = up_rows;
         a.up_cols = up_cols;
         a.up_off = up_off;
-        a.up_box_bytes = up_rows * up_cols * a.swx;
         a.stages = 3 * stage + 1024 <= kTcSmemMax ? 3 : 2;
         break;
     }
@@ -1013,59 +1038,48 @@ cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t
     while (a.tmem_cols < 3 * a.sets * a.Np) a.tmem_cols *= 2;
     a.tiles_y = (w.H + a.TR - 1) / a.TR;
     a.total_tiles = w.N * a.tiles_y * a.tiles_x;
-    const int nchunks = Ci / a.Kc;
     // split K: one wave of CTAs over all (chunk, N tile) pairs (each CTA's
     // partial sums cost one reduction per weight), at least two tiles each
     a.sk = std::max(1, std::min(a.total_tiles / 2, sm_count() / (nchunks * ntn)));
-    // tensor maps: the input (channels, x, y, image) and the gradient
-    CUtensorMap mx, mg;
-    std::memset(&mx, 0, sizeof(mx));
-    std::memset(&mg, 0, sizeof(mg));
+    // tensor maps: the inputs (channels, x, y, image) with 32- and 16-channel
+    // boxes (as the chunks need them), and the gradient
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    {
-        cuuint64_t dims[4] = {(cuuint64_t)w.C1, (cuuint64_t)w.W, (cuuint64_t)w.H, (cuuint64_t)w.N};
-        cuuint64_t str[3] = {(cuuint64_t)w.C1 * 2, (cuuint64_t)w.W * w.C1 * 2,
-                             (cuuint64_t)w.H * w.W * w.C1 * 2};
-        cuuint32_t box[4] = {(cuuint32_t)a.Kc, (cuuint32_t)a.rs, (cuuint32_t)(a.TR + 2), 1};
-        if (encode_fn()(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w.in1),
-                        dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
-    {
-        cuuint64_t dims[4] = {(cuuint64_t)w.Co, (cuuint64_t)w.W, (cuuint64_t)w.H, (cuuint64_t)w.N};
-        cuuint64_t str[3] = {(cuuint64_t)w.Co * 2, (cuuint64_t)w.W * w.Co * 2,
-                             (cuuint64_t)w.H * w.W * w.Co * 2};
-        cuuint32_t box[4] = {16, (cuuint32_t)a.Wt, (cuuint32_t)a.TR, 1};
-        if (encode_fn()(&mg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w.g),
-                        dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
-    CUtensorMap mu = mx;
-    if (w.C2 > 0) {
-        cuuint64_t dims[4] = {(cuuint64_t)w.C2, (cuuint64_t)(w.W / 2), (cuuint64_t)(w.H / 2),
-                              (cuuint64_t)w.N};
-        cuuint64_t str[3] = {(cuuint64_t)w.C2 * 2, (cuuint64_t)(w.W / 2) * w.C2 * 2,
-                             (cuuint64_t)(w.H / 2) * (w.W / 2) * w.C2 * 2};
-        cuuint32_t box[4] = {(cuuint32_t)a.Kc, (cuuint32_t)a.up_cols, (cuuint32_t)a.up_rows, 1};
-        if (encode_fn()(&mu, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(w.in2),
-                        dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        a.Kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
+    auto encode = [&](CUtensorMap* m, const __nv_bfloat16* p, int C, int Wd, int Hd, int bc,
+                      int bw, int bh) {
+        cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)Wd, (cuuint64_t)Hd, (cuuint64_t)w.N};
+        cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)Wd * C * 2,
+                             (cuuint64_t)Hd * Wd * C * 2};
+        cuuint32_t box[4] = {(cuuint32_t)bc, (cuuint32_t)bw, (cuuint32_t)bh, 1};
+        return encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(p),
+                           dims, str, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           bc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                    : (bc == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_32B),
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap mg, mx32, mx16, mu32, mu16;
+    std::memset(&mg, 0, sizeof(mg));
+    if (!encode(&mg, w.g, w.Co, w.W, w.H, 16, a.Wt, a.TR)) return cudaErrorInvalidValue;
+    bool need[2][2] = {{false, false}, {false, false}};  // [in2][16-channel]
+    for (int k = 0; k < nchunks; ++k) need[a.ck_up[k]][a.ck_kc[k] == 16] = true;
+    mx32 = mx16 = mu32 = mu16 = mg;  // placeholders for the boxes no chunk uses
+    if (need[0][0] && !encode(&mx32, w.in1, w.C1, w.W, w.H, 32, a.rs, a.TR + 2))
+        return cudaErrorInvalidValue;
+    if (need[0][1] && !encode(&mx16, w.in1, w.C1, w.W, w.H, 16, a.rs, a.TR + 2))
+        return cudaErrorInvalidValue;
+    if (need[1][0] &&
+        !encode(&mu32, w.in2, w.C2, w.W / 2, w.H / 2, 32, a.up_cols, a.up_rows))
+        return cudaErrorInvalidValue;
+    if (need[1][1] &&
+        !encode(&mu16, w.in2, w.C2, w.W / 2, w.H / 2, 16, a.up_cols, a.up_rows))
+        return cudaErrorInvalidValue;
     int smem = a.stages * a.stage_bytes + 1024;
     const int by_tmem = 512 / a.tmem_cols;
     smem = std::min(kTcSmemMax, std::max(smem, kTcSmemSM / (by_tmem + 1) - 1024 + 256));
     auto kern = w.C2 > 0 ? nn::conv3x3_wgrad_tc_kernel<true> : nn::conv3x3_wgrad_tc_kernel<false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx, mg, mu, a);
+    kern<<<dim3(a.sk, nchunks, ntn), nn::kTcThreads, smem, s>>>(mx32, mx16, mu32, mu16, mg, a);
     return cudaGetLastError();
 }
 

@@ -70,7 +70,7 @@ cudaError_t tc_tile_weights(const void* w, int Co, int Ci, void* wt, cudaStream_
 cudaError_t tc_conv3x3(const nn::ConvArgs& c, const void* wt, unsigned* err, cudaStream_t s);
 // The weight gradient on tcgen05 (conv_tc.cu): whether a layer's shape is
 // supported (W from 16 up to 128 in multiples of 16, or a multiple of 128;
-// channels multiples of 16, C1 a multiple of the chunk width), and the
+// channels multiples of 16, at most 384 input channels), and the
 // gradient itself (w.dw and w.db accumulated; err as for the convolution).
 bool tc_wgrad_supported(int H, int W, int C1, int C2, int Co);
 cudaError_t tc_conv3x3_wgrad(const nn::WgradArgs& w, unsigned* err, cudaStream_t s);

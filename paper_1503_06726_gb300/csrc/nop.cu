@@ -239,12 +239,9 @@ cudaError_t conv_wgrad(lbib_nop* n, const Layer& l, const bf16* in1, const bf16*
     a.C1 = C1;
     a.C2 = C2;
     a.Co = l.cop;
-    // the tcgen05 kernel where it measured faster (batch 16): every level from
-    // 64^2 up except the decoder's upsampled-input layers at 128^2 and 256^2,
-    // and the 32^2 layers of 96 or more input channels
-    const int Ci = C1 + C2;
-    const bool tc = tc_wgrad_supported(a.H, a.W, C1, C2, a.Co) &&
-                    ((a.W >= 64 && !(C2 > 0 && a.W >= 128)) || (a.W == 32 && Ci >= 96));
+    // the tcgen05 kernel wherever it measured faster (batch 16): every level
+    // it supports (W >= 16) except the plain 16^2 layers
+    const bool tc = tc_wgrad_supported(a.H, a.W, C1, C2, a.Co) && (a.W >= 32 || C2 > 0);
     if (tc) return tc_conv3x3_wgrad(a, n->tc_err, n->stream);
     const int tiles = ((a.H + kTH - 1) / kTH) * ((a.W + kTW - 1) / kTW) * N;
     a.tiles_per_cta = tiles > 4096 ? 32 : (tiles > 512 ? 8 : 1);

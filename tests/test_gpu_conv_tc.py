@@ -160,12 +160,15 @@ def test_tc_conv_shape_support(lb):
     (2, 8, 16, 16, 32, 48),     # 16-channel chunks (eight shifts per M), upsampled input
     (1, 5, 128, 64, 0, 64),     # rows of 128, two chunks, a row tile overhanging the image
     (1, 4, 256, 32, 32, 192),   # two tiles per row, two N tiles of 96, upsampled 32-channel chunk
-    (4, 64, 64, 48, 0, 16),     # the smallest N tile (four accumulator sets), 48 channels
+    (4, 64, 64, 48, 0, 16),     # the smallest N tile (four accumulator sets), 32 + 16 channels
+    (1, 4, 256, 32, 48, 32),    # upsampled 48 channels: a 32- and a 16-channel chunk
+    (2, 8, 32, 16, 16, 32),     # 16-channel chunks of both inputs
 ])
 def test_tc_wgrad_matches_oracle_and_mma_sync(lb, orc, N, H, W, C1, C2, Co):
     """The weight gradient on tcgen05 (MN-major operands, the input channels of
-    three tap shifts as M) against the FP64 oracle and the warp-level kernel:
-    BF16-exact inputs, FP32 accumulation in a different order."""
+    three tap shifts as M; 32-channel chunks where an input has them, 16 for a
+    remainder) against the FP64 oracle and the warp-level kernel: BF16-exact
+    inputs, FP32 accumulation in a different order."""
     import torch
     from oracle import nn as onn
     L = lb.load()
@@ -205,5 +208,6 @@ def test_tc_wgrad_shape_support(lb):
     assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 8, 32, 0, 32) == 0     # W below 16
     assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 40, 32, 0, 32) == 0    # W not a multiple of 16
     assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 32, 32, 0, 40) == 0    # Co not a multiple of 16
-    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 32, 16, 16, 32) == 0   # 32-channel chunks, C1 = 16
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 32, 16, 0, 32) == 1    # one 16-channel chunk
+    assert L.lbib_nn_conv3x3_wgrad_tc_supported(8, 32, 16, 16, 32) == 1   # a 16-channel chunk of each input
     assert L.lbib_nn_conv3x3_wgrad_tc_supported(256, 256, 16, 0, 32) == 1
