@@ -276,8 +276,10 @@ def oracle_sample(w, target_s: float, max_steps: int, threads: int | None = None
 
 # ------------------------------------------------------------------ arms
 def run_ensemble(args, rank, world, dist):
-    """64 independent tissues of uneven sizes advanced by one persistent
-    cooperative launch per step call (replayed from a CUDA graph)."""
+    """64 independent tissues of uneven sizes advanced together, by one
+    persistent cooperative launch per step call or by the split schedule of
+    two launches per step (either replayed from a CUDA graph; the autotuner
+    picks the schedule unless --ens-schedule names one)."""
     import torch
     from paper_1503_06726_gb300 import lbib
 
@@ -288,6 +290,12 @@ def run_ensemble(args, rank, world, dist):
     N = sum(w.params.nx * w.params.ny for w in ws)
     ens = lbib.Ensemble([w.params for w in ws], [w.tissue for w in ws], device=dev)
     tune = ens.tune_cached(f"c4-{len(ws)}-{N}", trial_steps=10)
+    forced = {"persistent": lbib.LBIB_ENS_PERSISTENT, "split": lbib.LBIB_ENS_SPLIT,
+              "split_wide": lbib.LBIB_ENS_SPLIT_WIDE}.get(args.ens_schedule)
+    if forced is not None:
+        ens.schedule(forced)
+    sched = ens.schedule()
+    split = sched != lbib.LBIB_ENS_PERSISTENT
     warmup = max(args.warmup, 4)
     ens.step(warmup)
     ens.status()
@@ -357,16 +365,25 @@ def run_ensemble(args, rank, world, dist):
                    "sides": [w.params.nx for w in ws], "cells": cells,
                    "storage": "fp32", "vertex_precision": "fp64",
                    "l2": f"inputs larger than L2: {2 * bpn * N / 2**20:.0f} MiB of populations",
-                   "launch": "one persistent cooperative kernel per step call",
-                   "graph": info["graph"], "grid": info["grid"], "tuned": tune},
+                   "launch": ("split schedule: one lattice launch over every tissue and one IB "
+                              "launch over every cell per step, programmatic, one graph per "
+                              "step call" + (" (wide lattice kernel)"
+                                             if sched == lbib.LBIB_ENS_SPLIT_WIDE else "")
+                              if split else "one persistent cooperative kernel per step call"),
+                   "schedule": {0: "persistent", 1: "split", 2: "split_wide"}[sched],
+                   "graph": info["graph"], "grid": None if split else info["grid"],
+                   "tuned": tune},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (lambda t: t * args.steps if t is not None else None)(
-                         recorded_traffic("c4-per-step", "dram_bytes_per_step",
-                                          ensemble_kernel_hash())),
-                     "kernel": "ensemble_kernel (whole persistent launch: lattice + IB phases)",
+                         recorded_traffic("c4-split-per-step" if split else "c4-per-step",
+                                          "dram_bytes_per_step", ensemble_kernel_hash())),
+                     "kernel": ("ens_lattice_kernel + ens_ib_kernel (whole steps: every launch "
+                                "of the step call)" if split else
+                                "ensemble_kernel (whole persistent launch: lattice + IB phases)"),
                      "alg_bytes_per_node": bpn, "peak_kind": f"{peak_kind} hbm_gbs (copy)"},
-        "e2e": e2e, "gpu_launches": 1, "clocks": clk, "cpu_baseline": None,
+        "e2e": e2e, "gpu_launches": 2 * args.steps + 1 if split else 1, "clocks": clk,
+        "cpu_baseline": None,
     }
 
 
@@ -951,6 +968,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="c3-fp32")
     ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--ens-schedule", default="tuned",
+                    choices=["tuned", "persistent", "split", "split_wide"],
+                    help="c4: the ensemble's schedule (tuned: the autotuner's choice)")
     ap.add_argument("--c3-n", type=int, default=4096,
                     help="side of the c3 tissue (4096: the configuration; smaller for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -383,7 +383,12 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
  * An ensemble holds n tissues (each with its own lbib_params -- lattice
  * size, tau, boundary -- and its own cells) in one caller-owned workspace and
  * advances all of them by one persistent cooperative kernel launch per
- * lbib_ensemble_step() call, captured once per step count into a CUDA graph.
+ * lbib_ensemble_step() call (LBIB_ENS_PERSISTENT: lattice and IB phases
+ * separated by grid barriers), or by two launches per step (LBIB_ENS_SPLIT:
+ * one lattice launch over every node of every tissue, one IB launch over every
+ * cell, ordered by programmatic dependent launches; LBIB_ENS_SPLIT_WIDE: the
+ * same with more registers and fewer CTAs per SM for the lattice launch),
+ * captured once per step count into a CUDA graph.
  * All tissues use LBIB_FP32 storage and share n_species and forcing.  Each
  * tissue is a context: lbib_ensemble_tissue() returns it for
  * lbib_set_cells(), lbib_get_fields(), lbib_get_state() and the like (do not
@@ -404,11 +409,20 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
  *                                 per SM (0 = as many as fit; < 0 keeps it);
  *                                 reports whether the graph path is in use
  *                                 and the grid size
+ *   lbib_ensemble_schedule        set the schedule (LBIB_ENS_PERSISTENT,
+ *                                 LBIB_ENS_SPLIT or LBIB_ENS_SPLIT_WIDE; < 0
+ *                                 keeps it); schedule_out
+ *                                 (may be NULL) receives the one in use;
+ *                                 LBIB_E_PARAM for another value
  *   lbib_ensemble_tune            time every (nodes_per_item in 256/512/1024/2048/4096)
- *                                 x (CTAs per SM) candidate over trial_steps
- *                                 steps (which advances the tissues), keep the
- *                                 fastest; config_out[2] = {nodes_per_item,
- *                                 CTAs per SM}, ms_out = ms per step
+ *                                 x (the two split schedules, and the persistent
+ *                                 kernel at each CTAs per SM) candidate over
+ *                                 trial_steps steps (which advances the
+ *                                 tissues), keep the fastest;
+ *                                 config_out[2] = {nodes_per_item, the
+ *                                 persistent kernel's best CTAs per SM},
+ *                                 ms_out = ms per step; the schedule chosen
+ *                                 is read with lbib_ensemble_schedule()
  *   lbib_ensemble_selftest_timeout  run one grid barrier that cannot
  *                                 complete, to check that the bounded wait
  *                                 ends (seconds_out) and is reported as
@@ -416,6 +430,9 @@ int lbib_steady_solve(int32_t nx, int32_t ny, int32_t batch, const uint8_t* d_sr
  * The paper runs one tissue per process (Sec. 3.4); the ensemble is the
  * parameter-sweep form of the same step. */
 typedef struct lbib_ensemble lbib_ensemble;
+#define LBIB_ENS_PERSISTENT 0
+#define LBIB_ENS_SPLIT 1
+#define LBIB_ENS_SPLIT_WIDE 2
 int lbib_ensemble_workspace_size(int32_t n, const lbib_params* params,
                                  const int32_t* max_vertices, const int32_t* max_cells,
                                  uint64_t* bytes_out);
@@ -427,6 +444,7 @@ int lbib_ensemble_step(lbib_ensemble* ens, int32_t n_steps);
 int lbib_ensemble_status(lbib_ensemble* ens);
 int lbib_ensemble_config(lbib_ensemble* ens, int32_t nodes_per_item, int32_t blocks_per_sm,
                          int32_t* graph_out, int32_t* grid_out);
+int lbib_ensemble_schedule(lbib_ensemble* ens, int32_t schedule, int32_t* schedule_out);
 int lbib_ensemble_tune(lbib_ensemble* ens, int32_t trial_steps, int32_t* config_out,
                        double* ms_out);
 int lbib_ensemble_selftest_timeout(lbib_ensemble* ens, double* seconds_out);

@@ -11,8 +11,19 @@
 // nodes (rows padded to 32 so a warp stays in one row) and one item per cell
 // -- strided over the persistent CTAs, which balances tissues of very
 // different sizes.  The launch is captured once per step count into a CUDA
-// graph and replayed.  The two launch parameters (nodes per item and CTAs per
-// SM) are chosen by lbib_ensemble_tune(), which times the candidates.
+// graph and replayed.
+//
+// The split schedule runs the same items as two kernels per step instead --
+// one lattice launch over every lattice item of every tissue (128-thread
+// CTAs held to the standalone lattice kernel's registers, so an SM keeps
+// twice the warps, and loads, of the persistent kernel in flight) and one IB
+// launch over every cell -- ordered by programmatic dependent launches in
+// place of the grid barriers: each kernel issues its loads of what the launch
+// two back wrote before it waits on the launch just before, as the
+// single-tissue steps do.  All 2n + 1 launches of n steps are one graph.
+// The schedule and the two launch parameters (nodes per item, and CTAs per SM
+// of the persistent kernel) are chosen by lbib_ensemble_tune(), which times
+// the candidates.
 //
 // The grid barrier spins on a generation word with a bounded wait (a
 // globaltimer limit of about one second): if a barrier cannot complete, the
@@ -27,7 +38,7 @@
 #include <vector>
 
 #include "ib_cell.cuh"
-#include "lattice_node.cuh"
+#include "lattice_kernel.cuh"
 #include "lbib_ctx.cuh"
 
 namespace lbib {
@@ -41,6 +52,9 @@ struct TissueDev {
     int cur;           // buffer parity at the start of the launch
     int pad;
 };
+
+static_assert(sizeof(TissueDev) % 4 == 0 && sizeof(IBArgs) % 4 == 0,
+              "the tables are copied to shared memory in 4-byte words");
 
 struct EnsArgs {
     const TissueDev* tis;
@@ -207,6 +221,93 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
     }
 }
 
+// The split schedule's lattice launch: one CTA per lattice item (nodes_per_item
+// nodes of one tissue), the update of lbib_step's lattice kernel with its
+// programmatic wait on the IB launch before it.  WIDE: two CTAs per SM fewer
+// than the standalone kernel, for registers enough not to spill (at the
+// standalone kernel's 40 registers with one species the update spills about
+// 120 bytes: the tissue's arguments are read from shared memory, not from the
+// constant bank).
+template <int S, int FORCING, bool WIDE>
+__global__ void __launch_bounds__(kLatticeThreads,
+                                  LatticeOccupancy<float, S>::kMinBlocks - (WIDE ? 2 : 0))
+    ens_lattice_kernel(EnsArgs e, int step, int out) {
+    // the tissue's arguments in shared memory, read from there at each use
+    // (held in registers they would spill at the standalone kernel's budget)
+    __shared__ TissueDev td;
+    const int item = blockIdx.x;
+    const int t = find_tissue(e.item_pfx, e.n, item);
+    {
+        const int* src = reinterpret_cast<const int*>(e.tis + t);
+        int* dst = reinterpret_cast<int*>(&td);
+        for (int i = threadIdx.x; i < (int)(sizeof(TissueDev) / 4); i += kLatticeThreads)
+            dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if ((td.cur + step) & 1) {
+            const void* f0 = td.la.fsrc;
+            td.la.fsrc = td.la.fdst;
+            td.la.fdst = const_cast<void*>(f0);
+            const void* g0 = td.la.gsrc;
+            td.la.gsrc = td.la.gdst;
+            td.la.gdst = const_cast<void*>(g0);
+        }
+        td.la.out = out;
+    }
+    __syncthreads();
+    // node indices below 2^31 + nodes_per_item: unsigned 32-bit
+    const unsigned nxr = (unsigned)td.nxr;
+    const unsigned v0 = (unsigned)(item - e.item_pfx[t]) * (unsigned)e.nodes_per_item;
+    for (int v = threadIdx.x; v < e.nodes_per_item; v += kLatticeThreads) {
+        const unsigned vv = v0 + (unsigned)v;
+        const unsigned yu = vv / nxr, xu = vv - yu * nxr;
+        if (yu >= (unsigned)td.la.ny || xu >= (unsigned)td.la.nx) continue;
+        const int x = (int)xu, y = (int)yu;
+        if (td.bc_y)
+            lattice_node<float, float, S, true, FORCING, false, true>(td.la, td.k, x, y);
+        else
+            lattice_node<float, float, S, false, FORCING, false, true>(td.la, td.k, x, y);
+    }
+}
+
+// The split schedule's IB launch: one CTA of NT threads per cell of every
+// tissue (move and/or prep as lbib_step's IB launch, with its programmatic
+// wait on the lattice launch before it).
+template <int NT>
+__global__ void __launch_bounds__(NT) ens_ib_kernel(EnsArgs e, int move, int prep, int vforce) {
+    extern __shared__ __align__(16) unsigned char ens_ib_smem[];
+    IBShared32 view;
+    int* fixed = reinterpret_cast<int*>(ens_ib_smem);
+    view.rowcnt = fixed;
+    view.thr = fixed + kMaxRows;
+    view.sbox = view.thr + kMaxRows * kMaxCross;
+    view.s_flag = view.sbox + 4;
+    view.sx = reinterpret_cast<double2*>(ens_ib_smem + kIBSmemFixed);
+    view.sb = reinterpret_cast<int2*>(view.sx + e.maxv);
+    view.sf = reinterpret_cast<float2*>(view.sb + e.maxv);
+    view.maxv = e.maxv;
+    // the tissue's arguments in shared memory (a local copy would live on
+    // the stack)
+    __shared__ IBArgs ia;
+    const int item = blockIdx.x;
+    const int t = find_tissue(e.cell_pfx, e.n, item);
+    {
+        const int* src = reinterpret_cast<const int*>(&e.tis[t].ia);
+        int* dst = reinterpret_cast<int*>(&ia);
+        for (int i = threadIdx.x; i < (int)(sizeof(IBArgs) / 4); i += NT) dst[i] = __ldg(src + i);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ia.do_move = move;
+        ia.do_prep = prep;
+        ia.write_vforce = vforce;
+        ia.do_ids = vforce;
+    }
+    __syncthreads();
+    ib_cell_f32<NT, true, false, false>(ia, item - e.cell_pfx[t], view, threadIdx.x, 0);
+}
+
 // A barrier that cannot complete (it waits for one CTA more than the grid
 // has): used by lbib_ensemble_selftest_timeout() to exercise the bounded wait.
 __global__ void barrier_timeout_kernel(unsigned* bar, unsigned nblocks) {
@@ -230,6 +331,28 @@ static EnsKernel pick_kernel(int S, int forcing) {
     }
 }
 
+typedef void (*EnsLatticeKernel)(EnsArgs, int, int);
+
+template <bool WIDE>
+static EnsLatticeKernel pick_lattice_kernel_w(int S, int forcing) {
+    switch (S * 2 + (forcing ? 1 : 0)) {
+        case 0: return ens_lattice_kernel<0, 0, WIDE>;
+        case 1: return ens_lattice_kernel<0, 1, WIDE>;
+        case 2: return ens_lattice_kernel<1, 0, WIDE>;
+        case 3: return ens_lattice_kernel<1, 1, WIDE>;
+        case 4: return ens_lattice_kernel<2, 0, WIDE>;
+        case 5: return ens_lattice_kernel<2, 1, WIDE>;
+        case 6: return ens_lattice_kernel<3, 0, WIDE>;
+        case 7: return ens_lattice_kernel<3, 1, WIDE>;
+        case 8: return ens_lattice_kernel<4, 0, WIDE>;
+        default: return ens_lattice_kernel<4, 1, WIDE>;
+    }
+}
+
+static EnsLatticeKernel pick_lattice_kernel(int S, int forcing, bool wide) {
+    return wide ? pick_lattice_kernel_w<true>(S, forcing) : pick_lattice_kernel_w<false>(S, forcing);
+}
+
 static uint64_t up256(uint64_t v) { return (v + 255) / 256 * 256; }
 
 }  // namespace lbib
@@ -250,6 +373,7 @@ struct lbib_ensemble {
     int max_blocks_per_sm = 0;
     int n_sms = 0;
     int maxv = 0;           // vertex slots per cell in shared memory (largest cell)
+    int schedule = LBIB_ENS_PERSISTENT;
     std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;
     bool graph_ok = true;
     std::string err;
@@ -291,6 +415,16 @@ static cudaError_t ens_fit_cells(lbib_ensemble* e) {
         er = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kIBThreads, smem);
     if (er != cudaSuccess) return er;
     if (per < 1) return cudaErrorInvalidConfiguration;
+    // the split schedule's IB kernel: one cell slot per CTA
+    const size_t smem1 = ens_cell_smem(mv);
+    if (smem1 > 48 * 1024) {
+        er = ens_cell_threads(mv) == 64
+                 ? cudaFuncSetAttribute((const void*)ens_ib_kernel<64>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1)
+                 : cudaFuncSetAttribute((const void*)ens_ib_kernel<128>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+        if (er != cudaSuccess) return er;
+    }
     ens_drop_graphs(e);
     e->maxv = mv;
     e->max_blocks_per_sm = per;
@@ -376,6 +510,39 @@ static cudaError_t ens_launch(lbib_ensemble* e, const EnsArgs& a, unsigned grid,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, pick_kernel(e->S, e->forcing), a);
+}
+
+// The split schedule of n steps: the prep, then per step the lattice launch
+// and the IB launch (move, and the prep of the next step but after the last).
+// Every launch after the first is programmatic; without cells the lattice
+// launches follow one another and wait for each other in full.
+static cudaError_t ens_split_enqueue(lbib_ensemble* e, const EnsArgs& a, cudaStream_t st) {
+    const size_t smem = ens_cell_smem(a.maxv);
+    auto ib = [&](int move, int prep, int vforce, bool pdl) -> cudaError_t {
+        if (a.total_cells == 0) return cudaSuccess;
+        if (a.cell_threads == 64)
+            return launch_kernel(ens_ib_kernel<64>, dim3(a.total_cells), dim3(64), smem, st, pdl,
+                                 a, move, prep, vforce);
+        return launch_kernel(ens_ib_kernel<128>, dim3(a.total_cells), dim3(128), smem, st, pdl, a,
+                             move, prep, vforce);
+    };
+    const EnsLatticeKernel lk =
+        pick_lattice_kernel(e->S, e->forcing, e->schedule == LBIB_ENS_SPLIT_WIDE);
+    const bool pdl = a.total_cells > 0;
+    cudaError_t er = ib(0, 1, a.n_steps == 1, false);
+    for (int s = 0; s < a.n_steps && er == cudaSuccess; ++s) {
+        const bool last = (s == a.n_steps - 1);
+        er = launch_kernel(lk, dim3(a.total_items), dim3(kLatticeThreads), 0, st, pdl, a, s,
+                           last ? 1 : 0);
+        if (er == cudaSuccess) er = ib(1, last ? 0 : 1, s == a.n_steps - 2, true);
+    }
+    return er;
+}
+
+static cudaError_t ens_enqueue(lbib_ensemble* e, const EnsArgs& a, unsigned grid,
+                               cudaStream_t st) {
+    return e->schedule == LBIB_ENS_PERSISTENT ? ens_launch(e, a, grid, st)
+                                              : ens_split_enqueue(e, a, st);
 }
 
 extern "C" {
@@ -492,7 +659,7 @@ int lbib_ensemble_step(lbib_ensemble* e, int32_t n_steps) {
         cudaGraph_t g = nullptr;
         if (er == cudaSuccess) er = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (er == cudaSuccess) {
-            cudaError_t e2 = ens_launch(e, a, grid, cap);
+            cudaError_t e2 = ens_enqueue(e, a, grid, cap);
             er = cudaStreamEndCapture(cap, &g);
             if (e2 != cudaSuccess) er = e2;
         }
@@ -504,14 +671,14 @@ int lbib_ensemble_step(lbib_ensemble* e, int32_t n_steps) {
             it = e->graphs.emplace(key, ex).first;
         } else {
             cudaGetLastError();
-            e->graph_ok = false;  // fall back to direct cooperative launches
+            e->graph_ok = false;  // fall back to direct launches
         }
     }
     if (e->graph_ok && it != e->graphs.end()) {
         er = cudaGraphLaunch(it->second, e->stream);
         launched = true;
     }
-    if (!launched) er = ens_launch(e, a, grid, e->stream);
+    if (!launched) er = ens_enqueue(e, a, grid, e->stream);
     if (er != cudaSuccess)
         return ens_fail(e, LBIB_E_CUDA, std::string("lbib_ensemble_step: ") + cudaGetErrorString(er));
     for (auto* c : e->ctx) {
@@ -557,19 +724,39 @@ int lbib_ensemble_config(lbib_ensemble* e, int32_t nodes_per_item, int32_t block
     return LBIB_OK;
 }
 
+int lbib_ensemble_schedule(lbib_ensemble* e, int32_t schedule, int32_t* schedule_out) {
+    if (!e) return LBIB_E_PARAM;
+    if (schedule >= 0) {
+        if (schedule != LBIB_ENS_PERSISTENT && schedule != LBIB_ENS_SPLIT &&
+            schedule != LBIB_ENS_SPLIT_WIDE)
+            return ens_fail(e, LBIB_E_PARAM,
+                            "schedule must be LBIB_ENS_PERSISTENT, LBIB_ENS_SPLIT or "
+                            "LBIB_ENS_SPLIT_WIDE");
+        if (schedule != e->schedule) ens_drop_graphs(e);
+        e->schedule = schedule;
+    }
+    if (schedule_out) *schedule_out = e->schedule;
+    return LBIB_OK;
+}
+
 int lbib_ensemble_tune(lbib_ensemble* e, int32_t trial_steps, int32_t* config_out,
                        double* ms_out) {
     if (!e || trial_steps < 1 || !config_out) return LBIB_E_PARAM;
     const int npis[5] = {256, 512, 1024, 2048, 4096};
     double best = 1e300;
-    int best_npi = e->nodes_per_item, best_bps = e->blocks_per_sm;
+    int best_npi = e->nodes_per_item, best_bps = e->blocks_per_sm, best_sched = e->schedule;
+    double best_p = 1e300;  // the persistent kernel's best, whose CTAs per SM are kept
     cudaEvent_t t0, t1;
     cudaEventCreate(&t0);
     cudaEventCreate(&t1);
     for (int npi : npis) {
-        for (int bps = 1; bps <= e->max_blocks_per_sm; ++bps) {
+        // bps 1..max: the persistent kernel; bps -1 and 0: the split
+        // schedule (-1 its wide lattice kernel)
+        for (int bps = -1; bps <= e->max_blocks_per_sm; ++bps) {
             e->nodes_per_item = npi;
-            e->blocks_per_sm = bps;
+            e->schedule = bps > 0 ? LBIB_ENS_PERSISTENT
+                                  : (bps == 0 ? LBIB_ENS_SPLIT : LBIB_ENS_SPLIT_WIDE);
+            e->blocks_per_sm = bps > 0 ? bps : 1;
             int items = 0, cells = 0;
             cudaError_t er = ens_upload(e, &items, &cells);
             const unsigned grid = ens_grid(e);
@@ -577,7 +764,7 @@ int lbib_ensemble_tune(lbib_ensemble* e, int32_t trial_steps, int32_t* config_ou
             float ms = 0.f, msb = 1e30f;
             for (int rep = 0; rep < 2 && er == cudaSuccess; ++rep) {
                 er = cudaEventRecord(t0, e->stream);
-                if (er == cudaSuccess) er = ens_launch(e, a, grid, e->stream);
+                if (er == cudaSuccess) er = ens_enqueue(e, a, grid, e->stream);
                 if (er == cudaSuccess) er = cudaEventRecord(t1, e->stream);
                 if (er == cudaSuccess) er = cudaEventSynchronize(t1);
                 if (er == cudaSuccess) er = cudaEventElapsedTime(&ms, t0, t1);
@@ -599,6 +786,10 @@ int lbib_ensemble_tune(lbib_ensemble* e, int32_t trial_steps, int32_t* config_ou
             if (msb < best) {
                 best = msb;
                 best_npi = npi;
+                best_sched = e->schedule;
+            }
+            if (bps > 0 && msb < best_p) {
+                best_p = msb;
                 best_bps = bps;
             }
         }
@@ -612,6 +803,7 @@ int lbib_ensemble_tune(lbib_ensemble* e, int32_t trial_steps, int32_t* config_ou
     ens_drop_graphs(e);
     e->nodes_per_item = best_npi;
     e->blocks_per_sm = best_bps;
+    e->schedule = best_sched;
     config_out[0] = best_npi;
     config_out[1] = best_bps;
     if (ms_out) *ms_out = best / trial_steps;

@@ -539,10 +539,14 @@ __device__ __forceinline__ void collide_node(const Coefs<typename Lane<V>::S>& k
     }
 }
 
-template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED>
-__device__ __forceinline__ void lattice_node(const LatticeArgs a, const Coefs<C> k, int x,
+// WAIT: the caller is a kernel of its own, launched programmatically after an
+// IB launch (the ensemble's split schedule), with the population loads issued
+// before the wait as in the standalone kernel; without it the caller orders
+// the phases itself (the persistent kernel's grid barriers).
+template <typename T, typename C, int S, bool WALLS, int FORCING, bool SCALED, bool WAIT = false>
+__device__ __forceinline__ void lattice_node(const LatticeArgs& a, const Coefs<C>& k, int x,
                                              int y) {
-    constexpr bool GRIDDEP = false;
+    constexpr bool GRIDDEP = WAIT;
     // the ensemble's tissues confine no species and have no mass sources,
     // node sources or pressure nodes
     constexpr bool CONF = false;

@@ -37,6 +37,7 @@ LBIB_FP64, LBIB_FP32, LBIB_FP16 = 0, 1, 2
 LBIB_GUO, LBIB_HE_PAPER = 0, 1
 LBIB_REACT_LINEAR, LBIB_REACT_SCHNAKENBERG = 0, 1
 LBIB_NOFLUX_CLOSURE, LBIB_NOFLUX_BOUNCEBACK = 0, 1
+LBIB_ENS_PERSISTENT, LBIB_ENS_SPLIT, LBIB_ENS_SPLIT_WIDE = 0, 1, 2
 LBIB_RHO, LBIB_U, LBIB_PHI, LBIB_X = 1, 2, 4, 8
 LBIB_AREA, LBIB_ID, LBIB_FORCE, LBIB_VFORCE = 16, 32, 64, 128
 
@@ -52,7 +53,8 @@ EXPORTS = (
     "lbib_get_state", "lbib_set_state", "lbib_step_noalloc", "lbib_destroy", "lbib_last_error",
     "lbib_status_string", "lbib_label_cells", "lbib_steady_workspace_size", "lbib_steady_solve",
     "lbib_ensemble_workspace_size", "lbib_ensemble_create", "lbib_ensemble_tissue",
-    "lbib_ensemble_step", "lbib_ensemble_status", "lbib_ensemble_config", "lbib_ensemble_tune",
+    "lbib_ensemble_step", "lbib_ensemble_status", "lbib_ensemble_config",
+    "lbib_ensemble_schedule", "lbib_ensemble_tune",
     "lbib_ensemble_selftest_timeout", "lbib_ensemble_destroy", "lbib_ensemble_last_error",
     "lbib_nop_workspace_size", "lbib_nop_create", "lbib_nop_num_params", "lbib_nop_layers",
     "lbib_nop_set_params", "lbib_nop_get_params", "lbib_nop_get_grads", "lbib_nop_forward",
@@ -140,6 +142,7 @@ def load(path: str = None) -> ctypes.CDLL:
         "lbib_ensemble_step": (ctypes.c_int, [vp, i32]),
         "lbib_ensemble_status": (ctypes.c_int, [vp]),
         "lbib_ensemble_config": (ctypes.c_int, [vp, i32, i32, vp, vp]),
+        "lbib_ensemble_schedule": (ctypes.c_int, [vp, i32, vp]),
         "lbib_ensemble_tune": (ctypes.c_int, [vp, i32, vp, vp]),
         "lbib_ensemble_selftest_timeout": (ctypes.c_int, [vp, vp]),
         "lbib_ensemble_destroy": (None, [vp]),
@@ -572,8 +575,9 @@ def _ens_check(rc, ens):
 
 class Ensemble:
     """Many independent FP32 tissues advanced by one persistent launch per
-    step call.  ``params`` is a list of parameter objects; ``tissues`` the
-    matching list of tissues (lbib_inputs.Tissue-like)."""
+    step call, or by two launches per step (the split schedules).  ``params``
+    is a list of parameter objects; ``tissues`` the matching list of tissues
+    (lbib_inputs.Tissue-like; None for a tissue without cells)."""
 
     def __init__(self, params, tissues, device=None, stream=None):
         import torch
@@ -587,8 +591,8 @@ class Ensemble:
         arr = (lbib_params * n)(*[make_params(p, LBIB_FP32) for p in params])
         self._params = arr
         self.dims = [(int(p.nx), int(p.ny), int(p.n_species)) for p in params]
-        mv = np.array([t.n_vertices for t in tissues], np.int32)
-        mc = np.array([t.n_cells for t in tissues], np.int32)
+        mv = np.array([t.n_vertices if t is not None else 0 for t in tissues], np.int32)
+        mc = np.array([t.n_cells if t is not None else 0 for t in tissues], np.int32)
         nb = ctypes.c_uint64(0)
         vp = ctypes.c_void_p
         _ens_check(L.lbib_ensemble_workspace_size(n, arr, mv.ctypes.data_as(vp),
@@ -621,6 +625,14 @@ class Ensemble:
                                                ctypes.byref(g), ctypes.byref(gr)), self.ens)
         return {"graph": bool(g.value), "grid": int(gr.value)}
 
+    def schedule(self, schedule: int = -1) -> int:
+        """Set the schedule (LBIB_ENS_PERSISTENT / LBIB_ENS_SPLIT /
+        LBIB_ENS_SPLIT_WIDE; < 0 keeps it); returns the one in use."""
+        out = ctypes.c_int32(0)
+        _ens_check(load().lbib_ensemble_schedule(self.ens, int(schedule), ctypes.byref(out)),
+                   self.ens)
+        return int(out.value)
+
     def tune(self, trial_steps: int = 20):
         cfg = np.zeros(2, np.int32)
         ms = ctypes.c_double(0.0)
@@ -628,7 +640,7 @@ class Ensemble:
                                              cfg.ctypes.data_as(ctypes.c_void_p),
                                              ctypes.byref(ms)), self.ens)
         return {"nodes_per_item": int(cfg[0]), "blocks_per_sm": int(cfg[1]),
-                "ms_per_step": float(ms.value)}
+                "schedule": self.schedule(), "ms_per_step": float(ms.value)}
 
     def tune_cached(self, key: str, trial_steps: int = 20, path: Optional[str] = None):
         """Autotune once per ``key`` and keep the choice in a JSON cache
@@ -646,6 +658,7 @@ class Ensemble:
         if key in cache:
             c = cache[key]
             self.config(c["nodes_per_item"], c["blocks_per_sm"])
+            self.schedule(c.get("schedule", LBIB_ENS_PERSISTENT))
             return dict(c, cached=True)
         c = self.tune(trial_steps)
         cache[key] = c

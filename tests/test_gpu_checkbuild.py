@@ -4,7 +4,7 @@ making it, skip an access that fails, and the host reports LBIB_E_CHECK.
 
   - the coupled step (FP64, FP32, FP16 with two nodes per thread; walls;
     junctions; mass sources and pressure nodes), confined species under the
-    no-flux closure, the ensemble, the allocation-free step and the sums run
+    no-flux closure, the ensemble (both schedules), the allocation-free step and the sums run
     in the checking build without a single failed check;
   - a cell whose offsets claim more vertices than the arrays hold (the
     allocation-free step reads offsets only on the device) is caught by the
@@ -92,6 +92,9 @@ def test_check_build_hot_path_clean():
         ws = li.config4(seed=44, n_tissues=3, n_steps=4, side_min=96, side_max=160)
         ens = lbib.Ensemble([w.params for w in ws], [w.tissue for w in ws])
         ens.step(4)
+        ens.status()
+        ens.schedule(lbib.LBIB_ENS_SPLIT)
+        ens.step(3)
         ens.status()
         for i in range(len(ws)):
             ens.fields(i)

@@ -1,6 +1,7 @@
 """The ensemble (many tissues, one persistent cooperative launch per step
-call) against the same tissues run one by one through lbib_step, and one
-tissue against the FP64 oracle.
+call, or the split schedule of two launches per step) against the same
+tissues run one by one through lbib_step, and one tissue against the FP64
+oracle, under each schedule.
 
 Tolerances: ensemble vs single-tissue runs, both FP32 with the same kernels
 and only the atomic order of the spreading differing: relative L-infinity
@@ -41,10 +42,20 @@ def small_ensemble():
     return ws + [w2]
 
 
-def test_ensemble_matches_single_tissues(lb):
+SCHEDULES = ("persistent", "split", "split_wide")
+
+
+def schedule_of(lb, name):
+    return {"persistent": lb.LBIB_ENS_PERSISTENT, "split": lb.LBIB_ENS_SPLIT,
+            "split_wide": lb.LBIB_ENS_SPLIT_WIDE}[name]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+def test_ensemble_matches_single_tissues(lb, sched):
     ws = small_ensemble()
     ens = lb.Ensemble([w.params for w in ws], [w.tissue for w in ws])
-    for n in (5, 4):   # an odd then an even call
+    assert ens.schedule(schedule_of(lb, sched)) == schedule_of(lb, sched)
+    for n in (5, 4, 1):   # an odd, an even and a one-step call
         ens.step(n)
     ens.status()
     for t, w in enumerate(ws):
@@ -52,6 +63,7 @@ def test_ensemble_matches_single_tissues(lb):
         sim.set_cells(w.tissue)
         sim.step(5)
         sim.step(4)
+        sim.step(1)
         a = ens.fields(t)
         b = sim.fields()
         assert max(rel(a["ux"], b["ux"]), rel(a["uy"], b["uy"])) < 1e-5, t
@@ -61,9 +73,11 @@ def test_ensemble_matches_single_tissues(lb):
     ens.close()
 
 
-def test_ensemble_tissue_matches_oracle(lb, orc):
+@pytest.mark.parametrize("sched", ("persistent", "split"))
+def test_ensemble_tissue_matches_oracle(lb, orc, sched):
     ws = small_ensemble()
     ens = lb.Ensemble([w.params for w in ws], [w.tissue for w in ws])
+    ens.schedule(schedule_of(lb, sched))
     ens.step(12)
     t = 1
     got = ens.fields(t)
@@ -78,10 +92,14 @@ def test_ensemble_autotune_and_graph(lb, tmp_path):
     ws = small_ensemble()
     ens = lb.Ensemble([w.params for w in ws], [w.tissue for w in ws])
     c = ens.tune_cached("test-small", trial_steps=3, path=str(tmp_path / "tune.json"))
-    assert c["nodes_per_item"] in (256, 512, 1024) and c["blocks_per_sm"] >= 1
+    assert c["nodes_per_item"] in (256, 512, 1024, 2048, 4096) and c["blocks_per_sm"] >= 1
+    assert c["schedule"] in (lb.LBIB_ENS_PERSISTENT, lb.LBIB_ENS_SPLIT, lb.LBIB_ENS_SPLIT_WIDE)
     assert c["cached"] is False
+    assert ens.schedule() == c["schedule"]
+    ens.schedule(lb.LBIB_ENS_PERSISTENT if c["schedule"] else lb.LBIB_ENS_SPLIT)
     c2 = ens.tune_cached("test-small", path=str(tmp_path / "tune.json"))
     assert c2["cached"] is True and c2["nodes_per_item"] == c["nodes_per_item"]
+    assert ens.schedule() == c["schedule"]
     ens.step(6)
     ens.step(6)
     ens.status()
@@ -100,4 +118,35 @@ def test_ensemble_bounded_barrier_reports_timeout(lb):
     assert 0.5 < sec < 10.0
     ens.step(3)
     ens.status()
+    ens.close()
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+def test_ensemble_without_cells(lb, sched):
+    """Tissues without cells: under the split schedule the lattice launches
+    follow one another (no IB launch between them) and are not programmatic."""
+    ws = small_ensemble()[:3]
+    ens = lb.Ensemble([w.params for w in ws], [None] * len(ws))
+    ens.schedule(schedule_of(lb, sched))
+    ens.step(3)
+    ens.step(2)
+    ens.status()
+    for t, w in enumerate(ws):
+        sim = lb.Simulation(w.params, lb.LBIB_FP32, 0, 0)
+        sim.step(3)
+        sim.step(2)
+        a = ens.fields(t)
+        b = sim.fields()
+        # no spreading: the same kernels in the same order give the same bits
+        assert np.array_equal(a["ux"], b["ux"]) and np.array_equal(a["phi"], b["phi"]), t
+        sim.close()
+    ens.close()
+
+
+def test_ensemble_schedule_rejects_unknown(lb):
+    ws = small_ensemble()[:1]
+    ens = lb.Ensemble([w.params for w in ws], [w.tissue for w in ws])
+    with pytest.raises(lb.LbibError):
+        ens.schedule(7)
+    assert ens.schedule() == lb.LBIB_ENS_PERSISTENT
     ens.close()
