@@ -796,6 +796,14 @@ def run_gb300(args, rank, world, dist):
     sim = lbib.Simulation(p, lbib.PRECISIONS[prec], T.n_vertices, T.n_cells, device=dev)
     sim.set_cells(T)
     prepare(sim, w)
+    # FP16 storage: nodes per lattice thread (the pair or the quad update
+    # where the width allows it)
+    npt = 1
+    if prec == "fp16":
+        sim.set_lattice_variant(args.fp16_npt)
+        npt = args.fp16_npt or (4 if p.n_species <= 1 else 2)
+        if p.nx % npt:
+            npt = 2 if p.nx % 2 == 0 else 1
     stream = sim.stream
     # warm-up: 4 + 5 steps capture and instantiate the two-step graphs of
     # both buffer parities (ordinary and final chunks) before the timed region
@@ -883,12 +891,13 @@ def run_gb300(args, rank, world, dist):
     warm = None
     if world == 1 and not args.no_warm_start:
         warm = warm_start_sample(args, dev)
-    traffic = recorded_traffic(args.workload)
+    traffic = recorded_traffic(args.workload + ("-quad" if npt == 4 else ""))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "dram_frac": (traffic / (lat_avg * 1e-3) / 1e9 / peak) if traffic else None,
-            "kernel": ("lattice_pair_kernel (two nodes per thread)"
-                       if prec == "fp16" and w.params.nx % 2 == 0 else "lattice_kernel"),
+            "kernel": {4: ("lattice_quad_async_kernel (four nodes per thread, staged)"
+                           if p.n_species <= 1 else "lattice_quad_kernel (four nodes per thread)"),
+                       2: "lattice_pair_kernel (two nodes per thread)"}.get(npt, "lattice_kernel"),
             "alg_bytes_per_launch": alg_bytes,
             "alg_bytes_per_node": bpn, "launch_ms": lat_avg,
             "peak_kind": f"{peak_kind} hbm_gbs (copy)",
@@ -971,6 +980,8 @@ def main():
     ap.add_argument("--ens-schedule", default="tuned",
                     choices=["tuned", "persistent", "split", "split_wide"],
                     help="c4: the ensemble's schedule (tuned: the autotuner's choice)")
+    ap.add_argument("--fp16-npt", type=int, default=0, choices=[0, 1, 2, 4],
+                    help="FP16 storage: lattice nodes per thread (0: the library's choice)")
     ap.add_argument("--c3-n", type=int, default=4096,
                     help="side of the c3 tissue (4096: the configuration; smaller for profiling)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

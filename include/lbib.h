@@ -242,13 +242,17 @@ int lbib_set_pressure_nodes(lbib_ctx* ctx, const uint8_t* mask);
 int lbib_set_node_sources(lbib_ctx* ctx, const double* S);
 
 /* Choose how many lattice nodes one thread of the lattice update handles.
- * 2 (the default) lets FP16 storage update two adjacent nodes per thread,
- * moving every population as one 32-bit word of two halves, whenever the
- * lattice width nx is even; 1 forces one node per thread.  FP32 and FP64
- * storage always use one node per thread.  Both give the same arithmetic
- * (the collision of Sec. 6.1, Eq. bgkequation, node by node); the setting
- * exists to compare and time the two.  LBIB_E_PARAM for other values.  Waits
- * for the context stream when the choice changes. */
+ * 2 lets FP16 storage update two adjacent nodes per thread, moving every
+ * population as one 32-bit word of two halves, whenever the lattice width nx
+ * is even; 4 updates four adjacent nodes per thread (one 64-bit word of four
+ * halves per population; with at most one species the words are staged in
+ * shared memory by asynchronous copies) when nx is a multiple of four, else
+ * two; 1 forces one node per thread; 0 (the default) is 4 with at most one
+ * species and 2 with more.  FP32 and FP64 storage always use
+ * one node per thread.  All give the same arithmetic (the collision of
+ * Sec. 6.1, Eq. bgkequation, node by node); the setting exists to compare and
+ * time them.  LBIB_E_PARAM for other values.  Waits for the context stream
+ * when the choice changes. */
 int lbib_set_lattice_variant(lbib_ctx* ctx, int32_t nodes_per_thread);
 
 /* Update the per-cell pressure and source flags of the current cells (the

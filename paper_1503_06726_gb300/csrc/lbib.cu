@@ -362,7 +362,7 @@ static cudaError_t enqueue_lattice(lbib_ctx* c, int src_buf, bool out, bool pdl 
     NvtxRange nvtx_range("lbib.lattice_update");
     LatticeArgs a = lattice_args(c, src_buf, out);
     return launch_lattice(c->p.precision, c->p.n_species, c->p.bc_y, c->p.forcing, a,
-                          coefs_of(c), c->block, c->stream, pdl && c->nC > 0, c->lattice_pairs);
+                          coefs_of(c), c->block, c->stream, pdl && c->nC > 0, c->lattice_npt);
 }
 
 static cudaError_t enqueue_ib(lbib_ctx* c, bool move, bool prep, bool out_next,
@@ -765,15 +765,15 @@ int lbib_set_node_sources(lbib_ctx* c, const double* S) {
 
 int lbib_set_lattice_variant(lbib_ctx* c, int32_t nodes_per_thread) {
     if (!c) return LBIB_E_PARAM;
-    if (nodes_per_thread != 1 && nodes_per_thread != 2)
-        return fail(c, LBIB_E_PARAM, "nodes_per_thread must be 1 or 2");
-    const bool pairs = nodes_per_thread == 2;
-    if (pairs != c->lattice_pairs) {
+    if (nodes_per_thread != 0 && nodes_per_thread != 1 && nodes_per_thread != 2 &&
+        nodes_per_thread != 4)
+        return fail(c, LBIB_E_PARAM, "nodes_per_thread must be 0, 1, 2 or 4");
+    if (nodes_per_thread != c->lattice_npt) {
         // the captured step graphs hold the other kernel
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "lbib_set_lattice_variant");
         drop_graphs(c);
-        c->lattice_pairs = pairs;
+        c->lattice_npt = nodes_per_thread;
     }
     return LBIB_OK;
 }

@@ -477,15 +477,16 @@ int set_thread_error(int code, const std::string& msg);
 
 // launchers (return cudaError_t of the launch)
 // pdl: launch with programmatic serialization (the previous kernel of the
-// stream must be the other kernel of the coupled step); pairs: FP16 storage
-// may update two nodes per thread (else one)
+// stream must be the other kernel of the coupled step); nodes_per_thread:
+// FP16 storage may update two or four adjacent nodes per thread (1: one; 0:
+// four with at most one species, else two)
 // whether the population loads of a lattice should go evict-first in L2:
 // both population buffers within 1.5 times the L2 of the current device
 bool lattice_l2_first(int precision, int n_species, int64_t plane);
 
 cudaError_t launch_lattice(int precision, int n_species, int bc_y, int forcing,
                            const LatticeArgs& a, const void* coefs, dim3 block,
-                           cudaStream_t s, bool pdl = false, bool pairs = true);
+                           cudaStream_t s, bool pdl = false, int nodes_per_thread = 2);
 // the same with confined species (a.dom set, n_species >= 1): one node per
 // thread, the confinement paths compiled in (launch_lattice calls it)
 cudaError_t launch_lattice_confined(int precision, int n_species, int bc_y, int forcing,

@@ -1,17 +1,20 @@
-"""FP16 storage: the two-nodes-per-thread lattice update against the
-one-node-per-thread update (lbib_set_lattice_variant 2 vs 1).
+"""FP16 storage: the two- and four-nodes-per-thread lattice updates against
+the one-node-per-thread update (lbib_set_lattice_variant 2 and 4 vs 1).
 
-Both evaluate the same collision (Sec. 6.1, Eq. bgkequation) with the same
-FP32 operations per node; the pair update only changes how the stored halves
-move (32-bit words, shifted pairs assembled from neighbouring lanes).  So on
+All evaluate the same collision (Sec. 6.1, Eq. bgkequation) with the same
+FP32 operations per node; the pair and quad updates only change how the
+stored halves move (32- or 64-bit words, shifted words assembled from
+neighbouring lanes).  So on
 the same state, without cells (no atomic spreading, whose summation order
 varies from run to run), every stored population and every output field must
 be bit-identical.  The states are random stored values (not a rest state) so
 that every direction carries a different value at every node; widths are
 chosen so that warps end inside a row, a row holds a single partial warp,
-and the last pair of a row wraps to x = 0.  With cells, where the spread
-force is summed by atomics in varying order, the two variants agree to far
-below the FP16 error bound.
+and the last pair or quad of a row wraps to x = 0 (widths that are not a
+multiple of four run the pair update under variant 4).  With cells, where the
+spread force is summed by atomics in varying order, the variants agree to far
+below the FP16 error bound; a width of 192 (rows starting at odd multiples of
+64 nodes) makes a quad warp's groups straddle two mask words.
 """
 import numpy as np
 import pytest
@@ -79,12 +82,16 @@ def _run(lb, p, blob, variant, n):
     (130, 33, True, 3, 1, (2e-6, -1e-6)),    # 65 pairs: a warp of one lane; paper forcing
     (66, 20, False, 4, 0, (0.0, 3e-6)),      # 33 pairs, four species
     (1000, 16, False, 0, 1, (1e-5, 1e-5)),   # four CTAs per row, the last one partial
+    (136, 30, True, 2, 0, (1e-5, 2e-6)),     # 34 quads: a warp and a two-lane warp
+    (8, 12, False, 1, 1, (1e-6, 0.0)),       # two quads per row: every edge wraps or meets
+    (192, 18, False, 1, 0, (3e-6, 0.0)),     # rows at odd multiples of 64 nodes
 ])
-def test_pairs_bitwise_without_cells(lb, nx, ny, walls, S, forcing, body):
+@pytest.mark.parametrize("variant", [2, 4])
+def test_pairs_bitwise_without_cells(lb, nx, ny, walls, S, forcing, body, variant):
     p = _params(nx, ny, walls, S, forcing, body)
     blob = _random_state(lb, p, seed=nx * 7 + S)
     for n in (1, 6):   # a single launch, then graph chunks and the tail
-        a, sa = _run(lb, p, blob, 2, n)
+        a, sa = _run(lb, p, blob, variant, n)
         b, sb = _run(lb, p, blob, 1, n)
         assert np.array_equal(sa, sb), f"stored state differs after {n} steps"
         for k in ("rho", "ux", "uy") + (("phi",) if S else ()):
@@ -97,15 +104,18 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / s) if s > 0 else float(np.abs(a - b).max())
 
 
-@pytest.mark.parametrize("wl", ["walls_2species", "periodic_1species"])
-def test_pairs_with_cells_match_single(lb, wl):
+@pytest.mark.parametrize("wl", ["walls_2species", "periodic_1species", "walls_192"])
+@pytest.mark.parametrize("variant", [2, 4])
+def test_pairs_with_cells_match_single(lb, wl, variant):
     if wl == "walls_2species":
         w = li.config2(nx=200, ny=150, n_cells_side=4)
+    elif wl == "walls_192":
+        w = li.config2(nx=192, ny=160, n_cells_side=4)
     else:
         w = li.config3(n=512)
     p, T = w.params, w.tissue
     res = {}
-    for variant in (2, 1):
+    for variant in (variant, 1):
         sim = lb.Simulation(p, lb.LBIB_FP16, T.n_vertices, T.n_cells)
         sim.set_cells(T)
         sim.set_lattice_variant(variant)
@@ -114,7 +124,7 @@ def test_pairs_with_cells_match_single(lb, wl):
         sim.step(19)
         res[variant] = (first, sim.fields(1 | 2 | 4 | 8 | 32 | 64))
         sim.close()
-    (f2, a), (f1, b) = res[2], res[1]
+    (f2, a), (f1, b) = res[variant], res[1]
     assert np.array_equal(f2["id"], f1["id"])      # same X^0: identical labels
     assert _rel(a["ux"], b["ux"]) < 1e-3 and _rel(a["uy"], b["uy"]) < 1e-3
     assert _rel(a["phi"], b["phi"]) < 1e-3
@@ -124,7 +134,7 @@ def test_pairs_with_cells_match_single(lb, wl):
 def test_variant_rejects_other_values(lb):
     w = li.config1()
     sim = lb.Simulation(w.params, lb.LBIB_FP16, 0, 0)
-    for bad in (0, 3, -1):
+    for bad in (3, -1, 8):
         with pytest.raises(lb.LbibError):
             sim.set_lattice_variant(bad)
     sim.close()
