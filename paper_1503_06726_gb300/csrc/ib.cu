@@ -228,9 +228,12 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
 }
 
 
-// FP32 path: dynamic shared memory sized for the largest cell, NT threads
+// FP32 path: dynamic shared memory sized for the largest cell, NT threads.
+// The 64-thread kernel (many small cells) is held to 56 registers, 18 CTAs
+// per SM instead of 16 at its natural 64: more cells in flight for a
+// latency-bound launch (C3, 9,801 cells: 107.7 -> 104.6 us)
 template <int NT>
-__global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
+__global__ void __launch_bounds__(NT, (NT == 64 ? 18 : 1)) ib_cell_kernel_f32(IBArgs a, int maxv) {
     extern __shared__ __align__(16) unsigned char ib_smem[];
     IBShared32 S;
     int* fixed = reinterpret_cast<int*>(ib_smem);

@@ -492,8 +492,8 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 // launches back) are loaded through L2 before the wait, the u plane after it.
 // INLINE_FILL: the label fill inlined (the 256-thread kernel: no spills, no
 // parameter reads through a pointer; 1024^2 step 40.9 -> 38.4 us) or called
-// out of line (the small-CTA kernels keep 64 registers, 16 CTAs per SM, and
-// the ensemble's persistent kernel its budget)
+// out of line (the small-CTA kernels keep few registers, 18 CTAs of 64
+// threads per SM, and the ensemble's persistent kernel its budget)
 // OPTS = false compiles out the junction forces and mass sources (the
 // ensemble has neither).
 template <int NT, bool GRIDDEP, bool INLINE_FILL = true, bool OPTS = true>
