@@ -228,12 +228,9 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
 }
 
 
-// FP32 path: dynamic shared memory sized for the largest cell, NT threads.
-// The 64-thread kernel (many small cells) is held to 56 registers, 18 CTAs
-// per SM instead of 16 at its natural 64: more cells in flight for a
-// latency-bound launch (C3, 9,801 cells: 107.7 -> 104.6 us)
+// FP32 path: dynamic shared memory sized for the largest cell, NT threads
 template <int NT>
-__global__ void __launch_bounds__(NT, (NT == 64 ? 18 : 1)) ib_cell_kernel_f32(IBArgs a, int maxv) {
+__device__ __forceinline__ void ib_f32_body(const IBArgs& a, int maxv) {
     extern __shared__ __align__(16) unsigned char ib_smem[];
     IBShared32 S;
     int* fixed = reinterpret_cast<int*>(ib_smem);
@@ -248,6 +245,19 @@ __global__ void __launch_bounds__(NT, (NT == 64 ? 18 : 1)) ib_cell_kernel_f32(IB
     ib_cell_f32<NT, true, NT == 256>(a, blockIdx.x, S, threadIdx.x, 0);
 }
 
+// the 128- and 256-thread kernels at the registers the compiler chooses
+template <int NT>
+__global__ void __launch_bounds__(NT) ib_cell_kernel_f32(IBArgs a, int maxv) {
+    ib_f32_body<NT>(a, maxv);
+}
+
+// the 64-thread kernel (many small cells) held to 56 registers, 18 CTAs per
+// SM instead of 16 at its natural 64: more cells in flight for a
+// latency-bound launch (C3, 9,801 cells: 107.7 -> 104.6 us)
+__global__ void __launch_bounds__(64, 18) ib_cell_kernel_f32_64(IBArgs a, int maxv) {
+    ib_f32_body<64>(a, maxv);
+}
+
 cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_t s, bool pdl) {
     if (a.n_cells <= 0) return cudaSuccess;
     if (precision == LBIB_FP64)
@@ -259,7 +269,7 @@ cudaError_t launch_ib(int precision, const IBArgs& a, int maxv_cell, cudaStream_
     maxv = (maxv + 7) / 8 * 8;
     const size_t smem = kIBSmemFixed + (size_t)maxv * kIBSmemPerVertex;
     if (maxv <= 64 && a.n_cells >= 2048)
-        return launch_kernel(ib_cell_kernel_f32<64>, dim3(a.n_cells), dim3(64), smem, s, pdl, a,
+        return launch_kernel(ib_cell_kernel_f32_64, dim3(a.n_cells), dim3(64), smem, s, pdl, a,
                              maxv);
     if (maxv <= 128 && a.n_cells >= 2048)
         return launch_kernel(ib_cell_kernel_f32<128>, dim3(a.n_cells), dim3(128), smem, s, pdl, a,
