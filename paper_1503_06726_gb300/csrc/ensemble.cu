@@ -138,19 +138,8 @@ __global__ void __launch_bounds__(kIBThreads, 3) ensemble_kernel(EnsArgs e) {
     const int tid = threadIdx.x;
     const int cgroups = kIBThreads / e.cell_threads;
     const int half = tid / e.cell_threads, htid = tid % e.cell_threads;
-    IBShared32 view;
-    {
-        unsigned char* base = ens_smem + (size_t)half * ens_cell_smem(e.maxv);
-        int* fixed = reinterpret_cast<int*>(base);
-        view.rowcnt = fixed;
-        view.thr = fixed + kMaxRows;
-        view.sbox = view.thr + kMaxRows * kMaxCross;
-        view.s_flag = view.sbox + 4;
-        view.sx = reinterpret_cast<double2*>(base + kIBSmemFixed);
-        view.sb = reinterpret_cast<int2*>(view.sx + e.maxv);
-        view.sf = reinterpret_cast<float2*>(view.sb + e.maxv);
-        view.maxv = e.maxv;
-    }
+    const IBShared32 view =
+        ib_shared32_view(ens_smem + (size_t)half * ens_cell_smem(e.maxv), e.maxv);
     if (tid == 0) s_t = -1;
 
     auto load_tissue = [&](int t) {
@@ -277,16 +266,7 @@ __global__ void __launch_bounds__(kLatticeThreads,
 template <int NT>
 __global__ void __launch_bounds__(NT) ens_ib_kernel(EnsArgs e, int move, int prep, int vforce) {
     extern __shared__ __align__(16) unsigned char ens_ib_smem[];
-    IBShared32 view;
-    int* fixed = reinterpret_cast<int*>(ens_ib_smem);
-    view.rowcnt = fixed;
-    view.thr = fixed + kMaxRows;
-    view.sbox = view.thr + kMaxRows * kMaxCross;
-    view.s_flag = view.sbox + 4;
-    view.sx = reinterpret_cast<double2*>(ens_ib_smem + kIBSmemFixed);
-    view.sb = reinterpret_cast<int2*>(view.sx + e.maxv);
-    view.sf = reinterpret_cast<float2*>(view.sb + e.maxv);
-    view.maxv = e.maxv;
+    const IBShared32 view = ib_shared32_view(ens_ib_smem, e.maxv);
     // the tissue's arguments in shared memory (a local copy would live on
     // the stack)
     __shared__ IBArgs ia;

@@ -232,16 +232,7 @@ __global__ void __launch_bounds__(kIBThreads) ib_cell_kernel(IBArgs a) {
 template <int NT>
 __device__ __forceinline__ void ib_f32_body(const IBArgs& a, int maxv) {
     extern __shared__ __align__(16) unsigned char ib_smem[];
-    IBShared32 S;
-    int* fixed = reinterpret_cast<int*>(ib_smem);
-    S.rowcnt = fixed;
-    S.thr = fixed + kMaxRows;
-    S.sbox = S.thr + kMaxRows * kMaxCross;
-    S.s_flag = S.sbox + 4;
-    S.sx = reinterpret_cast<double2*>(ib_smem + kIBSmemFixed);
-    S.sb = reinterpret_cast<int2*>(S.sx + maxv);
-    S.sf = reinterpret_cast<float2*>(S.sb + maxv);
-    S.maxv = maxv;
+    const IBShared32 S = ib_shared32_view(ib_smem, maxv);
     ib_cell_f32<NT, true, NT == 256>(a, blockIdx.x, S, threadIdx.x, 0);
 }
 

@@ -193,6 +193,45 @@ __device__ __forceinline__ void mark_row(const IBArgs& a, uint32_t* mask, int64_
     if (LBIB_CHK_INDEX(a.diag, kSiteMask, wd, mask_words(a.plane))) atomicOr(mask + wd, bits);
 }
 
+// OR `bits` into mask word `wd` through the CTA's table of the cell's words
+// (open addressing in shared memory; the word goes to the mask once, at the
+// flush after the spreading); a full table falls back to the global atomic.
+__device__ __forceinline__ void mask_or_table(const IBArgs& a, uint32_t* mask, int64_t wd,
+                                              uint32_t bits, uint32_t* mkey, uint32_t* mval) {
+    if (!LBIB_CHK_INDEX(a.diag, kSiteMask, wd, mask_words(a.plane))) return;
+    const uint32_t k = (uint32_t)wd;
+    uint32_t h = (k * 2654435761u) >> (32 - kMaskTableLog2);
+#pragma unroll 1
+    for (int probe = 0; probe < 16; ++probe) {
+        const uint32_t old = atomicCAS(mkey + h, kMaskEmpty, k);
+        if (old == kMaskEmpty || old == k) {
+            atomicOr(mval + h, bits);
+            return;
+        }
+        h = (h + 1) & (uint32_t)(kMaskTable - 1);
+    }
+    atomicOr(mask + wd, bits);
+}
+
+// mark_row through the table
+__device__ __forceinline__ void mark_row_table(const IBArgs& a, uint32_t* mask, int64_t rowbase,
+                                               const int ix[4], uint32_t* mkey, uint32_t* mval) {
+    if (!mask) return;
+    int64_t wd = -1;
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t g = (rowbase + ix[i]) >> 2;
+        if ((g >> 5) != wd) {
+            if (bits) mask_or_table(a, mask, wd, bits, mkey, mval);
+            wd = g >> 5;
+            bits = 0u;
+        }
+        bits |= 1u << (g & 31);
+    }
+    mask_or_table(a, mask, wd, bits, mkey, mval);
+}
+
 // Mark the groups of the nodes [s, e) of one row (no wrap inside the range)
 // in `mask`: lanes take one 32-group word each.
 __device__ __forceinline__ void mark_range(const IBArgs& a, uint32_t* mask, int64_t rowbase,
@@ -495,8 +534,15 @@ __device__ __forceinline__ float2 spring32(float2 d, float L0, float kk) {
 // out of line (the small-CTA kernels keep few registers, 18 CTAs of 64
 // threads per SM, and the ensemble's persistent kernel its budget)
 // OPTS = false compiles out the junction forces and mass sources (the
-// ensemble has neither).
-template <int NT, bool GRIDDEP, bool INLINE_FILL = true, bool OPTS = true>
+// ensemble has neither).  The force-mask bits go through the cell slot's
+// table of mask words (one global OR per distinct word instead of one per
+// vertex and stencil row: the small-CTA kernels of many cells, whose ORs to
+// shared words throttle the launch; 4096^2, 9,801 cells: IB launch 104 -> 93
+// us), or straight to the mask (the 256-thread kernel of few large cells,
+// where the table's extra barrier lengthens each cell's chain: 1024^2, 400
+// cells, 16.7 -> 22 us with it).
+template <int NT, bool GRIDDEP, bool INLINE_FILL = true, bool OPTS = true,
+          bool MASK_TABLE = (NT <= 128)>
 static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, int tid,
                                    int bar) {
     static_assert(NT % 64 == 0, "CTA size");
@@ -527,6 +573,12 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
     }
 
     for (int r = tid; r < kMaxRows; r += NT) rowcnt[r] = 0;
+    if (MASK_TABLE) {
+        for (int i = tid; i < kMaskTable; i += NT) {
+            S.mkey[i] = kMaskEmpty;
+            S.mval[i] = 0u;
+        }
+    }
     if (tid == 0) {
         sbox[0] = INT_MAX; sbox[1] = INT_MIN; sbox[2] = INT_MAX; sbox[3] = INT_MIN;
         s_flag = 0;
@@ -770,7 +822,10 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
 #pragma unroll
                         for (int i = 0; i < 4; ++i) spread_add(a, &row[ix[i]], cx4[i], cy4[i]);
                     }
-                    mark_row(a, a.fmask, (int64_t)J * a.pitch, ix);
+                    if (MASK_TABLE)
+                        mark_row_table(a, a.fmask, (int64_t)J * a.pitch, ix, S.mkey, S.mval);
+                    else
+                        mark_row(a, a.fmask, (int64_t)J * a.pitch, ix);
                 }
             }
         }
@@ -805,6 +860,14 @@ static __device__ void ib_cell_f32(const IBArgs& a, int c, const IBShared32& S, 
                 else
                     s_flag = 1;
             }
+        }
+    }
+    // every distinct force-mask word of the cell into the mask, once
+    if (MASK_TABLE && a.do_force && a.fmask) {
+        cell_sync<NT>(bar);
+        for (int i = tid; i < kMaskTable; i += NT) {
+            const uint32_t k = S.mkey[i];
+            if (k != kMaskEmpty) atomicOr(a.fmask + k, S.mval[i]);
         }
     }
     if (!labels) return;  // uniform over the CTA

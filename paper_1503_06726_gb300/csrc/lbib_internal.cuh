@@ -338,12 +338,40 @@ struct IBShared32 {
     int* thr;     // kMaxRows * kMaxCross
     int* sbox;    // 4
     int* s_flag;  // 1
+    // the cell's force-mask words (kMaskTable keys and bits): the spreading
+    // ORs its group bits here and the CTA then ORs each distinct word into
+    // the mask once
+    uint32_t* mkey;
+    uint32_t* mval;
     int maxv;
 };
 
+constexpr int kMaskTableLog2 = 8;
+constexpr int kMaskTable = 1 << kMaskTableLog2;
+constexpr uint32_t kMaskEmpty = 0xFFFFFFFFu;
+
 // fixed part of the FP32 IB kernel's dynamic shared memory (bytes, 16-aligned)
-constexpr int kIBSmemFixed = ((kMaxRows + kMaxRows * kMaxCross + 4 + 1) * 4 + 15) / 16 * 16;
+constexpr int kIBSmemFixed =
+    ((kMaxRows + kMaxRows * kMaxCross + 4 + 1 + 2 * kMaskTable) * 4 + 15) / 16 * 16;
 constexpr int kIBSmemPerVertex = 16 + 8 + 8;
+
+// the views of one cell slot of that shared memory (fixed part, then maxv
+// vertices)
+__device__ __forceinline__ IBShared32 ib_shared32_view(unsigned char* base, int maxv) {
+    IBShared32 v;
+    int* fixed = reinterpret_cast<int*>(base);
+    v.rowcnt = fixed;
+    v.thr = fixed + kMaxRows;
+    v.sbox = v.thr + kMaxRows * kMaxCross;
+    v.s_flag = v.sbox + 4;
+    v.mkey = reinterpret_cast<uint32_t*>(v.s_flag + 1);
+    v.mval = v.mkey + kMaskTable;
+    v.sx = reinterpret_cast<double2*>(base + kIBSmemFixed);
+    v.sb = reinterpret_cast<int2*>(v.sx + maxv);
+    v.sf = reinterpret_cast<float2*>(v.sb + maxv);
+    v.maxv = maxv;
+    return v;
+}
 
 // a static shared-memory block for the largest cells (the persistent kernel)
 struct IBSmem32 {
