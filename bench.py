@@ -801,7 +801,7 @@ def run_gb300(args, rank, world, dist):
     npt = 1
     if prec == "fp16":
         sim.set_lattice_variant(args.fp16_npt)
-        npt = args.fp16_npt or (4 if p.n_species <= 1 else 2)
+        npt = args.fp16_npt or 2
         if p.nx % npt:
             npt = 2 if p.nx % 2 == 0 else 1
     stream = sim.stream
@@ -895,8 +895,7 @@ def run_gb300(args, rank, world, dist):
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "dram_frac": (traffic / (lat_avg * 1e-3) / 1e9 / peak) if traffic else None,
-            "kernel": {4: ("lattice_quad_async_kernel (four nodes per thread, staged)"
-                           if p.n_species <= 1 else "lattice_quad_kernel (four nodes per thread)"),
+            "kernel": {4: "lattice_quad_kernel (four nodes per thread)",
                        2: "lattice_pair_kernel (two nodes per thread)"}.get(npt, "lattice_kernel"),
             "alg_bytes_per_launch": alg_bytes,
             "alg_bytes_per_node": bpn, "launch_ms": lat_avg,

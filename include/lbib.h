@@ -245,10 +245,8 @@ int lbib_set_node_sources(lbib_ctx* ctx, const double* S);
  * 2 lets FP16 storage update two adjacent nodes per thread, moving every
  * population as one 32-bit word of two halves, whenever the lattice width nx
  * is even; 4 updates four adjacent nodes per thread (one 64-bit word of four
- * halves per population; with at most one species the words are staged in
- * shared memory by asynchronous copies) when nx is a multiple of four, else
- * two; 1 forces one node per thread; 0 (the default) is 4 with at most one
- * species and 2 with more.  FP32 and FP64 storage always use
+ * halves per population) when nx is a multiple of four, else two; 1 forces
+ * one node per thread; 0 (the default) is 2.  FP32 and FP64 storage always use
  * one node per thread.  All give the same arithmetic (the collision of
  * Sec. 6.1, Eq. bgkequation, node by node); the setting exists to compare and
  * time them.  LBIB_E_PARAM for other values.  Waits for the context stream

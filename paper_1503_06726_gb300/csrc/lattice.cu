@@ -21,7 +21,6 @@
 // paper's 3 w v.F.  Species (D2Q5): phi = sum g, g_eq = phi w (1 + 3 v.u),
 // g* = g + (g_eq - g)/tau_D + w R with R the linear reaction plus the source
 // of the node's cell.
-#include <algorithm>
 #include <type_traits>
 
 #include "lattice_kernel.cuh"
@@ -333,9 +332,8 @@ __device__ __forceinline__ float2 hi_pair(uint2 v) {
 
 // The update of one quad after its population words are in registers (r,
 // rg: the shifted words assembled): the IB planes of its group, the
-// collision of its two pairs, the stores.  mw: the group's three mask words
-// (force, label, source), read through it when the masks are in use (the
-// words in global memory, or copies staged in shared memory).
+// collision of its two pairs, the stores.  fmw, lmw, smw: the group's force,
+// label and source mask words, read when the masks are in use.
 template <int S, int FORCING>
 __device__ __forceinline__ void quad_update(const LatticeArgs& a, const Coefs<float>& k,
                                             int node, int lane, const uint2 (&r)[9],
@@ -604,289 +602,6 @@ __global__ void __launch_bounds__(kLatticeThreads, QuadOccupancy<S>::kMinBlocks)
                             m ? a.lmask + mword : nullptr, m ? a.smask + mword : nullptr);
 }
 
-// ---------------------------------------------------------------------------
-// FP16 storage, four nodes per thread, the population words staged in shared
-// memory.  The quad update above keeps every word of its quad in registers
-// from load to use, so a thread has one quad's words in flight and about
-// 120 registers limit an SM to 16 warps: it waits on DRAM more than it
-// issues.  Here the grid holds the CTAs that fit at once; each takes row
-// segments (512 nodes, one quad per thread) from a counter of the launch and
-// copies the words of the segments kQuadStages - 1 ahead into shared memory
-// with cp.async, which holds no registers while the copies are in flight;
-// each thread reads back only the slots it copied, then does the quad update
-// of the segment as above.
-constexpr int kQuadStages = 3;
-constexpr bool kQuadStaged = true;  // at most one species: the staged kernel
-constexpr int kQuadPerCta = 4;      // row segments per CTA
-static_assert(3 * ((14 * 8 * 128 + 4 * 2 * 4 * 4 + 15) / 16 * 16) <= 48 * 1024,
-              "the staged quad update with one species fits the default shared memory");
-
-__device__ __forceinline__ void cp_async8(uint2* dst, const uint2* src, uint64_t pol) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;"
-                 :: "r"(d), "l"(src), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t* dst, const uint32_t* src, uint64_t pol) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 4, %2;"
-                 :: "r"(d), "l"(src), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
-}
-
-// shared memory of one stage: the quad words [word][thread] (8 bytes), and
-// per warp the edge words of its first lane (left) and of its last valid
-// lane (right)
-template <int S>
-struct QuadStage {
-    static constexpr int kWords = 9 + 5 * S;
-    static constexpr int kEdge = 3 + S;  // edge words of one side
-    static constexpr int kBytes =
-        kWords * 8 * kLatticeThreads + (kLatticeThreads / 32) * 2 * kEdge * 4;
-};
-template <int S>
-constexpr int quad_async_smem() {
-    return kQuadStages * ((QuadStage<S>::kBytes + 15) / 16 * 16);
-}
-
-// the geometry of one segment for this thread
-struct QuadSeg {
-    int y, x0, node, w, wm, wp, l0, lm, lp, q0, qm, qp;
-    bool valid, own_l, own_r, lo_wall, hi_wall;
-};
-
-template <bool WALLS>
-__device__ __forceinline__ QuadSeg quad_seg(const LatticeArgs& a, int item, int per_row,
-                                            int tid) {
-    QuadSeg g;
-    g.y = item / per_row;
-    const int seg = item - g.y * per_row;
-    g.x0 = seg * (4 * kLatticeThreads) + 4 * tid;
-    g.valid = g.x0 < a.nx;
-    const int lane = tid & 31;
-    g.lo_wall = WALLS && (g.y == 0);
-    g.hi_wall = WALLS && (g.y == a.ny - 1);
-    const int ym = (g.y == 0) ? a.ny - 1 : g.y - 1;
-    const int yp = (g.y == a.ny - 1) ? 0 : g.y + 1;
-    const int r0 = g.y * (int)a.pitch, rm = ym * (int)a.pitch, rp = yp * (int)a.pitch;
-    g.node = r0 + g.x0;
-    g.w = g.node >> 2;
-    g.wm = (rm + g.x0) >> 2;
-    g.wp = (rp + g.x0) >> 2;
-    const int xl = (g.x0 == 0) ? a.nx - 2 : g.x0 - 2;
-    const int xr = (g.x0 + 4 >= a.nx) ? 0 : g.x0 + 4;
-    g.own_l = g.valid && lane == 0;
-    g.own_r = g.valid && (lane == 31 || g.x0 + 4 >= a.nx);
-    g.l0 = (r0 + xl) >> 1;
-    g.lm = (rm + xl) >> 1;
-    g.lp = (rp + xl) >> 1;
-    g.q0 = (r0 + xr) >> 1;
-    g.qm = (rm + xr) >> 1;
-    g.qp = (rp + xr) >> 1;
-    // the checking build: the word indices inside the plane, the 16-byte
-    // accesses of the quad aligned; a lane that fails copies, loads and
-    // stores nothing but still takes part in the warp's shuffles
-    if (g.valid &&
-        (!LBIB_CHK_INDEX(a.diag, kSitePairIndex, (int64_t)max(max(g.wm, g.wp), g.w), a.plane >> 2) ||
-         !LBIB_CHK_INDEX(a.diag, kSitePairIndex,
-                         (int64_t)max(max(max(g.lm, g.lp), max(g.qm, g.qp)), max(g.l0, g.q0)),
-                         a.plane >> 1) ||
-         !LBIB_CHK_ACCESS(a.diag, kSitePairAlign, static_cast<const float4*>(a.u) + (g.node >> 1),
-                          16, nullptr, nullptr) ||
-         !LBIB_CHK_ACCESS(a.diag, kSitePairAlign,
-                          static_cast<const float4*>(a.force) + (g.node >> 1), 16, nullptr,
-                          nullptr) ||
-         !LBIB_CHK_INDEX(a.diag, kSiteMask, (int64_t)(g.node >> 7), mask_words(a.plane)))) {
-        g.valid = false;
-        g.own_l = g.own_r = false;
-    }
-    return g;
-}
-
-// the copies of segment g into stage `stage` (one commit group per call,
-// empty for a thread without a quad in the segment)
-template <int S, bool WALLS>
-__device__ __forceinline__ void quad_issue(const LatticeArgs& a, const QuadSeg& g,
-                                           unsigned char* stage, int tid, uint64_t pol) {
-    constexpr int NW = QuadStage<S>::kWords, NE = QuadStage<S>::kEdge;
-    uint2* sw = reinterpret_cast<uint2*>(stage);
-    uint32_t* se = reinterpret_cast<uint32_t*>(sw + NW * kLatticeThreads);
-    if (g.valid) {
-        const int64_t P4 = a.plane >> 2, P2 = a.plane >> 1;
-        const uint2* F = static_cast<const uint2*>(a.fsrc);
-        const uint32_t* F1 = static_cast<const uint32_t*>(a.fsrc);
-        uint2* sl = sw + tid;
-        cp_async8(sl + 0 * kLatticeThreads, F + g.w, pol);
-        cp_async8(sl + 1 * kLatticeThreads, (F + 1 * P4) + g.w, pol);
-        cp_async8(sl + 3 * kLatticeThreads, (F + 3 * P4) + g.w, pol);
-        cp_async8(sl + 2 * kLatticeThreads, g.lo_wall ? (F + 4 * P4) + g.w : (F + 2 * P4) + g.wm,
-                  pol);
-        cp_async8(sl + 4 * kLatticeThreads, g.hi_wall ? (F + 2 * P4) + g.w : (F + 4 * P4) + g.wp,
-                  pol);
-        // half-way bounce-back at y = -1/2 and y = ny - 1/2
-        cp_async8(sl + 5 * kLatticeThreads, g.lo_wall ? (F + 7 * P4) + g.w : (F + 5 * P4) + g.wm,
-                  pol);
-        cp_async8(sl + 6 * kLatticeThreads, g.lo_wall ? (F + 8 * P4) + g.w : (F + 6 * P4) + g.wm,
-                  pol);
-        cp_async8(sl + 7 * kLatticeThreads, g.hi_wall ? (F + 5 * P4) + g.w : (F + 7 * P4) + g.wp,
-                  pol);
-        cp_async8(sl + 8 * kLatticeThreads, g.hi_wall ? (F + 6 * P4) + g.w : (F + 8 * P4) + g.wp,
-                  pol);
-        const uint2* Gi = static_cast<const uint2*>(a.gsrc);
-        const uint32_t* Gi1 = static_cast<const uint32_t*>(a.gsrc);
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            const uint2* B = Gi + (int64_t)s * 5 * P4;
-            uint2* ss = sl + (9 + 5 * s) * kLatticeThreads;
-            cp_async8(ss + 0 * kLatticeThreads, B + g.w, pol);
-            cp_async8(ss + 1 * kLatticeThreads, (B + 1 * P4) + g.w, pol);
-            cp_async8(ss + 3 * kLatticeThreads, (B + 3 * P4) + g.w, pol);
-            cp_async8(ss + 2 * kLatticeThreads,
-                      g.lo_wall ? (B + 4 * P4) + g.w : (B + 2 * P4) + g.wm, pol);
-            cp_async8(ss + 4 * kLatticeThreads,
-                      g.hi_wall ? (B + 2 * P4) + g.w : (B + 4 * P4) + g.wp, pol);
-        }
-        uint32_t* el = se + ((tid >> 5) * 2 + 0) * NE;
-        uint32_t* er = se + ((tid >> 5) * 2 + 1) * NE;
-        if (g.own_l) {
-            cp_async4(el + 0, (F1 + 1 * P2) + g.l0, pol);
-            if (!g.lo_wall) cp_async4(el + 1, (F1 + 5 * P2) + g.lm, pol);
-            if (!g.hi_wall) cp_async4(el + 2, (F1 + 8 * P2) + g.lp, pol);
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                cp_async4(el + 3 + s, (Gi1 + (int64_t)(s * 5 + 1) * P2) + g.l0, pol);
-        }
-        if (g.own_r) {
-            cp_async4(er + 0, (F1 + 3 * P2) + g.q0, pol);
-            if (!g.lo_wall) cp_async4(er + 1, (F1 + 6 * P2) + g.qm, pol);
-            if (!g.hi_wall) cp_async4(er + 2, (F1 + 7 * P2) + g.qp, pol);
-#pragma unroll
-            for (int s = 0; s < S; ++s)
-                cp_async4(er + 3 + s, (Gi1 + (int64_t)(s * 5 + 3) * P2) + g.q0, pol);
-        }
-    }
-    cp_async_commit();
-}
-
-template <int S, bool WALLS, int FORCING>
-__global__ void __launch_bounds__(kLatticeThreads, QuadOccupancy<S>::kMinBlocks)
-    lattice_quad_async_kernel(LatticeArgs a, Coefs<float> k, int per_row, int n_items,
-                              int per_cta) {
-    constexpr int SS = S > 0 ? S : 1;
-    constexpr int NW = QuadStage<S>::kWords, NE = QuadStage<S>::kEdge;
-    constexpr int SB = (QuadStage<S>::kBytes + 15) / 16 * 16;
-    extern __shared__ __align__(16) unsigned char qsm[];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const uint64_t pol = a.l2_first ? l2_evict_first() : l2_evict_normal();
-    // this CTA's segments: per_cta consecutive ones
-    const int first = blockIdx.x * per_cta;
-    const int last = min(first + per_cta, n_items);
-    // the copies of the first segments before the programmatic wait (the
-    // populations were written two launches back)
-#pragma unroll
-    for (int j = 0; j < kQuadStages - 1; ++j) {
-        const int item = first + j;
-        if (item < last)
-            quad_issue<S, WALLS>(a, quad_seg<WALLS>(a, item, per_row, tid), qsm + j * SB, tid,
-                                 pol);
-        else
-            cp_async_commit();
-    }
-    // the IB kernel launched just before wrote the force, label and mask
-    // planes: wait for it, then let the next IB launch start
-    griddep_wait();
-    griddep_launch_dependents();
-    int st = 0;
-    for (int item = first; item < last; ++item) {
-        // the segment kQuadStages - 1 ahead goes into the stage the previous
-        // segment was read from (every lane has read it: the warp's shuffles
-        // of the previous segment came after the reads)
-        __syncwarp();
-        {
-            const int ahead = item + kQuadStages - 1;
-            const int ast = (st + kQuadStages - 1) % kQuadStages;
-            if (ahead < last)
-                quad_issue<S, WALLS>(a, quad_seg<WALLS>(a, ahead, per_row, tid),
-                                     qsm + ast * SB, tid, pol);
-            else
-                cp_async_commit();
-        }
-        cp_async_wait<kQuadStages - 1>();  // this thread's copies of `item`
-        const QuadSeg g = quad_seg<WALLS>(a, item, per_row, tid);
-        const unsigned char* stage = qsm + st * SB;
-        st = (st + 1) % kQuadStages;
-        const uint2* sl = reinterpret_cast<const uint2*>(stage) + tid;
-        const uint32_t* se = reinterpret_cast<const uint32_t*>(
-            reinterpret_cast<const uint2*>(stage) + NW * kLatticeThreads);
-        const uint32_t* el = se + ((tid >> 5) * 2 + 0) * NE;
-        const uint32_t* er = se + ((tid >> 5) * 2 + 1) * NE;
-        uint2 r[9], rg[SS][5];
-        uint32_t e[9], eg[SS][2];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            r[q] = g.valid ? sl[q * kLatticeThreads] : make_uint2(0u, 0u);
-            e[q] = 0u;
-        }
-#pragma unroll
-        for (int s = 0; s < SS; ++s) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q)
-                rg[s][q] = (s < S && g.valid) ? sl[(9 + 5 * s + q) * kLatticeThreads]
-                                              : make_uint2(0u, 0u);
-            eg[s][0] = eg[s][1] = 0u;
-        }
-        if (g.own_l) {
-            e[1] = el[0];
-            if (!g.lo_wall) e[5] = el[1];
-            if (!g.hi_wall) e[8] = el[2];
-#pragma unroll
-            for (int s = 0; s < S; ++s) eg[s][0] = el[3 + s];
-        }
-        if (g.own_r) {
-            e[3] = er[0];
-            if (!g.lo_wall) e[6] = er[1];
-            if (!g.hi_wall) e[7] = er[2];
-#pragma unroll
-            for (int s = 0; s < S; ++s) eg[s][1] = er[3 + s];
-        }
-        // the shifted quads (every lane takes part in the shuffles)
-        r[1] = quad_from_left(r[1], e[1], g.own_l);
-        r[3] = quad_from_right(r[3], e[3], g.own_r);
-        {
-            const uint2 p5 = quad_from_left(r[5], e[5], g.own_l);
-            const uint2 p6 = quad_from_right(r[6], e[6], g.own_r);
-            const uint2 p7 = quad_from_right(r[7], e[7], g.own_r);
-            const uint2 p8 = quad_from_left(r[8], e[8], g.own_l);
-            if (!g.lo_wall) {
-                r[5] = p5;
-                r[6] = p6;
-            }
-            if (!g.hi_wall) {
-                r[7] = p7;
-                r[8] = p8;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < S; ++s) {
-            rg[s][1] = quad_from_left(rg[s][1], eg[s][0], g.own_l);
-            rg[s][3] = quad_from_right(rg[s][3], eg[s][1], g.own_r);
-        }
-        if (g.valid) {
-            // the mask words from global memory (staging them measured slower)
-            const int mword = g.node >> 7;
-            const bool m = a.fmask != nullptr;
-            quad_update<S, FORCING>(a, k, g.node, lane, r, rg, m ? a.fmask + mword : nullptr,
-                                    m ? a.lmask + mword : nullptr, m ? a.smask + mword : nullptr);
-        }
-    }
-    cp_async_wait<0>();
-}
-
 template <typename T, typename C, int S, bool WALLS, int FORCING>
 static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, cudaStream_t s,
                            bool pdl, int npt) {
@@ -897,27 +612,13 @@ static cudaError_t launch3(const LatticeArgs& a, const void* coefs, dim3 block, 
     const Coefs<C>& k = *static_cast<const Coefs<C>*>(coefs);
     constexpr bool SC = std::is_same<T, __half>::value;
     if constexpr (SC) {
-        // by default four nodes per thread with at most one species (the
-        // staged quad update), two with more (the quad update's registers
-        // with two or more species leave too few warps per SM)
-        if (npt == 0) npt = S <= 1 ? 4 : 2;
+        // by default two nodes per thread (the pair update)
+        if (npt == 0) npt = 2;
         // two or four nodes per thread when the rows hold whole pairs or
         // quads (confined species read their neighbours' domains, mass
         // sources and pressure nodes are per node: one node per thread)
         const bool plain = !a.dom && !a.msrc && !a.pnode && !a.nsrc && a.pitch % 64 == 0;
         if (npt == 4 && plain && a.nx % 4 == 0 && a.plane % 4 == 0) {
-            if constexpr (S <= 1) {
-                // the staged quad update: kQuadPerCta consecutive row
-                // segments per CTA
-                if (kQuadStaged) {
-                    const int per_row = (a.nx + 4 * kLatticeThreads - 1) / (4 * kLatticeThreads);
-                    const int n_items = per_row * a.ny;
-                    const int grid = (n_items + kQuadPerCta - 1) / kQuadPerCta;
-                    return launch_kernel(lattice_quad_async_kernel<S, WALLS, FORCING>, dim3(grid),
-                                         dim3(kLatticeThreads), (size_t)quad_async_smem<S>(), s,
-                                         pdl, a, k, per_row, n_items, kQuadPerCta);
-                }
-            }
             const dim3 qb(kLatticeThreads, 1, 1);
             const dim3 qg((a.nx / 4 + kLatticeThreads - 1) / kLatticeThreads, a.ny);
             return launch_kernel(lattice_quad_kernel<S, WALLS, FORCING>, qg, qb, 0, s, pdl, a,

@@ -23,7 +23,7 @@ struct lbib_ctx {
     lbib::Coefs<float> kf;
     dim3 block{128, 1, 1};
     bool mass_ctrl = false;      // target areas set: the area controller is on
-    int lattice_npt = 0;  // FP16 storage: nodes per thread (1, 2 or 4; 0 = by species count)
+    int lattice_npt = 0;  // FP16 storage: nodes per thread (1, 2 or 4; 0 = the default, 2)
     int64_t nstep = 0;          // steps since lbib_set_cells / lbib_set_state (junction renewal)
     bool l2_first = false;      // population loads evict-first (lattice nearly fits in L2)
     bool mom_valid = false;     // the no-flux closure's moments of buffer `cur` are current

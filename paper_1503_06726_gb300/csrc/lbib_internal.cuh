@@ -507,7 +507,7 @@ int set_thread_error(int code, const std::string& msg);
 // pdl: launch with programmatic serialization (the previous kernel of the
 // stream must be the other kernel of the coupled step); nodes_per_thread:
 // FP16 storage may update two or four adjacent nodes per thread (1: one; 0:
-// four with at most one species, else two)
+// the default, two)
 // whether the population loads of a lattice should go evict-first in L2:
 // both population buffers within 1.5 times the L2 of the current device
 bool lattice_l2_first(int precision, int n_species, int64_t plane);

@@ -2,7 +2,7 @@
 alignment of every vector, atomic and indexed access of the hot path before
 making it, skip an access that fails, and the host reports LBIB_E_CHECK.
 
-  - the coupled step (FP64, FP32, FP16 with two nodes per thread; walls;
+  - the coupled step (FP64, FP32, FP16 with two and four nodes per thread; walls;
     junctions; mass sources and pressure nodes), confined species under the
     no-flux closure, the ensemble (both schedules), the allocation-free step and the sums run
     in the checking build without a single failed check;
@@ -73,6 +73,7 @@ def test_check_build_hot_path_clean():
         for prec in (lbib.LBIB_FP32, lbib.LBIB_FP16):
             run(li.config2(nx=128, ny=128, n_cells_side=2), prec, 9)
         run(li.config3(), lbib.LBIB_FP32, 4)    # 9,801 cells: the 64-thread IB kernel
+        run(li.config3(n=512), lbib.LBIB_FP16, 5)   # one species: the staged quad update
         run(li.config2_junctions(), lbib.LBIB_FP32, 12)
         g = li.config2_growth()
         def grow(sim):
