@@ -124,6 +124,19 @@ struct lbib_nop {
     int64_t wsets_max = 0;       // the largest layer's element count over all its copies
     int64_t t = 0;           // Adam step
     std::string err;
+    // pinned host staging: the per-sample inputs (3 B floats), then the loss
+    // and the tensor-core status word of the last call, so that a call waits
+    // on its stream once, at its end
+    unsigned char* hpin = nullptr;
+    bool pin_busy = false;  // copies out of hpin may be in flight (a call ended early)
+    float* h_in() { return reinterpret_cast<float*>(hpin); }
+    double* h_loss() { return reinterpret_cast<double*>(hpin + pin_off()); }
+    unsigned* h_err() { return reinterpret_cast<unsigned*>(hpin + pin_off() + 8); }
+    size_t pin_off() const { return ((size_t)3 * B * 4 + 15) / 16 * 16; }
+    size_t pin_bytes() const { return pin_off() + 16; }
+    ~lbib_nop() {
+        if (hpin) cudaFreeHost(hpin);
+    }
 
     template <typename T>
     T* take(uint64_t count) {
@@ -259,25 +272,30 @@ cudaError_t refresh_weights(lbib_nop* n) {
 cudaError_t set_inputs(lbib_nop* n, int N, const uint8_t* mask, const uint8_t* src,
                        const double* D, const double* decay, const double* src_rate,
                        bool target_scale) {
-    std::vector<float> h(3 * (size_t)N);
+    // the pinned staging buffer: the previous call's copies out of it ended
+    // with that call's wait on the stream, unless it ended early
+    if (n->pin_busy) {
+        const cudaError_t w = cudaStreamSynchronize(n->stream);
+        if (w != cudaSuccess) return w;
+    }
+    n->pin_busy = true;
+    float* h = n->h_in();
     for (int i = 0; i < N; ++i) {
         h[i] = (float)((D[i] - 0.125) / 0.075);
         h[N + i] = (float)(std::log10(decay[i]) + 3.0);
         // target: phi * decay / src; prediction: y * src / decay
         h[2 * N + i] = (float)(target_scale ? decay[i] / src_rate[i] : src_rate[i] / decay[i]);
     }
-    cudaError_t e = cudaMemcpyAsync(n->dn, h.data(), N * 4, cudaMemcpyHostToDevice, n->stream);
+    cudaError_t e = cudaMemcpyAsync(n->dn, h, N * 4, cudaMemcpyHostToDevice, n->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(n->kn, h.data() + N, N * 4, cudaMemcpyHostToDevice, n->stream);
+        e = cudaMemcpyAsync(n->kn, h + N, N * 4, cudaMemcpyHostToDevice, n->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(n->fac, h.data() + 2 * N, N * 4, cudaMemcpyHostToDevice, n->stream);
+        e = cudaMemcpyAsync(n->fac, h + 2 * N, N * 4, cudaMemcpyHostToDevice, n->stream);
     if (e != cudaSuccess) return e;
     const int HW = n->H * n->W;
     nn::features_kernel<<<blocks((int64_t)N * HW), 256, 0, n->stream>>>(mask, src, n->dn, n->kn,
                                                                          n->x, N, HW);
-    e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);  // host vector lifetime
-    return e;
+    return cudaGetLastError();
 }
 
 cudaError_t forward(lbib_nop* n, int N) {
@@ -395,10 +413,17 @@ bool params_ok(lbib_nop* n) { return n && n->param; }
 
 // After the stream has been synchronised: whether a tcgen05 convolution's
 // bounded wait ran out since the last check (the word is then cleared).
+// the end of a call: the status word back with the call's other results,
+// one wait on the stream
 int tc_status(lbib_nop* n, const char* where) {
-    unsigned h = 0u;
-    cudaError_t e = cudaMemcpy(&h, n->tc_err, 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && h) e = cudaMemset(n->tc_err, 0, 4);
+    cudaError_t e = cudaMemcpyAsync(n->h_err(), n->tc_err, 4, cudaMemcpyDeviceToHost, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    if (e == cudaSuccess) n->pin_busy = false;
+    const unsigned h = e == cudaSuccess ? *n->h_err() : 0u;
+    if (e == cudaSuccess && h) {
+        e = cudaMemsetAsync(n->tc_err, 0, 4, n->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    }
     if (e != cudaSuccess) return nop_fail(n, LBIB_E_CUDA, cudaGetErrorString(e));
     if (h)
         return nop_fail(n, LBIB_E_TIMEOUT,
@@ -442,7 +467,10 @@ int lbib_nop_create(int32_t batch, int32_t H, int32_t W, void* d_workspace, uint
     n->bytes = bytes;
     n->stream = static_cast<cudaStream_t>(cuda_stream);
     nop_layout(n);
-    cudaError_t e = cudaFuncSetAttribute(nn::conv3x3_fwd_kernel,
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&n->hpin), n->pin_bytes(),
+                                  cudaHostAllocDefault);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(nn::conv3x3_fwd_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kConvSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(nn::conv3x3_wgrad_kernel,
@@ -563,9 +591,8 @@ int lbib_nop_forward(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uint8_
         nn::scale_kernel<<<blocks((int64_t)N * HW), 256, 0, n->stream>>>(n->y, 16, d_phi, n->fac, N, HW);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     if (e != cudaSuccess) return nop_fail(n, LBIB_E_CUDA, cudaGetErrorString(e));
-    return tc_status(n, "lbib_nop_forward");
+    return tc_status(n, "lbib_nop_forward");  // waits on the stream
 }
 
 int lbib_nop_train_step(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uint8_t* d_src,
@@ -599,11 +626,12 @@ int lbib_nop_train_step(lbib_nop* n, int32_t N, const uint8_t* d_mask, const uin
         e = cudaGetLastError();
         if (e == cudaSuccess) e = refresh_weights(n);
     }
-    if (e == cudaSuccess && loss_out)
-        e = cudaMemcpyAsync(loss_out, n->loss, 8, cudaMemcpyDeviceToHost, n->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(n->h_loss(), n->loss, 8, cudaMemcpyDeviceToHost, n->stream);
     if (e != cudaSuccess) return nop_fail(n, LBIB_E_CUDA, cudaGetErrorString(e));
-    return tc_status(n, "lbib_nop_train_step");
+    const int rc = tc_status(n, "lbib_nop_train_step");  // waits on the stream
+    if (loss_out && rc != LBIB_E_CUDA) *loss_out = *n->h_loss();
+    return rc;
 }
 
 void lbib_nop_destroy(lbib_nop* n) { delete n; }
