@@ -298,6 +298,24 @@ int lbib_get_fields(lbib_ctx* ctx, uint32_t which, double* rho, double* ux, doub
                     double* phi, double* xy, double* area, int32_t* id, double* force,
                     double* vforce);
 
+/* Asynchronous readback of the cell outputs for a pipelined host loop: the
+ * current vertex positions (LBIB_X: xy, 2*V doubles) and/or the FP64 cell
+ * areas (LBIB_AREA: area, n_cells) are copied to the host buffers on a copy
+ * stream of the context, after the work enqueued so far on the context
+ * stream, and the call returns at once.  The steps enqueued afterwards run
+ * beside the copies (the first vertex move of lbib_advance() waits for them;
+ * lbib_step(), lbib_set_cells(), lbib_set_state() and lbib_get_fields()
+ * wait before they start); the buffers must stay valid until
+ * lbib_wait_readback() returns, and should be pinned for the copy to overlap.
+ * One readback is outstanding at a time: a second call first waits for the
+ * previous one and returns its status if that failed.  LBIB_E_PARAM for
+ * other bits in `which` or a NULL buffer that is needed.
+ * lbib_wait_readback() waits for the outstanding readback (LBIB_OK when
+ * there is none) and reports the device diagnostics read with it, as
+ * lbib_get_fields() does (LBIB_E_NONFINITE, LBIB_E_CHECK). */
+int lbib_get_cells_async(lbib_ctx* ctx, uint32_t which, double* xy, double* area);
+int lbib_wait_readback(lbib_ctx* ctx);
+
 /* FP64 conservation sums of the last step's fields (the per-cell and global
  * budgets beside the per-cell area of Sec. 3.3, computeAreas), computed on
  * the device from the output of the last lbib_step() (LBIB_E_STATE after

@@ -624,6 +624,9 @@ int lbib_ensemble_step(lbib_ensemble* e, int32_t n_steps) {
     if (n_steps == 0) return LBIB_OK;
     int items = 0, cells = 0;
     cudaError_t er = ens_upload(e, &items, &cells);
+    // a tissue's pending asynchronous readback ends before its cells move
+    for (auto* c : e->ctx)
+        if (er == cudaSuccess) er = rb_fence(c, e->stream);
     if (er != cudaSuccess)
         return ens_fail(e, LBIB_E_CUDA, std::string("lbib_ensemble_step: ") + cudaGetErrorString(er));
     const unsigned grid = ens_grid(e);

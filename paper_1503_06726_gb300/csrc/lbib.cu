@@ -605,6 +605,10 @@ int lbib_set_cells(lbib_ctx* c, int32_t n_cells, const int32_t* cell_off, const 
                    const uint8_t* src_flag) {
     NvtxRange nvtx_range("lbib_set_cells");
     if (!c) return LBIB_E_PARAM;
+    {
+        const cudaError_t fe = rb_fence(c, c->stream);
+        if (fe != cudaSuccess) return cuda_fail(c, fe, "lbib_set_cells");
+    }
     if (n_cells < 0 || n_cells > c->maxC) return fail(c, LBIB_E_CELLS, "n_cells exceeds capacity");
     if (n_cells > 0 && (!cell_off || !xy)) return fail(c, LBIB_E_CELLS, "cell_off and xy are required");
     int V = n_cells > 0 ? cell_off[n_cells] : 0;
@@ -829,6 +833,10 @@ int lbib_step(lbib_ctx* c, int32_t n_steps) {
     if (!c) return LBIB_E_PARAM;
     if (n_steps < 0) return fail(c, LBIB_E_PARAM, "n_steps must be >= 0");
     if (n_steps == 0) return LBIB_OK;
+    {
+        const cudaError_t fe = rb_fence(c, c->stream);
+        if (fe != cudaSuccess) return cuda_fail(c, fe, "lbib_step");
+    }
     cudaError_t e = ensure_moments(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbib_step");
     const bool ib = c->nC > 0;
@@ -882,12 +890,20 @@ int lbib_advance(lbib_ctx* c, int32_t n_steps) {
     int left = n_steps;
     // an odd count starts with one directly launched step (programmatic after
     // the prep); its IB launch moves, and preps unless it is the only step
+    // a pending readback of the vertex positions and areas runs beside the
+    // prep and the lattice update; the first move waits for it
     if (left % 2 == 1) {
         if (e == cudaSuccess) e = enqueue_lattice(c, c->cur, false, ib);
-        if (e == cudaSuccess && ib) e = enqueue_ib(c, true, left > 1, false, true);
+        if (e == cudaSuccess && ib) {
+            const bool fenced = c->rb_pending;
+            e = rb_fence(c, c->stream);
+            // after an event wait the move is not a programmatic launch
+            if (e == cudaSuccess) e = enqueue_ib(c, true, left > 1, false, !fenced);
+        }
         c->cur = 1 - c->cur;
         --left;
     }
+    if (e == cudaSuccess && left > 0) e = rb_fence(c, c->stream);
     while (e == cudaSuccess && left > 0) {
         cudaGraphExec_t g;
         e = get_chunk_graph(c, c->cur, &g, left == 2);
@@ -904,6 +920,10 @@ int lbib_advance(lbib_ctx* c, int32_t n_steps) {
 int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
     if (!c || !ms_out) return LBIB_E_PARAM;
     if (n_steps <= 0) return fail(c, LBIB_E_PARAM, "n_steps must be > 0");
+    {
+        const cudaError_t fe = rb_fence(c, c->stream);
+        if (fe != cudaSuccess) return cuda_fail(c, fe, "lbib_step_profiled");
+    }
     const bool ib = c->nC > 0;
     const bool junctions = ib && c->p.junction_period > 0;
     // one event before and after every launch: 2 per launch (with junctions
@@ -951,10 +971,32 @@ int lbib_step_profiled(lbib_ctx* c, int32_t n_steps, double* ms_out) {
     return LBIB_OK;
 }
 
+// the status the device-side diagnostic words report (checking build,
+// non-finite fields, blown-up cells)
+static int diag_status(lbib_ctx* c, const uint32_t* diag) {
+    if (diag[kDiagCheck]) {
+        char msg[160];
+        std::snprintf(msg, sizeof(msg),
+                      "checking build: an access failed its bounds or alignment check "
+                      "(site %u, address low bits 0x%08x) and was skipped",
+                      diag[kDiagCheckSite], diag[kDiagCheckAddr]);
+        return fail(c, LBIB_E_CHECK, msg);
+    }
+    if (diag[kDiagNonFinite])
+        return fail(c, LBIB_E_NONFINITE, "a non-finite density or velocity was produced");
+    if (diag[kDiagGeometry])
+        return fail(c, LBIB_E_NONFINITE, "a cell became non-finite or larger than the lattice");
+    return LBIB_OK;
+}
+
 int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double* uy, double* phi,
                     double* xy, double* area, int32_t* id, double* force, double* vforce) {
     NvtxRange nvtx_range("lbib_get_fields");
     if (!c) return LBIB_E_PARAM;
+    {
+        const cudaError_t fe = rb_fence(c, c->stream);
+        if (fe != cudaSuccess) return cuda_fail(c, fe, "lbib_get_fields");
+    }
     const uint32_t lattice_bits = LBIB_RHO | LBIB_U | LBIB_PHI | LBIB_ID | LBIB_FORCE;
     if ((which & lattice_bits) && !c->fields_valid)
         return fail(c, LBIB_E_STATE, "no completed step since the last create or reset");
@@ -1035,19 +1077,64 @@ int lbib_get_fields(lbib_ctx* c, uint32_t which, double* rho, double* ux, double
                 force[2 * ((size_t)y * nx + x)] = val(r_force, 2 * n);
                 force[2 * ((size_t)y * nx + x) + 1] = val(r_force, 2 * n + 1);
             }
-    if (diag[kDiagCheck]) {
-        char msg[160];
-        std::snprintf(msg, sizeof(msg),
-                      "checking build: an access failed its bounds or alignment check "
-                      "(site %u, address low bits 0x%08x) and was skipped",
-                      diag[kDiagCheckSite], diag[kDiagCheckAddr]);
-        return fail(c, LBIB_E_CHECK, msg);
+    return diag_status(c, diag);
+}
+
+// Asynchronous readback of the cell outputs.  The copies run on the
+// context's copy stream after an event of the context stream, so that the
+// steps enqueued afterwards overlap them; every call that writes the vertex
+// positions or the areas orders itself after rb_done (rb_fence).
+int lbib_get_cells_async(lbib_ctx* c, uint32_t which, double* xy, double* area) {
+    NvtxRange nvtx_range("lbib_get_cells_async");
+    if (!c) return LBIB_E_PARAM;
+    if (which & ~(LBIB_X | LBIB_AREA))
+        return fail(c, LBIB_E_PARAM, "lbib_get_cells_async: only LBIB_X and LBIB_AREA");
+    if (((which & LBIB_X) && c->nV > 0 && !xy) || ((which & LBIB_AREA) && c->nC > 0 && !area))
+        return fail(c, LBIB_E_PARAM, "lbib_get_cells_async: NULL output buffer");
+    // one readback at a time: the previous one ends first (its status stands)
+    if (c->rb_pending) {
+        const int rc = lbib_wait_readback(c);
+        if (rc != LBIB_OK) return rc;
     }
-    if (diag[kDiagNonFinite])
-        return fail(c, LBIB_E_NONFINITE, "a non-finite density or velocity was produced");
-    if (diag[kDiagGeometry])
-        return fail(c, LBIB_E_NONFINITE, "a cell became non-finite or larger than the lattice");
+    cudaError_t e = cudaSuccess;
+    if (!c->rb_stream) {
+        e = cudaStreamCreateWithFlags(&c->rb_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->rb_ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->rb_done, cudaEventDisableTiming);
+        if (e == cudaSuccess)
+            e = cudaHostAlloc(reinterpret_cast<void**>(&c->rb_diag), (kDiagCheckAddr + 1) * 4,
+                              cudaHostAllocDefault);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_cells_async");
+    }
+    const Layout& L = c->L;
+    if ((which & LBIB_AREA) && c->nC > 0)
+        e = launch_areas(c->at<double2>(L.xy), c->at<int32_t>(L.off), c->nC, c->at<double>(L.area),
+                         c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->rb_ready, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->rb_stream, c->rb_ready, 0);
+    if (e == cudaSuccess && (which & LBIB_X) && c->nV > 0)
+        e = cudaMemcpyAsync(xy, c->ws + L.xy, (size_t)c->nV * 16, cudaMemcpyDeviceToHost,
+                            c->rb_stream);
+    if (e == cudaSuccess && (which & LBIB_AREA) && c->nC > 0)
+        e = cudaMemcpyAsync(area, c->ws + L.area, (size_t)c->nC * 8, cudaMemcpyDeviceToHost,
+                            c->rb_stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->rb_diag, c->ws + L.diag, (kDiagCheckAddr + 1) * 4,
+                            cudaMemcpyDeviceToHost, c->rb_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->rb_done, c->rb_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_get_cells_async");
+    c->rb_pending = true;
     return LBIB_OK;
+}
+
+int lbib_wait_readback(lbib_ctx* c) {
+    NvtxRange nvtx_range("lbib_wait_readback");
+    if (!c) return LBIB_E_PARAM;
+    if (!c->rb_pending) return LBIB_OK;
+    const cudaError_t e = cudaEventSynchronize(c->rb_done);
+    c->rb_pending = false;
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbib_wait_readback");
+    return diag_status(c, c->rb_diag);
 }
 
 int lbib_get_sizes(const lbib_ctx* c, int32_t* n_vertices, int32_t* n_cells) {
@@ -1107,6 +1194,10 @@ int lbib_get_state(lbib_ctx* c, void* host, uint64_t bytes) {
 
 int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
     if (!c || !host) return LBIB_E_PARAM;
+    {
+        const cudaError_t fe = rb_fence(c, c->stream);
+        if (fe != cudaSuccess) return cuda_fail(c, fe, "lbib_set_state");
+    }
     if (bytes < state_bytes(c)) return fail(c, LBIB_E_PARAM, "state buffer too small");
     const char* h = static_cast<const char*>(host);
     int32_t hdr[4];
@@ -1156,6 +1247,11 @@ int lbib_set_state(lbib_ctx* c, const void* host, uint64_t bytes) {
 
 void lbib_destroy(lbib_ctx* c) {
     if (!c) return;
+    if (c->rb_done) cudaEventSynchronize(c->rb_done);  // a pending readback's copies
+    if (c->rb_stream) cudaStreamDestroy(c->rb_stream);
+    if (c->rb_ready) cudaEventDestroy(c->rb_ready);
+    if (c->rb_done) cudaEventDestroy(c->rb_done);
+    if (c->rb_diag) cudaFreeHost(c->rb_diag);
     drop_graphs(c);
     if (c->hstage_done) {
         cudaEventSynchronize(c->hstage_done);

@@ -38,6 +38,14 @@ struct lbib_ctx {
     char* hstage = nullptr;
     cudaEvent_t hstage_done = nullptr;
     bool hstage_pending = false;
+    // the asynchronous readback of the cell outputs (lbib_get_cells_async):
+    // its copy stream, the events before and after its copies, the pinned
+    // diagnostic words read back with it; while one is pending, work that
+    // writes the vertex positions or the areas first waits for rb_done
+    cudaStream_t rb_stream = nullptr;
+    cudaEvent_t rb_ready = nullptr, rb_done = nullptr;
+    uint32_t* rb_diag = nullptr;
+    bool rb_pending = false;
     std::string err;
 
     template <typename T>
@@ -45,6 +53,11 @@ struct lbib_ctx {
 };
 
 namespace lbib {
+// order the context stream after a pending asynchronous readback (work that
+// writes the vertex positions or the cell areas must not overtake its copies)
+inline cudaError_t rb_fence(lbib_ctx* c, cudaStream_t s) {
+    return c->rb_pending ? cudaStreamWaitEvent(s, c->rb_done, 0) : cudaSuccess;
+}
 // kernel arguments of a context (its buffers, parity src_buf)
 LatticeArgs ctx_lattice_args(lbib_ctx* c, int src_buf, bool out);
 IBArgs ctx_ib_args(lbib_ctx* c, bool move, bool prep, bool out_next);

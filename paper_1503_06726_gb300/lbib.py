@@ -46,6 +46,7 @@ PRECISIONS = {"fp64": LBIB_FP64, "fp32": LBIB_FP32, "fp16": LBIB_FP16}
 # every symbol declared in include/lbib.h
 EXPORTS = (
     "lbib_workspace_size", "lbib_create", "lbib_set_cells", "lbib_set_lattice_variant",
+    "lbib_get_cells_async", "lbib_wait_readback",
     "lbib_set_domains", "lbib_set_mass_sources", "lbib_set_pressure_nodes",
     "lbib_set_node_sources",
     "lbib_set_cell_params",
@@ -117,6 +118,8 @@ def load(path: str = None) -> ctypes.CDLL:
         "lbib_set_cells": (ctypes.c_int, [vp, i32, vp, vp, vp, vp, vp, vp]),
         "lbib_set_cell_params": (ctypes.c_int, [vp, vp, vp]),
         "lbib_set_lattice_variant": (ctypes.c_int, [vp, i32]),
+        "lbib_get_cells_async": (ctypes.c_int, [vp, ctypes.c_uint32, vp, vp]),
+        "lbib_wait_readback": (ctypes.c_int, [vp]),
         "lbib_set_domains": (ctypes.c_int, [vp, vp]),
         "lbib_set_mass_sources": (ctypes.c_int, [vp, vp, vp]),
         "lbib_set_pressure_nodes": (ctypes.c_int, [vp, vp]),
@@ -291,6 +294,19 @@ def lbib_set_node_sources(ctx, S=None):
 
 def lbib_set_lattice_variant(ctx, nodes_per_thread: int):
     _check(load().lbib_set_lattice_variant(ctx, int(nodes_per_thread)), ctx)
+
+
+def lbib_get_cells_async(ctx, which: int, xy_ptr, area_ptr):
+    """Start the asynchronous readback of the vertex positions (LBIB_X) and /
+    or the cell areas (LBIB_AREA) into host buffers given by address (pinned
+    for the copy to overlap the next steps); lbib_wait_readback ends it."""
+    vp = ctypes.c_void_p
+    _check(load().lbib_get_cells_async(ctx, int(which), vp(xy_ptr) if xy_ptr else None,
+                                       vp(area_ptr) if area_ptr else None), ctx)
+
+
+def lbib_wait_readback(ctx):
+    _check(load().lbib_wait_readback(ctx), ctx)
 
 
 def lbib_set_cell_params(ctx, pressure=None, src_flag=None):
